@@ -399,9 +399,12 @@ int64_t ora_contacts(int64_t n, const double *pos, const double *vel, const doub
 /*
  * Eq. (particle_gravity), softened (Plummer, length eps):
  *   F_i = sum_{j != i} G m_i m_j (r_j - r_i) / (|r_j - r_i|^2 + eps^2)^{3/2}.
- * All j != i of the pile are summed, as the equation is written (members of
- * the same aggregate included; exclude_same_agg = 1 drops them, for the
- * identity check that internal pairs change no aggregate total).
+ * exclude_same_agg = 0 sums every j != i of the pile, as the equation is
+ * written.  The step uses exclude_same_agg = 1, which drops the members of
+ * i's own aggregate: inside a rigid body those central pair forces cancel in
+ * both the aggregate force and torque (Eq. agg_gravity, Eq. gravity_torque),
+ * so every aggregate total is the same in exact arithmetic, and the per-sphere
+ * force F_i is then the force from the other aggregates only.
  * rows == NULL computes every sphere; otherwise only the n_rows listed ones,
  * written to F[3*k] for the k-th listed sphere.  Fmag (optional) receives
  * sum_j |F_ij|.
@@ -597,7 +600,7 @@ static int ora_forces(ora_sim *S, const ora_params *P, int want_scales)
     memcpy(S->h_partner, hp_new, sizeof(int32_t) * (size_t)n * S->hcap);
     memcpy(S->h_S, hS_new, sizeof(double) * (size_t)n * S->hcap * 3);
     free(hn_new); free(hp_new); free(hS_new);
-    ora_gravity(n, S->sph_pos, S->m, S->agg_of, P->G, P->eps, 0, 0, NULL, S->Fg, Fmg);
+    ora_gravity(n, S->sph_pos, S->m, S->agg_of, P->G, P->eps, 1, 0, NULL, S->Fg, Fmg);
     for (int64_t i = 0; i < n; ++i) {
         if (P->ext_mass > 0)
             ora_planet_force(S->planet, P->ext_mass, P->G, S->sph_pos + 3 * i, S->m[i], S->Fe + 3 * i);
@@ -715,7 +718,7 @@ int ora_step_sampled(ora_sim *S, const ora_params *P, int64_t n_rows, const int6
     ora_expand(S, h);
     int64_t n = S->n_sph;
     double *Fgm = Fmag ? (double *)malloc(sizeof(double) * (size_t)n_rows) : NULL;
-    ora_gravity(n, S->sph_pos, S->m, S->agg_of, P->G, P->eps, 0, n_rows, rows, Fg, Fgm);
+    ora_gravity(n, S->sph_pos, S->m, S->agg_of, P->G, P->eps, 1, n_rows, rows, Fg, Fgm);
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t k = 0; k < n_rows; ++k) {
         int64_t i = rows[k];
