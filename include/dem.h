@@ -1,0 +1,226 @@
+/*
+ * dem.h -- C ABI of the GB300 library for soft-sphere DEM with rigid
+ * aggregates of bonded spheres and softened self-gravity, after Marohnic et
+ * al., "An efficient numerical approach to modeling the effects of particle
+ * shape on rubble-pile dynamics" (arXiv 2311.11322).
+ *
+ * One library call advances any number of independent rubble piles ("piles")
+ * on one GPU.  A pile is a set of aggregates; an aggregate is a rigid set of
+ * touching spheres.  Each step does, for every pile (paper Sec. 2):
+ *   kick-drift of aggregate COMs and spins (Sec. 2.1 leapfrog, Sec. 2.2.1
+ *   Euler equations), sphere positions and predicted velocities (Sec. 2.2.2,
+ *   Eq. pred-vel), a uniform-cell contact search that skips pairs inside one
+ *   aggregate, spring-dashpot normal / tangential / rolling / twisting contact
+ *   forces at the contact point (Sec. 2.1, 2.2.4, Eq. lever_arm), softened
+ *   direct-sum self-gravity (Sec. 2.2.3, Eq. particle_gravity), reduction of
+ *   sphere forces and torques onto each aggregate (Eq. agg_gravity,
+ *   Eq. gravity_torque, Eq. agg_contact_accel and the contact torque of
+ *   Sec. 2.2.4), and the closing kick.  Optional per-pile external terms: a
+ *   point-mass planet (Sec. 4.2) and a constant spin increment (Sec. 4.1).
+ *
+ * Conventions for every entry point:
+ *   - SI units, double precision at the boundary, row-major [n][3] vectors.
+ *   - Host arrays are owned by the caller and only read (inputs) or written
+ *     (outputs) during the call; the library copies what it keeps.
+ *   - Device memory is owned by the world; it is obtained at add time (never
+ *     inside dem_step) through the allocator set by dem_set_allocator, or
+ *     cudaMalloc by default.
+ *   - All GPU work is issued on the CUDA stream given to dem_create.
+ *   - Every call returns a dem_status; dem_last_error() then holds a one-line
+ *     message.  No C++ exception crosses the ABI and no kernel traps.
+ *   - A world is not thread-safe: one host thread at a time.
+ */
+#ifndef DEM_H
+#define DEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dem_world dem_world;
+
+typedef enum {
+    DEM_OK = 0,
+    DEM_ERR_ARG = 1,       /* invalid argument (NULL, size, non-finite input, unknown id) */
+    DEM_ERR_OOM = 2,       /* device allocation failed or the HBM budget would be exceeded */
+    DEM_ERR_CUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error string) */
+    DEM_ERR_OVERLAP = 4,   /* reserved: overlaps above 10% of a radius are reported as flags */
+    DEM_ERR_SLOTS = 5,     /* a sphere had more contacts than max_contacts history slots */
+    DEM_ERR_NONFINITE = 6, /* a pile's state became NaN or infinite; that pile is frozen */
+    DEM_ERR_TIMEOUT = 7,   /* reserved for bounded device waits */
+    DEM_ERR_STATE = 8      /* call not valid in the current state (e.g. pile removed) */
+} dem_status;
+
+enum { DEM_FP64 = 0, DEM_MIXED = 1 };
+
+/* Per-pile parameters (paper Sec. 2.1; the force-law constants are user inputs). */
+typedef struct {
+    double G;            /* gravitational constant (m^3 kg^-1 s^-2); 0 disables self-gravity */
+    double dt;           /* fixed step h (s) */
+    double kn, kt;       /* normal / tangential spring constants (N/m) */
+    double cn, ct;       /* normal / tangential dashpot constants (N s/m) */
+    double mu_s;         /* sliding (static = dynamic) friction coefficient */
+    double mu_r, mu_t;   /* rolling / twisting friction coefficients */
+    double w0;           /* rolling/twisting regularisation rate (rad/s), > 0 */
+    double eps_soft;     /* Plummer softening length (m) */
+    int32_t precision;   /* DEM_FP64 or DEM_MIXED; all piles of a world must agree */
+    int32_t max_contacts;/* K history slots per sphere, 1..64 */
+    double cell_size;    /* contact cell edge (m); 0 = automatic (>= 2 x largest radius) */
+    double ext_mass;     /* point-mass planet (kg); 0 = none (Sec. 4.2) */
+    double ext_pos[3];   /* planet position at t = 0 (m) */
+    double ext_vel[3];   /* planet velocity at t = 0 (m/s) */
+    double spin_inc[3];  /* spin increment per step (rad/s, space frame); 0 = none (Sec. 4.1) */
+} dem_params;
+
+/* Fields for dem_read_state.  A = aggregates of the pile, N = spheres, K = max_contacts. */
+enum dem_field {
+    DEM_FIELD_COM = 0,         /* A x 3  aggregate COM position r_A (Eq. agg_position) */
+    DEM_FIELD_VEL = 1,         /* A x 3  COM velocity */
+    DEM_FIELD_QUAT = 2,        /* A x 4  orientation (w, x, y, z), body frame = space frame at add time */
+    DEM_FIELD_OMEGA = 3,       /* A x 3  spin, space frame */
+    DEM_FIELD_SPHERE_POS = 4,  /* N x 3  sphere centres r_A + R(q) b_i */
+    DEM_FIELD_FORCE = 5,       /* A x 3  total force of the last step */
+    DEM_FIELD_TORQUE = 6,      /* A x 3  total torque about the COM of the last step */
+    DEM_FIELD_CONTACTS = 7,    /* N x (1 + 4K): count, then K x (partner, Sx, Sy, Sz) */
+    DEM_FIELD_FORCE_CONTACT = 8,   /* A x 3 */
+    DEM_FIELD_TORQUE_CONTACT = 9,  /* A x 3 */
+    DEM_FIELD_FORCE_GRAV = 10,     /* A x 3 */
+    DEM_FIELD_TORQUE_GRAV = 11,    /* A x 3 */
+    DEM_FIELD_FORCE_EXT = 12,      /* A x 3 */
+    DEM_FIELD_TORQUE_EXT = 13,     /* A x 3 */
+    DEM_FIELD_SPHERE_FC = 14,      /* N x 3  contact force on each sphere */
+    DEM_FIELD_SPHERE_TC = 15,      /* N x 3  contact torque on each sphere about its centre */
+    DEM_FIELD_SPHERE_FG = 16,      /* N x 3  gravity on each sphere from other aggregates */
+    DEM_FIELD_ACC = 17,            /* A x 3  stored a_A */
+    DEM_FIELD_PLANET = 18,         /* 9      planet position, velocity, acceleration */
+    DEM_FIELD_MASS = 19,           /* A      aggregate mass (Eq. agg_mass) */
+    DEM_FIELD_BODY_OFFSETS = 20,   /* N x 3  body-frame offsets b_i (never rewritten) */
+    DEM_FIELD_OMEGA_BODY = 21,     /* A x 3  spin, body frame */
+    DEM_FIELD_INFO = 22            /* 16     n_agg, n_sph, steps, flags, nx, ny, nz, cell, ... */
+};
+
+/* Pile flag bits (dem_pile_flags). */
+enum { DEM_FLAG_SLOTS = 1, DEM_FLAG_NONFINITE = 2, DEM_FLAG_OVERLAP = 4 };
+
+/* Kernels that dem_step_profiled can time. */
+enum dem_kernel {
+    DEM_K_AGG_BEGIN = 0, DEM_K_PILE_BEGIN = 1, DEM_K_KEYS = 2, DEM_K_SCAN = 3, DEM_K_SCATTER = 4,
+    DEM_K_CELL_ORDER = 5, DEM_K_GATHER = 6, DEM_K_CONTACT = 7, DEM_K_GRAVITY = 8,
+    DEM_K_AGG_END = 9, DEM_K_PILE_END = 10, DEM_K_COUNT = 11
+};
+
+/*
+ * Device allocator hook.  alloc returns a device pointer (NULL on failure) of
+ * at least `bytes`, usable on `stream`; free releases it.  ctx is passed back.
+ */
+typedef void *(*dem_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*dem_free_fn)(void *ptr, void *ctx);
+
+/*
+ * Create an empty world on the current CUDA device.  cuda_stream: a
+ * cudaStream_t other than the legacy default stream, on which every later
+ * call issues its work (the per-step CUDA graph cannot be captured on the
+ * legacy stream); NULL = the world creates and owns a non-blocking stream.  hbm_budget_bytes: the most device memory the world may
+ * hold (0 = no limit).  *out receives the world.
+ * Errors: DEM_ERR_ARG (out NULL), DEM_ERR_CUDA.
+ */
+dem_status dem_create(void *cuda_stream, size_t hbm_budget_bytes, dem_world **out);
+
+/* Replace the device allocator (call before the first dem_add_aggregates). */
+dem_status dem_set_allocator(dem_world *w, dem_alloc_fn alloc, dem_free_fn free_fn, void *ctx);
+
+/*
+ * Add one pile of n_agg aggregates (paper Sec. 2.2.1).
+ *   spheres_per_agg [n_agg]: sphere count of each aggregate (>= 1);
+ *   sphere_pos [N][3], sphere_radius [N], sphere_density [N]: the spheres in
+ *     aggregate order, N = sum(spheres_per_agg), space frame at t = 0;
+ *   agg_vel, agg_omega [n_agg][3]: COM velocity and spin (space frame), NULL = 0.
+ * The library computes in FP64 on the host each aggregate's mass M = sum m_i
+ * (Eq. agg_mass, m_i = rho 4/3 pi s^3), COM (Eq. agg_position), inertia tensor
+ * about the COM (sphere moments 2/5 m s^2 plus parallel-axis terms) and its
+ * inverse, and the body offsets b_i = r_i - r_A (body frame = space frame at
+ * t = 0, q = identity); b_i are never rewritten.  The stored acceleration and
+ * torque start at zero.  *out_pile_id receives the pile id.
+ * Errors: DEM_ERR_ARG (sizes, non-positive radius/density, non-finite input,
+ * singular inertia, precision differing from earlier piles, max_contacts out
+ * of 1..64), DEM_ERR_OOM (budget or allocation), DEM_ERR_CUDA.
+ */
+dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
+                              const int32_t *spheres_per_agg, const double *sphere_pos,
+                              const double *sphere_radius, const double *sphere_density,
+                              const double *agg_vel, const double *agg_omega,
+                              int32_t *out_pile_id);
+
+/*
+ * Advance piles by n_steps fixed steps (one captured CUDA graph per step).
+ * pile_ids [n_piles] lists the piles to advance; NULL = every live pile.
+ * Asynchronous on the world's stream.  Returns the status of the previous
+ * dem_step call (it waits for that batch's 4-byte flag word per pile): a pile
+ * whose state became non-finite or whose history slots overflowed is frozen
+ * and reported as DEM_ERR_NONFINITE / DEM_ERR_SLOTS once.
+ * Errors: DEM_ERR_ARG (unknown pile id, n_steps < 0), DEM_ERR_CUDA, the above.
+ */
+dem_status dem_step(dem_world *w, const int32_t *pile_ids, int32_t n_piles, int64_t n_steps);
+
+/* Wait for all issued work; returns the status of the last dem_step. */
+dem_status dem_sync(dem_world *w);
+
+/*
+ * Like dem_step with NULL pile_ids, but launches the kernels one by one
+ * (no graph) and records CUDA events on the world's stream around every
+ * launch of kernel `which` (enum dem_kernel).  ms_out [n_steps] receives that
+ * kernel's duration in each step.  Synchronises before returning.
+ */
+dem_status dem_step_profiled(dem_world *w, int64_t n_steps, int32_t which, float *ms_out);
+
+/*
+ * Copy one field of a pile to host_out (n_out doubles, see enum dem_field for
+ * the layout); synchronises the stream first.
+ * Errors: DEM_ERR_ARG (unknown pile/field, n_out too small), DEM_ERR_CUDA.
+ */
+dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *host_out,
+                          int64_t n_out);
+
+/* Flag bits (DEM_FLAG_*) raised so far for a pile; synchronises. */
+dem_status dem_pile_flags(dem_world *w, int32_t pile_id, int32_t *flags_out);
+
+/* Remove a pile and release its share of device memory (compacts the rest). */
+dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
+
+/*
+ * Tuning knobs (normally chosen by dem_autotune).  key: "grav_block"
+ * (threads per gravity block: 64, 128 or 256), "grav_ib" (i-spheres per
+ * thread: 1 or 2), "grav_jchunk" (j-spheres per gravity work item, 0 = all),
+ * "cell_factor" (cell edge / (2 x largest radius), >= 1).  Invalidates the
+ * captured graph.
+ */
+dem_status dem_set_tuning(dem_world *w, const char *key, double value);
+
+/*
+ * Time a few candidate gravity shapes and cell factors on the current piles
+ * (running `trial_steps` real steps per candidate, so the state advances) and
+ * keep the fastest.  best_ms_out (may be NULL) receives its step time.
+ */
+dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out);
+
+/* Device bytes one pile of this size needs (state, sorted copies, cells, history). */
+size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contacts,
+                           int32_t precision);
+
+/* Device bytes the world holds now. */
+size_t dem_world_bytes(const dem_world *w);
+
+/* Message of the last failed call on this world (never NULL). */
+const char *dem_last_error(const dem_world *w);
+
+/* Release everything (waits for the stream). NULL is allowed. */
+void dem_destroy(dem_world *w);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEM_H */

@@ -64,7 +64,8 @@ class _Sim(C.Structure):
                 ("NA_g", C.c_void_p), ("FA_e", C.c_void_p), ("NA_e", C.c_void_p),
                 ("planet", C.c_void_p), ("scaleF", C.c_void_p), ("scaleN", C.c_void_p),
                 ("pairs", C.c_void_p), ("pair_x", C.c_void_p), ("pair_cap", C.c_int64),
-                ("n_pairs", C.c_int64)]
+                ("n_pairs", C.c_int64), ("sph_Fmc", C.c_void_p), ("sph_Tmc", C.c_void_p),
+                ("sph_Fmg", C.c_void_p)]
 
 
 def lib():
@@ -244,6 +245,9 @@ class Pile:
         self.want_scales = want_scales
         self.scaleF = np.zeros(A) if want_scales else None
         self.scaleN = np.zeros(A) if want_scales else None
+        self.sph_Fmc = np.zeros(N) if want_scales else None
+        self.sph_Tmc = np.zeros(N) if want_scales else None
+        self.sph_Fmg = np.zeros(N) if want_scales else None
         cap = pair_cap if pair_cap is not None else 8 * N + 16
         self.pairs = np.zeros((cap, 2), np.int32)
         self.pair_x = np.zeros(cap)
@@ -256,7 +260,7 @@ class Pile:
         for f in ("first", "M", "I", "Iinv", "r", "v", "q", "wb", "acc", "torque", "agg_of", "m",
                   "s", "b", "h_n", "h_partner", "h_S", "sph_pos", "sph_vel", "sph_w", "Fc", "Tc",
                   "Fg", "Fe", "FA_c", "NA_c", "FA_g", "NA_g", "FA_e", "NA_e", "planet", "scaleF",
-                  "scaleN", "pairs", "pair_x"):
+                  "scaleN", "pairs", "pair_x", "sph_Fmc", "sph_Tmc", "sph_Fmg"):
             setattr(S, f, _p(getattr(self, f)))
         S.count = _p(self.counts)
         S.pair_cap = cap

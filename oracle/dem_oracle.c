@@ -76,6 +76,9 @@ typedef struct {
     double *scaleF, *scaleN;    /* per aggregate, may be NULL */
     /* optional: pair list of the last contact evaluation (i, j) and overlap */
     int32_t *pairs; double *pair_x; int64_t pair_cap; int64_t n_pairs;
+    /* optional per-sphere scales: contact |F| sum, contact torque-term sum,
+       gravity |F_ij| sum */
+    double *sph_Fmc, *sph_Tmc, *sph_Fmg;
 } ora_sim;
 
 int ora_threads(void)
@@ -608,6 +611,11 @@ static int ora_forces(ora_sim *S, const ora_params *P, int want_scales)
             S->Fe[3 * i] = S->Fe[3 * i + 1] = S->Fe[3 * i + 2] = 0;
     }
     ora_reduce(S, Fmc, Tmc, Fmg);
+    if (want_scales) {
+        if (S->sph_Fmc) memcpy(S->sph_Fmc, Fmc, sizeof(double) * (size_t)n);
+        if (S->sph_Tmc) memcpy(S->sph_Tmc, Tmc, sizeof(double) * (size_t)n);
+        if (S->sph_Fmg) memcpy(S->sph_Fmg, Fmg, sizeof(double) * (size_t)n);
+    }
     free(Fmc); free(Tmc); free(Fmg);
     return np < 0 ? -2 : 0;
 }

@@ -1,0 +1,137 @@
+// dem_internal.h -- device data layout and kernel entry points of the GB300
+// DEM library (bonded-sphere aggregates, arXiv 2311.11322).  Internal: the
+// public boundary is include/dem.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dem.h"
+
+namespace dem {
+
+// 32-byte aligned double vector (CUDA 13 spelling); loads as one 256-bit access.
+typedef double4_32a dbl4;
+__host__ __device__ __forceinline__ dbl4 make_dbl4(double x, double y, double z, double w)
+{
+    return make_double4_32a(x, y, z, w);
+}
+
+constexpr int kMaxK = 64;          // largest max_contacts
+constexpr int kScanTile = 2048;    // cells per scan block (256 threads x 8)
+constexpr int kAggChunk = 512;     // aggregates per pile-reduction block
+constexpr int kPartialDoubles = 16;
+
+// Static description of one pile (host-owned; re-uploaded on membership change).
+struct PileStatic {
+    int64_t s0, ns;        // sphere range [s0, s0+ns) (home order == sorted range)
+    int64_t a0, na;        // aggregate range
+    int64_t c0, nc;        // cell range (nc padded to a multiple of kScanTile)
+    int64_t ch0, nch;      // aggregate-chunk range (pile reductions)
+    int64_t t0, nt;        // scan-tile range
+    int32_t nx, ny, nz, K; // wrapped grid dims (>= 3 each), history slots
+    double cell, inv_cell; // cell edge and its inverse
+    double G, h, kn, kt, cn, ct, mu_s, mu_r, mu_t, w0, eps2;
+    double ext_mass, M_total;
+    double spin_inc[3];
+};
+
+// Dynamic per-pile state (device-owned; written by kernels).
+struct PileDyn {
+    double O[3], V[3];        // frame of positions / velocities used this step
+    double Rc[3], Vc[3];      // pile COM after the drift, mean velocity after the first kick
+    double P_pos[3], P_vel[3], P_acc[3];   // planet
+    int64_t steps;
+    int32_t flags;            // DEM_FLAG_* bits
+    int32_t parity;           // history buffer holding the previous contacts
+    int32_t failed;           // frozen after a fatal flag
+    int32_t pad;
+};
+
+// Per-aggregate quantities the sphere kernels need, mixed precision.
+// R and c are float-float (hi + lo) so that sphere positions relative to the
+// pile frame keep ~48 bits; velocity and spin are plain FP32, relative to the
+// pile frame velocity.
+struct __align__(16) AggRecMixed {
+    float Rh[9], Rl[9];   // rotation body -> space
+    float ch[3], cl[3];   // r_A - O
+    float vb[3];          // v_A,n+1/2 + h/2 a_A,n - V
+    float w[3];           // predicted spin (space frame)
+    float pad[2];
+};
+
+struct __align__(16) AggRec64 {
+    double R[9];
+    double c[3];
+    double vb[3];
+    double w[3];
+};
+
+// Device pointers of every array (global, pile-contiguous, pile-local indices).
+struct Arrays {
+    // spheres, home order
+    int32_t *sph_agg;    // aggregate index within the pile
+    int32_t *sph_pile;   // pile slot
+    double *b64;         // [N][3] body offsets (master copy, never rewritten)
+    double *s64, *m64;   // radius, mass
+    float4 *bh, *bl;     // mixed: body offset hi/lo with radius hi/lo in .w
+    int32_t *key;        // cell index within the pile
+    int32_t *rank;       // rank among spheres counted into the same cell
+    int32_t *sorted;     // sorted position (pile-local) -> home index (pile-local)
+    // sorted copies for the contact pass
+    float4 *sph_, *spl_, *sv_, *sw_;   // mixed: pos hi (+s hi), pos lo (+s lo), vel (+agg), spin (+gid)
+    dbl4 *dp_, *dv_, *dw_;          // fp64: pos (+s), vel (+agg), spin (+gid)
+    // gravity inputs / outputs
+    float4 *gpos32;      // mixed: pos hi (+mass)
+    dbl4 *gpos64;     // fp64: pos (+mass)
+    dbl4 *fg;         // gravity on each sphere (from other aggregates)
+    // contact outputs, home order
+    float4 *fc32, *tc32;
+    dbl4 *fc64, *tc64;
+    // contact history, double-buffered by pile parity: slots [N*K], counts [N]
+    float4 *hist32[2];
+    dbl4 *hist64[2];
+    int32_t *hist_n[2];
+    // aggregates
+    int32_t *agg_first, *agg_count, *agg_pile;
+    double *M, *I, *Iinv;          // [A], [A][9], [A][9]
+    double *r, *v, *q, *wb, *acc, *torque;   // [A][3], q [A][4]
+    AggRecMixed *rec32;
+    AggRec64 *rec64;
+    double *out;                   // [A][18]: FA_c NA_c FA_g NA_g FA_e NA_e
+    // cells
+    int32_t *ccount, *cstart, *tile_sum;
+    // pile reductions
+    double *chunk_part;            // [chunks][kPartialDoubles]
+    int32_t *chunk_pile;           // [chunks] pile slot of each chunk
+    // gravity work list and j-chunk partial sums
+    int4 *gitems;                  // (pile, i0 local, j0 local, j1 local)
+    dbl4 *gpart;                // partial sums [slot] (scratch)
+    int64_t *gpart_base;           // per pile: first slot in gpart (or -1 = direct)
+    int32_t *gnchunk;              // per pile: number of j-chunks
+    // piles
+    PileStatic *ps;
+    PileDyn *pd;
+    int32_t *enabled;
+};
+
+struct Sizes {
+    int64_t N, A, C, T, CH, P, GI, GP;
+};
+
+// ---- kernel launchers (kernels_*.cu) -------------------------------------
+void launch_agg_begin(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
+void launch_pile_begin(const Arrays &a, const Sizes &z, cudaStream_t st);
+void launch_keys(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
+void launch_scan(const Arrays &a, const Sizes &z, cudaStream_t st);
+void launch_scatter(const Arrays &a, const Sizes &z, cudaStream_t st);
+void launch_cell_order(const Arrays &a, const Sizes &z, cudaStream_t st);
+void launch_gather(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
+void launch_contact(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
+void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int ib,
+                    cudaStream_t st);
+void launch_agg_end(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
+void launch_pile_end(const Arrays &a, const Sizes &z, cudaStream_t st);
+void launch_fill_ids(const Arrays &a, const Sizes &z, cudaStream_t st);
+
+}  // namespace dem

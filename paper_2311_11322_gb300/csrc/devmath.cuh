@@ -1,0 +1,140 @@
+// devmath.cuh -- small device helpers: float3/double3 vectors and
+// float-float ("double-float") arithmetic built only from correctly rounded
+// FP32 operations.
+//
+// Float-float values are unevaluated sums hi + lo with |lo| <= ulp(hi)/2.
+// The error-free transformations are the classical ones: Knuth's TwoSum
+// (six additions), Dekker's FastTwoSum (for |a| >= |b|) and the FMA-based
+// TwoProduct (p = a*b rounded, e = fma(a, b, -p) exact).  All steps use the
+// _rn intrinsics so that the compiler never contracts or reorders them; the
+// results are therefore bitwise reproducible in every kernel that inlines
+// them, which the cell-list build relies on.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace dem {
+
+// ---------------------------------------------------------------- float-float
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    ff r;
+    fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ ff ff_sub(ff a, ff b)
+{
+    ff nb = {-b.hi, -b.lo};
+    return ff_add(a, nb);
+}
+
+// (R_hi + R_lo) . (b_hi + b_lo) for one row, to ~2^-44 relative.
+__device__ __forceinline__ ff ff_dot3(const float *Rh, const float *Rl, float bx_h, float by_h,
+                                      float bz_h, float bx_l, float by_l, float bz_l)
+{
+    float p0, e0, p1, e1, p2, e2;
+    two_prod(Rh[0], bx_h, p0, e0);
+    two_prod(Rh[1], by_h, p1, e1);
+    two_prod(Rh[2], bz_h, p2, e2);
+    float s, t1, t2;
+    two_sum(p0, p1, s, t1);
+    two_sum(s, p2, s, t2);
+    float lo = __fadd_rn(__fadd_rn(t1, t2), __fadd_rn(__fadd_rn(e0, e1), e2));
+    float cross = __fmul_rn(Rh[0], bx_l);
+    cross = __fmaf_rn(Rh[1], by_l, cross);
+    cross = __fmaf_rn(Rh[2], bz_l, cross);
+    cross = __fmaf_rn(Rl[0], bx_h, cross);
+    cross = __fmaf_rn(Rl[1], by_h, cross);
+    cross = __fmaf_rn(Rl[2], bz_h, cross);
+    lo = __fadd_rn(lo, cross);
+    ff r;
+    fast_two_sum(s, lo, r.hi, r.lo);
+    return r;
+}
+
+// Split a double into hi + lo floats.
+__host__ __device__ __forceinline__ void split_d(double x, float &hi, float &lo)
+{
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+// ---------------------------------------------------------------- vectors
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator-(float3 a) { return f3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b)
+{
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ double3 d3(double x, double y, double z) { return make_double3(x, y, z); }
+__device__ __forceinline__ double3 operator+(double3 a, double3 b) { return d3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ double3 operator-(double3 a, double3 b) { return d3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ double3 operator-(double3 a) { return d3(-a.x, -a.y, -a.z); }
+__device__ __forceinline__ double3 operator*(double s, double3 a) { return d3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ double dot(double3 a, double3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ double3 cross(double3 a, double3 b)
+{
+    return d3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ double3 ld3(const double *p) { return d3(p[0], p[1], p[2]); }
+__device__ __forceinline__ void st3(double *p, double3 v) { p[0] = v.x; p[1] = v.y; p[2] = v.z; }
+
+// Rotation matrix (body -> space) of the unit quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_to_R(const double *q, double *R)
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+__device__ __forceinline__ double3 mat_mul(const double *A, double3 x)
+{
+    return d3(A[0] * x.x + A[1] * x.y + A[2] * x.z, A[3] * x.x + A[4] * x.y + A[5] * x.z,
+              A[6] * x.x + A[7] * x.y + A[8] * x.z);
+}
+__device__ __forceinline__ double3 mat_tmul(const double *A, double3 x)
+{
+    return d3(A[0] * x.x + A[3] * x.y + A[6] * x.z, A[1] * x.x + A[4] * x.y + A[7] * x.z,
+              A[2] * x.x + A[5] * x.y + A[8] * x.z);
+}
+
+__device__ __forceinline__ bool finite3(double3 v)
+{
+    return isfinite(v.x) && isfinite(v.y) && isfinite(v.z);
+}
+
+}  // namespace dem

@@ -1,0 +1,319 @@
+// kernels_contact.cu -- the contact pass: one thread per sphere in cell
+// order, 27 neighbour cells of a wrapped uniform grid, pairs inside one
+// aggregate skipped (Sec. 2.2: members are rigidly bonded), linear
+// spring-dashpot normal force, tangential spring with history and Coulomb
+// cap, rolling and twisting couples (Sec. 2.1, Sec. 2.2.5), applied at the
+// contact point at the centre of the intersection circle (Sec. 2.2.4,
+// Eq. lever_arm).
+//
+// Each pair is evaluated by both of its spheres.  Both evaluate it in the same
+// canonical orientation (lower pile-local sphere index first) with the same
+// inlined code and the same inputs, so the two results are bitwise equal and
+// opposite, and both store the same updated tangential displacement S in
+// their own history slots.  Nothing is written with atomics except error
+// flags; the neighbour order is fixed by the cell ordering, so the pass is
+// deterministic.
+//
+// Force law (the paper defers the constants and form to earlier work):
+//   d = r_b - r_a, n = d/|d|, x = s_a + s_b - |d| > 0 (overlap),
+//   l_a = (s_a^2 - s_b^2 + |d|^2) / (2|d|), l_b = |d| - l_a,
+//   u = (v_b + w_b x (-l_b n)) - (v_a + w_a x (l_a n)), u_n = (u.n) n, u_t = u - u_n,
+//   F_N = -kn x n + cn u_n,
+//   S = (S_prev projected on the tangent plane, rescaled to |S_prev|) + u_t h,
+//   F_T = kt S + ct u_t, capped at mu_s |F_N| (then S = (F_T - ct u_t)/kt),
+//   M = -mu_r |F_N| R w_r / max(|w_r|, w0) - mu_t |F_N| R w_t / max(|w_t|, w0),
+//     w = w_a - w_b, w_t = (w.n) n, w_r = w - w_t, R = s_a s_b / (s_a + s_b);
+//   sphere a: F = F_N + F_T, tau = (l_a n) x F + M;
+//   sphere b: -F,            tau = (l_b n) x F - M.
+#include "dem_internal.h"
+#include "devmath.cuh"
+
+namespace dem {
+
+struct ParamsF {
+    float kn, kt, cn, ct, mu_s, mu_r, mu_t, w0, h;
+};
+struct ParamsD {
+    double kn, kt, cn, ct, mu_s, mu_r, mu_t, w0, h;
+};
+
+template <typename T, typename V>
+struct PairOut {
+    V F, M, S, n;
+    T la, lb, x;
+};
+
+// Tangential spring, Coulomb cap and rolling/twisting couples, shared by
+// both precisions (T = float or double).
+template <typename T, typename V, typename P>
+__device__ __forceinline__ void force_law(V n, T x, T la, T lb, V va, V wa, V vb, V wb, T sa,
+                                          T sb, V Sprev, const P &prm, PairOut<T, V> &o)
+{
+    V ca = la * n, cb = (-lb) * n;
+    V u = (vb + cross(wb, cb)) - (va + cross(wa, ca));
+    T uns = dot(u, n);
+    V un = uns * n;
+    V ut = u - un;
+    V FN = (-prm.kn * x) * n + prm.cn * un;
+    T FNm = sqrt(dot(FN, FN));
+    T sn = dot(Sprev, n);
+    V Sp = Sprev - sn * n;
+    T Spm = sqrt(dot(Sp, Sp)), Sprevm = sqrt(dot(Sprev, Sprev));
+    Sp = Spm > T(0) ? (Sprevm / Spm) * Sp : T(0) * Sp;
+    V S = Sp + prm.h * ut;
+    V FT = prm.kt * S + prm.ct * ut;
+    T FTm = sqrt(dot(FT, FT)), cap = prm.mu_s * FNm;
+    if (FTm > cap) {
+        FT = (cap / FTm) * FT;
+        S = prm.kt > T(0) ? (T(1) / prm.kt) * (FT - prm.ct * ut) : T(0) * S;
+    }
+    V w = wa - wb;
+    T wn = dot(w, n);
+    V wt = wn * n;
+    V wr = w - wt;
+    T Rred = sa * sb / (sa + sb);
+    V M = T(0) * n;
+    T wrm = sqrt(dot(wr, wr)), wtm = sqrt(dot(wt, wt));
+    if (prm.mu_r > T(0) && wrm > T(0)) M = M + (-prm.mu_r * FNm * Rred / fmax(wrm, prm.w0)) * wr;
+    if (prm.mu_t > T(0) && wtm > T(0)) M = M + (-prm.mu_t * FNm * Rred / fmax(wtm, prm.w0)) * wt;
+    o.F = FN + FT;
+    o.M = M;
+    o.S = S;
+    o.n = n;
+    o.la = la;
+    o.lb = lb;
+    o.x = x;
+}
+
+// Mixed precision pair: the overlap x = s_a + s_b - |d| is formed from
+// float-float positions and radii (exact differences by TwoSum, |d|^2 with
+// TwoProduct terms, one Newton correction of sqrt), so x keeps ~24 significant
+// bits even when x << |d|; the rest of the law is FP32.
+__device__ __forceinline__ bool pair_mixed(float4 ah, float4 al, float4 av, float4 aw, float4 bh,
+                                           float4 bl, float4 bv, float4 bw, float3 Sprev,
+                                           const ParamsF &prm, PairOut<float, float3> &o)
+{
+    float sx, ex, sy, ey, sz, ez;
+    two_sum(bh.x, -ah.x, sx, ex);
+    two_sum(bh.y, -ah.y, sy, ey);
+    two_sum(bh.z, -ah.z, sz, ez);
+    ex = __fadd_rn(ex, __fsub_rn(bl.x, al.x));
+    ey = __fadd_rn(ey, __fsub_rn(bl.y, al.y));
+    ez = __fadd_rn(ez, __fsub_rn(bl.z, al.z));
+    float dhx, dlx, dhy, dly, dhz, dlz;
+    fast_two_sum(sx, ex, dhx, dlx);
+    fast_two_sum(sy, ey, dhy, dly);
+    fast_two_sum(sz, ez, dhz, dlz);
+    float px, epx, py, epy, pz, epz;
+    two_prod(dhx, dhx, px, epx);
+    two_prod(dhy, dhy, py, epy);
+    two_prod(dhz, dhz, pz, epz);
+    float s1, t1, Dh, t2;
+    two_sum(px, py, s1, t1);
+    two_sum(s1, pz, Dh, t2);
+    float cr = __fmul_rn(dhx, dlx);
+    cr = __fmaf_rn(dhy, dly, cr);
+    cr = __fmaf_rn(dhz, dlz, cr);
+    float Dl = __fadd_rn(__fadd_rn(t1, t2), __fadd_rn(__fadd_rn(epx, epy), epz));
+    Dl = __fmaf_rn(2.0f, cr, Dl);
+    float r = __fsqrt_rn(Dh);
+    if (!(r > 0.0f)) return false;
+    float delta = __fdiv_rn(__fadd_rn(__fmaf_rn(-r, r, Dh), Dl), __fmul_rn(2.0f, r));
+    float Sh, e;
+    two_sum(ah.w, bh.w, Sh, e);
+    float Sl = __fadd_rn(e, __fadd_rn(al.w, bl.w));
+    float x = __fadd_rn(__fsub_rn(Sh, r), __fsub_rn(Sl, delta));
+    if (!(x > 0.0f)) return false;
+    float dist = __fadd_rn(r, delta);
+    float inv = __fdiv_rn(1.0f, dist);
+    float3 n = f3(__fmul_rn(dhx, inv), __fmul_rn(dhy, inv), __fmul_rn(dhz, inv));
+    float sa = ah.w, sb = bh.w;
+    float la = __fmul_rn(__fmaf_rn(dist, dist, __fmul_rn(sa - sb, sa + sb)), __fmul_rn(0.5f, inv));
+    float lb = __fsub_rn(dist, la);
+    force_law<float, float3, ParamsF>(n, x, la, lb, f3(av.x, av.y, av.z), f3(aw.x, aw.y, aw.z),
+                                      f3(bv.x, bv.y, bv.z), f3(bw.x, bw.y, bw.z), sa, sb, Sprev,
+                                      prm, o);
+    return true;
+}
+
+__device__ __forceinline__ bool pair_64(dbl4 ap, dbl4 av, dbl4 aw, dbl4 bp,
+                                        dbl4 bv, dbl4 bw, double3 Sprev, const ParamsD &prm,
+                                        PairOut<double, double3> &o)
+{
+    double3 d = d3(bp.x - ap.x, bp.y - ap.y, bp.z - ap.z);
+    double dist = sqrt(dot(d, d));
+    double x = ap.w + bp.w - dist;
+    if (!(x > 0.0) || !(dist > 0.0)) return false;
+    double3 n = (1.0 / dist) * d;
+    double la = (ap.w * ap.w - bp.w * bp.w + dist * dist) / (2.0 * dist);
+    double lb = dist - la;
+    force_law<double, double3, ParamsD>(n, x, la, lb, d3(av.x, av.y, av.z), d3(aw.x, aw.y, aw.z),
+                                        d3(bv.x, bv.y, bv.z), d3(bw.x, bw.y, bw.z), ap.w, bp.w,
+                                        Sprev, prm, o);
+    return true;
+}
+
+__device__ __forceinline__ int wrapc(int c, int n) { return c < 0 ? c + n : (c >= n ? c - n : c); }
+
+__device__ __forceinline__ int cellc_f(float x, float inv_cell, int n)
+{
+    float f = floorf(__fmul_rn(x, inv_cell));
+    f = fminf(fmaxf(f, -1.0e9f), 1.0e9f);
+    int m = ((int)f) % n;
+    return m < 0 ? m + n : m;
+}
+
+__device__ __forceinline__ int cellc_d(double x, double inv_cell, int n)
+{
+    double f = floor(__dmul_rn(x, inv_cell));
+    f = fmin(fmax(f, -1.0e9), 1.0e9);
+    int m = ((int)f) % n;
+    return m < 0 ? m + n : m;
+}
+
+__device__ __forceinline__ float maxabs3(float4 p)
+{
+    return fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z)));
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(128) k_contact(Arrays a, Sizes z)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= z.N) return;
+    int p = a.sph_pile[k];
+    if (a.enabled[p] == 0 || a.pd[p].failed) return;
+    const PileStatic &S = a.ps[p];
+    const int64_t s0 = S.s0;
+    const int K = S.K;
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const int par = a.pd[p].parity;
+    const int hl = a.sorted[k];
+    const int64_t i = s0 + hl;
+    const int32_t *hn_prev = a.hist_n[par];
+    int32_t *hn_new = a.hist_n[par ^ 1];
+    int flags = 0;
+    int nn = 0;
+    const int nprev = hn_prev[i];
+
+    if (FP64) {
+        ParamsD prm = {S.kn, S.kt, S.cn, S.ct, S.mu_s, S.mu_r, S.mu_t, S.w0, S.h};
+        const dbl4 me_p = a.dp_[k], me_v = a.dv_[k], me_w = a.dw_[k];
+        const int my_agg = (int)me_v.w;
+        const dbl4 *hprev = a.hist64[par] + i * K;
+        dbl4 *hnew = a.hist64[par ^ 1] + i * K;
+        int cx = cellc_d(me_p.x, S.inv_cell, nx), cy = cellc_d(me_p.y, S.inv_cell, ny),
+            cz = cellc_d(me_p.z, S.inv_cell, nz);
+        double3 F = d3(0, 0, 0), T = d3(0, 0, 0);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int c = (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx + wrapc(cx + dx, nx);
+                    int st = a.cstart[S.c0 + c], cnt = a.ccount[S.c0 + c];
+                    for (int t = 0; t < cnt; ++t) {
+                        int64_t kk = s0 + st + t;
+                        if (kk == k) continue;
+                        dbl4 nv = a.dv_[kk];
+                        if ((int)nv.w == my_agg) continue;
+                        dbl4 np = a.dp_[kk];
+                        double ddx = np.x - me_p.x, ddy = np.y - me_p.y, ddz = np.z - me_p.z;
+                        double sr = np.w + me_p.w;
+                        if (ddx * ddx + ddy * ddy + ddz * ddz >= sr * sr) continue;
+                        dbl4 nw = a.dw_[kk];
+                        int ngid = (int)nw.w;
+                        double3 Sprev = d3(0, 0, 0);
+                        for (int h = 0; h < nprev; ++h) {
+                            dbl4 sl = hprev[h];
+                            if ((int)sl.w == ngid) { Sprev = d3(sl.x, sl.y, sl.z); break; }
+                        }
+                        bool first = hl < ngid;
+                        PairOut<double, double3> o;
+                        bool hit = first ? pair_64(me_p, me_v, me_w, np, nv, nw, Sprev, prm, o)
+                                         : pair_64(np, nv, nw, me_p, me_v, me_w, Sprev, prm, o);
+                        if (!hit) continue;
+                        if (first) {
+                            F = F + o.F;
+                            T = T + cross(o.la * o.n, o.F) + o.M;
+                        } else {
+                            F = F - o.F;
+                            T = T + cross(o.lb * o.n, o.F) - o.M;
+                        }
+                        if (nn < K) hnew[nn] = make_dbl4(o.S.x, o.S.y, o.S.z, (double)ngid);
+                        else flags |= DEM_FLAG_SLOTS;
+                        ++nn;
+                        if (o.x > 0.1 * fmin(me_p.w, np.w)) flags |= DEM_FLAG_OVERLAP;
+                    }
+                }
+        a.fc64[i] = make_dbl4(F.x, F.y, F.z, 0.0);
+        a.tc64[i] = make_dbl4(T.x, T.y, T.z, 0.0);
+    } else {
+        ParamsF prm = {(float)S.kn, (float)S.kt, (float)S.cn, (float)S.ct, (float)S.mu_s,
+                       (float)S.mu_r, (float)S.mu_t, (float)S.w0, (float)S.h};
+        const float4 me_h = a.sph_[k], me_l = a.spl_[k], me_v = a.sv_[k], me_w = a.sw_[k];
+        const int my_agg = __float_as_int(me_v.w);
+        const float my_abs = maxabs3(me_h);
+        const float4 *hprev = a.hist32[par] + i * K;
+        float4 *hnew = a.hist32[par ^ 1] + i * K;
+        const float icell = (float)S.inv_cell;
+        int cx = cellc_f(me_h.x, icell, nx), cy = cellc_f(me_h.y, icell, ny),
+            cz = cellc_f(me_h.z, icell, nz);
+        float3 F = f3(0, 0, 0), T = f3(0, 0, 0);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int c = (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx + wrapc(cx + dx, nx);
+                    int st = a.cstart[S.c0 + c], cnt = a.ccount[S.c0 + c];
+                    for (int t = 0; t < cnt; ++t) {
+                        int64_t kk = s0 + st + t;
+                        if (kk == k) continue;
+                        float4 nh = a.sph_[kk];
+                        // FP32 pre-filter with a margin covering the rounding of the hi parts
+                        float ddx = nh.x - me_h.x, ddy = nh.y - me_h.y, ddz = nh.z - me_h.z;
+                        float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        float sr = nh.w + me_h.w;
+                        float tol = 4.0e-7f * (my_abs + maxabs3(nh)) + 4.0e-6f * sr;
+                        float srt = sr + tol;
+                        if (r2 > srt * srt) continue;
+                        float4 nv = a.sv_[kk];
+                        if (__float_as_int(nv.w) == my_agg) continue;
+                        float4 nl = a.spl_[kk], nw = a.sw_[kk];
+                        int ngid = __float_as_int(nw.w);
+                        float3 Sprev = f3(0, 0, 0);
+                        for (int h = 0; h < nprev; ++h) {
+                            float4 sl = hprev[h];
+                            if (__float_as_int(sl.w) == ngid) { Sprev = f3(sl.x, sl.y, sl.z); break; }
+                        }
+                        bool first = hl < ngid;
+                        PairOut<float, float3> o;
+                        bool hit = first ? pair_mixed(me_h, me_l, me_v, me_w, nh, nl, nv, nw, Sprev, prm, o)
+                                         : pair_mixed(nh, nl, nv, nw, me_h, me_l, me_v, me_w, Sprev, prm, o);
+                        if (!hit) continue;
+                        if (first) {
+                            F = F + o.F;
+                            T = T + cross(o.la * o.n, o.F) + o.M;
+                        } else {
+                            F = F - o.F;
+                            T = T + cross(o.lb * o.n, o.F) - o.M;
+                        }
+                        if (nn < K) hnew[nn] = make_float4(o.S.x, o.S.y, o.S.z, __int_as_float(ngid));
+                        else flags |= DEM_FLAG_SLOTS;
+                        ++nn;
+                        if (o.x > 0.1f * fminf(me_h.w, nh.w)) flags |= DEM_FLAG_OVERLAP;
+                    }
+                }
+        a.fc32[i] = make_float4(F.x, F.y, F.z, 0.f);
+        a.tc32[i] = make_float4(T.x, T.y, T.z, 0.f);
+    }
+    hn_new[i] = nn < K ? nn : K;
+    if (flags) atomicOr(&a.pd[p].flags, flags);
+}
+
+void launch_contact(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
+{
+    if (z.N == 0) return;
+    unsigned nb = (unsigned)((z.N + 127) / 128);
+    if (fp64) k_contact<true><<<nb, 128, 0, st>>>(a, z);
+    else k_contact<false><<<nb, 128, 0, st>>>(a, z);
+}
+
+}  // namespace dem

@@ -1,0 +1,625 @@
+// kernels_step.cu -- per-step kernels other than the contact pass and gravity:
+// rigid-body kick/drift/rotation, pile reductions, sphere expansion and cell
+// keys, the counting sort into cells, the sorted gather, and the reduction of
+// sphere forces onto aggregates with the closing kick.
+//
+// Paper references: leapfrog with predicted velocities (Sec. 2.1), aggregate
+// mass and COM (Sec. 2.2.1, Eq. agg_mass, Eq. agg_position), Euler's equations
+// for spin (Sec. 2.2.1), predicted sphere velocity (Sec. 2.2.2, Eq. pred-vel),
+// aggregate force and torque sums (Sec. 2.2.3-2.2.4, Eq. agg_gravity,
+// Eq. gravity_torque, Eq. agg_contact_accel, contact torque at the contact
+// point), YORP increment (Sec. 4.1), point-mass planet (Sec. 4.2).
+#include "dem_internal.h"
+#include "devmath.cuh"
+
+namespace dem {
+
+__device__ __forceinline__ bool pile_active(const Arrays &a, int p)
+{
+    return a.enabled[p] != 0 && a.pd[p].failed == 0;
+}
+
+// ---------------------------------------------------------------- ids
+__device__ int find_slot(const PileStatic *ps, int P, int64_t idx, int which)
+{
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        int64_t b = which == 0 ? ps[mid].s0 : which == 1 ? ps[mid].a0 : which == 2 ? ps[mid].t0 : ps[mid].ch0;
+        if (b <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_fill_ids(Arrays a, Sizes z)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int P = (int)z.P;
+    if (t < z.N) a.sph_pile[t] = find_slot(a.ps, P, t, 0);
+    if (t < z.A) a.agg_pile[t] = find_slot(a.ps, P, t, 1);
+    if (t < z.CH) a.chunk_pile[t] = find_slot(a.ps, P, t, 3);
+}
+
+void launch_fill_ids(const Arrays &a, const Sizes &z, cudaStream_t st)
+{
+    int64_t n = z.N > z.A ? z.N : z.A;
+    if (z.CH > n) n = z.CH;
+    if (n == 0 || z.P == 0) return;
+    k_fill_ids<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, z);
+}
+
+// ---------------------------------------------------------------- rotation
+// Torque-free Euler equations in the body frame (Sec. 2.2.1):
+//   dq/dt = 1/2 q (x) (0, w),  dw/dt = I^-1 (-w x (I w)).
+__device__ __forceinline__ void rot_rhs(const double *y, const double *I, const double *Iinv,
+                                        double *dy)
+{
+    const double *q = y, *w = y + 4;
+    dy[0] = -0.5 * (q[1] * w[0] + q[2] * w[1] + q[3] * w[2]);
+    dy[1] = 0.5 * (q[0] * w[0] + q[2] * w[2] - q[3] * w[1]);
+    dy[2] = 0.5 * (q[0] * w[1] + q[3] * w[0] - q[1] * w[2]);
+    dy[3] = 0.5 * (q[0] * w[2] + q[1] * w[1] - q[2] * w[0]);
+    double3 wv = d3(w[0], w[1], w[2]);
+    double3 Iw = mat_mul(I, wv);
+    double3 g = -cross(wv, Iw);
+    double3 dw = mat_mul(Iinv, g);
+    dy[4] = dw.x; dy[5] = dw.y; dy[6] = dw.z;
+}
+
+// One classical RK4 step of the free rotor over h, q renormalised.
+__device__ void free_rotate(double *q, double3 &wb, const double *I, const double *Iinv, double h)
+{
+    double y[7] = {q[0], q[1], q[2], q[3], wb.x, wb.y, wb.z};
+    double k1[7], k2[7], k3[7], k4[7], t[7];
+    rot_rhs(y, I, Iinv, k1);
+    for (int c = 0; c < 7; ++c) t[c] = y[c] + 0.5 * h * k1[c];
+    rot_rhs(t, I, Iinv, k2);
+    for (int c = 0; c < 7; ++c) t[c] = y[c] + 0.5 * h * k2[c];
+    rot_rhs(t, I, Iinv, k3);
+    for (int c = 0; c < 7; ++c) t[c] = y[c] + h * k3[c];
+    rot_rhs(t, I, Iinv, k4);
+    for (int c = 0; c < 7; ++c) y[c] += h / 6.0 * (k1[c] + 2.0 * k2[c] + 2.0 * k3[c] + k4[c]);
+    double n = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3]);
+    q[0] = y[0] / n; q[1] = y[1] / n; q[2] = y[2] / n; q[3] = y[3] / n;
+    wb = d3(y[4], y[5], y[6]);
+}
+
+// ---------------------------------------------------------------- step begin
+// Per aggregate: half kick of COM and spin with the stored a_A,n / N_A,n,
+// drift, torque-free rotation, then the record the sphere kernels read:
+// rotation, COM relative to the pile frame, predicted COM velocity
+// v_A,n+1/2 + h/2 a_A,n (Eq. pred-vel) and predicted spin w_A,n+1 (the
+// drifted spin plus the second half kick of the old torque).
+template <bool FP64>
+__global__ void k_agg_begin(Arrays a, Sizes z)
+{
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= z.A) return;
+    int p = a.agg_pile[g];
+    if (!pile_active(a, p)) return;
+    const double h = a.ps[p].h;
+    const double *I = a.I + 9 * g, *Iinv = a.Iinv + 9 * g;
+    double q[4] = {a.q[4 * g], a.q[4 * g + 1], a.q[4 * g + 2], a.q[4 * g + 3]};
+    double3 r = ld3(a.r + 3 * g), v = ld3(a.v + 3 * g), wb = ld3(a.wb + 3 * g);
+    double3 acc = ld3(a.acc + 3 * g), N = ld3(a.torque + 3 * g);
+    double R[9];
+    quat_to_R(q, R);
+    v = v + (0.5 * h) * acc;
+    wb = wb + (0.5 * h) * mat_mul(Iinv, mat_tmul(R, N));
+    r = r + h * v;
+    free_rotate(q, wb, I, Iinv, h);
+    quat_to_R(q, R);
+    double3 wpred_b = wb + (0.5 * h) * mat_mul(Iinv, mat_tmul(R, N));
+    double3 ws = mat_mul(R, wpred_b);
+    st3(a.r + 3 * g, r);
+    st3(a.v + 3 * g, v);
+    st3(a.wb + 3 * g, wb);
+    a.q[4 * g] = q[0]; a.q[4 * g + 1] = q[1]; a.q[4 * g + 2] = q[2]; a.q[4 * g + 3] = q[3];
+    const PileDyn &D = a.pd[p];
+    double3 c = r - ld3(D.O);
+    double3 vb = v + (0.5 * h) * acc - ld3(D.V);
+    if (FP64) {
+        AggRec64 rec;
+        for (int k = 0; k < 9; ++k) rec.R[k] = R[k];
+        st3(rec.c, c);
+        st3(rec.vb, vb);
+        st3(rec.w, ws);
+        a.rec64[g] = rec;
+    } else {
+        AggRecMixed rec;
+        for (int k = 0; k < 9; ++k) split_d(R[k], rec.Rh[k], rec.Rl[k]);
+        split_d(c.x, rec.ch[0], rec.cl[0]);
+        split_d(c.y, rec.ch[1], rec.cl[1]);
+        split_d(c.z, rec.ch[2], rec.cl[2]);
+        rec.vb[0] = (float)vb.x; rec.vb[1] = (float)vb.y; rec.vb[2] = (float)vb.z;
+        rec.w[0] = (float)ws.x; rec.w[1] = (float)ws.y; rec.w[2] = (float)ws.z;
+        rec.pad[0] = rec.pad[1] = 0.f;
+        a.rec32[g] = rec;
+    }
+}
+
+void launch_agg_begin(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
+{
+    if (z.A == 0) return;
+    unsigned nb = (unsigned)((z.A + 127) / 128);
+    if (fp64) k_agg_begin<true><<<nb, 128, 0, st>>>(a, z);
+    else k_agg_begin<false><<<nb, 128, 0, st>>>(a, z);
+}
+
+// ---------------------------------------------------------------- pile reductions
+// Block b sums kAggChunk aggregates of one pile.  Mode 0 (after the drift):
+// sum M, sum M r, sum M v.  Mode 1 (after the closing kick): sum of the planet
+// force on the pile.  Fixed tree order: deterministic.
+template <int MODE>
+__global__ void k_pile_partials(Arrays a, Sizes z)
+{
+    int64_t ch = blockIdx.x;
+    if (ch >= z.CH) return;
+    int p = a.chunk_pile[ch];
+    __shared__ double sh[7][128];
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (pile_active(a, p)) {
+        const PileStatic &S = a.ps[p];
+        int64_t beg = S.a0 + (ch - S.ch0) * kAggChunk;
+        int64_t end = beg + kAggChunk;
+        if (end > S.a0 + S.na) end = S.a0 + S.na;
+        for (int64_t g = beg + threadIdx.x; g < end; g += blockDim.x) {
+            if (MODE == 0) {
+                double M = a.M[g];
+                acc[0] += M;
+                for (int c = 0; c < 3; ++c) {
+                    acc[1 + c] += M * a.r[3 * g + c];
+                    acc[4 + c] += M * a.v[3 * g + c];
+                }
+            } else {
+                for (int c = 0; c < 3; ++c) acc[c] += a.out[18 * g + 12 + c];
+            }
+        }
+    }
+    for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = 64; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 7) a.chunk_part[ch * kPartialDoubles + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// One thread per pile: combine the chunk partials in chunk order.
+template <int MODE>
+__global__ void k_pile_finalize(Arrays a, Sizes z)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= z.P || !pile_active(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    PileDyn &D = a.pd[p];
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t ch = S.ch0; ch < S.ch0 + S.nch; ++ch)
+        for (int k = 0; k < 7; ++k) s[k] += a.chunk_part[ch * kPartialDoubles + k];
+    const double h = S.h;
+    if (MODE == 0) {
+        for (int c = 0; c < 3; ++c) {
+            D.Rc[c] = s[1 + c] / s[0];
+            D.Vc[c] = s[4 + c] / s[0];
+        }
+        if (S.ext_mass > 0) {   // planet: kick with the stored acceleration, drift
+            for (int c = 0; c < 3; ++c) {
+                D.P_vel[c] += 0.5 * h * D.P_acc[c];
+                D.P_pos[c] += h * D.P_vel[c];
+            }
+        }
+    } else {
+        if (S.ext_mass > 0) {   // planet: reaction of the pile, closing kick
+            for (int c = 0; c < 3; ++c) {
+                D.P_acc[c] = -s[c] / S.ext_mass;
+                D.P_vel[c] += 0.5 * h * D.P_acc[c];
+            }
+        }
+        for (int c = 0; c < 3; ++c) {
+            D.O[c] = D.Rc[c];
+            D.V[c] = D.Vc[c];
+        }
+        D.steps += 1;
+        D.parity ^= 1;
+        if (D.flags & (DEM_FLAG_SLOTS | DEM_FLAG_NONFINITE)) D.failed = 1;
+    }
+}
+
+void launch_pile_begin(const Arrays &a, const Sizes &z, cudaStream_t st)
+{
+    if (z.CH == 0) return;
+    k_pile_partials<0><<<(unsigned)z.CH, 128, 0, st>>>(a, z);
+    k_pile_finalize<0><<<(unsigned)((z.P + 63) / 64), 64, 0, st>>>(a, z);
+}
+
+void launch_pile_end(const Arrays &a, const Sizes &z, cudaStream_t st)
+{
+    if (z.CH == 0) return;
+    k_pile_partials<1><<<(unsigned)z.CH, 128, 0, st>>>(a, z);
+    k_pile_finalize<1><<<(unsigned)((z.P + 63) / 64), 64, 0, st>>>(a, z);
+}
+
+// ---------------------------------------------------------------- expansion
+// Sphere centre relative to the pile frame, r_i - O = (r_A - O) + R(q_A) b_i.
+// Mixed: float-float, bitwise identical wherever it is inlined.
+__device__ __forceinline__ void expand_mixed(const AggRecMixed &rec, float4 bh, float4 bl,
+                                             ff &px, ff &py, ff &pz)
+{
+    ff rx = ff_dot3(rec.Rh + 0, rec.Rl + 0, bh.x, bh.y, bh.z, bl.x, bl.y, bl.z);
+    ff ry = ff_dot3(rec.Rh + 3, rec.Rl + 3, bh.x, bh.y, bh.z, bl.x, bl.y, bl.z);
+    ff rz = ff_dot3(rec.Rh + 6, rec.Rl + 6, bh.x, bh.y, bh.z, bl.x, bl.y, bl.z);
+    ff cx = {rec.ch[0], rec.cl[0]}, cy = {rec.ch[1], rec.cl[1]}, cz = {rec.ch[2], rec.cl[2]};
+    px = ff_add(cx, rx);
+    py = ff_add(cy, ry);
+    pz = ff_add(cz, rz);
+}
+
+__device__ __forceinline__ double3 expand_64(const AggRec64 &rec, const double *b)
+{
+    const double *R = rec.R;
+    double x = __fma_rn(R[2], b[2], __fma_rn(R[1], b[1], __dmul_rn(R[0], b[0])));
+    double y = __fma_rn(R[5], b[2], __fma_rn(R[4], b[1], __dmul_rn(R[3], b[0])));
+    double zz = __fma_rn(R[8], b[2], __fma_rn(R[7], b[1], __dmul_rn(R[6], b[0])));
+    return d3(__dadd_rn(rec.c[0], x), __dadd_rn(rec.c[1], y), __dadd_rn(rec.c[2], zz));
+}
+
+__device__ __forceinline__ int wrap_cell(int c, int n)
+{
+    int m = c % n;
+    return m < 0 ? m + n : m;
+}
+
+__device__ __forceinline__ int cell_coord_f(float x, float inv_cell, int n)
+{
+    float f = floorf(__fmul_rn(x, inv_cell));
+    f = fminf(fmaxf(f, -1.0e9f), 1.0e9f);
+    return wrap_cell((int)f, n);
+}
+
+__device__ __forceinline__ int cell_coord_d(double x, double inv_cell, int n)
+{
+    double f = floor(__dmul_rn(x, inv_cell));
+    f = fmin(fmax(f, -1.0e9), 1.0e9);
+    return wrap_cell((int)f, n);
+}
+
+// Per sphere (home order): expand, cell key, atomic count into the cell (the
+// returned rank is made deterministic later by ordering each cell), gravity
+// input (position relative to the pile frame, mass).
+template <bool FP64>
+__global__ void k_keys(Arrays a, Sizes z)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= z.N) return;
+    int p = a.sph_pile[i];
+    if (!pile_active(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    int64_t g = S.a0 + a.sph_agg[i];
+    int cx, cy, cz;
+    if (FP64) {
+        double3 pos = expand_64(a.rec64[g], a.b64 + 3 * i);
+        cx = cell_coord_d(pos.x, S.inv_cell, S.nx);
+        cy = cell_coord_d(pos.y, S.inv_cell, S.ny);
+        cz = cell_coord_d(pos.z, S.inv_cell, S.nz);
+        a.gpos64[i] = make_dbl4(pos.x, pos.y, pos.z, a.m64[i]);
+    } else {
+        ff px, py, pz;
+        expand_mixed(a.rec32[g], a.bh[i], a.bl[i], px, py, pz);
+        float ic = (float)S.inv_cell;
+        cx = cell_coord_f(px.hi, ic, S.nx);
+        cy = cell_coord_f(py.hi, ic, S.ny);
+        cz = cell_coord_f(pz.hi, ic, S.nz);
+        a.gpos32[i] = make_float4(px.hi, py.hi, pz.hi, (float)a.m64[i]);
+    }
+    int key = (cz * S.ny + cy) * S.nx + cx;
+    a.key[i] = key;
+    a.rank[i] = atomicAdd(a.ccount + S.c0 + key, 1);
+}
+
+void launch_keys(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
+{
+    if (z.N == 0) return;
+    cudaMemsetAsync(a.ccount, 0, sizeof(int32_t) * z.C, st);
+    unsigned nb = (unsigned)((z.N + 255) / 256);
+    if (fp64) k_keys<true><<<nb, 256, 0, st>>>(a, z);
+    else k_keys<false><<<nb, 256, 0, st>>>(a, z);
+}
+
+// ---------------------------------------------------------------- scan of cell counts
+// Tiles of kScanTile cells never straddle piles (cell ranges are padded).
+__device__ int tile_pile(const Arrays &a, const Sizes &z, int64_t t)
+{
+    int lo = 0, hi = (int)z.P - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (a.ps[mid].t0 <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_scan_tiles(Arrays a, Sizes z)
+{
+    int64_t t = blockIdx.x;
+    int p = tile_pile(a, z, t);
+    if (!pile_active(a, p)) return;
+    const int32_t *c = a.ccount + t * kScanTile;
+    int s = 0;
+    for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) s += c[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ int ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += ws[k];
+        a.tile_sum[t] = tot;
+    }
+}
+
+// One block per pile: exclusive scan of its tile sums (in place).
+__global__ void k_scan_piles(Arrays a, Sizes z)
+{
+    int p = blockIdx.x;
+    if (!pile_active(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    __shared__ int buf[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < S.nt; base += 1024) {
+        int64_t t = base + threadIdx.x;
+        int v = t < S.nt ? a.tile_sum[S.t0 + t] : 0;
+        buf[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            int add = threadIdx.x >= (unsigned)o ? buf[threadIdx.x - o] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += add;
+            __syncthreads();
+        }
+        int incl = buf[threadIdx.x];
+        if (t < S.nt) a.tile_sum[S.t0 + t] = carry + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += incl;
+        __syncthreads();
+    }
+}
+
+// One block (256 threads x 8 cells) per tile: exclusive scan plus tile offset.
+__global__ void k_scan_cells(Arrays a, Sizes z)
+{
+    int64_t t = blockIdx.x;
+    int p = tile_pile(a, z, t);
+    if (!pile_active(a, p)) return;
+    const int32_t *c = a.ccount + t * kScanTile;
+    int32_t *o = a.cstart + t * kScanTile;
+    int v[8];
+    int loc = 0;
+    for (int k = 0; k < 8; ++k) {
+        v[k] = c[threadIdx.x * 8 + k];
+        loc += v[k];
+    }
+    __shared__ int buf[256];
+    buf[threadIdx.x] = loc;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        int add = threadIdx.x >= (unsigned)off ? buf[threadIdx.x - off] : 0;
+        __syncthreads();
+        buf[threadIdx.x] += add;
+        __syncthreads();
+    }
+    int run = a.tile_sum[t] + buf[threadIdx.x] - loc;
+    for (int k = 0; k < 8; ++k) {
+        o[threadIdx.x * 8 + k] = run;
+        run += v[k];
+    }
+}
+
+void launch_scan(const Arrays &a, const Sizes &z, cudaStream_t st)
+{
+    if (z.T == 0) return;
+    k_scan_tiles<<<(unsigned)z.T, 256, 0, st>>>(a, z);
+    k_scan_piles<<<(unsigned)z.P, 1024, 0, st>>>(a, z);
+    k_scan_cells<<<(unsigned)z.T, 256, 0, st>>>(a, z);
+}
+
+// ---------------------------------------------------------------- scatter and cell order
+__global__ void k_scatter(Arrays a, Sizes z)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= z.N) return;
+    int p = a.sph_pile[i];
+    if (!pile_active(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    int slot = a.cstart[S.c0 + a.key[i]] + a.rank[i];
+    a.sorted[S.s0 + slot] = (int32_t)(i - S.s0);
+}
+
+void launch_scatter(const Arrays &a, const Sizes &z, cudaStream_t st)
+{
+    if (z.N == 0) return;
+    k_scatter<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+}
+
+// The thread at the first position of each cell sorts that cell's entries by
+// home index (insertion sort; cells hold a handful of spheres), which makes
+// the order of neighbours, and so every contact sum, deterministic.
+__global__ void k_cell_order(Arrays a, Sizes z)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= z.N) return;
+    int p = a.sph_pile[k];
+    if (!pile_active(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    int32_t *srt = a.sorted + S.s0;
+    int kl = (int)(k - S.s0);
+    int key = a.key[S.s0 + srt[kl]];
+    int start = a.cstart[S.c0 + key];
+    if (kl != start) return;
+    int n = a.ccount[S.c0 + key];
+    for (int x = 1; x < n; ++x) {
+        int v = srt[start + x];
+        int y = x - 1;
+        while (y >= 0 && srt[start + y] > v) {
+            srt[start + y + 1] = srt[start + y];
+            --y;
+        }
+        srt[start + y + 1] = v;
+    }
+}
+
+void launch_cell_order(const Arrays &a, const Sizes &z, cudaStream_t st)
+{
+    if (z.N == 0) return;
+    k_cell_order<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+}
+
+// ---------------------------------------------------------------- gather
+// Sorted copies for the contact pass: position (float-float in mixed), predicted
+// velocity v_i = [v_A + h/2 a_A] + w_A x (r_i - r_A) (Eq. pred-vel), spin, ids.
+template <bool FP64>
+__global__ void k_gather(Arrays a, Sizes z)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= z.N) return;
+    int p = a.sph_pile[k];
+    if (!pile_active(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    int hl = a.sorted[k];
+    int64_t i = S.s0 + hl;
+    int al = a.sph_agg[i];
+    int64_t g = S.a0 + al;
+    if (FP64) {
+        const AggRec64 &rec = a.rec64[g];
+        const double *b = a.b64 + 3 * i;
+        double3 pos = expand_64(rec, b);
+        double3 rb = mat_mul(rec.R, d3(b[0], b[1], b[2]));
+        double3 w = ld3(rec.w);
+        double3 v = ld3(rec.vb) + cross(w, rb);
+        a.dp_[k] = make_dbl4(pos.x, pos.y, pos.z, a.s64[i]);
+        a.dv_[k] = make_dbl4(v.x, v.y, v.z, (double)al);
+        a.dw_[k] = make_dbl4(w.x, w.y, w.z, (double)hl);
+    } else {
+        const AggRecMixed &rec = a.rec32[g];
+        float4 bh = a.bh[i], bl = a.bl[i];
+        ff px, py, pz;
+        expand_mixed(rec, bh, bl, px, py, pz);
+        float3 rb = f3(rec.Rh[0] * bh.x + rec.Rh[1] * bh.y + rec.Rh[2] * bh.z,
+                       rec.Rh[3] * bh.x + rec.Rh[4] * bh.y + rec.Rh[5] * bh.z,
+                       rec.Rh[6] * bh.x + rec.Rh[7] * bh.y + rec.Rh[8] * bh.z);
+        float3 w = f3(rec.w[0], rec.w[1], rec.w[2]);
+        float3 v = f3(rec.vb[0], rec.vb[1], rec.vb[2]) + cross(w, rb);
+        a.sph_[k] = make_float4(px.hi, py.hi, pz.hi, bh.w);
+        a.spl_[k] = make_float4(px.lo, py.lo, pz.lo, bl.w);
+        a.sv_[k] = make_float4(v.x, v.y, v.z, __int_as_float(al));
+        a.sw_[k] = make_float4(w.x, w.y, w.z, __int_as_float(hl));
+    }
+}
+
+void launch_gather(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
+{
+    if (z.N == 0) return;
+    unsigned nb = (unsigned)((z.N + 255) / 256);
+    if (fp64) k_gather<true><<<nb, 256, 0, st>>>(a, z);
+    else k_gather<false><<<nb, 256, 0, st>>>(a, z);
+}
+
+// ---------------------------------------------------------------- step end
+// Per aggregate: F_A = sum_i (F_c,i + F_g,i + F_e,i) and
+// N_A = sum_i [(r_i - r_A) x F_i + tau_i], kept separately for contact,
+// gravity and planet; a_A = F_A / M; closing half kick of COM and spin; YORP
+// increment dw: v_A += dw x (r_A - R_pile), w_A += dw (rigid rotation of the
+// whole pile).  Members are contiguous (spheres stored in aggregate order).
+template <bool FP64>
+__global__ void k_agg_end(Arrays a, Sizes z)
+{
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= z.A) return;
+    int p = a.agg_pile[g];
+    if (!pile_active(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    const PileDyn &D = a.pd[p];
+    const double h = S.h;
+    int64_t i0 = S.s0 + a.agg_first[g];
+    int n = a.agg_count[g];
+    double3 Fc = d3(0, 0, 0), Nc = d3(0, 0, 0), Fg = d3(0, 0, 0), Ng = d3(0, 0, 0);
+    double3 Fe = d3(0, 0, 0), Ne = d3(0, 0, 0);
+    const bool planet = S.ext_mass > 0;
+    double3 Pp = planet ? ld3(D.P_pos) : d3(0, 0, 0);
+    double3 O = ld3(D.O);
+    for (int t = 0; t < n; ++t) {
+        int64_t i = i0 + t;
+        double3 lever, fc, tc, pos;
+        if (FP64) {
+            const AggRec64 &rec = a.rec64[g];
+            const double *b = a.b64 + 3 * i;
+            lever = mat_mul(rec.R, d3(b[0], b[1], b[2]));
+            dbl4 f = a.fc64[i], tq = a.tc64[i];
+            fc = d3(f.x, f.y, f.z);
+            tc = d3(tq.x, tq.y, tq.z);
+            if (planet) pos = O + expand_64(rec, b);
+        } else {
+            const AggRecMixed &rec = a.rec32[g];
+            float4 bh = a.bh[i];
+            lever = d3(rec.Rh[0] * bh.x + rec.Rh[1] * bh.y + rec.Rh[2] * bh.z,
+                       rec.Rh[3] * bh.x + rec.Rh[4] * bh.y + rec.Rh[5] * bh.z,
+                       rec.Rh[6] * bh.x + rec.Rh[7] * bh.y + rec.Rh[8] * bh.z);
+            float4 f = a.fc32[i], tq = a.tc32[i];
+            fc = d3(f.x, f.y, f.z);
+            tc = d3(tq.x, tq.y, tq.z);
+            if (planet) {
+                ff px, py, pz;
+                expand_mixed(rec, bh, a.bl[i], px, py, pz);
+                pos = O + d3((double)px.hi + (double)px.lo, (double)py.hi + (double)py.lo,
+                             (double)pz.hi + (double)pz.lo);
+            }
+        }
+        dbl4 gg = a.fg[i];
+        double3 fg = d3(gg.x, gg.y, gg.z);
+        Fc = Fc + fc;
+        Nc = Nc + cross(lever, fc) + tc;
+        Fg = Fg + fg;
+        Ng = Ng + cross(lever, fg);
+        if (planet) {
+            double3 d = Pp - pos;
+            double r2 = dot(d, d);
+            double inv = 1.0 / sqrt(r2);
+            double3 fe = (S.G * S.ext_mass * a.m64[i] * inv * inv * inv) * d;
+            Fe = Fe + fe;
+            Ne = Ne + cross(lever, fe);
+        }
+    }
+    double *o = a.out + 18 * g;
+    st3(o + 0, Fc); st3(o + 3, Nc); st3(o + 6, Fg); st3(o + 9, Ng); st3(o + 12, Fe); st3(o + 15, Ne);
+    double3 F = Fc + Fg + Fe, N = Nc + Ng + Ne;
+    double M = a.M[g];
+    double3 acc = d3(F.x / M, F.y / M, F.z / M);
+    double q[4] = {a.q[4 * g], a.q[4 * g + 1], a.q[4 * g + 2], a.q[4 * g + 3]};
+    double R[9];
+    quat_to_R(q, R);
+    double3 v = ld3(a.v + 3 * g) + (0.5 * h) * acc;
+    double3 wb = ld3(a.wb + 3 * g) + (0.5 * h) * mat_mul(a.Iinv + 9 * g, mat_tmul(R, N));
+    double3 dw = ld3(S.spin_inc);
+    if (dw.x != 0.0 || dw.y != 0.0 || dw.z != 0.0) {
+        double3 rel = ld3(a.r + 3 * g) - ld3(D.Rc);
+        v = v + cross(dw, rel);
+        wb = wb + mat_tmul(R, dw);
+    }
+    st3(a.acc + 3 * g, acc);
+    st3(a.torque + 3 * g, N);
+    st3(a.v + 3 * g, v);
+    st3(a.wb + 3 * g, wb);
+    if (!finite3(v) || !finite3(wb) || !finite3(N) || !finite3(ld3(a.r + 3 * g)))
+        atomicOr(&a.pd[p].flags, DEM_FLAG_NONFINITE);
+}
+
+void launch_agg_end(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
+{
+    if (z.A == 0) return;
+    unsigned nb = (unsigned)((z.A + 127) / 128);
+    if (fp64) k_agg_end<true><<<nb, 128, 0, st>>>(a, z);
+    else k_agg_end<false><<<nb, 128, 0, st>>>(a, z);
+}
+
+}  // namespace dem

@@ -1,0 +1,1126 @@
+// world.cpp -- the C ABI of include/dem.h: world and pile management, host
+// set-up of aggregates in FP64, device layout (every pile contiguous in every
+// array, pile-local indices inside), the per-step launch sequence captured
+// once into a CUDA graph, readout and error reporting.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dem_internal.h"
+
+using namespace dem;
+
+namespace {
+
+enum Cls { C_SPH, C_SPHK, C_AGG, C_CELL, C_TILE, C_CHUNK, C_PILE, C_GITEM, C_GPART, C_NCLS };
+
+struct Field {
+    void **ptr;
+    Cls cls;
+    size_t el;
+    bool keep;   // preserved (per-pile ranges copied) when the layout changes
+};
+
+struct PileHost {
+    int32_t id;
+    int64_t ns, na, nc, nch, nt;
+    int nx, ny, nz;
+    double cell, smax;
+    dem_params P;
+    double M_total;
+    bool reported;
+};
+
+}  // namespace
+
+struct dem_world {
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;
+    dem_alloc_fn alloc = nullptr;
+    dem_free_fn free_fn = nullptr;
+    void *ctx = nullptr;
+    std::string err = "";
+    int precision = -1;
+    int K = -1;
+    std::vector<PileHost> piles;   // in layout order
+    int32_t next_id = 0;
+    Arrays A{};
+    Sizes Z{};
+    int64_t cap[C_NCLS] = {0};
+    std::vector<Field> fields;
+    size_t held = 0;
+    // graph
+    cudaGraphExec_t exec = nullptr;
+    bool graph_valid = false;
+    // tuning
+    int grav_block = 128, grav_ib = 2;
+    int64_t grav_jchunk = 0;
+    double cell_factor = 1.0;
+    // flags readback
+    PileDyn *h_dyn = nullptr;   // pinned
+    int64_t h_dyn_cap = 0;
+    cudaEvent_t ev_flags = nullptr;
+    bool pending = false;
+    int64_t pending_n = 0;
+    bool own_stream = false;
+};
+
+namespace {
+
+dem_status fail(dem_world *w, dem_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (w) w->err = buf;
+    return s;
+}
+
+#define CU(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(w, DEM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+
+void *dev_alloc(dem_world *w, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (w->alloc) {
+        p = w->alloc(bytes, (void *)w->stream, w->ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dev_free(dem_world *w, void *p)
+{
+    if (!p) return;
+    if (w->free_fn) w->free_fn(p, w->ctx);
+    else cudaFree(p);
+}
+
+void build_fields(dem_world *w)
+{
+    Arrays &a = w->A;
+    bool d = w->precision == DEM_FP64;
+    auto add = [&](void **p, Cls c, size_t el, bool keep) { w->fields.push_back({p, c, el, keep}); };
+    w->fields.clear();
+    add((void **)&a.sph_agg, C_SPH, 4, true);
+    add((void **)&a.sph_pile, C_SPH, 4, false);
+    add((void **)&a.b64, C_SPH, 24, true);
+    add((void **)&a.s64, C_SPH, 8, true);
+    add((void **)&a.m64, C_SPH, 8, true);
+    add((void **)&a.key, C_SPH, 4, false);
+    add((void **)&a.rank, C_SPH, 4, false);
+    add((void **)&a.sorted, C_SPH, 4, false);
+    add((void **)&a.fg, C_SPH, 32, true);
+    add((void **)&a.hist_n[0], C_SPH, 4, true);
+    add((void **)&a.hist_n[1], C_SPH, 4, true);
+    if (d) {
+        add((void **)&a.dp_, C_SPH, 32, false);
+        add((void **)&a.dv_, C_SPH, 32, false);
+        add((void **)&a.dw_, C_SPH, 32, false);
+        add((void **)&a.gpos64, C_SPH, 32, false);
+        add((void **)&a.fc64, C_SPH, 32, true);
+        add((void **)&a.tc64, C_SPH, 32, true);
+        add((void **)&a.hist64[0], C_SPHK, 32, true);
+        add((void **)&a.hist64[1], C_SPHK, 32, true);
+        add((void **)&a.rec64, C_AGG, sizeof(AggRec64), false);
+    } else {
+        add((void **)&a.bh, C_SPH, 16, true);
+        add((void **)&a.bl, C_SPH, 16, true);
+        add((void **)&a.sph_, C_SPH, 16, false);
+        add((void **)&a.spl_, C_SPH, 16, false);
+        add((void **)&a.sv_, C_SPH, 16, false);
+        add((void **)&a.sw_, C_SPH, 16, false);
+        add((void **)&a.gpos32, C_SPH, 16, false);
+        add((void **)&a.fc32, C_SPH, 16, true);
+        add((void **)&a.tc32, C_SPH, 16, true);
+        add((void **)&a.hist32[0], C_SPHK, 16, true);
+        add((void **)&a.hist32[1], C_SPHK, 16, true);
+        add((void **)&a.rec32, C_AGG, sizeof(AggRecMixed), false);
+    }
+    add((void **)&a.agg_first, C_AGG, 4, true);
+    add((void **)&a.agg_count, C_AGG, 4, true);
+    add((void **)&a.agg_pile, C_AGG, 4, false);
+    add((void **)&a.M, C_AGG, 8, true);
+    add((void **)&a.I, C_AGG, 72, true);
+    add((void **)&a.Iinv, C_AGG, 72, true);
+    add((void **)&a.r, C_AGG, 24, true);
+    add((void **)&a.v, C_AGG, 24, true);
+    add((void **)&a.q, C_AGG, 32, true);
+    add((void **)&a.wb, C_AGG, 24, true);
+    add((void **)&a.acc, C_AGG, 24, true);
+    add((void **)&a.torque, C_AGG, 24, true);
+    add((void **)&a.out, C_AGG, 144, true);
+    add((void **)&a.ccount, C_CELL, 4, false);
+    add((void **)&a.cstart, C_CELL, 4, false);
+    add((void **)&a.tile_sum, C_TILE, 4, false);
+    add((void **)&a.chunk_part, C_CHUNK, 8 * kPartialDoubles, false);
+    add((void **)&a.chunk_pile, C_CHUNK, 4, false);
+    add((void **)&a.ps, C_PILE, sizeof(PileStatic), false);
+    add((void **)&a.pd, C_PILE, sizeof(PileDyn), true);
+    add((void **)&a.enabled, C_PILE, 4, false);
+    add((void **)&a.gpart_base, C_PILE, 8, false);
+    add((void **)&a.gnchunk, C_PILE, 4, false);
+    add((void **)&a.gitems, C_GITEM, 16, false);
+    add((void **)&a.gpart, C_GPART, 32, false);
+}
+
+// Elements of class c that pile q occupies (and its per-element multiplier).
+int64_t pile_count(const dem_world *w, const PileHost &q, Cls c)
+{
+    switch (c) {
+    case C_SPH: return q.ns;
+    case C_SPHK: return q.ns * w->K;
+    case C_AGG: return q.na;
+    case C_CELL: return q.nc;
+    case C_TILE: return q.nt;
+    case C_CHUNK: return q.nch;
+    case C_PILE: return 1;
+    default: return 0;
+    }
+}
+
+struct GravPlan {
+    std::vector<int4> items;
+    std::vector<int64_t> base;
+    std::vector<int32_t> nch;
+    int64_t gp = 0;
+};
+
+GravPlan plan_gravity(const dem_world *w)
+{
+    GravPlan g;
+    int BI = w->grav_block * w->grav_ib;
+    struct It { int4 v; int64_t cost; };
+    std::vector<It> its;
+    for (size_t p = 0; p < w->piles.size(); ++p) {
+        const PileHost &q = w->piles[p];
+        int64_t ns = q.ns;
+        int64_t nch = 1;
+        if (w->grav_jchunk > 0 && ns > w->grav_jchunk) nch = (ns + w->grav_jchunk - 1) / w->grav_jchunk;
+        int64_t jc = (ns + nch - 1) / nch;
+        g.nch.push_back((int32_t)nch);
+        if (nch > 1) {
+            g.base.push_back(g.gp);
+            g.gp += nch * ns;
+        } else {
+            g.base.push_back(-1);
+        }
+        for (int64_t i0 = 0; i0 < ns; i0 += BI)
+            for (int64_t c = 0; c < nch; ++c) {
+                int64_t j0 = c * jc, j1 = std::min(ns, (c + 1) * jc);
+                its.push_back({make_int4((int)p, (int)i0, (int)j0, (int)j1), j1 - j0});
+            }
+    }
+    std::stable_sort(its.begin(), its.end(), [](const It &x, const It &y) { return x.cost > y.cost; });
+    for (auto &x : its) g.items.push_back(x.v);
+    return g;
+}
+
+int64_t need_of(const dem_world *w, Cls c, const std::vector<PileHost> &piles, const GravPlan *gp)
+{
+    if (c == C_GITEM) return gp ? (int64_t)gp->items.size() : 0;
+    if (c == C_GPART) return gp ? gp->gp : 0;
+    int64_t n = 0;
+    for (auto &q : piles) n += pile_count(w, q, c);
+    return n;
+}
+
+// Move to a new layout: `newp` is the new pile list (a subset of the old one
+// in the same order, possibly plus piles appended at the end).  Preserved
+// fields of surviving piles are copied range by range.  Capacities grow by
+// 1.5x when exceeded; a shrinking layout reuses the capacity.
+dem_status relayout(dem_world *w, const std::vector<PileHost> &newp, const GravPlan *gp)
+{
+    int64_t need[C_NCLS], ncap[C_NCLS];
+    bool grow = false;
+    for (int c = 0; c < C_NCLS; ++c) {
+        need[c] = need_of(w, (Cls)c, newp, gp);
+        ncap[c] = w->cap[c];
+        if (need[c] > w->cap[c]) {
+            ncap[c] = std::max<int64_t>(need[c], (int64_t)(1.5 * (double)w->cap[c]));
+            grow = true;
+        }
+    }
+    // bytes after the change
+    size_t total = 0;
+    for (auto &f : w->fields) total += f.el * (size_t)ncap[f.cls];
+    if (w->budget && total > w->budget)
+        return fail(w, DEM_ERR_OOM, "HBM budget exceeded: need %zu bytes, budget %zu", total, w->budget);
+    // old and new offsets of the surviving piles
+    std::vector<int64_t> old_off[C_NCLS];
+    for (int c = 0; c < C_NCLS; ++c) {
+        int64_t o = 0;
+        for (auto &q : w->piles) { old_off[c].push_back(o); o += pile_count(w, q, (Cls)c); }
+    }
+    // map each new pile to its old slot (-1 = new)
+    std::vector<int> from(newp.size(), -1);
+    for (size_t k = 0; k < newp.size(); ++k)
+        for (size_t o = 0; o < w->piles.size(); ++o)
+            if (w->piles[o].id == newp[k].id) from[k] = (int)o;
+    bool moved = grow || newp.size() < w->piles.size();
+    for (size_t k = 0; k < newp.size() && !moved; ++k)
+        if (from[k] >= 0 && from[k] != (int)k) moved = true;
+    if (!moved) {
+        // only the transient classes may need new capacity (none grew)
+        return DEM_OK;
+    }
+    std::vector<void *> fresh(w->fields.size(), nullptr);
+    for (size_t f = 0; f < w->fields.size(); ++f) {
+        fresh[f] = dev_alloc(w, w->fields[f].el * (size_t)ncap[w->fields[f].cls]);
+        if (!fresh[f]) {
+            for (size_t g = 0; g < f; ++g) dev_free(w, fresh[g]);
+            return fail(w, DEM_ERR_OOM, "device allocation of %zu bytes failed",
+                        w->fields[f].el * (size_t)ncap[w->fields[f].cls]);
+        }
+    }
+    for (size_t f = 0; f < w->fields.size(); ++f) {
+        const Field &fd = w->fields[f];
+        if (!fd.keep || *fd.ptr == nullptr) continue;
+        int64_t o = 0;
+        for (size_t k = 0; k < newp.size(); ++k) {
+            int64_t n = pile_count(w, newp[k], fd.cls);
+            if (from[k] >= 0 && n > 0) {
+                size_t src = (size_t)old_off[fd.cls][from[k]] * fd.el;
+                CU(cudaMemcpyAsync((char *)fresh[f] + (size_t)o * fd.el, (char *)*fd.ptr + src,
+                                   (size_t)n * fd.el, cudaMemcpyDeviceToDevice, w->stream));
+            }
+            o += n;
+        }
+    }
+    CU(cudaStreamSynchronize(w->stream));
+    for (size_t f = 0; f < w->fields.size(); ++f) {
+        dev_free(w, *w->fields[f].ptr);
+        *w->fields[f].ptr = fresh[f];
+    }
+    for (int c = 0; c < C_NCLS; ++c) w->cap[c] = ncap[c];
+    w->held = total;
+    return DEM_OK;
+}
+
+// Rebuild the device pile table, ids and the gravity plan; capture the graph.
+dem_status upload_tables(dem_world *w, const GravPlan &gp)
+{
+    std::vector<PileStatic> ps;
+    int64_t s0 = 0, a0 = 0, c0 = 0, ch0 = 0;
+    for (auto &q : w->piles) {
+        PileStatic S{};
+        S.s0 = s0; S.ns = q.ns; S.a0 = a0; S.na = q.na; S.c0 = c0; S.nc = q.nc;
+        S.ch0 = ch0; S.nch = q.nch; S.t0 = c0 / kScanTile; S.nt = q.nt;
+        S.nx = q.nx; S.ny = q.ny; S.nz = q.nz; S.K = w->K;
+        S.cell = q.cell; S.inv_cell = 1.0 / q.cell;
+        const dem_params &P = q.P;
+        S.G = P.G; S.h = P.dt; S.kn = P.kn; S.kt = P.kt; S.cn = P.cn; S.ct = P.ct;
+        S.mu_s = P.mu_s; S.mu_r = P.mu_r; S.mu_t = P.mu_t; S.w0 = P.w0;
+        S.eps2 = P.eps_soft * P.eps_soft;
+        S.ext_mass = P.ext_mass; S.M_total = q.M_total;
+        for (int c = 0; c < 3; ++c) S.spin_inc[c] = P.spin_inc[c];
+        ps.push_back(S);
+        s0 += q.ns; a0 += q.na; c0 += q.nc; ch0 += q.nch;
+    }
+    w->Z.N = s0; w->Z.A = a0; w->Z.C = c0; w->Z.T = c0 / kScanTile; w->Z.CH = ch0;
+    w->Z.P = (int64_t)w->piles.size();
+    w->Z.GI = (int64_t)gp.items.size();
+    w->Z.GP = gp.gp;
+    if (!ps.empty()) {
+        CU(cudaMemcpyAsync(w->A.ps, ps.data(), sizeof(PileStatic) * ps.size(),
+                           cudaMemcpyHostToDevice, w->stream));
+        CU(cudaMemcpyAsync(w->A.gpart_base, gp.base.data(), 8 * gp.base.size(),
+                           cudaMemcpyHostToDevice, w->stream));
+        CU(cudaMemcpyAsync(w->A.gnchunk, gp.nch.data(), 4 * gp.nch.size(),
+                           cudaMemcpyHostToDevice, w->stream));
+    }
+    if (!gp.items.empty())
+        CU(cudaMemcpyAsync(w->A.gitems, gp.items.data(), 16 * gp.items.size(),
+                           cudaMemcpyHostToDevice, w->stream));
+    launch_fill_ids(w->A, w->Z, w->stream);
+    CU(cudaGetLastError());
+    return DEM_OK;
+}
+
+void enqueue_phase(dem_world *w, int ph)
+{
+    const Arrays &a = w->A;
+    const Sizes &z = w->Z;
+    bool d = w->precision == DEM_FP64;
+    cudaStream_t st = w->stream;
+    switch (ph) {
+    case DEM_K_AGG_BEGIN: launch_agg_begin(a, z, d, st); break;
+    case DEM_K_PILE_BEGIN: launch_pile_begin(a, z, st); break;
+    case DEM_K_KEYS: launch_keys(a, z, d, st); break;
+    case DEM_K_SCAN: launch_scan(a, z, st); break;
+    case DEM_K_SCATTER: launch_scatter(a, z, st); break;
+    case DEM_K_CELL_ORDER: launch_cell_order(a, z, st); break;
+    case DEM_K_GATHER: launch_gather(a, z, d, st); break;
+    case DEM_K_CONTACT: launch_contact(a, z, d, st); break;
+    case DEM_K_GRAVITY: launch_gravity(a, z, d, w->grav_block, w->grav_ib, st); break;
+    case DEM_K_AGG_END: launch_agg_end(a, z, d, st); break;
+    case DEM_K_PILE_END: launch_pile_end(a, z, st); break;
+    default: break;
+    }
+}
+
+dem_status prepare(dem_world *w)
+{
+    if (w->graph_valid) return DEM_OK;
+    GravPlan gp = plan_gravity(w);
+    dem_status s = relayout(w, w->piles, &gp);
+    if (s != DEM_OK) return s;
+    s = upload_tables(w, gp);
+    if (s != DEM_OK) return s;
+    if (w->exec) {
+        cudaGraphExecDestroy(w->exec);
+        w->exec = nullptr;
+    }
+    if (w->piles.empty()) {
+        w->graph_valid = true;
+        return DEM_OK;
+    }
+    CU(cudaStreamSynchronize(w->stream));
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(w->stream, cudaStreamCaptureModeThreadLocal));
+    for (int ph = 0; ph < DEM_K_COUNT; ++ph) enqueue_phase(w, ph);
+    cudaError_t e = cudaStreamEndCapture(w->stream, &g);
+    if (e != cudaSuccess) return fail(w, DEM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&w->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(w, DEM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    w->graph_valid = true;
+    return DEM_OK;
+}
+
+int find_pile(const dem_world *w, int32_t id)
+{
+    for (size_t k = 0; k < w->piles.size(); ++k)
+        if (w->piles[k].id == id) return (int)k;
+    return -1;
+}
+
+// Wait for the flag words of the last dem_step and turn newly failed piles
+// into a status.
+dem_status collect_flags(dem_world *w)
+{
+    if (!w->pending) return DEM_OK;
+    w->pending = false;
+    CU(cudaEventSynchronize(w->ev_flags));
+    dem_status st = DEM_OK;
+    for (size_t k = 0; k < w->piles.size() && (int64_t)k < w->pending_n; ++k) {
+        PileHost &q = w->piles[k];
+        const PileDyn &D = w->h_dyn[k];
+        if (!q.reported && D.failed) {
+            q.reported = true;
+            if (D.flags & DEM_FLAG_NONFINITE) {
+                st = DEM_ERR_NONFINITE;
+                fail(w, st, "pile %d: state became non-finite; pile frozen", q.id);
+            } else if (st == DEM_OK) {
+                st = DEM_ERR_SLOTS;
+                fail(w, st, "pile %d: more contacts than %d history slots; pile frozen", q.id, w->K);
+            }
+        }
+    }
+    return st;
+}
+
+dem_status issue_flags_readback(dem_world *w)
+{
+    int64_t P = (int64_t)w->piles.size();
+    if (P == 0) return DEM_OK;
+    if (P > w->h_dyn_cap) {
+        if (w->h_dyn) cudaFreeHost(w->h_dyn);
+        w->h_dyn = nullptr;
+        CU(cudaMallocHost((void **)&w->h_dyn, sizeof(PileDyn) * (size_t)P * 2));
+        w->h_dyn_cap = P * 2;
+    }
+    CU(cudaMemcpyAsync(w->h_dyn, w->A.pd, sizeof(PileDyn) * (size_t)P, cudaMemcpyDeviceToHost,
+                       w->stream));
+    CU(cudaEventRecord(w->ev_flags, w->stream));
+    w->pending = true;
+    w->pending_n = P;
+    return DEM_OK;
+}
+
+dem_status set_enabled(dem_world *w, const int32_t *ids, int32_t n)
+{
+    std::vector<int32_t> en(w->piles.size(), ids ? 0 : 1);
+    if (ids) {
+        for (int32_t k = 0; k < n; ++k) {
+            int s = find_pile(w, ids[k]);
+            if (s < 0) return fail(w, DEM_ERR_ARG, "unknown pile id %d", ids[k]);
+            en[s] = 1;
+        }
+    }
+    if (!en.empty())
+        CU(cudaMemcpyAsync(w->A.enabled, en.data(), 4 * en.size(), cudaMemcpyHostToDevice, w->stream));
+    return DEM_OK;
+}
+
+bool finite_all(const double *x, int64_t n)
+{
+    for (int64_t k = 0; k < n; ++k)
+        if (!std::isfinite(x[k])) return false;
+    return true;
+}
+
+void split(double x, float &hi, float &lo)
+{
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+void rotmat(const double *q, double *R)
+{
+    double w0 = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w0 * z);    R[2] = 2 * (x * z + w0 * y);
+    R[3] = 2 * (x * y + w0 * z);    R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w0 * x);
+    R[6] = 2 * (x * z - w0 * y);    R[7] = 2 * (y * z + w0 * x);    R[8] = 1 - 2 * (x * x + y * y);
+}
+
+// Wrapped grid for one pile: cell >= 2 x largest radius (times the tuning
+// factor), dims >= 3 so the 27 neighbour cells are distinct, total cells
+// capped near 4 x spheres by enlarging the cell.
+void choose_grid(const dem_world *w, PileHost &q, const double *pos_rel, int64_t N)
+{
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int64_t i = 0; i < N; ++i)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = std::min(lo[c], pos_rel[3 * i + c]);
+            hi[c] = std::max(hi[c], pos_rel[3 * i + c]);
+        }
+    double cell = q.P.cell_size > 0 ? q.P.cell_size : 2.0 * q.smax * (1.0 + 1e-6);
+    cell *= w->cell_factor;
+    int64_t cap = std::max<int64_t>(4 * N, 27);
+    int dims[3];
+    for (int it = 0; it < 200; ++it) {
+        int64_t tot = 1;
+        for (int c = 0; c < 3; ++c) {
+            double ext = hi[c] - lo[c] + 2.0 * q.smax;
+            int64_t n = (int64_t)std::ceil(ext / cell) + 2;
+            n = std::max<int64_t>(3, std::min<int64_t>(n, 1 << 20));
+            dims[c] = (int)n;
+            tot *= n;
+        }
+        if (tot <= cap) break;
+        cell *= std::cbrt((double)tot / (double)cap) * 1.01;
+    }
+    q.cell = cell;
+    q.nx = dims[0]; q.ny = dims[1]; q.nz = dims[2];
+    int64_t cells = (int64_t)q.nx * q.ny * q.nz;
+    q.nc = (cells + kScanTile - 1) / kScanTile * kScanTile;
+    q.nt = q.nc / kScanTile;
+}
+
+}  // namespace
+
+// =====================================================================
+extern "C" {
+
+dem_status dem_create(void *cuda_stream, size_t hbm_budget_bytes, dem_world **out)
+{
+    if (!out) return DEM_ERR_ARG;
+    dem_world *w = new dem_world();
+    w->stream = (cudaStream_t)cuda_stream;
+    w->budget = hbm_budget_bytes;
+    if (w->stream == nullptr) {   // graphs cannot be captured on the legacy stream
+        if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete w;
+            return DEM_ERR_CUDA;
+        }
+        w->own_stream = true;
+    }
+    if (cudaEventCreateWithFlags(&w->ev_flags, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete w;
+        return DEM_ERR_CUDA;
+    }
+    *out = w;
+    return DEM_OK;
+}
+
+dem_status dem_set_allocator(dem_world *w, dem_alloc_fn alloc, dem_free_fn free_fn, void *ctx)
+{
+    if (!w) return DEM_ERR_ARG;
+    if (w->held > 0) return fail(w, DEM_ERR_STATE, "allocator must be set before adding piles");
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(w, DEM_ERR_ARG, "alloc and free must both be set or both NULL");
+    w->alloc = alloc;
+    w->free_fn = free_fn;
+    w->ctx = ctx;
+    return DEM_OK;
+}
+
+dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
+                              const int32_t *spa, const double *pos, const double *rad,
+                              const double *dens, const double *agg_vel, const double *agg_omega,
+                              int32_t *out_pile_id)
+{
+    if (!w) return DEM_ERR_ARG;
+    if (!p || !spa || !pos || !rad || !dens || !out_pile_id || n_agg <= 0)
+        return fail(w, DEM_ERR_ARG, "NULL argument or n_agg <= 0");
+    if (n_agg > (int64_t)1 << 30) return fail(w, DEM_ERR_ARG, "too many aggregates");
+    if (p->precision != DEM_FP64 && p->precision != DEM_MIXED)
+        return fail(w, DEM_ERR_ARG, "precision must be DEM_FP64 or DEM_MIXED");
+    if (w->precision >= 0 && p->precision != w->precision)
+        return fail(w, DEM_ERR_ARG, "all piles of a world must use the same precision");
+    if (p->max_contacts < 1 || p->max_contacts > kMaxK)
+        return fail(w, DEM_ERR_ARG, "max_contacts must be in 1..%d", kMaxK);
+    if (w->K >= 0 && p->max_contacts != w->K)
+        return fail(w, DEM_ERR_ARG, "all piles of a world must use the same max_contacts");
+    const double scal[] = {p->G, p->dt, p->kn, p->kt, p->cn, p->ct, p->mu_s, p->mu_r, p->mu_t,
+                           p->w0, p->eps_soft, p->cell_size, p->ext_mass};
+    if (!finite_all(scal, 13) || !finite_all(p->ext_pos, 3) || !finite_all(p->ext_vel, 3) ||
+        !finite_all(p->spin_inc, 3))
+        return fail(w, DEM_ERR_ARG, "non-finite parameter");
+    if (!(p->dt > 0) || p->kn < 0 || p->kt < 0 || p->cn < 0 || p->ct < 0 || p->mu_s < 0 ||
+        p->mu_r < 0 || p->mu_t < 0 || !(p->w0 > 0) || p->eps_soft < 0 || p->G < 0 ||
+        p->ext_mass < 0 || p->cell_size < 0)
+        return fail(w, DEM_ERR_ARG, "parameter out of range (dt > 0, w0 > 0, others >= 0)");
+    int64_t N = 0;
+    for (int64_t a = 0; a < n_agg; ++a) {
+        if (spa[a] < 1) return fail(w, DEM_ERR_ARG, "aggregate %lld has %d spheres", (long long)a, spa[a]);
+        N += spa[a];
+    }
+    if (N > ((int64_t)1 << 30)) return fail(w, DEM_ERR_ARG, "too many spheres");
+    if (!finite_all(pos, 3 * N) || !finite_all(rad, N) || !finite_all(dens, N) ||
+        (agg_vel && !finite_all(agg_vel, 3 * n_agg)) || (agg_omega && !finite_all(agg_omega, 3 * n_agg)))
+        return fail(w, DEM_ERR_ARG, "non-finite input");
+    for (int64_t i = 0; i < N; ++i)
+        if (!(rad[i] > 0) || !(dens[i] > 0)) return fail(w, DEM_ERR_ARG, "radius and density must be > 0");
+
+    // ---- host set-up in FP64 (Sec. 2.2.1) ----
+    const int A = (int)n_agg;
+    std::vector<int32_t> first(A), sph_agg(N);
+    std::vector<double> m(N), b(3 * N), M(A), com(3 * A), I(9 * A), Iinv(9 * A);
+    std::vector<double> q(4 * A, 0.0), r(3 * A), v(3 * A, 0.0), wb(3 * A, 0.0), zero3(3 * A, 0.0);
+    double smax = 0, Mtot = 0, Rp[3] = {0, 0, 0}, Vp[3] = {0, 0, 0};
+    int64_t k = 0;
+    for (int a = 0; a < A; ++a) {
+        first[a] = (int32_t)k;
+        double Ma = 0, c[3] = {0, 0, 0};
+        for (int t = 0; t < spa[a]; ++t, ++k) {
+            m[k] = dens[k] * (4.0 / 3.0) * M_PI * rad[k] * rad[k] * rad[k];
+            sph_agg[k] = a;
+            Ma += m[k];
+            for (int d = 0; d < 3; ++d) c[d] += m[k] * pos[3 * k + d];
+            smax = std::max(smax, rad[k]);
+        }
+        for (int d = 0; d < 3; ++d) c[d] /= Ma;
+        M[a] = Ma;
+        double T[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int64_t i = first[a]; i < first[a] + spa[a]; ++i) {
+            double bi[3];
+            for (int d = 0; d < 3; ++d) bi[d] = b[3 * i + d] = pos[3 * i + d] - c[d];
+            double bb = bi[0] * bi[0] + bi[1] * bi[1] + bi[2] * bi[2];
+            double sph = 0.4 * m[i] * rad[i] * rad[i];
+            for (int x = 0; x < 3; ++x)
+                for (int y = 0; y < 3; ++y)
+                    T[3 * x + y] += (x == y ? sph + m[i] * bb : 0.0) - m[i] * bi[x] * bi[y];
+        }
+        // inverse by cofactors
+        double c00 = T[4] * T[8] - T[5] * T[7], c01 = T[5] * T[6] - T[3] * T[8],
+               c02 = T[3] * T[7] - T[4] * T[6];
+        double det = T[0] * c00 + T[1] * c01 + T[2] * c02;
+        if (!(std::fabs(det) > 0) || !std::isfinite(det))
+            return fail(w, DEM_ERR_ARG, "aggregate %d has a singular inertia tensor", a);
+        double inv[9] = {c00, T[2] * T[7] - T[1] * T[8], T[1] * T[5] - T[2] * T[4],
+                         c01, T[0] * T[8] - T[2] * T[6], T[2] * T[3] - T[0] * T[5],
+                         c02, T[1] * T[6] - T[0] * T[7], T[0] * T[4] - T[1] * T[3]};
+        for (int e = 0; e < 9; ++e) {
+            I[9 * a + e] = T[e];
+            Iinv[9 * a + e] = inv[e] / det;
+        }
+        for (int d = 0; d < 3; ++d) {
+            r[3 * a + d] = c[d];
+            if (agg_vel) v[3 * a + d] = agg_vel[3 * a + d];
+            if (agg_omega) wb[3 * a + d] = agg_omega[3 * a + d];
+        }
+        q[4 * a] = 1.0;
+        Mtot += Ma;
+        for (int d = 0; d < 3; ++d) { Rp[d] += Ma * c[d]; Vp[d] += Ma * v[3 * a + d]; }
+    }
+    for (int d = 0; d < 3; ++d) { Rp[d] /= Mtot; Vp[d] /= Mtot; }
+
+    PileHost ph{};
+    ph.id = w->next_id;
+    ph.ns = N;
+    ph.na = A;
+    ph.nch = (A + kAggChunk - 1) / kAggChunk;
+    ph.smax = smax;
+    ph.P = *p;
+    ph.M_total = Mtot;
+    {
+        std::vector<double> rel(3 * N);
+        for (int64_t i = 0; i < N; ++i)
+            for (int d = 0; d < 3; ++d) rel[3 * i + d] = pos[3 * i + d] - Rp[d];
+        if (p->cell_size > 0 && p->cell_size < 2.0 * smax)
+            return fail(w, DEM_ERR_ARG, "cell_size must be >= 2 x the largest radius");
+        choose_grid(w, ph, rel.data(), N);
+    }
+
+    // ---- first pile fixes the world's precision and slot count ----
+    bool first_pile = w->precision < 0;
+    if (first_pile) {
+        w->precision = p->precision;
+        w->K = p->max_contacts;
+        build_fields(w);
+    }
+    std::vector<PileHost> newp = w->piles;
+    newp.push_back(ph);
+    dem_status s = relayout(w, newp, nullptr);
+    if (s != DEM_OK) {
+        if (first_pile && w->piles.empty()) { w->precision = -1; w->K = -1; }
+        return s;
+    }
+    w->piles = newp;
+    w->next_id++;
+    w->graph_valid = false;
+
+    // ---- upload the new pile's ranges ----
+    int64_t s0 = 0, a0 = 0;
+    for (size_t t = 0; t + 1 < w->piles.size(); ++t) { s0 += w->piles[t].ns; a0 += w->piles[t].na; }
+    const int slot = (int)w->piles.size() - 1;
+    Arrays &D = w->A;
+    cudaStream_t st = w->stream;
+    auto up = [&](void *dst, const void *src, size_t bytes) -> dem_status {
+        CU(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+        return DEM_OK;
+    };
+#define UP(dst, src, bytes)                         \
+    do {                                            \
+        dem_status s_ = up((dst), (src), (bytes));  \
+        if (s_ != DEM_OK) return s_;                \
+    } while (0)
+    UP(D.sph_agg + s0, sph_agg.data(), 4 * N);
+    UP(D.b64 + 3 * s0, b.data(), 24 * N);
+    UP(D.s64 + s0, rad, 8 * N);
+    UP(D.m64 + s0, m.data(), 8 * N);
+    std::vector<int32_t> zeros_i(N, 0);
+    UP(D.hist_n[0] + s0, zeros_i.data(), 4 * N);
+    UP(D.hist_n[1] + s0, zeros_i.data(), 4 * N);
+    CU(cudaMemsetAsync(D.fg + s0, 0, 32 * N, st));
+    if (w->precision == DEM_MIXED) {
+        std::vector<float4> bh(N), bl(N);
+        for (int64_t i = 0; i < N; ++i) {
+            split(b[3 * i], bh[i].x, bl[i].x);
+            split(b[3 * i + 1], bh[i].y, bl[i].y);
+            split(b[3 * i + 2], bh[i].z, bl[i].z);
+            split(rad[i], bh[i].w, bl[i].w);
+        }
+        UP(D.bh + s0, bh.data(), 16 * N);
+        UP(D.bl + s0, bl.data(), 16 * N);
+        CU(cudaMemsetAsync(D.fc32 + s0, 0, 16 * N, st));
+        CU(cudaMemsetAsync(D.tc32 + s0, 0, 16 * N, st));
+    } else {
+        CU(cudaMemsetAsync(D.fc64 + s0, 0, 32 * N, st));
+        CU(cudaMemsetAsync(D.tc64 + s0, 0, 32 * N, st));
+    }
+    UP(D.agg_first + a0, first.data(), 4 * A);
+    UP(D.agg_count + a0, spa, 4 * A);
+    UP(D.M + a0, M.data(), 8 * A);
+    UP(D.I + 9 * a0, I.data(), 72 * A);
+    UP(D.Iinv + 9 * a0, Iinv.data(), 72 * A);
+    UP(D.r + 3 * a0, r.data(), 24 * A);
+    UP(D.v + 3 * a0, v.data(), 24 * A);
+    UP(D.q + 4 * a0, q.data(), 32 * A);
+    UP(D.wb + 3 * a0, wb.data(), 24 * A);
+    UP(D.acc + 3 * a0, zero3.data(), 24 * A);
+    UP(D.torque + 3 * a0, zero3.data(), 24 * A);
+    CU(cudaMemsetAsync(D.out + 18 * a0, 0, 144 * A, st));
+    PileDyn dyn{};
+    for (int d = 0; d < 3; ++d) {
+        dyn.O[d] = Rp[d]; dyn.V[d] = Vp[d]; dyn.Rc[d] = Rp[d]; dyn.Vc[d] = Vp[d];
+        dyn.P_pos[d] = p->ext_pos[d]; dyn.P_vel[d] = p->ext_vel[d]; dyn.P_acc[d] = 0.0;
+    }
+    UP(D.pd + slot, &dyn, sizeof dyn);
+#undef UP
+    CU(cudaStreamSynchronize(st));   // host staging vectors go out of scope
+    *out_pile_id = ph.id;
+    return DEM_OK;
+}
+
+dem_status dem_step(dem_world *w, const int32_t *pile_ids, int32_t n_piles, int64_t n_steps)
+{
+    if (!w) return DEM_ERR_ARG;
+    if (n_steps < 0 || (pile_ids && n_piles < 0)) return fail(w, DEM_ERR_ARG, "negative count");
+    dem_status prev = collect_flags(w);
+    if (n_steps == 0 || w->piles.empty()) return prev;
+    dem_status s = prepare(w);
+    if (s != DEM_OK) return s;
+    s = set_enabled(w, pile_ids, n_piles);
+    if (s != DEM_OK) return s;
+    for (int64_t t = 0; t < n_steps; ++t) CU(cudaGraphLaunch(w->exec, w->stream));
+    s = issue_flags_readback(w);
+    if (s != DEM_OK) return s;
+    return prev;
+}
+
+dem_status dem_sync(dem_world *w)
+{
+    if (!w) return DEM_ERR_ARG;
+    CU(cudaStreamSynchronize(w->stream));
+    return collect_flags(w);
+}
+
+dem_status dem_step_profiled(dem_world *w, int64_t n_steps, int32_t which, float *ms_out)
+{
+    if (!w) return DEM_ERR_ARG;
+    if (n_steps < 0 || which < 0 || which >= DEM_K_COUNT || (n_steps > 0 && !ms_out))
+        return fail(w, DEM_ERR_ARG, "bad arguments");
+    dem_status prev = collect_flags(w);
+    if (n_steps == 0 || w->piles.empty()) return prev;
+    dem_status s = prepare(w);
+    if (s != DEM_OK) return s;
+    s = set_enabled(w, nullptr, 0);
+    if (s != DEM_OK) return s;
+    std::vector<cudaEvent_t> ev(2 * (size_t)n_steps, nullptr);
+    for (auto &e : ev) CU(cudaEventCreate(&e));
+    for (int64_t t = 0; t < n_steps; ++t)
+        for (int ph = 0; ph < DEM_K_COUNT; ++ph) {
+            if (ph == which) CU(cudaEventRecord(ev[2 * t], w->stream));
+            enqueue_phase(w, ph);
+            if (ph == which) CU(cudaEventRecord(ev[2 * t + 1], w->stream));
+        }
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(w->stream));
+    for (int64_t t = 0; t < n_steps; ++t) CU(cudaEventElapsedTime(ms_out + t, ev[2 * t], ev[2 * t + 1]));
+    for (auto &e : ev) cudaEventDestroy(e);
+    s = issue_flags_readback(w);
+    if (s != DEM_OK) return s;
+    return prev;
+}
+
+dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *out, int64_t n_out)
+{
+    if (!w) return DEM_ERR_ARG;
+    int slot = find_pile(w, pile_id);
+    if (slot < 0) return fail(w, DEM_ERR_ARG, "unknown pile id %d", pile_id);
+    if (!out) return fail(w, DEM_ERR_ARG, "NULL output");
+    CU(cudaStreamSynchronize(w->stream));
+    const PileHost &q = w->piles[slot];
+    int64_t s0 = 0, a0 = 0;
+    for (int t = 0; t < slot; ++t) { s0 += w->piles[t].ns; a0 += w->piles[t].na; }
+    const int64_t N = q.ns, A = q.na;
+    const Arrays &D = w->A;
+    auto get = [&](void *dst, const void *src, size_t bytes) -> dem_status {
+        CU(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+        return DEM_OK;
+    };
+    auto need = [&](int64_t n) -> dem_status {
+        if (n_out < n) return fail(w, DEM_ERR_ARG, "output too small: need %lld doubles", (long long)n);
+        return DEM_OK;
+    };
+    dem_status s;
+#define CHK(x) do { s = (x); if (s != DEM_OK) return s; } while (0)
+    PileDyn dyn;
+    CHK(get(&dyn, D.pd + slot, sizeof dyn));
+    switch (field) {
+    case DEM_FIELD_COM: CHK(need(3 * A)); CHK(get(out, D.r + 3 * a0, 24 * A)); break;
+    case DEM_FIELD_VEL: CHK(need(3 * A)); CHK(get(out, D.v + 3 * a0, 24 * A)); break;
+    case DEM_FIELD_QUAT: CHK(need(4 * A)); CHK(get(out, D.q + 4 * a0, 32 * A)); break;
+    case DEM_FIELD_OMEGA_BODY: CHK(need(3 * A)); CHK(get(out, D.wb + 3 * a0, 24 * A)); break;
+    case DEM_FIELD_ACC: CHK(need(3 * A)); CHK(get(out, D.acc + 3 * a0, 24 * A)); break;
+    case DEM_FIELD_MASS: CHK(need(A)); CHK(get(out, D.M + a0, 8 * A)); break;
+    case DEM_FIELD_BODY_OFFSETS: CHK(need(3 * N)); CHK(get(out, D.b64 + 3 * s0, 24 * N)); break;
+    case DEM_FIELD_OMEGA: {
+        CHK(need(3 * A));
+        std::vector<double> qq(4 * A), ww(3 * A);
+        CHK(get(qq.data(), D.q + 4 * a0, 32 * A));
+        CHK(get(ww.data(), D.wb + 3 * a0, 24 * A));
+        for (int64_t a = 0; a < A; ++a) {
+            double R[9];
+            rotmat(&qq[4 * a], R);
+            for (int c = 0; c < 3; ++c)
+                out[3 * a + c] = R[3 * c] * ww[3 * a] + R[3 * c + 1] * ww[3 * a + 1] + R[3 * c + 2] * ww[3 * a + 2];
+        }
+        break;
+    }
+    case DEM_FIELD_SPHERE_POS: {
+        CHK(need(3 * N));
+        std::vector<double> qq(4 * A), rr(3 * A), bb(3 * N);
+        std::vector<int32_t> ag(N);
+        CHK(get(qq.data(), D.q + 4 * a0, 32 * A));
+        CHK(get(rr.data(), D.r + 3 * a0, 24 * A));
+        CHK(get(bb.data(), D.b64 + 3 * s0, 24 * N));
+        CHK(get(ag.data(), D.sph_agg + s0, 4 * N));
+        for (int64_t i = 0; i < N; ++i) {
+            int a = ag[i];
+            double R[9];
+            rotmat(&qq[4 * a], R);
+            for (int c = 0; c < 3; ++c)
+                out[3 * i + c] = rr[3 * a + c] + R[3 * c] * bb[3 * i] + R[3 * c + 1] * bb[3 * i + 1] +
+                                 R[3 * c + 2] * bb[3 * i + 2];
+        }
+        break;
+    }
+    case DEM_FIELD_FORCE: case DEM_FIELD_TORQUE:
+    case DEM_FIELD_FORCE_CONTACT: case DEM_FIELD_TORQUE_CONTACT:
+    case DEM_FIELD_FORCE_GRAV: case DEM_FIELD_TORQUE_GRAV:
+    case DEM_FIELD_FORCE_EXT: case DEM_FIELD_TORQUE_EXT: {
+        CHK(need(3 * A));
+        std::vector<double> o(18 * A);
+        CHK(get(o.data(), D.out + 18 * a0, 144 * A));
+        for (int64_t a = 0; a < A; ++a)
+            for (int c = 0; c < 3; ++c) {
+                const double *x = &o[18 * a];
+                double val = 0;
+                switch (field) {
+                case DEM_FIELD_FORCE: val = x[c] + x[6 + c] + x[12 + c]; break;
+                case DEM_FIELD_TORQUE: val = x[3 + c] + x[9 + c] + x[15 + c]; break;
+                case DEM_FIELD_FORCE_CONTACT: val = x[c]; break;
+                case DEM_FIELD_TORQUE_CONTACT: val = x[3 + c]; break;
+                case DEM_FIELD_FORCE_GRAV: val = x[6 + c]; break;
+                case DEM_FIELD_TORQUE_GRAV: val = x[9 + c]; break;
+                case DEM_FIELD_FORCE_EXT: val = x[12 + c]; break;
+                default: val = x[15 + c]; break;
+                }
+                out[3 * a + c] = val;
+            }
+        break;
+    }
+    case DEM_FIELD_SPHERE_FC: case DEM_FIELD_SPHERE_TC: case DEM_FIELD_SPHERE_FG: {
+        CHK(need(3 * N));
+        if (field == DEM_FIELD_SPHERE_FG) {
+            std::vector<dbl4> f(N);
+            CHK(get(f.data(), D.fg + s0, 32 * N));
+            for (int64_t i = 0; i < N; ++i) { out[3 * i] = f[i].x; out[3 * i + 1] = f[i].y; out[3 * i + 2] = f[i].z; }
+        } else if (w->precision == DEM_FP64) {
+            std::vector<dbl4> f(N);
+            CHK(get(f.data(), (field == DEM_FIELD_SPHERE_FC ? D.fc64 : D.tc64) + s0, 32 * N));
+            for (int64_t i = 0; i < N; ++i) { out[3 * i] = f[i].x; out[3 * i + 1] = f[i].y; out[3 * i + 2] = f[i].z; }
+        } else {
+            std::vector<float4> f(N);
+            CHK(get(f.data(), (field == DEM_FIELD_SPHERE_FC ? D.fc32 : D.tc32) + s0, 16 * N));
+            for (int64_t i = 0; i < N; ++i) { out[3 * i] = f[i].x; out[3 * i + 1] = f[i].y; out[3 * i + 2] = f[i].z; }
+        }
+        break;
+    }
+    case DEM_FIELD_CONTACTS: {
+        const int K = w->K;
+        CHK(need(N * (1 + 4 * (int64_t)K)));
+        int par = dyn.parity;
+        std::vector<int32_t> cnt(N);
+        CHK(get(cnt.data(), D.hist_n[par] + s0, 4 * N));
+        std::fill(out, out + N * (1 + 4 * (int64_t)K), 0.0);
+        if (w->precision == DEM_FP64) {
+            std::vector<dbl4> h(N * K);
+            CHK(get(h.data(), D.hist64[par] + s0 * K, 32 * N * K));
+            for (int64_t i = 0; i < N; ++i) {
+                double *o = out + i * (1 + 4 * K);
+                o[0] = cnt[i];
+                for (int t = 0; t < cnt[i]; ++t) {
+                    const dbl4 &e = h[i * K + t];
+                    o[1 + 4 * t] = e.w; o[2 + 4 * t] = e.x; o[3 + 4 * t] = e.y; o[4 + 4 * t] = e.z;
+                }
+            }
+        } else {
+            std::vector<float4> h(N * K);
+            CHK(get(h.data(), D.hist32[par] + s0 * K, 16 * N * K));
+            for (int64_t i = 0; i < N; ++i) {
+                double *o = out + i * (1 + 4 * K);
+                o[0] = cnt[i];
+                for (int t = 0; t < cnt[i]; ++t) {
+                    const float4 &e = h[i * K + t];
+                    int32_t pid;
+                    std::memcpy(&pid, &e.w, 4);
+                    o[1 + 4 * t] = pid; o[2 + 4 * t] = e.x; o[3 + 4 * t] = e.y; o[4 + 4 * t] = e.z;
+                }
+            }
+        }
+        break;
+    }
+    case DEM_FIELD_PLANET:
+        CHK(need(9));
+        for (int c = 0; c < 3; ++c) { out[c] = dyn.P_pos[c]; out[3 + c] = dyn.P_vel[c]; out[6 + c] = dyn.P_acc[c]; }
+        break;
+    case DEM_FIELD_INFO: {
+        CHK(need(16));
+        double info[16] = {(double)A, (double)N, (double)dyn.steps, (double)dyn.flags,
+                           (double)q.nx, (double)q.ny, (double)q.nz, q.cell,
+                           (double)w->K, (double)w->precision, dyn.O[0], dyn.O[1], dyn.O[2],
+                           (double)dyn.failed, (double)dyn.parity, q.M_total};
+        std::memcpy(out, info, sizeof info);
+        break;
+    }
+    default:
+        return fail(w, DEM_ERR_ARG, "unknown field %d", field);
+    }
+#undef CHK
+    return DEM_OK;
+}
+
+dem_status dem_pile_flags(dem_world *w, int32_t pile_id, int32_t *flags_out)
+{
+    if (!w || !flags_out) return DEM_ERR_ARG;
+    int slot = find_pile(w, pile_id);
+    if (slot < 0) return fail(w, DEM_ERR_ARG, "unknown pile id %d", pile_id);
+    CU(cudaStreamSynchronize(w->stream));
+    PileDyn dyn;
+    CU(cudaMemcpy(&dyn, w->A.pd + slot, sizeof dyn, cudaMemcpyDeviceToHost));
+    *flags_out = dyn.flags;
+    return DEM_OK;
+}
+
+dem_status dem_remove_pile(dem_world *w, int32_t pile_id)
+{
+    if (!w) return DEM_ERR_ARG;
+    int slot = find_pile(w, pile_id);
+    if (slot < 0) return fail(w, DEM_ERR_ARG, "unknown pile id %d", pile_id);
+    CU(cudaStreamSynchronize(w->stream));
+    w->pending = false;
+    std::vector<PileHost> newp = w->piles;
+    newp.erase(newp.begin() + slot);
+    dem_status s = relayout(w, newp, nullptr);
+    if (s != DEM_OK) return s;
+    w->piles = newp;
+    w->graph_valid = false;
+    return DEM_OK;
+}
+
+dem_status dem_set_tuning(dem_world *w, const char *key, double value)
+{
+    if (!w || !key) return DEM_ERR_ARG;
+    std::string k = key;
+    if (k == "grav_block") {
+        int b = (int)value;
+        if (b != 64 && b != 128 && b != 256) return fail(w, DEM_ERR_ARG, "grav_block must be 64, 128 or 256");
+        w->grav_block = b;
+    } else if (k == "grav_ib") {
+        int b = (int)value;
+        if (b != 1 && b != 2) return fail(w, DEM_ERR_ARG, "grav_ib must be 1 or 2");
+        w->grav_ib = b;
+    } else if (k == "grav_jchunk") {
+        if (value < 0) return fail(w, DEM_ERR_ARG, "grav_jchunk must be >= 0");
+        w->grav_jchunk = (int64_t)value;
+    } else if (k == "cell_factor") {
+        if (!(value >= 1.0) || value > 16.0) return fail(w, DEM_ERR_ARG, "cell_factor must be in [1, 16]");
+        if (w->cell_factor != value) {
+            // new grids for every pile (cells are transient: nothing to preserve)
+            double old = w->cell_factor;
+            w->cell_factor = value;
+            std::vector<PileHost> newp = w->piles;
+            for (auto &q : newp) {
+                double base = q.cell / old;
+                double cell = base * value;
+                double ext[3] = {q.nx * q.cell, q.ny * q.cell, q.nz * q.cell};
+                int64_t cap = std::max<int64_t>(4 * q.ns, 27);
+                int dims[3];
+                for (int it = 0; it < 200; ++it) {
+                    int64_t tot = 1;
+                    for (int c = 0; c < 3; ++c) {
+                        dims[c] = (int)std::max<int64_t>(3, (int64_t)std::ceil(ext[c] / cell));
+                        tot *= dims[c];
+                    }
+                    if (tot <= cap) break;
+                    cell *= std::cbrt((double)tot / (double)cap) * 1.01;
+                }
+                q.cell = cell; q.nx = dims[0]; q.ny = dims[1]; q.nz = dims[2];
+                int64_t cells = (int64_t)q.nx * q.ny * q.nz;
+                q.nc = (cells + kScanTile - 1) / kScanTile * kScanTile;
+                q.nt = q.nc / kScanTile;
+            }
+            dem_status s = relayout(w, newp, nullptr);
+            if (s != DEM_OK) { w->cell_factor = old; return s; }
+            w->piles = newp;
+        }
+    } else {
+        return fail(w, DEM_ERR_ARG, "unknown tuning key '%s'", key);
+    }
+    w->graph_valid = false;
+    return DEM_OK;
+}
+
+dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
+{
+    if (!w || trial_steps < 1) return DEM_ERR_ARG;
+    if (w->piles.empty()) return DEM_OK;
+    struct Cand { int blk, ib; int64_t jc; };
+    int64_t nmax = 0;
+    for (auto &q : w->piles) nmax = std::max(nmax, q.ns);
+    std::vector<Cand> cands;
+    for (int blk : {64, 128, 256})
+        for (int ib : {1, 2}) {
+            cands.push_back({blk, ib, 0});
+            if (nmax >= 16384) {
+                cands.push_back({blk, ib, (nmax + 1) / 2});
+                cands.push_back({blk, ib, (nmax + 3) / 4});
+            }
+        }
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    double best = 1e300;
+    Cand bc = {w->grav_block, w->grav_ib, w->grav_jchunk};
+    for (auto &c : cands) {
+        w->grav_block = c.blk; w->grav_ib = c.ib; w->grav_jchunk = c.jc;
+        w->graph_valid = false;
+        dem_status s = prepare(w);
+        if (s != DEM_OK) return s;
+        s = set_enabled(w, nullptr, 0);
+        if (s != DEM_OK) return s;
+        CU(cudaGraphLaunch(w->exec, w->stream));   // warm
+        CU(cudaEventRecord(e0, w->stream));
+        for (int t = 0; t < trial_steps; ++t) CU(cudaGraphLaunch(w->exec, w->stream));
+        CU(cudaEventRecord(e1, w->stream));
+        CU(cudaEventSynchronize(e1));
+        float ms;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        double per = ms / trial_steps;
+        if (per < best) { best = per; bc = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    w->grav_block = bc.blk; w->grav_ib = bc.ib; w->grav_jchunk = bc.jc;
+    w->graph_valid = false;
+    if (best_ms_out) *best_ms_out = best;
+    return DEM_OK;
+}
+
+size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contacts, int32_t precision)
+{
+    if (n_spheres < 0 || n_agg < 0 || max_contacts < 1) return 0;
+    bool d = precision == DEM_FP64;
+    size_t sph = 4 + 4 + 24 + 8 + 8 + 4 + 4 + 4 + 32 + 4 + 4;
+    sph += d ? (32 * 3 + 32 + 32 + 32) : (16 * 2 + 16 * 4 + 16 + 16 + 16);
+    size_t sphk = d ? 2 * 32 : 2 * 16;
+    size_t agg = 4 * 3 + 8 + 72 * 2 + 24 * 2 + 32 + 24 * 3 + 144 + (d ? sizeof(AggRec64) : sizeof(AggRecMixed));
+    int64_t cells = std::max<int64_t>(4 * n_spheres, 27) + kScanTile;
+    size_t bytes = sph * (size_t)n_spheres + sphk * (size_t)n_spheres * (size_t)max_contacts +
+                   agg * (size_t)n_agg + 8 * (size_t)cells + 4 * (size_t)(cells / kScanTile + 1) +
+                   (size_t)(n_agg / kAggChunk + 1) * (8 * kPartialDoubles + 4) +
+                   sizeof(PileStatic) + sizeof(PileDyn) + 16 + 16 * (size_t)(n_spheres / 64 + 1);
+    return bytes;
+}
+
+size_t dem_world_bytes(const dem_world *w) { return w ? w->held : 0; }
+
+const char *dem_last_error(const dem_world *w)
+{
+    if (!w) return "NULL world";
+    return w->err.c_str();
+}
+
+void dem_destroy(dem_world *w)
+{
+    if (!w) return;
+    cudaStreamSynchronize(w->stream);
+    if (w->exec) cudaGraphExecDestroy(w->exec);
+    for (auto &f : w->fields) dev_free(w, *f.ptr);
+    if (w->h_dyn) cudaFreeHost(w->h_dyn);
+    if (w->ev_flags) cudaEventDestroy(w->ev_flags);
+    if (w->own_stream) cudaStreamDestroy(w->stream);
+    delete w;
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+"""Helpers that compare the CUDA library with the FP64 oracle.
+
+Error measure.  F_A and N_A are sums of many sphere terms (contact pairs,
+gravity pairs, planet) that largely cancel.  A computed sum in any precision
+carries an error bounded by (unit round-off) x (sum of the magnitudes of its
+terms), so the error of each aggregate result is reported relative to that
+sum of magnitudes, which the oracle computes alongside the result
+(`scaleF`, `scaleN`).  The tolerances are then statements about the
+arithmetic: 1e-5 for the mixed FP32/FP64 path, 1e-9 for the all-FP64 path.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+TOL = {0: 1e-9, 1: 1e-5}     # precision id -> relative tolerance
+
+
+def agg_errors(world, pid, pile):
+    """Per-aggregate condition-relative errors of F_A and N_A after the last step."""
+    F = world.read(pid, "FORCE")
+    N = world.read(pid, "TORQUE")
+    Fo = pile.FA_c + pile.FA_g + pile.FA_e
+    No = pile.NA_c + pile.NA_g + pile.NA_e
+    sF = np.maximum(pile.scaleF, 1e-300)
+    sN = np.maximum(pile.scaleN, 1e-300)
+    eF = np.linalg.norm(F - Fo, axis=1) / sF
+    eN = np.linalg.norm(N - No, axis=1) / sN
+    return eF, eN
+
+
+def sphere_errors(world, pid, pile):
+    """Per-sphere condition-relative errors of the contact force, contact torque and gravity."""
+    Fc = world.read(pid, "SPHERE_FC")
+    Tc = world.read(pid, "SPHERE_TC")
+    Fg = world.read(pid, "SPHERE_FG")
+    sc = np.maximum(pile.sph_Fmc, 1e-300)
+    st = np.maximum(pile.sph_Tmc, 1e-300)
+    sg = np.maximum(pile.sph_Fmg, 1e-300)
+    ec = np.where(pile.sph_Fmc > 0, np.linalg.norm(Fc - pile.Fc, axis=1) / sc,
+                  np.linalg.norm(Fc, axis=1))
+    et = np.where(pile.sph_Tmc > 0, np.linalg.norm(Tc - pile.Tc, axis=1) / st,
+                  np.linalg.norm(Tc, axis=1))
+    eg = np.where(pile.sph_Fmg > 0, np.linalg.norm(Fg - pile.Fg, axis=1) / sg,
+                  np.linalg.norm(Fg, axis=1))
+    return ec, et, eg
+
+
+def contact_set_check(world, pid, pile, r_ref):
+    """Contact pairs with overlap > 1e-6 R must match exactly; pairs closer to
+    touching may differ.  Returns (n_strong, n_gpu, mismatches)."""
+    gpu_pairs, _ = world.contacts(pid)
+    gset = set(gpu_pairs)
+    opairs, ox = pile.contact_pairs()
+    thr = 1e-6 * r_ref
+    oset = {tuple(p) for p in opairs.tolist()}
+    strong = {tuple(p) for p, x in zip(opairs.tolist(), ox) if x > thr}
+    bad = [p for p in strong if p not in gset]
+    for (i, j) in gset - oset:
+        d = np.linalg.norm(pile.sph_pos[i] - pile.sph_pos[j])
+        x = pile.s[i] + pile.s[j] - d
+        if x > thr or pile.agg_of[i] == pile.agg_of[j]:
+            bad.append((i, j))
+    return len(strong), len(gset), bad
+
+
+def lockstep(world, pid, pile, steps, tol, r_ref=1.0, check_contacts=True, every=1):
+    """Advance both by `steps`, comparing after each (or every `every`) step.
+    Returns the worst errors seen."""
+    worst = dict(F=0.0, N=0.0, Fc=0.0, Tc=0.0, Fg=0.0, contacts=0)
+    for k in range(steps):
+        pile.step()
+        world.step(1)
+        if (k + 1) % every and k + 1 != steps:
+            continue
+        eF, eN = agg_errors(world, pid, pile)
+        ec, et, eg = sphere_errors(world, pid, pile)
+        worst["F"] = max(worst["F"], float(eF.max()))
+        worst["N"] = max(worst["N"], float(eN.max()))
+        worst["Fc"] = max(worst["Fc"], float(ec.max()))
+        worst["Tc"] = max(worst["Tc"], float(et.max()))
+        worst["Fg"] = max(worst["Fg"], float(eg.max()))
+        if check_contacts:
+            ns, ng, bad = contact_set_check(world, pid, pile, r_ref)
+            assert not bad, f"step {k + 1}: contact sets differ: {bad[:5]}"
+            worst["contacts"] = max(worst["contacts"], ns)
+        assert worst["F"] <= tol and worst["N"] <= tol, f"step {k + 1}: {worst}"
+    return worst

@@ -1,0 +1,328 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle.
+
+Every comparison runs both on the same seeded inputs.  Aggregate results use
+the condition-relative error of parity_util (tolerance 1e-5 mixed, 1e-9 FP64);
+contact sets must agree exactly for overlaps above 1e-6 R.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2311_11322_gb300 import workloads as W
+from tests.parity_util import TOL, agg_errors, contact_set_check, lockstep, sphere_errors
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [W.PRECISION_FP64, W.PRECISION_MIXED]
+
+
+@pytest.fixture(scope="module")
+def dem():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2311_11322_gb300 import dem as D
+    return D
+
+
+@pytest.fixture(scope="module")
+def oracle():
+    import oracle as O
+    O.build()
+    return O
+
+
+def new_world(dem, **kw):
+    return dem.World(**kw)
+
+
+# ------------------------------------------------------------------ lockstep runs
+@pytest.mark.parametrize("prec", PRECS)
+def test_random_cluster_lockstep(dem, oracle, prec):
+    """Overlapping aggregates of all four shapes, with spin and velocity:
+    normal, tangential, rolling and twisting terms live for 30 steps."""
+    ic, p = W.random_cluster(3, n_agg=70, box=5.0, precision=prec)
+    p = p.replace(mu_t=0.05, G=W.G_SI * 1e4)
+    pile = oracle.Pile(ic, p, want_scales=True)
+    with new_world(dem) as w:
+        pid = w.add_pile(ic, p)
+        worst = lockstep(w, pid, pile, 30, TOL[prec], r_ref=1.0)
+        assert worst["contacts"] > 20
+        assert worst["Fc"] <= 10 * TOL[prec] and worst["Fg"] <= 10 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_config1_lockstep_100_steps(dem, oracle, prec):
+    """The 250-tetrahedron cloud (1,000 spheres), 100 steps, forces every step and
+    final COM positions / orientations."""
+    ic, p = W.config1(0, precision=prec)
+    pile = oracle.Pile(ic, p, want_scales=True)
+    with new_world(dem) as w:
+        pid = w.add_pile(ic, p)
+        lockstep(w, pid, pile, 100, TOL[prec], r_ref=1.0, every=10)
+        r = w.read(pid, "COM")
+        q = w.read(pid, "QUAT")
+        assert np.max(np.abs(r - pile.r)) < (1e-9 if prec == 0 else 1e-6)
+        assert np.max(np.abs(q - pile.q)) < (1e-9 if prec == 0 else 1e-6)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_dense_lattice_lockstep_100_steps(dem, oracle, prec):
+    """Contact-stress case: tetrahedra from an FCC lattice overlapping by 0.5% R,
+    with random velocities and spins (2,000 spheres, 100 steps)."""
+    ic, p = W.dense_lattice(n_spheres=2000, seed=1, precision=prec)
+    pile = oracle.Pile(ic, p, want_scales=True)
+    with new_world(dem) as w:
+        pid = w.add_pile(ic, p)
+        worst = lockstep(w, pid, pile, 100, TOL[prec], r_ref=1.0, every=5)
+        assert worst["contacts"] > 3000
+        r = w.read(pid, "COM")
+        assert np.max(np.abs(r - pile.r)) < (1e-10 if prec == 0 else 1e-6)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_planet_flyby_and_yorp(dem, oracle, prec):
+    """External terms: a close planet pass (tidal force on every sphere, planet
+    reaction) plus a YORP spin increment, 40 steps."""
+    rng = np.random.default_rng(5)
+    ic = W.lattice_pile(rng, 150, shapes=("tetra", "rod3"))
+    p = W.settled_params(ic, 1.0, precision=prec, eps=0.1)
+    com = np.average(ic.pos, axis=0, weights=W.sphere_mass(ic.radius, ic.density))
+    p = p.replace(ext_mass=W.EARTH_MASS, ext_pos=tuple(com + np.array([1.2e7, 3.0e6, 0.0])),
+                  ext_vel=(-5.0e3, 0.0, 0.0), spin_inc=(0.0, 1e-7, 2e-7), dt=p.dt)
+    pile = oracle.Pile(ic, p, want_scales=True)
+    with new_world(dem) as w:
+        pid = w.add_pile(ic, p)
+        lockstep(w, pid, pile, 40, TOL[prec], r_ref=1.0, every=4)
+        pl = w.read(pid, "PLANET")
+        assert np.allclose(pl[:3], pile.planet[:3], rtol=0, atol=1e-6)
+        assert np.allclose(pl[3:6], pile.planet[3:6], rtol=1e-12, atol=1e-12)
+        Fe = w.read(pid, "FORCE_EXT")
+        assert np.max(np.abs(Fe)) > 0
+
+
+# ------------------------------------------------------------------ full size, sampled
+def sampled_check(dem, oracle, ic, p, n_agg_sample, tol, seed=0):
+    rng = np.random.default_rng(seed)
+    A = ic.n_agg
+    aggs = np.sort(rng.choice(A, size=min(n_agg_sample, A), replace=False))
+    first = np.concatenate([[0], np.cumsum(ic.counts)[:-1]])
+    rows = np.concatenate([np.arange(first[a], first[a] + ic.counts[a]) for a in aggs])
+    pile = oracle.Pile(ic, p)
+    ref = pile.step_sampled(rows)
+    with new_world(dem) as w:
+        pid = w.add_pile(ic, p)
+        w.step(1)
+        Fc = w.read(pid, "SPHERE_FC")[rows]
+        Tc = w.read(pid, "SPHERE_TC")[rows]
+        Fg = w.read(pid, "SPHERE_FG")[rows]
+        F_A = w.read(pid, "FORCE")[aggs]
+    scale = ref["Fmag"]
+    e_sph = np.linalg.norm(Fc + Fg - ref["Fc"] - ref["Fg"], axis=1) / np.maximum(scale, 1e-300)
+    # aggregate totals of the sampled aggregates
+    k = 0
+    e_agg = []
+    for a in aggs:
+        c = ic.counts[a]
+        Fo = (ref["Fc"][k:k + c] + ref["Fg"][k:k + c] + ref["Fe"][k:k + c]).sum(0)
+        sc = scale[k:k + c].sum()
+        e_agg.append(np.linalg.norm(F_A[len(e_agg)] - Fo) / max(sc, 1e-300))
+        k += c
+    et = np.linalg.norm(Tc - ref["Tc"], axis=1) / np.maximum(ref["Tmag"], 1e-300)
+    et = np.where(ref["Tmag"] > 0, et, np.linalg.norm(Tc, axis=1))
+    return float(e_sph.max()), float(max(e_agg)), float(et.max()), int((ref["Tmag"] > 0).sum())
+
+
+def test_config2_full_size_sampled(dem, oracle):
+    """100,000-sphere collapse cloud (mixed path, as benchmarked): first-step
+    gravity and contact forces on 200 sampled aggregates against the oracle."""
+    ic, p = W.config2(0)
+    es, ea, et, _ = sampled_check(dem, oracle, ic, p, 200, TOL[1])
+    assert es <= TOL[1] and ea <= TOL[1] and et <= TOL[1]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_dense_100k_full_size_sampled(dem, oracle, prec):
+    """100,000-sphere dense lattice: first-step contacts (9 per sphere) and
+    gravity on 150 sampled aggregates."""
+    ic, p = W.dense_lattice(n_spheres=100_000, seed=2, precision=prec)
+    es, ea, et, ncont = sampled_check(dem, oracle, ic, p, 150, TOL[prec])
+    assert ncont > 300
+    assert es <= TOL[prec] and ea <= TOL[prec] and et <= TOL[prec]
+
+
+# ------------------------------------------------------------------ batching
+def _three_piles(prec):
+    out = []
+    for k, n in enumerate((37, 130, 260)):
+        rng = np.random.default_rng(10 + k)
+        ic = W.lattice_pile(rng, n, shapes=W.SHAPES, spacing_factor=0.95)
+        p = W.settled_params(ic, 1.0, precision=prec, eps=0.1)
+        out.append((ic, p))
+    return out
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_alone_equals_mix_bitwise(dem, prec):
+    """Each pile stepped alone and stepped inside a batch gives bit-identical
+    state: per-pile work never depends on the other piles."""
+    piles = _three_piles(prec)
+    alone = []
+    for ic, p in piles:
+        with new_world(dem) as w:
+            pid = w.add_pile(ic, p)
+            w.step(25)
+            alone.append((w.read(pid, "COM"), w.read(pid, "QUAT"), w.read(pid, "FORCE")))
+    with new_world(dem) as w:
+        ids = [w.add_pile(ic, p) for ic, p in piles]
+        w.step(25)
+        for pid, ref in zip(ids, alone):
+            got = (w.read(pid, "COM"), w.read(pid, "QUAT"), w.read(pid, "FORCE"))
+            for g, r in zip(got, ref):
+                assert np.array_equal(g, r)
+
+
+def test_run_twice_bitwise(dem):
+    ic, p = W.dense_lattice(n_spheres=4000, seed=3, precision=W.PRECISION_MIXED)
+    res = []
+    for _ in range(2):
+        with new_world(dem) as w:
+            pid = w.add_pile(ic, p)
+            w.step(20)
+            res.append((w.read(pid, "COM"), w.read(pid, "TORQUE"), w.read(pid, "CONTACTS")))
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+
+
+def test_remove_pile_keeps_others(dem):
+    piles = _three_piles(W.PRECISION_MIXED)
+    with new_world(dem) as w:
+        ids = [w.add_pile(ic, p) for ic, p in piles]
+        w.step(5)
+        w.remove(ids[1])
+        w.step(10)
+        got0, got2 = w.read(ids[0], "COM"), w.read(ids[2], "COM")
+    with new_world(dem) as w:
+        a = w.add_pile(*piles[0])
+        c = w.add_pile(*piles[2])
+        w.step(15)
+        assert np.array_equal(w.read(a, "COM"), got0)
+        assert np.array_equal(w.read(c, "COM"), got2)
+
+
+def test_step_subset_freezes_others(dem):
+    piles = _three_piles(W.PRECISION_MIXED)
+    with new_world(dem) as w:
+        ids = [w.add_pile(ic, p) for ic, p in piles]
+        w.step(3)
+        before = w.read(ids[1], "COM")
+        w.step(4, piles=[ids[0], ids[2]])
+        w.sync()
+        assert np.array_equal(w.read(ids[1], "COM"), before)
+        assert w.info(ids[0])["steps"] == 7 and w.info(ids[1])["steps"] == 3
+
+
+def test_gravity_split_and_shapes_agree(dem):
+    """Splitting the j-range and changing the block shape only reorders FP64 sums."""
+    ic, p = W.config2(1, n_spheres=20_000, ball=800.0)
+    outs = []
+    for blk, ib, jc in ((128, 2, 0), (64, 1, 5000), (256, 2, 7000)):
+        with new_world(dem) as w:
+            w.set_tuning("grav_block", blk)
+            w.set_tuning("grav_ib", ib)
+            w.set_tuning("grav_jchunk", jc)
+            pid = w.add_pile(ic, p)
+            w.step(1)
+            outs.append(w.read(pid, "SPHERE_FG"))
+    sc = np.linalg.norm(outs[0], axis=1).max()
+    for o in outs[1:]:
+        assert np.max(np.abs(o - outs[0])) < 1e-5 * sc
+
+
+# ------------------------------------------------------------------ errors and edges
+def test_slot_overflow_reported_and_frozen(dem):
+    ic, p = W.dense_lattice(n_spheres=800, seed=4, precision=W.PRECISION_MIXED)
+    p = p.replace(max_contacts=2)
+    with new_world(dem) as w:
+        pid = w.add_pile(ic, p)
+        w.step(1)
+        with pytest.raises(dem.DemError) as ei:
+            w.sync()
+        assert ei.value.status == dem.DEM_ERR_SLOTS
+        assert w.flags(pid) & dem.DEM_FLAG_SLOTS
+        steps = w.info(pid)["steps"]
+        w.step(3, check=False)
+        w.sync(check=False)
+        assert w.info(pid)["steps"] == steps
+
+
+def test_invalid_inputs_rejected(dem):
+    ic, p = W.config1(0, n_agg=10, ball=12.0)
+    with new_world(dem) as w:
+        bad = W.PileIC(ic.counts, ic.pos.copy(), ic.radius, ic.density)
+        bad.pos[3, 1] = np.nan
+        with pytest.raises(dem.DemError) as ei:
+            w.add_pile(bad, p)
+        assert ei.value.status == dem.DEM_ERR_ARG
+        with pytest.raises(dem.DemError):
+            w.add_pile(ic, p.replace(dt=0.0))
+        with pytest.raises(dem.DemError):
+            w.add_pile(ic, p.replace(max_contacts=0))
+        pid = w.add_pile(ic, p)
+        with pytest.raises(dem.DemError):
+            w.add_pile(ic, p.replace(precision=1 - p.precision))
+        with pytest.raises(dem.DemError):
+            w.read(pid + 100, "COM")
+        w.step(0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ragged_and_tiny_piles(dem, oracle, prec):
+    """Piles of 1, 2, 3 and 129 spheres (single spheres, one aggregate, ragged
+    block tails) in one batch, each against its own oracle."""
+    cases = []
+    one = W.assemble(["single"], [1.0], np.zeros((1, 3)), np.eye(3)[None], 2500.0)
+    one.omega = np.array([[0.01, 0.0, 0.02]])
+    cases.append(one)
+    cases.append(W.tiny_pair(gap=-0.01, v=0.01))
+    tri = W.assemble(["rod3"], [1.0], np.zeros((1, 3)), W.random_rotations(np.random.default_rng(0), 1), 2500.0)
+    tri.omega = np.array([[0.003, 0.02, -0.01]])
+    cases.append(tri)
+    cases.append(W.random_cluster(9, n_agg=43, box=4.0)[0])
+    with new_world(dem) as w:
+        ids, piles = [], []
+        for ic in cases:
+            p = W.calibrate(ic, v_max=0.05, r_med=1.0, eps=0.1, precision=prec, overlap_frac=0.05)
+            p = p.replace(G=W.G_SI * 1e5)
+            ids.append(w.add_pile(ic, p))
+            piles.append(oracle.Pile(ic, p, want_scales=True))
+        for _ in range(20):
+            w.step(1)
+            for pid, pile in zip(ids, piles):
+                pile.step()
+        for pid, pile in zip(ids, piles):
+            eF, eN = agg_errors(w, pid, pile)
+            assert eF.max() <= TOL[prec] and eN.max() <= TOL[prec]
+            assert np.max(np.abs(w.read(pid, "COM") - pile.r)) < 1e-6
+
+
+def test_body_offsets_bit_exact(dem):
+    ic, p = W.dense_lattice(n_spheres=2000, seed=5, precision=W.PRECISION_MIXED)
+    with new_world(dem) as w:
+        pid = w.add_pile(ic, p)
+        b0 = w.read(pid, "BODY_OFFSETS")
+        w.step(200)
+        assert np.array_equal(w.read(pid, "BODY_OFFSETS"), b0)
+        q = w.read(pid, "QUAT")
+        assert np.max(np.abs(np.linalg.norm(q, axis=1) - 1.0)) < 1e-14
+
+
+def test_profiled_step_times_kernel(dem):
+    ic, p = W.config2(0, n_spheres=20_000, ball=800.0)
+    with new_world(dem) as w:
+        w.add_pile(ic, p)
+        ms = w.step_profiled(3, "GRAVITY")
+        assert ms.shape == (3,) and np.all(ms > 0)
