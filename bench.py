@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Benchmark: sphere-steps/s of the 100,000-sphere self-gravitating collapse.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (synthetic, seeded): 100,000 spheres bonded into 30,787 rigid
+aggregates drawn uniformly from dumbbell / 3-rod / tetrahedron / square,
+radii lognormal (median 5 m, sigma 0.2, per aggregate), COMs uniform in a
+2 km ball at rest, spring-dashpot contacts (max overlap ~1% R, e = 0.5,
+mu_s = 0.5, mu_r = 0.1), Plummer-softened direct-sum self-gravity
+(eps = 0.5 m), h = t_contact / 50.  One step = the whole per-step path
+(kick/drift/rotation, expansion, cell sort, contact pass, gravity,
+aggregate reduction, closing kick) as one CUDA-graph launch.
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
+on the library's stream, with a 512 MiB write between steps to flush L2 (the
+working set, ~40 MB, would otherwise stay in the 129 MB L2).  The gravity
+kernel is timed by event nodes inside the same graph launches.  With N GPUs
+(torchrun), each rank runs an independent replica (seed = rank); the job
+value is all spheres x steps / the slowest rank's time.
+
+One JSON line on rank 0.  Extra keys: fp64_path (the all-FP64 GPU path on
+the same workload), roofline_contact (the contact pass on a 1M-sphere dense
+lattice, HBM-bound), e2e (through the public API with host buffers).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sphere-steps/s at 100k spheres, mixed vs FP64 form; batched p50/p99 sim latency"
+UNIT = "sphere-steps/s"
+N_SPHERES = 100_000
+FLOP_PER_INTERACTION = 20.0
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-contact", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(ic):
+    return {"workload": "collapse-100k: 100,000 spheres in %d rigid aggregates (dumbbell, rod3, "
+                        "tetra, square; radii lognormal median 5 m sigma 0.2) uniform in a 2 km "
+                        "ball at rest, contacts + softened direct-sum self-gravity" % ic.n_agg,
+            "n_spheres": int(ic.n_sph), "n_aggregates": int(ic.n_agg), "precision": "mixed",
+            "l2": "flushed between timed steps (512 MiB write on the library stream)",
+            "seed": 0}
+
+
+def interactions(ic):
+    """Ordered gravity pairs evaluated per step: spheres of other aggregates."""
+    n = ic.n_sph
+    return float(n) * n - float(np.sum(ic.counts.astype(np.float64) ** 2))
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(x, ws, device=None):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- pieces
+def traffic_for(kernel_file, kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source has not changed since the counters were taken; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_2311_11322_gb300", "csrc", kernel_file)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("source_sha256_16") != h:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def run_fp64(dem, W, steps):
+    ic, p = W.config2(0, precision=W.PRECISION_FP64)
+    with dem.World() as w:
+        w.add_pile(ic, p)
+        w.step_timed()
+        ms = [w.step_timed()[0] for _ in range(steps)]
+    t = sum(ms) / 1e3
+    return {"value": ic.n_sph * steps / t, "unit": UNIT, "ms_per_step": 1e3 * t / steps,
+            "steps": steps, "dtype": "f64"}
+
+
+def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576):
+    """Contact pass on a dense FCC-tetrahedra lattice (0.5% R overlaps, 9 contacts
+    per sphere), gravity off, working set far above L2."""
+    import torch
+    ic, p = W.dense_lattice(n_spheres=n, seed=0, precision=W.PRECISION_MIXED)
+    p = p.replace(G=0.0)
+    with dem.World() as w:
+        pid = w.add_pile(ic, p)
+        w.set_timed_kernel("CONTACT")
+        flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+        st = torch.cuda.ExternalStream(w.stream)
+        for _ in range(3):
+            w.step_timed()
+        ks = []
+        for _ in range(steps):
+            with torch.cuda.stream(st):
+                flush.zero_()
+            ks.append(w.step_timed()[1])
+        info = w.info(pid)
+        cnt = w.read(pid, "CONTACTS")[:, 0]
+    z = float(cnt.sum())
+    cells = info["nx"] * info["ny"] * info["nz"]
+    N = ic.n_sph
+    # compulsory bytes per launch: own sorted state 4 x float4, sorted index,
+    # history count in/out, F and tau out (2 x float4), every contact's history
+    # slot read and written (float4 each), and the cell table (start + count)
+    algo = N * (64 + 4 + 4 + 4 + 32) + z * 32 + cells * 8
+    ms = statistics.median(ks)
+    achieved = algo / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+            "frac": achieved / peak_gbs, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": traffic_for("kernels_contact.cu", "k_contact_mixed"),
+            "kernel_ms": ms, "n_spheres": N, "contacts_per_sphere": z / N,
+            "algorithmic_bytes_per_launch": algo, "workload": "dense FCC tetrahedra lattice, "
+            "1,048,576 spheres, overlaps 0.5% R, gravity off"}
+
+
+def run_e2e(dem, W, ic, p, steps):
+    """Through the public API with pinned host buffers: add the pile (host->device
+    copy of the initial conditions), then per step dem_step + read the COMs back."""
+    import torch
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        return t.numpy()
+
+    hic = W.PileIC(pinned(ic.counts), pinned(ic.pos), pinned(ic.radius), pinned(ic.density),
+                   pinned(ic.vel), pinned(ic.omega))
+    h2d = sum(a.nbytes for a in (hic.counts, hic.pos, hic.radius, hic.density, hic.vel, hic.omega))
+    with dem.World() as w:
+        pid = w.add_pile(hic, p)      # warm the allocator and the code paths
+        w.step(1)
+        w.read(pid, "COM")
+        w.remove(pid)
+        w.sync()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pid = w.add_pile(hic, p)
+        d2h = 0
+        for _ in range(steps):
+            w.step(1)
+            d2h = w.read(pid, "COM").nbytes
+        w.remove(pid)
+        w.sync()
+        t = time.perf_counter() - t0
+    return {"value": ic.n_sph * steps / t, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h, "steps": steps,
+            "definition": "add_pile from pinned host arrays + steps x (dem_step(1) + read COM) + "
+                          "remove, wall clock"}
+
+
+def cpu_baseline(W, ic, p, rows_frac=1.0):
+    import oracle
+    oracle.build()
+    pile = oracle.Pile(ic, p)
+    n = ic.n_sph
+    rows = np.arange(0, n, max(1, int(round(1.0 / rows_frac))), dtype=np.int64)
+    t0 = time.perf_counter()
+    pile.step_sampled(rows)
+    t = time.perf_counter() - t0
+    return {"value": len(rows) / t, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "one FP64 oracle step of the same 100k-sphere workload, forces of %d of "
+                      "its %d spheres (every %d-th; brute-force contacts + direct gravity over "
+                      "all spheres), %.1f s" % (len(rows), n, n // len(rows), t)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------- arms
+def run_ours(args):
+    import torch
+    from paper_2311_11322_gb300 import dem
+    from paper_2311_11322_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(ws)
+    dem.load()
+
+    ic, p = W.config2(rank)
+    pk = peaks()
+    hbm_peak = float(pk.get("hbm_gbs", 6800.0))
+    w = dem.World()
+    pid = w.add_pile(ic, p)
+    w.set_timed_kernel("GRAVITY")
+    n_kern = w.graph_kernel_count()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.ExternalStream(w.stream)
+    for _ in range(max(args.warmup, 0)):
+        w.step_timed()
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    wall0 = time.perf_counter()
+    step_ms, grav_ms = [], []
+    for _ in range(args.steps):
+        with torch.cuda.stream(st):
+            flush.zero_()
+        s, g = w.step_timed()
+        step_ms.append(s)
+        grav_ms.append(g)
+    torch.cuda.synchronize()
+    barrier(ws)
+    wall = time.perf_counter() - wall0
+    ck = clocks.stop()
+    w.sync()
+    t_rank = sum(step_ms) / 1e3
+    t_max = max_over_ranks(t_rank, ws, device="cuda")
+    value = ws * ic.n_sph * args.steps / t_max
+    g_ms = statistics.mean(grav_ms)
+    flops = FLOP_PER_INTERACTION * interactions(ic)
+    achieved = flops / (g_ms / 1e3) / 1e12
+    w.close()
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32/f64", "data": "synthetic (seeded generator, no dataset)",
+           "config": workload_config(ic), "wall_s_timed_region": wall,
+           "gpu_launches": n_kern * args.steps,
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                        "traffic": traffic_for("kernels_gravity.cu", "k_gravity32"),
+                        "kernel": "k_gravity32 (softened direct-sum gravity)",
+                        "kernel_ms": g_ms, "share_of_step": g_ms / statistics.mean(step_ms),
+                        "flops_per_launch": flops,
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"},
+           "clocks": ck}
+    if rank == 0 and not args.no_fp64:
+        out["fp64_path"] = run_fp64(dem, W, steps=3)
+        out["fp64_path"]["mixed_over_fp64"] = value / ws / out["fp64_path"]["value"]
+    if rank == 0 and not args.no_contact:
+        out["roofline_contact"] = run_contact_roofline(dem, W, hbm_peak)
+    if not args.no_e2e:
+        e = run_e2e(dem, W, ic, p, steps=args.steps)
+        e_t = max_over_ranks(ic.n_sph * args.steps / e["value"], ws, device="cuda")
+        e["value"] = ws * ic.n_sph * args.steps / e_t
+        out["e2e"] = e
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(W, ic, p, rows_frac=1.0)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle (plain FP64 CPU program) timed on the host cores, on bounded
+    samples of the same workload: each step computes the forces of 1/8 of the
+    spheres against all spheres."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2311_11322_gb300 import workloads as W
+    import oracle
+    oracle.build()
+    ic, p = W.config2(0)
+    pile = oracle.Pile(ic, p)
+    rows = np.arange(0, ic.n_sph, 8, dtype=np.int64)
+    for _ in range(max(args.warmup, 0)):
+        pile.step_sampled(rows)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        pile.step_sampled(rows)
+    t = time.perf_counter() - t0
+    value = len(rows) * args.steps / t
+    cb = {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+          "sample": "per step: FP64 oracle forces of %d of the %d spheres (every 8th) against "
+                    "all spheres, brute-force contacts + direct gravity" % (len(rows), ic.n_sph)}
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded generator, no dataset)", "config": workload_config(ic),
+           "cpu_baseline": cb,
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

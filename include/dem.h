@@ -177,6 +177,23 @@ dem_status dem_sync(dem_world *w);
 dem_status dem_step_profiled(dem_world *w, int64_t n_steps, int32_t which, float *ms_out);
 
 /*
+ * Put CUDA event records around kernel `which` (enum dem_kernel; -1 = none)
+ * inside the captured step graph.  Recaptures the graph on the next step.
+ */
+dem_status dem_set_timed_kernel(dem_world *w, int32_t which);
+
+/*
+ * One step of every live pile as one graph launch, bracketed by CUDA events
+ * on the world's stream; synchronises.  step_ms receives the launch's device
+ * time; kernel_ms (may be NULL) the time of the kernel chosen with
+ * dem_set_timed_kernel inside that launch (0 if none was chosen).
+ */
+dem_status dem_step_timed(dem_world *w, float *step_ms, float *kernel_ms);
+
+/* Number of kernel nodes in the captured step graph (captures it if needed). */
+dem_status dem_graph_kernel_count(dem_world *w, int32_t *n_out);
+
+/*
  * Copy one field of a pile to host_out (n_out doubles, see enum dem_field for
  * the layout); synchronises the stream first.
  * Errors: DEM_ERR_ARG (unknown pile/field, n_out too small), DEM_ERR_CUDA.

@@ -67,6 +67,11 @@ struct dem_world {
     bool pending = false;
     int64_t pending_n = 0;
     bool own_stream = false;
+    // timing inside the graph
+    int timed_kernel = -1;
+    cudaEvent_t kev[2] = {nullptr, nullptr};
+    cudaEvent_t sev[2] = {nullptr, nullptr};
+    int32_t graph_kernels = 0;
 };
 
 namespace {
@@ -211,6 +216,11 @@ GravPlan plan_gravity(const dem_world *w)
         int64_t nch = 1;
         if (w->grav_jchunk > 0 && ns > w->grav_jchunk) nch = (ns + w->grav_jchunk - 1) / w->grav_jchunk;
         int64_t jc = (ns + nch - 1) / nch;
+        if (q.P.G == 0.0) {   // no self-gravity: no work items; fg stays zero from set-up
+            g.nch.push_back(1);
+            g.base.push_back(-1);
+            continue;
+        }
         g.nch.push_back((int32_t)nch);
         if (nch > 1) {
             g.base.push_back(g.gp);
@@ -390,10 +400,28 @@ dem_status prepare(dem_world *w)
     }
     CU(cudaStreamSynchronize(w->stream));
     cudaGraph_t g = nullptr;
+    if (w->timed_kernel >= 0 && !w->kev[0]) {
+        CU(cudaEventCreate(&w->kev[0]));
+        CU(cudaEventCreate(&w->kev[1]));
+    }
     CU(cudaStreamBeginCapture(w->stream, cudaStreamCaptureModeThreadLocal));
-    for (int ph = 0; ph < DEM_K_COUNT; ++ph) enqueue_phase(w, ph);
+    for (int ph = 0; ph < DEM_K_COUNT; ++ph) {
+        if (ph == w->timed_kernel) cudaEventRecordWithFlags(w->kev[0], w->stream, cudaEventRecordExternal);
+        enqueue_phase(w, ph);
+        if (ph == w->timed_kernel) cudaEventRecordWithFlags(w->kev[1], w->stream, cudaEventRecordExternal);
+    }
     cudaError_t e = cudaStreamEndCapture(w->stream, &g);
     if (e != cudaSuccess) return fail(w, DEM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    int32_t nk = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+    }
+    w->graph_kernels = nk;
     e = cudaGraphInstantiate(&w->exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(w, DEM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
@@ -801,6 +829,53 @@ dem_status dem_step_profiled(dem_world *w, int64_t n_steps, int32_t which, float
     return prev;
 }
 
+dem_status dem_set_timed_kernel(dem_world *w, int32_t which)
+{
+    if (!w) return DEM_ERR_ARG;
+    if (which < -1 || which >= DEM_K_COUNT) return fail(w, DEM_ERR_ARG, "unknown kernel %d", which);
+    if (w->timed_kernel != which) {
+        w->timed_kernel = which;
+        w->graph_valid = false;
+    }
+    return DEM_OK;
+}
+
+dem_status dem_step_timed(dem_world *w, float *step_ms, float *kernel_ms)
+{
+    if (!w || !step_ms) return DEM_ERR_ARG;
+    dem_status prev = collect_flags(w);
+    if (w->piles.empty()) return fail(w, DEM_ERR_STATE, "no piles");
+    dem_status s = prepare(w);
+    if (s != DEM_OK) return s;
+    s = set_enabled(w, nullptr, 0);
+    if (s != DEM_OK) return s;
+    if (!w->sev[0]) {
+        CU(cudaEventCreate(&w->sev[0]));
+        CU(cudaEventCreate(&w->sev[1]));
+    }
+    CU(cudaEventRecord(w->sev[0], w->stream));
+    CU(cudaGraphLaunch(w->exec, w->stream));
+    CU(cudaEventRecord(w->sev[1], w->stream));
+    CU(cudaEventSynchronize(w->sev[1]));
+    CU(cudaEventElapsedTime(step_ms, w->sev[0], w->sev[1]));
+    if (kernel_ms) {
+        *kernel_ms = 0.f;
+        if (w->timed_kernel >= 0) CU(cudaEventElapsedTime(kernel_ms, w->kev[0], w->kev[1]));
+    }
+    s = issue_flags_readback(w);
+    if (s != DEM_OK) return s;
+    return prev;
+}
+
+dem_status dem_graph_kernel_count(dem_world *w, int32_t *n_out)
+{
+    if (!w || !n_out) return DEM_ERR_ARG;
+    dem_status s = prepare(w);
+    if (s != DEM_OK) return s;
+    *n_out = w->graph_kernels;
+    return DEM_OK;
+}
+
 dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *out, int64_t n_out)
 {
     if (!w) return DEM_ERR_ARG;
@@ -1119,6 +1194,10 @@ void dem_destroy(dem_world *w)
     for (auto &f : w->fields) dev_free(w, *f.ptr);
     if (w->h_dyn) cudaFreeHost(w->h_dyn);
     if (w->ev_flags) cudaEventDestroy(w->ev_flags);
+    for (int k = 0; k < 2; ++k) {
+        if (w->kev[k]) cudaEventDestroy(w->kev[k]);
+        if (w->sev[k]) cudaEventDestroy(w->sev[k]);
+    }
     if (w->own_stream) cudaStreamDestroy(w->stream);
     delete w;
 }

@@ -82,6 +82,9 @@ def load():
         "dem_world_bytes": (sz, [vp]),
         "dem_last_error": (C.c_char_p, [vp]),
         "dem_destroy": (None, [vp]),
+        "dem_set_timed_kernel": (i32, [vp, i32]),
+        "dem_step_timed": (i32, [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+        "dem_graph_kernel_count": (i32, [vp, C.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -207,6 +210,20 @@ class World:
         s = self._L.dem_sync(self.w)
         return self._check(s) if check else s
 
+    def set_timed_kernel(self, kernel):
+        self._check(self._L.dem_set_timed_kernel(self.w, -1 if kernel is None else KERNELS[kernel]))
+
+    def step_timed(self):
+        """One graph-launched step; returns (step_ms, timed_kernel_ms)."""
+        a, b = C.c_float(), C.c_float()
+        self._check(self._L.dem_step_timed(self.w, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def graph_kernel_count(self) -> int:
+        n = C.c_int32()
+        self._check(self._L.dem_graph_kernel_count(self.w, C.byref(n)))
+        return n.value
+
     def step_profiled(self, n, kernel="GRAVITY"):
         ms = np.zeros(int(n), np.float32)
         self._check(self._L.dem_step_profiled(self.w, int(n), KERNELS[kernel], _ptr(ms)))
@@ -215,6 +232,9 @@ class World:
     # ---- readout
     def read(self, pile, field):
         fid, rows, cols = FIELDS[field]
+        if pile not in self.piles:   # let the library report the unknown id
+            buf = np.zeros(16)
+            self._check(self._L.dem_read_state(self.w, int(pile), fid, _ptr(buf), buf.size))
         A, N, K = self.piles[pile]
         if field == "CONTACTS":
             out = np.zeros((N, 1 + 4 * K))

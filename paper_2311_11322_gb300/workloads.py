@@ -497,5 +497,6 @@ def random_cluster(seed, n_agg=40, shapes=SHAPES, s=1.0, box=6.0, speed=0.05,
     ic = assemble(sh, sizes, coms, random_rotations(rng, n_agg), 2500.0)
     ic.vel = rng.standard_normal((n_agg, 3)) * speed
     ic.omega = rng.standard_normal((n_agg, 3)) * speed / s
-    p = calibrate(ic, v_max=speed * 5, r_med=s, eps=0.1 * s, precision=precision, overlap_frac=0.05)
+    p = calibrate(ic, v_max=speed * 5, r_med=s, eps=0.1 * s, precision=precision, overlap_frac=0.05,
+                  max_contacts=32)
     return ic, p

@@ -295,7 +295,8 @@ def test_ragged_and_tiny_piles(dem, oracle, prec):
     with new_world(dem) as w:
         ids, piles = [], []
         for ic in cases:
-            p = W.calibrate(ic, v_max=0.05, r_med=1.0, eps=0.1, precision=prec, overlap_frac=0.05)
+            p = W.calibrate(ic, v_max=0.05, r_med=1.0, eps=0.1, precision=prec, overlap_frac=0.05,
+                            max_contacts=32)
             p = p.replace(G=W.G_SI * 1e5)
             ids.append(w.add_pile(ic, p))
             piles.append(oracle.Pile(ic, p, want_scales=True))
