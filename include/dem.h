@@ -223,6 +223,39 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value);
  */
 dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out);
 
+/*
+ * Softened direct-sum gravity of one set of spheres that allocates nothing.
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * allocate device memory -- code running inside another program's memory
+ * pool or arena, real-time loops that forbid allocation after start-up, or
+ * plugins whose host owns every allocation -- and so cannot create a world.
+ * It computes, for i < n,
+ *   F_i = G m_i sum_{j : agg_id[j] != agg_id[i]} m_j (r_j - r_i) / (|r_j - r_i|^2 + eps^2)^{3/2}
+ * with FP32 pair terms and FP64 sums, exactly like the world's gravity pass.
+ *   pos_mass  device, float4 [n] (16-byte aligned): x, y, z in m about any
+ *             common origin, mass in kg (used in the pair terms);
+ *   mass      device, double [n]: masses in kg (the final G m_i factor);
+ *   agg_id    device, int32 [n]: aggregate of each sphere (pairs with equal
+ *             ids are skipped, and so is i = j);
+ *   force_out device, double [n][4] (32-byte aligned): Fx, Fy, Fz, 0 in N.
+ * The caller owns all four buffers.  Work is queued on cuda_stream (NULL =
+ * legacy stream) and the call returns without waiting.  Scratch for the
+ * partial sums is a fixed 16 MiB device array inside the library, present on
+ * every GPU that loads it until the process exits; hence n <= 131072, and a
+ * larger n is refused with DEM_ERR_ARG.  The first call on each device looks
+ * up that array's device address (with the device current); make that first
+ * call before any stream capture.  All calls share the array: two calls whose
+ * kernels overlap on the GPU (different streams, or different host threads)
+ * race on it and must be serialised by the caller.  No value from an earlier
+ * call is read, so nothing needs clearing.  msg (may be NULL) receives a
+ * one-line error text of at most msg_len bytes.
+ * Errors: DEM_ERR_ARG (NULL pointer, n out of range, bad G/eps, misaligned
+ * buffer), DEM_ERR_CUDA (no device, symbol lookup or launch failure).
+ */
+dem_status dem_gravity_noalloc(const void *pos_mass, const double *mass, const int32_t *agg_id,
+                               int32_t n, double G, double eps_soft, double *force_out,
+                               void *cuda_stream, char *msg, size_t msg_len);
+
 /* Device bytes one pile of this size needs (state, sorted copies, cells, history). */
 size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contacts,
                            int32_t precision);

@@ -85,6 +85,7 @@ def load():
         "dem_set_timed_kernel": (i32, [vp, i32]),
         "dem_step_timed": (i32, [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
         "dem_graph_kernel_count": (i32, [vp, C.POINTER(i32)]),
+        "dem_gravity_noalloc": (i32, [vp, vp, vp, i32, dbl, dbl, vp, vp, C.c_char_p, sz]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
