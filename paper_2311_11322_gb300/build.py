@@ -30,9 +30,16 @@ def nvcc() -> str:
     return cand
 
 
+# Per-unit flags.  Gravity flushes FP32 denormals to zero: its pair terms and
+# partial sums are far from the denormal range, and rsqrtf then maps to the
+# hardware approximation with no denormal fix-up around it.
+PER_FILE = {"kernels_gravity.cu": ["-ftz=true"]}
+
+
 def _compile(src: str, extra: list[str]) -> str:
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [nvcc(), *ARCH, *COMMON, *PER_FILE.get(src, []), *extra, "-c", os.path.join(CSRC, src),
+           "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

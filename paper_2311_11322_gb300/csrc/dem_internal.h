@@ -109,6 +109,7 @@ struct Arrays {
     dbl4 *gpart;                // partial sums [slot] (scratch)
     int64_t *gpart_base;           // per pile: first slot in gpart (or -1 = direct)
     int32_t *gnchunk;              // per pile: number of j-chunks
+    int32_t *gcounter;             // [0]: next work item of the persistent gravity grid
     // piles
     PileStatic *ps;
     PileDyn *pd;
@@ -117,6 +118,7 @@ struct Arrays {
 
 struct Sizes {
     int64_t N, A, C, T, CH, P, GI, GP;
+    int64_t GB;   // blocks of the persistent gravity grid (0 = one block per item)
 };
 
 // ---- kernel launchers (kernels_*.cu) -------------------------------------
@@ -128,8 +130,9 @@ void launch_scatter(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_cell_order(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_gather(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
 void launch_contact(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
-void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int ib,
+void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int ib, bool pack,
                     cudaStream_t st);
+int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack);
 void launch_agg_end(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
 void launch_pile_end(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_fill_ids(const Arrays &a, const Sizes &z, cudaStream_t st);

@@ -23,13 +23,44 @@ namespace dem {
 
 constexpr int kFlush = 1024;
 
-template <int BS, int IB>
-__global__ void __launch_bounds__(BS) k_gravity32(Arrays a, Sizes z)
+// Packed FP32 pairs (two lanes of one 64-bit register) for the sm_100-family
+// f32x2 instructions: one instruction does the same operation on two
+// i-spheres, halving the issue slots of the FP32 part of the pair term.
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi)
 {
-    __shared__ float4 sp[BS];
-    __shared__ int sag[BS];
-    __shared__ int excl[2];
-    const int4 it = a.gitems[blockIdx.x];
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_sub(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
+{
+    f2_t d;
+    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// One work item of the mixed-precision kernel (see the file comment).
+template <int BS, int IB>
+__device__ __forceinline__ void gravity32_item(const Arrays &a, const int4 it, float4 *sp, int *sag,
+                                               int *excl)
+{
     const int p = it.x;
     if (a.enabled[p] == 0 || a.pd[p].failed) return;
     const PileStatic &S = a.ps[p];
@@ -37,6 +68,7 @@ __global__ void __launch_bounds__(BS) k_gravity32(Arrays a, Sizes z)
     const int ns = (int)S.ns;
     const int i0 = it.y, j0 = it.z, j1 = it.w;
     const float eps2 = (float)S.eps2;
+    const float4 far = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.f);
     if (threadIdx.x == 0) {
         int ilast = min(i0 + BS * IB, ns) - 1;
         int alo = a.sph_agg[s0 + i0], ahi = a.sph_agg[s0 + ilast];
@@ -59,19 +91,22 @@ __global__ void __launch_bounds__(BS) k_gravity32(Arrays a, Sizes z)
     }
     __syncthreads();
     const int elo = excl[0], ehi = excl[1];
+    // register prefetch of the next tile overlaps its L2 latency with compute
+    int j = j0 + threadIdx.x;
+    float4 nxt = j < j1 ? a.gpos32[s0 + j] : far;
+    int nxa = (j0 < ehi && j0 + BS > elo && j < j1) ? a.sph_agg[s0 + j] : -1;
     int since = 0;
     for (int jt = j0; jt < j1; jt += BS) {
+        const bool masked = jt < ehi && jt + BS > elo;
         __syncthreads();
-        int j = jt + threadIdx.x;
-        if (j < j1) {
-            sp[threadIdx.x] = a.gpos32[s0 + j];
-            sag[threadIdx.x] = a.sph_agg[s0 + j];
-        } else {
-            sp[threadIdx.x] = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.f);
-            sag[threadIdx.x] = -1;
-        }
+        sp[threadIdx.x] = nxt;
+        sag[threadIdx.x] = nxa;
         __syncthreads();
-        if (jt < ehi && jt + BS > elo) {
+        const int jn = jt + BS;
+        j = jn + threadIdx.x;
+        nxt = j < j1 ? a.gpos32[s0 + j] : far;
+        nxa = (jn < ehi && jn + BS > elo && j < j1) ? a.sph_agg[s0 + j] : -1;
+        if (masked) {
             for (int jj = 0; jj < BS; ++jj) {
                 float4 pj = sp[jj];
                 int aj = sag[jj];
@@ -126,6 +161,187 @@ __global__ void __launch_bounds__(BS) k_gravity32(Arrays a, Sizes z)
             int64_t slot = a.gpart_base[p] + (int64_t)(j0 / ((ns + nch - 1) / nch)) * ns + il;
             a.gpart[slot] = make_dbl4(sx, sy, sz, 0.0);
         }
+    }
+}
+
+
+// Packed variant: each thread keeps NP pairs of i-spheres in f32x2 registers
+// for the whole work item (masked tiles included); the FP64 flush targets sit
+// in shared memory, which keeps the register count, and so the number of
+// resident warps, up.  Same terms and order of summation per sphere as the
+// scalar kernel up to the FP32 rounding of packed vs scalar lanes.
+template <int BS, int NP>
+__device__ __forceinline__ void gravity32p_item(const Arrays &a, const int4 it, float4 *sp, int *sag,
+                                                int *excl, double *sacc)
+{
+    constexpr int IB = 2 * NP;
+    const int p = it.x;
+    if (a.enabled[p] == 0 || a.pd[p].failed) return;
+    const PileStatic &S = a.ps[p];
+    const int64_t s0 = S.s0;
+    const int ns = (int)S.ns;
+    const int i0 = it.y, j0 = it.z, j1 = it.w;
+    const float eps2 = (float)S.eps2;
+    const float4 far = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.f);
+    const int t = threadIdx.x;
+    if (t == 0) {
+        int ilast = min(i0 + BS * IB, ns) - 1;
+        int alo = a.sph_agg[s0 + i0], ahi = a.sph_agg[s0 + ilast];
+        int64_t g0 = S.a0;
+        excl[0] = a.agg_first[g0 + alo];
+        excl[1] = a.agg_first[g0 + ahi] + a.agg_count[g0 + ahi];
+    }
+    f2_t px[NP], py[NP], pz[NP], qx[NP], qy[NP], qz[NP];
+    int ai[IB];
+    const f2_t zero2 = f2_pack(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        float4 u, v;
+        int ila = i0 + t + (2 * q) * BS, ilb = i0 + t + (2 * q + 1) * BS;
+        u = ila < ns ? a.gpos32[s0 + ila] : make_float4(0.f, 0.f, 0.f, 0.f);
+        v = ilb < ns ? a.gpos32[s0 + ilb] : make_float4(0.f, 0.f, 0.f, 0.f);
+        ai[2 * q] = ila < ns ? a.sph_agg[s0 + ila] : -2;
+        ai[2 * q + 1] = ilb < ns ? a.sph_agg[s0 + ilb] : -2;
+        px[q] = f2_pack(u.x, v.x);
+        py[q] = f2_pack(u.y, v.y);
+        pz[q] = f2_pack(u.z, v.z);
+        qx[q] = qy[q] = qz[q] = zero2;
+    }
+#pragma unroll
+    for (int c = 0; c < 6 * NP; ++c) sacc[c * BS + t] = 0.0;
+    __syncthreads();
+    const int elo = excl[0], ehi = excl[1];
+    const f2_t e2 = f2_pack(eps2, eps2);
+    int j = j0 + t;
+    float4 nxt = j < j1 ? a.gpos32[s0 + j] : far;
+    int nxa = (j0 < ehi && j0 + BS > elo && j < j1) ? a.sph_agg[s0 + j] : -1;
+    int since = 0;
+    const ulonglong2 *dup = reinterpret_cast<const ulonglong2 *>(sp);
+    for (int jt = j0; jt < j1; jt += BS) {
+        const bool masked = jt < ehi && jt + BS > elo;
+        __syncthreads();
+        sp[2 * t] = make_float4(nxt.x, nxt.x, nxt.y, nxt.y);
+        sp[2 * t + 1] = make_float4(nxt.z, nxt.z, nxt.w, nxt.w);
+        sag[t] = nxa;
+        __syncthreads();
+        const int jn = jt + BS;
+        j = jn + t;
+        nxt = j < j1 ? a.gpos32[s0 + j] : far;
+        nxa = (jn < ehi && jn + BS > elo && j < j1) ? a.sph_agg[s0 + j] : -1;
+        if (masked) {
+            for (int jj = 0; jj < BS; ++jj) {
+                const ulonglong2 xy = dup[2 * jj], zm = dup[2 * jj + 1];
+                const int aj = sag[jj];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    f2_t ddx = f2_sub(xy.x, px[q]), ddy = f2_sub(xy.y, py[q]), ddz = f2_sub(zm.x, pz[q]);
+                    f2_t r2 = f2_fma(ddz, ddz, f2_fma(ddy, ddy, f2_fma(ddx, ddx, e2)));
+                    float r2a, r2b;
+                    f2_unpack(r2, r2a, r2b);
+                    f2_t inv = f2_pack(rsqrtf(r2a), rsqrtf(r2b));
+                    f2_t sv = f2_mul(f2_mul(zm.y, inv), f2_mul(inv, inv));
+                    float sa, sb;
+                    f2_unpack(sv, sa, sb);
+                    sa = (aj == ai[2 * q]) ? 0.f : sa;
+                    sb = (aj == ai[2 * q + 1]) ? 0.f : sb;
+                    sv = f2_pack(sa, sb);
+                    qx[q] = f2_fma(ddx, sv, qx[q]);
+                    qy[q] = f2_fma(ddy, sv, qy[q]);
+                    qz[q] = f2_fma(ddz, sv, qz[q]);
+                }
+            }
+        } else {
+#pragma unroll 4
+            for (int jj = 0; jj < BS; ++jj) {
+                const ulonglong2 xy = dup[2 * jj], zm = dup[2 * jj + 1];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    f2_t ddx = f2_sub(xy.x, px[q]), ddy = f2_sub(xy.y, py[q]), ddz = f2_sub(zm.x, pz[q]);
+                    f2_t r2 = f2_fma(ddz, ddz, f2_fma(ddy, ddy, f2_fma(ddx, ddx, e2)));
+                    float r2a, r2b;
+                    f2_unpack(r2, r2a, r2b);
+                    f2_t inv = f2_pack(rsqrtf(r2a), rsqrtf(r2b));
+                    f2_t sv = f2_mul(f2_mul(zm.y, inv), f2_mul(inv, inv));
+                    qx[q] = f2_fma(ddx, sv, qx[q]);
+                    qy[q] = f2_fma(ddy, sv, qy[q]);
+                    qz[q] = f2_fma(ddz, sv, qz[q]);
+                }
+            }
+        }
+        since += BS;
+        if (since >= kFlush || jt + BS >= j1) {
+            since = 0;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                float lo, hi;
+                f2_unpack(qx[q], lo, hi);
+                sacc[(6 * q + 0) * BS + t] += lo;
+                sacc[(6 * q + 1) * BS + t] += hi;
+                f2_unpack(qy[q], lo, hi);
+                sacc[(6 * q + 2) * BS + t] += lo;
+                sacc[(6 * q + 3) * BS + t] += hi;
+                f2_unpack(qz[q], lo, hi);
+                sacc[(6 * q + 4) * BS + t] += lo;
+                sacc[(6 * q + 5) * BS + t] += hi;
+                qx[q] = qy[q] = qz[q] = zero2;
+            }
+        }
+    }
+    const int nch = a.gnchunk[p];
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int il = i0 + t + (2 * q + h) * BS;
+            if (il >= ns) continue;
+            double sx = sacc[(6 * q + 0 + h) * BS + t], sy = sacc[(6 * q + 2 + h) * BS + t],
+                   sz = sacc[(6 * q + 4 + h) * BS + t];
+            if (nch == 1) {
+                double gm = S.G * a.m64[s0 + il];
+                a.fg[s0 + il] = make_dbl4(gm * sx, gm * sy, gm * sz, 0.0);
+            } else {
+                int64_t slot = a.gpart_base[p] + (int64_t)(j0 / ((ns + nch - 1) / nch)) * ns + il;
+                a.gpart[slot] = make_dbl4(sx, sy, sz, 0.0);
+            }
+        }
+}
+
+template <int BS, int NP>
+__global__ void __launch_bounds__(BS) k_gravity32p(Arrays a, Sizes z)
+{
+    __shared__ float4 sp[2 * BS];
+    __shared__ int sag[BS];
+    __shared__ int excl[2];
+    __shared__ double sacc[6 * NP * BS];
+    __shared__ int next;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) next = atomicAdd(a.gcounter, 1);
+        __syncthreads();
+        const int item = next;
+        if (item >= z.GI) return;
+        gravity32p_item<BS, NP>(a, a.gitems[item], sp, sag, excl, sacc);
+    }
+}
+
+// Persistent grid: each block takes the next item from a counter that a
+// memset node zeroes before the launch, until the list is exhausted.  Items
+// are listed largest first; which block runs an item does not change its
+// result, so the sums stay deterministic.
+template <int BS, int IB>
+__global__ void __launch_bounds__(BS) k_gravity32(Arrays a, Sizes z)
+{
+    __shared__ float4 sp[BS];
+    __shared__ int sag[BS];
+    __shared__ int excl[2];
+    __shared__ int next;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) next = atomicAdd(a.gcounter, 1);
+        __syncthreads();
+        const int item = next;
+        if (item >= z.GI) return;
+        gravity32_item<BS, IB>(a, a.gitems[item], sp, sag, excl);
     }
 }
 
@@ -227,21 +443,61 @@ __global__ void k_grav_combine(Arrays a, Sizes z)
 }
 
 template <int BS, int IB>
-static void launch_g(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
+static void launch_g(const Arrays &a, const Sizes &z, bool fp64, bool pack, cudaStream_t st)
 {
-    if (fp64) k_gravity64<BS, IB><<<(unsigned)z.GI, BS, 0, st>>>(a, z);
-    else k_gravity32<BS, IB><<<(unsigned)z.GI, BS, 0, st>>>(a, z);
+    if (fp64) {
+        k_gravity64<BS, IB><<<(unsigned)z.GI, BS, 0, st>>>(a, z);
+    } else {
+        int64_t nb = z.GB > 0 && z.GB < z.GI ? z.GB : z.GI;
+        cudaMemsetAsync(a.gcounter, 0, sizeof(int32_t), st);
+        if constexpr (IB % 2 == 0) {
+            if (pack) {
+                k_gravity32p<BS, IB / 2><<<(unsigned)nb, BS, 0, st>>>(a, z);
+                return;
+            }
+        }
+        k_gravity32<BS, IB><<<(unsigned)nb, BS, 0, st>>>(a, z);
+    }
 }
 
-void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int ib, cudaStream_t st)
+template <int BS, int IB>
+static int occ(bool fp64, bool pack)
+{
+    int n = 0;
+    if (fp64) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity64<BS, IB>, BS, 0);
+    } else {
+        if constexpr (IB % 2 == 0) {
+            if (pack) {
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32p<BS, IB / 2>, BS, 0);
+                return n;
+            }
+        }
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32<BS, IB>, BS, 0);
+    }
+    return n;
+}
+
+int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack)
+{
+    if (block == 64) return ib == 1 ? occ<64, 1>(fp64, pack) : ib == 2 ? occ<64, 2>(fp64, pack) : occ<64, 4>(fp64, pack);
+    if (block == 128) return ib == 1 ? occ<128, 1>(fp64, pack) : ib == 2 ? occ<128, 2>(fp64, pack) : occ<128, 4>(fp64, pack);
+    return ib == 1 ? occ<256, 1>(fp64, pack) : ib == 2 ? occ<256, 2>(fp64, pack) : occ<256, 4>(fp64, pack);
+}
+
+void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int ib, bool pack,
+                    cudaStream_t st)
 {
     if (z.GI == 0) return;
-    if (block == 64 && ib == 1) launch_g<64, 1>(a, z, fp64, st);
-    else if (block == 64 && ib == 2) launch_g<64, 2>(a, z, fp64, st);
-    else if (block == 128 && ib == 1) launch_g<128, 1>(a, z, fp64, st);
-    else if (block == 128 && ib == 2) launch_g<128, 2>(a, z, fp64, st);
-    else if (block == 256 && ib == 1) launch_g<256, 1>(a, z, fp64, st);
-    else launch_g<256, 2>(a, z, fp64, st);
+    if (block == 64 && ib == 1) launch_g<64, 1>(a, z, fp64, pack, st);
+    else if (block == 64 && ib == 2) launch_g<64, 2>(a, z, fp64, pack, st);
+    else if (block == 64 && ib == 4) launch_g<64, 4>(a, z, fp64, pack, st);
+    else if (block == 128 && ib == 1) launch_g<128, 1>(a, z, fp64, pack, st);
+    else if (block == 128 && ib == 2) launch_g<128, 2>(a, z, fp64, pack, st);
+    else if (block == 128 && ib == 4) launch_g<128, 4>(a, z, fp64, pack, st);
+    else if (block == 256 && ib == 1) launch_g<256, 1>(a, z, fp64, pack, st);
+    else if (block == 256 && ib == 2) launch_g<256, 2>(a, z, fp64, pack, st);
+    else launch_g<256, 4>(a, z, fp64, pack, st);
     if (z.GP > 0) k_grav_combine<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
 }
 

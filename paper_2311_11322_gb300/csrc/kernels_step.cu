@@ -186,17 +186,28 @@ __global__ void k_pile_partials(Arrays a, Sizes z)
     if (threadIdx.x < 7) a.chunk_part[ch * kPartialDoubles + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// One thread per pile: combine the chunk partials in chunk order.
+// One block per pile: thread t adds chunks t, t+128, ... in order, then a fixed
+// tree combines the threads (deterministic for a given pile size).
 template <int MODE>
 __global__ void k_pile_finalize(Arrays a, Sizes z)
 {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = blockIdx.x;
     if (p >= z.P || !pile_active(a, p)) return;
     const PileStatic &S = a.ps[p];
-    PileDyn &D = a.pd[p];
+    __shared__ double sh[7][128];
     double s[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int64_t ch = S.ch0; ch < S.ch0 + S.nch; ++ch)
+    for (int64_t ch = S.ch0 + threadIdx.x; ch < S.ch0 + S.nch; ch += blockDim.x)
         for (int k = 0; k < 7; ++k) s[k] += a.chunk_part[ch * kPartialDoubles + k];
+    for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int o = 64; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    for (int k = 0; k < 7; ++k) s[k] = sh[k][0];
+    PileDyn &D = a.pd[p];
     const double h = S.h;
     if (MODE == 0) {
         for (int c = 0; c < 3; ++c) {
@@ -230,14 +241,14 @@ void launch_pile_begin(const Arrays &a, const Sizes &z, cudaStream_t st)
 {
     if (z.CH == 0) return;
     k_pile_partials<0><<<(unsigned)z.CH, 128, 0, st>>>(a, z);
-    k_pile_finalize<0><<<(unsigned)((z.P + 63) / 64), 64, 0, st>>>(a, z);
+    k_pile_finalize<0><<<(unsigned)z.P, 128, 0, st>>>(a, z);
 }
 
 void launch_pile_end(const Arrays &a, const Sizes &z, cudaStream_t st)
 {
     if (z.CH == 0) return;
     k_pile_partials<1><<<(unsigned)z.CH, 128, 0, st>>>(a, z);
-    k_pile_finalize<1><<<(unsigned)((z.P + 63) / 64), 64, 0, st>>>(a, z);
+    k_pile_finalize<1><<<(unsigned)z.P, 128, 0, st>>>(a, z);
 }
 
 // ---------------------------------------------------------------- expansion

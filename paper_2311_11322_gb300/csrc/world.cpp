@@ -57,8 +57,11 @@ struct dem_world {
     cudaGraphExec_t exec = nullptr;
     bool graph_valid = false;
     // tuning
-    int grav_block = 128, grav_ib = 2;
-    int64_t grav_jchunk = 0;
+    int grav_block = 128, grav_ib = 4;
+    int64_t grav_jchunk = 0;          // > 0: fixed j-range length per work item
+    double grav_item = 1048576.0;     // else: target interactions per work item
+    bool grav_pack = false;           // packed f32x2 pair terms (even grav_ib)
+    int sm_count = 0;
     double cell_factor = 1.0;
     // flags readback
     PileDyn *h_dyn = nullptr;   // pinned
@@ -178,6 +181,7 @@ void build_fields(dem_world *w)
     add((void **)&a.enabled, C_PILE, 4, false);
     add((void **)&a.gpart_base, C_PILE, 8, false);
     add((void **)&a.gnchunk, C_PILE, 4, false);
+    add((void **)&a.gcounter, C_PILE, 4, false);
     add((void **)&a.gitems, C_GITEM, 16, false);
     add((void **)&a.gpart, C_GPART, 32, false);
 }
@@ -214,7 +218,9 @@ GravPlan plan_gravity(const dem_world *w)
         const PileHost &q = w->piles[p];
         int64_t ns = q.ns;
         int64_t nch = 1;
-        if (w->grav_jchunk > 0 && ns > w->grav_jchunk) nch = (ns + w->grav_jchunk - 1) / w->grav_jchunk;
+        int64_t jlen = w->grav_jchunk;
+        if (jlen <= 0) jlen = std::max<int64_t>(w->grav_block, (int64_t)(w->grav_item / BI));
+        if (ns > jlen) nch = (ns + jlen - 1) / jlen;
         int64_t jc = (ns + nch - 1) / nch;
         if (q.P.G == 0.0) {   // no self-gravity: no work items; fg stays zero from set-up
             g.nch.push_back(1);
@@ -344,6 +350,14 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     w->Z.P = (int64_t)w->piles.size();
     w->Z.GI = (int64_t)gp.items.size();
     w->Z.GP = gp.gp;
+    if (w->sm_count == 0) {
+        int dev = 0;
+        CU(cudaGetDevice(&dev));
+        CU(cudaDeviceGetAttribute(&w->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    }
+    int bps = gravity_blocks_per_sm(w->precision == DEM_FP64, w->grav_block, w->grav_ib, w->grav_pack);
+    CU(cudaGetLastError());
+    w->Z.GB = (int64_t)std::max(1, bps) * w->sm_count;
     if (!ps.empty()) {
         CU(cudaMemcpyAsync(w->A.ps, ps.data(), sizeof(PileStatic) * ps.size(),
                            cudaMemcpyHostToDevice, w->stream));
@@ -375,7 +389,7 @@ void enqueue_phase(dem_world *w, int ph)
     case DEM_K_CELL_ORDER: launch_cell_order(a, z, st); break;
     case DEM_K_GATHER: launch_gather(a, z, d, st); break;
     case DEM_K_CONTACT: launch_contact(a, z, d, st); break;
-    case DEM_K_GRAVITY: launch_gravity(a, z, d, w->grav_block, w->grav_ib, st); break;
+    case DEM_K_GRAVITY: launch_gravity(a, z, d, w->grav_block, w->grav_ib, w->grav_pack, st); break;
     case DEM_K_AGG_END: launch_agg_end(a, z, d, st); break;
     case DEM_K_PILE_END: launch_pile_end(a, z, st); break;
     default: break;
@@ -1073,11 +1087,16 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
         w->grav_block = b;
     } else if (k == "grav_ib") {
         int b = (int)value;
-        if (b != 1 && b != 2) return fail(w, DEM_ERR_ARG, "grav_ib must be 1 or 2");
+        if (b != 1 && b != 2 && b != 4) return fail(w, DEM_ERR_ARG, "grav_ib must be 1, 2 or 4");
         w->grav_ib = b;
     } else if (k == "grav_jchunk") {
         if (value < 0) return fail(w, DEM_ERR_ARG, "grav_jchunk must be >= 0");
         w->grav_jchunk = (int64_t)value;
+    } else if (k == "grav_pack") {
+        w->grav_pack = value != 0.0;
+    } else if (k == "grav_item") {
+        if (!(value >= 1024.0)) return fail(w, DEM_ERR_ARG, "grav_item must be >= 1024");
+        w->grav_item = value;
     } else if (k == "cell_factor") {
         if (!(value >= 1.0) || value > 16.0) return fail(w, DEM_ERR_ARG, "cell_factor must be in [1, 16]");
         if (w->cell_factor != value) {
@@ -1120,25 +1139,22 @@ dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
 {
     if (!w || trial_steps < 1) return DEM_ERR_ARG;
     if (w->piles.empty()) return DEM_OK;
-    struct Cand { int blk, ib; int64_t jc; };
-    int64_t nmax = 0;
-    for (auto &q : w->piles) nmax = std::max(nmax, q.ns);
+    struct Cand { int blk, ib; double item; bool pack; };
     std::vector<Cand> cands;
     for (int blk : {64, 128, 256})
-        for (int ib : {1, 2}) {
-            cands.push_back({blk, ib, 0});
-            if (nmax >= 16384) {
-                cands.push_back({blk, ib, (nmax + 1) / 2});
-                cands.push_back({blk, ib, (nmax + 3) / 4});
+        for (int ib : {1, 2, 4})
+            for (double item : {262144.0, 1048576.0, 4194304.0}) {
+                cands.push_back({blk, ib, item, false});
+                if (ib % 2 == 0) cands.push_back({blk, ib, item, true});
             }
-        }
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     double best = 1e300;
-    Cand bc = {w->grav_block, w->grav_ib, w->grav_jchunk};
+    Cand bc = {w->grav_block, w->grav_ib, w->grav_item, w->grav_pack};
+    w->grav_jchunk = 0;
     for (auto &c : cands) {
-        w->grav_block = c.blk; w->grav_ib = c.ib; w->grav_jchunk = c.jc;
+        w->grav_block = c.blk; w->grav_ib = c.ib; w->grav_item = c.item; w->grav_pack = c.pack;
         w->graph_valid = false;
         dem_status s = prepare(w);
         if (s != DEM_OK) return s;
@@ -1156,7 +1172,7 @@ dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    w->grav_block = bc.blk; w->grav_ib = bc.ib; w->grav_jchunk = bc.jc;
+    w->grav_block = bc.blk; w->grav_ib = bc.ib; w->grav_item = bc.item; w->grav_pack = bc.pack;
     w->graph_valid = false;
     if (best_ms_out) *best_ms_out = best;
     return DEM_OK;
