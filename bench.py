@@ -206,10 +206,11 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576):
     z = float(cnt.sum())
     cells = info["nx"] * info["ny"] * info["nz"]
     N = ic.n_sph
-    # compulsory bytes per launch: own sorted state 4 x float4, sorted index,
-    # history count in/out, F and tau out (2 x float4), every contact's history
-    # slot read and written (float4 each), and the cell table (start + count)
-    algo = N * (64 + 4 + 4 + 4 + 32) + z * 32 + cells * 8
+    # compulsory bytes per launch: own sorted state 4 x float4 (64), sorted
+    # index, previous sorted position, previous and new history counts (4 x 4),
+    # F and tau out (2 x float4 = 32), every contact's history slot read and
+    # written (float4 each), and the cell table (start + count, 8 per cell)
+    algo = N * (64 + 16 + 32) + z * 32 + cells * 8
     ms = statistics.median(ks)
     achieved = algo / (ms / 1e3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",

@@ -99,7 +99,9 @@ enum dem_field {
     DEM_FIELD_MASS = 19,           /* A      aggregate mass (Eq. agg_mass) */
     DEM_FIELD_BODY_OFFSETS = 20,   /* N x 3  body-frame offsets b_i (never rewritten) */
     DEM_FIELD_OMEGA_BODY = 21,     /* A x 3  spin, body frame */
-    DEM_FIELD_INFO = 22            /* 16     n_agg, n_sph, steps, flags, nx, ny, nz, cell, ... */
+    DEM_FIELD_INFO = 22,           /* 16     n_agg, n_sph, steps, flags, nx, ny, nz, cell, ... */
+    DEM_FIELD_FRAME = 23,          /* 6      origin and velocity of the pile frame */
+    DEM_FIELD_TORQUE_STORED = 24   /* A x 3  stored N_A used by the next step's first half kick */
 };
 
 /* Pile flag bits (dem_pile_flags). */
@@ -200,6 +202,20 @@ dem_status dem_graph_kernel_count(dem_world *w, int32_t *n_out);
  */
 dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *host_out,
                           int64_t n_out);
+
+/*
+ * Overwrite one field of a pile from host memory (checkpoint restore, or
+ * re-synchronising with another integrator).  Writable fields, same layouts
+ * as dem_read_state: COM, VEL, QUAT (renormalised is the caller's duty),
+ * OMEGA_BODY, ACC, TORQUE_STORED, CONTACTS (only the first count entries of
+ * each sphere are read; partners must be pile-local indices < N), PLANET
+ * (position, velocity, acceleration) and FRAME.  Synchronises the stream
+ * first; the next dem_step starts from the written state.
+ * Errors: DEM_ERR_ARG (unknown pile or field, n_in too small, non-finite
+ * value, bad contact count or partner), DEM_ERR_CUDA.
+ */
+dem_status dem_write_state(dem_world *w, int32_t pile_id, int32_t field, const double *host_in,
+                           int64_t n_in);
 
 /* Flag bits (DEM_FLAG_*) raised so far for a pile; synchronises. */
 dem_status dem_pile_flags(dem_world *w, int32_t pile_id, int32_t *flags_out);

@@ -85,10 +85,14 @@ struct Arrays {
     float4 *gpos32;      // mixed: pos hi (+mass)
     dbl4 *gpos64;     // fp64: pos (+mass)
     dbl4 *fg;         // gravity on each sphere (from other aggregates)
-    // contact outputs, home order
-    float4 *fc32, *tc32;
-    dbl4 *fc64, *tc64;
-    // contact history, double-buffered by pile parity: slots [N*K], counts [N]
+    // contact outputs in sorted order, interleaved: [2k] = force, [2k+1] = torque
+    float4 *ftc32;
+    dbl4 *ftc64;
+    // sorted position (pile-local) of each home sphere, double-buffered by parity
+    int32_t *pos_of_home[2];
+    // contact history in sorted order, double-buffered by pile parity.  Slots
+    // are slot-major inside each pile: slot t of the sphere at pile-local
+    // sorted position k is element s0*K + t*ns + k; counts hist_n[s0 + k].
     float4 *hist32[2];
     dbl4 *hist64[2];
     int32_t *hist_n[2];
@@ -129,7 +133,7 @@ void launch_scan(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_scatter(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_cell_order(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_gather(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
-void launch_contact(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
+void launch_contact(const Arrays &a, const Sizes &z, bool fp64, int K, cudaStream_t st);
 void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int ib, bool pack,
                     cudaStream_t st);
 int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack);

@@ -14,6 +14,17 @@
 // flags; the neighbour order is fixed by the cell ordering, so the pass is
 // deterministic.
 //
+// Memory layout for coalescing: a thread handles the sphere at sorted
+// position k; the three x-adjacent cells of each (dy, dz) row are consecutive
+// in the sorted order, so the 27 neighbour cells are read as 9 index ranges.
+// History slots are stored in sorted order (slot-major inside each pile) and
+// read at the position the sphere had in the previous step, which neighbours
+// in the current order mostly share; the previous partners' ids are staged in
+// shared memory and matched with a cursor that follows the (deterministic)
+// order in which contacts are found.  Force and torque are written in sorted
+// order, interleaved, so that the aggregate reduction gathers one 32-byte
+// sector per sphere.
+//
 // Force law (the paper defers the constants and form to earlier work):
 //   d = r_b - r_a, n = d/|d|, x = s_a + s_b - |d| > 0 (overlap),
 //   l_a = (s_a^2 - s_b^2 + |d|^2) / (2|d|), l_b = |d| - l_a,
@@ -43,6 +54,15 @@ struct PairOut {
     T la, lb, x;
 };
 
+// Division and square root of the force law: fast hardware approximations in
+// FP32 (relative error ~1e-7, far inside the FP32 path's tolerance; both
+// spheres of a pair run the same instructions, so they still agree bitwise),
+// IEEE in FP64.
+__device__ __forceinline__ float qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float qsqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
+
 // Tangential spring, Coulomb cap and rolling/twisting couples, shared by
 // both precisions (T = float or double).
 template <typename T, typename V, typename P>
@@ -55,27 +75,32 @@ __device__ __forceinline__ void force_law(V n, T x, T la, T lb, V va, V wa, V vb
     V un = uns * n;
     V ut = u - un;
     V FN = (-prm.kn * x) * n + prm.cn * un;
-    T FNm = sqrt(dot(FN, FN));
+    T FNm = qsqrt(dot(FN, FN));
     T sn = dot(Sprev, n);
     V Sp = Sprev - sn * n;
-    T Spm = sqrt(dot(Sp, Sp)), Sprevm = sqrt(dot(Sprev, Sprev));
-    Sp = Spm > T(0) ? (Sprevm / Spm) * Sp : T(0) * Sp;
+    T Spm = qsqrt(dot(Sp, Sp)), Sprevm = qsqrt(dot(Sprev, Sprev));
+    Sp = Spm > T(0) ? qdiv(Sprevm, Spm) * Sp : T(0) * Sp;
     V S = Sp + prm.h * ut;
     V FT = prm.kt * S + prm.ct * ut;
-    T FTm = sqrt(dot(FT, FT)), cap = prm.mu_s * FNm;
+    T FTm = qsqrt(dot(FT, FT)), cap = prm.mu_s * FNm;
     if (FTm > cap) {
-        FT = (cap / FTm) * FT;
-        S = prm.kt > T(0) ? (T(1) / prm.kt) * (FT - prm.ct * ut) : T(0) * S;
+        FT = qdiv(cap, FTm) * FT;
+        S = prm.kt > T(0) ? qdiv(T(1), prm.kt) * (FT - prm.ct * ut) : T(0) * S;
     }
     V w = wa - wb;
     T wn = dot(w, n);
     V wt = wn * n;
     V wr = w - wt;
-    T Rred = sa * sb / (sa + sb);
+    T Rred = qdiv(sa * sb, sa + sb);
     V M = T(0) * n;
-    T wrm = sqrt(dot(wr, wr)), wtm = sqrt(dot(wt, wt));
-    if (prm.mu_r > T(0) && wrm > T(0)) M = M + (-prm.mu_r * FNm * Rred / fmax(wrm, prm.w0)) * wr;
-    if (prm.mu_t > T(0) && wtm > T(0)) M = M + (-prm.mu_t * FNm * Rred / fmax(wtm, prm.w0)) * wt;
+    if (prm.mu_r > T(0)) {
+        T wrm = qsqrt(dot(wr, wr));
+        if (wrm > T(0)) M = M + qdiv(-prm.mu_r * FNm * Rred, fmax(wrm, prm.w0)) * wr;
+    }
+    if (prm.mu_t > T(0)) {
+        T wtm = qsqrt(dot(wt, wt));
+        if (wtm > T(0)) M = M + qdiv(-prm.mu_t * FNm * Rred, fmax(wtm, prm.w0)) * wt;
+    }
     o.F = FN + FT;
     o.M = M;
     o.S = S;
@@ -87,8 +112,8 @@ __device__ __forceinline__ void force_law(V n, T x, T la, T lb, V va, V wa, V vb
 
 // Mixed precision pair: the overlap x = s_a + s_b - |d| is formed from
 // float-float positions and radii (exact differences by TwoSum, |d|^2 with
-// TwoProduct terms, one Newton correction of sqrt), so x keeps ~24 significant
-// bits even when x << |d|; the rest of the law is FP32.
+// TwoProduct terms, one Newton correction of a correctly rounded sqrt), so x
+// keeps ~24 significant bits even when x << |d|; the rest of the law is FP32.
 __device__ __forceinline__ bool pair_mixed(float4 ah, float4 al, float4 av, float4 aw, float4 bh,
                                            float4 bl, float4 bv, float4 bw, float3 Sprev,
                                            const ParamsF &prm, PairOut<float, float3> &o)
@@ -118,14 +143,14 @@ __device__ __forceinline__ bool pair_mixed(float4 ah, float4 al, float4 av, floa
     Dl = __fmaf_rn(2.0f, cr, Dl);
     float r = __fsqrt_rn(Dh);
     if (!(r > 0.0f)) return false;
-    float delta = __fdiv_rn(__fadd_rn(__fmaf_rn(-r, r, Dh), Dl), __fmul_rn(2.0f, r));
+    float inv = __frcp_rn(r);
+    float delta = __fmul_rn(__fadd_rn(__fmaf_rn(-r, r, Dh), Dl), __fmul_rn(0.5f, inv));
     float Sh, e;
     two_sum(ah.w, bh.w, Sh, e);
     float Sl = __fadd_rn(e, __fadd_rn(al.w, bl.w));
     float x = __fadd_rn(__fsub_rn(Sh, r), __fsub_rn(Sl, delta));
     if (!(x > 0.0f)) return false;
     float dist = __fadd_rn(r, delta);
-    float inv = __fdiv_rn(1.0f, dist);
     float3 n = f3(__fmul_rn(dhx, inv), __fmul_rn(dhy, inv), __fmul_rn(dhz, inv));
     float sa = ah.w, sb = bh.w;
     float la = __fmul_rn(__fmaf_rn(dist, dist, __fmul_rn(sa - sb, sa + sb)), __fmul_rn(0.5f, inv));
@@ -136,8 +161,8 @@ __device__ __forceinline__ bool pair_mixed(float4 ah, float4 al, float4 av, floa
     return true;
 }
 
-__device__ __forceinline__ bool pair_64(dbl4 ap, dbl4 av, dbl4 aw, dbl4 bp,
-                                        dbl4 bv, dbl4 bw, double3 Sprev, const ParamsD &prm,
+__device__ __forceinline__ bool pair_64(dbl4 ap, dbl4 av, dbl4 aw, dbl4 bp, dbl4 bv, dbl4 bw,
+                                        double3 Sprev, const ParamsD &prm,
                                         PairOut<double, double3> &o)
 {
     double3 d = d3(bp.x - ap.x, bp.y - ap.y, bp.z - ap.z);
@@ -171,65 +196,97 @@ __device__ __forceinline__ int cellc_d(double x, double inv_cell, int n)
     return m < 0 ? m + n : m;
 }
 
-__device__ __forceinline__ float maxabs3(float4 p)
+// The (up to 3) sorted index ranges of the x-neighbour cells cx-1..cx+1 of
+// one (y, z) row: one range when no wrap-around splits them.
+struct Strip {
+    int beg[3], end[3], n;
+};
+
+__device__ __forceinline__ void strip_ranges(const int32_t *cstart, const int32_t *ccount,
+                                             int rowbase, int cx, int nx, Strip &s)
 {
-    return fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z)));
+    if (cx >= 1 && cx + 1 < nx) {
+        int c0 = rowbase + cx - 1, c2 = rowbase + cx + 1;
+        s.beg[0] = cstart[c0];
+        s.end[0] = cstart[c2] + ccount[c2];
+        s.n = 1;
+    } else {
+        s.n = 0;
+        for (int dx = -1; dx <= 1; ++dx) {
+            int c = rowbase + wrapc(cx + dx, nx);
+            s.beg[s.n] = cstart[c];
+            s.end[s.n] = cstart[c] + ccount[c];
+            ++s.n;
+        }
+    }
 }
 
+constexpr int kContactBlock = 128;
+
 template <bool FP64>
-__global__ void __launch_bounds__(128) k_contact(Arrays a, Sizes z)
+__global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
 {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    extern __shared__ int s_prev[];   // [K][kContactBlock] partner ids of the previous contacts
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= z.N) return;
-    int p = a.sph_pile[k];
+    const int p = a.sph_pile[k];
     if (a.enabled[p] == 0 || a.pd[p].failed) return;
     const PileStatic &S = a.ps[p];
     const int64_t s0 = S.s0;
+    const int ns = (int)S.ns;
     const int K = S.K;
     const int nx = S.nx, ny = S.ny, nz = S.nz;
     const int par = a.pd[p].parity;
+    const int kl = (int)(k - s0);
     const int hl = a.sorted[k];
-    const int64_t i = s0 + hl;
-    const int32_t *hn_prev = a.hist_n[par];
+    const int prevk = a.pos_of_home[par][s0 + hl];
+    const int nprev = a.hist_n[par][s0 + prevk];
     int32_t *hn_new = a.hist_n[par ^ 1];
-    int flags = 0;
-    int nn = 0;
-    const int nprev = hn_prev[i];
+    const int32_t *cstart = a.cstart + S.c0, *ccount = a.ccount + S.c0;
+    int *myprev = s_prev + threadIdx.x;
+    int flags = 0, nn = 0, cursor = 0;
 
     if (FP64) {
-        ParamsD prm = {S.kn, S.kt, S.cn, S.ct, S.mu_s, S.mu_r, S.mu_t, S.w0, S.h};
+        const ParamsD prm = {S.kn, S.kt, S.cn, S.ct, S.mu_s, S.mu_r, S.mu_t, S.w0, S.h};
+        const dbl4 *hprev = a.hist64[par] + s0 * K + prevk;
+        dbl4 *hnew = a.hist64[par ^ 1] + s0 * K + kl;
+        for (int t = 0; t < nprev; ++t) myprev[t * kContactBlock] = (int)hprev[(int64_t)t * ns].w;
         const dbl4 me_p = a.dp_[k], me_v = a.dv_[k], me_w = a.dw_[k];
         const int my_agg = (int)me_v.w;
-        const dbl4 *hprev = a.hist64[par] + i * K;
-        dbl4 *hnew = a.hist64[par ^ 1] + i * K;
-        int cx = cellc_d(me_p.x, S.inv_cell, nx), cy = cellc_d(me_p.y, S.inv_cell, ny),
-            cz = cellc_d(me_p.z, S.inv_cell, nz);
+        const int cx = cellc_d(me_p.x, S.inv_cell, nx), cy = cellc_d(me_p.y, S.inv_cell, ny),
+                  cz = cellc_d(me_p.z, S.inv_cell, nz);
         double3 F = d3(0, 0, 0), T = d3(0, 0, 0);
         for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int c = (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx + wrapc(cx + dx, nx);
-                    int st = a.cstart[S.c0 + c], cnt = a.ccount[S.c0 + c];
-                    for (int t = 0; t < cnt; ++t) {
-                        int64_t kk = s0 + st + t;
+            for (int dy = -1; dy <= 1; ++dy) {
+                Strip sr;
+                strip_ranges(cstart, ccount, (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx, cx, nx, sr);
+                for (int r = 0; r < sr.n; ++r)
+                    for (int t = sr.beg[r]; t < sr.end[r]; ++t) {
+                        const int64_t kk = s0 + t;
                         if (kk == k) continue;
-                        dbl4 nv = a.dv_[kk];
+                        const dbl4 np = a.dp_[kk];
+                        const double ddx = np.x - me_p.x, ddy = np.y - me_p.y, ddz = np.z - me_p.z;
+                        const double sr2 = np.w + me_p.w;
+                        if (ddx * ddx + ddy * ddy + ddz * ddz >= sr2 * sr2) continue;
+                        const dbl4 nv = a.dv_[kk];
                         if ((int)nv.w == my_agg) continue;
-                        dbl4 np = a.dp_[kk];
-                        double ddx = np.x - me_p.x, ddy = np.y - me_p.y, ddz = np.z - me_p.z;
-                        double sr = np.w + me_p.w;
-                        if (ddx * ddx + ddy * ddy + ddz * ddz >= sr * sr) continue;
-                        dbl4 nw = a.dw_[kk];
-                        int ngid = (int)nw.w;
+                        const dbl4 nw = a.dw_[kk];
+                        const int ngid = (int)nw.w;
+                        int slot = -1;
+                        if (cursor < nprev && myprev[cursor * kContactBlock] == ngid) slot = cursor;
+                        else
+                            for (int h = 0; h < nprev; ++h)
+                                if (myprev[h * kContactBlock] == ngid) { slot = h; break; }
                         double3 Sprev = d3(0, 0, 0);
-                        for (int h = 0; h < nprev; ++h) {
-                            dbl4 sl = hprev[h];
-                            if ((int)sl.w == ngid) { Sprev = d3(sl.x, sl.y, sl.z); break; }
+                        if (slot >= 0) {
+                            const dbl4 sl = hprev[(int64_t)slot * ns];
+                            Sprev = d3(sl.x, sl.y, sl.z);
+                            cursor = slot + 1;
                         }
-                        bool first = hl < ngid;
+                        const bool first = hl < ngid;
                         PairOut<double, double3> o;
-                        bool hit = first ? pair_64(me_p, me_v, me_w, np, nv, nw, Sprev, prm, o)
-                                         : pair_64(np, nv, nw, me_p, me_v, me_w, Sprev, prm, o);
+                        const bool hit = first ? pair_64(me_p, me_v, me_w, np, nv, nw, Sprev, prm, o)
+                                               : pair_64(np, nv, nw, me_p, me_v, me_w, Sprev, prm, o);
                         if (!hit) continue;
                         if (first) {
                             F = F + o.F;
@@ -238,55 +295,62 @@ __global__ void __launch_bounds__(128) k_contact(Arrays a, Sizes z)
                             F = F - o.F;
                             T = T + cross(o.lb * o.n, o.F) - o.M;
                         }
-                        if (nn < K) hnew[nn] = make_dbl4(o.S.x, o.S.y, o.S.z, (double)ngid);
+                        if (nn < K) hnew[(int64_t)nn * ns] = make_dbl4(o.S.x, o.S.y, o.S.z, (double)ngid);
                         else flags |= DEM_FLAG_SLOTS;
                         ++nn;
                         if (o.x > 0.1 * fmin(me_p.w, np.w)) flags |= DEM_FLAG_OVERLAP;
                     }
-                }
-        a.fc64[i] = make_dbl4(F.x, F.y, F.z, 0.0);
-        a.tc64[i] = make_dbl4(T.x, T.y, T.z, 0.0);
+            }
+        a.ftc64[2 * k] = make_dbl4(F.x, F.y, F.z, 0.0);
+        a.ftc64[2 * k + 1] = make_dbl4(T.x, T.y, T.z, 0.0);
     } else {
-        ParamsF prm = {(float)S.kn, (float)S.kt, (float)S.cn, (float)S.ct, (float)S.mu_s,
-                       (float)S.mu_r, (float)S.mu_t, (float)S.w0, (float)S.h};
-        const float4 me_h = a.sph_[k], me_l = a.spl_[k], me_v = a.sv_[k], me_w = a.sw_[k];
-        const int my_agg = __float_as_int(me_v.w);
-        const float my_abs = maxabs3(me_h);
-        const float4 *hprev = a.hist32[par] + i * K;
-        float4 *hnew = a.hist32[par ^ 1] + i * K;
+        const ParamsF prm = {(float)S.kn, (float)S.kt, (float)S.cn, (float)S.ct, (float)S.mu_s,
+                             (float)S.mu_r, (float)S.mu_t, (float)S.w0, (float)S.h};
+        const float4 *hprev = a.hist32[par] + s0 * K + prevk;
+        float4 *hnew = a.hist32[par ^ 1] + s0 * K + kl;
+        for (int t = 0; t < nprev; ++t) myprev[t * kContactBlock] = __float_as_int(hprev[(int64_t)t * ns].w);
+        const float4 me_h = a.sph_[k];
         const float icell = (float)S.inv_cell;
-        int cx = cellc_f(me_h.x, icell, nx), cy = cellc_f(me_h.y, icell, ny),
-            cz = cellc_f(me_h.z, icell, nz);
+        const int cx = cellc_f(me_h.x, icell, nx), cy = cellc_f(me_h.y, icell, ny),
+                  cz = cellc_f(me_h.z, icell, nz);
+        // rounding of the hi parts is at most ulp(|p|)/2 per coordinate; every
+        // neighbour lies within 2 cells, so one margin serves all candidates
+        const float my_abs = fmaxf(fabsf(me_h.x), fmaxf(fabsf(me_h.y), fabsf(me_h.z)));
+        const float tol = 4.0e-7f * (2.0f * my_abs + 3.0f * (float)S.cell) + 4.0e-6f * me_h.w;
+        const float4 me_l = a.spl_[k], me_v = a.sv_[k], me_w = a.sw_[k];
+        const int my_agg = __float_as_int(me_v.w);
         float3 F = f3(0, 0, 0), T = f3(0, 0, 0);
         for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int c = (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx + wrapc(cx + dx, nx);
-                    int st = a.cstart[S.c0 + c], cnt = a.ccount[S.c0 + c];
-                    for (int t = 0; t < cnt; ++t) {
-                        int64_t kk = s0 + st + t;
-                        if (kk == k) continue;
-                        float4 nh = a.sph_[kk];
-                        // FP32 pre-filter with a margin covering the rounding of the hi parts
-                        float ddx = nh.x - me_h.x, ddy = nh.y - me_h.y, ddz = nh.z - me_h.z;
-                        float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        float sr = nh.w + me_h.w;
-                        float tol = 4.0e-7f * (my_abs + maxabs3(nh)) + 4.0e-6f * sr;
-                        float srt = sr + tol;
-                        if (r2 > srt * srt) continue;
-                        float4 nv = a.sv_[kk];
+            for (int dy = -1; dy <= 1; ++dy) {
+                Strip sr;
+                strip_ranges(cstart, ccount, (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx, cx, nx, sr);
+                for (int r = 0; r < sr.n; ++r)
+                    for (int t = sr.beg[r]; t < sr.end[r]; ++t) {
+                        const int64_t kk = s0 + t;
+                        const float4 nh = a.sph_[kk];
+                        const float ddx = nh.x - me_h.x, ddy = nh.y - me_h.y, ddz = nh.z - me_h.z;
+                        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        const float srt = nh.w + me_h.w + tol;
+                        if (r2 > srt * srt || kk == k) continue;
+                        const float4 nv = a.sv_[kk];
                         if (__float_as_int(nv.w) == my_agg) continue;
-                        float4 nl = a.spl_[kk], nw = a.sw_[kk];
-                        int ngid = __float_as_int(nw.w);
+                        const float4 nl = a.spl_[kk], nw = a.sw_[kk];
+                        const int ngid = __float_as_int(nw.w);
+                        int slot = -1;
+                        if (cursor < nprev && myprev[cursor * kContactBlock] == ngid) slot = cursor;
+                        else
+                            for (int h = 0; h < nprev; ++h)
+                                if (myprev[h * kContactBlock] == ngid) { slot = h; break; }
                         float3 Sprev = f3(0, 0, 0);
-                        for (int h = 0; h < nprev; ++h) {
-                            float4 sl = hprev[h];
-                            if (__float_as_int(sl.w) == ngid) { Sprev = f3(sl.x, sl.y, sl.z); break; }
+                        if (slot >= 0) {
+                            const float4 sl = hprev[(int64_t)slot * ns];
+                            Sprev = f3(sl.x, sl.y, sl.z);
+                            cursor = slot + 1;
                         }
-                        bool first = hl < ngid;
+                        const bool first = hl < ngid;
                         PairOut<float, float3> o;
-                        bool hit = first ? pair_mixed(me_h, me_l, me_v, me_w, nh, nl, nv, nw, Sprev, prm, o)
-                                         : pair_mixed(nh, nl, nv, nw, me_h, me_l, me_v, me_w, Sprev, prm, o);
+                        const bool hit = first ? pair_mixed(me_h, me_l, me_v, me_w, nh, nl, nv, nw, Sprev, prm, o)
+                                               : pair_mixed(nh, nl, nv, nw, me_h, me_l, me_v, me_w, Sprev, prm, o);
                         if (!hit) continue;
                         if (first) {
                             F = F + o.F;
@@ -295,25 +359,26 @@ __global__ void __launch_bounds__(128) k_contact(Arrays a, Sizes z)
                             F = F - o.F;
                             T = T + cross(o.lb * o.n, o.F) - o.M;
                         }
-                        if (nn < K) hnew[nn] = make_float4(o.S.x, o.S.y, o.S.z, __int_as_float(ngid));
+                        if (nn < K) hnew[(int64_t)nn * ns] = make_float4(o.S.x, o.S.y, o.S.z, __int_as_float(ngid));
                         else flags |= DEM_FLAG_SLOTS;
                         ++nn;
                         if (o.x > 0.1f * fminf(me_h.w, nh.w)) flags |= DEM_FLAG_OVERLAP;
                     }
-                }
-        a.fc32[i] = make_float4(F.x, F.y, F.z, 0.f);
-        a.tc32[i] = make_float4(T.x, T.y, T.z, 0.f);
+            }
+        a.ftc32[2 * k] = make_float4(F.x, F.y, F.z, 0.f);
+        a.ftc32[2 * k + 1] = make_float4(T.x, T.y, T.z, 0.f);
     }
-    hn_new[i] = nn < K ? nn : K;
+    hn_new[k] = nn < K ? nn : K;
     if (flags) atomicOr(&a.pd[p].flags, flags);
 }
 
-void launch_contact(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
+void launch_contact(const Arrays &a, const Sizes &z, bool fp64, int K, cudaStream_t st)
 {
     if (z.N == 0) return;
-    unsigned nb = (unsigned)((z.N + 127) / 128);
-    if (fp64) k_contact<true><<<nb, 128, 0, st>>>(a, z);
-    else k_contact<false><<<nb, 128, 0, st>>>(a, z);
+    unsigned nb = (unsigned)((z.N + kContactBlock - 1) / kContactBlock);
+    size_t smem = sizeof(int) * (size_t)K * kContactBlock;
+    if (fp64) k_contact<true><<<nb, kContactBlock, smem, st>>>(a, z);
+    else k_contact<false><<<nb, kContactBlock, smem, st>>>(a, z);
 }
 
 }  // namespace dem

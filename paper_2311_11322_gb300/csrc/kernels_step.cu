@@ -501,6 +501,7 @@ __global__ void k_gather(Arrays a, Sizes z)
     int64_t i = S.s0 + hl;
     int al = a.sph_agg[i];
     int64_t g = S.a0 + al;
+    a.pos_of_home[a.pd[p].parity ^ 1][i] = (int32_t)(k - S.s0);
     if (FP64) {
         const AggRec64 &rec = a.rec64[g];
         const double *b = a.b64 + 3 * i;
@@ -559,6 +560,7 @@ __global__ void k_agg_end(Arrays a, Sizes z)
     const bool planet = S.ext_mass > 0;
     double3 Pp = planet ? ld3(D.P_pos) : d3(0, 0, 0);
     double3 O = ld3(D.O);
+    const int32_t *poh = a.pos_of_home[D.parity ^ 1];
     for (int t = 0; t < n; ++t) {
         int64_t i = i0 + t;
         double3 lever, fc, tc, pos;
@@ -566,7 +568,8 @@ __global__ void k_agg_end(Arrays a, Sizes z)
             const AggRec64 &rec = a.rec64[g];
             const double *b = a.b64 + 3 * i;
             lever = mat_mul(rec.R, d3(b[0], b[1], b[2]));
-            dbl4 f = a.fc64[i], tq = a.tc64[i];
+            int64_t ks = S.s0 + poh[i];
+            dbl4 f = a.ftc64[2 * ks], tq = a.ftc64[2 * ks + 1];
             fc = d3(f.x, f.y, f.z);
             tc = d3(tq.x, tq.y, tq.z);
             if (planet) pos = O + expand_64(rec, b);
@@ -576,7 +579,8 @@ __global__ void k_agg_end(Arrays a, Sizes z)
             lever = d3(rec.Rh[0] * bh.x + rec.Rh[1] * bh.y + rec.Rh[2] * bh.z,
                        rec.Rh[3] * bh.x + rec.Rh[4] * bh.y + rec.Rh[5] * bh.z,
                        rec.Rh[6] * bh.x + rec.Rh[7] * bh.y + rec.Rh[8] * bh.z);
-            float4 f = a.fc32[i], tq = a.tc32[i];
+            int64_t ks = S.s0 + poh[i];
+            float4 f = a.ftc32[2 * ks], tq = a.ftc32[2 * ks + 1];
             fc = d3(f.x, f.y, f.z);
             tc = d3(tq.x, tq.y, tq.z);
             if (planet) {

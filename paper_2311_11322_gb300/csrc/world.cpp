@@ -134,13 +134,14 @@ void build_fields(dem_world *w)
     add((void **)&a.fg, C_SPH, 32, true);
     add((void **)&a.hist_n[0], C_SPH, 4, true);
     add((void **)&a.hist_n[1], C_SPH, 4, true);
+    add((void **)&a.pos_of_home[0], C_SPH, 4, true);
+    add((void **)&a.pos_of_home[1], C_SPH, 4, true);
     if (d) {
         add((void **)&a.dp_, C_SPH, 32, false);
         add((void **)&a.dv_, C_SPH, 32, false);
         add((void **)&a.dw_, C_SPH, 32, false);
         add((void **)&a.gpos64, C_SPH, 32, false);
-        add((void **)&a.fc64, C_SPH, 32, true);
-        add((void **)&a.tc64, C_SPH, 32, true);
+        add((void **)&a.ftc64, C_SPH, 64, true);
         add((void **)&a.hist64[0], C_SPHK, 32, true);
         add((void **)&a.hist64[1], C_SPHK, 32, true);
         add((void **)&a.rec64, C_AGG, sizeof(AggRec64), false);
@@ -152,8 +153,7 @@ void build_fields(dem_world *w)
         add((void **)&a.sv_, C_SPH, 16, false);
         add((void **)&a.sw_, C_SPH, 16, false);
         add((void **)&a.gpos32, C_SPH, 16, false);
-        add((void **)&a.fc32, C_SPH, 16, true);
-        add((void **)&a.tc32, C_SPH, 16, true);
+        add((void **)&a.ftc32, C_SPH, 32, true);
         add((void **)&a.hist32[0], C_SPHK, 16, true);
         add((void **)&a.hist32[1], C_SPHK, 16, true);
         add((void **)&a.rec32, C_AGG, sizeof(AggRecMixed), false);
@@ -388,7 +388,7 @@ void enqueue_phase(dem_world *w, int ph)
     case DEM_K_SCATTER: launch_scatter(a, z, st); break;
     case DEM_K_CELL_ORDER: launch_cell_order(a, z, st); break;
     case DEM_K_GATHER: launch_gather(a, z, d, st); break;
-    case DEM_K_CONTACT: launch_contact(a, z, d, st); break;
+    case DEM_K_CONTACT: launch_contact(a, z, d, w->K, st); break;
     case DEM_K_GRAVITY: launch_gravity(a, z, d, w->grav_block, w->grav_ib, w->grav_pack, st); break;
     case DEM_K_AGG_END: launch_agg_end(a, z, d, st); break;
     case DEM_K_PILE_END: launch_pile_end(a, z, st); break;
@@ -751,6 +751,10 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     std::vector<int32_t> zeros_i(N, 0);
     UP(D.hist_n[0] + s0, zeros_i.data(), 4 * N);
     UP(D.hist_n[1] + s0, zeros_i.data(), 4 * N);
+    std::vector<int32_t> iota(N);
+    for (int64_t i = 0; i < N; ++i) iota[i] = (int32_t)i;
+    UP(D.pos_of_home[0] + s0, iota.data(), 4 * N);
+    UP(D.pos_of_home[1] + s0, iota.data(), 4 * N);
     CU(cudaMemsetAsync(D.fg + s0, 0, 32 * N, st));
     if (w->precision == DEM_MIXED) {
         std::vector<float4> bh(N), bl(N);
@@ -762,11 +766,9 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
         }
         UP(D.bh + s0, bh.data(), 16 * N);
         UP(D.bl + s0, bl.data(), 16 * N);
-        CU(cudaMemsetAsync(D.fc32 + s0, 0, 16 * N, st));
-        CU(cudaMemsetAsync(D.tc32 + s0, 0, 16 * N, st));
+        CU(cudaMemsetAsync(D.ftc32 + 2 * s0, 0, 32 * N, st));
     } else {
-        CU(cudaMemsetAsync(D.fc64 + s0, 0, 32 * N, st));
-        CU(cudaMemsetAsync(D.tc64 + s0, 0, 32 * N, st));
+        CU(cudaMemsetAsync(D.ftc64 + 2 * s0, 0, 64 * N, st));
     }
     UP(D.agg_first + a0, first.data(), 4 * A);
     UP(D.agg_count + a0, spa, 4 * A);
@@ -920,6 +922,11 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
     case DEM_FIELD_QUAT: CHK(need(4 * A)); CHK(get(out, D.q + 4 * a0, 32 * A)); break;
     case DEM_FIELD_OMEGA_BODY: CHK(need(3 * A)); CHK(get(out, D.wb + 3 * a0, 24 * A)); break;
     case DEM_FIELD_ACC: CHK(need(3 * A)); CHK(get(out, D.acc + 3 * a0, 24 * A)); break;
+    case DEM_FIELD_TORQUE_STORED: CHK(need(3 * A)); CHK(get(out, D.torque + 3 * a0, 24 * A)); break;
+    case DEM_FIELD_FRAME:
+        CHK(need(6));
+        for (int c = 0; c < 3; ++c) { out[c] = dyn.O[c]; out[3 + c] = dyn.V[c]; }
+        break;
     case DEM_FIELD_MASS: CHK(need(A)); CHK(get(out, D.M + a0, 8 * A)); break;
     case DEM_FIELD_BODY_OFFSETS: CHK(need(3 * N)); CHK(get(out, D.b64 + 3 * s0, 24 * N)); break;
     case DEM_FIELD_OMEGA: {
@@ -984,14 +991,25 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
             std::vector<dbl4> f(N);
             CHK(get(f.data(), D.fg + s0, 32 * N));
             for (int64_t i = 0; i < N; ++i) { out[3 * i] = f[i].x; out[3 * i + 1] = f[i].y; out[3 * i + 2] = f[i].z; }
-        } else if (w->precision == DEM_FP64) {
-            std::vector<dbl4> f(N);
-            CHK(get(f.data(), (field == DEM_FIELD_SPHERE_FC ? D.fc64 : D.tc64) + s0, 32 * N));
-            for (int64_t i = 0; i < N; ++i) { out[3 * i] = f[i].x; out[3 * i + 1] = f[i].y; out[3 * i + 2] = f[i].z; }
+            break;
+        }
+        std::vector<int32_t> pos(N);
+        CHK(get(pos.data(), D.pos_of_home[dyn.parity] + s0, 4 * N));
+        const int sel = field == DEM_FIELD_SPHERE_FC ? 0 : 1;
+        if (w->precision == DEM_FP64) {
+            std::vector<dbl4> f(2 * N);
+            CHK(get(f.data(), D.ftc64 + 2 * s0, 64 * N));
+            for (int64_t i = 0; i < N; ++i) {
+                const dbl4 &e = f[2 * (int64_t)pos[i] + sel];
+                out[3 * i] = e.x; out[3 * i + 1] = e.y; out[3 * i + 2] = e.z;
+            }
         } else {
-            std::vector<float4> f(N);
-            CHK(get(f.data(), (field == DEM_FIELD_SPHERE_FC ? D.fc32 : D.tc32) + s0, 16 * N));
-            for (int64_t i = 0; i < N; ++i) { out[3 * i] = f[i].x; out[3 * i + 1] = f[i].y; out[3 * i + 2] = f[i].z; }
+            std::vector<float4> f(2 * N);
+            CHK(get(f.data(), D.ftc32 + 2 * s0, 32 * N));
+            for (int64_t i = 0; i < N; ++i) {
+                const float4 &e = f[2 * (int64_t)pos[i] + sel];
+                out[3 * i] = e.x; out[3 * i + 1] = e.y; out[3 * i + 2] = e.z;
+            }
         }
         break;
     }
@@ -999,32 +1017,34 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
         const int K = w->K;
         CHK(need(N * (1 + 4 * (int64_t)K)));
         int par = dyn.parity;
-        std::vector<int32_t> cnt(N);
+        std::vector<int32_t> cnt(N), pos(N);
         CHK(get(cnt.data(), D.hist_n[par] + s0, 4 * N));
+        CHK(get(pos.data(), D.pos_of_home[par] + s0, 4 * N));
         std::fill(out, out + N * (1 + 4 * (int64_t)K), 0.0);
+        std::vector<double> slot(4 * N * K);
         if (w->precision == DEM_FP64) {
             std::vector<dbl4> h(N * K);
             CHK(get(h.data(), D.hist64[par] + s0 * K, 32 * N * K));
-            for (int64_t i = 0; i < N; ++i) {
-                double *o = out + i * (1 + 4 * K);
-                o[0] = cnt[i];
-                for (int t = 0; t < cnt[i]; ++t) {
-                    const dbl4 &e = h[i * K + t];
-                    o[1 + 4 * t] = e.w; o[2 + 4 * t] = e.x; o[3 + 4 * t] = e.y; o[4 + 4 * t] = e.z;
-                }
+            for (int64_t e = 0; e < N * K; ++e) {
+                slot[4 * e] = h[e].w; slot[4 * e + 1] = h[e].x; slot[4 * e + 2] = h[e].y; slot[4 * e + 3] = h[e].z;
             }
         } else {
             std::vector<float4> h(N * K);
             CHK(get(h.data(), D.hist32[par] + s0 * K, 16 * N * K));
-            for (int64_t i = 0; i < N; ++i) {
-                double *o = out + i * (1 + 4 * K);
-                o[0] = cnt[i];
-                for (int t = 0; t < cnt[i]; ++t) {
-                    const float4 &e = h[i * K + t];
-                    int32_t pid;
-                    std::memcpy(&pid, &e.w, 4);
-                    o[1 + 4 * t] = pid; o[2 + 4 * t] = e.x; o[3 + 4 * t] = e.y; o[4 + 4 * t] = e.z;
-                }
+            for (int64_t e = 0; e < N * K; ++e) {
+                int32_t pid;
+                std::memcpy(&pid, &h[e].w, 4);
+                slot[4 * e] = pid; slot[4 * e + 1] = h[e].x; slot[4 * e + 2] = h[e].y; slot[4 * e + 3] = h[e].z;
+            }
+        }
+        for (int64_t i = 0; i < N; ++i) {
+            double *o = out + i * (1 + 4 * K);
+            int64_t k = pos[i];
+            int n = cnt[k];
+            o[0] = n;
+            for (int t = 0; t < n; ++t) {
+                const double *e = &slot[4 * ((int64_t)t * N + k)];
+                o[1 + 4 * t] = e[0]; o[2 + 4 * t] = e[1]; o[3 + 4 * t] = e[2]; o[4 + 4 * t] = e[3];
             }
         }
         break;
@@ -1044,6 +1064,96 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
     }
     default:
         return fail(w, DEM_ERR_ARG, "unknown field %d", field);
+    }
+#undef CHK
+    return DEM_OK;
+}
+
+dem_status dem_write_state(dem_world *w, int32_t pile_id, int32_t field, const double *in,
+                           int64_t n_in)
+{
+    if (!w) return DEM_ERR_ARG;
+    int slot = find_pile(w, pile_id);
+    if (slot < 0) return fail(w, DEM_ERR_ARG, "unknown pile id %d", pile_id);
+    if (!in) return fail(w, DEM_ERR_ARG, "NULL input");
+    CU(cudaStreamSynchronize(w->stream));
+    const PileHost &q = w->piles[slot];
+    int64_t s0 = 0, a0 = 0;
+    for (int t = 0; t < slot; ++t) { s0 += w->piles[t].ns; a0 += w->piles[t].na; }
+    const int64_t N = q.ns, A = q.na;
+    const Arrays &D = w->A;
+    auto put = [&](void *dst, const void *src, size_t bytes) -> dem_status {
+        CU(cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice));
+        return DEM_OK;
+    };
+    auto need = [&](int64_t n) -> dem_status {
+        if (n_in < n) return fail(w, DEM_ERR_ARG, "input too small: need %lld doubles", (long long)n);
+        if (!finite_all(in, n)) return fail(w, DEM_ERR_ARG, "non-finite input");
+        return DEM_OK;
+    };
+    dem_status s;
+#define CHK(x) do { s = (x); if (s != DEM_OK) return s; } while (0)
+    PileDyn dyn;
+    CU(cudaMemcpy(&dyn, D.pd + slot, sizeof dyn, cudaMemcpyDeviceToHost));
+    switch (field) {
+    case DEM_FIELD_COM: CHK(need(3 * A)); CHK(put(D.r + 3 * a0, in, 24 * A)); break;
+    case DEM_FIELD_VEL: CHK(need(3 * A)); CHK(put(D.v + 3 * a0, in, 24 * A)); break;
+    case DEM_FIELD_QUAT: CHK(need(4 * A)); CHK(put(D.q + 4 * a0, in, 32 * A)); break;
+    case DEM_FIELD_OMEGA_BODY: CHK(need(3 * A)); CHK(put(D.wb + 3 * a0, in, 24 * A)); break;
+    case DEM_FIELD_ACC: CHK(need(3 * A)); CHK(put(D.acc + 3 * a0, in, 24 * A)); break;
+    case DEM_FIELD_TORQUE_STORED: CHK(need(3 * A)); CHK(put(D.torque + 3 * a0, in, 24 * A)); break;
+    case DEM_FIELD_PLANET:
+    case DEM_FIELD_FRAME: {
+        CHK(need(field == DEM_FIELD_PLANET ? 9 : 6));
+        for (int c = 0; c < 3; ++c) {
+            if (field == DEM_FIELD_PLANET) {
+                dyn.P_pos[c] = in[c]; dyn.P_vel[c] = in[3 + c]; dyn.P_acc[c] = in[6 + c];
+            } else {
+                dyn.O[c] = in[c]; dyn.V[c] = in[3 + c];
+            }
+        }
+        CHK(put(D.pd + slot, &dyn, sizeof dyn));
+        break;
+    }
+    case DEM_FIELD_CONTACTS: {
+        const int K = w->K;
+        const int64_t row = 1 + 4 * (int64_t)K;
+        if (n_in < N * row) return fail(w, DEM_ERR_ARG, "input too small: need %lld doubles", (long long)(N * row));
+        const int par = dyn.parity;
+        std::vector<int32_t> pos(N), cnt(N, 0);
+        CU(cudaMemcpy(pos.data(), D.pos_of_home[par] + s0, 4 * N, cudaMemcpyDeviceToHost));
+        const bool d64 = w->precision == DEM_FP64;
+        std::vector<float4> h32(d64 ? 0 : N * K);
+        std::vector<dbl4> h64(d64 ? N * K : 0);
+        for (int64_t i = 0; i < N; ++i) {
+            const double *e = in + i * row;
+            int n = (int)e[0];
+            if (!(e[0] >= 0) || n > K || (double)n != e[0])
+                return fail(w, DEM_ERR_ARG, "sphere %lld: bad contact count", (long long)i);
+            int64_t k = pos[i];
+            cnt[k] = n;
+            for (int t = 0; t < n; ++t) {
+                const double *sl = e + 1 + 4 * t;
+                if (!(sl[0] >= 0 && sl[0] < (double)N) || !finite_all(sl + 1, 3))
+                    return fail(w, DEM_ERR_ARG, "sphere %lld: bad contact entry", (long long)i);
+                int64_t idx = (int64_t)t * N + k;
+                if (d64) {
+                    h64[idx] = make_dbl4(sl[1], sl[2], sl[3], sl[0]);
+                } else {
+                    int32_t pid = (int32_t)sl[0];
+                    float pf;
+                    std::memcpy(&pf, &pid, 4);
+                    h32[idx] = make_float4((float)sl[1], (float)sl[2], (float)sl[3], pf);
+                }
+            }
+        }
+        CHK(put(D.hist_n[par] + s0, cnt.data(), 4 * N));
+        if (d64) CHK(put(D.hist64[par] + s0 * K, h64.data(), 32 * N * K));
+        else CHK(put(D.hist32[par] + s0 * K, h32.data(), 16 * N * K));
+        break;
+    }
+    default:
+        return fail(w, DEM_ERR_ARG, "field %d is not writable", field);
     }
 #undef CHK
     return DEM_OK;
@@ -1183,7 +1293,8 @@ size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contact
     if (n_spheres < 0 || n_agg < 0 || max_contacts < 1) return 0;
     bool d = precision == DEM_FP64;
     size_t sph = 4 + 4 + 24 + 8 + 8 + 4 + 4 + 4 + 32 + 4 + 4;
-    sph += d ? (32 * 3 + 32 + 32 + 32) : (16 * 2 + 16 * 4 + 16 + 16 + 16);
+    sph += 8;   // pos_of_home, both parities
+    sph += d ? (32 * 3 + 32 + 64) : (16 * 2 + 16 * 4 + 16 + 32);
     size_t sphk = d ? 2 * 32 : 2 * 16;
     size_t agg = 4 * 3 + 8 + 72 * 2 + 24 * 2 + 32 + 24 * 3 + 144 + (d ? sizeof(AggRec64) : sizeof(AggRecMixed));
     int64_t cells = std::max<int64_t>(4 * n_spheres, 27) + kScanTile;

@@ -33,6 +33,7 @@ FIELDS = {  # name: (id, rows ('A' aggregates / 'N' spheres / int), cols)
     "TORQUE_EXT": (13, "A", 3), "SPHERE_FC": (14, "N", 3), "SPHERE_TC": (15, "N", 3),
     "SPHERE_FG": (16, "N", 3), "ACC": (17, "A", 3), "PLANET": (18, 9, None), "MASS": (19, "A", 1),
     "BODY_OFFSETS": (20, "N", 3), "OMEGA_BODY": (21, "A", 3), "INFO": (22, 16, None),
+    "FRAME": (23, 6, None), "TORQUE_STORED": (24, "A", 3),
 }
 KERNELS = {"AGG_BEGIN": 0, "PILE_BEGIN": 1, "KEYS": 2, "SCAN": 3, "SCATTER": 4,
            "CELL_ORDER": 5, "GATHER": 6, "CONTACT": 7, "GRAVITY": 8, "AGG_END": 9,
@@ -86,6 +87,7 @@ def load():
         "dem_step_timed": (i32, [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
         "dem_graph_kernel_count": (i32, [vp, C.POINTER(i32)]),
         "dem_gravity_noalloc": (i32, [vp, vp, vp, i32, dbl, dbl, vp, vp, C.c_char_p, sz]),
+        "dem_write_state": (i32, [vp, i32, i32, vp, i64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -246,6 +248,21 @@ class World:
             out = np.zeros((n, cols)) if cols > 1 else np.zeros(n)
         self._check(self._L.dem_read_state(self.w, pile, fid, _ptr(out), out.size))
         return out
+
+    def write(self, pile, field, values):
+        fid = FIELDS[field][0]
+        v = np.ascontiguousarray(values, np.float64)
+        self._check(self._L.dem_write_state(self.w, int(pile), fid, _ptr(v), v.size))
+
+    def checkpoint(self, pile):
+        """Everything the next step reads, as host arrays (bit-exact restore)."""
+        names = ("COM", "VEL", "QUAT", "OMEGA_BODY", "ACC", "TORQUE_STORED", "CONTACTS",
+                 "PLANET", "FRAME")
+        return {n: self.read(pile, n) for n in names}
+
+    def restore(self, pile, ck):
+        for n, v in ck.items():
+            self.write(pile, n, v)
 
     def contacts(self, pile):
         """Contact pairs (i < j, pile-local sphere indices) and their S vectors."""

@@ -85,3 +85,52 @@ def lockstep(world, pid, pile, steps, tol, r_ref=1.0, check_contacts=True, every
             worst["contacts"] = max(worst["contacts"], ns)
         assert worst["F"] <= tol and worst["N"] <= tol, f"step {k + 1}: {worst}"
     return worst
+
+
+def oracle_contacts_field(pile, K):
+    """The oracle's contact history as the CONTACTS layout of dem_read_state:
+    per sphere, count then (partner, Sx, Sy, Sz); both spheres of a pair carry S."""
+    N = pile.N
+    out = np.zeros((N, 1 + 4 * K))
+    hc = pile.h_n
+    hp = pile.h_partner.reshape(N, -1)
+    hS = pile.h_S.reshape(N, -1, 3)
+    for i in range(N):
+        for t in range(hc[i]):
+            j = hp[i, t]
+            for a, b in ((i, j), (j, i)):
+                n = int(out[a, 0])
+                assert n < K, "too many contacts for the GPU history"
+                out[a, 1 + 4 * n:5 + 4 * n] = (b, *hS[i, t])
+                out[a, 0] = n + 1
+    return out
+
+
+def resync(world, pid, pile, K):
+    """Copy the oracle's full state into the GPU pile (oracle -> GPU only)."""
+    world.write(pid, "COM", pile.r)
+    world.write(pid, "VEL", pile.v)
+    world.write(pid, "QUAT", pile.q)
+    world.write(pid, "OMEGA_BODY", pile.wb)
+    world.write(pid, "ACC", pile.acc)
+    world.write(pid, "TORQUE_STORED", pile.torque)
+    world.write(pid, "PLANET", pile.planet)
+    world.write(pid, "CONTACTS", oracle_contacts_field(pile, K))
+
+
+def resynced_steps(world, pid, pile, steps, tol, K, r_ref=1.0):
+    """Per-step errors from identical states: before each step the GPU pile is
+    overwritten with the oracle's state, then both take one step."""
+    worst = dict(F=0.0, N=0.0, contacts=0)
+    for k in range(steps):
+        resync(world, pid, pile, K)
+        pile.step()
+        world.step(1)
+        eF, eN = agg_errors(world, pid, pile)
+        worst["F"] = max(worst["F"], float(eF.max()))
+        worst["N"] = max(worst["N"], float(eN.max()))
+        ns, ng, bad = contact_set_check(world, pid, pile, r_ref)
+        assert not bad, f"step {k + 1}: contact sets differ: {bad[:5]}"
+        worst["contacts"] = max(worst["contacts"], ns)
+        assert worst["F"] <= tol and worst["N"] <= tol, f"step {k + 1}: {worst}"
+    return worst

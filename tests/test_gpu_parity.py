@@ -10,7 +10,8 @@ import numpy as np
 import pytest
 
 from paper_2311_11322_gb300 import workloads as W
-from tests.parity_util import TOL, agg_errors, contact_set_check, lockstep, sphere_errors
+from tests.parity_util import (TOL, agg_errors, contact_set_check, lockstep, resynced_steps,
+                               sphere_errors)
 
 pytestmark = pytest.mark.gpu
 
@@ -43,15 +44,19 @@ def new_world(dem, **kw):
 @pytest.mark.parametrize("prec", PRECS)
 def test_random_cluster_lockstep(dem, oracle, prec):
     """Overlapping aggregates of all four shapes, with spin and velocity:
-    normal, tangential, rolling and twisting terms live for 30 steps."""
+    normal, tangential, rolling and twisting terms live.  10 free steps side by
+    side (trajectories of this violent, heavily overlapping cluster separate
+    chaotically after that), then 30 steps each taken from the oracle's state."""
     ic, p = W.random_cluster(3, n_agg=70, box=5.0, precision=prec)
     p = p.replace(mu_t=0.05, G=W.G_SI * 1e4)
     pile = oracle.Pile(ic, p, want_scales=True)
     with new_world(dem) as w:
         pid = w.add_pile(ic, p)
-        worst = lockstep(w, pid, pile, 30, TOL[prec], r_ref=1.0)
+        worst = lockstep(w, pid, pile, 10, TOL[prec], r_ref=1.0)
         assert worst["contacts"] > 20
         assert worst["Fc"] <= 10 * TOL[prec] and worst["Fg"] <= 10 * TOL[prec]
+        worst = resynced_steps(w, pid, pile, 30, TOL[prec], p.max_contacts)
+        assert worst["contacts"] > 20
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -327,3 +332,37 @@ def test_profiled_step_times_kernel(dem):
         w.add_pile(ic, p)
         ms = w.step_profiled(3, "GRAVITY")
         assert ms.shape == (3,) and np.all(ms > 0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_checkpoint_restore_bitwise(dem, prec):
+    """Run 20 steps; separately run 10, checkpoint, restore into a fresh world
+    and run 10 more: the final states are bit-identical."""
+    ic, p = W.dense_lattice(n_spheres=3000, seed=6, precision=prec)
+    p = p.replace(G=W.G_SI * 1e3)
+    with new_world(dem) as w:
+        pid = w.add_pile(ic, p)
+        w.step(10)
+        ck = w.checkpoint(pid)
+        w.step(10)
+        ref = (w.read(pid, "COM"), w.read(pid, "QUAT"), w.read(pid, "TORQUE"),
+               w.read(pid, "CONTACTS"))
+    with new_world(dem) as w:
+        pid = w.add_pile(ic, p)
+        w.restore(pid, ck)
+        w.step(10)
+        got = (w.read(pid, "COM"), w.read(pid, "QUAT"), w.read(pid, "TORQUE"),
+               w.read(pid, "CONTACTS"))
+    for g, r in zip(got, ref):
+        assert np.array_equal(g, r)
+
+
+def test_dense_lattice_resynced_steps_mixed(dem, oracle):
+    """Per-step error of the mixed path from identical states (no trajectory
+    drift): contacts with friction and rolling on the dense lattice."""
+    ic, p = W.dense_lattice(n_spheres=2000, seed=7, precision=W.PRECISION_MIXED)
+    pile = oracle.Pile(ic, p, want_scales=True)
+    with new_world(dem) as w:
+        pid = w.add_pile(ic, p)
+        worst = resynced_steps(w, pid, pile, 20, TOL[1], p.max_contacts)
+        assert worst["contacts"] > 3000
