@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-contact", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--part", default="all", choices=["all", "contact"],
+                    help="contact: only the contact-pass roofline on the 1M-sphere lattice")
+    ap.add_argument("--contact-n", type=int, default=1_048_576)
     return ap.parse_args()
 
 
@@ -183,7 +186,7 @@ def run_fp64(dem, W, steps):
             "steps": steps, "dtype": "f64"}
 
 
-def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576):
+def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3):
     """Contact pass on a dense FCC-tetrahedra lattice (0.5% R overlaps, 9 contacts
     per sphere), gravity off, working set far above L2."""
     import torch
@@ -194,7 +197,7 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576):
         w.set_timed_kernel("CONTACT")
         flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
         st = torch.cuda.ExternalStream(w.stream)
-        for _ in range(3):
+        for _ in range(warmup):
             w.step_timed()
         ks = []
         for _ in range(steps):
@@ -395,9 +398,23 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_contact_only(args):
+    import torch
+    from paper_2311_11322_gb300 import dem
+    from paper_2311_11322_gb300 import workloads as W
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    r = run_contact_roofline(dem, W, float(peaks().get("hbm_gbs", 6800.0)), steps=args.steps,
+                             n=args.contact_n, warmup=args.warmup)
+    print(json.dumps({"part": "contact", "roofline_contact": r}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.part == "contact":
+        run_contact_only(a)
     else:
         run_ours(a)

@@ -81,6 +81,7 @@ struct Arrays {
     // sorted copies for the contact pass
     float4 *sph_, *spl_, *sv_, *sw_;   // mixed: pos hi (+s hi), pos lo (+s lo), vel (+agg), spin (+gid)
     dbl4 *dp_, *dv_, *dw_;          // fp64: pos (+s), vel (+agg), spin (+gid)
+    int32_t *sagg;                  // aggregate (pile-local) of each sorted position
     // gravity inputs / outputs
     float4 *gpos32;      // mixed: pos hi (+mass)
     dbl4 *gpos64;     // fp64: pos (+mass)
@@ -123,6 +124,8 @@ struct Arrays {
 struct Sizes {
     int64_t N, A, C, T, CH, P, GI, GP;
     int64_t GB;   // blocks of the persistent gravity grid (0 = one block per item)
+    int32_t K;    // history slots per sphere (world-wide)
+    int32_t stage;  // contact pass may stage neighbour rows in shared memory
 };
 
 // ---- kernel launchers (kernels_*.cu) -------------------------------------
@@ -134,6 +137,7 @@ void launch_scatter(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_cell_order(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_gather(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
 void launch_contact(const Arrays &a, const Sizes &z, bool fp64, int K, cudaStream_t st);
+cudaError_t contact_setup(bool fp64, int K);
 void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int ib, bool pack,
                     cudaStream_t st);
 int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack);

@@ -222,161 +222,327 @@ __device__ __forceinline__ void strip_ranges(const int32_t *cstart, const int32_
 }
 
 constexpr int kContactBlock = 128;
+constexpr int kStageCap = 1536;      // staged neighbour spheres per block
+constexpr int kMaxStageRows = 12;
+constexpr int kHitList = 16;         // filter hits buffered per thread before the pair pass
+
+template <bool FP64> struct CT;
+template <> struct CT<false> {
+    typedef float T;
+    typedef float3 V;
+    typedef float4 P4;
+    typedef ParamsF Prm;
+};
+template <> struct CT<true> {
+    typedef double T;
+    typedef double3 V;
+    typedef dbl4 P4;
+    typedef ParamsD Prm;
+};
+
+// Per-sphere state of the thread's own sphere and its running sums.
+template <bool FP64>
+struct Me {
+    typename CT<FP64>::P4 p, v, w;   // position(+radius hi), velocity(+agg), spin(+gid)
+    float4 l;                        // mixed: position lo (+radius lo)
+    int agg, hl, nprev, nn, cursor, flags;
+    float tol;                       // mixed: pre-filter margin
+    typename CT<FP64>::V F, T;
+};
+
+// Candidate filter: overlap possible (bounding test with the FP32 rounding
+// margin in mixed precision), not the sphere itself, other aggregate.
+template <bool FP64>
+__device__ __forceinline__ bool candidate(int64_t k, int64_t kk, const typename CT<FP64>::P4 &nh,
+                                          int nagg, const Me<FP64> &m)
+{
+    if constexpr (FP64) {
+        const double ddx = nh.x - m.p.x, ddy = nh.y - m.p.y, ddz = nh.z - m.p.z;
+        const double sr2 = nh.w + m.p.w;
+        return ddx * ddx + ddy * ddy + ddz * ddz < sr2 * sr2 && kk != k && nagg != m.agg;
+    } else {
+        const float ddx = nh.x - m.p.x, ddy = nh.y - m.p.y, ddz = nh.z - m.p.z;
+        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+        const float srt = nh.w + m.p.w + m.tol;
+        return r2 <= srt * srt && kk != k && nagg != m.agg;
+    }
+}
+
+// One candidate that passed the filter: history lookup, canonical pair
+// evaluation, accumulation and slot write.
+template <bool FP64>
+__device__ __forceinline__ void process(const Arrays &a, int64_t kk, Me<FP64> &m, const int *myprev,
+                                        const void *hprev_v, void *hnew_v, int ns, int K,
+                                        const typename CT<FP64>::Prm &prm)
+{
+    typedef typename CT<FP64>::V V;
+    typename CT<FP64>::P4 nh, nv, nw;
+    int ngid;
+    if constexpr (FP64) {
+        nh = a.dp_[kk];
+        nv = a.dv_[kk];
+        nw = a.dw_[kk];
+        ngid = (int)nw.w;
+    } else {
+        nh = a.sph_[kk];
+        nv = a.sv_[kk];
+        nw = a.sw_[kk];
+        ngid = __float_as_int(nw.w);
+    }
+    int slot = -1;
+    if (m.cursor < m.nprev && myprev[m.cursor * kContactBlock] == ngid) slot = m.cursor;
+    else
+        for (int h = 0; h < m.nprev; ++h)
+            if (myprev[h * kContactBlock] == ngid) { slot = h; break; }
+    V Sprev;
+    if constexpr (FP64) Sprev = d3(0, 0, 0);
+    else Sprev = f3(0, 0, 0);
+    if (slot >= 0) {
+        if constexpr (FP64) {
+            const dbl4 sl = ((const dbl4 *)hprev_v)[(int64_t)slot * ns];
+            Sprev = d3(sl.x, sl.y, sl.z);
+        } else {
+            const float4 sl = ((const float4 *)hprev_v)[(int64_t)slot * ns];
+            Sprev = f3(sl.x, sl.y, sl.z);
+        }
+        m.cursor = slot + 1;
+    }
+    // canonical orientation: the lower pile-local index is sphere a.  The
+    // operands are selected first and the pair law is inlined once, so both
+    // spheres of a pair run one instruction stream (bitwise equal results)
+    // and the lanes of a warp do not split over two copies of it.
+    const bool first = m.hl < ngid;
+    PairOut<typename CT<FP64>::T, V> o;
+    bool hit;
+    if constexpr (FP64) {
+        const dbl4 ap = first ? m.p : nh, av = first ? m.v : nv, aw = first ? m.w : nw;
+        const dbl4 bp = first ? nh : m.p, bv = first ? nv : m.v, bw = first ? nw : m.w;
+        hit = pair_64(ap, av, aw, bp, bv, bw, Sprev, prm, o);
+    } else {
+        const float4 nl = a.spl_[kk];
+        const float4 ah = first ? m.p : nh, al = first ? m.l : nl, av = first ? m.v : nv,
+                     aw = first ? m.w : nw;
+        const float4 bh = first ? nh : m.p, bl = first ? nl : m.l, bv = first ? nv : m.v,
+                     bw = first ? nw : m.w;
+        hit = pair_mixed(ah, al, av, aw, bh, bl, bv, bw, Sprev, prm, o);
+    }
+    if (!hit) return;
+    // sphere a: F, (l_a n) x F + M;  sphere b: -F, (l_b n) x F - M
+    const typename CT<FP64>::T sg = first ? 1 : -1;
+    const typename CT<FP64>::T lev = first ? o.la : o.lb;
+    m.F = m.F + sg * o.F;
+    m.T = m.T + cross(lev * o.n, o.F) + sg * o.M;
+    if (m.nn < K) {
+        if constexpr (FP64)
+            ((dbl4 *)hnew_v)[(int64_t)m.nn * ns] = make_dbl4(o.S.x, o.S.y, o.S.z, (double)ngid);
+        else
+            ((float4 *)hnew_v)[(int64_t)m.nn * ns] = make_float4(o.S.x, o.S.y, o.S.z, __int_as_float(ngid));
+    } else {
+        m.flags |= DEM_FLAG_SLOTS;
+    }
+    ++m.nn;
+    if (o.x > typename CT<FP64>::T(0.1) * fmin(m.p.w, nh.w)) m.flags |= DEM_FLAG_OVERLAP;
+}
 
 template <bool FP64>
 __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
 {
-    extern __shared__ int s_prev[];   // [K][kContactBlock] partner ids of the previous contacts
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    typedef typename CT<FP64>::P4 P4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_off[kMaxStageRows + 1], s_beg[kMaxStageRows];
+    __shared__ int s_ok, s_ya, s_span, s_zc, s_total, s_nq;
+    const int K = z.K;
+    P4 *st_pos = (P4 *)smem_raw;
+    int *st_agg = (int *)(st_pos + kStageCap);
+    int *s_list = st_agg + kStageCap;   // [kHitList][kContactBlock]
+    int *s_prev = s_list + kHitList * kContactBlock;   // [K][kContactBlock]
+
+    // ---- block set-up: can this tile's neighbourhood be staged?
+    const int64_t kfirst = (int64_t)blockIdx.x * kContactBlock;
+    if (threadIdx.x == 0) {
+        s_ok = 0;
+        const int64_t klast = min(kfirst + kContactBlock, z.N) - 1;
+        const int p = a.sph_pile[kfirst];
+        if (z.stage && p == a.sph_pile[klast] && a.enabled[p] != 0 && a.pd[p].failed == 0) {
+            const PileStatic &S = a.ps[p];
+            const int nx = S.nx, ny = S.ny, nz = S.nz;
+            const int rf = a.key[S.s0 + a.sorted[kfirst]] / nx;
+            const int rl = a.key[S.s0 + a.sorted[klast]] / nx;
+            const int yf = rf % ny, zf = rf / ny, yl = rl % ny, zl = rl / ny;
+            int span = 0;
+            if (rf == rl) span = 3;
+            else if (zl == zf && yl == yf + 1) span = 4;
+            if (span) {
+                const int32_t *cs = a.cstart + S.c0, *cc = a.ccount + S.c0;
+                int tot = 0;
+                const int nq = 3 * span;
+                for (int q = 0; q < nq; ++q) {
+                    const int dz = q / span - 1, yy = q % span;
+                    const int row = wrapc(zf + dz, nz) * ny + wrapc(yf - 1 + yy, ny);
+                    const int c0 = row * nx, c1 = c0 + nx - 1;
+                    s_beg[q] = cs[c0];
+                    s_off[q] = tot;
+                    tot += cs[c1] + cc[c1] - cs[c0];
+                }
+                s_off[nq] = tot;
+                if (tot <= kStageCap) {
+                    s_ok = 1;
+                    s_ya = yf - 1;
+                    s_span = span;
+                    s_zc = zf;
+                    s_total = tot;
+                    s_nq = nq;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const bool staged = s_ok != 0;
+    if (staged) {
+        const PileStatic &S = a.ps[a.sph_pile[kfirst]];
+        const int tot = s_total, nq = s_nq;
+        for (int idx = threadIdx.x; idx < tot; idx += kContactBlock) {
+            int q = 0;
+            while (q + 1 < nq && s_off[q + 1] <= idx) ++q;
+            const int64_t src = S.s0 + s_beg[q] + (idx - s_off[q]);
+            if constexpr (FP64) st_pos[idx] = a.dp_[src];
+            else st_pos[idx] = a.sph_[src];
+            st_agg[idx] = a.sagg[src];
+        }
+    }
+    __syncthreads();
+
+    const int64_t k = kfirst + threadIdx.x;
     if (k >= z.N) return;
     const int p = a.sph_pile[k];
     if (a.enabled[p] == 0 || a.pd[p].failed) return;
     const PileStatic &S = a.ps[p];
     const int64_t s0 = S.s0;
     const int ns = (int)S.ns;
-    const int K = S.K;
     const int nx = S.nx, ny = S.ny, nz = S.nz;
     const int par = a.pd[p].parity;
     const int kl = (int)(k - s0);
-    const int hl = a.sorted[k];
-    const int prevk = a.pos_of_home[par][s0 + hl];
-    const int nprev = a.hist_n[par][s0 + prevk];
-    int32_t *hn_new = a.hist_n[par ^ 1];
+    Me<FP64> m;
+    m.hl = a.sorted[k];
+    const int prevk = a.pos_of_home[par][s0 + m.hl];
+    m.nprev = a.hist_n[par][s0 + prevk];
+    m.nn = 0;
+    m.cursor = 0;
+    m.flags = 0;
     const int32_t *cstart = a.cstart + S.c0, *ccount = a.ccount + S.c0;
     int *myprev = s_prev + threadIdx.x;
-    int flags = 0, nn = 0, cursor = 0;
-
-    if (FP64) {
-        const ParamsD prm = {S.kn, S.kt, S.cn, S.ct, S.mu_s, S.mu_r, S.mu_t, S.w0, S.h};
-        const dbl4 *hprev = a.hist64[par] + s0 * K + prevk;
-        dbl4 *hnew = a.hist64[par ^ 1] + s0 * K + kl;
-        for (int t = 0; t < nprev; ++t) myprev[t * kContactBlock] = (int)hprev[(int64_t)t * ns].w;
-        const dbl4 me_p = a.dp_[k], me_v = a.dv_[k], me_w = a.dw_[k];
-        const int my_agg = (int)me_v.w;
-        const int cx = cellc_d(me_p.x, S.inv_cell, nx), cy = cellc_d(me_p.y, S.inv_cell, ny),
-                  cz = cellc_d(me_p.z, S.inv_cell, nz);
-        double3 F = d3(0, 0, 0), T = d3(0, 0, 0);
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy) {
-                Strip sr;
-                strip_ranges(cstart, ccount, (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx, cx, nx, sr);
-                for (int r = 0; r < sr.n; ++r)
-                    for (int t = sr.beg[r]; t < sr.end[r]; ++t) {
-                        const int64_t kk = s0 + t;
-                        if (kk == k) continue;
-                        const dbl4 np = a.dp_[kk];
-                        const double ddx = np.x - me_p.x, ddy = np.y - me_p.y, ddz = np.z - me_p.z;
-                        const double sr2 = np.w + me_p.w;
-                        if (ddx * ddx + ddy * ddy + ddz * ddz >= sr2 * sr2) continue;
-                        const dbl4 nv = a.dv_[kk];
-                        if ((int)nv.w == my_agg) continue;
-                        const dbl4 nw = a.dw_[kk];
-                        const int ngid = (int)nw.w;
-                        int slot = -1;
-                        if (cursor < nprev && myprev[cursor * kContactBlock] == ngid) slot = cursor;
-                        else
-                            for (int h = 0; h < nprev; ++h)
-                                if (myprev[h * kContactBlock] == ngid) { slot = h; break; }
-                        double3 Sprev = d3(0, 0, 0);
-                        if (slot >= 0) {
-                            const dbl4 sl = hprev[(int64_t)slot * ns];
-                            Sprev = d3(sl.x, sl.y, sl.z);
-                            cursor = slot + 1;
-                        }
-                        const bool first = hl < ngid;
-                        PairOut<double, double3> o;
-                        const bool hit = first ? pair_64(me_p, me_v, me_w, np, nv, nw, Sprev, prm, o)
-                                               : pair_64(np, nv, nw, me_p, me_v, me_w, Sprev, prm, o);
-                        if (!hit) continue;
-                        if (first) {
-                            F = F + o.F;
-                            T = T + cross(o.la * o.n, o.F) + o.M;
-                        } else {
-                            F = F - o.F;
-                            T = T + cross(o.lb * o.n, o.F) - o.M;
-                        }
-                        if (nn < K) hnew[(int64_t)nn * ns] = make_dbl4(o.S.x, o.S.y, o.S.z, (double)ngid);
-                        else flags |= DEM_FLAG_SLOTS;
-                        ++nn;
-                        if (o.x > 0.1 * fmin(me_p.w, np.w)) flags |= DEM_FLAG_OVERLAP;
-                    }
-            }
-        a.ftc64[2 * k] = make_dbl4(F.x, F.y, F.z, 0.0);
-        a.ftc64[2 * k + 1] = make_dbl4(T.x, T.y, T.z, 0.0);
+    const void *hprev;
+    void *hnew;
+    int cx, cy, cz;
+    typename CT<FP64>::Prm prm;
+    if constexpr (FP64) {
+        prm = {S.kn, S.kt, S.cn, S.ct, S.mu_s, S.mu_r, S.mu_t, S.w0, S.h};
+        const dbl4 *hp = a.hist64[par] + s0 * K + prevk;
+        for (int t = 0; t < m.nprev; ++t) myprev[t * kContactBlock] = (int)hp[(int64_t)t * ns].w;
+        hprev = hp;
+        hnew = a.hist64[par ^ 1] + s0 * K + kl;
+        m.p = a.dp_[k];
+        m.v = a.dv_[k];
+        m.w = a.dw_[k];
+        m.agg = (int)m.v.w;
+        m.tol = 0.f;
+        cx = cellc_d(m.p.x, S.inv_cell, nx);
+        cy = cellc_d(m.p.y, S.inv_cell, ny);
+        cz = cellc_d(m.p.z, S.inv_cell, nz);
+        m.F = d3(0, 0, 0);
+        m.T = d3(0, 0, 0);
     } else {
-        const ParamsF prm = {(float)S.kn, (float)S.kt, (float)S.cn, (float)S.ct, (float)S.mu_s,
-                             (float)S.mu_r, (float)S.mu_t, (float)S.w0, (float)S.h};
-        const float4 *hprev = a.hist32[par] + s0 * K + prevk;
-        float4 *hnew = a.hist32[par ^ 1] + s0 * K + kl;
-        for (int t = 0; t < nprev; ++t) myprev[t * kContactBlock] = __float_as_int(hprev[(int64_t)t * ns].w);
-        const float4 me_h = a.sph_[k];
+        prm = {(float)S.kn, (float)S.kt, (float)S.cn, (float)S.ct, (float)S.mu_s,
+               (float)S.mu_r, (float)S.mu_t, (float)S.w0, (float)S.h};
+        const float4 *hp = a.hist32[par] + s0 * K + prevk;
+        for (int t = 0; t < m.nprev; ++t) myprev[t * kContactBlock] = __float_as_int(hp[(int64_t)t * ns].w);
+        hprev = hp;
+        hnew = a.hist32[par ^ 1] + s0 * K + kl;
+        m.p = a.sph_[k];
+        m.l = a.spl_[k];
+        m.v = a.sv_[k];
+        m.w = a.sw_[k];
+        m.agg = __float_as_int(m.v.w);
         const float icell = (float)S.inv_cell;
-        const int cx = cellc_f(me_h.x, icell, nx), cy = cellc_f(me_h.y, icell, ny),
-                  cz = cellc_f(me_h.z, icell, nz);
+        cx = cellc_f(m.p.x, icell, nx);
+        cy = cellc_f(m.p.y, icell, ny);
+        cz = cellc_f(m.p.z, icell, nz);
         // rounding of the hi parts is at most ulp(|p|)/2 per coordinate; every
         // neighbour lies within 2 cells, so one margin serves all candidates
-        const float my_abs = fmaxf(fabsf(me_h.x), fmaxf(fabsf(me_h.y), fabsf(me_h.z)));
-        const float tol = 4.0e-7f * (2.0f * my_abs + 3.0f * (float)S.cell) + 4.0e-6f * me_h.w;
-        const float4 me_l = a.spl_[k], me_v = a.sv_[k], me_w = a.sw_[k];
-        const int my_agg = __float_as_int(me_v.w);
-        float3 F = f3(0, 0, 0), T = f3(0, 0, 0);
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy) {
-                Strip sr;
-                strip_ranges(cstart, ccount, (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx, cx, nx, sr);
+        const float my_abs = fmaxf(fabsf(m.p.x), fmaxf(fabsf(m.p.y), fabsf(m.p.z)));
+        m.tol = 4.0e-7f * (2.0f * my_abs + 3.0f * (float)S.cell) + 4.0e-6f * m.p.w;
+        m.F = f3(0, 0, 0);
+        m.T = f3(0, 0, 0);
+    }
+
+    // pass 1 filters candidates into a per-thread list (traversal order kept);
+    // pass 2 evaluates the listed pairs, so that the lanes of a warp run the
+    // expensive pair evaluation together rather than one hit at a time
+    int *mylist = s_list + threadIdx.x;
+    int nl = 0;
+    auto flush = [&]() {
+        for (int e = 0; e < nl; ++e)
+            process<FP64>(a, s0 + mylist[e * kContactBlock], m, myprev, hprev, hnew, ns, K, prm);
+        nl = 0;
+    };
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int rowbase = (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx;
+            Strip sr;
+            strip_ranges(cstart, ccount, rowbase, cx, nx, sr);
+            if (staged) {
+                const int q = (dz + 1) * s_span + (cy + dy - s_ya);
+                const int base = s_off[q] - s_beg[q];
+                for (int r = 0; r < sr.n; ++r)
+                    for (int t = sr.beg[r]; t < sr.end[r]; ++t)
+                        if (candidate<FP64>(k, s0 + t, st_pos[base + t], st_agg[base + t], m)) {
+                            mylist[nl * kContactBlock] = t;
+                            if (++nl == kHitList) flush();
+                        }
+            } else {
                 for (int r = 0; r < sr.n; ++r)
                     for (int t = sr.beg[r]; t < sr.end[r]; ++t) {
                         const int64_t kk = s0 + t;
-                        const float4 nh = a.sph_[kk];
-                        const float ddx = nh.x - me_h.x, ddy = nh.y - me_h.y, ddz = nh.z - me_h.z;
-                        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                        const float srt = nh.w + me_h.w + tol;
-                        if (r2 > srt * srt || kk == k) continue;
-                        const float4 nv = a.sv_[kk];
-                        if (__float_as_int(nv.w) == my_agg) continue;
-                        const float4 nl = a.spl_[kk], nw = a.sw_[kk];
-                        const int ngid = __float_as_int(nw.w);
-                        int slot = -1;
-                        if (cursor < nprev && myprev[cursor * kContactBlock] == ngid) slot = cursor;
-                        else
-                            for (int h = 0; h < nprev; ++h)
-                                if (myprev[h * kContactBlock] == ngid) { slot = h; break; }
-                        float3 Sprev = f3(0, 0, 0);
-                        if (slot >= 0) {
-                            const float4 sl = hprev[(int64_t)slot * ns];
-                            Sprev = f3(sl.x, sl.y, sl.z);
-                            cursor = slot + 1;
+                        P4 nh;
+                        if constexpr (FP64) nh = a.dp_[kk];
+                        else nh = a.sph_[kk];
+                        if (candidate<FP64>(k, kk, nh, a.sagg[kk], m)) {
+                            mylist[nl * kContactBlock] = t;
+                            if (++nl == kHitList) flush();
                         }
-                        const bool first = hl < ngid;
-                        PairOut<float, float3> o;
-                        const bool hit = first ? pair_mixed(me_h, me_l, me_v, me_w, nh, nl, nv, nw, Sprev, prm, o)
-                                               : pair_mixed(nh, nl, nv, nw, me_h, me_l, me_v, me_w, Sprev, prm, o);
-                        if (!hit) continue;
-                        if (first) {
-                            F = F + o.F;
-                            T = T + cross(o.la * o.n, o.F) + o.M;
-                        } else {
-                            F = F - o.F;
-                            T = T + cross(o.lb * o.n, o.F) - o.M;
-                        }
-                        if (nn < K) hnew[(int64_t)nn * ns] = make_float4(o.S.x, o.S.y, o.S.z, __int_as_float(ngid));
-                        else flags |= DEM_FLAG_SLOTS;
-                        ++nn;
-                        if (o.x > 0.1f * fminf(me_h.w, nh.w)) flags |= DEM_FLAG_OVERLAP;
                     }
             }
-        a.ftc32[2 * k] = make_float4(F.x, F.y, F.z, 0.f);
-        a.ftc32[2 * k + 1] = make_float4(T.x, T.y, T.z, 0.f);
+        }
+    flush();
+    if constexpr (FP64) {
+        a.ftc64[2 * k] = make_dbl4(m.F.x, m.F.y, m.F.z, 0.0);
+        a.ftc64[2 * k + 1] = make_dbl4(m.T.x, m.T.y, m.T.z, 0.0);
+    } else {
+        a.ftc32[2 * k] = make_float4(m.F.x, m.F.y, m.F.z, 0.f);
+        a.ftc32[2 * k + 1] = make_float4(m.T.x, m.T.y, m.T.z, 0.f);
     }
-    hn_new[k] = nn < K ? nn : K;
-    if (flags) atomicOr(&a.pd[p].flags, flags);
+    a.hist_n[par ^ 1][k] = m.nn < K ? m.nn : K;
+    if (m.flags) atomicOr(&a.pd[p].flags, m.flags);
+}
+
+static size_t contact_smem(bool fp64, int K)
+{
+    size_t stage = (fp64 ? sizeof(dbl4) : sizeof(float4)) * kStageCap + sizeof(int) * kStageCap;
+    return stage + sizeof(int) * (size_t)(kHitList + K) * kContactBlock;
+}
+
+cudaError_t contact_setup(bool fp64, int K)
+{
+    int smem = (int)contact_smem(fp64, K);
+    if (fp64) return cudaFuncSetAttribute(k_contact<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return cudaFuncSetAttribute(k_contact<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 void launch_contact(const Arrays &a, const Sizes &z, bool fp64, int K, cudaStream_t st)
 {
     if (z.N == 0) return;
     unsigned nb = (unsigned)((z.N + kContactBlock - 1) / kContactBlock);
-    size_t smem = sizeof(int) * (size_t)K * kContactBlock;
+    size_t smem = contact_smem(fp64, K);
     if (fp64) k_contact<true><<<nb, kContactBlock, smem, st>>>(a, z);
     else k_contact<false><<<nb, kContactBlock, smem, st>>>(a, z);
 }

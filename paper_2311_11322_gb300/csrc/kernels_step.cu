@@ -502,6 +502,7 @@ __global__ void k_gather(Arrays a, Sizes z)
     int al = a.sph_agg[i];
     int64_t g = S.a0 + al;
     a.pos_of_home[a.pd[p].parity ^ 1][i] = (int32_t)(k - S.s0);
+    a.sagg[k] = al;
     if (FP64) {
         const AggRec64 &rec = a.rec64[g];
         const double *b = a.b64 + 3 * i;

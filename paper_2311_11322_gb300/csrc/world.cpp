@@ -61,6 +61,7 @@ struct dem_world {
     int64_t grav_jchunk = 0;          // > 0: fixed j-range length per work item
     double grav_item = 1048576.0;     // else: target interactions per work item
     bool grav_pack = false;           // packed f32x2 pair terms (even grav_ib)
+    bool contact_stage = false;       // stage neighbour rows in shared memory (measured slower)
     int sm_count = 0;
     double cell_factor = 1.0;
     // flags readback
@@ -131,6 +132,7 @@ void build_fields(dem_world *w)
     add((void **)&a.key, C_SPH, 4, false);
     add((void **)&a.rank, C_SPH, 4, false);
     add((void **)&a.sorted, C_SPH, 4, false);
+    add((void **)&a.sagg, C_SPH, 4, false);
     add((void **)&a.fg, C_SPH, 32, true);
     add((void **)&a.hist_n[0], C_SPH, 4, true);
     add((void **)&a.hist_n[1], C_SPH, 4, true);
@@ -350,6 +352,8 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     w->Z.P = (int64_t)w->piles.size();
     w->Z.GI = (int64_t)gp.items.size();
     w->Z.GP = gp.gp;
+    w->Z.K = w->K;
+    w->Z.stage = w->contact_stage ? 1 : 0;
     if (w->sm_count == 0) {
         int dev = 0;
         CU(cudaGetDevice(&dev));
@@ -357,6 +361,7 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     }
     int bps = gravity_blocks_per_sm(w->precision == DEM_FP64, w->grav_block, w->grav_ib, w->grav_pack);
     CU(cudaGetLastError());
+    CU(contact_setup(w->precision == DEM_FP64, w->K));
     w->Z.GB = (int64_t)std::max(1, bps) * w->sm_count;
     if (!ps.empty()) {
         CU(cudaMemcpyAsync(w->A.ps, ps.data(), sizeof(PileStatic) * ps.size(),
@@ -1202,6 +1207,8 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
     } else if (k == "grav_jchunk") {
         if (value < 0) return fail(w, DEM_ERR_ARG, "grav_jchunk must be >= 0");
         w->grav_jchunk = (int64_t)value;
+    } else if (k == "contact_stage") {
+        w->contact_stage = value != 0.0;
     } else if (k == "grav_pack") {
         w->grav_pack = value != 0.0;
     } else if (k == "grav_item") {
@@ -1292,7 +1299,7 @@ size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contact
 {
     if (n_spheres < 0 || n_agg < 0 || max_contacts < 1) return 0;
     bool d = precision == DEM_FP64;
-    size_t sph = 4 + 4 + 24 + 8 + 8 + 4 + 4 + 4 + 32 + 4 + 4;
+    size_t sph = 4 + 4 + 24 + 8 + 8 + 4 + 4 + 4 + 4 + 32 + 4 + 4;
     sph += 8;   // pos_of_home, both parities
     sph += d ? (32 * 3 + 32 + 64) : (16 * 2 + 16 * 4 + 16 + 32);
     size_t sphk = d ? 2 * 32 : 2 * 16;
