@@ -229,9 +229,8 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
  * thread: 1, 2 or 4), "grav_item" (target pair interactions per gravity work
  * item, >= 1024; sets the j-range split), "grav_jchunk" (fixed j-range length
  * per work item, 0 = use grav_item), "grav_pack" (1 = packed f32x2 pair terms
- * when grav_ib is even, 0 = scalar FP32), "contact_stage" (1 = the contact
- * pass stages neighbour cell rows in shared memory where they fit), "cell_factor"
- * (cell edge / (2 x largest radius), >= 1).  Invalidates the captured graph.
+ * when grav_ib is even, 0 = scalar FP32), "cell_factor" (cell edge / (2 x
+ * largest radius), >= 1).  Invalidates the captured graph.
  */
 dem_status dem_set_tuning(dem_world *w, const char *key, double value);
 

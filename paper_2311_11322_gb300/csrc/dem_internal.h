@@ -21,6 +21,7 @@ constexpr int kMaxK = 64;          // largest max_contacts
 constexpr int kScanTile = 2048;    // cells per scan block (256 threads x 8)
 constexpr int kAggChunk = 512;     // aggregates per pile-reduction block
 constexpr int kPartialDoubles = 16;
+constexpr int kHitCap = 24;        // contact candidates listed per sphere (more: searched again)
 
 // Static description of one pile (host-owned; re-uploaded on membership change).
 struct PileStatic {
@@ -82,6 +83,8 @@ struct Arrays {
     float4 *sph_, *spl_, *sv_, *sw_;   // mixed: pos hi (+s hi), pos lo (+s lo), vel (+agg), spin (+gid)
     dbl4 *dp_, *dv_, *dw_;          // fp64: pos (+s), vel (+agg), spin (+gid)
     int32_t *sagg;                  // aggregate (pile-local) of each sorted position
+    int32_t *hits;                  // contact candidates, slot-major per pile like the history
+    int32_t *hitn;                  // number of candidates of each sorted position
     // gravity inputs / outputs
     float4 *gpos32;      // mixed: pos hi (+mass)
     dbl4 *gpos64;     // fp64: pos (+mass)
@@ -125,7 +128,7 @@ struct Sizes {
     int64_t N, A, C, T, CH, P, GI, GP;
     int64_t GB;   // blocks of the persistent gravity grid (0 = one block per item)
     int32_t K;    // history slots per sphere (world-wide)
-    int32_t stage;  // contact pass may stage neighbour rows in shared memory
+    int32_t pad;
 };
 
 // ---- kernel launchers (kernels_*.cu) -------------------------------------

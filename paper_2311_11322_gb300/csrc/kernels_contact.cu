@@ -14,9 +14,15 @@
 // flags; the neighbour order is fixed by the cell ordering, so the pass is
 // deterministic.
 //
-// Memory layout for coalescing: a thread handles the sphere at sorted
-// position k; the three x-adjacent cells of each (dy, dz) row are consecutive
-// in the sorted order, so the 27 neighbour cells are read as 9 index ranges.
+// Two kernels.  k_contact_filter (one thread per sphere in sorted order, few
+// registers, many resident warps) walks the 27 neighbour cells -- the three
+// x-adjacent cells of each (dy, dz) row are consecutive in the sorted order, so
+// they are read as 9 index ranges -- and writes the candidates that pass a
+// bounding test (other aggregate, centres closer than the radii sum plus the
+// FP32 rounding margin) to a per-sphere hit list, in traversal order.
+// k_contact then evaluates the listed pairs; its lanes stay converged because
+// every lane works through a short list of real candidates.  A sphere whose
+// list overflowed searches its cells again inside k_contact.
 // History slots are stored in sorted order (slot-major inside each pile) and
 // read at the position the sphere had in the previous step, which neighbours
 // in the current order mostly share; the previous partners' ids are staged in
@@ -222,9 +228,7 @@ __device__ __forceinline__ void strip_ranges(const int32_t *cstart, const int32_
 }
 
 constexpr int kContactBlock = 128;
-constexpr int kStageCap = 1536;      // staged neighbour spheres per block
-constexpr int kMaxStageRows = 12;
-constexpr int kHitList = 16;         // filter hits buffered per thread before the pair pass
+
 
 template <bool FP64> struct CT;
 template <> struct CT<false> {
@@ -344,75 +348,36 @@ __device__ __forceinline__ void process(const Arrays &a, int64_t kk, Me<FP64> &m
     if (o.x > typename CT<FP64>::T(0.1) * fmin(m.p.w, nh.w)) m.flags |= DEM_FLAG_OVERLAP;
 }
 
+// Pile, sorted-position and cell set-up shared by both kernels.
 template <bool FP64>
-__global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
+__device__ __forceinline__ void own_cell(const PileStatic &S, const typename CT<FP64>::P4 &p, int &cx,
+                                         int &cy, int &cz)
+{
+    if constexpr (FP64) {
+        cx = cellc_d(p.x, S.inv_cell, S.nx);
+        cy = cellc_d(p.y, S.inv_cell, S.ny);
+        cz = cellc_d(p.z, S.inv_cell, S.nz);
+    } else {
+        const float icell = (float)S.inv_cell;
+        cx = cellc_f(p.x, icell, S.nx);
+        cy = cellc_f(p.y, icell, S.ny);
+        cz = cellc_f(p.z, icell, S.nz);
+    }
+}
+
+// Rounding of the hi position parts is at most ulp(|p|)/2 per coordinate and
+// every neighbour lies within 2 cells, so one margin serves all candidates.
+__device__ __forceinline__ float filter_tol(const PileStatic &S, float4 p)
+{
+    const float my_abs = fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z)));
+    return 4.0e-7f * (2.0f * my_abs + 3.0f * (float)S.cell) + 4.0e-6f * p.w;
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(kContactBlock) k_contact_filter(Arrays a, Sizes z)
 {
     typedef typename CT<FP64>::P4 P4;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_off[kMaxStageRows + 1], s_beg[kMaxStageRows];
-    __shared__ int s_ok, s_ya, s_span, s_zc, s_total, s_nq;
-    const int K = z.K;
-    P4 *st_pos = (P4 *)smem_raw;
-    int *st_agg = (int *)(st_pos + kStageCap);
-    int *s_list = st_agg + kStageCap;   // [kHitList][kContactBlock]
-    int *s_prev = s_list + kHitList * kContactBlock;   // [K][kContactBlock]
-
-    // ---- block set-up: can this tile's neighbourhood be staged?
-    const int64_t kfirst = (int64_t)blockIdx.x * kContactBlock;
-    if (threadIdx.x == 0) {
-        s_ok = 0;
-        const int64_t klast = min(kfirst + kContactBlock, z.N) - 1;
-        const int p = a.sph_pile[kfirst];
-        if (z.stage && p == a.sph_pile[klast] && a.enabled[p] != 0 && a.pd[p].failed == 0) {
-            const PileStatic &S = a.ps[p];
-            const int nx = S.nx, ny = S.ny, nz = S.nz;
-            const int rf = a.key[S.s0 + a.sorted[kfirst]] / nx;
-            const int rl = a.key[S.s0 + a.sorted[klast]] / nx;
-            const int yf = rf % ny, zf = rf / ny, yl = rl % ny, zl = rl / ny;
-            int span = 0;
-            if (rf == rl) span = 3;
-            else if (zl == zf && yl == yf + 1) span = 4;
-            if (span) {
-                const int32_t *cs = a.cstart + S.c0, *cc = a.ccount + S.c0;
-                int tot = 0;
-                const int nq = 3 * span;
-                for (int q = 0; q < nq; ++q) {
-                    const int dz = q / span - 1, yy = q % span;
-                    const int row = wrapc(zf + dz, nz) * ny + wrapc(yf - 1 + yy, ny);
-                    const int c0 = row * nx, c1 = c0 + nx - 1;
-                    s_beg[q] = cs[c0];
-                    s_off[q] = tot;
-                    tot += cs[c1] + cc[c1] - cs[c0];
-                }
-                s_off[nq] = tot;
-                if (tot <= kStageCap) {
-                    s_ok = 1;
-                    s_ya = yf - 1;
-                    s_span = span;
-                    s_zc = zf;
-                    s_total = tot;
-                    s_nq = nq;
-                }
-            }
-        }
-    }
-    __syncthreads();
-    const bool staged = s_ok != 0;
-    if (staged) {
-        const PileStatic &S = a.ps[a.sph_pile[kfirst]];
-        const int tot = s_total, nq = s_nq;
-        for (int idx = threadIdx.x; idx < tot; idx += kContactBlock) {
-            int q = 0;
-            while (q + 1 < nq && s_off[q + 1] <= idx) ++q;
-            const int64_t src = S.s0 + s_beg[q] + (idx - s_off[q]);
-            if constexpr (FP64) st_pos[idx] = a.dp_[src];
-            else st_pos[idx] = a.sph_[src];
-            st_agg[idx] = a.sagg[src];
-        }
-    }
-    __syncthreads();
-
-    const int64_t k = kfirst + threadIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * kContactBlock + threadIdx.x;
     if (k >= z.N) return;
     const int p = a.sph_pile[k];
     if (a.enabled[p] == 0 || a.pd[p].failed) return;
@@ -420,6 +385,56 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
     const int64_t s0 = S.s0;
     const int ns = (int)S.ns;
     const int nx = S.nx, ny = S.ny, nz = S.nz;
+    const int kl = (int)(k - s0);
+    Me<FP64> m;
+    if constexpr (FP64) {
+        m.p = a.dp_[k];
+        m.tol = 0.f;
+    } else {
+        m.p = a.sph_[k];
+        m.tol = filter_tol(S, m.p);
+    }
+    m.agg = a.sagg[k];
+    int cx, cy, cz;
+    own_cell<FP64>(S, m.p, cx, cy, cz);
+    const int32_t *cstart = a.cstart + S.c0, *ccount = a.ccount + S.c0;
+    int32_t *hl = a.hits + s0 * kHitCap + kl;
+    int n = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy) {
+            Strip sr;
+            strip_ranges(cstart, ccount, (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx, cx, nx, sr);
+            for (int r = 0; r < sr.n; ++r) {
+#pragma unroll 4
+                for (int t = sr.beg[r]; t < sr.end[r]; ++t) {
+                    const int64_t kk = s0 + t;
+                    P4 nh;
+                    if constexpr (FP64) nh = a.dp_[kk];
+                    else nh = a.sph_[kk];
+                    if (candidate<FP64>(k, kk, nh, a.sagg[kk], m)) {
+                        if (n < kHitCap) hl[(int64_t)n * ns] = t;
+                        ++n;
+                    }
+                }
+            }
+        }
+    a.hitn[k] = n;
+}
+
+template <bool FP64>
+__global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
+{
+    typedef typename CT<FP64>::P4 P4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int K = z.K;
+    int *s_prev = (int *)smem_raw;   // [K][kContactBlock] partner ids of the previous contacts
+    const int64_t k = (int64_t)blockIdx.x * kContactBlock + threadIdx.x;
+    if (k >= z.N) return;
+    const int p = a.sph_pile[k];
+    if (a.enabled[p] == 0 || a.pd[p].failed) return;
+    const PileStatic &S = a.ps[p];
+    const int64_t s0 = S.s0;
+    const int ns = (int)S.ns;
     const int par = a.pd[p].parity;
     const int kl = (int)(k - s0);
     Me<FP64> m;
@@ -429,11 +444,9 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
     m.nn = 0;
     m.cursor = 0;
     m.flags = 0;
-    const int32_t *cstart = a.cstart + S.c0, *ccount = a.ccount + S.c0;
     int *myprev = s_prev + threadIdx.x;
     const void *hprev;
     void *hnew;
-    int cx, cy, cz;
     typename CT<FP64>::Prm prm;
     if constexpr (FP64) {
         prm = {S.kn, S.kt, S.cn, S.ct, S.mu_s, S.mu_r, S.mu_t, S.w0, S.h};
@@ -446,9 +459,6 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
         m.w = a.dw_[k];
         m.agg = (int)m.v.w;
         m.tol = 0.f;
-        cx = cellc_d(m.p.x, S.inv_cell, nx);
-        cy = cellc_d(m.p.y, S.inv_cell, ny);
-        cz = cellc_d(m.p.z, S.inv_cell, nz);
         m.F = d3(0, 0, 0);
         m.T = d3(0, 0, 0);
     } else {
@@ -463,57 +473,36 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
         m.v = a.sv_[k];
         m.w = a.sw_[k];
         m.agg = __float_as_int(m.v.w);
-        const float icell = (float)S.inv_cell;
-        cx = cellc_f(m.p.x, icell, nx);
-        cy = cellc_f(m.p.y, icell, ny);
-        cz = cellc_f(m.p.z, icell, nz);
-        // rounding of the hi parts is at most ulp(|p|)/2 per coordinate; every
-        // neighbour lies within 2 cells, so one margin serves all candidates
-        const float my_abs = fmaxf(fabsf(m.p.x), fmaxf(fabsf(m.p.y), fabsf(m.p.z)));
-        m.tol = 4.0e-7f * (2.0f * my_abs + 3.0f * (float)S.cell) + 4.0e-6f * m.p.w;
+        m.tol = filter_tol(S, m.p);
         m.F = f3(0, 0, 0);
         m.T = f3(0, 0, 0);
     }
-
-    // pass 1 filters candidates into a per-thread list (traversal order kept);
-    // pass 2 evaluates the listed pairs, so that the lanes of a warp run the
-    // expensive pair evaluation together rather than one hit at a time
-    int *mylist = s_list + threadIdx.x;
-    int nl = 0;
-    auto flush = [&]() {
-        for (int e = 0; e < nl; ++e)
-            process<FP64>(a, s0 + mylist[e * kContactBlock], m, myprev, hprev, hnew, ns, K, prm);
-        nl = 0;
-    };
-    for (int dz = -1; dz <= 1; ++dz)
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int rowbase = (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx;
-            Strip sr;
-            strip_ranges(cstart, ccount, rowbase, cx, nx, sr);
-            if (staged) {
-                const int q = (dz + 1) * s_span + (cy + dy - s_ya);
-                const int base = s_off[q] - s_beg[q];
-                for (int r = 0; r < sr.n; ++r)
-                    for (int t = sr.beg[r]; t < sr.end[r]; ++t)
-                        if (candidate<FP64>(k, s0 + t, st_pos[base + t], st_agg[base + t], m)) {
-                            mylist[nl * kContactBlock] = t;
-                            if (++nl == kHitList) flush();
-                        }
-            } else {
+    const int nh = a.hitn[k];
+    if (nh <= kHitCap) {
+        const int32_t *hl = a.hits + s0 * kHitCap + kl;
+        for (int e = 0; e < nh; ++e)
+            process<FP64>(a, s0 + hl[(int64_t)e * ns], m, myprev, hprev, hnew, ns, K, prm);
+    } else {
+        // the hit list overflowed: search the neighbour cells again, in the same order
+        const int nx = S.nx, ny = S.ny, nz = S.nz;
+        int cx, cy, cz;
+        own_cell<FP64>(S, m.p, cx, cy, cz);
+        const int32_t *cstart = a.cstart + S.c0, *ccount = a.ccount + S.c0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy) {
+                Strip sr;
+                strip_ranges(cstart, ccount, (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx, cx, nx, sr);
                 for (int r = 0; r < sr.n; ++r)
                     for (int t = sr.beg[r]; t < sr.end[r]; ++t) {
                         const int64_t kk = s0 + t;
-                        P4 nh;
-                        if constexpr (FP64) nh = a.dp_[kk];
-                        else nh = a.sph_[kk];
-                        if (candidate<FP64>(k, kk, nh, a.sagg[kk], m)) {
-                            mylist[nl * kContactBlock] = t;
-                            if (++nl == kHitList) flush();
-                        }
+                        P4 q;
+                        if constexpr (FP64) q = a.dp_[kk];
+                        else q = a.sph_[kk];
+                        if (candidate<FP64>(k, kk, q, a.sagg[kk], m))
+                            process<FP64>(a, kk, m, myprev, hprev, hnew, ns, K, prm);
                     }
             }
-        }
-    flush();
+    }
     if constexpr (FP64) {
         a.ftc64[2 * k] = make_dbl4(m.F.x, m.F.y, m.F.z, 0.0);
         a.ftc64[2 * k + 1] = make_dbl4(m.T.x, m.T.y, m.T.z, 0.0);
@@ -525,15 +514,11 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
     if (m.flags) atomicOr(&a.pd[p].flags, m.flags);
 }
 
-static size_t contact_smem(bool fp64, int K)
-{
-    size_t stage = (fp64 ? sizeof(dbl4) : sizeof(float4)) * kStageCap + sizeof(int) * kStageCap;
-    return stage + sizeof(int) * (size_t)(kHitList + K) * kContactBlock;
-}
+static size_t contact_smem(int K) { return sizeof(int) * (size_t)K * kContactBlock; }
 
 cudaError_t contact_setup(bool fp64, int K)
 {
-    int smem = (int)contact_smem(fp64, K);
+    int smem = (int)contact_smem(K);
     if (fp64) return cudaFuncSetAttribute(k_contact<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return cudaFuncSetAttribute(k_contact<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
@@ -542,9 +527,14 @@ void launch_contact(const Arrays &a, const Sizes &z, bool fp64, int K, cudaStrea
 {
     if (z.N == 0) return;
     unsigned nb = (unsigned)((z.N + kContactBlock - 1) / kContactBlock);
-    size_t smem = contact_smem(fp64, K);
-    if (fp64) k_contact<true><<<nb, kContactBlock, smem, st>>>(a, z);
-    else k_contact<false><<<nb, kContactBlock, smem, st>>>(a, z);
+    size_t smem = contact_smem(K);
+    if (fp64) {
+        k_contact_filter<true><<<nb, kContactBlock, 0, st>>>(a, z);
+        k_contact<true><<<nb, kContactBlock, smem, st>>>(a, z);
+    } else {
+        k_contact_filter<false><<<nb, kContactBlock, 0, st>>>(a, z);
+        k_contact<false><<<nb, kContactBlock, smem, st>>>(a, z);
+    }
 }
 
 }  // namespace dem

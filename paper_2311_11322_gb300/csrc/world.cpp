@@ -16,7 +16,7 @@ using namespace dem;
 
 namespace {
 
-enum Cls { C_SPH, C_SPHK, C_AGG, C_CELL, C_TILE, C_CHUNK, C_PILE, C_GITEM, C_GPART, C_NCLS };
+enum Cls { C_SPH, C_SPHK, C_SPHL, C_AGG, C_CELL, C_TILE, C_CHUNK, C_PILE, C_GITEM, C_GPART, C_NCLS };
 
 struct Field {
     void **ptr;
@@ -61,7 +61,6 @@ struct dem_world {
     int64_t grav_jchunk = 0;          // > 0: fixed j-range length per work item
     double grav_item = 1048576.0;     // else: target interactions per work item
     bool grav_pack = false;           // packed f32x2 pair terms (even grav_ib)
-    bool contact_stage = false;       // stage neighbour rows in shared memory (measured slower)
     int sm_count = 0;
     double cell_factor = 1.0;
     // flags readback
@@ -133,6 +132,8 @@ void build_fields(dem_world *w)
     add((void **)&a.rank, C_SPH, 4, false);
     add((void **)&a.sorted, C_SPH, 4, false);
     add((void **)&a.sagg, C_SPH, 4, false);
+    add((void **)&a.hits, C_SPHL, 4, false);
+    add((void **)&a.hitn, C_SPH, 4, false);
     add((void **)&a.fg, C_SPH, 32, true);
     add((void **)&a.hist_n[0], C_SPH, 4, true);
     add((void **)&a.hist_n[1], C_SPH, 4, true);
@@ -194,6 +195,7 @@ int64_t pile_count(const dem_world *w, const PileHost &q, Cls c)
     switch (c) {
     case C_SPH: return q.ns;
     case C_SPHK: return q.ns * w->K;
+    case C_SPHL: return q.ns * kHitCap;
     case C_AGG: return q.na;
     case C_CELL: return q.nc;
     case C_TILE: return q.nt;
@@ -353,7 +355,6 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     w->Z.GI = (int64_t)gp.items.size();
     w->Z.GP = gp.gp;
     w->Z.K = w->K;
-    w->Z.stage = w->contact_stage ? 1 : 0;
     if (w->sm_count == 0) {
         int dev = 0;
         CU(cudaGetDevice(&dev));
@@ -1207,8 +1208,6 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
     } else if (k == "grav_jchunk") {
         if (value < 0) return fail(w, DEM_ERR_ARG, "grav_jchunk must be >= 0");
         w->grav_jchunk = (int64_t)value;
-    } else if (k == "contact_stage") {
-        w->contact_stage = value != 0.0;
     } else if (k == "grav_pack") {
         w->grav_pack = value != 0.0;
     } else if (k == "grav_item") {
@@ -1299,7 +1298,7 @@ size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contact
 {
     if (n_spheres < 0 || n_agg < 0 || max_contacts < 1) return 0;
     bool d = precision == DEM_FP64;
-    size_t sph = 4 + 4 + 24 + 8 + 8 + 4 + 4 + 4 + 4 + 32 + 4 + 4;
+    size_t sph = 4 + 4 + 24 + 8 + 8 + 4 + 4 + 4 + 4 + 4 + 32 + 4 + 4 + 4 * kHitCap;
     sph += 8;   // pos_of_home, both parities
     sph += d ? (32 * 3 + 32 + 64) : (16 * 2 + 16 * 4 + 16 + 32);
     size_t sphk = d ? 2 * 32 : 2 * 16;
