@@ -230,6 +230,8 @@ __device__ __forceinline__ void strip_ranges(const int32_t *cstart, const int32_
 constexpr int kContactBlock = 128;
 
 
+constexpr int kSlotStage = 16;       // previous slots copied to shared memory (mixed)
+
 template <bool FP64> struct CT;
 template <> struct CT<false> {
     typedef float T;
@@ -251,6 +253,7 @@ struct Me {
     float4 l;                        // mixed: position lo (+radius lo)
     int agg, hl, nprev, nn, cursor, flags;
     float tol;                       // mixed: pre-filter margin
+    const float4 *sslot;             // mixed: this thread's previous slots in shared memory
     typename CT<FP64>::V F, T;
 };
 
@@ -306,7 +309,8 @@ __device__ __forceinline__ void process(const Arrays &a, int64_t kk, Me<FP64> &m
             const dbl4 sl = ((const dbl4 *)hprev_v)[(int64_t)slot * ns];
             Sprev = d3(sl.x, sl.y, sl.z);
         } else {
-            const float4 sl = ((const float4 *)hprev_v)[(int64_t)slot * ns];
+            const float4 sl = slot < kSlotStage ? m.sslot[slot * kContactBlock]
+                                                : ((const float4 *)hprev_v)[(int64_t)slot * ns];
             Sprev = f3(sl.x, sl.y, sl.z);
         }
         m.cursor = slot + 1;
@@ -427,7 +431,11 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
     typedef typename CT<FP64>::P4 P4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int K = z.K;
-    int *s_prev = (int *)smem_raw;   // [K][kContactBlock] partner ids of the previous contacts
+    // shared memory: [S of the previous slots (mixed), kSlotStage x block]
+    // [hit list, kHitCap x block] [partner ids of the previous slots, K x block]
+    float4 *s_slot = (float4 *)smem_raw;
+    int *s_hit = (int *)(s_slot + (FP64 ? 0 : kSlotStage * kContactBlock));
+    int *s_prev = s_hit + kHitCap * kContactBlock;
     const int64_t k = (int64_t)blockIdx.x * kContactBlock + threadIdx.x;
     if (k >= z.N) return;
     const int p = a.sph_pile[k];
@@ -465,7 +473,13 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
         prm = {(float)S.kn, (float)S.kt, (float)S.cn, (float)S.ct, (float)S.mu_s,
                (float)S.mu_r, (float)S.mu_t, (float)S.w0, (float)S.h};
         const float4 *hp = a.hist32[par] + s0 * K + prevk;
-        for (int t = 0; t < m.nprev; ++t) myprev[t * kContactBlock] = __float_as_int(hp[(int64_t)t * ns].w);
+        float4 *myslot = s_slot + threadIdx.x;
+        for (int t = 0; t < m.nprev; ++t) {
+            const float4 e = hp[(int64_t)t * ns];
+            if (t < kSlotStage) myslot[t * kContactBlock] = e;
+            myprev[t * kContactBlock] = __float_as_int(e.w);
+        }
+        m.sslot = myslot;
         hprev = hp;
         hnew = a.hist32[par ^ 1] + s0 * K + kl;
         m.p = a.sph_[k];
@@ -479,9 +493,12 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
     }
     const int nh = a.hitn[k];
     if (nh <= kHitCap) {
+        // all hit indices first (independent loads), then the pairs
         const int32_t *hl = a.hits + s0 * kHitCap + kl;
+        int *myhit = s_hit + threadIdx.x;
+        for (int e = 0; e < nh; ++e) myhit[e * kContactBlock] = hl[(int64_t)e * ns];
         for (int e = 0; e < nh; ++e)
-            process<FP64>(a, s0 + hl[(int64_t)e * ns], m, myprev, hprev, hnew, ns, K, prm);
+            process<FP64>(a, s0 + myhit[e * kContactBlock], m, myprev, hprev, hnew, ns, K, prm);
     } else {
         // the hit list overflowed: search the neighbour cells again, in the same order
         const int nx = S.nx, ny = S.ny, nz = S.nz;
@@ -514,11 +531,15 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
     if (m.flags) atomicOr(&a.pd[p].flags, m.flags);
 }
 
-static size_t contact_smem(int K) { return sizeof(int) * (size_t)K * kContactBlock; }
+static size_t contact_smem(bool fp64, int K)
+{
+    return sizeof(int) * (size_t)(K + kHitCap) * kContactBlock +
+           (fp64 ? 0 : sizeof(float4) * (size_t)kSlotStage * kContactBlock);
+}
 
 cudaError_t contact_setup(bool fp64, int K)
 {
-    int smem = (int)contact_smem(K);
+    int smem = (int)contact_smem(fp64, K);
     if (fp64) return cudaFuncSetAttribute(k_contact<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return cudaFuncSetAttribute(k_contact<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
@@ -527,7 +548,7 @@ void launch_contact(const Arrays &a, const Sizes &z, bool fp64, int K, cudaStrea
 {
     if (z.N == 0) return;
     unsigned nb = (unsigned)((z.N + kContactBlock - 1) / kContactBlock);
-    size_t smem = contact_smem(K);
+    size_t smem = contact_smem(fp64, K);
     if (fp64) {
         k_contact_filter<true><<<nb, kContactBlock, 0, st>>>(a, z);
         k_contact<true><<<nb, kContactBlock, smem, st>>>(a, z);
