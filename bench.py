@@ -21,7 +21,9 @@ value is all spheres x steps / the slowest rank's time.
 
 One JSON line on rank 0.  Extra keys: fp64_path (the all-FP64 GPU path on
 the same workload), roofline_contact (the contact pass on a 1M-sphere dense
-lattice, HBM-bound), e2e (through the public API with host buffers).
+lattice), batched (256 piles in one graph launch vs one pile at a time),
+serving (p50/p99 time-to-finish of a served Poisson trace), e2e (through the
+public API with host buffers).
 """
 from __future__ import annotations
 
@@ -60,6 +62,8 @@ def parse():
     ap.add_argument("--no-contact", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--part", default="all", choices=["all", "contact"],
                     help="contact: only the contact-pass roofline on the 1M-sphere lattice")
     ap.add_argument("--contact-n", type=int, default=1_048_576)
@@ -224,6 +228,50 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3):
             "1,048,576 spheres, overlaps 0.5% R, gravity off"}
 
 
+def run_batched(dem, W, steps=5, n_piles=256):
+    """256 independent piles of tetrahedra (sizes lognormal in [500, 20000]):
+    all stepped by one graph launch per step after autotuning, against looping
+    the plain path one pile at a time (each pile alone in its own world)."""
+    piles = W.config4(0, n_piles=n_piles)
+    n_tot = sum(ic.n_sph for ic, _ in piles)
+    with dem.World() as w:
+        for ic, p in piles:
+            w.add_pile(ic, p)
+        best = w.autotune(2)
+        for _ in range(2):
+            w.step_timed()
+        ms = [w.step_timed()[0] for _ in range(steps)]
+    t_batch = sum(ms) / 1e3 / steps
+    t_loop = 0.0
+    for ic, p in piles:
+        with dem.World() as w:
+            w.add_pile(ic, p)
+            w.step_timed()
+            t_loop += statistics.median([w.step_timed()[0] for _ in range(3)]) / 1e3
+    return {"value": n_tot / t_batch, "unit": UNIT, "ms_per_step": 1e3 * t_batch,
+            "n_piles": n_piles, "n_spheres": n_tot, "autotune_best_ms": best,
+            "loop_one_pile_at_a_time": {"value": n_tot / t_loop, "ms_per_step": 1e3 * t_loop},
+            "batched_over_loop": t_loop / t_batch,
+            "workload": "256 piles of tetrahedra, sizes lognormal median 3,000 in [500, 20,000], "
+                        "each on a jittered lattice in a ball, mixed precision"}
+
+
+def run_serving(dem, W, n_req=24, steps=2000, n_hi=20000):
+    """Poisson trace (4 arrivals/s) of tidal-flyby piles, sizes log-uniform in
+    [1,000, n_hi] spheres, `steps` steps each, served by continuous batching."""
+    from paper_2311_11322_gb300 import serve
+    trace = W.config5_trace(0, n_arrivals=n_req, rate=4.0, n_hi=n_hi, steps=steps)
+    reqs = serve.trace_requests(trace, W.config5_pile)
+    with dem.World() as w:
+        srv = serve.Server(w, dem.dem_footprint_bytes, budget_bytes=64 << 30, max_piles=64,
+                           chunk=250)
+        st = srv.run(reqs)
+    st.update({"trace": "%d Poisson arrivals at 4/s, sizes log-uniform [1000, %d] spheres, %d "
+                        "steps each (reduced from 20,000 to keep the run short), tidal flyby "
+                        "of an Earth-mass planet" % (n_req, n_hi, steps)})
+    return st
+
+
 def run_e2e(dem, W, ic, p, steps):
     """Through the public API with pinned host buffers: add the pile (host->device
     copy of the initial conditions), then per step dem_step + read the COMs back."""
@@ -352,6 +400,10 @@ def run_ours(args):
         out["fp64_path"]["mixed_over_fp64"] = value / ws / out["fp64_path"]["value"]
     if rank == 0 and not args.no_contact:
         out["roofline_contact"] = run_contact_roofline(dem, W, hbm_peak)
+    if rank == 0 and not args.no_batched:
+        out["batched"] = run_batched(dem, W)
+    if rank == 0 and not args.no_serving:
+        out["serving"] = run_serving(dem, W)
     if not args.no_e2e:
         e = run_e2e(dem, W, ic, p, steps=args.steps)
         e_t = max_over_ranks(ic.n_sph * args.steps / e["value"], ws, device="cuda")

@@ -235,9 +235,11 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
 dem_status dem_set_tuning(dem_world *w, const char *key, double value);
 
 /*
- * Time a few candidate gravity shapes and cell factors on the current piles
- * (running `trial_steps` real steps per candidate, so the state advances) and
- * keep the fastest.  best_ms_out (may be NULL) receives its step time.
+ * Autotuner: time the candidate gravity shapes (block 64/128/256, 1/2/4
+ * i-spheres per thread, scalar or packed, three work-item sizes) and then
+ * cell factors 1, 1.25, 1.5, 2 on the current piles, running `trial_steps`
+ * real steps per candidate (so the state advances), and keep the fastest.
+ * best_ms_out (may be NULL) receives its step time.
  */
 dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out);
 

@@ -114,7 +114,8 @@ struct Arrays {
     int32_t *chunk_pile;           // [chunks] pile slot of each chunk
     // gravity work list and j-chunk partial sums
     int4 *gitems;                  // (pile, i0 local, j0 local, j1 local)
-    dbl4 *gpart;                // partial sums [slot] (scratch)
+    void *gpart;                   // partial sum of one j-range per sphere (scratch):
+                                   // float4 in the mixed path, dbl4 in the FP64 path
     int64_t *gpart_base;           // per pile: first slot in gpart (or -1 = direct)
     int32_t *gnchunk;              // per pile: number of j-chunks
     int32_t *gcounter;             // [0]: next work item of the persistent gravity grid

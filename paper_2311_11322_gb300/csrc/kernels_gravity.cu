@@ -14,8 +14,9 @@
 // or two tiles that overlap it take the masked inner loop.
 // Mixed: FP32 pair terms, FP32 partial sums flushed into FP64 every kFlush
 // j-spheres.  FP64: double throughout.
-// A pile with several j-ranges writes one FP64 partial per (range, sphere)
-// and k_grav_combine adds them in range order (deterministic).
+// A pile with several j-ranges writes one partial per (range, sphere), the
+// range's FP64 sum rounded to FP32 (one more rounding of a sum of ~2,000
+// terms), and k_grav_combine adds them in FP64 in range order (deterministic).
 #include "dem_internal.h"
 #include "devmath.cuh"
 
@@ -159,7 +160,7 @@ __device__ __forceinline__ void gravity32_item(const Arrays &a, const int4 it, f
             a.fg[s0 + il] = make_dbl4(gm * sx, gm * sy, gm * sz, 0.0);
         } else {
             int64_t slot = a.gpart_base[p] + (int64_t)(j0 / ((ns + nch - 1) / nch)) * ns + il;
-            a.gpart[slot] = make_dbl4(sx, sy, sz, 0.0);
+            ((float4 *)a.gpart)[slot] = make_float4((float)sx, (float)sy, (float)sz, 0.f);
         }
     }
 }
@@ -301,7 +302,7 @@ __device__ __forceinline__ void gravity32p_item(const Arrays &a, const int4 it, 
                 a.fg[s0 + il] = make_dbl4(gm * sx, gm * sy, gm * sz, 0.0);
             } else {
                 int64_t slot = a.gpart_base[p] + (int64_t)(j0 / ((ns + nch - 1) / nch)) * ns + il;
-                a.gpart[slot] = make_dbl4(sx, sy, sz, 0.0);
+                ((float4 *)a.gpart)[slot] = make_float4((float)sx, (float)sy, (float)sz, 0.f);
             }
         }
 }
@@ -417,12 +418,13 @@ __global__ void __launch_bounds__(BS) k_gravity64(Arrays a, Sizes z)
             a.fg[s0 + il] = make_dbl4(gm * ax[k], gm * ay[k], gm * az[k], 0.0);
         } else {
             int64_t slot = a.gpart_base[p] + (int64_t)(j0 / ((ns + nch - 1) / nch)) * ns + il;
-            a.gpart[slot] = make_dbl4(ax[k], ay[k], az[k], 0.0);
+            ((dbl4 *)a.gpart)[slot] = make_dbl4(ax[k], ay[k], az[k], 0.0);
         }
     }
 }
 
 // Sum the j-range partials of piles that were split, in range order.
+template <bool FP64>
 __global__ void k_grav_combine(Arrays a, Sizes z)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -435,8 +437,14 @@ __global__ void k_grav_combine(Arrays a, Sizes z)
     int64_t il = i - S.s0;
     double sx = 0, sy = 0, sz = 0;
     for (int c = 0; c < nch; ++c) {
-        dbl4 v = a.gpart[a.gpart_base[p] + (int64_t)c * S.ns + il];
-        sx += v.x; sy += v.y; sz += v.z;
+        const int64_t slot = a.gpart_base[p] + (int64_t)c * S.ns + il;
+        if (FP64) {
+            const dbl4 v = ((const dbl4 *)a.gpart)[slot];
+            sx += v.x; sy += v.y; sz += v.z;
+        } else {
+            const float4 v = ((const float4 *)a.gpart)[slot];
+            sx += v.x; sy += v.y; sz += v.z;
+        }
     }
     double gm = S.G * a.m64[i];
     a.fg[i] = make_dbl4(gm * sx, gm * sy, gm * sz, 0.0);
@@ -498,7 +506,10 @@ void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int i
     else if (block == 256 && ib == 1) launch_g<256, 1>(a, z, fp64, pack, st);
     else if (block == 256 && ib == 2) launch_g<256, 2>(a, z, fp64, pack, st);
     else launch_g<256, 4>(a, z, fp64, pack, st);
-    if (z.GP > 0) k_grav_combine<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+    if (z.GP > 0) {
+        if (fp64) k_grav_combine<true><<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+        else k_grav_combine<false><<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+    }
 }
 
 }  // namespace dem

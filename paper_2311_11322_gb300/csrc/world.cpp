@@ -186,7 +186,7 @@ void build_fields(dem_world *w)
     add((void **)&a.gnchunk, C_PILE, 4, false);
     add((void **)&a.gcounter, C_PILE, 4, false);
     add((void **)&a.gitems, C_GITEM, 16, false);
-    add((void **)&a.gpart, C_GPART, 32, false);
+    add((void **)&a.gpart, C_GPART, d ? 32 : 16, false);
 }
 
 // Elements of class c that pile q occupies (and its per-element multiplier).
@@ -1290,6 +1290,31 @@ dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
     cudaEventDestroy(e1);
     w->grav_block = bc.blk; w->grav_ib = bc.ib; w->grav_item = bc.item; w->grav_pack = bc.pack;
     w->graph_valid = false;
+    // then the cell edge (contact search), with the chosen gravity shape
+    double bf = w->cell_factor;
+    for (double f : {1.0, 1.25, 1.5, 2.0}) {
+        dem_status s = dem_set_tuning(w, "cell_factor", f);
+        if (s != DEM_OK) return s;
+        s = prepare(w);
+        if (s != DEM_OK) return s;
+        s = set_enabled(w, nullptr, 0);
+        if (s != DEM_OK) return s;
+        cudaEvent_t f0, f1;
+        CU(cudaEventCreate(&f0));
+        CU(cudaEventCreate(&f1));
+        CU(cudaGraphLaunch(w->exec, w->stream));
+        CU(cudaEventRecord(f0, w->stream));
+        for (int t = 0; t < trial_steps; ++t) CU(cudaGraphLaunch(w->exec, w->stream));
+        CU(cudaEventRecord(f1, w->stream));
+        CU(cudaEventSynchronize(f1));
+        float ms;
+        CU(cudaEventElapsedTime(&ms, f0, f1));
+        cudaEventDestroy(f0);
+        cudaEventDestroy(f1);
+        if (ms / trial_steps < best) { best = ms / trial_steps; bf = f; }
+    }
+    dem_status s2 = dem_set_tuning(w, "cell_factor", bf);
+    if (s2 != DEM_OK) return s2;
     if (best_ms_out) *best_ms_out = best;
     return DEM_OK;
 }

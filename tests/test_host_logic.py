@@ -1,0 +1,194 @@
+"""Host-side logic on CPU: the serving loop against a fake engine, pile
+sharding across ranks (also under a 2-rank gloo group), workload generators."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2311_11322_gb300 import serve, shard
+from paper_2311_11322_gb300 import workloads as W
+
+
+class FakeWorld:
+    """Stand-in engine with the World interface: piles advance a counter."""
+
+    def __init__(self, fail_pile_after=None):
+        self.piles = {}
+        self.next = 0
+        self.log = []
+        self.fail_after = fail_pile_after or {}
+
+    def add_pile(self, ic, p):
+        pid = self.next
+        self.next += 1
+        self.piles[pid] = {"n": len(ic.radius), "steps": 0}
+        self.log.append(("add", pid))
+        return pid
+
+    def step(self, n, piles=None, check=True):
+        for pid, st in self.piles.items():
+            st["steps"] += n
+        self.log.append(("step", n, tuple(sorted(self.piles))))
+        return 0
+
+    def sync(self, check=True):
+        return 0
+
+    def flags(self, pid):
+        lim = self.fail_after.get(pid)
+        return 2 if lim is not None and self.piles[pid]["steps"] >= lim else 0
+
+    def read(self, pid, field):
+        return np.full(3, float(self.piles[pid]["steps"]))
+
+    def remove(self, pid):
+        del self.piles[pid]
+        self.log.append(("remove", pid))
+
+
+class VirtualClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += dt
+
+
+def fake_footprint(n, a, k, prec):
+    return 1000 * n
+
+
+def req(rid, n, steps, t):
+    ic = W.PileIC(counts=np.ones(n, np.int32), pos=np.zeros((n, 3)), radius=np.ones(n),
+                  density=np.ones(n))
+    return serve.Request(rid=rid, ic=ic, params=W.Params(), steps=steps, t_arrival=t)
+
+
+def test_server_admits_by_budget_and_slots_and_finishes_all():
+    clk = VirtualClock()
+    w = FakeWorld()
+    srv = serve.Server(w, fake_footprint, budget_bytes=1000 * 250, max_piles=2, chunk=50,
+                       clock=clk, sleep=clk.sleep)
+    reqs = [req(0, 100, 120, 0.0), req(1, 100, 60, 0.0), req(2, 100, 30, 0.0), req(3, 200, 10, 5.0)]
+    st = srv.run(reqs)
+    assert st["completed"] == 4 and st["failed"] == 0
+    # never more than 2 piles, never more than the budget
+    live = set()
+    for e in w.log:
+        if e[0] == "add":
+            live.add(e[1])
+            assert len(live) <= 2
+        elif e[0] == "remove":
+            live.discard(e[1])
+    # each request ran exactly its number of steps
+    for r in srv.done:
+        assert r.result["COM"][0] == r.steps
+    # the third request waited for a slot; the 200-sphere one waited for memory
+    r2 = [r for r in srv.done if r.rid == 2][0]
+    assert r2.t_admit is not None
+    steps_taken = [e for e in w.log if e[0] == "step"]
+    assert steps_taken[0][1] == 50          # chunk-limited
+    assert st["p50_time_to_finish_s"] is not None
+
+
+def test_server_rejects_oversize_and_retires_failed_piles():
+    clk = VirtualClock()
+    w = FakeWorld(fail_pile_after={0: 20})
+    srv = serve.Server(w, fake_footprint, budget_bytes=1000 * 150, max_piles=4, chunk=10,
+                       clock=clk, sleep=clk.sleep)
+    reqs = [req(0, 100, 100, 0.0), req(1, 500, 10, 0.0), req(2, 40, 30, 0.0)]
+    st = srv.run(reqs)
+    status = {r.rid: r.status for r in srv.done}
+    assert status == {0: "failed", 1: "failed", 2: "done"}
+    assert "budget" in [r for r in srv.done if r.rid == 1][0].result["error"]
+    assert st["completed"] == 1
+
+
+def test_server_overlaps_late_arrivals():
+    """A request arriving while another runs is admitted at the next round
+    boundary and runs alongside it."""
+    clk = VirtualClock()
+
+    class TimedWorld(FakeWorld):
+        def step(self, n, piles=None, check=True):
+            clk.t += 0.01 * n
+            return super().step(n, piles, check)
+
+    w = TimedWorld()
+    srv = serve.Server(w, fake_footprint, budget_bytes=10 ** 9, max_piles=8, chunk=10,
+                       clock=clk, sleep=clk.sleep)
+    srv.run([req(0, 10, 200, 0.0), req(1, 10, 50, 0.35)])
+    overlap = [e for e in w.log if e[0] == "step" and len(e[2]) == 2]
+    assert overlap, "the late request never ran together with the first"
+
+
+def test_shard_is_complete_disjoint_and_balanced():
+    rng = np.random.default_rng(0)
+    sizes = W.pile_sizes_config4(rng, 256)
+    for ws in (1, 2, 4, 8):
+        sh = shard.shard_piles(sizes, ws)
+        flat = sorted(k for s in sh for k in s)
+        assert flat == list(range(len(sizes)))
+        assert shard.imbalance(sizes, sh) < 1.1
+    assert shard.shard_piles(sizes, 4) == shard.shard_piles(sizes, 4)
+
+
+def _gloo_worker(rank, ws, port, q):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    rng = np.random.default_rng(1)
+    sizes = W.pile_sizes_config4(rng, 64)
+    mine = shard.shard_piles(sizes, ws)[rank]
+    # every rank derives the same placement: gather and compare
+    objs = [None] * ws
+    dist.all_gather_object(objs, mine)
+    # max over ranks of a per-rank time, as bench.py reduces it
+    t = torch.tensor([float(sum(sizes[k] ** 2 for k in mine))], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    q.put((rank, objs, float(t.item())))
+    dist.destroy_process_group()
+
+
+def test_shard_under_two_rank_gloo_group():
+    import multiprocessing as mp
+    torch = pytest.importorskip("torch")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + (os.getpid() % 2000)
+    ps = [ctx.Process(target=_gloo_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(2)]
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, objs0, t0), (r1, objs1, t1) = sorted(out)
+    assert objs0 == objs1
+    assert sorted(objs0[0] + objs0[1]) == list(range(64))
+    assert t0 == t1 and t0 > 0
+
+
+def test_workloads_are_seeded_and_consistent():
+    a, pa = W.config1(3)
+    b, pb = W.config1(3)
+    assert np.array_equal(a.pos, b.pos) and pa == pb
+    assert a.n_sph == 1000 and a.n_agg == 250
+    ic, p = W.config2(0, n_spheres=3001, ball=300.0)
+    assert ic.n_sph == 3001
+    # touching spheres inside each aggregate
+    first = np.concatenate([[0], np.cumsum(ic.counts)[:-1]])
+    for a_, c in zip(first[:50], ic.counts[:50]):
+        if c >= 2:
+            d = np.linalg.norm(ic.pos[a_] - ic.pos[a_ + 1])
+            assert d == pytest.approx(2 * ic.radius[a_], rel=1e-12) or c == 4
+    dl, _ = W.dense_lattice(n_spheres=4000, seed=1)
+    assert dl.n_sph == 4000
+    tr = W.config5_trace(0, n_arrivals=10)
+    assert all(1000 <= t["n_spheres"] <= 100000 for t in tr)
+    assert all(tr[k]["t_arrival"] < tr[k + 1]["t_arrival"] for k in range(9))
