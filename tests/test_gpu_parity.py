@@ -366,3 +366,12 @@ def test_dense_lattice_resynced_steps_mixed(dem, oracle):
         pid = w.add_pile(ic, p)
         worst = resynced_steps(w, pid, pile, 20, TOL[1], p.max_contacts)
         assert worst["contacts"] > 3000
+
+
+def test_config3_full_size_sampled(dem, oracle):
+    """200,000-sphere spin-up pile (2-8-sphere clusters in a 3:2:1.5 ellipsoid,
+    YORP increment on), mixed path: first-step forces on 100 sampled aggregates."""
+    ic, p = W.config3(0)
+    assert ic.n_sph == 200_000
+    es, ea, et, _ = sampled_check(dem, oracle, ic, p, 100, TOL[1])
+    assert es <= TOL[1] and ea <= TOL[1] and et <= TOL[1]
