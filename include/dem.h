@@ -99,7 +99,9 @@ enum dem_field {
     DEM_FIELD_MASS = 19,           /* A      aggregate mass (Eq. agg_mass) */
     DEM_FIELD_BODY_OFFSETS = 20,   /* N x 3  body-frame offsets b_i (never rewritten) */
     DEM_FIELD_OMEGA_BODY = 21,     /* A x 3  spin, body frame */
-    DEM_FIELD_INFO = 22,           /* 16     n_agg, n_sph, steps, flags, nx, ny, nz, cell, ... */
+    DEM_FIELD_INFO = 22,           /* 20     n_agg, n_sph, steps, flags, nx, ny, nz, cell, K,
+                                              precision, frame origin[3], failed, parity,
+                                              M_total, rebuilds, skin, rebuild next step, 0 */
     DEM_FIELD_FRAME = 23,          /* 6      origin and velocity of the pile frame */
     DEM_FIELD_TORQUE_STORED = 24   /* A x 3  stored N_A used by the next step's first half kick */
 };
@@ -230,7 +232,15 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
  * item, >= 1024; sets the j-range split), "grav_jchunk" (fixed j-range length
  * per work item, 0 = use grav_item), "grav_pack" (1 = packed f32x2 pair terms
  * when grav_ib is even, 0 = scalar FP32), "cell_factor" (cell edge / (2 x
- * largest radius), >= 1).  Invalidates the captured graph.
+ * largest radius), >= 1), "skin" (neighbour-list skin as a fraction of the
+ * pile's largest radius, in [0, 4], default 0.1; 0 = search contacts afresh
+ * every step).  With a skin the cell list and the per-sphere candidate lists
+ * are rebuilt only when some aggregate may have moved more than half the skin
+ * relative to the pile frame since the last rebuild (and after any state
+ * write or layout change).  Neither knob changes results: contacts are summed
+ * in partner order, so trajectories are bitwise the same for every cell size
+ * and skin.  Changing cell_factor or skin re-grids every pile.  Invalidates
+ * the captured graph.
  */
 dem_status dem_set_tuning(dem_world *w, const char *key, double value);
 

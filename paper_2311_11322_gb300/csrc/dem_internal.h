@@ -32,6 +32,7 @@ struct PileStatic {
     int64_t t0, nt;        // scan-tile range
     int32_t nx, ny, nz, K; // wrapped grid dims (>= 3 each), history slots
     double cell, inv_cell; // cell edge and its inverse
+    double skin;           // neighbour-list skin (>= 0; 0 = search every step)
     double G, h, kn, kt, cn, ct, mu_s, mu_r, mu_t, w0, eps2;
     double ext_mass, M_total;
     double spin_inc[3];
@@ -46,7 +47,9 @@ struct PileDyn {
     int32_t flags;            // DEM_FLAG_* bits
     int32_t parity;           // history buffer holding the previous contacts
     int32_t failed;           // frozen after a fatal flag
-    int32_t pad;
+    int32_t rebuild;          // this step rebuilds the cell list and hit lists
+    int32_t hit_overflow;     // a hit list overflowed: rebuild again next step
+    int32_t rebuilds;         // number of rebuilds so far
 };
 
 // Per-aggregate quantities the sphere kernels need, mixed precision.
@@ -107,6 +110,10 @@ struct Arrays {
     AggRecMixed *rec32;
     AggRec64 *rec64;
     double *out;                   // [A][18]: FA_c NA_c FA_g NA_g FA_e NA_e
+    // neighbour-list reference per aggregate: position relative to the
+    // extrapolated pile frame and orientation at the last rebuild, and the
+    // largest member offset |b| (fixed): [A][8] = c_ref[3], q_ref[4], bmax
+    double *aref;
     // cells
     int32_t *ccount, *cstart, *tile_sum;
     // pile reductions
@@ -148,5 +155,6 @@ int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack);
 void launch_agg_end(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
 void launch_pile_end(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_fill_ids(const Arrays &a, const Sizes &z, cudaStream_t st);
+void launch_force_rebuild(const Arrays &a, const Sizes &z, int slot, cudaStream_t st);
 
 }  // namespace dem

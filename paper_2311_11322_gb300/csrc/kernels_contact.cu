@@ -19,17 +19,24 @@
 // x-adjacent cells of each (dy, dz) row are consecutive in the sorted order, so
 // they are read as 9 index ranges -- and writes the candidates that pass a
 // bounding test (other aggregate, centres closer than the radii sum plus the
-// FP32 rounding margin) to a per-sphere hit list, in traversal order.
-// k_contact then evaluates the listed pairs; its lanes stay converged because
-// every lane works through a short list of real candidates.  A sphere whose
-// list overflowed searches its cells again inside k_contact.
+// skin plus the FP32 rounding margin) to a per-sphere hit list, ordered by the
+// partner's pile-local index.  It runs only in steps that rebuild the cell
+// list: in between, the lists stay complete as long as no sphere has moved
+// more than half the skin (checked per aggregate at the drift).  k_contact
+// evaluates the listed pairs every step; its lanes stay converged because
+// every lane works through a short list of candidates.  A sphere whose list
+// overflowed searches its cells again inside k_contact (its pile then
+// rebuilds every step, so the cells are current).
+// Every sphere sums its contacts in the order of the partners' indices, so
+// forces, torques and history do not depend on the cell size, the skin or
+// the steps at which the lists were rebuilt: the trajectory is bitwise the
+// same for any of them.
 // History slots are stored in sorted order (slot-major inside each pile) and
-// read at the position the sphere had in the previous step, which neighbours
-// in the current order mostly share; the previous partners' ids are staged in
-// shared memory and matched with a cursor that follows the (deterministic)
-// order in which contacts are found.  Force and torque are written in sorted
-// order, interleaved, so that the aggregate reduction gathers one 32-byte
-// sector per sphere.
+// read at the position the sphere had in the previous step; the previous
+// partners' ids are staged in shared memory and matched with a cursor, since
+// slots and hits are both in partner order.  Force and torque are written in
+// sorted order, interleaved, so that the aggregate reduction gathers one
+// 32-byte sector per sphere.
 //
 // Force law (the paper defers the constants and form to earlier work):
 //   d = r_b - r_a, n = d/|d|, x = s_a + s_b - |d| > 0 (overlap),
@@ -253,6 +260,7 @@ struct Me {
     float4 l;                        // mixed: position lo (+radius lo)
     int agg, hl, nprev, nn, cursor, flags;
     float tol;                       // mixed: pre-filter margin
+    typename CT<FP64>::T skin;       // filter: neighbour-list skin (0 in k_contact)
     const float4 *sslot;             // mixed: this thread's previous slots in shared memory
     typename CT<FP64>::V F, T;
 };
@@ -265,12 +273,12 @@ __device__ __forceinline__ bool candidate(int64_t k, int64_t kk, const typename 
 {
     if constexpr (FP64) {
         const double ddx = nh.x - m.p.x, ddy = nh.y - m.p.y, ddz = nh.z - m.p.z;
-        const double sr2 = nh.w + m.p.w;
+        const double sr2 = nh.w + m.p.w + m.skin;
         return ddx * ddx + ddy * ddy + ddz * ddz < sr2 * sr2 && kk != k && nagg != m.agg;
     } else {
         const float ddx = nh.x - m.p.x, ddy = nh.y - m.p.y, ddz = nh.z - m.p.z;
         const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-        const float srt = nh.w + m.p.w + m.tol;
+        const float srt = nh.w + m.p.w + m.tol + m.skin;
         return r2 <= srt * srt && kk != k && nagg != m.agg;
     }
 }
@@ -381,10 +389,13 @@ template <bool FP64>
 __global__ void __launch_bounds__(kContactBlock) k_contact_filter(Arrays a, Sizes z)
 {
     typedef typename CT<FP64>::P4 P4;
+    // per thread: the hits found so far, (partner index << 32 | sorted
+    // position), kept in increasing order by insertion
+    __shared__ unsigned long long s_list[kHitCap][kContactBlock];
     const int64_t k = (int64_t)blockIdx.x * kContactBlock + threadIdx.x;
     if (k >= z.N) return;
     const int p = a.sph_pile[k];
-    if (a.enabled[p] == 0 || a.pd[p].failed) return;
+    if (a.enabled[p] == 0 || a.pd[p].failed || !a.pd[p].rebuild) return;
     const PileStatic &S = a.ps[p];
     const int64_t s0 = S.s0;
     const int ns = (int)S.ns;
@@ -394,15 +405,18 @@ __global__ void __launch_bounds__(kContactBlock) k_contact_filter(Arrays a, Size
     if constexpr (FP64) {
         m.p = a.dp_[k];
         m.tol = 0.f;
+        m.skin = S.skin;
     } else {
         m.p = a.sph_[k];
         m.tol = filter_tol(S, m.p);
+        m.skin = (float)S.skin;
     }
     m.agg = a.sagg[k];
     int cx, cy, cz;
     own_cell<FP64>(S, m.p, cx, cy, cz);
     const int32_t *cstart = a.cstart + S.c0, *ccount = a.ccount + S.c0;
-    int32_t *hl = a.hits + s0 * kHitCap + kl;
+    const int32_t *srt = a.sorted + s0;
+    unsigned long long *list = &s_list[0][threadIdx.x];
     int n = 0;
     for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy) {
@@ -416,13 +430,69 @@ __global__ void __launch_bounds__(kContactBlock) k_contact_filter(Arrays a, Size
                     if constexpr (FP64) nh = a.dp_[kk];
                     else nh = a.sph_[kk];
                     if (candidate<FP64>(k, kk, nh, a.sagg[kk], m)) {
-                        if (n < kHitCap) hl[(int64_t)n * ns] = t;
+                        if (n < kHitCap) {
+                            const unsigned long long e =
+                                ((unsigned long long)(unsigned)srt[t] << 32) | (unsigned)t;
+                            int j = n;
+                            while (j > 0 && list[(j - 1) * kContactBlock] > e) {
+                                list[j * kContactBlock] = list[(j - 1) * kContactBlock];
+                                --j;
+                            }
+                            list[j * kContactBlock] = e;
+                        }
                         ++n;
                     }
                 }
             }
         }
+    int32_t *hl = a.hits + s0 * kHitCap + kl;
+    const int nw = n < kHitCap ? n : kHitCap;
+    for (int e = 0; e < nw; ++e) hl[(int64_t)e * ns] = (int32_t)(unsigned)list[e * kContactBlock];
     a.hitn[k] = n;
+    if (n > kHitCap) atomicOr(&a.pd[p].hit_overflow, 1);
+}
+
+// A sphere whose hit list overflowed (its pile rebuilt the cells this step:
+// an overflow forces a rebuild every step) searches its neighbour cells
+// again: the candidate with the smallest partner index above `last`, or -1.
+// Kept out of line, so that the rare path costs the pair kernel no registers.
+template <bool FP64>
+__device__ __noinline__ int64_t overflow_next(const Arrays &a, const PileStatic &S, int64_t k,
+                                              typename CT<FP64>::P4 p, int agg, float tol, int last)
+{
+    typedef typename CT<FP64>::P4 P4;
+    Me<FP64> m;
+    m.p = p;
+    m.agg = agg;
+    m.tol = tol;
+    m.skin = 0;
+    const int64_t s0 = S.s0;
+    const int nx = S.nx, ny = S.ny, nz = S.nz;
+    int cx, cy, cz;
+    own_cell<FP64>(S, m.p, cx, cy, cz);
+    const int32_t *cstart = a.cstart + S.c0, *ccount = a.ccount + S.c0;
+    const int32_t *srt = a.sorted + s0;
+    int best = 0x7fffffff;
+    int64_t bk = -1;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy) {
+            Strip sr;
+            strip_ranges(cstart, ccount, (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx, cx, nx, sr);
+            for (int r = 0; r < sr.n; ++r)
+                for (int t = sr.beg[r]; t < sr.end[r]; ++t) {
+                    const int id = srt[t];
+                    if (id <= last || id >= best) continue;
+                    const int64_t kk = s0 + t;
+                    P4 q;
+                    if constexpr (FP64) q = a.dp_[kk];
+                    else q = a.sph_[kk];
+                    if (candidate<FP64>(k, kk, q, a.sagg[kk], m)) {
+                        best = id;
+                        bk = kk;
+                    }
+                }
+        }
+    return bk;
 }
 
 template <bool FP64>
@@ -467,6 +537,7 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
         m.w = a.dw_[k];
         m.agg = (int)m.v.w;
         m.tol = 0.f;
+        m.skin = 0.0;
         m.F = d3(0, 0, 0);
         m.T = d3(0, 0, 0);
     } else {
@@ -488,37 +559,29 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
         m.w = a.sw_[k];
         m.agg = __float_as_int(m.v.w);
         m.tol = filter_tol(S, m.p);
+        m.skin = 0.f;
         m.F = f3(0, 0, 0);
         m.T = f3(0, 0, 0);
     }
     const int nh = a.hitn[k];
-    if (nh <= kHitCap) {
-        // all hit indices first (independent loads), then the pairs
+    const bool listed = nh <= kHitCap;
+    int *myhit = s_hit + threadIdx.x;
+    if (listed) {   // all hit indices first (independent loads), then the pairs
         const int32_t *hl = a.hits + s0 * kHitCap + kl;
-        int *myhit = s_hit + threadIdx.x;
         for (int e = 0; e < nh; ++e) myhit[e * kContactBlock] = hl[(int64_t)e * ns];
-        for (int e = 0; e < nh; ++e)
-            process<FP64>(a, s0 + myhit[e * kContactBlock], m, myprev, hprev, hnew, ns, K, prm);
-    } else {
-        // the hit list overflowed: search the neighbour cells again, in the same order
-        const int nx = S.nx, ny = S.ny, nz = S.nz;
-        int cx, cy, cz;
-        own_cell<FP64>(S, m.p, cx, cy, cz);
-        const int32_t *cstart = a.cstart + S.c0, *ccount = a.ccount + S.c0;
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy) {
-                Strip sr;
-                strip_ranges(cstart, ccount, (wrapc(cz + dz, nz) * ny + wrapc(cy + dy, ny)) * nx, cx, nx, sr);
-                for (int r = 0; r < sr.n; ++r)
-                    for (int t = sr.beg[r]; t < sr.end[r]; ++t) {
-                        const int64_t kk = s0 + t;
-                        P4 q;
-                        if constexpr (FP64) q = a.dp_[kk];
-                        else q = a.sph_[kk];
-                        if (candidate<FP64>(k, kk, q, a.sagg[kk], m))
-                            process<FP64>(a, kk, m, myprev, hprev, hnew, ns, K, prm);
-                    }
-            }
+    }
+    int last = -1;
+    for (int e = 0;; ++e) {
+        int64_t kk;
+        if (listed) {
+            if (e >= nh) break;
+            kk = s0 + myhit[e * kContactBlock];
+        } else {
+            kk = overflow_next<FP64>(a, S, k, m.p, m.agg, m.tol, last);
+            if (kk < 0) break;
+            last = a.sorted[kk];
+        }
+        process<FP64>(a, kk, m, myprev, hprev, hnew, ns, K, prm);
     }
     if constexpr (FP64) {
         a.ftc64[2 * k] = make_dbl4(m.F.x, m.F.y, m.F.z, 0.0);

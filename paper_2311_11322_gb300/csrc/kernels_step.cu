@@ -118,6 +118,24 @@ __global__ void k_agg_begin(Arrays a, Sizes z)
     const PileDyn &D = a.pd[p];
     double3 c = r - ld3(D.O);
     double3 vb = v + (0.5 * h) * acc - ld3(D.V);
+    // Neighbour-list validity.  Every sphere of the aggregate moved, relative
+    // to the pile frame extrapolated by one step (O + h V), by at most
+    // |c' - c'_ref| + |(R - R_ref) b| <= |c' - c'_ref| + 2 |b|max min|q -+ q_ref|
+    // since the last rebuild.  The hit lists hold every pair closer than the
+    // radii sum plus the skin at the rebuild, so they stay complete while no
+    // sphere has moved more than half the skin.
+    const double skin = a.ps[p].skin;
+    if (skin > 0.0) {
+        const double *ar = a.aref + 8 * g;
+        double3 dc = c - h * ld3(D.V) - d3(ar[0], ar[1], ar[2]);
+        double dm = 0.0, dp = 0.0;
+        for (int k = 0; k < 4; ++k) {
+            dm += (q[k] - ar[3 + k]) * (q[k] - ar[3 + k]);
+            dp += (q[k] + ar[3 + k]) * (q[k] + ar[3 + k]);
+        }
+        double disp = sqrt(dot(dc, dc)) + 2.0 * ar[7] * sqrt(fmin(dm, dp));
+        if (!(disp <= 0.5 * skin * (1.0 - 1e-6))) atomicOr(&a.pd[p].rebuild, 1);
+    }
     if (FP64) {
         AggRec64 rec;
         for (int k = 0; k < 9; ++k) rec.R[k] = R[k];
@@ -165,6 +183,12 @@ __global__ void k_pile_partials(Arrays a, Sizes z)
         if (end > S.a0 + S.na) end = S.a0 + S.na;
         for (int64_t g = beg + threadIdx.x; g < end; g += blockDim.x) {
             if (MODE == 0) {
+                if (a.pd[p].rebuild) {   // new neighbour-list reference
+                    const PileDyn &D = a.pd[p];
+                    double *ar = a.aref + 8 * g;
+                    for (int c = 0; c < 3; ++c) ar[c] = a.r[3 * g + c] - D.O[c] - S.h * D.V[c];
+                    for (int c = 0; c < 4; ++c) ar[3 + c] = a.q[4 * g + c];
+                }
                 double M = a.M[g];
                 acc[0] += M;
                 for (int c = 0; c < 3; ++c) {
@@ -234,6 +258,9 @@ __global__ void k_pile_finalize(Arrays a, Sizes z)
         D.steps += 1;
         D.parity ^= 1;
         if (D.flags & (DEM_FLAG_SLOTS | DEM_FLAG_NONFINITE)) D.failed = 1;
+        if (D.rebuild) D.rebuilds += 1;
+        D.rebuild = (S.skin <= 0.0 || D.hit_overflow) ? 1 : 0;
+        D.hit_overflow = 0;
     }
 }
 
@@ -323,18 +350,45 @@ __global__ void k_keys(Arrays a, Sizes z)
         cz = cell_coord_f(pz.hi, ic, S.nz);
         a.gpos32[i] = make_float4(px.hi, py.hi, pz.hi, (float)a.m64[i]);
     }
+    if (!a.pd[p].rebuild) return;   // cell list kept from the last rebuild
     int key = (cz * S.ny + cy) * S.nx + cx;
     a.key[i] = key;
     a.rank[i] = atomicAdd(a.ccount + S.c0 + key, 1);
 }
 
+__device__ int tile_pile(const Arrays &a, const Sizes &z, int64_t t);
+
+// Zero the cell counts of the piles that rebuild this step.
+__global__ void k_clear_cells(Arrays a, Sizes z)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= z.C) return;
+    int p = tile_pile(a, z, c / kScanTile);
+    if (pile_active(a, p) && a.pd[p].rebuild) a.ccount[c] = 0;
+}
+
 void launch_keys(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
 {
     if (z.N == 0) return;
-    cudaMemsetAsync(a.ccount, 0, sizeof(int32_t) * z.C, st);
+    k_clear_cells<<<(unsigned)((z.C + 255) / 256), 256, 0, st>>>(a, z);
     unsigned nb = (unsigned)((z.N + 255) / 256);
     if (fp64) k_keys<true><<<nb, 256, 0, st>>>(a, z);
     else k_keys<false><<<nb, 256, 0, st>>>(a, z);
+}
+
+// Host request (after a state write or a new layout): the next step rebuilds
+// the cell list and hit lists of pile `slot` (all piles for slot < 0).
+__global__ void k_force_rebuild(Arrays a, Sizes z, int slot)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= z.P || (slot >= 0 && p != slot)) return;
+    a.pd[p].rebuild = 1;
+}
+
+void launch_force_rebuild(const Arrays &a, const Sizes &z, int slot, cudaStream_t st)
+{
+    if (z.P == 0) return;
+    k_force_rebuild<<<(unsigned)((z.P + 127) / 128), 128, 0, st>>>(a, z, slot);
 }
 
 // ---------------------------------------------------------------- scan of cell counts
@@ -353,7 +407,7 @@ __global__ void k_scan_tiles(Arrays a, Sizes z)
 {
     int64_t t = blockIdx.x;
     int p = tile_pile(a, z, t);
-    if (!pile_active(a, p)) return;
+    if (!pile_active(a, p) || !a.pd[p].rebuild) return;
     const int32_t *c = a.ccount + t * kScanTile;
     int s = 0;
     for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) s += c[k];
@@ -372,7 +426,7 @@ __global__ void k_scan_tiles(Arrays a, Sizes z)
 __global__ void k_scan_piles(Arrays a, Sizes z)
 {
     int p = blockIdx.x;
-    if (!pile_active(a, p)) return;
+    if (!pile_active(a, p) || !a.pd[p].rebuild) return;
     const PileStatic &S = a.ps[p];
     __shared__ int buf[1024];
     __shared__ int carry;
@@ -402,7 +456,7 @@ __global__ void k_scan_cells(Arrays a, Sizes z)
 {
     int64_t t = blockIdx.x;
     int p = tile_pile(a, z, t);
-    if (!pile_active(a, p)) return;
+    if (!pile_active(a, p) || !a.pd[p].rebuild) return;
     const int32_t *c = a.ccount + t * kScanTile;
     int32_t *o = a.cstart + t * kScanTile;
     int v[8];
@@ -441,7 +495,7 @@ __global__ void k_scatter(Arrays a, Sizes z)
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= z.N) return;
     int p = a.sph_pile[i];
-    if (!pile_active(a, p)) return;
+    if (!pile_active(a, p) || !a.pd[p].rebuild) return;
     const PileStatic &S = a.ps[p];
     int slot = a.cstart[S.c0 + a.key[i]] + a.rank[i];
     a.sorted[S.s0 + slot] = (int32_t)(i - S.s0);
@@ -461,7 +515,7 @@ __global__ void k_cell_order(Arrays a, Sizes z)
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= z.N) return;
     int p = a.sph_pile[k];
-    if (!pile_active(a, p)) return;
+    if (!pile_active(a, p) || !a.pd[p].rebuild) return;
     const PileStatic &S = a.ps[p];
     int32_t *srt = a.sorted + S.s0;
     int kl = (int)(k - S.s0);

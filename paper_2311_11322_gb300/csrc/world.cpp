@@ -30,6 +30,7 @@ struct PileHost {
     int64_t ns, na, nc, nch, nt;
     int nx, ny, nz;
     double cell, smax;
+    double ext[3];         // extent of the wrapped grid at creation (cell x dims)
     dem_params P;
     double M_total;
     bool reported;
@@ -63,6 +64,7 @@ struct dem_world {
     bool grav_pack = false;           // packed f32x2 pair terms (even grav_ib)
     int sm_count = 0;
     double cell_factor = 1.0;
+    double skin_frac = 0.1;           // neighbour-list skin / largest radius
     // flags readback
     PileDyn *h_dyn = nullptr;   // pinned
     int64_t h_dyn_cap = 0;
@@ -115,6 +117,19 @@ void dev_free(dem_world *w, void *p)
     if (!p) return;
     if (w->free_fn) w->free_fn(p, w->ctx);
     else cudaFree(p);
+}
+
+// Contact range of a pile's cells: the largest radii sum, and that plus the
+// neighbour-list skin.
+double min_cell(const PileHost &q) { return 2.0 * q.smax * (1.0 + 1e-6); }
+
+// Skin actually used by a pile: the requested fraction of its largest radius,
+// limited by what its cell edge leaves beyond the radii sum.
+double skin_of(const dem_world *w, const PileHost &q)
+{
+    double want = w->skin_frac * q.smax;
+    double room = q.cell - min_cell(q);
+    return std::max(0.0, std::min(want, room));
 }
 
 void build_fields(dem_world *w)
@@ -174,6 +189,7 @@ void build_fields(dem_world *w)
     add((void **)&a.acc, C_AGG, 24, true);
     add((void **)&a.torque, C_AGG, 24, true);
     add((void **)&a.out, C_AGG, 144, true);
+    add((void **)&a.aref, C_AGG, 64, true);
     add((void **)&a.ccount, C_CELL, 4, false);
     add((void **)&a.cstart, C_CELL, 4, false);
     add((void **)&a.tile_sum, C_TILE, 4, false);
@@ -341,6 +357,7 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
         S.ch0 = ch0; S.nch = q.nch; S.t0 = c0 / kScanTile; S.nt = q.nt;
         S.nx = q.nx; S.ny = q.ny; S.nz = q.nz; S.K = w->K;
         S.cell = q.cell; S.inv_cell = 1.0 / q.cell;
+        S.skin = skin_of(w, q);
         const dem_params &P = q.P;
         S.G = P.G; S.h = P.dt; S.kn = P.kn; S.kt = P.kt; S.cn = P.cn; S.ct = P.ct;
         S.mu_s = P.mu_s; S.mu_r = P.mu_r; S.mu_t = P.mu_t; S.w0 = P.w0;
@@ -376,6 +393,8 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
         CU(cudaMemcpyAsync(w->A.gitems, gp.items.data(), 16 * gp.items.size(),
                            cudaMemcpyHostToDevice, w->stream));
     launch_fill_ids(w->A, w->Z, w->stream);
+    // a new layout leaves the transient sort and hit lists undefined
+    launch_force_rebuild(w->A, w->Z, -1, w->stream);
     CU(cudaGetLastError());
     return DEM_OK;
 }
@@ -538,23 +557,19 @@ void rotmat(const double *q, double *R)
 // Wrapped grid for one pile: cell >= 2 x largest radius (times the tuning
 // factor), dims >= 3 so the 27 neighbour cells are distinct, total cells
 // capped near 4 x spheres by enlarging the cell.
-void choose_grid(const dem_world *w, PileHost &q, const double *pos_rel, int64_t N)
+// Cell edge and wrapped grid dims for an extent `ext` (plus `pad` cells per
+// axis): cell = base x cell_factor, at least the radii sum plus the skin,
+// enlarged until the grid holds at most max(4 N, 27) cells.
+void set_grid(const dem_world *w, PileHost &q, const double *ext, int pad)
 {
-    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-    for (int64_t i = 0; i < N; ++i)
-        for (int c = 0; c < 3; ++c) {
-            lo[c] = std::min(lo[c], pos_rel[3 * i + c]);
-            hi[c] = std::max(hi[c], pos_rel[3 * i + c]);
-        }
-    double cell = q.P.cell_size > 0 ? q.P.cell_size : 2.0 * q.smax * (1.0 + 1e-6);
-    cell *= w->cell_factor;
-    int64_t cap = std::max<int64_t>(4 * N, 27);
+    double cell = (q.P.cell_size > 0 ? q.P.cell_size : min_cell(q)) * w->cell_factor;
+    cell = std::max(cell, min_cell(q) + w->skin_frac * q.smax);
+    int64_t cap = std::max<int64_t>(4 * q.ns, 27);
     int dims[3];
     for (int it = 0; it < 200; ++it) {
         int64_t tot = 1;
         for (int c = 0; c < 3; ++c) {
-            double ext = hi[c] - lo[c] + 2.0 * q.smax;
-            int64_t n = (int64_t)std::ceil(ext / cell) + 2;
+            int64_t n = (int64_t)std::ceil(ext[c] / cell) + pad;
             n = std::max<int64_t>(3, std::min<int64_t>(n, 1 << 20));
             dims[c] = (int)n;
             tot *= n;
@@ -567,6 +582,34 @@ void choose_grid(const dem_world *w, PileHost &q, const double *pos_rel, int64_t
     int64_t cells = (int64_t)q.nx * q.ny * q.nz;
     q.nc = (cells + kScanTile - 1) / kScanTile * kScanTile;
     q.nt = q.nc / kScanTile;
+}
+
+// New grids for every pile (cells, hit lists and the sort are transient:
+// nothing to preserve; every pile rebuilds at its next step).
+dem_status regrid(dem_world *w);
+
+void choose_grid(const dem_world *w, PileHost &q, const double *pos_rel, int64_t N)
+{
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int64_t i = 0; i < N; ++i)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = std::min(lo[c], pos_rel[3 * i + c]);
+            hi[c] = std::max(hi[c], pos_rel[3 * i + c]);
+        }
+    double ext[3];
+    for (int c = 0; c < 3; ++c) ext[c] = hi[c] - lo[c] + 2.0 * q.smax;
+    set_grid(w, q, ext, 2);
+    for (int c = 0; c < 3; ++c) q.ext[c] = q.cell * (c == 0 ? q.nx : c == 1 ? q.ny : q.nz);
+}
+
+dem_status regrid(dem_world *w)
+{
+    std::vector<PileHost> newp = w->piles;
+    for (auto &q : newp) set_grid(w, q, q.ext, 0);
+    dem_status s = relayout(w, newp, nullptr);
+    if (s != DEM_OK) return s;
+    w->piles = newp;
+    return DEM_OK;
 }
 
 }  // namespace
@@ -788,7 +831,17 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     UP(D.acc + 3 * a0, zero3.data(), 24 * A);
     UP(D.torque + 3 * a0, zero3.data(), 24 * A);
     CU(cudaMemsetAsync(D.out + 18 * a0, 0, 144 * A, st));
+    std::vector<double> aref(8 * (size_t)A, 0.0);
+    for (int a = 0; a < A; ++a) {
+        double bm = 0;
+        for (int64_t i = first[a]; i < first[a] + spa[a]; ++i)
+            bm = std::max(bm, std::sqrt(b[3 * i] * b[3 * i] + b[3 * i + 1] * b[3 * i + 1] +
+                                        b[3 * i + 2] * b[3 * i + 2]));
+        aref[8 * a + 7] = bm;
+    }
+    UP(D.aref + 8 * a0, aref.data(), 64 * A);
     PileDyn dyn{};
+    dyn.rebuild = 1;
     for (int d = 0; d < 3; ++d) {
         dyn.O[d] = Rp[d]; dyn.V[d] = Vp[d]; dyn.Rc[d] = Rp[d]; dyn.Vc[d] = Vp[d];
         dyn.P_pos[d] = p->ext_pos[d]; dyn.P_vel[d] = p->ext_vel[d]; dyn.P_acc[d] = 0.0;
@@ -1060,11 +1113,12 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
         for (int c = 0; c < 3; ++c) { out[c] = dyn.P_pos[c]; out[3 + c] = dyn.P_vel[c]; out[6 + c] = dyn.P_acc[c]; }
         break;
     case DEM_FIELD_INFO: {
-        CHK(need(16));
-        double info[16] = {(double)A, (double)N, (double)dyn.steps, (double)dyn.flags,
+        CHK(need(20));
+        double info[20] = {(double)A, (double)N, (double)dyn.steps, (double)dyn.flags,
                            (double)q.nx, (double)q.ny, (double)q.nz, q.cell,
                            (double)w->K, (double)w->precision, dyn.O[0], dyn.O[1], dyn.O[2],
-                           (double)dyn.failed, (double)dyn.parity, q.M_total};
+                           (double)dyn.failed, (double)dyn.parity, q.M_total,
+                           (double)dyn.rebuilds, skin_of(w, q), (double)dyn.rebuild, 0.0};
         std::memcpy(out, info, sizeof info);
         break;
     }
@@ -1162,6 +1216,11 @@ dem_status dem_write_state(dem_world *w, int32_t pile_id, int32_t field, const d
         return fail(w, DEM_ERR_ARG, "field %d is not writable", field);
     }
 #undef CHK
+    // positions, orientations or contacts may have changed: rebuild the
+    // neighbour lists of this pile at its next step
+    launch_force_rebuild(w->A, w->Z, slot, w->stream);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(w->stream));
     return DEM_OK;
 }
 
@@ -1213,36 +1272,17 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
     } else if (k == "grav_item") {
         if (!(value >= 1024.0)) return fail(w, DEM_ERR_ARG, "grav_item must be >= 1024");
         w->grav_item = value;
-    } else if (k == "cell_factor") {
-        if (!(value >= 1.0) || value > 16.0) return fail(w, DEM_ERR_ARG, "cell_factor must be in [1, 16]");
-        if (w->cell_factor != value) {
-            // new grids for every pile (cells are transient: nothing to preserve)
-            double old = w->cell_factor;
-            w->cell_factor = value;
-            std::vector<PileHost> newp = w->piles;
-            for (auto &q : newp) {
-                double base = q.cell / old;
-                double cell = base * value;
-                double ext[3] = {q.nx * q.cell, q.ny * q.cell, q.nz * q.cell};
-                int64_t cap = std::max<int64_t>(4 * q.ns, 27);
-                int dims[3];
-                for (int it = 0; it < 200; ++it) {
-                    int64_t tot = 1;
-                    for (int c = 0; c < 3; ++c) {
-                        dims[c] = (int)std::max<int64_t>(3, (int64_t)std::ceil(ext[c] / cell));
-                        tot *= dims[c];
-                    }
-                    if (tot <= cap) break;
-                    cell *= std::cbrt((double)tot / (double)cap) * 1.01;
-                }
-                q.cell = cell; q.nx = dims[0]; q.ny = dims[1]; q.nz = dims[2];
-                int64_t cells = (int64_t)q.nx * q.ny * q.nz;
-                q.nc = (cells + kScanTile - 1) / kScanTile * kScanTile;
-                q.nt = q.nc / kScanTile;
-            }
-            dem_status s = relayout(w, newp, nullptr);
-            if (s != DEM_OK) { w->cell_factor = old; return s; }
-            w->piles = newp;
+    } else if (k == "cell_factor" || k == "skin") {
+        if (k == "cell_factor" && (!(value >= 1.0) || value > 16.0))
+            return fail(w, DEM_ERR_ARG, "cell_factor must be in [1, 16]");
+        if (k == "skin" && (!(value >= 0.0) || value > 4.0))
+            return fail(w, DEM_ERR_ARG, "skin must be in [0, 4] (fraction of the largest radius)");
+        double &knob = k == "skin" ? w->skin_frac : w->cell_factor;
+        if (knob != value) {
+            double old = knob;
+            knob = value;
+            dem_status s = regrid(w);
+            if (s != DEM_OK) { knob = old; return s; }
         }
     } else {
         return fail(w, DEM_ERR_ARG, "unknown tuning key '%s'", key);
@@ -1327,7 +1367,8 @@ size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contact
     sph += 8;   // pos_of_home, both parities
     sph += d ? (32 * 3 + 32 + 64) : (16 * 2 + 16 * 4 + 16 + 32);
     size_t sphk = d ? 2 * 32 : 2 * 16;
-    size_t agg = 4 * 3 + 8 + 72 * 2 + 24 * 2 + 32 + 24 * 3 + 144 + (d ? sizeof(AggRec64) : sizeof(AggRecMixed));
+    size_t agg = 4 * 3 + 8 + 72 * 2 + 24 * 2 + 32 + 24 * 3 + 144 + 64 +
+                 (d ? sizeof(AggRec64) : sizeof(AggRecMixed));
     int64_t cells = std::max<int64_t>(4 * n_spheres, 27) + kScanTile;
     size_t bytes = sph * (size_t)n_spheres + sphk * (size_t)n_spheres * (size_t)max_contacts +
                    agg * (size_t)n_agg + 8 * (size_t)cells + 4 * (size_t)(cells / kScanTile + 1) +

@@ -32,7 +32,7 @@ FIELDS = {  # name: (id, rows ('A' aggregates / 'N' spheres / int), cols)
     "FORCE_GRAV": (10, "A", 3), "TORQUE_GRAV": (11, "A", 3), "FORCE_EXT": (12, "A", 3),
     "TORQUE_EXT": (13, "A", 3), "SPHERE_FC": (14, "N", 3), "SPHERE_TC": (15, "N", 3),
     "SPHERE_FG": (16, "N", 3), "ACC": (17, "A", 3), "PLANET": (18, 9, None), "MASS": (19, "A", 1),
-    "BODY_OFFSETS": (20, "N", 3), "OMEGA_BODY": (21, "A", 3), "INFO": (22, 16, None),
+    "BODY_OFFSETS": (20, "N", 3), "OMEGA_BODY": (21, "A", 3), "INFO": (22, 20, None),
     "FRAME": (23, 6, None), "TORQUE_STORED": (24, "A", 3),
 }
 KERNELS = {"AGG_BEGIN": 0, "PILE_BEGIN": 1, "KEYS": 2, "SCAN": 3, "SCATTER": 4,
@@ -286,7 +286,8 @@ class World:
     def info(self, pile) -> dict:
         v = self.read(pile, "INFO")
         keys = ("n_agg", "n_sph", "steps", "flags", "nx", "ny", "nz", "cell", "K", "precision",
-                "Ox", "Oy", "Oz", "failed", "parity", "M_total")
+                "Ox", "Oy", "Oz", "failed", "parity", "M_total", "rebuilds", "skin",
+                "rebuild_next", "reserved")
         return dict(zip(keys, v.tolist()))
 
     # ---- tuning
