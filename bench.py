@@ -46,7 +46,12 @@ if ROOT not in sys.path:
 METRIC = "sphere-steps/s at 100k spheres, mixed vs FP64 form; batched p50/p99 sim latency"
 UNIT = "sphere-steps/s"
 N_SPHERES = 100_000
+# Gravity arithmetic.  One-sided (gather) form: 20 flop per ordered pair (3 sub,
+# 3 FMA, rsqrt counted as 2, 3 mul, 3 FMA).  Symmetric form, which the mixed
+# path runs: each unordered pair once, 27 flop (3 sub, 3 FMA, rsqrt as 2,
+# 2 mul for r^-3, 2 mul for the two mass factors, 6 FMA for the two sums).
 FLOP_PER_INTERACTION = 20.0
+FLOP_PER_PAIR_SYM = 27.0
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 SM_MAX_MHZ = 2070.0
@@ -192,7 +197,10 @@ def run_fp64(dem, W, steps):
 
 def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3):
     """Contact pass on a dense FCC-tetrahedra lattice (0.5% R overlaps, 9 contacts
-    per sphere), gravity off, working set far above L2."""
+    per sphere), gravity off, working set far above L2.  Steady state: the pair
+    pass over the candidate lists kept since the last rebuild (the lattice moves
+    ~1e-4 R per step, so its lists are rebuilt every few hundred steps); the
+    rebuild step (cell sort + candidate filter + pair pass) is timed separately."""
     import torch
     ic, p = W.dense_lattice(n_spheres=n, seed=0, precision=W.PRECISION_MIXED)
     p = p.replace(G=0.0)
@@ -203,6 +211,7 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3):
         st = torch.cuda.ExternalStream(w.stream)
         for _ in range(warmup):
             w.step_timed()
+        r0 = w.info(pid)["rebuilds"]
         ks = []
         for _ in range(steps):
             with torch.cuda.stream(st):
@@ -210,20 +219,31 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3):
             ks.append(w.step_timed()[1])
         info = w.info(pid)
         cnt = w.read(pid, "CONTACTS")[:, 0]
+        # rebuild steps: a state write (the same velocities) forces one
+        vel = w.read(pid, "VEL")
+        rb = []
+        for _ in range(3):
+            w.write(pid, "VEL", vel)
+            with torch.cuda.stream(st):
+                flush.zero_()
+            rb.append(w.step_timed()[1])
     z = float(cnt.sum())
-    cells = info["nx"] * info["ny"] * info["nz"]
     N = ic.n_sph
-    # compulsory bytes per launch: own sorted state 4 x float4 (64), sorted
-    # index, previous sorted position, previous and new history counts (4 x 4),
-    # F and tau out (2 x float4 = 32), every contact's history slot read and
-    # written (float4 each), and the cell table (start + count, 8 per cell)
-    algo = N * (64 + 16 + 32) + z * 32 + cells * 8
+    # compulsory bytes per step: own sorted state 4 x float4 (64), candidate
+    # count, sorted index, previous sorted position, previous and new history
+    # counts (5 x 4), F and tau out (2 x float4 = 32), the candidate list (4 per
+    # entry, at least one per contact) and every contact's history slot read
+    # and written (float4 each)
+    algo = N * (64 + 20 + 32) + z * (4 + 32)
     ms = statistics.median(ks)
     achieved = algo / (ms / 1e3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
             "frac": achieved / peak_gbs, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
             "traffic": traffic_for("kernels_contact.cu", "k_contact_mixed"),
-            "kernel_ms": ms, "n_spheres": N, "contacts_per_sphere": z / N,
+            "kernel": "k_contact (pair pass over the kept candidate lists)",
+            "kernel_ms": ms, "rebuilds_in_timed_steps": info["rebuilds"] - r0,
+            "rebuild_step_contact_ms": statistics.median(rb),
+            "n_spheres": N, "contacts_per_sphere": z / N,
             "algorithmic_bytes_per_launch": algo, "workload": "dense FCC tetrahedra lattice, "
             "1,048,576 spheres, overlaps 0.5% R, gravity off"}
 
@@ -377,7 +397,8 @@ def run_ours(args):
     t_max = max_over_ranks(t_rank, ws, device="cuda")
     value = ws * ic.n_sph * args.steps / t_max
     g_ms = statistics.mean(grav_ms)
-    flops = FLOP_PER_INTERACTION * interactions(ic)
+    n_int = interactions(ic)
+    flops = FLOP_PER_PAIR_SYM * n_int / 2.0
     achieved = flops / (g_ms / 1e3) / 1e12
     w.close()
 
@@ -389,10 +410,14 @@ def run_ours(args):
            "gpu_launches": n_kern * args.steps,
            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                         "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                        "traffic": traffic_for("kernels_gravity.cu", "k_gravity32"),
-                        "kernel": "k_gravity32 (softened direct-sum gravity)",
+                        "traffic": traffic_for("kernels_gravity.cu", "k_gravity32s"),
+                        "kernel": "k_gravity32s (softened direct-sum gravity, symmetric "
+                                  "tile pairs, packed f32x2) + k_grav_combine_sym",
                         "kernel_ms": g_ms, "share_of_step": g_ms / statistics.mean(step_ms),
                         "flops_per_launch": flops,
+                        "flop_count": "27 per unordered pair of spheres in different aggregates",
+                        "interactions_per_s": n_int / (g_ms / 1e3),
+                        "one_sided_equivalent_tflops": FLOP_PER_INTERACTION * n_int / (g_ms / 1e3) / 1e12,
                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"},
            "clocks": ck}
     if rank == 0 and not args.no_fp64:

@@ -231,7 +231,10 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
  * thread: 1, 2 or 4), "grav_item" (target pair interactions per gravity work
  * item, >= 1024; sets the j-range split), "grav_jchunk" (fixed j-range length
  * per work item, 0 = use grav_item), "grav_pack" (1 = packed f32x2 pair terms
- * when grav_ib is even, 0 = scalar FP32), "cell_factor" (cell edge / (2 x
+ * when grav_ib is even, 0 = scalar FP32), "grav_sym" (mixed path: 1 =
+ * symmetric tile-pair form, each pair evaluated once and applied to both
+ * spheres, the default; 0 = one-sided form shaped by the keys above),
+ * "cell_factor" (cell edge / (2 x
  * largest radius), >= 1), "skin" (neighbour-list skin as a fraction of the
  * pile's largest radius, in [0, 4], default 0.1; 0 = search contacts afresh
  * every step).  With a skin the cell list and the per-sphere candidate lists
@@ -245,8 +248,9 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
 dem_status dem_set_tuning(dem_world *w, const char *key, double value);
 
 /*
- * Autotuner: time the candidate gravity shapes (block 64/128/256, 1/2/4
- * i-spheres per thread, scalar or packed, three work-item sizes) and then
+ * Autotuner: time the candidate gravity shapes (the symmetric form in the
+ * mixed path; block 64/128/256, 1/2/4 i-spheres per thread, scalar or packed,
+ * three work-item sizes of the one-sided form) and then
  * cell factors 1, 1.25, 1.5, 2 on the current piles, running `trial_steps`
  * real steps per candidate (so the state advances), and keep the fastest.
  * best_ms_out (may be NULL) receives its step time.

@@ -149,9 +149,12 @@ void launch_cell_order(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_gather(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
 void launch_contact(const Arrays &a, const Sizes &z, bool fp64, int K, cudaStream_t st);
 cudaError_t contact_setup(bool fp64, int K);
+// sym: symmetric tile-pair form (mixed path; items are (pile, tile a, tile b)
+// with 512-sphere tiles, gnchunk = tiles per pile)
+constexpr int kGravSymTile = 512;
 void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int ib, bool pack,
-                    cudaStream_t st);
-int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack);
+                    bool sym, cudaStream_t st);
+int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym);
 void launch_agg_end(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
 void launch_pile_end(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_fill_ids(const Arrays &a, const Sizes &z, cudaStream_t st);

@@ -237,7 +237,19 @@ __device__ __forceinline__ void strip_ranges(const int32_t *cstart, const int32_
 constexpr int kContactBlock = 128;
 
 
-constexpr int kSlotStage = 16;       // previous slots copied to shared memory (mixed)
+// launch bounds of the pair kernel (optionally with a minimum number of
+// resident blocks per SM, which caps its registers)
+// partner data of the next hit loaded one hit ahead (1), plus the S of the
+// slot the next hit most likely matches (2)
+#ifndef DEM_CONTACT_PREFETCH
+#define DEM_CONTACT_PREFETCH 0
+#endif
+#ifdef DEM_CONTACT_MINB
+#define DEM_CONTACT_BOUNDS __launch_bounds__(kContactBlock, DEM_CONTACT_MINB)
+#else
+#define DEM_CONTACT_BOUNDS __launch_bounds__(kContactBlock)
+#endif
+
 
 template <bool FP64> struct CT;
 template <> struct CT<false> {
@@ -261,7 +273,6 @@ struct Me {
     int agg, hl, nprev, nn, cursor, flags;
     float tol;                       // mixed: pre-filter margin
     typename CT<FP64>::T skin;       // filter: neighbour-list skin (0 in k_contact)
-    const float4 *sslot;             // mixed: this thread's previous slots in shared memory
     typename CT<FP64>::V F, T;
 };
 
@@ -283,27 +294,42 @@ __device__ __forceinline__ bool candidate(int64_t k, int64_t kk, const typename 
     }
 }
 
-// One candidate that passed the filter: history lookup, canonical pair
-// evaluation, accumulation and slot write.
+// Partner data of one candidate (sorted SoA entries).
 template <bool FP64>
-__device__ __forceinline__ void process(const Arrays &a, int64_t kk, Me<FP64> &m, const int *myprev,
-                                        const void *hprev_v, void *hnew_v, int ns, int K,
-                                        const typename CT<FP64>::Prm &prm)
+struct Nb {
+    typename CT<FP64>::P4 h, v, w;   // position (+radius), velocity (+agg), spin (+index)
+    float4 l;                        // mixed: position lo (+radius lo)
+};
+
+template <bool FP64>
+__device__ __forceinline__ void load_nb(const Arrays &a, int64_t kk, Nb<FP64> &nb)
+{
+    if constexpr (FP64) {
+        nb.h = a.dp_[kk];
+        nb.v = a.dv_[kk];
+        nb.w = a.dw_[kk];
+    } else {
+        nb.h = a.sph_[kk];
+        nb.l = a.spl_[kk];
+        nb.v = a.sv_[kk];
+        nb.w = a.sw_[kk];
+    }
+}
+
+// One candidate that passed the filter: history lookup, canonical pair
+// evaluation, accumulation and slot write.  `spec`/`Sspec`: the previous slot
+// guessed for this partner and its S, loaded ahead (spec < 0: none).
+template <bool FP64>
+__device__ __forceinline__ void process(const Arrays &a, const Nb<FP64> &nb, Me<FP64> &m,
+                                        const int *myprev, const void *hprev_v, void *hnew_v, int ns,
+                                        int K, const typename CT<FP64>::Prm &prm, int spec,
+                                        const typename CT<FP64>::V &Sspec)
 {
     typedef typename CT<FP64>::V V;
-    typename CT<FP64>::P4 nh, nv, nw;
+    const typename CT<FP64>::P4 &nh = nb.h, &nv = nb.v, &nw = nb.w;
     int ngid;
-    if constexpr (FP64) {
-        nh = a.dp_[kk];
-        nv = a.dv_[kk];
-        nw = a.dw_[kk];
-        ngid = (int)nw.w;
-    } else {
-        nh = a.sph_[kk];
-        nv = a.sv_[kk];
-        nw = a.sw_[kk];
-        ngid = __float_as_int(nw.w);
-    }
+    if constexpr (FP64) ngid = (int)nw.w;
+    else ngid = __float_as_int(nw.w);
     int slot = -1;
     if (m.cursor < m.nprev && myprev[m.cursor * kContactBlock] == ngid) slot = m.cursor;
     else
@@ -313,12 +339,13 @@ __device__ __forceinline__ void process(const Arrays &a, int64_t kk, Me<FP64> &m
     if constexpr (FP64) Sprev = d3(0, 0, 0);
     else Sprev = f3(0, 0, 0);
     if (slot >= 0) {
-        if constexpr (FP64) {
+        if (slot == spec) {
+            Sprev = Sspec;
+        } else if constexpr (FP64) {
             const dbl4 sl = ((const dbl4 *)hprev_v)[(int64_t)slot * ns];
             Sprev = d3(sl.x, sl.y, sl.z);
         } else {
-            const float4 sl = slot < kSlotStage ? m.sslot[slot * kContactBlock]
-                                                : ((const float4 *)hprev_v)[(int64_t)slot * ns];
+            const float4 sl = ((const float4 *)hprev_v)[(int64_t)slot * ns];
             Sprev = f3(sl.x, sl.y, sl.z);
         }
         m.cursor = slot + 1;
@@ -335,7 +362,7 @@ __device__ __forceinline__ void process(const Arrays &a, int64_t kk, Me<FP64> &m
         const dbl4 bp = first ? nh : m.p, bv = first ? nv : m.v, bw = first ? nw : m.w;
         hit = pair_64(ap, av, aw, bp, bv, bw, Sprev, prm, o);
     } else {
-        const float4 nl = a.spl_[kk];
+        const float4 nl = nb.l;
         const float4 ah = first ? m.p : nh, al = first ? m.l : nl, av = first ? m.v : nv,
                      aw = first ? m.w : nw;
         const float4 bh = first ? nh : m.p, bl = first ? nl : m.l, bv = first ? nv : m.v,
@@ -496,15 +523,14 @@ __device__ __noinline__ int64_t overflow_next(const Arrays &a, const PileStatic 
 }
 
 template <bool FP64>
-__global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
+__global__ void DEM_CONTACT_BOUNDS k_contact(Arrays a, Sizes z)
 {
     typedef typename CT<FP64>::P4 P4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int K = z.K;
-    // shared memory: [S of the previous slots (mixed), kSlotStage x block]
-    // [hit list, kHitCap x block] [partner ids of the previous slots, K x block]
-    float4 *s_slot = (float4 *)smem_raw;
-    int *s_hit = (int *)(s_slot + (FP64 ? 0 : kSlotStage * kContactBlock));
+    // shared memory: [hit list, kHitCap x block] [partner ids of the previous
+    // slots, K x block]
+    int *s_hit = (int *)smem_raw;
     int *s_prev = s_hit + kHitCap * kContactBlock;
     const int64_t k = (int64_t)blockIdx.x * kContactBlock + threadIdx.x;
     if (k >= z.N) return;
@@ -544,13 +570,7 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
         prm = {(float)S.kn, (float)S.kt, (float)S.cn, (float)S.ct, (float)S.mu_s,
                (float)S.mu_r, (float)S.mu_t, (float)S.w0, (float)S.h};
         const float4 *hp = a.hist32[par] + s0 * K + prevk;
-        float4 *myslot = s_slot + threadIdx.x;
-        for (int t = 0; t < m.nprev; ++t) {
-            const float4 e = hp[(int64_t)t * ns];
-            if (t < kSlotStage) myslot[t * kContactBlock] = e;
-            myprev[t * kContactBlock] = __float_as_int(e.w);
-        }
-        m.sslot = myslot;
+        for (int t = 0; t < m.nprev; ++t) myprev[t * kContactBlock] = __float_as_int(hp[(int64_t)t * ns].w);
         hprev = hp;
         hnew = a.hist32[par ^ 1] + s0 * K + kl;
         m.p = a.sph_[k];
@@ -570,18 +590,51 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
         const int32_t *hl = a.hits + s0 * kHitCap + kl;
         for (int e = 0; e < nh; ++e) myhit[e * kContactBlock] = hl[(int64_t)e * ns];
     }
-    int last = -1;
-    for (int e = 0;; ++e) {
-        int64_t kk;
-        if (listed) {
-            if (e >= nh) break;
-            kk = s0 + myhit[e * kContactBlock];
-        } else {
-            kk = overflow_next<FP64>(a, S, k, m.p, m.agg, m.tol, last);
+    typedef typename CT<FP64>::V V;
+    V Snone;
+    if constexpr (FP64) Snone = d3(0, 0, 0);
+    else Snone = f3(0, 0, 0);
+    if (listed) {
+#if DEM_CONTACT_PREFETCH
+        // partner data one hit ahead, and the S of the slot the next hit most
+        // likely matches (hits and slots are both in partner order)
+        Nb<FP64> cur, nxt;
+        if (nh > 0) load_nb<FP64>(a, s0 + myhit[0], cur);
+        for (int e = 0; e < nh; ++e) {
+            if (e + 1 < nh) load_nb<FP64>(a, s0 + myhit[(e + 1) * kContactBlock], nxt);
+            int spec = -1;
+            V Sspec = Snone;
+#if DEM_CONTACT_PREFETCH > 1
+            if (m.cursor < m.nprev) {
+                spec = m.cursor;
+                if constexpr (FP64) {
+                    const dbl4 sl = ((const dbl4 *)hprev)[(int64_t)spec * ns];
+                    Sspec = d3(sl.x, sl.y, sl.z);
+                } else {
+                    const float4 sl = ((const float4 *)hprev)[(int64_t)spec * ns];
+                    Sspec = f3(sl.x, sl.y, sl.z);
+                }
+            }
+#endif
+            process<FP64>(a, cur, m, myprev, hprev, hnew, ns, K, prm, spec, Sspec);
+            cur = nxt;
+        }
+#else
+        for (int e = 0; e < nh; ++e) {
+            Nb<FP64> nb;
+            load_nb<FP64>(a, s0 + myhit[e * kContactBlock], nb);
+            process<FP64>(a, nb, m, myprev, hprev, hnew, ns, K, prm, -1, Snone);
+        }
+#endif
+    } else {
+        for (int last = -1;;) {
+            const int64_t kk = overflow_next<FP64>(a, S, k, m.p, m.agg, m.tol, last);
             if (kk < 0) break;
             last = a.sorted[kk];
+            Nb<FP64> nb;
+            load_nb<FP64>(a, kk, nb);
+            process<FP64>(a, nb, m, myprev, hprev, hnew, ns, K, prm, -1, Snone);
         }
-        process<FP64>(a, kk, m, myprev, hprev, hnew, ns, K, prm);
     }
     if constexpr (FP64) {
         a.ftc64[2 * k] = make_dbl4(m.F.x, m.F.y, m.F.z, 0.0);
@@ -594,10 +647,9 @@ __global__ void __launch_bounds__(kContactBlock) k_contact(Arrays a, Sizes z)
     if (m.flags) atomicOr(&a.pd[p].flags, m.flags);
 }
 
-static size_t contact_smem(bool fp64, int K)
+static size_t contact_smem(bool, int K)
 {
-    return sizeof(int) * (size_t)(K + kHitCap) * kContactBlock +
-           (fp64 ? 0 : sizeof(float4) * (size_t)kSlotStage * kContactBlock);
+    return sizeof(int) * (size_t)(K + kHitCap) * kContactBlock;
 }
 
 cudaError_t contact_setup(bool fp64, int K)

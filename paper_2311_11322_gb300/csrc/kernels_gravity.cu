@@ -17,6 +17,19 @@
 // A pile with several j-ranges writes one partial per (range, sphere), the
 // range's FP64 sum rounded to FP32 (one more rounding of a sum of ~2,000
 // terms), and k_grav_combine adds them in FP64 in range order (deterministic).
+//
+// Symmetric form (mixed path, default).  The pair term is antisymmetric
+// (Newton's third law): F_ij = -F_ji.  The pile is cut into tiles of 512
+// spheres; a work item is a pair of tiles (a, b), a < b, and evaluates each of
+// its 512 x 512 pairs once, adding the term to sphere i of tile a and its
+// negative to sphere j of tile b.  Each warp keeps 128 i-spheres in registers
+// (4 per lane) and passes 32 j-spheres round the warp by register shuffles,
+// each j carrying its own running sum, so a j-sphere visits all 128 i-spheres
+// of the warp in 32 steps; per pair this costs 16 FP32 instructions and one
+// reciprocal square root where the one-sided form needs 24 and two.  Items
+// (a, a) take the one-sided form.  Every item writes its i-sums (one per b)
+// and j-sums (one per a) as FP32 partials; k_grav_combine_sym adds a sphere's
+// partials in FP64 in tile order (deterministic).
 #include "dem_internal.h"
 #include "devmath.cuh"
 
@@ -423,6 +436,294 @@ __global__ void __launch_bounds__(BS) k_gravity64(Arrays a, Sizes z)
     }
 }
 
+// ---------------------------------------------------------------- symmetric form
+constexpr int kSymBS = 128, kSymIB = 4, kSymTile = kSymBS * kSymIB;   // 512 spheres per tile
+// launch bounds of the symmetric kernel (optionally with a minimum number of
+// resident blocks per SM, which caps its registers)
+#ifdef DEM_GSYM_MINB
+#define DEM_GSYM_BOUNDS __launch_bounds__(kSymBS, DEM_GSYM_MINB)
+#else
+#define DEM_GSYM_BOUNDS __launch_bounds__(kSymBS)
+#endif
+
+// Partial slots of pile p: i-sums of tile pair (a, b) at [b][i], j-sums at
+// [T + a][j], rows of ns spheres from gpart_base[p].
+__device__ __forceinline__ int64_t sym_slot(const Arrays &a, int p, int64_t ns, int64_t row, int64_t i)
+{
+    return a.gpart_base[p] + row * ns + i;
+}
+
+// One step of the ring: the lane's 4 i-spheres against the j-sphere it holds.
+template <bool MASK>
+__device__ __forceinline__ void sym_pairs(const float4 &pj, int aj, const float4 (&xi)[kSymIB],
+                                          const float (&nm)[kSymIB], const int (&ai)[kSymIB],
+                                          float (&ax)[kSymIB], float (&ay)[kSymIB],
+                                          float (&az)[kSymIB], float &fx, float &fy, float &fz,
+                                          float eps2)
+{
+#pragma unroll
+    for (int k = 0; k < kSymIB; ++k) {
+        const float dx = pj.x - xi[k].x, dy = pj.y - xi[k].y, dz = pj.z - xi[k].z;
+        const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+        const float inv = rsqrtf(r2);
+        const float inv3 = (inv * inv) * inv;
+        float si = pj.w * inv3, sj = nm[k] * inv3;
+        if (MASK && aj == ai[k]) si = sj = 0.f;
+        ax[k] = fmaf(dx, si, ax[k]);
+        ay[k] = fmaf(dy, si, ay[k]);
+        az[k] = fmaf(dz, si, az[k]);
+        fx = fmaf(dx, sj, fx);
+        fy = fmaf(dy, sj, fy);
+        fz = fmaf(dz, sj, fz);
+    }
+}
+
+// 32 ring steps over one chunk of 32 j-spheres (one per lane at the start,
+// back in its lane at the end with the sum over the warp's 128 i-spheres).
+template <bool MASK>
+__device__ __forceinline__ float4 sym_ring(float4 pj, int aj, const float4 (&xi)[kSymIB],
+                                           const float (&nm)[kSymIB], const int (&ai)[kSymIB],
+                                           float (&ax)[kSymIB], float (&ay)[kSymIB],
+                                           float (&az)[kSymIB], float eps2)
+{
+    const int src = (threadIdx.x + 1) & 31;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+#pragma unroll 4
+    for (int s = 0; s < 32; ++s) {
+        sym_pairs<MASK>(pj, aj, xi, nm, ai, ax, ay, az, fx, fy, fz, eps2);
+        pj.x = __shfl_sync(0xffffffffu, pj.x, src);
+        pj.y = __shfl_sync(0xffffffffu, pj.y, src);
+        pj.z = __shfl_sync(0xffffffffu, pj.z, src);
+        pj.w = __shfl_sync(0xffffffffu, pj.w, src);
+        fx = __shfl_sync(0xffffffffu, fx, src);
+        fy = __shfl_sync(0xffffffffu, fy, src);
+        fz = __shfl_sync(0xffffffffu, fz, src);
+        if (MASK) aj = __shfl_sync(0xffffffffu, aj, src);
+    }
+    return make_float4(fx, fy, fz, 0.f);
+}
+
+// Packed ring (unmasked tile pairs): each lane holds two j-spheres, packed
+// into the two halves of 64-bit registers, and its 4 i-spheres duplicated into
+// both halves, so one f32x2 instruction evaluates the same step of two pairs.
+// A chunk is 64 j-spheres (j and j + 32 in lane l).  The i-sums are kept per
+// half and added at the end of the item; the j-sums travel with their j.
+__device__ __forceinline__ void sym_ring2(const float4 &pa, const float4 &pb,
+                                          const f2_t (&xx)[kSymIB], const f2_t (&xy)[kSymIB],
+                                          const f2_t (&xz)[kSymIB], const f2_t (&nm2)[kSymIB],
+                                          f2_t (&qx)[kSymIB], f2_t (&qy)[kSymIB], f2_t (&qz)[kSymIB],
+                                          f2_t e2, float4 &fa, float4 &fb)
+{
+    const int src = (threadIdx.x + 1) & 31;
+    f2_t jx = f2_pack(pa.x, pb.x), jy = f2_pack(pa.y, pb.y), jz = f2_pack(pa.z, pb.z),
+         jm = f2_pack(pa.w, pb.w);
+    f2_t fx = f2_pack(0.f, 0.f), fy = fx, fz = fx;
+#pragma unroll 2
+    for (int s = 0; s < 32; ++s) {
+#pragma unroll
+        for (int k = 0; k < kSymIB; ++k) {
+            const f2_t dx = f2_sub(jx, xx[k]), dy = f2_sub(jy, xy[k]), dz = f2_sub(jz, xz[k]);
+            const f2_t r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_fma(dx, dx, e2)));
+            float ra, rb;
+            f2_unpack(r2, ra, rb);
+            const f2_t inv = f2_pack(rsqrtf(ra), rsqrtf(rb));
+            const f2_t inv3 = f2_mul(f2_mul(inv, inv), inv);
+            const f2_t si = f2_mul(jm, inv3), sj = f2_mul(nm2[k], inv3);
+            qx[k] = f2_fma(dx, si, qx[k]);
+            qy[k] = f2_fma(dy, si, qy[k]);
+            qz[k] = f2_fma(dz, si, qz[k]);
+            fx = f2_fma(dx, sj, fx);
+            fy = f2_fma(dy, sj, fy);
+            fz = f2_fma(dz, sj, fz);
+        }
+        jx = __shfl_sync(0xffffffffu, jx, src);
+        jy = __shfl_sync(0xffffffffu, jy, src);
+        jz = __shfl_sync(0xffffffffu, jz, src);
+        jm = __shfl_sync(0xffffffffu, jm, src);
+        fx = __shfl_sync(0xffffffffu, fx, src);
+        fy = __shfl_sync(0xffffffffu, fy, src);
+        fz = __shfl_sync(0xffffffffu, fz, src);
+    }
+    float ax, bx, ay, by, az, bz;
+    f2_unpack(fx, ax, bx);
+    f2_unpack(fy, ay, by);
+    f2_unpack(fz, az, bz);
+    fa = make_float4(ax, ay, az, 0.f);
+    fb = make_float4(bx, by, bz, 0.f);
+}
+
+// Work item (pile, tile a, tile b): the symmetric pass for a < b, the
+// one-sided pass over the tile itself for a == b.  sp/sag: tile b staged in
+// shared memory; sj: per-warp j-sums.
+__device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, float4 *sp, int *sag,
+                                                float4 *sj)
+{
+    const int p = it.x;
+    if (a.enabled[p] == 0 || a.pd[p].failed) return;
+    const PileStatic &S = a.ps[p];
+    const int64_t s0 = S.s0;
+    const int ns = (int)S.ns;
+    const int T = a.gnchunk[p];
+    const int ta = it.y, tb = it.z;
+    const bool diag = ta == tb;
+    const float eps2 = (float)S.eps2;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int jb0 = tb * kSymTile;
+    const int nj = min(kSymTile, ns - jb0);
+    for (int m = threadIdx.x; m < kSymTile; m += kSymBS) {
+        const int j = jb0 + m;
+        sp[m] = j < ns ? a.gpos32[s0 + j] : make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.f);
+        sag[m] = j < ns ? a.sph_agg[s0 + j] : -1;
+    }
+    float4 xi[kSymIB];
+    float nm[kSymIB];
+    int ai[kSymIB];
+    float ax[kSymIB], ay[kSymIB], az[kSymIB];
+    const int i0 = ta * kSymTile + w * (32 * kSymIB) + l;
+#pragma unroll
+    for (int k = 0; k < kSymIB; ++k) {
+        const int i = i0 + 32 * k;
+        const bool ok = i < ns;
+        xi[k] = ok ? a.gpos32[s0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        ai[k] = ok ? a.sph_agg[s0 + i] : -2;
+        nm[k] = -xi[k].w;
+        ax[k] = ay[k] = az[k] = 0.f;
+    }
+    // an aggregate can span the two tiles only if it spans their boundary
+    const bool masked = diag || a.sph_agg[s0 + (int64_t)ta * kSymTile + kSymTile - 1] == a.sph_agg[s0 + jb0];
+    __syncthreads();
+    if (diag) {
+        for (int jj = 0; jj < nj; ++jj) {
+            const float4 pj = sp[jj];
+            const int aj = sag[jj];
+#pragma unroll
+            for (int k = 0; k < kSymIB; ++k) {
+                const float dx = pj.x - xi[k].x, dy = pj.y - xi[k].y, dz = pj.z - xi[k].z;
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+                const float inv = rsqrtf(r2);
+                float si = (pj.w * inv) * (inv * inv);
+                si = aj == ai[k] ? 0.f : si;
+                ax[k] = fmaf(dx, si, ax[k]);
+                ay[k] = fmaf(dy, si, ay[k]);
+                az[k] = fmaf(dz, si, az[k]);
+            }
+        }
+    } else if (masked) {
+        for (int c = 0; c * 32 < nj; ++c) {
+            const float4 pj = sp[c * 32 + l];
+            const int aj = sag[c * 32 + l];
+            sj[w * kSymTile + c * 32 + l] = sym_ring<true>(pj, aj, xi, nm, ai, ax, ay, az, eps2);
+        }
+    } else {
+        f2_t xx[kSymIB], xy[kSymIB], xz[kSymIB], nm2[kSymIB], qx[kSymIB], qy[kSymIB], qz[kSymIB];
+        const f2_t zero2 = f2_pack(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < kSymIB; ++k) {
+            xx[k] = f2_pack(xi[k].x, xi[k].x);
+            xy[k] = f2_pack(xi[k].y, xi[k].y);
+            xz[k] = f2_pack(xi[k].z, xi[k].z);
+            nm2[k] = f2_pack(nm[k], nm[k]);
+            qx[k] = qy[k] = qz[k] = zero2;
+        }
+        const f2_t e2 = f2_pack(eps2, eps2);
+        for (int c = 0; c * 64 < nj; ++c) {
+            float4 fa, fb;
+            sym_ring2(sp[c * 64 + l], sp[c * 64 + 32 + l], xx, xy, xz, nm2, qx, qy, qz, e2, fa, fb);
+            sj[w * kSymTile + c * 64 + l] = fa;
+            sj[w * kSymTile + c * 64 + 32 + l] = fb;
+        }
+#pragma unroll
+        for (int k = 0; k < kSymIB; ++k) {
+            float lo, hi;
+            f2_unpack(qx[k], lo, hi);
+            ax[k] = lo + hi;
+            f2_unpack(qy[k], lo, hi);
+            ay[k] = lo + hi;
+            f2_unpack(qz[k], lo, hi);
+            az[k] = lo + hi;
+        }
+    }
+    if (!diag) {
+        __syncthreads();
+        for (int m = threadIdx.x; m < nj; m += kSymBS) {
+            const float4 u0 = sj[m], u1 = sj[kSymTile + m], u2 = sj[2 * kSymTile + m],
+                         u3 = sj[3 * kSymTile + m];
+            const float fx = ((u0.x + u1.x) + u2.x) + u3.x, fy = ((u0.y + u1.y) + u2.y) + u3.y,
+                        fz = ((u0.z + u1.z) + u2.z) + u3.z;
+            ((float4 *)a.gpart)[sym_slot(a, p, ns, T + ta, jb0 + m)] = make_float4(fx, fy, fz, 0.f);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kSymIB; ++k) {
+        const int i = i0 + 32 * k;
+        if (i >= ns) continue;
+        if (T == 1) {
+            const double gm = S.G * a.m64[s0 + i];
+            a.fg[s0 + i] = make_dbl4(gm * ax[k], gm * ay[k], gm * az[k], 0.0);
+        } else {
+            ((float4 *)a.gpart)[sym_slot(a, p, ns, tb, i)] = make_float4(ax[k], ay[k], az[k], 0.f);
+        }
+    }
+}
+
+__global__ void DEM_GSYM_BOUNDS k_gravity32s(Arrays a, Sizes z)
+{
+    __shared__ float4 sp[kSymTile];
+    __shared__ int sag[kSymTile];
+    __shared__ float4 sj[4 * kSymTile];
+    __shared__ int next;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) next = atomicAdd(a.gcounter, 1);
+        __syncthreads();
+        const int item = next;
+        if (item >= z.GI) return;
+        gravity32s_item(a, a.gitems[item], sp, sag, sj);
+    }
+}
+
+// Running float-float sum (TwoSum of each term, rounding errors collected in
+// the low word): the FP32 partials of a sphere are added with ~FP64 accuracy
+// on the FP32 units (the FP64 units are ~60 times slower on this part).
+struct FFSum {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        float s, e;
+        two_sum(hi, v, s, e);
+        hi = s;
+        lo += e;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Sphere x of tile t: its i-sums of items (t, b), b >= t, then its j-sums of
+// items (a, t), a < t, in that fixed order.
+__global__ void k_grav_combine_sym(Arrays a, Sizes z)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= z.N) return;
+    int p = a.sph_pile[i];
+    if (a.enabled[p] == 0 || a.pd[p].failed) return;
+    const int T = a.gnchunk[p];
+    if (T <= 1) return;
+    const PileStatic &S = a.ps[p];
+    const int64_t il = i - S.s0;
+    const int t = (int)(il / kSymTile);
+    const float4 *gp = (const float4 *)a.gpart;
+    FFSum sx, sy, sz;
+    for (int b = t; b < T; ++b) {
+        const float4 v = gp[sym_slot(a, p, S.ns, b, il)];
+        sx.add(v.x); sy.add(v.y); sz.add(v.z);
+    }
+    for (int r = 0; r < t; ++r) {
+        const float4 v = gp[sym_slot(a, p, S.ns, T + r, il)];
+        sx.add(v.x); sy.add(v.y); sz.add(v.z);
+    }
+    const double gm = S.G * a.m64[i];
+    a.fg[i] = make_dbl4(gm * sx.value(), gm * sy.value(), gm * sz.value(), 0.0);
+}
+
 // Sum the j-range partials of piles that were split, in range order.
 template <bool FP64>
 __global__ void k_grav_combine(Arrays a, Sizes z)
@@ -486,17 +787,29 @@ static int occ(bool fp64, bool pack)
     return n;
 }
 
-int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack)
+int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym)
 {
+    if (sym && !fp64) {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s, kSymBS, 0);
+        return n;
+    }
     if (block == 64) return ib == 1 ? occ<64, 1>(fp64, pack) : ib == 2 ? occ<64, 2>(fp64, pack) : occ<64, 4>(fp64, pack);
     if (block == 128) return ib == 1 ? occ<128, 1>(fp64, pack) : ib == 2 ? occ<128, 2>(fp64, pack) : occ<128, 4>(fp64, pack);
     return ib == 1 ? occ<256, 1>(fp64, pack) : ib == 2 ? occ<256, 2>(fp64, pack) : occ<256, 4>(fp64, pack);
 }
 
 void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int ib, bool pack,
-                    cudaStream_t st)
+                    bool sym, cudaStream_t st)
 {
     if (z.GI == 0) return;
+    if (sym && !fp64) {
+        int64_t nb = z.GB > 0 && z.GB < z.GI ? z.GB : z.GI;
+        cudaMemsetAsync(a.gcounter, 0, sizeof(int32_t), st);
+        k_gravity32s<<<(unsigned)nb, kSymBS, 0, st>>>(a, z);
+        if (z.GP > 0) k_grav_combine_sym<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+        return;
+    }
     if (block == 64 && ib == 1) launch_g<64, 1>(a, z, fp64, pack, st);
     else if (block == 64 && ib == 2) launch_g<64, 2>(a, z, fp64, pack, st);
     else if (block == 64 && ib == 4) launch_g<64, 4>(a, z, fp64, pack, st);

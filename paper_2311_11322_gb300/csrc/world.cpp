@@ -62,6 +62,7 @@ struct dem_world {
     int64_t grav_jchunk = 0;          // > 0: fixed j-range length per work item
     double grav_item = 1048576.0;     // else: target interactions per work item
     bool grav_pack = false;           // packed f32x2 pair terms (even grav_ib)
+    bool grav_sym = true;             // mixed path: symmetric tile-pair form
     int sm_count = 0;
     double cell_factor = 1.0;
     double skin_frac = 0.1;           // neighbour-list skin / largest radius
@@ -228,9 +229,41 @@ struct GravPlan {
     int64_t gp = 0;
 };
 
+bool use_sym(const dem_world *w) { return w->grav_sym && w->precision == DEM_MIXED; }
+
 GravPlan plan_gravity(const dem_world *w)
 {
     GravPlan g;
+    if (use_sym(w)) {
+        // items: every pair of 512-sphere tiles (a, b), a <= b; partial rows
+        // [b][i] and [T + a][j] (2 T rows of ns) for piles with more than one tile
+        struct It { int4 v; int64_t cost; };
+        std::vector<It> its;
+        for (size_t p = 0; p < w->piles.size(); ++p) {
+            const PileHost &q = w->piles[p];
+            const int64_t T = (q.ns + kGravSymTile - 1) / kGravSymTile;
+            if (q.P.G == 0.0) {
+                g.nch.push_back(1);
+                g.base.push_back(-1);
+                continue;
+            }
+            g.nch.push_back((int32_t)T);
+            if (T > 1) {
+                g.base.push_back(g.gp);
+                g.gp += 2 * T * q.ns;
+            } else {
+                g.base.push_back(-1);
+            }
+            for (int64_t ta = 0; ta < T; ++ta)
+                for (int64_t tb = ta; tb < T; ++tb) {
+                    int64_t nb = std::min<int64_t>(kGravSymTile, q.ns - tb * kGravSymTile);
+                    its.push_back({make_int4((int)p, (int)ta, (int)tb, 0), nb});
+                }
+        }
+        std::stable_sort(its.begin(), its.end(), [](const It &x, const It &y) { return x.cost > y.cost; });
+        for (auto &x : its) g.items.push_back(x.v);
+        return g;
+    }
     int BI = w->grav_block * w->grav_ib;
     struct It { int4 v; int64_t cost; };
     std::vector<It> its;
@@ -377,7 +410,8 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
         CU(cudaGetDevice(&dev));
         CU(cudaDeviceGetAttribute(&w->sm_count, cudaDevAttrMultiProcessorCount, dev));
     }
-    int bps = gravity_blocks_per_sm(w->precision == DEM_FP64, w->grav_block, w->grav_ib, w->grav_pack);
+    int bps = gravity_blocks_per_sm(w->precision == DEM_FP64, w->grav_block, w->grav_ib, w->grav_pack,
+                                    use_sym(w));
     CU(cudaGetLastError());
     CU(contact_setup(w->precision == DEM_FP64, w->K));
     w->Z.GB = (int64_t)std::max(1, bps) * w->sm_count;
@@ -414,7 +448,9 @@ void enqueue_phase(dem_world *w, int ph)
     case DEM_K_CELL_ORDER: launch_cell_order(a, z, st); break;
     case DEM_K_GATHER: launch_gather(a, z, d, st); break;
     case DEM_K_CONTACT: launch_contact(a, z, d, w->K, st); break;
-    case DEM_K_GRAVITY: launch_gravity(a, z, d, w->grav_block, w->grav_ib, w->grav_pack, st); break;
+    case DEM_K_GRAVITY:
+        launch_gravity(a, z, d, w->grav_block, w->grav_ib, w->grav_pack, use_sym(w), st);
+        break;
     case DEM_K_AGG_END: launch_agg_end(a, z, d, st); break;
     case DEM_K_PILE_END: launch_pile_end(a, z, st); break;
     default: break;
@@ -1269,6 +1305,8 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
         w->grav_jchunk = (int64_t)value;
     } else if (k == "grav_pack") {
         w->grav_pack = value != 0.0;
+    } else if (k == "grav_sym") {
+        w->grav_sym = value != 0.0;
     } else if (k == "grav_item") {
         if (!(value >= 1024.0)) return fail(w, DEM_ERR_ARG, "grav_item must be >= 1024");
         w->grav_item = value;
@@ -1295,22 +1333,24 @@ dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
 {
     if (!w || trial_steps < 1) return DEM_ERR_ARG;
     if (w->piles.empty()) return DEM_OK;
-    struct Cand { int blk, ib; double item; bool pack; };
+    struct Cand { int blk, ib; double item; bool pack, sym; };
     std::vector<Cand> cands;
+    if (w->precision == DEM_MIXED) cands.push_back({128, 4, 1048576.0, false, true});
     for (int blk : {64, 128, 256})
         for (int ib : {1, 2, 4})
             for (double item : {262144.0, 1048576.0, 4194304.0}) {
-                cands.push_back({blk, ib, item, false});
-                if (ib % 2 == 0) cands.push_back({blk, ib, item, true});
+                cands.push_back({blk, ib, item, false, false});
+                if (ib % 2 == 0) cands.push_back({blk, ib, item, true, false});
             }
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     double best = 1e300;
-    Cand bc = {w->grav_block, w->grav_ib, w->grav_item, w->grav_pack};
+    Cand bc = {w->grav_block, w->grav_ib, w->grav_item, w->grav_pack, w->grav_sym};
     w->grav_jchunk = 0;
     for (auto &c : cands) {
         w->grav_block = c.blk; w->grav_ib = c.ib; w->grav_item = c.item; w->grav_pack = c.pack;
+        w->grav_sym = c.sym;
         w->graph_valid = false;
         dem_status s = prepare(w);
         if (s != DEM_OK) return s;
@@ -1329,6 +1369,7 @@ dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     w->grav_block = bc.blk; w->grav_ib = bc.ib; w->grav_item = bc.item; w->grav_pack = bc.pack;
+    w->grav_sym = bc.sym;
     w->graph_valid = false;
     // then the cell edge (contact search), with the chosen gravity shape
     double bf = w->cell_factor;
