@@ -106,6 +106,7 @@ struct Arrays {
     // aggregates
     int32_t *agg_first, *agg_count, *agg_pile;
     double *M, *I, *Iinv;          // [A], [A][9], [A][9]
+    float *I32;                    // mixed: [A][18] FP32 copies of I and I^-1
     double *r, *v, *q, *wb, *acc, *torque;   // [A][3], q [A][4]
     AggRecMixed *rec32;
     AggRec64 *rec64;

@@ -79,6 +79,21 @@ __device__ __forceinline__ ff ff_dot3(const float *Rh, const float *Rl, float bx
     return r;
 }
 
+// Running float-float sum (TwoSum of each term, rounding errors collected in
+// the low word): FP32 terms added with ~FP64 accuracy on the FP32 units (the
+// FP64 units of this part are ~60 times slower).
+struct FFSum {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        float s, e;
+        two_sum(hi, v, s, e);
+        hi = s;
+        lo += e;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Split a double into hi + lo floats.
 __host__ __device__ __forceinline__ void split_d(double x, float &hi, float &lo)
 {
@@ -129,6 +144,25 @@ __device__ __forceinline__ double3 mat_mul(const double *A, double3 x)
 __device__ __forceinline__ double3 mat_tmul(const double *A, double3 x)
 {
     return d3(A[0] * x.x + A[3] * x.y + A[6] * x.z, A[1] * x.x + A[4] * x.y + A[7] * x.z,
+              A[2] * x.x + A[5] * x.y + A[8] * x.z);
+}
+
+// FP32 copies of the above (increments and derivatives of the mixed path).
+__device__ __forceinline__ void quat_to_Rf(const float *q, float *R)
+{
+    float w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+__device__ __forceinline__ float3 mat_mulf(const float *A, float3 x)
+{
+    return f3(A[0] * x.x + A[1] * x.y + A[2] * x.z, A[3] * x.x + A[4] * x.y + A[5] * x.z,
+              A[6] * x.x + A[7] * x.y + A[8] * x.z);
+}
+__device__ __forceinline__ float3 mat_tmulf(const float *A, float3 x)
+{
+    return f3(A[0] * x.x + A[3] * x.y + A[6] * x.z, A[1] * x.x + A[4] * x.y + A[7] * x.z,
               A[2] * x.x + A[5] * x.y + A[8] * x.z);
 }
 

@@ -682,23 +682,8 @@ __global__ void DEM_GSYM_BOUNDS k_gravity32s(Arrays a, Sizes z)
     }
 }
 
-// Running float-float sum (TwoSum of each term, rounding errors collected in
-// the low word): the FP32 partials of a sphere are added with ~FP64 accuracy
-// on the FP32 units (the FP64 units are ~60 times slower on this part).
-struct FFSum {
-    float hi = 0.f, lo = 0.f;
-    __device__ __forceinline__ void add(float v)
-    {
-        float s, e;
-        two_sum(hi, v, s, e);
-        hi = s;
-        lo += e;
-    }
-    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-
 // Sphere x of tile t: its i-sums of items (t, b), b >= t, then its j-sums of
-// items (a, t), a < t, in that fixed order.
+// items (a, t), a < t, in that fixed order, as float-float sums (FFSum).
 __global__ void k_grav_combine_sym(Arrays a, Sizes z)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

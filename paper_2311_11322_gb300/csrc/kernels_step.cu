@@ -84,6 +84,43 @@ __device__ void free_rotate(double *q, double3 &wb, const double *I, const doubl
     wb = d3(y[4], y[5], y[6]);
 }
 
+// Mixed path: the same RK4 step with the stage derivatives evaluated in FP32
+// (from FP32 copies of q, w and the inertia tensor) and the step's increment
+// added to the FP64 state, which is then renormalised in FP64.  The increment
+// is O(h |w|), so its FP32 rounding is ~1e-7 of the change per step, far below
+// the FP32 error of the forces that drive it.
+__device__ __forceinline__ void rot_rhs_f(const float *y, const float *I, const float *Iinv, float *dy)
+{
+    const float *q = y, *w = y + 4;
+    dy[0] = -0.5f * (q[1] * w[0] + q[2] * w[1] + q[3] * w[2]);
+    dy[1] = 0.5f * (q[0] * w[0] + q[2] * w[2] - q[3] * w[1]);
+    dy[2] = 0.5f * (q[0] * w[1] + q[3] * w[0] - q[1] * w[2]);
+    dy[3] = 0.5f * (q[0] * w[2] + q[1] * w[1] - q[2] * w[0]);
+    const float3 wv = f3(w[0], w[1], w[2]);
+    const float3 dw = mat_mulf(Iinv, -cross(wv, mat_mulf(I, wv)));
+    dy[4] = dw.x; dy[5] = dw.y; dy[6] = dw.z;
+}
+
+__device__ void free_rotate_mixed(double *q, double3 &wb, const float *I, const float *Iinv, float h)
+{
+    float y[7] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3],
+                  (float)wb.x, (float)wb.y, (float)wb.z};
+    float k1[7], k2[7], k3[7], k4[7], t[7];
+    rot_rhs_f(y, I, Iinv, k1);
+    for (int c = 0; c < 7; ++c) t[c] = y[c] + 0.5f * h * k1[c];
+    rot_rhs_f(t, I, Iinv, k2);
+    for (int c = 0; c < 7; ++c) t[c] = y[c] + 0.5f * h * k2[c];
+    rot_rhs_f(t, I, Iinv, k3);
+    for (int c = 0; c < 7; ++c) t[c] = y[c] + h * k3[c];
+    rot_rhs_f(t, I, Iinv, k4);
+    float d[7];
+    for (int c = 0; c < 7; ++c) d[c] = (h / 6.0f) * (k1[c] + 2.0f * k2[c] + 2.0f * k3[c] + k4[c]);
+    double q0 = q[0] + d[0], q1 = q[1] + d[1], q2 = q[2] + d[2], q3 = q[3] + d[3];
+    double inv = rsqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    q[0] = q0 * inv; q[1] = q1 * inv; q[2] = q2 * inv; q[3] = q3 * inv;
+    wb = d3(wb.x + d[4], wb.y + d[5], wb.z + d[6]);
+}
+
 // ---------------------------------------------------------------- step begin
 // Per aggregate: half kick of COM and spin with the stored a_A,n / N_A,n,
 // drift, torque-free rotation, then the record the sphere kernels read:
@@ -103,14 +140,39 @@ __global__ void k_agg_begin(Arrays a, Sizes z)
     double3 r = ld3(a.r + 3 * g), v = ld3(a.v + 3 * g), wb = ld3(a.wb + 3 * g);
     double3 acc = ld3(a.acc + 3 * g), N = ld3(a.torque + 3 * g);
     double R[9];
-    quat_to_R(q, R);
-    v = v + (0.5 * h) * acc;
-    wb = wb + (0.5 * h) * mat_mul(Iinv, mat_tmul(R, N));
-    r = r + h * v;
-    free_rotate(q, wb, I, Iinv, h);
-    quat_to_R(q, R);
-    double3 wpred_b = wb + (0.5 * h) * mat_mul(Iinv, mat_tmul(R, N));
-    double3 ws = mat_mul(R, wpred_b);
+    double3 ws;
+    float3 wsf;
+    if constexpr (FP64) {
+        quat_to_R(q, R);
+        v = v + (0.5 * h) * acc;
+        wb = wb + (0.5 * h) * mat_mul(Iinv, mat_tmul(R, N));
+        r = r + h * v;
+        free_rotate(q, wb, I, Iinv, h);
+        quat_to_R(q, R);
+        double3 wpred_b = wb + (0.5 * h) * mat_mul(Iinv, mat_tmul(R, N));
+        ws = mat_mul(R, wpred_b);
+        wsf = f3(0.f, 0.f, 0.f);
+    } else {
+        // spin kicks and the rotor's stage derivatives are increments: FP32
+        const float *I32 = a.I32 + 18 * g, *Iinv32 = I32 + 9;
+        const float hf = (float)h;
+        float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
+        float Rf[9];
+        quat_to_Rf(qf, Rf);
+        const float3 Nf = f3((float)N.x, (float)N.y, (float)N.z);
+        const float3 dw = (0.5f * hf) * mat_mulf(Iinv32, mat_tmulf(Rf, Nf));
+        v = v + (0.5 * h) * acc;
+        wb = d3(wb.x + dw.x, wb.y + dw.y, wb.z + dw.z);
+        r = r + h * v;
+        free_rotate_mixed(q, wb, I32, Iinv32, hf);
+        quat_to_R(q, R);
+        for (int c = 0; c < 4; ++c) qf[c] = (float)q[c];
+        quat_to_Rf(qf, Rf);
+        const float3 wpred = f3((float)wb.x, (float)wb.y, (float)wb.z) +
+                             (0.5f * hf) * mat_mulf(Iinv32, mat_tmulf(Rf, Nf));
+        wsf = mat_mulf(Rf, wpred);
+        ws = d3(0, 0, 0);
+    }
     st3(a.r + 3 * g, r);
     st3(a.v + 3 * g, v);
     st3(a.wb + 3 * g, wb);
@@ -150,7 +212,7 @@ __global__ void k_agg_begin(Arrays a, Sizes z)
         split_d(c.y, rec.ch[1], rec.cl[1]);
         split_d(c.z, rec.ch[2], rec.cl[2]);
         rec.vb[0] = (float)vb.x; rec.vb[1] = (float)vb.y; rec.vb[2] = (float)vb.z;
-        rec.w[0] = (float)ws.x; rec.w[1] = (float)ws.y; rec.w[2] = (float)ws.z;
+        rec.w[0] = wsf.x; rec.w[1] = wsf.y; rec.w[2] = wsf.z;
         rec.pad[0] = rec.pad[1] = 0.f;
         a.rec32[g] = rec;
     }
@@ -610,71 +672,107 @@ __global__ void k_agg_end(Arrays a, Sizes z)
     const double h = S.h;
     int64_t i0 = S.s0 + a.agg_first[g];
     int n = a.agg_count[g];
-    double3 Fc = d3(0, 0, 0), Nc = d3(0, 0, 0), Fg = d3(0, 0, 0), Ng = d3(0, 0, 0);
+    double3 Fc, Nc, Fg, Ng;
     double3 Fe = d3(0, 0, 0), Ne = d3(0, 0, 0);
     const bool planet = S.ext_mass > 0;
     double3 Pp = planet ? ld3(D.P_pos) : d3(0, 0, 0);
     double3 O = ld3(D.O);
     const int32_t *poh = a.pos_of_home[D.parity ^ 1];
-    for (int t = 0; t < n; ++t) {
-        int64_t i = i0 + t;
-        double3 lever, fc, tc, pos;
-        if (FP64) {
-            const AggRec64 &rec = a.rec64[g];
+    if constexpr (FP64) {
+        Fc = Nc = Fg = Ng = d3(0, 0, 0);
+        const AggRec64 &rec = a.rec64[g];
+        for (int t = 0; t < n; ++t) {
+            int64_t i = i0 + t;
             const double *b = a.b64 + 3 * i;
-            lever = mat_mul(rec.R, d3(b[0], b[1], b[2]));
-            int64_t ks = S.s0 + poh[i];
-            dbl4 f = a.ftc64[2 * ks], tq = a.ftc64[2 * ks + 1];
-            fc = d3(f.x, f.y, f.z);
-            tc = d3(tq.x, tq.y, tq.z);
-            if (planet) pos = O + expand_64(rec, b);
-        } else {
-            const AggRecMixed &rec = a.rec32[g];
-            float4 bh = a.bh[i];
-            lever = d3(rec.Rh[0] * bh.x + rec.Rh[1] * bh.y + rec.Rh[2] * bh.z,
-                       rec.Rh[3] * bh.x + rec.Rh[4] * bh.y + rec.Rh[5] * bh.z,
-                       rec.Rh[6] * bh.x + rec.Rh[7] * bh.y + rec.Rh[8] * bh.z);
-            int64_t ks = S.s0 + poh[i];
-            float4 f = a.ftc32[2 * ks], tq = a.ftc32[2 * ks + 1];
-            fc = d3(f.x, f.y, f.z);
-            tc = d3(tq.x, tq.y, tq.z);
+            const double3 lever = mat_mul(rec.R, d3(b[0], b[1], b[2]));
+            const int64_t ks = S.s0 + poh[i];
+            const dbl4 f = a.ftc64[2 * ks], tq = a.ftc64[2 * ks + 1];
+            const double3 fc = d3(f.x, f.y, f.z), tc = d3(tq.x, tq.y, tq.z);
+            const dbl4 gg = a.fg[i];
+            const double3 fg = d3(gg.x, gg.y, gg.z);
+            Fc = Fc + fc;
+            Nc = Nc + cross(lever, fc) + tc;
+            Fg = Fg + fg;
+            Ng = Ng + cross(lever, fg);
+            if (planet) {
+                const double3 d = Pp - (O + expand_64(rec, b));
+                const double inv = 1.0 / sqrt(dot(d, d));
+                const double3 fe = (S.G * S.ext_mass * a.m64[i] * inv * inv * inv) * d;
+                Fe = Fe + fe;
+                Ne = Ne + cross(lever, fe);
+            }
+        }
+    } else {
+        // per-sphere terms in FP32 (their inputs are FP32), sums float-float
+        FFSum s[12];
+        const AggRecMixed &rec = a.rec32[g];
+        float Rh[9];
+        for (int k = 0; k < 9; ++k) Rh[k] = rec.Rh[k];
+        for (int t = 0; t < n; ++t) {
+            int64_t i = i0 + t;
+            const float4 bh = a.bh[i];
+            const float3 lever = mat_mulf(Rh, f3(bh.x, bh.y, bh.z));
+            const int64_t ks = S.s0 + poh[i];
+            const float4 f = a.ftc32[2 * ks], tq = a.ftc32[2 * ks + 1];
+            const float3 fc = f3(f.x, f.y, f.z);
+            const float3 nc = cross(lever, fc) + f3(tq.x, tq.y, tq.z);
+            const dbl4 gg = a.fg[i];
+            const float3 fg = f3((float)gg.x, (float)gg.y, (float)gg.z);
+            const float3 ng = cross(lever, fg);
+            s[0].add(fc.x); s[1].add(fc.y); s[2].add(fc.z);
+            s[3].add(nc.x); s[4].add(nc.y); s[5].add(nc.z);
+            s[6].add(fg.x); s[7].add(fg.y); s[8].add(fg.z);
+            s[9].add(ng.x); s[10].add(ng.y); s[11].add(ng.z);
             if (planet) {
                 ff px, py, pz;
                 expand_mixed(rec, bh, a.bl[i], px, py, pz);
-                pos = O + d3((double)px.hi + (double)px.lo, (double)py.hi + (double)py.lo,
-                             (double)pz.hi + (double)pz.lo);
+                const double3 pos = O + d3((double)px.hi + (double)px.lo, (double)py.hi + (double)py.lo,
+                                           (double)pz.hi + (double)pz.lo);
+                const double3 d = Pp - pos;
+                const double inv = 1.0 / sqrt(dot(d, d));
+                const double3 fe = (S.G * S.ext_mass * a.m64[i] * inv * inv * inv) * d;
+                const double3 lv = d3(lever.x, lever.y, lever.z);
+                Fe = Fe + fe;
+                Ne = Ne + cross(lv, fe);
             }
         }
-        dbl4 gg = a.fg[i];
-        double3 fg = d3(gg.x, gg.y, gg.z);
-        Fc = Fc + fc;
-        Nc = Nc + cross(lever, fc) + tc;
-        Fg = Fg + fg;
-        Ng = Ng + cross(lever, fg);
-        if (planet) {
-            double3 d = Pp - pos;
-            double r2 = dot(d, d);
-            double inv = 1.0 / sqrt(r2);
-            double3 fe = (S.G * S.ext_mass * a.m64[i] * inv * inv * inv) * d;
-            Fe = Fe + fe;
-            Ne = Ne + cross(lever, fe);
-        }
+        Fc = d3(s[0].value(), s[1].value(), s[2].value());
+        Nc = d3(s[3].value(), s[4].value(), s[5].value());
+        Fg = d3(s[6].value(), s[7].value(), s[8].value());
+        Ng = d3(s[9].value(), s[10].value(), s[11].value());
     }
     double *o = a.out + 18 * g;
     st3(o + 0, Fc); st3(o + 3, Nc); st3(o + 6, Fg); st3(o + 9, Ng); st3(o + 12, Fe); st3(o + 15, Ne);
     double3 F = Fc + Fg + Fe, N = Nc + Ng + Ne;
-    double M = a.M[g];
-    double3 acc = d3(F.x / M, F.y / M, F.z / M);
+    const double invM = 1.0 / a.M[g];
+    double3 acc = invM * F;
     double q[4] = {a.q[4 * g], a.q[4 * g + 1], a.q[4 * g + 2], a.q[4 * g + 3]};
-    double R[9];
-    quat_to_R(q, R);
     double3 v = ld3(a.v + 3 * g) + (0.5 * h) * acc;
-    double3 wb = ld3(a.wb + 3 * g) + (0.5 * h) * mat_mul(a.Iinv + 9 * g, mat_tmul(R, N));
-    double3 dw = ld3(S.spin_inc);
-    if (dw.x != 0.0 || dw.y != 0.0 || dw.z != 0.0) {
-        double3 rel = ld3(a.r + 3 * g) - ld3(D.Rc);
-        v = v + cross(dw, rel);
-        wb = wb + mat_tmul(R, dw);
+    double3 wb = ld3(a.wb + 3 * g);
+    const double3 dwy = ld3(S.spin_inc);
+    const bool yorp = dwy.x != 0.0 || dwy.y != 0.0 || dwy.z != 0.0;
+    if constexpr (FP64) {
+        double R[9];
+        quat_to_R(q, R);
+        wb = wb + (0.5 * h) * mat_mul(a.Iinv + 9 * g, mat_tmul(R, N));
+        if (yorp) {
+            v = v + cross(dwy, ld3(a.r + 3 * g) - ld3(D.Rc));
+            wb = wb + mat_tmul(R, dwy);
+        }
+    } else {
+        // closing spin kick: an increment, FP32
+        const float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
+        float Rf[9];
+        quat_to_Rf(qf, Rf);
+        const float3 Nf = f3((float)N.x, (float)N.y, (float)N.z);
+        const float3 dw = (0.5f * (float)h) * mat_mulf(a.I32 + 18 * g + 9, mat_tmulf(Rf, Nf));
+        wb = d3(wb.x + dw.x, wb.y + dw.y, wb.z + dw.z);
+        if (yorp) {   // rigid-rotation increment of the whole pile, FP64 as the state
+            double R[9];
+            quat_to_R(q, R);
+            v = v + cross(dwy, ld3(a.r + 3 * g) - ld3(D.Rc));
+            wb = wb + mat_tmul(R, dwy);
+        }
     }
     st3(a.acc + 3 * g, acc);
     st3(a.torque + 3 * g, N);

@@ -176,6 +176,7 @@ void build_fields(dem_world *w)
         add((void **)&a.hist32[0], C_SPHK, 16, true);
         add((void **)&a.hist32[1], C_SPHK, 16, true);
         add((void **)&a.rec32, C_AGG, sizeof(AggRecMixed), false);
+        add((void **)&a.I32, C_AGG, 72, true);
     }
     add((void **)&a.agg_first, C_AGG, 4, true);
     add((void **)&a.agg_count, C_AGG, 4, true);
@@ -860,6 +861,15 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     UP(D.M + a0, M.data(), 8 * A);
     UP(D.I + 9 * a0, I.data(), 72 * A);
     UP(D.Iinv + 9 * a0, Iinv.data(), 72 * A);
+    if (w->precision == DEM_MIXED) {
+        std::vector<float> I32(18 * (size_t)A);
+        for (int a = 0; a < A; ++a)
+            for (int e = 0; e < 9; ++e) {
+                I32[18 * a + e] = (float)I[9 * a + e];
+                I32[18 * a + 9 + e] = (float)Iinv[9 * a + e];
+            }
+        UP(D.I32 + 18 * a0, I32.data(), 72 * A);
+    }
     UP(D.r + 3 * a0, r.data(), 24 * A);
     UP(D.v + 3 * a0, v.data(), 24 * A);
     UP(D.q + 4 * a0, q.data(), 32 * A);
@@ -1409,7 +1419,7 @@ size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contact
     sph += d ? (32 * 3 + 32 + 64) : (16 * 2 + 16 * 4 + 16 + 32);
     size_t sphk = d ? 2 * 32 : 2 * 16;
     size_t agg = 4 * 3 + 8 + 72 * 2 + 24 * 2 + 32 + 24 * 3 + 144 + 64 +
-                 (d ? sizeof(AggRec64) : sizeof(AggRecMixed));
+                 (d ? sizeof(AggRec64) : sizeof(AggRecMixed) + 72);
     int64_t cells = std::max<int64_t>(4 * n_spheres, 27) + kScanTile;
     size_t bytes = sph * (size_t)n_spheres + sphk * (size_t)n_spheres * (size_t)max_contacts +
                    agg * (size_t)n_agg + 8 * (size_t)cells + 4 * (size_t)(cells / kScanTile + 1) +
