@@ -87,8 +87,10 @@ __device__ __forceinline__ void force_law(V n, T x, T la, T lb, V va, V wa, V vb
     T uns = dot(u, n);
     V un = uns * n;
     V ut = u - un;
-    V FN = (-prm.kn * x) * n + prm.cn * un;
-    T FNm = qsqrt(dot(FN, FN));
+    // F_N is along n: its signed magnitude is -kn x + cn (u.n)
+    const T fn = prm.cn * uns - prm.kn * x;
+    V FN = fn * n;
+    T FNm = fabs(fn);
     T sn = dot(Sprev, n);
     V Sp = Sprev - sn * n;
     T Spm = qsqrt(dot(Sp, Sp)), Sprevm = qsqrt(dot(Sprev, Sprev));
@@ -125,7 +127,7 @@ __device__ __forceinline__ void force_law(V n, T x, T la, T lb, V va, V wa, V vb
 
 // Mixed precision pair: the overlap x = s_a + s_b - |d| is formed from
 // float-float positions and radii (exact differences by TwoSum, |d|^2 with
-// TwoProduct terms, one Newton correction of a correctly rounded sqrt), so x
+// TwoProduct terms, one Newton correction of the hardware square root), so x
 // keeps ~24 significant bits even when x << |d|; the rest of the law is FP32.
 __device__ __forceinline__ bool pair_mixed(float4 ah, float4 al, float4 av, float4 aw, float4 bh,
                                            float4 bl, float4 bv, float4 bw, float3 Sprev,
@@ -154,9 +156,12 @@ __device__ __forceinline__ bool pair_mixed(float4 ah, float4 al, float4 av, floa
     cr = __fmaf_rn(dhz, dlz, cr);
     float Dl = __fadd_rn(__fadd_rn(t1, t2), __fadd_rn(__fadd_rn(epx, epy), epz));
     Dl = __fmaf_rn(2.0f, cr, Dl);
-    float r = __fsqrt_rn(Dh);
-    if (!(r > 0.0f)) return false;
-    float inv = __frcp_rn(r);
+    // |d| = r + delta: r from the hardware reciprocal square root (a few ulp),
+    // delta its Newton correction from the exact remainder Dh - r^2 (one FMA)
+    // and the low part Dl, so the overlap below keeps ~24 bits of its own.
+    if (!(Dh > 0.0f)) return false;
+    const float inv = rsqrtf(Dh);
+    const float r = __fmul_rn(Dh, inv);
     float delta = __fmul_rn(__fadd_rn(__fmaf_rn(-r, r, Dh), Dl), __fmul_rn(0.5f, inv));
     float Sh, e;
     two_sum(ah.w, bh.w, Sh, e);
@@ -542,8 +547,23 @@ __global__ void DEM_CONTACT_BOUNDS k_contact(Arrays a, Sizes z)
     const int par = a.pd[p].parity;
     const int kl = (int)(k - s0);
     Me<FP64> m;
-    m.hl = a.sorted[k];
-    const int prevk = a.pos_of_home[par][s0 + m.hl];
+    // own sorted state first (independent loads); the home index is in the
+    // spin record's fourth word
+    if constexpr (FP64) {
+        m.p = a.dp_[k];
+        m.v = a.dv_[k];
+        m.w = a.dw_[k];
+        m.hl = (int)m.w.w;
+    } else {
+        m.p = a.sph_[k];
+        m.l = a.spl_[k];
+        m.v = a.sv_[k];
+        m.w = a.sw_[k];
+        m.hl = __float_as_int(m.w.w);
+    }
+    const int nh = a.hitn[k];
+    // the previous step's sorted position: unchanged unless this step re-sorted
+    const int prevk = a.pd[p].rebuild ? a.pos_of_home[par][s0 + m.hl] : kl;
     m.nprev = a.hist_n[par][s0 + prevk];
     m.nn = 0;
     m.cursor = 0;
@@ -558,9 +578,6 @@ __global__ void DEM_CONTACT_BOUNDS k_contact(Arrays a, Sizes z)
         for (int t = 0; t < m.nprev; ++t) myprev[t * kContactBlock] = (int)hp[(int64_t)t * ns].w;
         hprev = hp;
         hnew = a.hist64[par ^ 1] + s0 * K + kl;
-        m.p = a.dp_[k];
-        m.v = a.dv_[k];
-        m.w = a.dw_[k];
         m.agg = (int)m.v.w;
         m.tol = 0.f;
         m.skin = 0.0;
@@ -573,17 +590,12 @@ __global__ void DEM_CONTACT_BOUNDS k_contact(Arrays a, Sizes z)
         for (int t = 0; t < m.nprev; ++t) myprev[t * kContactBlock] = __float_as_int(hp[(int64_t)t * ns].w);
         hprev = hp;
         hnew = a.hist32[par ^ 1] + s0 * K + kl;
-        m.p = a.sph_[k];
-        m.l = a.spl_[k];
-        m.v = a.sv_[k];
-        m.w = a.sw_[k];
         m.agg = __float_as_int(m.v.w);
         m.tol = filter_tol(S, m.p);
         m.skin = 0.f;
         m.F = f3(0, 0, 0);
         m.T = f3(0, 0, 0);
     }
-    const int nh = a.hitn[k];
     const bool listed = nh <= kHitCap;
     int *myhit = s_hit + threadIdx.x;
     if (listed) {   // all hit indices first (independent loads), then the pairs
