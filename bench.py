@@ -69,8 +69,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--part", default="all", choices=["all", "contact"],
-                    help="contact: only the contact-pass roofline on the 1M-sphere lattice")
+    ap.add_argument("--no-e2-collapse", action="store_true")
+    ap.add_argument("--part", default="all", choices=["all", "contact", "e2"],
+                    help="contact: only the contact-pass roofline on the 1M-sphere lattice; "
+                         "e2: only the paper's 2e4-sphere profiling collapse")
     ap.add_argument("--contact-n", type=int, default=1_048_576)
     return ap.parse_args()
 
@@ -246,6 +248,55 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3):
             "n_spheres": N, "contacts_per_sphere": z / N,
             "algorithmic_bytes_per_launch": algo, "workload": "dense FCC tetrahedra lattice, "
             "1,048,576 spheres, overlaps 0.5% R, gravity off"}
+
+
+PHASES = {"aggregate": ("AGG_BEGIN", "PILE_BEGIN", "AGG_END", "PILE_END"),
+          "search_and_contact": ("KEYS", "SCAN", "SCATTER", "CELL_ORDER", "GATHER", "CONTACT"),
+          "gravity": ("GRAVITY",)}
+
+
+def run_e2_collapse(dem, W, steps=10, warmup=3):
+    """The paper's self-gravity profiling collapse (Sec. 3): 2e4 spheres of 50 m as free
+    spheres, mixed grain shapes, dumbbells and cubes, each one pile; sphere-steps/s, and
+    for the mixed population the share of the step per group of kernels (the paper's
+    profile groups: aggregate operations, neighbour search and contacts, gravity)."""
+    import torch
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = {}
+    for kind in ("spheres", "mixed", "dumbbell", "cube8"):
+        ic, p = W.e2_collapse(kind, seed=0)
+        with dem.World() as w:
+            pid = w.add_pile(ic, p)
+            st = torch.cuda.ExternalStream(w.stream)
+            for _ in range(warmup):
+                w.step_timed()
+            ms = []
+            for _ in range(steps):
+                with torch.cuda.stream(st):
+                    flush.zero_()
+                ms.append(w.step_timed()[0])
+            rec = {"n_aggregates": ic.n_agg, "ms_per_step": statistics.median(ms),
+                   "value": ic.n_sph / (statistics.median(ms) / 1e3), "unit": UNIT}
+            if kind == "mixed":
+                share = {}
+                for grp, names in PHASES.items():
+                    tot = 0.0
+                    for nm in names:
+                        w.set_timed_kernel(nm)
+                        w.step_timed()
+                        tot += statistics.median([w.step_timed()[1] for _ in range(3)])
+                    share[grp] = tot
+                w.set_timed_kernel(None)
+                step = statistics.median([w.step_timed()[0] for _ in range(3)])
+                rec["phase_ms"] = share
+                rec["phase_share"] = {k: v / step for k, v in share.items()}
+            out[kind] = rec
+    out["n_spheres"] = 20_000
+    out["paper_context"] = ("pkdgrav on 1 core, mixed-aggregate collapse of 2e4 spheres, 1e4 steps: "
+                            "1.8e4 s before and 6.4e3 s after the paper's aggregate bookkeeping "
+                            "(1.1e4 -> 3.1e4 sphere-steps/s); aggregate operations 65.4% -> 0.3% of "
+                            "the time (Sec. 3); tree gravity there, direct sum here")
+    return out
 
 
 def run_batched(dem, W, steps=5, n_piles=256):
@@ -429,6 +480,8 @@ def run_ours(args):
         out["batched"] = run_batched(dem, W)
     if rank == 0 and not args.no_serving:
         out["serving"] = run_serving(dem, W)
+    if rank == 0 and not args.no_e2_collapse:
+        out["e2_collapse"] = run_e2_collapse(dem, W)
     if not args.no_e2e:
         e = run_e2e(dem, W, ic, p, steps=args.steps)
         e_t = max_over_ranks(ic.n_sph * args.steps / e["value"], ws, device="cuda")
@@ -487,11 +540,24 @@ def run_contact_only(args):
     print(json.dumps({"part": "contact", "roofline_contact": r}), flush=True)
 
 
+def run_e2_only(args):
+    import torch
+    from paper_2311_11322_gb300 import dem
+    from paper_2311_11322_gb300 import workloads as W
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    print(json.dumps({"part": "e2", "e2_collapse": run_e2_collapse(dem, W, steps=args.steps,
+                                                                    warmup=args.warmup)}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.part == "contact":
         run_contact_only(a)
+    elif a.part == "e2":
+        run_e2_only(a)
     else:
         run_ours(a)

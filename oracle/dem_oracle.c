@@ -146,7 +146,11 @@ int ora_build(int64_t n_agg, const int32_t *count, const double *pos,
     for (int64_t a = 0; a < n_agg; ++a) {
         if (count[a] <= 0) return -1;
         first[a] = (int32_t)k;
-        double Ma = 0, c[3] = {0, 0, 0};
+        /* Eq. agg_position, the mass-weighted mean, taken about the first
+         * member: a one-sphere aggregate then has its COM exactly at the
+         * sphere and a zero offset. */
+        double Ma = 0, c[3] = {0, 0, 0}, x0[3];
+        for (int d = 0; d < 3; ++d) x0[d] = pos[3 * k + d];
         for (int32_t t = 0; t < count[a]; ++t, ++k) {
             double s = radius[k], rho = density[k];
             if (!(s > 0) || !(rho > 0) || !isfinite(s) || !isfinite(rho)) return -1;
@@ -154,9 +158,9 @@ int ora_build(int64_t n_agg, const int32_t *count, const double *pos,
             m[k] = rho * 4.0 / 3.0 * M_PI * s * s * s;
             agg_of[k] = (int32_t)a;
             Ma += m[k];
-            for (int d = 0; d < 3; ++d) c[d] += m[k] * pos[3 * k + d];
+            for (int d = 0; d < 3; ++d) c[d] += m[k] * (pos[3 * k + d] - x0[d]);
         }
-        for (int d = 0; d < 3; ++d) c[d] /= Ma;
+        for (int d = 0; d < 3; ++d) c[d] = x0[d] + c[d] / Ma;
         M[a] = Ma;
         for (int d = 0; d < 3; ++d) com[3 * a + d] = c[d];
         double T[9] = {0};

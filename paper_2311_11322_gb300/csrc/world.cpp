@@ -736,15 +736,17 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     int64_t k = 0;
     for (int a = 0; a < A; ++a) {
         first[a] = (int32_t)k;
-        double Ma = 0, c[3] = {0, 0, 0};
+        // mass-weighted mean about the first member: a one-sphere aggregate
+        // gets its COM exactly at the sphere (zero offset, zero lever)
+        double Ma = 0, c[3] = {0, 0, 0}, x0[3] = {pos[3 * k], pos[3 * k + 1], pos[3 * k + 2]};
         for (int t = 0; t < spa[a]; ++t, ++k) {
             m[k] = dens[k] * (4.0 / 3.0) * M_PI * rad[k] * rad[k] * rad[k];
             sph_agg[k] = a;
             Ma += m[k];
-            for (int d = 0; d < 3; ++d) c[d] += m[k] * pos[3 * k + d];
+            for (int d = 0; d < 3; ++d) c[d] += m[k] * (pos[3 * k + d] - x0[d]);
             smax = std::max(smax, rad[k]);
         }
-        for (int d = 0; d < 3; ++d) c[d] /= Ma;
+        for (int d = 0; d < 3; ++d) c[d] = x0[d] + c[d] / Ma;
         M[a] = Ma;
         double T[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         for (int64_t i = first[a]; i < first[a] + spa[a]; ++i) {

@@ -10,8 +10,12 @@ Shapes (touching spheres of radius s, offsets from the shape centre):
   rod3     (3): (-2s, 0, 0), (0, 0, 0), (2s, 0, 0)
   tetra    (4): regular tetrahedron of edge 2s
   square   (4): (+-s, +-s, 0)
+  rod4     (4): (-3s, 0, 0), (-s, 0, 0), (s, 0, 0), (3s, 0, 0)
+  diamond  (4): planar rhombus, (0, +-s, 0), (+-sqrt(3) s, 0, 0)
+  cube8    (8): (+-s, +-s, +-s)
+  single   (1): a free sphere (an aggregate of one)
 These are the simple shapes the paper builds its grains from (Sec. 2.2 figure,
-Sec. 4.1).  Orientation is uniform on SO(3) (normalised 4-D Gaussian quaternion).
+Sec. 3, Sec. 4.1).  Orientation is uniform on SO(3) (normalised 4-D Gaussian quaternion).
 
 Parameter recipe (the paper delegates the force-law constants to earlier
 work; these are the calibration rules used for the synthetic workloads):
@@ -40,7 +44,10 @@ PRECISION_FP64 = 0
 PRECISION_MIXED = 1
 
 SHAPES = ("dumbbell", "rod3", "tetra", "square")
-SHAPE_SIZE = {"dumbbell": 2, "rod3": 3, "tetra": 4, "square": 4}
+# the grain shapes of the paper's profiling and spin-up runs (Sec. 3, Sec. 4.1)
+E_SHAPES = ("dumbbell", "diamond", "rod4", "tetra", "cube8")
+SHAPE_SIZE = {"dumbbell": 2, "rod3": 3, "tetra": 4, "square": 4, "rod4": 4, "diamond": 4,
+              "cube8": 8, "single": 1}
 
 
 @dataclass
@@ -100,6 +107,13 @@ def shape_offsets(name: str, s: float) -> np.ndarray:
         o = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], float) * (s / math.sqrt(2.0))
     elif name == "square":
         o = np.array([[1, 1, 0], [1, -1, 0], [-1, 1, 0], [-1, -1, 0]], float) * s
+    elif name == "rod4":
+        o = np.array([[-3, 0, 0], [-1, 0, 0], [1, 0, 0], [3, 0, 0]], float) * s
+    elif name == "diamond":
+        r3 = math.sqrt(3.0)
+        o = np.array([[0, 1, 0], [0, -1, 0], [r3, 0, 0], [-r3, 0, 0]], float) * s
+    elif name == "cube8":
+        o = np.array([[i, j, k] for i in (-1, 1) for j in (-1, 1) for k in (-1, 1)], float) * s
     elif name == "single":
         o = np.zeros((1, 3))
     else:
@@ -275,6 +289,46 @@ def config2(seed=0, precision=PRECISION_MIXED, n_spheres=100_000, ball=2000.0):
     vmax = math.sqrt(2 * G_SI * total_mass(ic) / ball)
     p = calibrate(ic, v_max=vmax, r_med=5.0, eps=0.5, precision=precision)
     ic.meta = dict(name="config2", seed=seed, ball=ball)
+    return ic, p
+
+
+def e2_collapse(kind="mixed", seed=0, precision=PRECISION_MIXED, n_spheres=20_000, s=50.0,
+                ball=None):
+    """The paper's self-gravity profiling collapse (Sec. 3): N = 2e4 equal spheres of
+    radius 50 m, all free ("spheres"), all bonded into one shape (one of E_SHAPES:
+    2,500 cubes ... 10,000 dumbbells), or a uniform mix of the five shapes ("mixed",
+    topped up with free spheres to the exact count); COMs uniform in a ball (bounding
+    spheres disjoint), at rest, random orientations.  The paper does not give the
+    cloud size: the ball is 3 km, or larger where the bounding spheres would fill
+    more than 15% of it (random placement fails much above that), so contacts form
+    as the cloud collapses."""
+    rng = np.random.default_rng(seed)
+    if kind == "spheres":
+        shapes = ["single"] * n_spheres
+    elif kind == "mixed":
+        shapes, left = [], n_spheres
+        while left > 0:
+            sh = E_SHAPES[rng.integers(0, len(E_SHAPES))]
+            if SHAPE_SIZE[sh] > left:
+                sh = "single"
+            shapes.append(sh)
+            left -= SHAPE_SIZE[sh]
+    elif kind in E_SHAPES:
+        if n_spheres % SHAPE_SIZE[kind]:
+            raise ValueError("sphere count not a multiple of the shape size")
+        shapes = [kind] * (n_spheres // SHAPE_SIZE[kind])
+    else:
+        raise ValueError(kind)
+    A = len(shapes)
+    sizes = np.full(A, float(s))
+    bound = np.array([bounding_radius(sh, s) for sh in shapes])
+    if ball is None:
+        ball = max(3000.0 * s / 50.0, float(np.sum(bound ** 3) / 0.15) ** (1.0 / 3.0))
+    coms = place_nonoverlapping(rng, bound, ball)
+    ic = assemble(shapes, sizes, coms, random_rotations(rng, A), 2500.0)
+    vmax = math.sqrt(2 * G_SI * total_mass(ic) / ball)
+    p = calibrate(ic, v_max=vmax, r_med=s, eps=0.1 * s, precision=precision)
+    ic.meta = dict(name=f"e2_{kind}", seed=seed, ball=ball, steps=10_000)
     return ic, p
 
 

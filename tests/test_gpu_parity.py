@@ -375,3 +375,30 @@ def test_config3_full_size_sampled(dem, oracle):
     assert ic.n_sph == 200_000
     es, ea, et, _ = sampled_check(dem, oracle, ic, p, 100, TOL[1])
     assert es <= TOL[1] and ea <= TOL[1] and et <= TOL[1]
+
+
+# ------------------------------------------------------------------ free spheres and mixed populations
+@pytest.mark.parametrize("prec", PRECS)
+def test_free_spheres_and_mixed_population_lockstep(dem, oracle, prec):
+    """Free spheres (aggregates of one) alone and mixed with the paper's grain
+    shapes (dumbbell, diamond, rod4, tetra, cube8), overlapping: 10 steps side by
+    side, then 20 steps each from the oracle's state."""
+    for shapes, box in ((("single",), 4.0), (W.E_SHAPES + ("single",), 5.0)):
+        ic, p = W.random_cluster(11, n_agg=90, shapes=shapes, box=box, precision=prec)
+        pile = oracle.Pile(ic, p, want_scales=True)
+        with new_world(dem) as w:
+            pid = w.add_pile(ic, p)
+            worst = lockstep(w, pid, pile, 10, TOL[prec], r_ref=1.0)
+            assert worst["contacts"] > 20
+            resynced_steps(w, pid, pile, 20, TOL[prec], p.max_contacts)
+
+
+def test_e2_collapse_full_size_lockstep(dem, oracle):
+    """The paper's profiling collapse (2e4 spheres of 50 m), mixed grain shapes and
+    free spheres, mixed path: 3 full steps side by side with the oracle."""
+    for kind in ("mixed", "spheres"):
+        ic, p = W.e2_collapse(kind, seed=0)
+        pile = oracle.Pile(ic, p, want_scales=True)
+        with new_world(dem) as w:
+            pid = w.add_pile(ic, p)
+            lockstep(w, pid, pile, 3, TOL[1], r_ref=50.0)

@@ -192,3 +192,26 @@ def test_workloads_are_seeded_and_consistent():
     tr = W.config5_trace(0, n_arrivals=10)
     assert all(1000 <= t["n_spheres"] <= 100000 for t in tr)
     assert all(tr[k]["t_arrival"] < tr[k + 1]["t_arrival"] for k in range(9))
+
+
+def test_e2_collapse_populations():
+    """The profiling collapse of Sec. 3: 2e4 spheres of 50 m, as free spheres, as
+    one grain shape (2,500 cubes ... 10,000 dumbbells) or as a mix; members of
+    every shape touch, bounding spheres do not overlap."""
+    for kind, n_agg in (("spheres", 20_000), ("dumbbell", 10_000), ("cube8", 2_500),
+                        ("diamond", 5_000), ("rod4", 5_000), ("tetra", 5_000)):
+        ic, p = W.e2_collapse(kind, seed=1)
+        assert ic.n_sph == 20_000 and ic.n_agg == n_agg
+        assert np.all(ic.radius == 50.0)
+        assert p.eps == 5.0 and p.dt > 0
+    ic, _ = W.e2_collapse("mixed", seed=1)
+    assert ic.n_sph == 20_000 and 2_500 < ic.n_agg < 20_000
+    sizes = set(ic.counts.tolist())
+    assert {2, 4, 8} <= sizes
+    for sh in W.E_SHAPES:
+        o = W.shape_offsets(sh, 1.0)
+        d = np.linalg.norm(o[:, None] - o[None], axis=2)
+        np.fill_diagonal(d, np.inf)
+        assert abs(d.min() - 2.0) < 1e-12          # touching, never overlapping
+        assert abs(o.mean(axis=0)).max() < 1e-12   # offsets about the centre
+        assert len(o) == W.SHAPE_SIZE[sh]

@@ -492,3 +492,16 @@ def test_gravity_two_aggregate_tidal_torque_sign(oracle_lib):
     # quadrupole limit: N_z = -3 G Mp / d^3 * (sum m b_x b_y) = -3 G Mp m s^2 / d^3
     expect = -3 * W.G_SI * Mp * m * s * s / d ** 3
     assert N[2] == pytest.approx(expect, rel=1e-2)
+
+
+def test_free_sphere_has_zero_offset_and_no_gravity_torque(oracle_lib):
+    """A one-sphere aggregate (a free sphere) has its COM exactly at the sphere:
+    zero body offset, so gravity and the planet exert no torque on it."""
+    import oracle as O
+    from paper_2311_11322_gb300 import workloads as W
+    ic, p = W.random_cluster(2, n_agg=30, shapes=("single",), box=3.0, precision=0)
+    ic.pos = ic.pos + 12345.678       # far from the origin: rounding would show
+    pile = O.Pile(ic, p.replace(G=W.G_SI * 1e6), want_scales=True)
+    pile.step()
+    assert np.all(pile.b == 0.0)
+    assert np.all(pile.NA_g == 0.0) and np.all(pile.NA_e == 0.0)
