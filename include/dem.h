@@ -73,6 +73,10 @@ typedef struct {
     double ext_pos[3];   /* planet position at t = 0 (m) */
     double ext_vel[3];   /* planet velocity at t = 0 (m/s) */
     double spin_inc[3];  /* spin increment per step (rad/s, space frame); 0 = none (Sec. 4.1) */
+    double rot_tol;      /* torque-free rotation over each step: 0 = one classical RK4 step;
+                            > 0 = the paper's time-adaptive fifth-order Runge-Kutta (embedded
+                            Cash-Karp RK5(4) substeps, error in q absolute and in w relative
+                            to |w| at most rot_tol; Sec. 2.2.1), in FP64 in both precisions */
 } dem_params;
 
 /* Fields for dem_read_state.  A = aggregates of the pile, N = spheres, K = max_contacts. */

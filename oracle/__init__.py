@@ -47,7 +47,7 @@ class Params(C.Structure):
                 ("kt", C.c_double), ("cn", C.c_double), ("ct", C.c_double),
                 ("mu_s", C.c_double), ("mu_r", C.c_double), ("mu_t", C.c_double),
                 ("w0", C.c_double), ("eps", C.c_double), ("ext_mass", C.c_double),
-                ("spin_inc", C.c_double * 3)]
+                ("spin_inc", C.c_double * 3), ("rot_tol", C.c_double)]
 
 
 class _Sim(C.Structure):
@@ -84,6 +84,8 @@ def lib():
         L.ora_gravity.argtypes = [i64, vp, vp, vp, dbl, dbl, C.c_int, i64, vp, vp, vp]
         L.ora_rotate.restype = None
         L.ora_rotate.argtypes = [vp, vp, vp, vp, vp, dbl]
+        L.ora_rotate_adaptive.restype = C.c_int
+        L.ora_rotate_adaptive.argtypes = [vp, vp, vp, vp, dbl, dbl]
         L.ora_spin_kick.restype = None
         L.ora_spin_kick.argtypes = [vp, vp, vp, vp, dbl]
         L.ora_rotmat.restype = None
@@ -115,6 +117,7 @@ def make_params(p) -> Params:
     si = getattr(p, "spin_inc", (0.0, 0.0, 0.0))
     for k in range(3):
         P.spin_inc[k] = float(si[k])
+    P.rot_tol = float(getattr(p, "rot_tol", 0.0))
     return P
 
 
@@ -206,6 +209,17 @@ def rotate(q, wb, I, Iinv, N_space, h):
     N = np.ascontiguousarray(N_space, np.float64)
     lib().ora_rotate(_p(q), _p(wb), _p(I), _p(Iinv), _p(N), float(h))
     return q, wb
+
+
+def rotate_adaptive(q, wb, I, Iinv, h, tol):
+    """Torque-free rotation over h by the adaptive embedded RK5(4) (Sec. 2.2.1);
+    returns new (q, wb, accepted substeps)."""
+    q = np.array(q, np.float64)
+    wb = np.array(wb, np.float64)
+    I = np.ascontiguousarray(I, np.float64)
+    Iinv = np.ascontiguousarray(Iinv, np.float64)
+    n = lib().ora_rotate_adaptive(_p(q), _p(wb), _p(I), _p(Iinv), float(h), float(tol))
+    return q, wb, int(n)
 
 
 class Pile:

@@ -48,6 +48,8 @@ typedef struct {
     double eps;        /* Plummer softening length */
     double ext_mass;   /* planet mass, 0 = no planet */
     double spin_inc[3];/* YORP spin increment per step (rad/s, space frame) */
+    double rot_tol;    /* 0: one classical RK4 step per rotation; > 0: adaptive
+                          embedded RK5(4) (Cash-Karp) to this tolerance */
 } ora_params;
 
 /* One rubble pile.  Arrays are owned by the caller. */
@@ -505,6 +507,79 @@ void ora_rotate(double q[4], double wb[3], const double *I, const double *Iinv,
     for (int c = 0; c < 3; ++c) wb[c] = y[4 + c];
 }
 
+/*
+ * The paper's rotation integrator (Sec. 2.2.1): a time-adaptive fifth-order
+ * Runge-Kutta scheme.  The torque-free rotation over h is taken in substeps of
+ * the embedded Runge-Kutta pair of Cash and Karp (6 stages: a fifth-order
+ * solution and a fourth-order one whose difference estimates the error).  A
+ * substep is accepted when its error, measured in q absolutely and in w
+ * relative to |w|, is at most tol; the next substep is the present one times
+ * 0.9 (tol/err)^(1/5) (at most 5 times larger), a rejected one is retried
+ * with 0.9 (tol/err)^(1/4) of it (at least a tenth).  The first trial is the
+ * whole step.  A substep shorter than h / 2^20 is accepted whatever its error,
+ * so the loop always ends.  q is renormalised at the end of the step, as in
+ * the RK4 reading.  Returns the number of accepted substeps.
+ */
+static const double ck_c[6] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 3.0 / 5.0, 1.0, 7.0 / 8.0};
+static const double ck_a[6][5] = {
+    {0, 0, 0, 0, 0},
+    {1.0 / 5.0, 0, 0, 0, 0},
+    {3.0 / 40.0, 9.0 / 40.0, 0, 0, 0},
+    {3.0 / 10.0, -9.0 / 10.0, 6.0 / 5.0, 0, 0},
+    {-11.0 / 54.0, 5.0 / 2.0, -70.0 / 27.0, 35.0 / 27.0, 0},
+    {1631.0 / 55296.0, 175.0 / 512.0, 575.0 / 13824.0, 44275.0 / 110592.0, 253.0 / 4096.0}};
+static const double ck_b5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
+static const double ck_b4[6] = {2825.0 / 27648.0, 0.0, 18575.0 / 48384.0, 13525.0 / 55296.0,
+                                277.0 / 14336.0, 1.0 / 4.0};
+
+int ora_rotate_adaptive(double q[4], double wb[3], const double *I, const double *Iinv,
+                        double h, double tol)
+{
+    const double zero[3] = {0, 0, 0};
+    double y[7] = {q[0], q[1], q[2], q[3], wb[0], wb[1], wb[2]};
+    double t = 0.0, dt = h;
+    int accepted = 0;
+    (void)ck_c;   /* autonomous equations: the stage times are not needed */
+    while (t < h) {
+        if (t + dt > h) dt = h - t;
+        double k[6][7], z[7];
+        ora_rot_deriv(y, I, Iinv, zero, k[0]);
+        for (int st = 1; st < 6; ++st) {
+            for (int c = 0; c < 7; ++c) {
+                double acc = 0.0;
+                for (int j = 0; j < st; ++j) acc += ck_a[st][j] * k[j][c];
+                z[c] = y[c] + dt * acc;
+            }
+            ora_rot_deriv(z, I, Iinv, zero, k[st]);
+        }
+        double y5[7], err = 0.0;
+        double wn = sqrt(y[4] * y[4] + y[5] * y[5] + y[6] * y[6]);
+        for (int c = 0; c < 7; ++c) {
+            double s5 = 0.0, s4 = 0.0;
+            for (int j = 0; j < 6; ++j) { s5 += ck_b5[j] * k[j][c]; s4 += ck_b4[j] * k[j][c]; }
+            y5[c] = y[c] + dt * s5;
+            double e = fabs(dt * (s5 - s4));
+            if (c >= 4) e /= (wn > 0 ? wn : 1.0);
+            if (e > err) err = e;
+        }
+        double ratio = err / tol;
+        if (ratio <= 1.0 || dt <= h * 0x1p-20) {
+            memcpy(y, y5, sizeof y);
+            t += dt;
+            ++accepted;
+            double grow = ratio > 0 ? 0.9 * pow(ratio, -0.2) : 5.0;
+            dt *= grow < 5.0 ? grow : 5.0;
+        } else {
+            double shrink = 0.9 * pow(ratio, -0.25);
+            dt *= shrink > 0.1 ? shrink : 0.1;
+        }
+    }
+    double qn = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3]);
+    for (int c = 0; c < 4; ++c) q[c] = y[c] / qn;
+    for (int c = 0; c < 3; ++c) wb[c] = y[4 + c];
+    return accepted;
+}
+
 /* Half kick of the spin: L_space += dt N  <=>  w_body += dt I^-1 R(q)^T N. */
 void ora_spin_kick(const double q[4], double wb[3], const double *Iinv, const double N_space[3],
                    double dt)
@@ -640,7 +715,7 @@ static int ora_forces(ora_sim *S, const ora_params *P, int want_scales)
  * The stored a_A and N_A of a new pile are zero.
  * Returns 0, -2 on history overflow.
  */
-static void ora_kick_drift(ora_sim *S, double h)
+static void ora_kick_drift(ora_sim *S, const ora_params *P, double h)
 {
     const double zero[3] = {0, 0, 0};
     for (int64_t a = 0; a < S->n_agg; ++a) {
@@ -649,14 +724,18 @@ static void ora_kick_drift(ora_sim *S, double h)
             S->r[3 * a + c] += h * S->v[3 * a + c];
         }
         ora_spin_kick(S->q + 4 * a, S->wb + 3 * a, S->Iinv + 9 * a, S->torque + 3 * a, 0.5 * h);
-        ora_rotate(S->q + 4 * a, S->wb + 3 * a, S->I + 9 * a, S->Iinv + 9 * a, zero, h);
+        if (P->rot_tol > 0)
+            ora_rotate_adaptive(S->q + 4 * a, S->wb + 3 * a, S->I + 9 * a, S->Iinv + 9 * a, h,
+                                P->rot_tol);
+        else
+            ora_rotate(S->q + 4 * a, S->wb + 3 * a, S->I + 9 * a, S->Iinv + 9 * a, zero, h);
     }
 }
 
 int ora_step(ora_sim *S, const ora_params *P, int want_scales)
 {
     double h = P->dt;
-    ora_kick_drift(S, h);
+    ora_kick_drift(S, P, h);
     if (P->ext_mass > 0) {
         for (int c = 0; c < 3; ++c) {
             S->planet[3 + c] += 0.5 * h * S->planet[6 + c];
@@ -718,7 +797,7 @@ int ora_step_sampled(ora_sim *S, const ora_params *P, int64_t n_rows, const int6
                      double *Fc, double *Tc, double *Fg, double *Fe, double *Fmag, double *Tmag)
 {
     double h = P->dt;
-    ora_kick_drift(S, h);
+    ora_kick_drift(S, P, h);
     double planet_pos[3] = {0, 0, 0};
     if (P->ext_mass > 0) {
         for (int c = 0; c < 3; ++c) {

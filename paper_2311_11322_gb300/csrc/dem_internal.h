@@ -36,6 +36,7 @@ struct PileStatic {
     double G, h, kn, kt, cn, ct, mu_s, mu_r, mu_t, w0, eps2;
     double ext_mass, M_total;
     double spin_inc[3];
+    double rot_tol;        // 0: RK4 rotation; > 0: adaptive RK5(4) tolerance
 };
 
 // Dynamic per-pile state (device-owned; written by kernels).
@@ -137,7 +138,7 @@ struct Sizes {
     int64_t N, A, C, T, CH, P, GI, GP;
     int64_t GB;   // blocks of the persistent gravity grid (0 = one block per item)
     int32_t K;    // history slots per sphere (world-wide)
-    int32_t pad;
+    int32_t adapt;   // some pile integrates rotation with the adaptive RK5(4)
 };
 
 // ---- kernel launchers (kernels_*.cu) -------------------------------------

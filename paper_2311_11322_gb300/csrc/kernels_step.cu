@@ -121,13 +121,76 @@ __device__ void free_rotate_mixed(double *q, double3 &wb, const float *I, const 
     wb = d3(wb.x + d[4], wb.y + d[5], wb.z + d[6]);
 }
 
+// The paper's rotation integrator (Sec. 2.2.1): time-adaptive fifth-order
+// Runge-Kutta.  The torque-free rotation over h is taken in substeps of the
+// embedded Cash-Karp RK5(4) pair; a substep is accepted when the difference
+// of its fifth- and fourth-order results (q absolute, w relative to |w|) is
+// within tol, the next one is scaled by 0.9 (tol/err)^(1/5) (at most x5), a
+// rejected one retried at 0.9 (tol/err)^(1/4) of it (at least x0.1); the first
+// trial is the whole step, and a substep below h / 2^20 is accepted whatever
+// its error, so the loop ends.  FP64 in both precisions; q renormalised at the
+// end as after RK4.
+__device__ void free_rotate_adaptive(double *q, double3 &wb, const double *I, const double *Iinv,
+                                     double h, double tol)
+{
+    // Cash-Karp coefficients
+    const double A21 = 1.0 / 5.0;
+    const double A31 = 3.0 / 40.0, A32 = 9.0 / 40.0;
+    const double A41 = 3.0 / 10.0, A42 = -9.0 / 10.0, A43 = 6.0 / 5.0;
+    const double A51 = -11.0 / 54.0, A52 = 5.0 / 2.0, A53 = -70.0 / 27.0, A54 = 35.0 / 27.0;
+    const double A61 = 1631.0 / 55296.0, A62 = 175.0 / 512.0, A63 = 575.0 / 13824.0,
+                 A64 = 44275.0 / 110592.0, A65 = 253.0 / 4096.0;
+    const double B1 = 37.0 / 378.0, B3 = 250.0 / 621.0, B4 = 125.0 / 594.0, B6 = 512.0 / 1771.0;
+    const double E1 = B1 - 2825.0 / 27648.0, E3 = B3 - 18575.0 / 48384.0,
+                 E4 = B4 - 13525.0 / 55296.0, E5 = -277.0 / 14336.0, E6 = B6 - 1.0 / 4.0;
+    double y[7] = {q[0], q[1], q[2], q[3], wb.x, wb.y, wb.z};
+    double t = 0.0, dt = h;
+    const double dt_min = h * 0x1p-20;
+    while (t < h) {
+        if (t + dt > h) dt = h - t;
+        double k1[7], k2[7], k3[7], k4[7], k5[7], k6[7], z[7];
+        rot_rhs(y, I, Iinv, k1);
+        for (int c = 0; c < 7; ++c) z[c] = y[c] + dt * (A21 * k1[c]);
+        rot_rhs(z, I, Iinv, k2);
+        for (int c = 0; c < 7; ++c) z[c] = y[c] + dt * (A31 * k1[c] + A32 * k2[c]);
+        rot_rhs(z, I, Iinv, k3);
+        for (int c = 0; c < 7; ++c) z[c] = y[c] + dt * (A41 * k1[c] + A42 * k2[c] + A43 * k3[c]);
+        rot_rhs(z, I, Iinv, k4);
+        for (int c = 0; c < 7; ++c)
+            z[c] = y[c] + dt * (A51 * k1[c] + A52 * k2[c] + A53 * k3[c] + A54 * k4[c]);
+        rot_rhs(z, I, Iinv, k5);
+        for (int c = 0; c < 7; ++c)
+            z[c] = y[c] + dt * (A61 * k1[c] + A62 * k2[c] + A63 * k3[c] + A64 * k4[c] + A65 * k5[c]);
+        rot_rhs(z, I, Iinv, k6);
+        const double wn = sqrt(y[4] * y[4] + y[5] * y[5] + y[6] * y[6]);
+        double err = 0.0;
+        for (int c = 0; c < 7; ++c) {
+            double e = fabs(dt * (E1 * k1[c] + E3 * k3[c] + E4 * k4[c] + E5 * k5[c] + E6 * k6[c]));
+            if (c >= 4 && wn > 0.0) e /= wn;
+            err = fmax(err, e);
+        }
+        const double ratio = err / tol;
+        if (ratio <= 1.0 || dt <= dt_min) {
+            for (int c = 0; c < 7; ++c)
+                y[c] += dt * (B1 * k1[c] + B3 * k3[c] + B4 * k4[c] + B6 * k6[c]);
+            t += dt;
+            dt *= ratio > 0.0 ? fmin(5.0, 0.9 * pow(ratio, -0.2)) : 5.0;
+        } else {
+            dt *= fmax(0.1, 0.9 * pow(ratio, -0.25));
+        }
+    }
+    double n = sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + y[3] * y[3]);
+    q[0] = y[0] / n; q[1] = y[1] / n; q[2] = y[2] / n; q[3] = y[3] / n;
+    wb = d3(y[4], y[5], y[6]);
+}
+
 // ---------------------------------------------------------------- step begin
 // Per aggregate: half kick of COM and spin with the stored a_A,n / N_A,n,
 // drift, torque-free rotation, then the record the sphere kernels read:
 // rotation, COM relative to the pile frame, predicted COM velocity
 // v_A,n+1/2 + h/2 a_A,n (Eq. pred-vel) and predicted spin w_A,n+1 (the
 // drifted spin plus the second half kick of the old torque).
-template <bool FP64>
+template <bool FP64, bool ADAPT>
 __global__ void k_agg_begin(Arrays a, Sizes z)
 {
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -147,7 +210,8 @@ __global__ void k_agg_begin(Arrays a, Sizes z)
         v = v + (0.5 * h) * acc;
         wb = wb + (0.5 * h) * mat_mul(Iinv, mat_tmul(R, N));
         r = r + h * v;
-        free_rotate(q, wb, I, Iinv, h);
+        if (ADAPT && a.ps[p].rot_tol > 0.0) free_rotate_adaptive(q, wb, I, Iinv, h, a.ps[p].rot_tol);
+        else free_rotate(q, wb, I, Iinv, h);
         quat_to_R(q, R);
         double3 wpred_b = wb + (0.5 * h) * mat_mul(Iinv, mat_tmul(R, N));
         ws = mat_mul(R, wpred_b);
@@ -164,7 +228,8 @@ __global__ void k_agg_begin(Arrays a, Sizes z)
         v = v + (0.5 * h) * acc;
         wb = d3(wb.x + dw.x, wb.y + dw.y, wb.z + dw.z);
         r = r + h * v;
-        free_rotate_mixed(q, wb, I32, Iinv32, hf);
+        if (ADAPT && a.ps[p].rot_tol > 0.0) free_rotate_adaptive(q, wb, I, Iinv, h, a.ps[p].rot_tol);
+        else free_rotate_mixed(q, wb, I32, Iinv32, hf);
         quat_to_R(q, R);
         for (int c = 0; c < 4; ++c) qf[c] = (float)q[c];
         quat_to_Rf(qf, Rf);
@@ -222,8 +287,15 @@ void launch_agg_begin(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t s
 {
     if (z.A == 0) return;
     unsigned nb = (unsigned)((z.A + 127) / 128);
-    if (fp64) k_agg_begin<true><<<nb, 128, 0, st>>>(a, z);
-    else k_agg_begin<false><<<nb, 128, 0, st>>>(a, z);
+    // the adaptive rotor needs many more registers: its variant runs only when
+    // some pile asks for it
+    if (z.adapt) {
+        if (fp64) k_agg_begin<true, true><<<nb, 128, 0, st>>>(a, z);
+        else k_agg_begin<false, true><<<nb, 128, 0, st>>>(a, z);
+    } else {
+        if (fp64) k_agg_begin<true, false><<<nb, 128, 0, st>>>(a, z);
+        else k_agg_begin<false, false><<<nb, 128, 0, st>>>(a, z);
+    }
 }
 
 // ---------------------------------------------------------------- pile reductions

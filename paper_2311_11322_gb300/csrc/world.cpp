@@ -398,6 +398,7 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
         S.eps2 = P.eps_soft * P.eps_soft;
         S.ext_mass = P.ext_mass; S.M_total = q.M_total;
         for (int c = 0; c < 3; ++c) S.spin_inc[c] = P.spin_inc[c];
+        S.rot_tol = P.rot_tol;
         ps.push_back(S);
         s0 += q.ns; a0 += q.na; c0 += q.nc; ch0 += q.nch;
     }
@@ -406,6 +407,9 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     w->Z.GI = (int64_t)gp.items.size();
     w->Z.GP = gp.gp;
     w->Z.K = w->K;
+    w->Z.adapt = 0;
+    for (auto &q : w->piles)
+        if (q.P.rot_tol > 0) w->Z.adapt = 1;
     if (w->sm_count == 0) {
         int dev = 0;
         CU(cudaGetDevice(&dev));
@@ -707,13 +711,13 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     if (w->K >= 0 && p->max_contacts != w->K)
         return fail(w, DEM_ERR_ARG, "all piles of a world must use the same max_contacts");
     const double scal[] = {p->G, p->dt, p->kn, p->kt, p->cn, p->ct, p->mu_s, p->mu_r, p->mu_t,
-                           p->w0, p->eps_soft, p->cell_size, p->ext_mass};
-    if (!finite_all(scal, 13) || !finite_all(p->ext_pos, 3) || !finite_all(p->ext_vel, 3) ||
+                           p->w0, p->eps_soft, p->cell_size, p->ext_mass, p->rot_tol};
+    if (!finite_all(scal, 14) || !finite_all(p->ext_pos, 3) || !finite_all(p->ext_vel, 3) ||
         !finite_all(p->spin_inc, 3))
         return fail(w, DEM_ERR_ARG, "non-finite parameter");
     if (!(p->dt > 0) || p->kn < 0 || p->kt < 0 || p->cn < 0 || p->ct < 0 || p->mu_s < 0 ||
         p->mu_r < 0 || p->mu_t < 0 || !(p->w0 > 0) || p->eps_soft < 0 || p->G < 0 ||
-        p->ext_mass < 0 || p->cell_size < 0)
+        p->ext_mass < 0 || p->cell_size < 0 || p->rot_tol < 0)
         return fail(w, DEM_ERR_ARG, "parameter out of range (dt > 0, w0 > 0, others >= 0)");
     int64_t N = 0;
     for (int64_t a = 0; a < n_agg; ++a) {

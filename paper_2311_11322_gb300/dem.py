@@ -47,7 +47,8 @@ class dem_params(C.Structure):
                 ("eps_soft", C.c_double), ("precision", C.c_int32),
                 ("max_contacts", C.c_int32), ("cell_size", C.c_double),
                 ("ext_mass", C.c_double), ("ext_pos", C.c_double * 3),
-                ("ext_vel", C.c_double * 3), ("spin_inc", C.c_double * 3)]
+                ("ext_vel", C.c_double * 3), ("spin_inc", C.c_double * 3),
+                ("rot_tol", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -121,6 +122,7 @@ def make_params(p) -> dem_params:
         P.ext_pos[k] = float(p.ext_pos[k])
         P.ext_vel[k] = float(p.ext_vel[k])
         P.spin_inc[k] = float(p.spin_inc[k])
+    P.rot_tol = float(getattr(p, "rot_tol", 0.0))
     return P
 
 

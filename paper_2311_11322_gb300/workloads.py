@@ -70,6 +70,7 @@ class Params:
     precision: int = PRECISION_MIXED
     max_contacts: int = 16
     cell_size: float = 0.0
+    rot_tol: float = 0.0        # 0: RK4 rotation; > 0: adaptive RK5(4) to this tolerance
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)

@@ -70,4 +70,4 @@ def test_params_struct_layout():
     P = dem.dem_params
     assert P.precision.offset == 88 and P.max_contacts.offset == 92
     assert P.cell_size.offset == 96 and P.spin_inc.offset == 160
-    assert C.sizeof(P) == 184
+    assert P.rot_tol.offset == 184 and C.sizeof(P) == 192

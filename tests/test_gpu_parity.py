@@ -402,3 +402,49 @@ def test_e2_collapse_full_size_lockstep(dem, oracle):
         with new_world(dem) as w:
             pid = w.add_pile(ic, p)
             lockstep(w, pid, pile, 3, TOL[1], r_ref=50.0)
+
+
+# ------------------------------------------------------------------ adaptive rotation (Sec. 2.2.1)
+@pytest.mark.parametrize("prec", PRECS)
+def test_adaptive_rotation_lockstep(dem, oracle, prec):
+    """The paper's adaptive fifth-order rotation (rot_tol > 0) on an overlapping
+    cluster: side by side with the oracle running the same scheme."""
+    ic, p = W.random_cluster(3, n_agg=70, box=5.0, precision=prec)
+    p = p.replace(rot_tol=1e-9, mu_t=0.05)
+    pile = oracle.Pile(ic, p, want_scales=True)
+    with new_world(dem) as w:
+        pid = w.add_pile(ic, p)
+        worst = lockstep(w, pid, pile, 10, TOL[prec], r_ref=1.0)
+        assert worst["contacts"] > 20
+        resynced_steps(w, pid, pile, 10, TOL[prec], p.max_contacts)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_adaptive_rotation_fast_spinners(dem, prec):
+    """Isolated asymmetric aggregates spinning fast for the step (|w| h ~ 0.3), no
+    gravity, no contacts: with the adaptive scheme the GPU keeps each body's spin
+    energy and |L| to ~1e-8 over 200 steps, where one RK4 step per h drifts."""
+    rng = np.random.default_rng(4)
+    n = 40
+    shapes = ["square", "rod3", "tetra", "dumbbell"] * (n // 4)
+    coms = np.stack([np.arange(n) * 20.0, np.zeros(n), np.zeros(n)], 1)
+    ic = W.assemble(shapes, np.ones(n), coms, W.random_rotations(rng, n), 2500.0)
+    ic.omega = rng.standard_normal((n, 3)) * 0.6
+    base = W.Params(G=0.0, dt=0.5, kn=0.0, kt=0.0, w0=1.0, eps=0.1, precision=prec, max_contacts=4)
+    drift = {}
+    for tol in (0.0, 1e-10):
+        with new_world(dem) as w:
+            pid = w.add_pile(ic, base.replace(rot_tol=tol))
+            wb0 = w.read(pid, "OMEGA_BODY")
+            w.step(200)
+            wb = w.read(pid, "OMEGA_BODY")
+            import oracle as O
+            agg = O.build_aggregates(ic.counts, ic.pos, ic.radius, ic.density)
+            I = agg["I"].reshape(n, 3, 3)
+            E0 = np.einsum("ai,aij,aj->a", wb0, I, wb0)
+            E1 = np.einsum("ai,aij,aj->a", wb, I, wb)
+            L0 = np.linalg.norm(np.einsum("aij,aj->ai", I, wb0), axis=1)
+            L1 = np.linalg.norm(np.einsum("aij,aj->ai", I, wb), axis=1)
+            drift[tol] = max(np.max(np.abs(E1 / E0 - 1)), np.max(np.abs(L1 / L0 - 1)))
+    assert drift[1e-10] < 1e-8
+    assert drift[0.0] > 100 * drift[1e-10]

@@ -505,3 +505,70 @@ def test_free_sphere_has_zero_offset_and_no_gravity_torque(oracle_lib):
     pile.step()
     assert np.all(pile.b == 0.0)
     assert np.all(pile.NA_g == 0.0) and np.all(pile.NA_e == 0.0)
+
+
+# ---------------------------------------------------------------- adaptive RK5 rotation (Sec. 2.2.1)
+def _square_body():
+    ic = W.assemble(["square"], [1.0], np.zeros((1, 3)), np.eye(3)[None], 2500.0)
+    import oracle as O
+    agg = O.build_aggregates(ic.counts, ic.pos, ic.radius, ic.density)
+    return agg["I"].reshape(3, 3), agg["Iinv"].reshape(3, 3)
+
+
+def _run_adaptive(oracle_lib, I, Iinv, w0, h, n, tol):
+    q, wb, subs = np.array([1.0, 0, 0, 0]), np.array(w0, float), 0
+    for _ in range(n):
+        q, wb, k = oracle_lib.rotate_adaptive(q, wb, I, Iinv, h, tol)
+        subs += k
+    return q, wb, subs
+
+
+def test_adaptive_rotation_fifth_order_and_tolerance(oracle_lib):
+    """The embedded RK5(4) of the adaptive integrator: with the tolerance out of
+    reach every step is one fifth-order step, and its error against a fine
+    reference falls ~32x when h halves; with a tolerance, a coarse step is cut
+    into substeps and the error stays near the tolerance."""
+    I, Iinv = _square_body()
+    w0 = [0.3, 0.2, 0.5]           # |w| h ~ 0.3 at h = 0.5: a hard step for RK4
+    T = 8.0
+    ref = _run_adaptive(oracle_lib, I, Iinv, w0, T / 2048, 2048, 1e30)[1]
+    e = []
+    for n in (64, 128, 256):
+        q, wb, subs = _run_adaptive(oracle_lib, I, Iinv, w0, T / n, n, 1e30)
+        assert subs == n
+        e.append(np.linalg.norm(wb - ref))
+    assert 24.0 < e[0] / e[1] < 40.0 and 24.0 < e[1] / e[2] < 40.0
+    q, wb, subs = _run_adaptive(oracle_lib, I, Iinv, w0, 0.5, 16, 1e-10)
+    assert subs > 16
+    assert np.linalg.norm(wb - ref) < 1e-8 * np.linalg.norm(ref)
+
+
+def test_adaptive_rotation_conserves_and_beats_rk4(oracle_lib):
+    """Torque-free asymmetric body at a coarse step: the adaptive scheme keeps
+    energy and |L| to ~1e-9 where one RK4 step per h drifts by orders more; the
+    symmetric top still follows its closed-form precession."""
+    I, Iinv = _square_body()
+    w0 = np.array([0.3, 0.2, 0.5])
+    E0, L0 = 0.5 * w0 @ I @ w0, np.linalg.norm(I @ w0)
+    q, wb, _ = _run_adaptive(oracle_lib, I, Iinv, w0, 0.5, 400, 1e-11)
+    dE_ad = abs(0.5 * wb @ I @ wb - E0) / E0
+    dL_ad = abs(np.linalg.norm(I @ wb) - L0) / L0
+    q4, wb4 = np.array([1.0, 0, 0, 0]), w0.copy()
+    for _ in range(400):
+        q4, wb4 = oracle_lib.rotate(q4, wb4, I, Iinv, np.zeros(3), 0.5)
+    dE_rk4 = abs(0.5 * wb4 @ I @ wb4 - E0) / E0
+    assert dE_ad < 1e-9 and dL_ad < 1e-9
+    assert dE_rk4 > 100 * dE_ad
+    # symmetric top (dumbbell about x): closed form
+    ic = W.assemble(["dumbbell"], [1.0], np.zeros((1, 3)), np.eye(3)[None], 2500.0)
+    import oracle as O
+    agg = O.build_aggregates(ic.counts, ic.pos, ic.radius, ic.density)
+    Id, Idi = agg["I"].reshape(3, 3), agg["Iinv"].reshape(3, 3)
+    w = np.array([0.4, 0.1, 0.0])
+    q, wb, _ = _run_adaptive(oracle_lib, Id, Idi, w, 0.5, 200, 1e-11)
+    Ia, Ip = Id[0, 0], Id[1, 1]
+    Om = (Ia - Ip) * w[0] / Ip
+    t = 0.5 * 200
+    assert wb[0] == pytest.approx(w[0], abs=1e-14)
+    assert wb[1] == pytest.approx(w[1] * np.cos(Om * t), abs=1e-8 * w[1])
+    assert wb[2] == pytest.approx(w[1] * np.sin(Om * t), abs=1e-8 * w[1])
