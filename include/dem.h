@@ -111,7 +111,10 @@ enum dem_field {
 };
 
 /* Pile flag bits (dem_pile_flags). */
-enum { DEM_FLAG_SLOTS = 1, DEM_FLAG_NONFINITE = 2, DEM_FLAG_OVERLAP = 4 };
+/* DEM_FLAG_TREE: tree gravity ran out of traversal stack for some group of
+ * spheres and took a cell as far that it would have opened (less accurate,
+ * not fatal). */
+enum { DEM_FLAG_SLOTS = 1, DEM_FLAG_NONFINITE = 2, DEM_FLAG_OVERLAP = 4, DEM_FLAG_TREE = 8 };
 
 /* Kernels that dem_step_profiled can time. */
 enum dem_kernel {

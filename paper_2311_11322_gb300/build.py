@@ -19,8 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdem.so")
 
-SOURCES = ["kernels_step.cu", "kernels_contact.cu", "kernels_gravity.cu", "gravity_noalloc.cu",
-           "world.cpp"]
+SOURCES = ["kernels_step.cu", "kernels_contact.cu", "kernels_gravity.cu", "kernels_tree.cu",
+           "gravity_noalloc.cu", "world.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
@@ -33,7 +33,7 @@ def nvcc() -> str:
 # Per-unit flags.  Gravity flushes FP32 denormals to zero: its pair terms and
 # partial sums are far from the denormal range, and rsqrtf then maps to the
 # hardware approximation with no denormal fix-up around it.
-PER_FILE = {"kernels_gravity.cu": ["-ftz=true"]}
+PER_FILE = {"kernels_gravity.cu": ["-ftz=true"], "kernels_tree.cu": ["-ftz=true"]}
 
 
 def _compile(src: str, extra: list[str]) -> str:

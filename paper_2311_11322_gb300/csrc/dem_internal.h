@@ -37,6 +37,10 @@ struct PileStatic {
     double ext_mass, M_total;
     double spin_inc[3];
     double rot_tol;        // 0: RK4 rotation; > 0: adaptive RK5(4) tolerance
+    // tree gravity (0 levels = direct sum): depth, opening angle, node and leaf ranges
+    int32_t tD;
+    float theta;
+    int64_t tnode0, tleaf0, tg0;   // first node, leaf and 32-sphere group of the pile
 };
 
 // Dynamic per-pile state (device-owned; written by kernels).
@@ -128,6 +132,18 @@ struct Arrays {
     int64_t *gpart_base;           // per pile: first slot in gpart (or -1 = direct)
     int32_t *gnchunk;              // per pile: number of j-chunks
     int32_t *gcounter;             // [0]: next work item of the persistent gravity grid
+    // tree gravity: per sphere leaf key, rank in its leaf, leaf-ordered home
+    // index; per pile cube (ordered-int min/max, 8 ints); nodes (3 float4 each:
+    // COM + mass, quadrupole, opening radius^2) level by level, Morton order
+    // inside a level; leaves (start, count); node and leaf owner piles
+    int32_t *tkey, *trank, *tsorted;
+    float4 *tpos;        // leaf-ordered positions (+mass)
+    int32_t *tagg;       // leaf-ordered aggregates
+    float4 *tpart;       // [64][N] partial sums of the 64 subtrees at level 2
+    int *tbox;
+    float4 *tnode;
+    int2 *tleaf;
+    int32_t *tnode_pile, *tleaf_pile;
     // piles
     PileStatic *ps;
     PileDyn *pd;
@@ -137,6 +153,7 @@ struct Arrays {
 struct Sizes {
     int64_t N, A, C, T, CH, P, GI, GP;
     int64_t GB;   // blocks of the persistent gravity grid (0 = one block per item)
+    int64_t TN, TL, TG;   // tree nodes, leaves and 32-sphere groups of all piles (TN = 0: direct sum)
     int32_t K;    // history slots per sphere (world-wide)
     int32_t adapt;   // some pile integrates rotation with the adaptive RK5(4)
 };
@@ -160,6 +177,7 @@ int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym);
 void launch_agg_end(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
 void launch_pile_end(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_fill_ids(const Arrays &a, const Sizes &z, cudaStream_t st);
+void launch_tree_gravity(const Arrays &a, const Sizes &z, int max_depth, cudaStream_t st);
 void launch_force_rebuild(const Arrays &a, const Sizes &z, int slot, cudaStream_t st);
 
 }  // namespace dem

@@ -1,0 +1,541 @@
+// kernels_tree.cu -- tree gravity (the paper's gravity method, Sec. 2.1: a
+// tree code with multipole expansions), as an option beside the direct sum.
+//
+// Per pile and step: a cubic box around the pile (min/max of the sphere
+// centres), an implicit octree of depth D over it (level L has 8^L cells in
+// Morton order, so the parent of cell m is m >> 3), spheres counted into the
+// leaf cells and ordered by leaf (counting sort, each leaf ordered by home
+// index, deterministic), leaf moments from their spheres and upper moments
+// from 8 children: mass, centre of mass and the traceless quadrupole
+//   Q = sum m (3 z z^T - |z|^2 I),  z = position - COM,
+// then each warp walks the tree depth-first for 32 spheres at once.  A cell is
+// accepted when the group of spheres is farther from its COM than
+// size/theta + |COM - centre| (so no sphere is inside an accepted cell) and
+// contributes
+//   a / G = M d / r^3 - Q d / r^5 + 5/2 (d^T Q d) d / r^7,   d = COM - x,
+// the gradient of the quadrupole potential; an opened leaf is summed directly
+// with Plummer softening, skipping the sphere itself and its aggregate mates
+// (pairs inside one aggregate cancel in its totals, Sec. 2.2.3).  Mates that
+// fall in an accepted distant cell are not removed: their share cancels in
+// the aggregate totals to the accuracy of the expansion.  FP32 throughout
+// (positions relative to the pile frame); the result is written to the same
+// per-sphere gravity array as the direct sum.
+#include "dem_internal.h"
+#include "devmath.cuh"
+
+namespace dem {
+
+// order-preserving map of floats to ints (min/max by integer atomics)
+__device__ __forceinline__ int f2o(float f)
+{
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float o2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__device__ __forceinline__ bool tree_pile(const Arrays &a, int p)
+{
+    return a.enabled[p] != 0 && a.pd[p].failed == 0 && a.ps[p].tD > 0;
+}
+
+// level offset inside a pile's node block: sum_{k<L} 8^k
+__host__ __device__ __forceinline__ int64_t lvl_off(int L) { return ((int64_t)1 << (3 * L)) / 7; }
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v)
+{
+    v &= 0x3ff;
+    v = (v | (v << 16)) & 0x030000ff;
+    v = (v | (v << 8)) & 0x0300f00f;
+    v = (v | (v << 4)) & 0x030c30c3;
+    v = (v | (v << 2)) & 0x09249249;
+    return v;
+}
+
+// One block per pile: reset the box and the leaf counts.
+__global__ void k_tree_init(Arrays a, Sizes z)
+{
+    const int p = blockIdx.x;
+    if (p >= z.P || !tree_pile(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    if (threadIdx.x < 3) {
+        a.tbox[8 * p + threadIdx.x] = f2o(3.0e38f);
+        a.tbox[8 * p + 3 + threadIdx.x] = f2o(-3.0e38f);
+    }
+    const int64_t nl = (int64_t)1 << (3 * S.tD);
+    for (int64_t c = threadIdx.x; c < nl; c += blockDim.x) a.tleaf[S.tleaf0 + c] = make_int2(0, 0);
+}
+
+// Box of each pile: per warp, lanes of the same pile reduce their min/max
+// first (piles are contiguous, so a warp holds one or two), then one atomic
+// per warp and pile (min/max do not depend on the order).
+__global__ void k_tree_box(Arrays a, Sizes z)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = i < z.N ? a.sph_pile[i] : -1;
+    const bool act = p >= 0 && tree_pile(a, p);
+    const float4 x = act ? a.gpos32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned todo = __ballot_sync(FULL, act);
+    while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int pp = __shfl_sync(FULL, p, leader);
+        const bool mine = act && p == pp;
+        todo &= ~__ballot_sync(FULL, mine);
+        int v[6] = {f2o(x.x), f2o(x.y), f2o(x.z), f2o(x.x), f2o(x.y), f2o(x.z)};
+        if (!mine) {
+            v[0] = v[1] = v[2] = 0x7fffffff;
+            v[3] = v[4] = v[5] = (int)0x80000000;
+        }
+        for (int o = 16; o > 0; o >>= 1)
+            for (int c = 0; c < 6; ++c) {
+                const int u = __shfl_xor_sync(FULL, v[c], o);
+                v[c] = c < 3 ? min(v[c], u) : max(v[c], u);
+            }
+        if ((threadIdx.x & 31) == leader)
+            for (int c = 0; c < 6; ++c) {
+                if (c < 3) atomicMin(&a.tbox[8 * pp + c], v[c]);
+                else atomicMax(&a.tbox[8 * pp + c], v[c]);
+            }
+    }
+}
+
+// cube of the pile: lower corner and edge
+__device__ __forceinline__ void tree_cube(const Arrays &a, int p, float3 &lo, float &edge)
+{
+    const int *b = a.tbox + 8 * p;
+    lo = f3(o2f(b[0]), o2f(b[1]), o2f(b[2]));
+    const float ex = o2f(b[3]) - lo.x, ey = o2f(b[4]) - lo.y, ez = o2f(b[5]) - lo.z;
+    edge = fmaxf(fmaxf(ex, ey), fmaxf(ez, 1e-6f)) * 1.0001f;
+}
+
+__global__ void k_tree_keys(Arrays a, Sizes z)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= z.N) return;
+    const int p = a.sph_pile[i];
+    if (!tree_pile(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    float3 lo;
+    float edge;
+    tree_cube(a, p, lo, edge);
+    const int n1 = 1 << S.tD;
+    const float sc = (float)n1 / edge;
+    const float4 x = a.gpos32[i];
+    const int cx = min(max((int)((x.x - lo.x) * sc), 0), n1 - 1);
+    const int cy = min(max((int)((x.y - lo.y) * sc), 0), n1 - 1);
+    const int cz = min(max((int)((x.z - lo.z) * sc), 0), n1 - 1);
+    const int key = (int)(spread3(cx) | (spread3(cy) << 1) | (spread3(cz) << 2));
+    a.tkey[i] = key;
+    a.trank[i] = atomicAdd(&a.tleaf[S.tleaf0 + key].y, 1);
+}
+
+// One block of 1024 threads per pile: exclusive scan of the leaf counts.
+__global__ void k_tree_scan(Arrays a, Sizes z)
+{
+    const int p = blockIdx.x;
+    if (p >= z.P || !tree_pile(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    const int64_t nl = (int64_t)1 << (3 * S.tD);
+    const int64_t per = (nl + blockDim.x - 1) / blockDim.x;
+    const int64_t b0 = threadIdx.x * per, b1 = min(nl, b0 + per);
+    int loc = 0;
+    for (int64_t c = b0; c < b1; ++c) loc += a.tleaf[S.tleaf0 + c].y;
+    __shared__ int buf[1024];
+    buf[threadIdx.x] = loc;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const int add = threadIdx.x >= (unsigned)o ? buf[threadIdx.x - o] : 0;
+        __syncthreads();
+        buf[threadIdx.x] += add;
+        __syncthreads();
+    }
+    int run = buf[threadIdx.x] - loc;
+    for (int64_t c = b0; c < b1; ++c) {
+        int2 &L = a.tleaf[S.tleaf0 + c];
+        L.x = run;
+        run += L.y;
+    }
+}
+
+__global__ void k_tree_scatter(Arrays a, Sizes z)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= z.N) return;
+    const int p = a.sph_pile[i];
+    if (!tree_pile(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    a.tsorted[S.s0 + a.tleaf[S.tleaf0 + a.tkey[i]].x + a.trank[i]] = (int32_t)(i - S.s0);
+}
+
+// The first position of each leaf orders the leaf by home index (insertion
+// sort; leaves hold a handful of spheres): deterministic sums.
+__global__ void k_tree_leaf_order(Arrays a, Sizes z)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= z.N) return;
+    const int p = a.sph_pile[k];
+    if (!tree_pile(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    int32_t *srt = a.tsorted + S.s0;
+    const int kl = (int)(k - S.s0);
+    const int2 L = a.tleaf[S.tleaf0 + a.tkey[S.s0 + srt[kl]]];
+    if (kl != L.x) return;
+    for (int x = 1; x < L.y; ++x) {
+        const int v = srt[L.x + x];
+        int y = x - 1;
+        while (y >= 0 && srt[L.x + y] > v) {
+            srt[L.x + y + 1] = srt[L.x + y];
+            --y;
+        }
+        srt[L.x + y + 1] = v;
+    }
+}
+
+// Leaf-ordered copies of the spheres' positions (+mass) and aggregates, so
+// that a leaf's spheres are contiguous for the moments and the walk.
+__global__ void k_tree_gather(Arrays a, Sizes z)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= z.N) return;
+    const int p = a.sph_pile[k];
+    if (!tree_pile(a, p)) return;
+    const int64_t s0 = a.ps[p].s0;
+    const int i = a.tsorted[k];
+    a.tpos[k] = a.gpos32[s0 + i];
+    a.tagg[k] = a.sph_agg[s0 + i];
+}
+
+// node record: A = (COM, M), B = (Qxx, Qyy, Qzz, Qxy), C = (Qxz, Qyz, r_open^2, 0)
+__device__ __forceinline__ void put_node(const Arrays &a, int64_t n, float3 c, float M, const float *Q,
+                                         float ropen2)
+{
+    a.tnode[3 * n] = make_float4(c.x, c.y, c.z, M);
+    a.tnode[3 * n + 1] = make_float4(Q[0], Q[1], Q[2], Q[3]);
+    a.tnode[3 * n + 2] = make_float4(Q[4], Q[5], ropen2, 0.f);
+}
+
+// centre of cell m (Morton) at level L of pile p's cube
+__device__ __forceinline__ float3 cell_centre(float3 lo, float edge, int L, uint32_t m)
+{
+    uint32_t x = 0, y = 0, zz = 0;
+    for (int b = 0; b < L; ++b) {
+        x |= ((m >> (3 * b)) & 1u) << b;
+        y |= ((m >> (3 * b + 1)) & 1u) << b;
+        zz |= ((m >> (3 * b + 2)) & 1u) << b;
+    }
+    const float s = edge / (float)(1 << L);
+    return f3(lo.x + (x + 0.5f) * s, lo.y + (y + 0.5f) * s, lo.z + (zz + 0.5f) * s);
+}
+
+__device__ __forceinline__ float opening2(float3 com, float3 ctr, float size, float theta)
+{
+    const float dx = com.x - ctr.x, dy = com.y - ctr.y, dz = com.z - ctr.z;
+    const float r = size / theta + sqrtf(dx * dx + dy * dy + dz * dz);
+    return r * r;
+}
+
+// Leaf moments: one thread per leaf of every tree pile.
+__global__ void k_tree_leaves(Arrays a, Sizes z)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= z.TL) return;
+    const int p = a.tleaf_pile[g];
+    if (p < 0 || !tree_pile(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    const uint32_t m = (uint32_t)(g - S.tleaf0);
+    const int2 L = a.tleaf[g];
+    const int64_t n = S.tnode0 + lvl_off(S.tD) + m;
+    float Q[6] = {0, 0, 0, 0, 0, 0};
+    if (L.y == 0) {
+        put_node(a, n, f3(0, 0, 0), 0.f, Q, 0.f);
+        return;
+    }
+    const float4 *tp = a.tpos + S.s0;
+    float M = 0.f;
+    float3 c = f3(0, 0, 0);
+    const float4 x0 = tp[L.x];
+    for (int k = 0; k < L.y; ++k) {   // COM about the first sphere
+        const float4 x = tp[L.x + k];
+        M += x.w;
+        c = c + x.w * f3(x.x - x0.x, x.y - x0.y, x.z - x0.z);
+    }
+    c = f3(x0.x, x0.y, x0.z) + (1.0f / M) * c;
+    for (int k = 0; k < L.y; ++k) {
+        const float4 x = tp[L.x + k];
+        const float zx = x.x - c.x, zy = x.y - c.y, zz = x.z - c.z;
+        const float r2 = zx * zx + zy * zy + zz * zz;
+        Q[0] += x.w * (3.f * zx * zx - r2);
+        Q[1] += x.w * (3.f * zy * zy - r2);
+        Q[2] += x.w * (3.f * zz * zz - r2);
+        Q[3] += x.w * 3.f * zx * zy;
+        Q[4] += x.w * 3.f * zx * zz;
+        Q[5] += x.w * 3.f * zy * zz;
+    }
+    float3 lo;
+    float edge;
+    tree_cube(a, p, lo, edge);
+    const float size = edge / (float)(1 << S.tD);
+    put_node(a, n, c, M, Q, opening2(c, cell_centre(lo, edge, S.tD, m), size, S.theta));
+}
+
+// Moments of level L from the 8 children (parallel axis for Q): one thread
+// per node of every tree pile deep enough.
+__global__ void k_tree_up(Arrays a, Sizes z, int L)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= z.TN) return;
+    const int p = a.tnode_pile[g];
+    if (p < 0 || !tree_pile(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    if (L >= S.tD) return;
+    const int64_t local = g - S.tnode0;
+    const int64_t o = lvl_off(L);
+    if (local < o || local >= o + ((int64_t)1 << (3 * L))) return;
+    const uint32_t m = (uint32_t)(local - o);
+    const int64_t c0 = S.tnode0 + lvl_off(L + 1) + 8 * (int64_t)m;
+    float M = 0.f;
+    float3 c = f3(0, 0, 0);
+    for (int k = 0; k < 8; ++k) {
+        const float4 A = a.tnode[3 * (c0 + k)];
+        M += A.w;
+        c = c + A.w * f3(A.x, A.y, A.z);
+    }
+    float Q[6] = {0, 0, 0, 0, 0, 0};
+    if (M == 0.f) {
+        put_node(a, g, f3(0, 0, 0), 0.f, Q, 0.f);
+        return;
+    }
+    c = (1.0f / M) * c;
+    for (int k = 0; k < 8; ++k) {
+        const float4 A = a.tnode[3 * (c0 + k)];
+        if (A.w == 0.f) continue;
+        const float4 B = a.tnode[3 * (c0 + k) + 1], C = a.tnode[3 * (c0 + k) + 2];
+        const float dx = A.x - c.x, dy = A.y - c.y, dz = A.z - c.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        Q[0] += B.x + A.w * (3.f * dx * dx - r2);
+        Q[1] += B.y + A.w * (3.f * dy * dy - r2);
+        Q[2] += B.z + A.w * (3.f * dz * dz - r2);
+        Q[3] += B.w + A.w * 3.f * dx * dy;
+        Q[4] += C.x + A.w * 3.f * dx * dz;
+        Q[5] += C.y + A.w * 3.f * dy * dz;
+    }
+    float3 lo;
+    float edge;
+    tree_cube(a, p, lo, edge);
+    put_node(a, g, c, M, Q, opening2(c, cell_centre(lo, edge, L, m), edge / (float)(1 << L), S.theta));
+}
+
+constexpr int kTreeStack = 2048;   // per warp
+// the walk of each group of spheres is split over the subtrees at this level
+#ifndef DEM_TREE_SPLIT_LEVEL
+#define DEM_TREE_SPLIT_LEVEL 2
+#endif
+constexpr int kSplitL = DEM_TREE_SPLIT_LEVEL, kSplit = 1 << (3 * kSplitL);
+
+// Monopole + quadrupole of node (A, B, C) on the sphere at x: a / G.
+__device__ __forceinline__ void node_force(const float4 &A, const float4 &B, const float4 &C, const float4 &x,
+                                           float &ax, float &ay, float &az)
+{
+    const float dx = A.x - x.x, dy = A.y - x.y, dz = A.z - x.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float inv = rsqrtf(r2);
+    const float inv2 = inv * inv, inv3 = inv2 * inv, inv5 = inv3 * inv2;
+    const float qx = B.x * dx + B.w * dy + C.x * dz;
+    const float qy = B.w * dx + B.y * dy + C.y * dz;
+    const float qz = C.x * dx + C.y * dy + B.z * dz;
+    const float dqd = dx * qx + dy * qy + dz * qz;
+    const float sc = A.w * inv3 + 2.5f * dqd * inv5 * inv2;
+    ax += sc * dx - inv5 * qx;
+    ay += sc * dy - inv5 * qy;
+    az += sc * dz - inv5 * qz;
+}
+
+// One warp walks the tree for a group of 32 consecutive spheres in leaf order.  Each round takes up to 32 nodes off the warp's stack, one per lane,
+// and tests them in parallel against the group's bounding box: a cell is
+// accepted when the box is farther from its COM than its opening radius (so
+// the test holds for every sphere of the group), an opened leaf is summed
+// directly, any other opened cell pushes its 8 children.  Every lane then
+// adds its own sphere's interaction with each accepted cell (cell data passed
+// by shuffles) and with the spheres of each opened leaf, so the arithmetic
+// has no divergence and the node loads of a round overlap.  Should the stack
+// ever fill, the cell is taken as accepted and the pile gets DEM_FLAG_TREE.
+// Groups are 32 consecutive spheres of one pile in leaf order, counted from
+// the pile's first sphere, so a pile's result does not depend on the other
+// piles of the batch.  The walk of each group is split over the kSplit
+// subtrees at level kSplitL (one warp each, grid dimension y), so that many
+// more warps hide the latency of the rounds; each writes its partial sum,
+// k_tree_combine adds them in order.
+__global__ void __launch_bounds__(128) k_tree_force(Arrays a, Sizes z)
+{
+    __shared__ int stk[4][kTreeStack];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    const int sub = blockIdx.y;   // subtree: cell sub at level kSplitL
+    int *st = stk[wid];
+    const int64_t wg = (int64_t)blockIdx.x * 4 + wid;   // group
+    if (wg >= z.TG) return;
+    int lo = 0, hi = (int)z.P - 1;   // pile of the group
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.ps[mid].tg0 <= wg) lo = mid; else hi = mid - 1;
+    }
+    const int pp = lo;
+    if (!tree_pile(a, pp)) return;   // uniform over the warp
+    const PileStatic &S = a.ps[pp];
+    const int64_t s0 = S.s0;
+    const int ti = (int)(32 * (wg - S.tg0)) + lane;   // leaf-order position in the pile
+    const bool mine = ti < S.ns;
+    const int64_t k = s0 + ti;
+    const float4 xi = mine ? a.tpos[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int ai = mine ? a.tagg[k] : -2;
+    // group box (lanes past the pile's end take lane 0's position)
+    const float lx = __shfl_sync(FULL, xi.x, 0), ly = __shfl_sync(FULL, xi.y, 0),
+                lz = __shfl_sync(FULL, xi.z, 0);
+    float bx0 = mine ? xi.x : lx, by0 = mine ? xi.y : ly, bz0 = mine ? xi.z : lz;
+    float bx1 = bx0, by1 = by0, bz1 = bz0;
+    for (int o = 16; o > 0; o >>= 1) {
+        bx0 = fminf(bx0, __shfl_xor_sync(FULL, bx0, o));
+        by0 = fminf(by0, __shfl_xor_sync(FULL, by0, o));
+        bz0 = fminf(bz0, __shfl_xor_sync(FULL, bz0, o));
+        bx1 = fmaxf(bx1, __shfl_xor_sync(FULL, bx1, o));
+        by1 = fmaxf(by1, __shfl_xor_sync(FULL, by1, o));
+        bz1 = fmaxf(bz1, __shfl_xor_sync(FULL, bz1, o));
+    }
+    const float eps2 = (float)S.eps2;
+    const int D = S.tD;
+    const float4 *nodes = a.tnode + 3 * S.tnode0;
+    const int2 *leaves = a.tleaf + S.tleaf0;
+    const float4 *tp = a.tpos + s0;
+    const int32_t *tg = a.tagg + s0;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    bool full = false;
+    int sp = 1;
+    if (lane == 0) st[0] = ((int)(lvl_off(kSplitL) + sub) << 3) | kSplitL;   // this warp's subtree
+    __syncwarp();
+    while (sp > 0) {
+        const int cnt = min(sp, 32);
+        const int e = lane < cnt ? st[sp - 1 - lane] : -1;
+        sp -= cnt;
+        __syncwarp();
+        // test this lane's node
+        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, C = A;
+        bool acc = false, leaf = false, open = false;
+        int2 lf = make_int2(0, 0);
+        if (e >= 0) {
+            const int n = e >> 3, L = e & 7;
+            A = nodes[3 * n];
+            if (A.w != 0.f) {
+                C = nodes[3 * n + 2];
+                const float gx = fmaxf(fmaxf(bx0 - A.x, A.x - bx1), 0.f);
+                const float gy = fmaxf(fmaxf(by0 - A.y, A.y - by1), 0.f);
+                const float gz = fmaxf(fmaxf(bz0 - A.z, A.z - bz1), 0.f);
+                acc = gx * gx + gy * gy + gz * gz > C.z;
+                leaf = !acc && L == D;
+                open = !acc && L < D;
+                if (acc) B = nodes[3 * n + 1];
+                if (leaf) lf = leaves[n - lvl_off(D)];
+            }
+        }
+        // push the children of opened cells (compacted); a full stack
+        // turns the cell into an accepted one
+        const unsigned om = __ballot_sync(FULL, open);
+        const int need = 8 * __popc(om);
+        if (sp + need > kTreeStack) {
+            if (open) {
+                acc = true;
+                open = false;
+                B = nodes[3 * (e >> 3) + 1];
+            }
+            full = true;
+        } else if (open) {
+            const int n = e >> 3, L = e & 7;
+            const int c0 = (int)(lvl_off(L + 1) + 8 * (n - lvl_off(L)));
+            const int at = sp + 8 * __popc(om & below);
+            for (int c = 0; c < 8; ++c) st[at + c] = ((c0 + 7 - c) << 3) | (L + 1);
+        }
+        if (sp + need <= kTreeStack) sp += need;
+        __syncwarp();
+        // accepted cells: every lane adds each of them
+        unsigned am = __ballot_sync(FULL, acc);
+        while (am) {
+            const int b = __ffs(am) - 1;
+            am &= am - 1;
+            const float4 Ab = make_float4(__shfl_sync(FULL, A.x, b), __shfl_sync(FULL, A.y, b),
+                                          __shfl_sync(FULL, A.z, b), __shfl_sync(FULL, A.w, b));
+            const float4 Bb = make_float4(__shfl_sync(FULL, B.x, b), __shfl_sync(FULL, B.y, b),
+                                          __shfl_sync(FULL, B.z, b), __shfl_sync(FULL, B.w, b));
+            const float4 Cb = make_float4(__shfl_sync(FULL, C.x, b), __shfl_sync(FULL, C.y, b), 0.f, 0.f);
+            if (mine) node_force(Ab, Bb, Cb, xi, ax, ay, az);
+        }
+        // opened leaves: lanes load a leaf's spheres side by side, then
+        // every lane adds each of them (passed by shuffles)
+        unsigned lm = __ballot_sync(FULL, leaf);
+        while (lm) {
+            const int b = __ffs(lm) - 1;
+            lm &= lm - 1;
+            const int l0 = __shfl_sync(FULL, lf.x, b), ln = __shfl_sync(FULL, lf.y, b);
+            for (int c0 = 0; c0 < ln; c0 += 32) {
+                const int t = l0 + c0 + lane;
+                const bool ok = c0 + lane < ln;
+                const float4 xq = ok ? tp[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int aq = ok ? tg[t] : -3;
+                const int m = min(32, ln - c0);
+                for (int u = 0; u < m; ++u) {
+                    const float4 xj = make_float4(__shfl_sync(FULL, xq.x, u), __shfl_sync(FULL, xq.y, u),
+                                                  __shfl_sync(FULL, xq.z, u), __shfl_sync(FULL, xq.w, u));
+                    const int aj = __shfl_sync(FULL, aq, u);
+                    if (mine && l0 + c0 + u != ti && aj != ai) {
+                        const float ex = xj.x - xi.x, ey = xj.y - xi.y, ez = xj.z - xi.z;
+                        const float q2 = fmaf(ez, ez, fmaf(ey, ey, fmaf(ex, ex, eps2)));
+                        const float iv = rsqrtf(q2);
+                        const float sj = xj.w * iv * iv * iv;
+                        ax = fmaf(ex, sj, ax);
+                        ay = fmaf(ey, sj, ay);
+                        az = fmaf(ez, sj, az);
+                    }
+                }
+            }
+        }
+    }
+    if (mine) a.tpart[(int64_t)sub * z.N + k] = make_float4(ax, ay, az, 0.f);
+    if (full && lane == 0) atomicOr(&a.pd[pp].flags, DEM_FLAG_TREE);
+}
+
+// Sum the subtree partials of each sphere (float-float, fixed order).
+__global__ void k_tree_combine(Arrays a, Sizes z)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= z.N) return;
+    const int p = a.sph_pile[k];
+    if (!tree_pile(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    FFSum sx, sy, sz;
+    for (int s = 0; s < kSplit; ++s) {
+        const float4 v = a.tpart[(int64_t)s * z.N + k];
+        sx.add(v.x); sy.add(v.y); sz.add(v.z);
+    }
+    const int i = a.tsorted[k];
+    const double gm = S.G * a.m64[S.s0 + i];
+    a.fg[S.s0 + i] = make_dbl4(gm * sx.value(), gm * sy.value(), gm * sz.value(), 0.0);
+}
+
+void launch_tree_gravity(const Arrays &a, const Sizes &z, int max_depth, cudaStream_t st)
+{
+    if (z.N == 0 || z.TN == 0) return;
+    const unsigned nb = (unsigned)((z.N + 255) / 256);
+    k_tree_init<<<(unsigned)z.P, 256, 0, st>>>(a, z);
+    k_tree_box<<<nb, 256, 0, st>>>(a, z);
+    k_tree_keys<<<nb, 256, 0, st>>>(a, z);
+    k_tree_scan<<<(unsigned)z.P, 1024, 0, st>>>(a, z);
+    k_tree_scatter<<<nb, 256, 0, st>>>(a, z);
+    k_tree_leaf_order<<<nb, 256, 0, st>>>(a, z);
+    k_tree_gather<<<nb, 256, 0, st>>>(a, z);
+    k_tree_leaves<<<(unsigned)((z.TL + 127) / 128), 128, 0, st>>>(a, z);
+    for (int L = max_depth - 1; L >= 0; --L)
+        k_tree_up<<<(unsigned)((z.TN + 255) / 256), 256, 0, st>>>(a, z, L);
+    k_tree_force<<<dim3((unsigned)((z.TG + 3) / 4), kSplit), 128, 0, st>>>(a, z);
+    k_tree_combine<<<nb, 256, 0, st>>>(a, z);
+}
+
+}  // namespace dem

@@ -16,7 +16,8 @@ using namespace dem;
 
 namespace {
 
-enum Cls { C_SPH, C_SPHK, C_SPHL, C_AGG, C_CELL, C_TILE, C_CHUNK, C_PILE, C_GITEM, C_GPART, C_NCLS };
+enum Cls { C_SPH, C_SPHK, C_SPHL, C_AGG, C_CELL, C_TILE, C_CHUNK, C_PILE, C_GITEM, C_GPART, C_TNODE,
+           C_TLEAF, C_NCLS };
 
 struct Field {
     void **ptr;
@@ -63,6 +64,8 @@ struct dem_world {
     double grav_item = 1048576.0;     // else: target interactions per work item
     bool grav_pack = false;           // packed f32x2 pair terms (even grav_ib)
     bool grav_sym = true;             // mixed path: symmetric tile-pair form
+    double grav_theta = 0.0;          // > 0 (mixed path): tree gravity with this opening angle
+    int tree_maxD = 0;                // deepest tree of the current layout
     int sm_count = 0;
     double cell_factor = 1.0;
     double skin_frac = 0.1;           // neighbour-list skin / largest radius
@@ -205,6 +208,27 @@ void build_fields(dem_world *w)
     add((void **)&a.gcounter, C_PILE, 4, false);
     add((void **)&a.gitems, C_GITEM, 16, false);
     add((void **)&a.gpart, C_GPART, d ? 32 : 16, false);
+    add((void **)&a.tkey, C_SPH, 4, false);
+    add((void **)&a.trank, C_SPH, 4, false);
+    add((void **)&a.tsorted, C_SPH, 4, false);
+    add((void **)&a.tpos, C_SPH, 16, false);
+    add((void **)&a.tagg, C_SPH, 4, false);
+    add((void **)&a.tpart, C_SPH, 64 * 16, false);
+    add((void **)&a.tbox, C_PILE, 32, false);
+    add((void **)&a.tnode, C_TNODE, 48, false);
+    add((void **)&a.tnode_pile, C_TNODE, 4, false);
+    add((void **)&a.tleaf, C_TLEAF, 8, false);
+    add((void **)&a.tleaf_pile, C_TLEAF, 4, false);
+}
+
+// Tree depth of a pile under tree gravity (0 = direct sum): leaves of ~4
+// spheres, 2..6 levels below the root.
+int tree_depth(const dem_world *w, const PileHost &q)
+{
+    if (!(w->grav_theta > 0) || w->precision != DEM_MIXED || q.P.G == 0.0) return 0;
+    int D = 2;   // the walk starts at the 64 cells of level 2
+    while (D < 6 && ((int64_t)1 << (3 * D)) * 4 < q.ns) ++D;
+    return D;
 }
 
 // Elements of class c that pile q occupies (and its per-element multiplier).
@@ -219,6 +243,8 @@ int64_t pile_count(const dem_world *w, const PileHost &q, Cls c)
     case C_TILE: return q.nt;
     case C_CHUNK: return q.nch;
     case C_PILE: return 1;
+    case C_TNODE: { int D = tree_depth(w, q); return D ? (((int64_t)1 << (3 * (D + 1))) - 1) / 7 : 0; }
+    case C_TLEAF: { int D = tree_depth(w, q); return D ? (int64_t)1 << (3 * D) : 0; }
     default: return 0;
     }
 }
@@ -235,6 +261,10 @@ bool use_sym(const dem_world *w) { return w->grav_sym && w->precision == DEM_MIX
 GravPlan plan_gravity(const dem_world *w)
 {
     GravPlan g;
+    if (w->grav_theta > 0 && w->precision == DEM_MIXED) {   // tree gravity: no direct items
+        for (size_t p = 0; p < w->piles.size(); ++p) { g.nch.push_back(1); g.base.push_back(-1); }
+        return g;
+    }
     if (use_sym(w)) {
         // items: every pair of 512-sphere tiles (a, b), a <= b; partial rows
         // [b][i] and [T + a][j] (2 T rows of ns) for piles with more than one tile
@@ -384,9 +414,23 @@ dem_status relayout(dem_world *w, const std::vector<PileHost> &newp, const GravP
 dem_status upload_tables(dem_world *w, const GravPlan &gp)
 {
     std::vector<PileStatic> ps;
-    int64_t s0 = 0, a0 = 0, c0 = 0, ch0 = 0;
+    int64_t s0 = 0, a0 = 0, c0 = 0, ch0 = 0, tn0 = 0, tl0 = 0, tg0 = 0;
+    std::vector<int32_t> tnode_pile, tleaf_pile;
+    w->tree_maxD = 0;
     for (auto &q : w->piles) {
         PileStatic S{};
+        S.tD = tree_depth(w, q);
+        S.theta = (float)w->grav_theta;
+        S.tnode0 = tn0;
+        S.tleaf0 = tl0;
+        S.tg0 = tg0;
+        tg0 += (q.ns + 31) / 32;
+        const int64_t nn = pile_count(w, q, C_TNODE), nl = pile_count(w, q, C_TLEAF);
+        tnode_pile.insert(tnode_pile.end(), nn, (int32_t)ps.size());
+        tleaf_pile.insert(tleaf_pile.end(), nl, (int32_t)ps.size());
+        tn0 += nn;
+        tl0 += nl;
+        w->tree_maxD = std::max(w->tree_maxD, S.tD);
         S.s0 = s0; S.ns = q.ns; S.a0 = a0; S.na = q.na; S.c0 = c0; S.nc = q.nc;
         S.ch0 = ch0; S.nch = q.nch; S.t0 = c0 / kScanTile; S.nt = q.nt;
         S.nx = q.nx; S.ny = q.ny; S.nz = q.nz; S.K = w->K;
@@ -407,6 +451,9 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     w->Z.GI = (int64_t)gp.items.size();
     w->Z.GP = gp.gp;
     w->Z.K = w->K;
+    w->Z.TN = tn0;
+    w->Z.TL = tl0;
+    w->Z.TG = tg0;
     w->Z.adapt = 0;
     for (auto &q : w->piles)
         if (q.P.rot_tol > 0) w->Z.adapt = 1;
@@ -431,6 +478,13 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     if (!gp.items.empty())
         CU(cudaMemcpyAsync(w->A.gitems, gp.items.data(), 16 * gp.items.size(),
                            cudaMemcpyHostToDevice, w->stream));
+    if (tn0 > 0) {
+        CU(cudaMemcpyAsync(w->A.tnode_pile, tnode_pile.data(), 4 * tnode_pile.size(),
+                           cudaMemcpyHostToDevice, w->stream));
+        CU(cudaMemcpyAsync(w->A.tleaf_pile, tleaf_pile.data(), 4 * tleaf_pile.size(),
+                           cudaMemcpyHostToDevice, w->stream));
+        CU(cudaStreamSynchronize(w->stream));   // host vectors go out of scope
+    }
     launch_fill_ids(w->A, w->Z, w->stream);
     // a new layout leaves the transient sort and hit lists undefined
     launch_force_rebuild(w->A, w->Z, -1, w->stream);
@@ -454,7 +508,8 @@ void enqueue_phase(dem_world *w, int ph)
     case DEM_K_GATHER: launch_gather(a, z, d, st); break;
     case DEM_K_CONTACT: launch_contact(a, z, d, w->K, st); break;
     case DEM_K_GRAVITY:
-        launch_gravity(a, z, d, w->grav_block, w->grav_ib, w->grav_pack, use_sym(w), st);
+        if (z.TN > 0) launch_tree_gravity(a, z, w->tree_maxD, st);
+        else launch_gravity(a, z, d, w->grav_block, w->grav_ib, w->grav_pack, use_sym(w), st);
         break;
     case DEM_K_AGG_END: launch_agg_end(a, z, d, st); break;
     case DEM_K_PILE_END: launch_pile_end(a, z, st); break;
@@ -1323,6 +1378,12 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
         w->grav_pack = value != 0.0;
     } else if (k == "grav_sym") {
         w->grav_sym = value != 0.0;
+    } else if (k == "grav_theta") {
+        if (!(value >= 0.0) || !(value < 1.0)) return fail(w, DEM_ERR_ARG, "grav_theta must be in [0, 1)");
+        const double old = w->grav_theta;
+        w->grav_theta = value;
+        dem_status s = relayout(w, w->piles, nullptr);   // tree arrays change size
+        if (s != DEM_OK) { w->grav_theta = old; return s; }
     } else if (k == "grav_item") {
         if (!(value >= 1024.0)) return fail(w, DEM_ERR_ARG, "grav_item must be >= 1024");
         w->grav_item = value;
