@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-e2-collapse", action="store_true")
+    ap.add_argument("--no-tree", action="store_true")
     ap.add_argument("--part", default="all", choices=["all", "contact", "e2"],
                     help="contact: only the contact-pass roofline on the 1M-sphere lattice; "
                          "e2: only the paper's 2e4-sphere profiling collapse")
@@ -299,6 +300,43 @@ def run_e2_collapse(dem, W, steps=10, warmup=3):
     return out
 
 
+def run_tree_gravity(dem, W, steps=5, theta=0.5):
+    """The tree-gravity option (monopole + quadrupole, opening angle theta) against
+    the direct sum on collapse-100k and on the 200,000-sphere spin-up pile: step
+    and gravity-phase times, and per-sphere relative force errors after one step."""
+    import torch
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    out = {"theta": theta}
+    for name, (ic, p) in (("collapse-100k", W.config2(0)), ("spinup-200k", W.config3(0))):
+        rec = {}
+        fg = {}
+        for mode, th in (("direct", 0.0), ("tree", theta)):
+            with dem.World() as w:
+                if th:
+                    w.set_tuning("grav_theta", th)
+                pid = w.add_pile(ic, p)
+                w.set_timed_kernel("GRAVITY")
+                w.step_timed()
+                fg[mode] = w.read(pid, "SPHERE_FG")
+                st = torch.cuda.ExternalStream(w.stream)
+                ss, gg = [], []
+                for _ in range(steps):
+                    with torch.cuda.stream(st):
+                        flush.zero_()
+                    s_, g_ = w.step_timed()
+                    ss.append(s_)
+                    gg.append(g_)
+                rec[mode] = {"ms_per_step": statistics.median(ss), "gravity_ms": statistics.median(gg),
+                             "value": ic.n_sph / (statistics.median(ss) / 1e3), "unit": UNIT,
+                             "flags": w.flags(pid)}
+        e = np.linalg.norm(fg["tree"] - fg["direct"], axis=1) / np.linalg.norm(fg["direct"], axis=1)
+        rec["force_rel_error"] = {"median": float(np.median(e)), "p99": float(np.quantile(e, 0.99)),
+                                  "max": float(e.max())}
+        rec["n_spheres"] = ic.n_sph
+        out[name] = rec
+    return out
+
+
 def run_batched(dem, W, steps=5, n_piles=256):
     """256 independent piles of tetrahedra (sizes lognormal in [500, 20000]):
     all stepped by one graph launch per step after autotuning, against looping
@@ -482,6 +520,8 @@ def run_ours(args):
         out["serving"] = run_serving(dem, W)
     if rank == 0 and not args.no_e2_collapse:
         out["e2_collapse"] = run_e2_collapse(dem, W)
+    if rank == 0 and not args.no_tree:
+        out["tree_gravity"] = run_tree_gravity(dem, W)
     if not args.no_e2e:
         e = run_e2e(dem, W, ic, p, steps=args.steps)
         e_t = max_over_ranks(ic.n_sph * args.steps / e["value"], ws, device="cuda")

@@ -241,6 +241,10 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
  * when grav_ib is even, 0 = scalar FP32), "grav_sym" (mixed path: 1 =
  * symmetric tile-pair form, each pair evaluated once and applied to both
  * spheres, the default; 0 = one-sided form shaped by the keys above),
+ * "grav_theta" (mixed path: > 0 replaces the direct sum by tree gravity with
+ * this opening angle, in [0, 1): monopole + quadrupole cells of an octree
+ * rebuilt every step, leaves of ~4 spheres summed directly; relative force
+ * errors ~2e-4 median at 0.5; 0 = direct sum, the default),
  * "cell_factor" (cell edge / (2 x
  * largest radius), >= 1), "skin" (neighbour-list skin as a fraction of the
  * pile's largest radius, in [0, 4], default 0.1; 0 = search contacts afresh
