@@ -71,9 +71,10 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-e2-collapse", action="store_true")
     ap.add_argument("--no-tree", action="store_true")
-    ap.add_argument("--part", default="all", choices=["all", "contact", "e2"],
+    ap.add_argument("--part", default="all", choices=["all", "contact", "e2", "tree"],
                     help="contact: only the contact-pass roofline on the 1M-sphere lattice; "
-                         "e2: only the paper's 2e4-sphere profiling collapse")
+                         "e2: only the paper's 2e4-sphere profiling collapse; "
+                         "tree: only tree vs direct gravity")
     ap.add_argument("--contact-n", type=int, default=1_048_576)
     return ap.parse_args()
 
@@ -591,6 +592,17 @@ def run_e2_only(args):
                                                                     warmup=args.warmup)}), flush=True)
 
 
+def run_tree_only(args):
+    import torch
+    from paper_2311_11322_gb300 import dem
+    from paper_2311_11322_gb300 import workloads as W
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    print(json.dumps({"part": "tree", "tree_gravity": run_tree_gravity(dem, W, steps=args.steps)}),
+          flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
@@ -599,5 +611,7 @@ if __name__ == "__main__":
         run_contact_only(a)
     elif a.part == "e2":
         run_e2_only(a)
+    elif a.part == "tree":
+        run_tree_only(a)
     else:
         run_ours(a)
