@@ -238,9 +238,9 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
  * thread: 1, 2 or 4), "grav_item" (target pair interactions per gravity work
  * item, >= 1024; sets the j-range split), "grav_jchunk" (fixed j-range length
  * per work item, 0 = use grav_item), "grav_pack" (1 = packed f32x2 pair terms
- * when grav_ib is even, 0 = scalar FP32), "grav_sym" (mixed path: 1 =
- * symmetric tile-pair form, each pair evaluated once and applied to both
- * spheres, the default; 0 = one-sided form shaped by the keys above),
+ * when grav_ib is even, 0 = scalar FP32), "grav_sym" (1 = symmetric
+ * tile-pair form, each pair evaluated once and applied to both spheres, the
+ * default in both precisions; 0 = one-sided form shaped by the keys above),
  * "grav_theta" (mixed path: > 0 replaces the direct sum by tree gravity with
  * this opening angle, in [0, 1): monopole + quadrupole cells of an octree
  * rebuilt every step, leaves of ~4 spheres summed directly; relative force

@@ -18,7 +18,8 @@
 // range's FP64 sum rounded to FP32 (one more rounding of a sum of ~2,000
 // terms), and k_grav_combine adds them in FP64 in range order (deterministic).
 //
-// Symmetric form (mixed path, default).  The pair term is antisymmetric
+// Symmetric form (default; packed FP32 in the mixed path, scalar FP64 in the
+// FP64 path).  The pair term is antisymmetric
 // (Newton's third law): F_ij = -F_ji.  The pile is cut into tiles of 512
 // spheres; a work item is a pair of tiles (a, b), a < b, and evaluates each of
 // its 512 x 512 pairs once, adding the term to sphere i of tile a and its
@@ -682,6 +683,166 @@ __global__ void DEM_GSYM_BOUNDS k_gravity32s(Arrays a, Sizes z)
     }
 }
 
+// FP64 path, symmetric form: the same tile pairs and ring as the mixed path
+// in double precision (scalar: no packed FP64 instructions), partial sums in
+// FP64 and combined in FP64.  Shared memory: tile b (32 B per sphere), its
+// aggregates and the per-warp j-sums (4 x 512 x 32 B): 82 KB per block.
+template <bool MASK>
+__device__ __forceinline__ dbl4 sym_ring64(dbl4 pj, int aj, const dbl4 (&xi)[kSymIB], const int (&ai)[kSymIB],
+                                           double (&ax)[kSymIB], double (&ay)[kSymIB], double (&az)[kSymIB],
+                                           double eps2)
+{
+    const int src = (threadIdx.x + 1) & 31;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    for (int s = 0; s < 32; ++s) {
+#pragma unroll
+        for (int k = 0; k < kSymIB; ++k) {
+            const double dx = pj.x - xi[k].x, dy = pj.y - xi[k].y, dz = pj.z - xi[k].z;
+            const double r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
+            const double inv = rsqrt(r2);
+            const double inv3 = (inv * inv) * inv;
+            double si = pj.w * inv3, sj = -xi[k].w * inv3;
+            if (MASK && aj == ai[k]) si = sj = 0.0;
+            ax[k] = fma(dx, si, ax[k]);
+            ay[k] = fma(dy, si, ay[k]);
+            az[k] = fma(dz, si, az[k]);
+            fx = fma(dx, sj, fx);
+            fy = fma(dy, sj, fy);
+            fz = fma(dz, sj, fz);
+        }
+        pj.x = __shfl_sync(0xffffffffu, pj.x, src);
+        pj.y = __shfl_sync(0xffffffffu, pj.y, src);
+        pj.z = __shfl_sync(0xffffffffu, pj.z, src);
+        pj.w = __shfl_sync(0xffffffffu, pj.w, src);
+        fx = __shfl_sync(0xffffffffu, fx, src);
+        fy = __shfl_sync(0xffffffffu, fy, src);
+        fz = __shfl_sync(0xffffffffu, fz, src);
+        if (MASK) aj = __shfl_sync(0xffffffffu, aj, src);
+    }
+    return make_dbl4(fx, fy, fz, 0.0);
+}
+
+__device__ __forceinline__ void gravity64s_item(const Arrays &a, const int4 it, dbl4 *sp, int *sag, dbl4 *sj)
+{
+    const int p = it.x;
+    if (a.enabled[p] == 0 || a.pd[p].failed) return;
+    const PileStatic &S = a.ps[p];
+    const int64_t s0 = S.s0;
+    const int ns = (int)S.ns;
+    const int T = a.gnchunk[p];
+    const int ta = it.y, tb = it.z;
+    const bool diag = ta == tb;
+    const double eps2 = S.eps2;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int jb0 = tb * kSymTile;
+    const int nj = min(kSymTile, ns - jb0);
+    for (int m = threadIdx.x; m < kSymTile; m += kSymBS) {
+        const int j = jb0 + m;
+        sp[m] = j < ns ? a.gpos64[s0 + j] : make_dbl4(1.0e150, 1.0e150, 1.0e150, 0.0);
+        sag[m] = j < ns ? a.sph_agg[s0 + j] : -1;
+    }
+    dbl4 xi[kSymIB];
+    int ai[kSymIB];
+    double ax[kSymIB], ay[kSymIB], az[kSymIB];
+    const int i0 = ta * kSymTile + w * (32 * kSymIB) + l;
+#pragma unroll
+    for (int k = 0; k < kSymIB; ++k) {
+        const int i = i0 + 32 * k;
+        const bool ok = i < ns;
+        xi[k] = ok ? a.gpos64[s0 + i] : make_dbl4(0.0, 0.0, 0.0, 0.0);
+        ai[k] = ok ? a.sph_agg[s0 + i] : -2;
+        ax[k] = ay[k] = az[k] = 0.0;
+    }
+    const bool masked = diag || a.sph_agg[s0 + (int64_t)ta * kSymTile + kSymTile - 1] == a.sph_agg[s0 + jb0];
+    __syncthreads();
+    if (diag) {
+        for (int jj = 0; jj < nj; ++jj) {
+            const dbl4 pj = sp[jj];
+            const int aj = sag[jj];
+#pragma unroll
+            for (int k = 0; k < kSymIB; ++k) {
+                const double dx = pj.x - xi[k].x, dy = pj.y - xi[k].y, dz = pj.z - xi[k].z;
+                const double r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
+                const double inv = rsqrt(r2);
+                double si = (pj.w * inv) * (inv * inv);
+                si = aj == ai[k] ? 0.0 : si;
+                ax[k] = fma(dx, si, ax[k]);
+                ay[k] = fma(dy, si, ay[k]);
+                az[k] = fma(dz, si, az[k]);
+            }
+        }
+    } else {
+        for (int c = 0; c * 32 < nj; ++c) {
+            const dbl4 pj = sp[c * 32 + l];
+            const int aj = sag[c * 32 + l];
+            sj[w * kSymTile + c * 32 + l] = masked ? sym_ring64<true>(pj, aj, xi, ai, ax, ay, az, eps2)
+                                                   : sym_ring64<false>(pj, aj, xi, ai, ax, ay, az, eps2);
+        }
+        __syncthreads();
+        for (int m = threadIdx.x; m < nj; m += kSymBS) {
+            const dbl4 u0 = sj[m], u1 = sj[kSymTile + m], u2 = sj[2 * kSymTile + m], u3 = sj[3 * kSymTile + m];
+            ((dbl4 *)a.gpart)[sym_slot(a, p, ns, T + ta, jb0 + m)] =
+                make_dbl4(((u0.x + u1.x) + u2.x) + u3.x, ((u0.y + u1.y) + u2.y) + u3.y,
+                          ((u0.z + u1.z) + u2.z) + u3.z, 0.0);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kSymIB; ++k) {
+        const int i = i0 + 32 * k;
+        if (i >= ns) continue;
+        if (T == 1) {
+            const double gm = S.G * a.m64[s0 + i];
+            a.fg[s0 + i] = make_dbl4(gm * ax[k], gm * ay[k], gm * az[k], 0.0);
+        } else {
+            ((dbl4 *)a.gpart)[sym_slot(a, p, ns, tb, i)] = make_dbl4(ax[k], ay[k], az[k], 0.0);
+        }
+    }
+}
+
+constexpr size_t kSym64Smem = sizeof(dbl4) * kSymTile * 5 + sizeof(int) * kSymTile;
+
+__global__ void __launch_bounds__(kSymBS) k_gravity64s(Arrays a, Sizes z)
+{
+    extern __shared__ __align__(32) unsigned char sm64[];
+    dbl4 *sp = (dbl4 *)sm64;
+    dbl4 *sj = sp + kSymTile;
+    int *sag = (int *)(sj + 4 * kSymTile);
+    __shared__ int next;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) next = atomicAdd(a.gcounter, 1);
+        __syncthreads();
+        const int item = next;
+        if (item >= z.GI) return;
+        gravity64s_item(a, a.gitems[item], sp, sag, sj);
+    }
+}
+
+__global__ void k_grav_combine_sym64(Arrays a, Sizes z)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= z.N) return;
+    int p = a.sph_pile[i];
+    if (a.enabled[p] == 0 || a.pd[p].failed) return;
+    const int T = a.gnchunk[p];
+    if (T <= 1) return;
+    const PileStatic &S = a.ps[p];
+    const int64_t il = i - S.s0;
+    const int t = (int)(il / kSymTile);
+    const dbl4 *gp = (const dbl4 *)a.gpart;
+    double sx = 0, sy = 0, sz = 0;
+    for (int b = t; b < T; ++b) {
+        const dbl4 v = gp[sym_slot(a, p, S.ns, b, il)];
+        sx += v.x; sy += v.y; sz += v.z;
+    }
+    for (int r = 0; r < t; ++r) {
+        const dbl4 v = gp[sym_slot(a, p, S.ns, T + r, il)];
+        sx += v.x; sy += v.y; sz += v.z;
+    }
+    const double gm = S.G * a.m64[i];
+    a.fg[i] = make_dbl4(gm * sx, gm * sy, gm * sz, 0.0);
+}
+
 // Sphere x of tile t: its i-sums of items (t, b), b >= t, then its j-sums of
 // items (a, t), a < t, in that fixed order, as float-float sums (FFSum).
 __global__ void k_grav_combine_sym(Arrays a, Sizes z)
@@ -774,9 +935,14 @@ static int occ(bool fp64, bool pack)
 
 int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym)
 {
-    if (sym && !fp64) {
+    if (sym) {
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s, kSymBS, 0);
+        if (fp64) {
+            cudaFuncSetAttribute(k_gravity64s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSym64Smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity64s, kSymBS, kSym64Smem);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s, kSymBS, 0);
+        }
         return n;
     }
     if (block == 64) return ib == 1 ? occ<64, 1>(fp64, pack) : ib == 2 ? occ<64, 2>(fp64, pack) : occ<64, 4>(fp64, pack);
@@ -788,11 +954,16 @@ void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int i
                     bool sym, cudaStream_t st)
 {
     if (z.GI == 0) return;
-    if (sym && !fp64) {
+    if (sym) {
         int64_t nb = z.GB > 0 && z.GB < z.GI ? z.GB : z.GI;
         cudaMemsetAsync(a.gcounter, 0, sizeof(int32_t), st);
-        k_gravity32s<<<(unsigned)nb, kSymBS, 0, st>>>(a, z);
-        if (z.GP > 0) k_grav_combine_sym<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+        if (fp64) {
+            k_gravity64s<<<(unsigned)nb, kSymBS, kSym64Smem, st>>>(a, z);
+            if (z.GP > 0) k_grav_combine_sym64<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+        } else {
+            k_gravity32s<<<(unsigned)nb, kSymBS, 0, st>>>(a, z);
+            if (z.GP > 0) k_grav_combine_sym<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+        }
         return;
     }
     if (block == 64 && ib == 1) launch_g<64, 1>(a, z, fp64, pack, st);

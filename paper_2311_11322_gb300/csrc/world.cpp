@@ -256,7 +256,7 @@ struct GravPlan {
     int64_t gp = 0;
 };
 
-bool use_sym(const dem_world *w) { return w->grav_sym && w->precision == DEM_MIXED; }
+bool use_sym(const dem_world *w) { return w->grav_sym; }
 
 GravPlan plan_gravity(const dem_world *w)
 {
@@ -1412,7 +1412,7 @@ dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
     if (w->piles.empty()) return DEM_OK;
     struct Cand { int blk, ib; double item; bool pack, sym; };
     std::vector<Cand> cands;
-    if (w->precision == DEM_MIXED) cands.push_back({128, 4, 1048576.0, false, true});
+    cands.push_back({128, 4, 1048576.0, false, true});
     for (int blk : {64, 128, 256})
         for (int ib : {1, 2, 4})
             for (double item : {262144.0, 1048576.0, 4194304.0}) {
