@@ -88,7 +88,8 @@ enum dem_field {
     DEM_FIELD_SPHERE_POS = 4,  /* N x 3  sphere centres r_A + R(q) b_i */
     DEM_FIELD_FORCE = 5,       /* A x 3  total force of the last step */
     DEM_FIELD_TORQUE = 6,      /* A x 3  total torque about the COM of the last step */
-    DEM_FIELD_CONTACTS = 7,    /* N x (1 + 4K): count, then K x (partner, Sx, Sy, Sz) */
+    DEM_FIELD_CONTACTS = 7,    /* N x (1 + 4K): count, then K x (partner, Sx, Sy, Sz); S of a
+                                  pair as seen from its lower-index sphere, so both rows agree */
     DEM_FIELD_FORCE_CONTACT = 8,   /* A x 3 */
     DEM_FIELD_TORQUE_CONTACT = 9,  /* A x 3 */
     DEM_FIELD_FORCE_GRAV = 10,     /* A x 3 */

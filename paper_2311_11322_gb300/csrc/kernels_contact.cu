@@ -6,13 +6,15 @@
 // contact point at the centre of the intersection circle (Sec. 2.2.4,
 // Eq. lever_arm).
 //
-// Each pair is evaluated by both of its spheres.  Both evaluate it in the same
-// canonical orientation (lower pile-local sphere index first) with the same
-// inlined code and the same inputs, so the two results are bitwise equal and
-// opposite, and both store the same updated tangential displacement S in
-// their own history slots.  Nothing is written with atomics except error
-// flags; the neighbour order is fixed by the cell ordering, so the pass is
-// deterministic.
+// Each pair is evaluated by both of its spheres, each taking itself as sphere
+// a.  Every step of the law maps exactly onto its negative or onto itself when
+// a and b swap (differences and products of negated operands round to the
+// negated or the same result, TwoSum's error term is exact, and l_a, l_b are
+// formed as |d|/2 +- (s_a^2 - s_b^2)/(2|d|)), so the two evaluations give
+// bitwise opposite forces and couples and the tangential displacements S_b =
+// -S_a each sphere keeps in its own history.  Nothing is written with atomics
+// except error flags; each sphere sums its contacts in partner order, so the
+// pass is deterministic.
 //
 // Two kernels.  k_contact_filter (one thread per sphere in sorted order, few
 // registers, many resident warps) walks the 27 neighbour cells -- the three
@@ -171,8 +173,11 @@ __device__ __forceinline__ bool pair_mixed(float4 ah, float4 al, float4 av, floa
     float dist = __fadd_rn(r, delta);
     float3 n = f3(__fmul_rn(dhx, inv), __fmul_rn(dhy, inv), __fmul_rn(dhz, inv));
     float sa = ah.w, sb = bh.w;
-    float la = __fmul_rn(__fmaf_rn(dist, dist, __fmul_rn(sa - sb, sa + sb)), __fmul_rn(0.5f, inv));
-    float lb = __fsub_rn(dist, la);
+    // l_a, l_b = |d|/2 +- (s_a^2 - s_b^2)/(2|d|): swapping a and b swaps them exactly
+    const float hd = __fmul_rn(0.5f, dist);
+    const float g = __fmul_rn(__fmul_rn(__fsub_rn(sa, sb), __fadd_rn(sa, sb)), __fmul_rn(0.5f, inv));
+    float la = __fadd_rn(hd, g);
+    float lb = __fsub_rn(hd, g);
     force_law<float, float3, ParamsF>(n, x, la, lb, f3(av.x, av.y, av.z), f3(aw.x, aw.y, aw.z),
                                       f3(bv.x, bv.y, bv.z), f3(bw.x, bw.y, bw.z), sa, sb, Sprev,
                                       prm, o);
@@ -187,9 +192,12 @@ __device__ __forceinline__ bool pair_64(dbl4 ap, dbl4 av, dbl4 aw, dbl4 bp, dbl4
     double dist = sqrt(dot(d, d));
     double x = ap.w + bp.w - dist;
     if (!(x > 0.0) || !(dist > 0.0)) return false;
-    double3 n = (1.0 / dist) * d;
-    double la = (ap.w * ap.w - bp.w * bp.w + dist * dist) / (2.0 * dist);
-    double lb = dist - la;
+    const double inv = 1.0 / dist;
+    double3 n = inv * d;
+    const double hd = __dmul_rn(0.5, dist);
+    const double g = __dmul_rn(__dmul_rn(__dsub_rn(ap.w, bp.w), __dadd_rn(ap.w, bp.w)), __dmul_rn(0.5, inv));
+    double la = __dadd_rn(hd, g);
+    double lb = __dsub_rn(hd, g);
     force_law<double, double3, ParamsD>(n, x, la, lb, d3(av.x, av.y, av.z), d3(aw.x, aw.y, aw.z),
                                         d3(bv.x, bv.y, bv.z), d3(bw.x, bw.y, bw.z), ap.w, bp.w,
                                         Sprev, prm, o);
@@ -355,31 +363,15 @@ __device__ __forceinline__ void process(const Arrays &a, const Nb<FP64> &nb, Me<
         }
         m.cursor = slot + 1;
     }
-    // canonical orientation: the lower pile-local index is sphere a.  The
-    // operands are selected first and the pair law is inlined once, so both
-    // spheres of a pair run one instruction stream (bitwise equal results)
-    // and the lanes of a warp do not split over two copies of it.
-    const bool first = m.hl < ngid;
+    // this sphere is sphere a of the law
     PairOut<typename CT<FP64>::T, V> o;
     bool hit;
-    if constexpr (FP64) {
-        const dbl4 ap = first ? m.p : nh, av = first ? m.v : nv, aw = first ? m.w : nw;
-        const dbl4 bp = first ? nh : m.p, bv = first ? nv : m.v, bw = first ? nw : m.w;
-        hit = pair_64(ap, av, aw, bp, bv, bw, Sprev, prm, o);
-    } else {
-        const float4 nl = nb.l;
-        const float4 ah = first ? m.p : nh, al = first ? m.l : nl, av = first ? m.v : nv,
-                     aw = first ? m.w : nw;
-        const float4 bh = first ? nh : m.p, bl = first ? nl : m.l, bv = first ? nv : m.v,
-                     bw = first ? nw : m.w;
-        hit = pair_mixed(ah, al, av, aw, bh, bl, bv, bw, Sprev, prm, o);
-    }
+    if constexpr (FP64) hit = pair_64(m.p, m.v, m.w, nh, nv, nw, Sprev, prm, o);
+    else hit = pair_mixed(m.p, m.l, m.v, m.w, nh, nb.l, nv, nw, Sprev, prm, o);
     if (!hit) return;
-    // sphere a: F, (l_a n) x F + M;  sphere b: -F, (l_b n) x F - M
-    const typename CT<FP64>::T sg = first ? 1 : -1;
-    const typename CT<FP64>::T lev = first ? o.la : o.lb;
-    m.F = m.F + sg * o.F;
-    m.T = m.T + cross(lev * o.n, o.F) + sg * o.M;
+    // sphere a: F, (l_a n) x F + M
+    m.F = m.F + o.F;
+    m.T = m.T + cross(o.la * o.n, o.F) + o.M;
     if (m.nn < K) {
         if constexpr (FP64)
             ((dbl4 *)hnew_v)[(int64_t)m.nn * ns] = make_dbl4(o.S.x, o.S.y, o.S.z, (double)ngid);

@@ -1203,6 +1203,8 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
                 slot[4 * e] = pid; slot[4 * e + 1] = h[e].x; slot[4 * e + 2] = h[e].y; slot[4 * e + 3] = h[e].z;
             }
         }
+        // each sphere keeps S from its own side (S_b = -S_a); the field reports
+        // the pair's S from the side of its lower-index sphere
         for (int64_t i = 0; i < N; ++i) {
             double *o = out + i * (1 + 4 * K);
             int64_t k = pos[i];
@@ -1210,7 +1212,8 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
             o[0] = n;
             for (int t = 0; t < n; ++t) {
                 const double *e = &slot[4 * ((int64_t)t * N + k)];
-                o[1 + 4 * t] = e[0]; o[2 + 4 * t] = e[1]; o[3 + 4 * t] = e[2]; o[4 + 4 * t] = e[3];
+                const double sg = (double)i > e[0] ? -1.0 : 1.0;
+                o[1 + 4 * t] = e[0]; o[2 + 4 * t] = sg * e[1]; o[3 + 4 * t] = sg * e[2]; o[4 + 4 * t] = sg * e[3];
             }
         }
         break;
@@ -1304,13 +1307,15 @@ dem_status dem_write_state(dem_world *w, int32_t pile_id, int32_t field, const d
                 if (!(sl[0] >= 0 && sl[0] < (double)N) || !finite_all(sl + 1, 3))
                     return fail(w, DEM_ERR_ARG, "sphere %lld: bad contact entry", (long long)i);
                 int64_t idx = (int64_t)t * N + k;
+                // stored from this sphere's own side (S_b = -S_a)
+                const double sg = (double)i > sl[0] ? -1.0 : 1.0;
                 if (d64) {
-                    h64[idx] = make_dbl4(sl[1], sl[2], sl[3], sl[0]);
+                    h64[idx] = make_dbl4(sg * sl[1], sg * sl[2], sg * sl[3], sl[0]);
                 } else {
                     int32_t pid = (int32_t)sl[0];
                     float pf;
                     std::memcpy(&pf, &pid, 4);
-                    h32[idx] = make_float4((float)sl[1], (float)sl[2], (float)sl[3], pf);
+                    h32[idx] = make_float4((float)(sg * sl[1]), (float)(sg * sl[2]), (float)(sg * sl[3]), pf);
                 }
             }
         }
