@@ -366,19 +366,23 @@ def run_batched(dem, W, steps=5, n_piles=256):
                         "each on a jittered lattice in a ball, mixed precision"}
 
 
-def run_serving(dem, W, n_req=24, steps=2000, n_hi=20000):
+def run_serving(dem, W, n_req=24, steps=2000, n_hi=20000, theta=0.0):
     """Poisson trace (4 arrivals/s) of tidal-flyby piles, sizes log-uniform in
-    [1,000, n_hi] spheres, `steps` steps each, served by continuous batching."""
+    [1,000, n_hi] spheres, `steps` steps each, served by continuous batching
+    (with tree gravity at opening angle theta when theta > 0)."""
     from paper_2311_11322_gb300 import serve
     trace = W.config5_trace(0, n_arrivals=n_req, rate=4.0, n_hi=n_hi, steps=steps)
     reqs = serve.trace_requests(trace, W.config5_pile)
     with dem.World() as w:
+        if theta:
+            w.set_tuning("grav_theta", theta)
         srv = serve.Server(w, dem.dem_footprint_bytes, budget_bytes=64 << 30, max_piles=64,
                            chunk=250)
         st = srv.run(reqs)
     st.update({"trace": "%d Poisson arrivals at 4/s, sizes log-uniform [1000, %d] spheres, %d "
                         "steps each (reduced from 20,000 to keep the run short), tidal flyby "
-                        "of an Earth-mass planet" % (n_req, n_hi, steps)})
+                        "of an Earth-mass planet" % (n_req, n_hi, steps),
+               "gravity": "tree, theta %.2f" % theta if theta else "direct sum"})
     return st
 
 
@@ -519,6 +523,8 @@ def run_ours(args):
         out["batched"] = run_batched(dem, W)
     if rank == 0 and not args.no_serving:
         out["serving"] = run_serving(dem, W)
+        # the configuration's full size range (1,000-100,000 spheres) with tree gravity
+        out["serving_tree"] = run_serving(dem, W, n_hi=100_000, theta=0.5)
     if rank == 0 and not args.no_e2_collapse:
         out["e2_collapse"] = run_e2_collapse(dem, W)
     if rank == 0 and not args.no_tree:
