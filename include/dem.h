@@ -302,7 +302,9 @@ dem_status dem_gravity_noalloc(const void *pos_mass, const double *mass, const i
                                int32_t n, double G, double eps_soft, double *force_out,
                                void *cuda_stream, char *msg, size_t msg_len);
 
-/* Device bytes one pile of this size needs (state, sorted copies, cells, history). */
+/* Device bytes one pile of this size needs with direct-sum gravity (state, sorted
+ * copies, cells, history, gravity partial sums).  Tree gravity (grav_theta > 0)
+ * needs instead about 1.1 KB per sphere plus 60 B per tree cell. */
 size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contacts,
                            int32_t precision);
 

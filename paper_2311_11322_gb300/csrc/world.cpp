@@ -17,7 +17,7 @@ using namespace dem;
 namespace {
 
 enum Cls { C_SPH, C_SPHK, C_SPHL, C_AGG, C_CELL, C_TILE, C_CHUNK, C_PILE, C_GITEM, C_GPART, C_TNODE,
-           C_TLEAF, C_NCLS };
+           C_TLEAF, C_TSPH, C_NCLS };
 
 struct Field {
     void **ptr;
@@ -208,12 +208,12 @@ void build_fields(dem_world *w)
     add((void **)&a.gcounter, C_PILE, 4, false);
     add((void **)&a.gitems, C_GITEM, 16, false);
     add((void **)&a.gpart, C_GPART, d ? 32 : 16, false);
-    add((void **)&a.tkey, C_SPH, 4, false);
-    add((void **)&a.trank, C_SPH, 4, false);
-    add((void **)&a.tsorted, C_SPH, 4, false);
-    add((void **)&a.tpos, C_SPH, 16, false);
-    add((void **)&a.tagg, C_SPH, 4, false);
-    add((void **)&a.tpart, C_SPH, 64 * 16, false);
+    add((void **)&a.tkey, C_TSPH, 4, false);
+    add((void **)&a.trank, C_TSPH, 4, false);
+    add((void **)&a.tsorted, C_TSPH, 4, false);
+    add((void **)&a.tpos, C_TSPH, 16, false);
+    add((void **)&a.tagg, C_TSPH, 4, false);
+    add((void **)&a.tpart, C_TSPH, 64 * 16, false);
     add((void **)&a.tbox, C_PILE, 32, false);
     add((void **)&a.tnode, C_TNODE, 48, false);
     add((void **)&a.tnode_pile, C_TNODE, 4, false);
@@ -245,6 +245,9 @@ int64_t pile_count(const dem_world *w, const PileHost &q, Cls c)
     case C_PILE: return 1;
     case C_TNODE: { int D = tree_depth(w, q); return D ? (((int64_t)1 << (3 * (D + 1))) - 1) / 7 : 0; }
     case C_TLEAF: { int D = tree_depth(w, q); return D ? (int64_t)1 << (3 * D) : 0; }
+    // per-sphere tree arrays, indexed like the sphere arrays: every pile gets
+    // them while tree gravity is on, none otherwise
+    case C_TSPH: return (w->grav_theta > 0 && w->precision == DEM_MIXED) ? q.ns : 0;
     default: return 0;
     }
 }
@@ -1497,6 +1500,11 @@ size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contact
                    agg * (size_t)n_agg + 8 * (size_t)cells + 4 * (size_t)(cells / kScanTile + 1) +
                    (size_t)(n_agg / kAggChunk + 1) * (8 * kPartialDoubles + 4) +
                    sizeof(PileStatic) + sizeof(PileDyn) + 16 + 16 * (size_t)(n_spheres / 64 + 1);
+    // direct-sum gravity: partial sums of the 512-sphere tile pairs (2 T rows of
+    // n spheres) and the work items (T (T + 1) / 2)
+    const int64_t T = (n_spheres + kGravSymTile - 1) / kGravSymTile;
+    if (T > 1) bytes += (size_t)(2 * T) * (size_t)n_spheres * (d ? 32 : 16);
+    bytes += 16 * (size_t)(T * (T + 1) / 2);
     return bytes;
 }
 
