@@ -365,15 +365,16 @@ __device__ __forceinline__ void node_force(const float4 &A, const float4 &B, con
 // subtrees at level kSplitL (one warp each, grid dimension y), so that many
 // more warps hide the latency of the rounds; each writes its partial sum,
 // k_tree_combine adds them in order.
-__global__ void __launch_bounds__(128) k_tree_force(Arrays a, Sizes z)
+__global__ void __launch_bounds__(32) k_tree_force(Arrays a, Sizes z)
 {
-    __shared__ int stk[4][kTreeStack];
+    // one warp per block: walks of very different lengths do not hold one
+    // another's block resident
+    __shared__ int st[kTreeStack];
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
     const int sub = blockIdx.y;   // subtree: cell sub at level kSplitL
-    int *st = stk[wid];
-    const int64_t wg = (int64_t)blockIdx.x * 4 + wid;   // group
+    const int64_t wg = blockIdx.x;   // group
     if (wg >= z.TG) return;
     int lo = 0, hi = (int)z.P - 1;   // pile of the group
     while (lo < hi) {
@@ -534,7 +535,7 @@ void launch_tree_gravity(const Arrays &a, const Sizes &z, int max_depth, cudaStr
     k_tree_leaves<<<(unsigned)((z.TL + 127) / 128), 128, 0, st>>>(a, z);
     for (int L = max_depth - 1; L >= 0; --L)
         k_tree_up<<<(unsigned)((z.TN + 255) / 256), 256, 0, st>>>(a, z, L);
-    k_tree_force<<<dim3((unsigned)((z.TG + 3) / 4), kSplit), 128, 0, st>>>(a, z);
+    k_tree_force<<<dim3((unsigned)z.TG, kSplit), 32, 0, st>>>(a, z);
     k_tree_combine<<<nb, 256, 0, st>>>(a, z);
 }
 
