@@ -504,6 +504,12 @@ __device__ __forceinline__ float4 sym_ring(float4 pj, int aj, const float4 (&xi)
     return make_float4(fx, fy, fz, 0.f);
 }
 
+// ring steps unrolled per loop iteration (a tuning constant)
+#ifndef DEM_RING_UNROLL
+#define DEM_RING_UNROLL 4
+#endif
+constexpr int kRingUnroll = DEM_RING_UNROLL;
+
 // Packed ring (unmasked tile pairs): each lane holds two j-spheres, packed
 // into the two halves of 64-bit registers, and its 4 i-spheres duplicated into
 // both halves, so one f32x2 instruction evaluates the same step of two pairs.
@@ -519,7 +525,7 @@ __device__ __forceinline__ void sym_ring2(const float4 &pa, const float4 &pb,
     f2_t jx = f2_pack(pa.x, pb.x), jy = f2_pack(pa.y, pb.y), jz = f2_pack(pa.z, pb.z),
          jm = f2_pack(pa.w, pb.w);
     f2_t fx = f2_pack(0.f, 0.f), fy = fx, fz = fx;
-#pragma unroll 2
+#pragma unroll kRingUnroll
     for (int s = 0; s < 32; ++s) {
 #pragma unroll
         for (int k = 0; k < kSymIB; ++k) {
