@@ -519,6 +519,12 @@ def run_ours(args):
         out["fp64_path"]["mixed_over_fp64"] = value / ws / out["fp64_path"]["value"]
     if rank == 0 and not args.no_contact:
         out["roofline_contact"] = run_contact_roofline(dem, W, hbm_peak)
+        # the same pass at 2M and 4M spheres (working sets of 0.9 and 1.8 GB)
+        out["roofline_contact_sweep"] = []
+        for n in (2 * 1_048_576, 4 * 1_048_576):
+            r = run_contact_roofline(dem, W, hbm_peak, n=n)
+            out["roofline_contact_sweep"].append({k: r[k] for k in ("n_spheres", "kernel_ms", "achieved",
+                                                                    "frac", "rebuild_step_contact_ms")})
     if rank == 0 and not args.no_batched:
         out["batched"] = run_batched(dem, W)
     if rank == 0 and not args.no_serving:
