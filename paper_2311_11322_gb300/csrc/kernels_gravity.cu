@@ -506,7 +506,7 @@ __device__ __forceinline__ float4 sym_ring(float4 pj, int aj, const float4 (&xi)
 
 // ring steps unrolled per loop iteration (a tuning constant)
 #ifndef DEM_RING_UNROLL
-#define DEM_RING_UNROLL 4
+#define DEM_RING_UNROLL 16
 #endif
 constexpr int kRingUnroll = DEM_RING_UNROLL;
 
