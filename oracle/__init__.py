@@ -222,6 +222,57 @@ def rotate_adaptive(q, wb, I, Iinv, h, tol):
     return q, wb, int(n)
 
 
+BULK_KEYS = ("mass", "com", "vcom", "axes", "radius", "density", "spin", "period", "p_crit",
+             "planet_dist", "L", "moments")
+
+
+def bulk(M, I, r, v, q, wb, G, planet_pos=None):
+    """Bulk shape and spin of a pile of rigid aggregates (Sec. 4.1, 4.2).
+
+    Reading: the paper measures the growth of a pile's radius and uses its
+    bulk density without defining either; both are taken from the uniform
+    ellipsoid with the pile's mass and principal moments of inertia about its
+    COM.  Inertia of the pile: every aggregate's own tensor rotated to space
+    plus its COM's orbital term; spin: the rigid rotation I^-1 L that carries
+    the pile's angular momentum about its COM; nominal critical period
+    sqrt(3 pi / (G rho)) of a rigid sphere of that bulk density (Sec. 4.1).
+    M [A], I [A][3][3] body frame, r, v [A][3], q [A][4], wb [A][3] body spin.
+    """
+    M = np.asarray(M, np.float64)
+    r = np.asarray(r, np.float64).reshape(-1, 3)
+    v = np.asarray(v, np.float64).reshape(-1, 3)
+    I = np.asarray(I, np.float64).reshape(-1, 3, 3)
+    wb = np.asarray(wb, np.float64).reshape(-1, 3)
+    Mt = float(M.sum())
+    c = (M[:, None] * r).sum(0) / Mt
+    vc = (M[:, None] * v).sum(0) / Mt
+    Ip = np.zeros((3, 3))
+    L = np.zeros(3)
+    for a in range(len(M)):
+        R = rotmat(q[a])
+        x = r[a] - c
+        Ip += M[a] * (np.dot(x, x) * np.eye(3) - np.outer(x, x)) + R @ I[a] @ R.T
+        L += M[a] * np.cross(x, v[a] - vc) + R @ (I[a] @ wb[a])
+    mom = np.linalg.eigvalsh(Ip)                       # ascending
+    k = 5.0 / (2.0 * Mt)
+    ax2 = k * np.array([mom[1] + mom[2] - mom[0], mom[0] + mom[2] - mom[1], mom[0] + mom[1] - mom[2]])
+    axes = np.sqrt(np.maximum(ax2, 0.0))
+    vol = float(np.prod(axes))
+    rho = 3.0 * Mt / (4.0 * np.pi * vol) if vol > 0 else np.inf
+    w = np.linalg.solve(Ip, L)
+    wn = float(np.linalg.norm(w))
+    dist = 0.0 if planet_pos is None else float(np.linalg.norm(np.asarray(planet_pos) - c))
+    return {"mass": Mt, "com": c, "vcom": vc, "axes": axes, "radius": vol ** (1.0 / 3.0),
+            "density": rho, "spin": w, "period": 2 * np.pi / wn if wn > 0 else np.inf,
+            "p_crit": float(np.sqrt(3 * np.pi / (G * rho))) if G > 0 and np.isfinite(rho) else np.inf,
+            "planet_dist": dist, "L": L, "moments": mom}
+
+
+def roche_distance(R_primary, rho_primary, rho_pile):
+    """Nominal disruption distance 1.26 R (rho_M / rho_m)^(1/3) (Sec. 4.2)."""
+    return 1.26 * R_primary * (rho_primary / rho_pile) ** (1.0 / 3.0)
+
+
 class Pile:
     """One rubble pile advanced by the oracle's leapfrog (Sec. 2.1, 2.2)."""
 
@@ -318,6 +369,11 @@ class Pile:
 
     def linear_momentum(self):
         return np.sum(self.M[:, None] * self.v, axis=0)
+
+    def bulk(self):
+        """Bulk shape and spin of this pile (module function ``bulk``)."""
+        planet = self.planet[:3] if getattr(self.params, "ext_mass", 0.0) > 0 else None
+        return bulk(self.M, self.I, self.r, self.v, self.q, self.wb, self.params.G, planet)
 
     def angular_momentum(self, about=None):
         about = np.zeros(3) if about is None else np.asarray(about, np.float64)

@@ -572,3 +572,127 @@ def test_adaptive_rotation_conserves_and_beats_rk4(oracle_lib):
     assert wb[0] == pytest.approx(w[0], abs=1e-14)
     assert wb[1] == pytest.approx(w[1] * np.cos(Om * t), abs=1e-8 * w[1])
     assert wb[2] == pytest.approx(w[1] * np.sin(Om * t), abs=1e-8 * w[1])
+
+
+# ---------------------------------------------------------------- bulk shape and spin (Sec. 4.1, 4.2)
+def _free_spheres(pos, s, rho=2500.0):
+    import oracle
+    n = len(pos)
+    return oracle.build_aggregates(np.ones(n, np.int32), pos, np.full(n, s), np.full(n, rho))
+
+
+def _unit_quats(rng, n):
+    q = rng.standard_normal((n, 4))
+    return q / np.linalg.norm(q, axis=1)[:, None]
+
+
+def test_bulk_single_sphere_closed_form(oracle_lib):
+    """One sphere: the equal-moment ellipsoid is the sphere itself, so the
+    semi-axes and bulk radius are its radius, the bulk density its density,
+    and the nominal critical period is sqrt(3 pi / (G rho)) (Sec. 4.1)."""
+    import oracle
+    s, rho, G = 3.0, 2000.0, W.G_SI
+    ag = _free_spheres(np.array([[1.0, -2.0, 5.0]]), s, rho)
+    b = oracle.bulk(ag["M"], ag["I"], ag["com"], np.zeros((1, 3)), np.array([[1.0, 0, 0, 0]]),
+                    np.zeros((1, 3)), G)
+    assert np.allclose(b["axes"], s, rtol=1e-13)
+    assert b["radius"] == pytest.approx(s, rel=1e-13)
+    assert b["density"] == pytest.approx(rho, rel=1e-13)
+    assert b["p_crit"] == pytest.approx(math.sqrt(3 * math.pi / (G * rho)), rel=1e-13)
+    assert b["period"] == math.inf and b["planet_dist"] == 0.0
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_bulk_six_sphere_cross_closed_form(oracle_lib, seed):
+    """Six equal spheres (radius s) at +-a x, +-b y, +-c z: the principal
+    moments are 2 m (b^2 + c^2) + 12/5 m s^2 and cyclic, so the semi-axes are
+    sqrt(5/3 a^2 + s^2) etc. (worked by hand); a rigid rotation of the whole
+    set changes neither them nor the moments."""
+    import oracle
+    a, b, c, s = 9.0, 5.0, 2.0, 0.5
+    pts = np.array([[a, 0, 0], [-a, 0, 0], [0, b, 0], [0, -b, 0], [0, 0, c], [0, 0, -c]])
+    rng = np.random.default_rng(seed)
+    Q = np.linalg.qr(rng.standard_normal((3, 3)))[0]
+    Q *= np.sign(np.linalg.det(Q))
+    shift = rng.uniform(-100, 100, 3)
+    want = np.sqrt(5.0 / 3.0 * np.array([a, b, c]) ** 2 + s * s)
+    m = 2500.0 * 4.0 / 3.0 * math.pi * s ** 3
+    mom = np.sort([2 * m * (b * b + c * c), 2 * m * (a * a + c * c), 2 * m * (a * a + b * b)]) + 12 / 5 * m * s * s
+    for P in (pts, pts @ Q.T + shift):
+        ag = _free_spheres(P, s)
+        q = _unit_quats(rng, 6)        # a sphere's orientation changes nothing
+        out = oracle.bulk(ag["M"], ag["I"], ag["com"], np.zeros((6, 3)), q, np.zeros((6, 3)), 0.0)
+        assert np.allclose(out["axes"], want, rtol=1e-12)
+        assert np.allclose(out["moments"], mom, rtol=1e-12)
+        assert np.allclose(out["com"], P.mean(0), atol=1e-12)
+        assert out["p_crit"] == math.inf
+
+
+def _rotated_pile(seed):
+    import oracle
+    ic, _ = W.random_cluster(seed, n_agg=30, box=8.0)
+    ag = oracle.build_aggregates(ic.counts, ic.pos, ic.radius, ic.density)
+    rng = np.random.default_rng(seed + 100)
+    return ic, ag, _unit_quats(rng, len(ic.counts))
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_bulk_inertia_equals_sphere_level_sum(oracle_lib, seed):
+    """The pile inertia built from rotated aggregate tensors equals the brute
+    sum over spheres (positions r_A + R b_i, own moments 2/5 m s^2): a
+    transposed rotation or a missing parallel-axis term fails this."""
+    import oracle
+    ic, ag, q = _rotated_pile(seed)
+    A = len(ic.counts)
+    out = oracle.bulk(ag["M"], ag["I"], ag["com"], np.zeros((A, 3)), q, np.zeros((A, 3)), 0.0)
+    x = np.array([ag["com"][ag["agg_of"][i]] + oracle.rotmat(q[ag["agg_of"][i]]) @ ag["b"][i]
+                  for i in range(len(ic.radius))])
+    m = ag["m"]
+    c = (m[:, None] * x).sum(0) / m.sum()
+    d = x - c
+    I = np.zeros((3, 3))
+    for i in range(len(m)):
+        I += m[i] * (d[i] @ d[i] * np.eye(3) - np.outer(d[i], d[i])) + 0.4 * m[i] * ic.radius[i] ** 2 * np.eye(3)
+    assert np.allclose(out["moments"], np.linalg.eigvalsh(I), rtol=1e-11)
+    assert np.allclose(out["com"], c, atol=1e-10)
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_bulk_rigid_rotation_recovers_spin(oracle_lib, seed):
+    """Every aggregate moving with one rigid rotation Omega (v_A = V + Omega x
+    (r_A - c), spin Omega): the pile spin is Omega, the period 2 pi / |Omega|,
+    and L = I Omega."""
+    import oracle
+    ic, ag, q = _rotated_pile(seed)
+    A = len(ic.counts)
+    rng = np.random.default_rng(seed)
+    Om = rng.standard_normal(3) * 1e-3
+    V = rng.standard_normal(3)
+    c = (ag["M"][:, None] * ag["com"]).sum(0) / ag["M"].sum()
+    v = V + np.cross(Om, ag["com"] - c)
+    wb = np.array([oracle.rotmat(q[a]).T @ Om for a in range(A)])
+    out = oracle.bulk(ag["M"], ag["I"], ag["com"], v, q, wb, 0.0)
+    assert np.allclose(out["spin"], Om, rtol=1e-10, atol=1e-16)
+    assert out["period"] == pytest.approx(2 * math.pi / np.linalg.norm(Om), rel=1e-10)
+    assert np.allclose(out["vcom"], V, atol=1e-12)
+
+
+def test_bulk_uniform_ball_and_roche(oracle_lib):
+    """20,000 small spheres uniform in a ball of radius 10: the equal-moment
+    ellipsoid is that ball to sampling accuracy (<x^2> = R^2 / 5), so the bulk
+    radius is 10 and the bulk density the mass over the ball's volume.  The
+    Roche normalisation reduces to 1.26 R for equal densities (Sec. 4.2)."""
+    import oracle
+    rng = np.random.default_rng(11)
+    n, R = 20000, 10.0
+    d = rng.standard_normal((n, 3))
+    d *= (R * rng.uniform(0, 1, n) ** (1 / 3) / np.linalg.norm(d, axis=1))[:, None]
+    ag = _free_spheres(d, 1e-3)
+    out = oracle.bulk(ag["M"], ag["I"], ag["com"], np.zeros((n, 3)), np.tile([1.0, 0, 0, 0], (n, 1)),
+                      np.zeros((n, 3)), 0.0, planet_pos=np.array([0.0, 0.0, 500.0]))
+    assert np.allclose(out["axes"], R, rtol=0.03)
+    assert out["radius"] == pytest.approx(R, rel=0.02)
+    assert out["density"] == pytest.approx(ag["M"].sum() / (4 / 3 * math.pi * R ** 3), rel=0.06)
+    assert out["planet_dist"] == pytest.approx(np.linalg.norm([0, 0, 500.0] - out["com"]), rel=1e-14)
+    assert oracle.roche_distance(7.0, 3000.0, 3000.0) == pytest.approx(1.26 * 7.0)
+    assert oracle.roche_distance(7.0, 3000.0, 375.0) == pytest.approx(1.26 * 7.0 * 2.0)
