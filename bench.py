@@ -30,6 +30,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -71,10 +72,12 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-e2-collapse", action="store_true")
     ap.add_argument("--no-tree", action="store_true")
-    ap.add_argument("--part", default="all", choices=["all", "contact", "e2", "tree"],
+    ap.add_argument("--no-analysis", action="store_true")
+    ap.add_argument("--part", default="all", choices=["all", "contact", "e2", "tree", "analysis"],
                     help="contact: only the contact-pass roofline on the 1M-sphere lattice; "
                          "e2: only the paper's 2e4-sphere profiling collapse; "
-                         "tree: only tree vs direct gravity")
+                         "tree: only tree vs direct gravity; "
+                         "analysis: only the spin-up and encounter runs with device-side watches")
     ap.add_argument("--contact-n", type=int, default=1_048_576)
     return ap.parse_args()
 
@@ -338,6 +341,63 @@ def run_tree_gravity(dem, W, steps=5, theta=0.5):
     return out
 
 
+def run_analysis(dem, W, n_agg=250, settle=150_000, omega_target=1.5, ramp_pcrit=2.0,
+                 max_steps=600_000, chunk=20_000):
+    """The spin-up and tidal-encounter analyses (Sec. 4.1, 4.2) on the device: a
+    lattice pile of n_agg tetrahedra settles under self-gravity; then two copies
+    step together in one world (one graph per step), one spun up by a constant
+    spin increment reaching omega_target x the nominal critical spin over
+    ramp_pcrit critical periods, one on a flyby of an Earth-mass planet (close
+    approach 1.2 Earth radii, v_inf 3 km/s, started 3 Roche distances out),
+    each with a radius-growth watch (5% and 0.5%) evaluated every 10 steps
+    inside the graph."""
+    from paper_2311_11322_gb300 import analysis
+    rng = np.random.default_rng(0)
+    ic = W.lattice_pile(rng, n_agg, shapes=("tetra",))
+    p = W.settled_params(ic, 1.0)
+    t0 = time.perf_counter()
+    with dem.World() as w:
+        pid = w.add_pile(ic, p)
+        b_lat = w.bulk(pid)
+        ic_s = analysis.settled(w, pid, settle, chunk)
+        b_set = w.bulk(pid)
+    t_settle = time.perf_counter() - t0
+    P_steps = b_set["p_crit"] / p.dt
+    ps = analysis.spinup_params(p, ic_s, omega_target * 2 * math.pi / b_set["p_crit"],
+                                int(ramp_pcrit * P_steps))
+    pe, orb = analysis.encounter_params(p, ic_s)
+    out = {"n_spheres": ic.n_sph, "n_aggregates": ic.n_agg, "dt_s": p.dt, "settle_steps": settle,
+           "settle_s": t_settle, "settle_value": ic.n_sph * settle / t_settle, "unit": UNIT,
+           "lattice_radius_m": b_lat["radius"], "settled_radius_m": b_set["radius"],
+           "settled_density": b_set["density"], "p_crit_s": b_set["p_crit"],
+           "spin_ramp": f"{omega_target} x nominal critical spin over {ramp_pcrit} critical periods",
+           "encounter": {"periapsis_earth_radii": orb["q"] / W.EARTH_RADIUS, "v_inf_kms": orb["vinf"] / 1e3}}
+    with dem.World() as w:
+        a, b = w.add_pile(ic_s, ps), w.add_pile(ic_s, pe)
+        w.watch(a, 0.05, 10)
+        w.watch(b, 0.005, 10)
+        live, taken, sph_steps = [a, b], 0, 0
+        t0 = time.perf_counter()
+        while live and taken < max_steps:
+            w.step(chunk, piles=live)
+            taken += chunk
+            sph_steps += chunk * ic.n_sph * len(live)
+            live = [x for x in live if w.watch_result(x)["fired_step"] is None]
+        w.sync()
+        t = time.perf_counter() - t0
+        ra, rb = w.watch_result(a), w.watch_result(b)
+    out["runs_s"] = t
+    out["runs_value"] = sph_steps / t
+    out["spinup"] = {"fired_step": ra["fired_step"], "critical_spin_ratio": analysis.critical_spin_ratio(ra),
+                     "period_at_fire_s": ra["at_fire"]["period"] if ra["at_fire"] else None}
+    out["encounter_run"] = {"fired_step": rb["fired_step"], "disruption_ratio": analysis.disruption_ratio(rb),
+                            "distance_at_fire_km": rb["at_fire"]["planet_dist"] / 1e3 if rb["at_fire"] else None}
+    out["paper_context"] = ("Sec. 4.1 / 4.2 tables: critical spin ratios 100-120% and disruption ratios "
+                            "55-85% for 2,500-20,000-grain piles; their initial conditions and spin-up "
+                            "rate are not published, so the ratios here are not comparable")
+    return out
+
+
 def run_batched(dem, W, steps=5, n_piles=256):
     """256 independent piles of tetrahedra (sizes lognormal in [500, 20000]):
     all stepped by one graph launch per step after autotuning, against looping
@@ -535,6 +595,8 @@ def run_ours(args):
         out["e2_collapse"] = run_e2_collapse(dem, W)
     if rank == 0 and not args.no_tree:
         out["tree_gravity"] = run_tree_gravity(dem, W)
+    if rank == 0 and not args.no_analysis:
+        out["analysis"] = run_analysis(dem, W)
     if not args.no_e2e:
         e = run_e2e(dem, W, ic, p, steps=args.steps)
         e_t = max_over_ranks(ic.n_sph * args.steps / e["value"], ws, device="cuda")
@@ -615,6 +677,16 @@ def run_tree_only(args):
           flush=True)
 
 
+def run_analysis_only(args):
+    import torch
+    from paper_2311_11322_gb300 import dem
+    from paper_2311_11322_gb300 import workloads as W
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    print(json.dumps({"part": "analysis", "analysis": run_analysis(dem, W)}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
@@ -625,5 +697,7 @@ if __name__ == "__main__":
         run_e2_only(a)
     elif a.part == "tree":
         run_tree_only(a)
+    elif a.part == "analysis":
+        run_analysis_only(a)
     else:
         run_ours(a)

@@ -270,6 +270,61 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value);
 dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out);
 
 /*
+ * Bulk shape and spin of a pile: the quantities behind the critical spin
+ * ratio (Sec. 4.1) and the disruption ratio (Sec. 4.2).  Computed on the
+ * device from the aggregate state after the last step, in FP64:
+ *   M, COM r_c, v_c: sums over the aggregates;
+ *   I: inertia tensor about r_c, sum of M_A (|x_A|^2 1 - x_A x_A^T) +
+ *      R_A I_A R_A^T with x_A = r_A - r_c (the spheres' own moments enter
+ *      through I_A);
+ *   L: angular momentum about r_c, sum of M_A x_A x (v_A - v_c) + R_A I_A w_A;
+ *   principal moments I1 <= I2 <= I3 of I (cyclic Jacobi);
+ *   semi-axes a >= b >= c of the uniform ellipsoid with the same mass and
+ *      principal moments: a^2 = 5 (I2 + I3 - I1) / (2 M), b^2 = 5 (I1 + I3 - I2)
+ *      / (2 M), c^2 = 5 (I1 + I2 - I3) / (2 M);
+ *   bulk radius R_b = (a b c)^(1/3) and bulk density rho_b = 3 M / (4 pi a b c);
+ *   spin w = I^-1 L (the rigid rotation carrying L), period 2 pi / |w|
+ *      (infinity at rest);
+ *   nominal critical period P_crit = sqrt(3 pi / (G rho_b)) (Sec. 4.1;
+ *      infinity when G = 0);
+ *   distance from r_c to the point-mass planet (0 when there is none).
+ * out [DEM_BULK_LEN] receives the record laid out as enum dem_bulk.
+ * Synchronises the stream.
+ * Errors: DEM_ERR_ARG (unknown pile, n_out < DEM_BULK_LEN), DEM_ERR_CUDA.
+ */
+enum dem_bulk {
+    DEM_BULK_MASS = 0, DEM_BULK_COM = 1, DEM_BULK_VCOM = 4, DEM_BULK_AXES = 7,
+    DEM_BULK_RADIUS = 10, DEM_BULK_DENSITY = 11, DEM_BULK_SPIN = 12, DEM_BULK_PERIOD = 15,
+    DEM_BULK_PCRIT = 16, DEM_BULK_PLANET_DIST = 17, DEM_BULK_L = 18, DEM_BULK_MOMENTS = 21,
+    DEM_BULK_LEN = 24
+};
+dem_status dem_pile_bulk(dem_world *w, int32_t pile_id, double *out, int64_t n_out);
+
+/*
+ * Radius-growth watch (the stopping rule of Sec. 4.1 and 4.2): evaluate the
+ * bulk record of a pile on the device inside the step graph, every `every`
+ * steps (counted from the pile's step counter), and latch the first record
+ * whose bulk radius reaches (1 + growth) R_b0, R_b0 being the bulk radius
+ * when the watch is armed.  growth > 0 arms (taking R_b0 and the record at
+ * that moment, and clearing an earlier latch); growth = 0 disarms.  The host
+ * polls with dem_watch_result; nothing is copied back while stepping.
+ * Arming or disarming recaptures the step graph on the next step.
+ * Errors: DEM_ERR_ARG (unknown pile, growth < 0 or not finite, every < 1),
+ * DEM_ERR_CUDA.
+ */
+dem_status dem_watch(dem_world *w, int32_t pile_id, double growth, int64_t every);
+
+/*
+ * State of a pile's watch, out [DEM_WATCH_LEN]: [0] step count at the latch
+ * (-1 while not reached), [1] growth, [2] every, [3] armed (1/0), [4..27] the
+ * bulk record when armed (enum dem_bulk), [28..51] the latched bulk record
+ * (zeros while not reached).  Synchronises the stream.
+ * Errors: DEM_ERR_ARG (unknown pile, n_out < DEM_WATCH_LEN), DEM_ERR_CUDA.
+ */
+enum { DEM_WATCH_LEN = 52 };
+dem_status dem_watch_result(dem_world *w, int32_t pile_id, double *out, int64_t n_out);
+
+/*
  * Softened direct-sum gravity of one set of spheres that allocates nothing.
  * The paper has no counterpart: this entry point serves callers that cannot
  * allocate device memory -- code running inside another program's memory

@@ -57,6 +57,20 @@ struct PileDyn {
     int32_t rebuilds;         // number of rebuilds so far
 };
 
+// Bulk shape and spin of a pile (record laid out as enum dem_bulk) and its
+// radius-growth watch (device-owned; the host writes it only to arm).
+constexpr int kBulkParts = 25;   // doubles summed per aggregate chunk
+struct PileWatch {
+    double growth;               // > 0: armed; trigger at R_b >= (1 + growth) R_b0
+    int64_t every;               // evaluate when steps % every == 0
+    int64_t fired;               // step count at the latch, -1 = not yet
+    int32_t arm;                 // 1: the next evaluation takes R_b0 (arming)
+    int32_t pad;
+    double now[DEM_BULK_LEN];    // last evaluation
+    double at_arm[DEM_BULK_LEN]; // evaluation when armed
+    double at_fire[DEM_BULK_LEN];// latched evaluation
+};
+
 // Per-aggregate quantities the sphere kernels need, mixed precision.
 // R and c are float-float (hi + lo) so that sphere positions relative to the
 // pile frame keep ~48 bits; velocity and spin are plain FP32, relative to the
@@ -125,6 +139,8 @@ struct Arrays {
     // pile reductions
     double *chunk_part;            // [chunks][kPartialDoubles]
     int32_t *chunk_pile;           // [chunks] pile slot of each chunk
+    double *bulk_part;             // [chunks][32] bulk-shape sums (kBulkParts used)
+    PileWatch *watch;              // [piles]
     // gravity work list and j-chunk partial sums
     int4 *gitems;                  // (pile, i0 local, j0 local, j1 local)
     void *gpart;                   // partial sum of one j-range per sphere (scratch):
@@ -179,5 +195,9 @@ void launch_pile_end(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_fill_ids(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_tree_gravity(const Arrays &a, const Sizes &z, int max_depth, cudaStream_t st);
 void launch_force_rebuild(const Arrays &a, const Sizes &z, int slot, cudaStream_t st);
+// bulk record of piles into watch.now (mode 0: every pile, or only slot
+// `only` when >= 0; mode 1: the watch evaluation inside the step graph, armed
+// piles whose step is due)
+void launch_bulk(const Arrays &a, const Sizes &z, int mode, int only, cudaStream_t st);
 
 }  // namespace dem

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -35,6 +36,7 @@ struct PileHost {
     dem_params P;
     double M_total;
     bool reported;
+    bool watch_on;         // a radius-growth watch is armed (evaluated in the step graph)
 };
 
 }  // namespace
@@ -200,6 +202,8 @@ void build_fields(dem_world *w)
     add((void **)&a.tile_sum, C_TILE, 4, false);
     add((void **)&a.chunk_part, C_CHUNK, 8 * kPartialDoubles, false);
     add((void **)&a.chunk_pile, C_CHUNK, 4, false);
+    add((void **)&a.bulk_part, C_CHUNK, 8 * 32, false);
+    add((void **)&a.watch, C_PILE, sizeof(PileWatch), true);
     add((void **)&a.ps, C_PILE, sizeof(PileStatic), false);
     add((void **)&a.pd, C_PILE, sizeof(PileDyn), true);
     add((void **)&a.enabled, C_PILE, 4, false);
@@ -495,6 +499,19 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     return DEM_OK;
 }
 
+bool any_watch(const dem_world *w)
+{
+    for (auto &q : w->piles)
+        if (q.watch_on) return true;
+    return false;
+}
+
+// Radius-growth watches: evaluated after the step's last phase.
+void enqueue_watch(dem_world *w)
+{
+    if (any_watch(w)) launch_bulk(w->A, w->Z, 1, -1, w->stream);
+}
+
 void enqueue_phase(dem_world *w, int ph)
 {
     const Arrays &a = w->A;
@@ -548,6 +565,7 @@ dem_status prepare(dem_world *w)
         enqueue_phase(w, ph);
         if (ph == w->timed_kernel) cudaEventRecordWithFlags(w->kev[1], w->stream, cudaEventRecordExternal);
     }
+    enqueue_watch(w);
     cudaError_t e = cudaStreamEndCapture(w->stream, &g);
     if (e != cudaSuccess) return fail(w, DEM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
     size_t nn = 0;
@@ -957,6 +975,10 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
         dyn.P_pos[d] = p->ext_pos[d]; dyn.P_vel[d] = p->ext_vel[d]; dyn.P_acc[d] = 0.0;
     }
     UP(D.pd + slot, &dyn, sizeof dyn);
+    PileWatch wat{};
+    wat.every = 1;
+    wat.fired = -1;
+    UP(D.watch + slot, &wat, sizeof wat);
 #undef UP
     CU(cudaStreamSynchronize(st));   // host staging vectors go out of scope
     *out_pile_id = ph.id;
@@ -999,12 +1021,14 @@ dem_status dem_step_profiled(dem_world *w, int64_t n_steps, int32_t which, float
     if (s != DEM_OK) return s;
     std::vector<cudaEvent_t> ev(2 * (size_t)n_steps, nullptr);
     for (auto &e : ev) CU(cudaEventCreate(&e));
-    for (int64_t t = 0; t < n_steps; ++t)
+    for (int64_t t = 0; t < n_steps; ++t) {
         for (int ph = 0; ph < DEM_K_COUNT; ++ph) {
             if (ph == which) CU(cudaEventRecord(ev[2 * t], w->stream));
             enqueue_phase(w, ph);
             if (ph == which) CU(cudaEventRecord(ev[2 * t + 1], w->stream));
         }
+        enqueue_watch(w);
+    }
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(w->stream));
     for (int64_t t = 0; t < n_steps; ++t) CU(cudaEventElapsedTime(ms_out + t, ev[2 * t], ev[2 * t + 1]));
@@ -1485,6 +1509,73 @@ dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
     return DEM_OK;
 }
 
+dem_status dem_pile_bulk(dem_world *w, int32_t pile_id, double *out, int64_t n_out)
+{
+    if (!w) return DEM_ERR_ARG;
+    if (!out || n_out < DEM_BULK_LEN) return fail(w, DEM_ERR_ARG, "output needs %d doubles", DEM_BULK_LEN);
+    int slot = find_pile(w, pile_id);
+    if (slot < 0) return fail(w, DEM_ERR_ARG, "unknown pile %d", pile_id);
+    dem_status s = prepare(w);
+    if (s != DEM_OK) return s;
+    slot = find_pile(w, pile_id);
+    launch_bulk(w->A, w->Z, 0, slot, w->stream);
+    CU(cudaGetLastError());
+    const char *src = (const char *)(w->A.watch + slot) + offsetof(PileWatch, now);
+    CU(cudaMemcpyAsync(out, src, 8 * DEM_BULK_LEN, cudaMemcpyDeviceToHost, w->stream));
+    CU(cudaStreamSynchronize(w->stream));
+    return DEM_OK;
+}
+
+dem_status dem_watch(dem_world *w, int32_t pile_id, double growth, int64_t every)
+{
+    if (!w) return DEM_ERR_ARG;
+    if (!(growth >= 0.0) || !std::isfinite(growth) || every < 1)
+        return fail(w, DEM_ERR_ARG, "bad watch (growth %g, every %lld)", growth, (long long)every);
+    int slot = find_pile(w, pile_id);
+    if (slot < 0) return fail(w, DEM_ERR_ARG, "unknown pile %d", pile_id);
+    dem_status s = prepare(w);
+    if (s != DEM_OK) return s;
+    slot = find_pile(w, pile_id);
+    PileWatch wat{};
+    wat.growth = growth;
+    wat.every = every;
+    wat.fired = -1;
+    wat.arm = growth > 0.0 ? 1 : 0;
+    CU(cudaMemcpyAsync(w->A.watch + slot, &wat, sizeof wat, cudaMemcpyHostToDevice, w->stream));
+    if (growth > 0.0) launch_bulk(w->A, w->Z, 0, slot, w->stream);   // takes R_b0
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(w->stream));   // wat goes out of scope
+    const bool on = growth > 0.0;
+    if (w->piles[slot].watch_on != on) {
+        w->piles[slot].watch_on = on;
+        w->graph_valid = false;   // the watch phase joins or leaves the graph
+    }
+    return DEM_OK;
+}
+
+dem_status dem_watch_result(dem_world *w, int32_t pile_id, double *out, int64_t n_out)
+{
+    if (!w) return DEM_ERR_ARG;
+    if (!out || n_out < DEM_WATCH_LEN) return fail(w, DEM_ERR_ARG, "output needs %d doubles", DEM_WATCH_LEN);
+    int slot = find_pile(w, pile_id);
+    if (slot < 0) return fail(w, DEM_ERR_ARG, "unknown pile %d", pile_id);
+    dem_status s = prepare(w);
+    if (s != DEM_OK) return s;
+    slot = find_pile(w, pile_id);
+    PileWatch wat;
+    CU(cudaMemcpyAsync(&wat, w->A.watch + slot, sizeof wat, cudaMemcpyDeviceToHost, w->stream));
+    CU(cudaStreamSynchronize(w->stream));
+    out[0] = (double)wat.fired;
+    out[1] = wat.growth;
+    out[2] = (double)wat.every;
+    out[3] = wat.growth > 0.0 ? 1.0 : 0.0;
+    for (int k = 0; k < DEM_BULK_LEN; ++k) {
+        out[4 + k] = wat.at_arm[k];
+        out[4 + DEM_BULK_LEN + k] = wat.fired >= 0 ? wat.at_fire[k] : 0.0;
+    }
+    return DEM_OK;
+}
+
 size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contacts, int32_t precision)
 {
     if (n_spheres < 0 || n_agg < 0 || max_contacts < 1) return 0;
@@ -1498,8 +1589,8 @@ size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contact
     int64_t cells = std::max<int64_t>(4 * n_spheres, 27) + kScanTile;
     size_t bytes = sph * (size_t)n_spheres + sphk * (size_t)n_spheres * (size_t)max_contacts +
                    agg * (size_t)n_agg + 8 * (size_t)cells + 4 * (size_t)(cells / kScanTile + 1) +
-                   (size_t)(n_agg / kAggChunk + 1) * (8 * kPartialDoubles + 4) +
-                   sizeof(PileStatic) + sizeof(PileDyn) + 16 + 16 * (size_t)(n_spheres / 64 + 1);
+                   (size_t)(n_agg / kAggChunk + 1) * (8 * kPartialDoubles + 4 + 8 * 32) +
+                   sizeof(PileStatic) + sizeof(PileDyn) + sizeof(PileWatch) + 16 + 16 * (size_t)(n_spheres / 64 + 1);
     // direct-sum gravity: partial sums of the 512-sphere tile pairs (2 T rows of
     // n spheres) and the work items (T (T + 1) / 2)
     const int64_t T = (n_spheres + kGravSymTile - 1) / kGravSymTile;

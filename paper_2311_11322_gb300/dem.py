@@ -35,6 +35,11 @@ FIELDS = {  # name: (id, rows ('A' aggregates / 'N' spheres / int), cols)
     "BODY_OFFSETS": (20, "N", 3), "OMEGA_BODY": (21, "A", 3), "INFO": (22, 20, None),
     "FRAME": (23, 6, None), "TORQUE_STORED": (24, "A", 3),
 }
+# record of dem_pile_bulk (enum dem_bulk): name -> (offset, length)
+BULK = {"mass": (0, 1), "com": (1, 3), "vcom": (4, 3), "axes": (7, 3), "radius": (10, 1),
+        "density": (11, 1), "spin": (12, 3), "period": (15, 1), "p_crit": (16, 1),
+        "planet_dist": (17, 1), "L": (18, 3), "moments": (21, 3)}
+DEM_BULK_LEN, DEM_WATCH_LEN = 24, 52
 KERNELS = {"AGG_BEGIN": 0, "PILE_BEGIN": 1, "KEYS": 2, "SCAN": 3, "SCATTER": 4,
            "CELL_ORDER": 5, "GATHER": 6, "CONTACT": 7, "GRAVITY": 8, "AGG_END": 9,
            "PILE_END": 10}
@@ -89,6 +94,9 @@ def load():
         "dem_graph_kernel_count": (i32, [vp, C.POINTER(i32)]),
         "dem_gravity_noalloc": (i32, [vp, vp, vp, i32, dbl, dbl, vp, vp, C.c_char_p, sz]),
         "dem_write_state": (i32, [vp, i32, i32, vp, i64]),
+        "dem_pile_bulk": (i32, [vp, i32, vp, i64]),
+        "dem_watch": (i32, [vp, i32, dbl, i64]),
+        "dem_watch_result": (i32, [vp, i32, vp, i64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -179,6 +187,7 @@ class World:
             self._cb = _torch_allocator()
             self._check(L.dem_set_allocator(self.w, self._cb[0], self._cb[1], None))
         self.piles = {}
+        self._static = {}
 
     def _check(self, s):
         if s != DEM_OK:
@@ -199,11 +208,21 @@ class World:
                                                _ptr(pos), _ptr(rad), _ptr(den), _ptr(vel),
                                                _ptr(om), C.byref(pid)))
         self.piles[pid.value] = (len(counts), len(rad), int(params.max_contacts))
+        self._static[pid.value] = (counts.copy(), rad.copy(), den.copy())
         return pid.value
+
+    def ic_of(self, pile):
+        """The pile's current state as initial conditions for add_pile (sphere
+        positions, aggregate COM velocities and spins; history not carried)."""
+        from .workloads import PileIC
+        counts, rad, den = self._static[pile]
+        return PileIC(counts=counts.copy(), pos=self.read(pile, "SPHERE_POS"), radius=rad.copy(),
+                      density=den.copy(), vel=self.read(pile, "VEL"), omega=self.read(pile, "OMEGA"))
 
     def remove(self, pile):
         self._check(self._L.dem_remove_pile(self.w, pile))
         self.piles.pop(pile, None)
+        self._static.pop(pile, None)
 
     # ---- stepping
     def step(self, n=1, piles=None, check=True):
@@ -279,6 +298,30 @@ class World:
                     pairs.append((i, j))
                     S.append(raw[i, 2 + 4 * t:5 + 4 * t])
         return pairs, np.array(S).reshape(-1, 3)
+
+    # ---- bulk shape and spin (Sec. 4.1, 4.2), computed on the device
+    @staticmethod
+    def _bulk_dict(v):
+        return {k: (float(v[o]) if n == 1 else v[o:o + n].copy()) for k, (o, n) in BULK.items()}
+
+    def bulk(self, pile) -> dict:
+        """Bulk record of a pile after the last step (see ``BULK`` for the keys)."""
+        out = np.zeros(DEM_BULK_LEN)
+        self._check(self._L.dem_pile_bulk(self.w, int(pile), _ptr(out), out.size))
+        return self._bulk_dict(out)
+
+    def watch(self, pile, growth, every=1):
+        """Arm (growth > 0) or disarm (0) the device-side radius-growth watch."""
+        self._check(self._L.dem_watch(self.w, int(pile), float(growth), int(every)))
+
+    def watch_result(self, pile) -> dict:
+        out = np.zeros(DEM_WATCH_LEN)
+        self._check(self._L.dem_watch_result(self.w, int(pile), _ptr(out), out.size))
+        fired = int(out[0])
+        return {"fired_step": fired if fired >= 0 else None, "growth": float(out[1]),
+                "every": int(out[2]), "armed": bool(out[3]),
+                "at_arm": self._bulk_dict(out[4:4 + DEM_BULK_LEN]),
+                "at_fire": self._bulk_dict(out[4 + DEM_BULK_LEN:]) if fired >= 0 else None}
 
     def flags(self, pile) -> int:
         f = C.c_int32()
