@@ -242,6 +242,12 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
  * when grav_ib is even, 0 = scalar FP32), "grav_sym" (1 = symmetric
  * tile-pair form, each pair evaluated once and applied to both spheres, the
  * default in both precisions; 0 = one-sided form shaped by the keys above),
+ * "grav_tile" (spheres per tile of the symmetric form in the mixed path:
+ * 512, or 128 for worlds whose piles all have at most 8,192 spheres -- more,
+ * smaller work items when the 512-sphere tile pairs would fill only a small
+ * part of the GPU; 0 = choose automatically (128 when the 512-sphere tile
+ * pairs of all piles fill less than a sixteenth of one wave), the default;
+ * piles above 8,192 spheres always use 512),
  * "grav_theta" (mixed path: > 0 replaces the direct sum by tree gravity with
  * this opening angle, in [0, 1): monopole + quadrupole cells of an octree
  * rebuilt every step, leaves of ~4 spheres summed directly; relative force

@@ -172,6 +172,7 @@ struct Sizes {
     int64_t TN, TL, TG;   // tree nodes, leaves and 32-sphere groups of all piles (TN = 0: direct sum)
     int32_t K;    // history slots per sphere (world-wide)
     int32_t adapt;   // some pile integrates rotation with the adaptive RK5(4)
+    int32_t gtile;   // spheres per tile of the symmetric gravity form (512, or 128 in the mixed path)
 };
 
 // ---- kernel launchers (kernels_*.cu) -------------------------------------
@@ -184,12 +185,12 @@ void launch_cell_order(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_gather(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
 void launch_contact(const Arrays &a, const Sizes &z, bool fp64, int K, cudaStream_t st);
 cudaError_t contact_setup(bool fp64, int K);
-// sym: symmetric tile-pair form (mixed path; items are (pile, tile a, tile b)
-// with 512-sphere tiles, gnchunk = tiles per pile)
-constexpr int kGravSymTile = 512;
+// sym: symmetric tile-pair form (items are (pile, tile a, tile b), gnchunk =
+// tiles per pile); tiles of 512 spheres, or of 128 (mixed path, small piles)
+constexpr int kGravSymTile = 512, kGravSymTileSmall = 128;
 void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int ib, bool pack,
                     bool sym, cudaStream_t st);
-int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym);
+int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym, int tile);
 void launch_agg_end(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
 void launch_pile_end(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_fill_ids(const Arrays &a, const Sizes &z, cudaStream_t st);

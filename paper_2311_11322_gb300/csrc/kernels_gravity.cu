@@ -442,9 +442,9 @@ constexpr int kSymBS = 128, kSymIB = 4, kSymTile = kSymBS * kSymIB;   // 512 sph
 // launch bounds of the symmetric kernel (optionally with a minimum number of
 // resident blocks per SM, which caps its registers)
 #ifdef DEM_GSYM_MINB
-#define DEM_GSYM_BOUNDS __launch_bounds__(kSymBS, DEM_GSYM_MINB)
+#define DEM_GSYM_BOUNDS __launch_bounds__(32 * WPB, DEM_GSYM_MINB)
 #else
-#define DEM_GSYM_BOUNDS __launch_bounds__(kSymBS)
+#define DEM_GSYM_BOUNDS __launch_bounds__(32 * WPB)
 #endif
 
 // Partial slots of pile p: i-sums of tile pair (a, b) at [b][i], j-sums at
@@ -561,10 +561,14 @@ __device__ __forceinline__ void sym_ring2(const float4 &pa, const float4 &pb,
 
 // Work item (pile, tile a, tile b): the symmetric pass for a < b, the
 // one-sided pass over the tile itself for a == b.  sp/sag: tile b staged in
-// shared memory; sj: per-warp j-sums.
+// shared memory; sj: per-warp j-sums.  WPB warps per block, each with
+// 32 x kSymIB i-spheres: tiles of 128 WPB spheres (512 for the large-pile
+// form, 128 for small piles whose 512-sphere tile pairs would not fill the GPU).
+template <int WPB>
 __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, float4 *sp, int *sag,
                                                 float4 *sj)
 {
+    constexpr int kSymBS = 32 * WPB, kSymTile = kSymBS * kSymIB;
     const int p = it.x;
     if (a.enabled[p] == 0 || a.pd[p].failed) return;
     const PileStatic &S = a.ps[p];
@@ -653,11 +657,15 @@ __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, 
     if (!diag) {
         __syncthreads();
         for (int m = threadIdx.x; m < nj; m += kSymBS) {
-            const float4 u0 = sj[m], u1 = sj[kSymTile + m], u2 = sj[2 * kSymTile + m],
-                         u3 = sj[3 * kSymTile + m];
-            const float fx = ((u0.x + u1.x) + u2.x) + u3.x, fy = ((u0.y + u1.y) + u2.y) + u3.y,
-                        fz = ((u0.z + u1.z) + u2.z) + u3.z;
-            ((float4 *)a.gpart)[sym_slot(a, p, ns, T + ta, jb0 + m)] = make_float4(fx, fy, fz, 0.f);
+            float4 u = sj[m];
+#pragma unroll
+            for (int v = 1; v < WPB; ++v) {
+                const float4 t = sj[v * kSymTile + m];
+                u.x += t.x;
+                u.y += t.y;
+                u.z += t.z;
+            }
+            ((float4 *)a.gpart)[sym_slot(a, p, ns, T + ta, jb0 + m)] = make_float4(u.x, u.y, u.z, 0.f);
         }
     }
 #pragma unroll
@@ -673,11 +681,13 @@ __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, 
     }
 }
 
+template <int WPB>
 __global__ void DEM_GSYM_BOUNDS k_gravity32s(Arrays a, Sizes z)
 {
-    __shared__ float4 sp[kSymTile];
-    __shared__ int sag[kSymTile];
-    __shared__ float4 sj[4 * kSymTile];
+    constexpr int kTile = 32 * WPB * kSymIB;
+    __shared__ float4 sp[kTile];
+    __shared__ int sag[kTile];
+    __shared__ float4 sj[WPB * kTile];
     __shared__ int next;
     for (;;) {
         __syncthreads();
@@ -685,7 +695,7 @@ __global__ void DEM_GSYM_BOUNDS k_gravity32s(Arrays a, Sizes z)
         __syncthreads();
         const int item = next;
         if (item >= z.GI) return;
-        gravity32s_item(a, a.gitems[item], sp, sag, sj);
+        gravity32s_item<WPB>(a, a.gitems[item], sp, sag, sj);
     }
 }
 
@@ -861,7 +871,7 @@ __global__ void k_grav_combine_sym(Arrays a, Sizes z)
     if (T <= 1) return;
     const PileStatic &S = a.ps[p];
     const int64_t il = i - S.s0;
-    const int t = (int)(il / kSymTile);
+    const int t = (int)(il / z.gtile);
     const float4 *gp = (const float4 *)a.gpart;
     FFSum sx, sy, sz;
     for (int b = t; b < T; ++b) {
@@ -939,7 +949,7 @@ static int occ(bool fp64, bool pack)
     return n;
 }
 
-int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym)
+int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym, int tile)
 {
     if (sym) {
         int n = 0;
@@ -947,7 +957,8 @@ int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym)
             cudaFuncSetAttribute(k_gravity64s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSym64Smem);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity64s, kSymBS, kSym64Smem);
         } else {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s, kSymBS, 0);
+            if (tile == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s<1>, 32, 0);
+            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s<4>, kSymBS, 0);
         }
         return n;
     }
@@ -967,7 +978,8 @@ void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int i
             k_gravity64s<<<(unsigned)nb, kSymBS, kSym64Smem, st>>>(a, z);
             if (z.GP > 0) k_grav_combine_sym64<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
         } else {
-            k_gravity32s<<<(unsigned)nb, kSymBS, 0, st>>>(a, z);
+            if (z.gtile == 128) k_gravity32s<1><<<(unsigned)nb, 32, 0, st>>>(a, z);
+            else k_gravity32s<4><<<(unsigned)nb, kSymBS, 0, st>>>(a, z);
             if (z.GP > 0) k_grav_combine_sym<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
         }
         return;

@@ -66,6 +66,7 @@ struct dem_world {
     double grav_item = 1048576.0;     // else: target interactions per work item
     bool grav_pack = false;           // packed f32x2 pair terms (even grav_ib)
     bool grav_sym = true;             // mixed path: symmetric tile-pair form
+    int grav_tile = 0;                // symmetric form's tile: 0 = automatic, 128 or 512
     double grav_theta = 0.0;          // > 0 (mixed path): tree gravity with this opening angle
     int tree_maxD = 0;                // deepest tree of the current layout
     int sm_count = 0;
@@ -257,6 +258,7 @@ int64_t pile_count(const dem_world *w, const PileHost &q, Cls c)
 }
 
 struct GravPlan {
+    int tile = kGravSymTile;   // symmetric form: spheres per tile
     std::vector<int4> items;
     std::vector<int64_t> base;
     std::vector<int32_t> nch;
@@ -265,7 +267,38 @@ struct GravPlan {
 
 bool use_sym(const dem_world *w) { return w->grav_sym; }
 
-GravPlan plan_gravity(const dem_world *w)
+// Tile of the symmetric form.  512-sphere tiles unless the mixed path's
+// 512-tile pairs of all piles would fill less than a sixteenth of one wave of
+// the persistent grid (single piles up to ~4,600 spheres; measured: 1,000
+// spheres 105 -> 86 us per step, 5,000 even, 8,000 slower) and no pile
+// exceeds 8,192 spheres: then 128-sphere tiles, 16 times the work items for
+// the same pairs (their partial rows, 2 T x N, stay <= 17 MB).
+int sym_tile(dem_world *w)
+{
+    if (w->precision != DEM_MIXED) return kGravSymTile;
+    int64_t items = 0, nmax = 0;
+    for (auto &q : w->piles) {
+        if (q.P.G == 0.0) continue;
+        const int64_t T = (q.ns + kGravSymTile - 1) / kGravSymTile;
+        items += T * (T + 1) / 2;
+        nmax = std::max(nmax, q.ns);
+    }
+    if (nmax == 0 || nmax > 8192) return kGravSymTile;
+    if (w->grav_tile) return w->grav_tile;
+    if (w->sm_count == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&w->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return kGravSymTile;
+        }
+    }
+    const int bps = gravity_blocks_per_sm(false, 128, 4, false, true, kGravSymTile);
+    cudaGetLastError();
+    return 16 * items < (int64_t)std::max(1, bps) * w->sm_count ? kGravSymTileSmall : kGravSymTile;
+}
+
+GravPlan plan_gravity(dem_world *w)
 {
     GravPlan g;
     if (w->grav_theta > 0 && w->precision == DEM_MIXED) {   // tree gravity: no direct items
@@ -273,13 +306,14 @@ GravPlan plan_gravity(const dem_world *w)
         return g;
     }
     if (use_sym(w)) {
-        // items: every pair of 512-sphere tiles (a, b), a <= b; partial rows
+        const int64_t tile = g.tile = sym_tile(w);
+        // items: every pair of tiles (a, b), a <= b; partial rows
         // [b][i] and [T + a][j] (2 T rows of ns) for piles with more than one tile
         struct It { int4 v; int64_t cost; };
         std::vector<It> its;
         for (size_t p = 0; p < w->piles.size(); ++p) {
             const PileHost &q = w->piles[p];
-            const int64_t T = (q.ns + kGravSymTile - 1) / kGravSymTile;
+            const int64_t T = (q.ns + tile - 1) / tile;
             if (q.P.G == 0.0) {
                 g.nch.push_back(1);
                 g.base.push_back(-1);
@@ -294,7 +328,7 @@ GravPlan plan_gravity(const dem_world *w)
             }
             for (int64_t ta = 0; ta < T; ++ta)
                 for (int64_t tb = ta; tb < T; ++tb) {
-                    int64_t nb = std::min<int64_t>(kGravSymTile, q.ns - tb * kGravSymTile);
+                    int64_t nb = std::min<int64_t>(tile, q.ns - tb * tile);
                     its.push_back({make_int4((int)p, (int)ta, (int)tb, 0), nb});
                 }
         }
@@ -469,8 +503,9 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
         CU(cudaGetDevice(&dev));
         CU(cudaDeviceGetAttribute(&w->sm_count, cudaDevAttrMultiProcessorCount, dev));
     }
+    w->Z.gtile = gp.tile;
     int bps = gravity_blocks_per_sm(w->precision == DEM_FP64, w->grav_block, w->grav_ib, w->grav_pack,
-                                    use_sym(w));
+                                    use_sym(w), gp.tile);
     CU(cudaGetLastError());
     CU(contact_setup(w->precision == DEM_FP64, w->K));
     w->Z.GB = (int64_t)std::max(1, bps) * w->sm_count;
@@ -1410,6 +1445,10 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
         w->grav_pack = value != 0.0;
     } else if (k == "grav_sym") {
         w->grav_sym = value != 0.0;
+    } else if (k == "grav_tile") {
+        const int t = (int)value;
+        if (t != 0 && t != 128 && t != 512) return fail(w, DEM_ERR_ARG, "grav_tile must be 0, 128 or 512");
+        w->grav_tile = t;
     } else if (k == "grav_theta") {
         if (!(value >= 0.0) || !(value < 1.0)) return fail(w, DEM_ERR_ARG, "grav_theta must be in [0, 1)");
         const double old = w->grav_theta;
@@ -1442,24 +1481,26 @@ dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
 {
     if (!w || trial_steps < 1) return DEM_ERR_ARG;
     if (w->piles.empty()) return DEM_OK;
-    struct Cand { int blk, ib; double item; bool pack, sym; };
+    struct Cand { int blk, ib; double item; bool pack, sym; int tile; };
     std::vector<Cand> cands;
-    cands.push_back({128, 4, 1048576.0, false, true});
+    cands.push_back({128, 4, 1048576.0, false, true, 512});
+    if (w->precision == DEM_MIXED) cands.push_back({128, 4, 1048576.0, false, true, 128});
     for (int blk : {64, 128, 256})
         for (int ib : {1, 2, 4})
             for (double item : {262144.0, 1048576.0, 4194304.0}) {
-                cands.push_back({blk, ib, item, false, false});
-                if (ib % 2 == 0) cands.push_back({blk, ib, item, true, false});
+                cands.push_back({blk, ib, item, false, false, 0});
+                if (ib % 2 == 0) cands.push_back({blk, ib, item, true, false, 0});
             }
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     double best = 1e300;
-    Cand bc = {w->grav_block, w->grav_ib, w->grav_item, w->grav_pack, w->grav_sym};
+    Cand bc = {w->grav_block, w->grav_ib, w->grav_item, w->grav_pack, w->grav_sym, w->grav_tile};
     w->grav_jchunk = 0;
     for (auto &c : cands) {
         w->grav_block = c.blk; w->grav_ib = c.ib; w->grav_item = c.item; w->grav_pack = c.pack;
         w->grav_sym = c.sym;
+        w->grav_tile = c.tile;
         w->graph_valid = false;
         dem_status s = prepare(w);
         if (s != DEM_OK) return s;
@@ -1479,6 +1520,7 @@ dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
     cudaEventDestroy(e1);
     w->grav_block = bc.blk; w->grav_ib = bc.ib; w->grav_item = bc.item; w->grav_pack = bc.pack;
     w->grav_sym = bc.sym;
+    w->grav_tile = bc.tile;
     w->graph_valid = false;
     // then the cell edge (contact search), with the chosen gravity shape
     double bf = w->cell_factor;
@@ -1593,7 +1635,9 @@ size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contact
                    sizeof(PileStatic) + sizeof(PileDyn) + sizeof(PileWatch) + 16 + 16 * (size_t)(n_spheres / 64 + 1);
     // direct-sum gravity: partial sums of the 512-sphere tile pairs (2 T rows of
     // n spheres) and the work items (T (T + 1) / 2)
-    const int64_t T = (n_spheres + kGravSymTile - 1) / kGravSymTile;
+    // (up to 8,192 spheres the mixed path may use 128-sphere tiles: count those)
+    const int64_t tile = (!d && n_spheres <= 8192) ? kGravSymTileSmall : kGravSymTile;
+    const int64_t T = (n_spheres + tile - 1) / tile;
     if (T > 1) bytes += (size_t)(2 * T) * (size_t)n_spheres * (d ? 32 : 16);
     bytes += 16 * (size_t)(T * (T + 1) / 2);
     return bytes;

@@ -230,21 +230,28 @@ def test_step_subset_freezes_others(dem):
         assert w.info(ids[0])["steps"] == 7 and w.info(ids[1])["steps"] == 3
 
 
-def test_gravity_split_and_shapes_agree(dem):
-    """Splitting the j-range and changing the block shape only reorders FP64 sums."""
-    ic, p = W.config2(1, n_spheres=20_000, ball=800.0)
+@pytest.mark.parametrize("n", [6000, 20_000])
+def test_gravity_split_and_shapes_agree(dem, n):
+    """The symmetric form with 512- and (up to 8,192 spheres) 128-sphere tiles,
+    and the one-sided form with split j-ranges and other block shapes, only
+    reorder sums: the gravity on every sphere agrees to FP32 rounding."""
+    ic, p = W.config2(1, n_spheres=n, ball=800.0 * (n / 20_000) ** (1 / 3))
+    shapes = [dict(grav_tile=512), dict(grav_sym=0, grav_block=128, grav_ib=2, grav_jchunk=0),
+              dict(grav_sym=0, grav_block=64, grav_ib=1, grav_jchunk=n // 4),
+              dict(grav_sym=0, grav_block=256, grav_ib=2, grav_jchunk=n // 3)]
+    if n <= 8192:
+        shapes.append(dict(grav_tile=128))
     outs = []
-    for blk, ib, jc in ((128, 2, 0), (64, 1, 5000), (256, 2, 7000)):
+    for kw in shapes:
         with new_world(dem) as w:
-            w.set_tuning("grav_block", blk)
-            w.set_tuning("grav_ib", ib)
-            w.set_tuning("grav_jchunk", jc)
+            for k, v in kw.items():
+                w.set_tuning(k, v)
             pid = w.add_pile(ic, p)
             w.step(1)
             outs.append(w.read(pid, "SPHERE_FG"))
     sc = np.linalg.norm(outs[0], axis=1).max()
-    for o in outs[1:]:
-        assert np.max(np.abs(o - outs[0])) < 1e-5 * sc
+    for kw, o in zip(shapes[1:], outs[1:]):
+        assert np.max(np.abs(o - outs[0])) < 1e-5 * sc, kw
 
 
 # ------------------------------------------------------------------ errors and edges
