@@ -249,9 +249,11 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
  * pairs of all piles fill less than a sixteenth of one wave), the default;
  * piles above 8,192 spheres always use 512),
  * "grav_theta" (mixed path: > 0 replaces the direct sum by tree gravity with
- * this opening angle, in [0, 1): monopole + quadrupole cells of an octree
- * rebuilt every step, leaves of ~4 spheres summed directly; relative force
- * errors ~2e-4 median at 0.5; 0 = direct sum, the default),
+ * this opening angle, in [0, 1): cells of an octree rebuilt every step with
+ * multipoles up to the hexadecapole (Sec. 2.1), leaves of ~4 spheres summed
+ * directly; 0 = direct sum, the default), "grav_order" (highest multipole
+ * rank of the tree's accepted cells: 4, the default, or 2 -- monopole and
+ * quadrupole only, cheaper per cell and less accurate),
  * "cell_factor" (cell edge / (2 x
  * largest radius), >= 1), "skin" (neighbour-list skin as a fraction of the
  * pile's largest radius, in [0, 4], default 0.1; 0 = search contacts afresh
@@ -365,7 +367,7 @@ dem_status dem_gravity_noalloc(const void *pos_mass, const double *mass, const i
 
 /* Device bytes one pile of this size needs with direct-sum gravity (state, sorted
  * copies, cells, history, gravity partial sums).  Tree gravity (grav_theta > 0)
- * needs instead about 1.1 KB per sphere plus 60 B per tree cell. */
+ * needs instead about 1.1 KB per sphere plus 280 B per tree cell. */
 size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contacts,
                            int32_t precision);
 

@@ -157,7 +157,8 @@ struct Arrays {
     int32_t *tagg;       // leaf-ordered aggregates
     float4 *tpart;       // [64][N] partial sums of the 64 subtrees at level 2
     int *tbox;
-    float4 *tnode;
+    float4 *tnode;       // per node 9 float4: COM, M, opening radius^2, traceless moments of ranks 2-4
+    float4 *traw;        // per node 8 float4: raw moments of ranks 2-4 about the COM (upward pass)
     int2 *tleaf;
     int32_t *tnode_pile, *tleaf_pile;
     // piles
@@ -194,7 +195,8 @@ int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym, int
 void launch_agg_end(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st);
 void launch_pile_end(const Arrays &a, const Sizes &z, cudaStream_t st);
 void launch_fill_ids(const Arrays &a, const Sizes &z, cudaStream_t st);
-void launch_tree_gravity(const Arrays &a, const Sizes &z, int max_depth, cudaStream_t st);
+// order: highest multipole rank of accepted cells (2 or 4)
+void launch_tree_gravity(const Arrays &a, const Sizes &z, int max_depth, int order, cudaStream_t st);
 void launch_force_rebuild(const Arrays &a, const Sizes &z, int slot, cudaStream_t st);
 // bulk record of piles into watch.now (mode 0: every pile, or only slot
 // `only` when >= 0; mode 1: the watch evaluation inside the step graph, armed

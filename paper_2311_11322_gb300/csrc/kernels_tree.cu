@@ -6,14 +6,15 @@
 // Morton order, so the parent of cell m is m >> 3), spheres counted into the
 // leaf cells and ordered by leaf (counting sort, each leaf ordered by home
 // index, deterministic), leaf moments from their spheres and upper moments
-// from 8 children: mass, centre of mass and the traceless quadrupole
-//   Q = sum m (3 z z^T - |z|^2 I),  z = position - COM,
-// then each warp walks the tree depth-first for 32 spheres at once.  A cell is
-// accepted when the group of spheres is farther from its COM than
-// size/theta + |COM - centre| (so no sphere is inside an accepted cell) and
-// contributes
-//   a / G = M d / r^3 - Q d / r^5 + 5/2 (d^T Q d) d / r^7,   d = COM - x,
-// the gradient of the quadrupole potential; an opened leaf is summed directly
+// from 8 children: mass, centre of mass and the raw moments of ranks 2-4
+// about the COM (shifted exactly from child to parent), kept for evaluation
+// as their traceless parts -- quadrupole, octupole and hexadecapole, the
+// expansion order of the paper's tree code (Sec. 2.1) -- then each warp
+// walks the tree depth-first for 32 spheres at once.  A cell is accepted when
+// the group of spheres is farther from its COM than size/theta +
+// |COM - centre| (so no sphere is inside an accepted cell) and contributes
+// the gradient of its multipole potential up to rank 4 (or rank 2, the
+// cheaper option); an opened leaf is summed directly
 // with Plummer softening, skipping the sphere itself and its aggregate mates
 // (pairs inside one aggregate cancel in its totals, Sec. 2.2.3).  Mates that
 // fall in an accepted distant cell are not removed: their share cancels in
@@ -205,13 +206,92 @@ __global__ void k_tree_gather(Arrays a, Sizes z)
     a.tagg[k] = a.sph_agg[s0 + i];
 }
 
-// node record: A = (COM, M), B = (Qxx, Qyy, Qzz, Qxy), C = (Qxz, Qyz, r_open^2, 0)
-__device__ __forceinline__ void put_node(const Arrays &a, int64_t n, float3 c, float M, const float *Q,
+// ---- multipole moments up to the hexadecapole
+// A symmetric tensor of rank n is kept as its (n+1)(n+2)/2 distinct
+// components, component (a, b, c) having a x-, b y- and c z-indices, in the
+// order of mono_idx.  Raw moments of a node about its COM, R_abc = sum m x^a
+// y^b z^c (rank 1 vanishes), ranks 2..4 at offsets 0, 6, 16 (31 floats,
+// traw: 8 float4 per node).  Node record (tnode: 9 float4 = 36 floats): COM
+// 0..2, M 3, opening radius^2 4, then the evaluation tensors T_n = c_n
+// detrace(R_n) of ranks 2, 3, 4 at 5, 11, 21 with c_n = (2n-1)!!/n!
+// (3/2, 5/2, 35/8), so that the potential of the node at offset x from its
+// COM is -G (M / r + sum_n T_n . x^n / r^(2n+1)).
+constexpr int kNodeF4 = 9, kRawF4 = 8;
+__host__ __device__ constexpr int mono_idx(int a, int b, int c)
+{
+    int n = a + b + c, i = 0;
+    for (int aa = n; aa > a; --aa) i += n - aa + 1;
+    return i + (n - a) - b;
+}
+__host__ __device__ constexpr int raw_off(int n) { return n == 2 ? 0 : n == 3 ? 6 : 16; }
+__host__ __device__ constexpr int node_off(int n) { return n == 2 ? 5 : n == 3 ? 11 : 21; }
+__host__ __device__ constexpr float binomf(int n, int k)
+{
+    return (k < 0 || k > n) ? 0.f : (k == 0 || k == n) ? 1.f : (n == 2 ? 2.f : n == 3 ? 3.f : (k == 2 ? 6.f : 4.f));
+}
+__host__ __device__ constexpr float factf(int n) { return n <= 1 ? 1.f : n == 2 ? 2.f : n == 3 ? 6.f : 24.f; }
+// number of ways to pair up 4 indices so that both pairs have equal axes
+__host__ __device__ constexpr float pairings4(int a, int b, int c)
+{
+    return ((a & 1) || (b & 1) || (c & 1)) ? 0.f : (a == 4 || b == 4 || c == 4) ? 3.f : 1.f;
+}
+
+__device__ __forceinline__ void powers4(float x, float *p)
+{
+    p[0] = 1.f;
+    p[1] = x;
+    p[2] = x * x;
+    p[3] = p[2] * x;
+    p[4] = p[2] * p[2];
+}
+
+// trace over one index pair of the rank-n raw moment, component f (rank n - 2)
+template <int N>
+__device__ __forceinline__ float trace1(const float *R, int fa, int fb, int fc)
+{
+    return R[raw_off(N) + mono_idx(fa + 2, fb, fc)] + R[raw_off(N) + mono_idx(fa, fb + 2, fc)] +
+           R[raw_off(N) + mono_idx(fa, fb, fc + 2)];
+}
+
+// Evaluation tensors from raw moments: the traceless part of each rank
+// (subtract the symmetrised traces: 1/(2n-1) of single traces, plus 1/35 of
+// the double trace at rank 4), scaled by (2n-1)!!/n!.
+template <int N>
+__device__ __forceinline__ void detrace_scaled(const float *R, float *T)
+{
+    constexpr float cn = N == 2 ? 1.5f : N == 3 ? 2.5f : 4.375f;
+    float W = 0.f;
+    if (N == 4) W = trace1<4>(R, 2, 0, 0) + trace1<4>(R, 0, 2, 0) + trace1<4>(R, 0, 0, 2);
+#pragma unroll
+    for (int a = N; a >= 0; --a)
+#pragma unroll
+        for (int b = N - a; b >= 0; --b) {
+            const int c = N - a - b;
+            float tr = 0.f;
+            if (a >= 2) tr += binomf(a, 2) * trace1<N>(R, a - 2, b, c);
+            if (b >= 2) tr += binomf(b, 2) * trace1<N>(R, a, b - 2, c);
+            if (c >= 2) tr += binomf(c, 2) * trace1<N>(R, a, b, c - 2);
+            float v = R[raw_off(N) + mono_idx(a, b, c)] - tr * (1.f / (2 * N - 1));
+            if (N == 4) v += pairings4(a, b, c) * W * (1.f / 35.f);
+            T[node_off(N) - 5 + mono_idx(a, b, c)] = cn * v;
+        }
+}
+
+__device__ __forceinline__ void put_node(const Arrays &a, int64_t n, float3 c, float M, const float *R,
                                          float ropen2)
 {
-    a.tnode[3 * n] = make_float4(c.x, c.y, c.z, M);
-    a.tnode[3 * n + 1] = make_float4(Q[0], Q[1], Q[2], Q[3]);
-    a.tnode[3 * n + 2] = make_float4(Q[4], Q[5], ropen2, 0.f);
+    float nd[4 * kNodeF4];
+    nd[0] = c.x; nd[1] = c.y; nd[2] = c.z; nd[3] = M; nd[4] = ropen2;
+    detrace_scaled<2>(R, nd + 5);
+    detrace_scaled<3>(R, nd + 5);
+    detrace_scaled<4>(R, nd + 5);
+    float4 *o = a.tnode + kNodeF4 * n;
+#pragma unroll
+    for (int k = 0; k < kNodeF4; ++k) o[k] = make_float4(nd[4 * k], nd[4 * k + 1], nd[4 * k + 2], nd[4 * k + 3]);
+    float4 *r = a.traw + kRawF4 * n;
+#pragma unroll
+    for (int k = 0; k < kRawF4; ++k)
+        r[k] = make_float4(R[4 * k], R[4 * k + 1], R[4 * k + 2], k == kRawF4 - 1 ? 0.f : R[4 * k + 3]);
 }
 
 // centre of cell m (Morton) at level L of pile p's cube
@@ -245,9 +325,11 @@ __global__ void k_tree_leaves(Arrays a, Sizes z)
     const uint32_t m = (uint32_t)(g - S.tleaf0);
     const int2 L = a.tleaf[g];
     const int64_t n = S.tnode0 + lvl_off(S.tD) + m;
-    float Q[6] = {0, 0, 0, 0, 0, 0};
+    float R[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) R[k] = 0.f;
     if (L.y == 0) {
-        put_node(a, n, f3(0, 0, 0), 0.f, Q, 0.f);
+        put_node(a, n, f3(0, 0, 0), 0.f, R, 0.f);
         return;
     }
     const float4 *tp = a.tpos + S.s0;
@@ -262,24 +344,31 @@ __global__ void k_tree_leaves(Arrays a, Sizes z)
     c = f3(x0.x, x0.y, x0.z) + (1.0f / M) * c;
     for (int k = 0; k < L.y; ++k) {
         const float4 x = tp[L.x + k];
-        const float zx = x.x - c.x, zy = x.y - c.y, zz = x.z - c.z;
-        const float r2 = zx * zx + zy * zy + zz * zz;
-        Q[0] += x.w * (3.f * zx * zx - r2);
-        Q[1] += x.w * (3.f * zy * zy - r2);
-        Q[2] += x.w * (3.f * zz * zz - r2);
-        Q[3] += x.w * 3.f * zx * zy;
-        Q[4] += x.w * 3.f * zx * zz;
-        Q[5] += x.w * 3.f * zy * zz;
+        float px[5], py[5], pz[5];
+        powers4(x.x - c.x, px);
+        powers4(x.y - c.y, py);
+        powers4(x.z - c.z, pz);
+#pragma unroll
+        for (int r = 2; r <= 4; ++r)
+#pragma unroll
+            for (int ea = r; ea >= 0; --ea)
+#pragma unroll
+                for (int eb = r - ea; eb >= 0; --eb) {
+                    const int ec = r - ea - eb;
+                    R[raw_off(r) + mono_idx(ea, eb, ec)] += x.w * (px[ea] * py[eb] * pz[ec]);
+                }
     }
     float3 lo;
     float edge;
     tree_cube(a, p, lo, edge);
     const float size = edge / (float)(1 << S.tD);
-    put_node(a, n, c, M, Q, opening2(c, cell_centre(lo, edge, S.tD, m), size, S.theta));
+    put_node(a, n, c, M, R, opening2(c, cell_centre(lo, edge, S.tD, m), size, S.theta));
 }
 
-// Moments of level L from the 8 children (parallel axis for Q): one thread
-// per node of every tree pile deep enough.
+// Moments of level L from the 8 children: raw moments shifted from each
+// child's COM to the parent's, R_e += sum_{f <= e} C(e, f) R_child,f s^(e-f)
+// with s = child COM - parent COM (rank-1 terms vanish about a COM), one
+// thread per node of every tree pile deep enough.
 __global__ void k_tree_up(Arrays a, Sizes z, int L)
 {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -296,33 +385,59 @@ __global__ void k_tree_up(Arrays a, Sizes z, int L)
     float M = 0.f;
     float3 c = f3(0, 0, 0);
     for (int k = 0; k < 8; ++k) {
-        const float4 A = a.tnode[3 * (c0 + k)];
+        const float4 A = a.tnode[kNodeF4 * (c0 + k)];
         M += A.w;
         c = c + A.w * f3(A.x, A.y, A.z);
     }
-    float Q[6] = {0, 0, 0, 0, 0, 0};
+    float R[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) R[k] = 0.f;
     if (M == 0.f) {
-        put_node(a, g, f3(0, 0, 0), 0.f, Q, 0.f);
+        put_node(a, g, f3(0, 0, 0), 0.f, R, 0.f);
         return;
     }
     c = (1.0f / M) * c;
     for (int k = 0; k < 8; ++k) {
-        const float4 A = a.tnode[3 * (c0 + k)];
+        const float4 A = a.tnode[kNodeF4 * (c0 + k)];
         if (A.w == 0.f) continue;
-        const float4 B = a.tnode[3 * (c0 + k) + 1], C = a.tnode[3 * (c0 + k) + 2];
-        const float dx = A.x - c.x, dy = A.y - c.y, dz = A.z - c.z;
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        Q[0] += B.x + A.w * (3.f * dx * dx - r2);
-        Q[1] += B.y + A.w * (3.f * dy * dy - r2);
-        Q[2] += B.z + A.w * (3.f * dz * dz - r2);
-        Q[3] += B.w + A.w * 3.f * dx * dy;
-        Q[4] += C.x + A.w * 3.f * dx * dz;
-        Q[5] += C.y + A.w * 3.f * dy * dz;
+        float Rc[32];
+        const float4 *r = a.traw + kRawF4 * (c0 + k);
+#pragma unroll
+        for (int q = 0; q < kRawF4; ++q) {
+            const float4 v = r[q];
+            Rc[4 * q] = v.x; Rc[4 * q + 1] = v.y; Rc[4 * q + 2] = v.z; Rc[4 * q + 3] = v.w;
+        }
+        float sx[5], sy[5], sz[5];
+        powers4(A.x - c.x, sx);
+        powers4(A.y - c.y, sy);
+        powers4(A.z - c.z, sz);
+#pragma unroll
+        for (int n = 2; n <= 4; ++n)
+#pragma unroll
+            for (int ea = n; ea >= 0; --ea)
+#pragma unroll
+                for (int eb = n - ea; eb >= 0; --eb) {
+                    const int ec = n - ea - eb;
+                    float v = 0.f;
+#pragma unroll
+                    for (int fa = 0; fa <= ea; ++fa)
+#pragma unroll
+                        for (int fb = 0; fb <= eb; ++fb)
+#pragma unroll
+                            for (int fc = 0; fc <= ec; ++fc) {
+                                const int deg = fa + fb + fc;
+                                if (deg == 1) continue;
+                                const float Rf = deg == 0 ? A.w : Rc[raw_off(deg) + mono_idx(fa, fb, fc)];
+                                v += (binomf(ea, fa) * binomf(eb, fb) * binomf(ec, fc)) * Rf *
+                                     (sx[ea - fa] * sy[eb - fb] * sz[ec - fc]);
+                            }
+                    R[raw_off(n) + mono_idx(ea, eb, ec)] += v;
+                }
     }
     float3 lo;
     float edge;
     tree_cube(a, p, lo, edge);
-    put_node(a, g, c, M, Q, opening2(c, cell_centre(lo, edge, L, m), edge / (float)(1 << L), S.theta));
+    put_node(a, g, c, M, R, opening2(c, cell_centre(lo, edge, L, m), edge / (float)(1 << L), S.theta));
 }
 
 constexpr int kTreeStack = 2048;   // per warp
@@ -332,22 +447,46 @@ constexpr int kTreeStack = 2048;   // per warp
 #endif
 constexpr int kSplitL = DEM_TREE_SPLIT_LEVEL, kSplit = 1 << (3 * kSplitL);
 
-// Monopole + quadrupole of node (A, B, C) on the sphere at x: a / G.
-__device__ __forceinline__ void node_force(const float4 &A, const float4 &B, const float4 &C, const float4 &x,
-                                           float &ax, float &ay, float &az)
+// The node's multipoles up to rank ORDER on the sphere at x: a / G.  With u
+// the unit vector from the node's COM to x and r the distance,
+//   a / G = -M u / r^2 + sum_n (n T_n . u^(n-1) - (2n+1) (T_n . u^n) u) / r^(n+2),
+// the gradient of the potential -G (M / r + sum_n T_n . x^n / r^(2n+1))
+// (unit-vector form: no power of r above the sixth is formed).
+template <int ORDER>
+__device__ __forceinline__ void node_force(const float *nd, const float4 &x, float &ax, float &ay, float &az)
 {
-    const float dx = A.x - x.x, dy = A.y - x.y, dz = A.z - x.z;
-    const float r2 = dx * dx + dy * dy + dz * dz;
-    const float inv = rsqrtf(r2);
-    const float inv2 = inv * inv, inv3 = inv2 * inv, inv5 = inv3 * inv2;
-    const float qx = B.x * dx + B.w * dy + C.x * dz;
-    const float qy = B.w * dx + B.y * dy + C.y * dz;
-    const float qz = C.x * dx + C.y * dy + B.z * dz;
-    const float dqd = dx * qx + dy * qy + dz * qz;
-    const float sc = A.w * inv3 + 2.5f * dqd * inv5 * inv2;
-    ax += sc * dx - inv5 * qx;
-    ay += sc * dy - inv5 * qy;
-    az += sc * dz - inv5 * qz;
+    const float dx = x.x - nd[0], dy = x.y - nd[1], dz = x.z - nd[2];
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    const float ux = dx * inv, uy = dy * inv, uz = dz * inv;
+    float px[5], py[5], pz[5];
+    powers4(ux, px);
+    powers4(uy, py);
+    powers4(uz, pz);
+    float tx = 0.f, ty = 0.f, tz = 0.f;   // sum_n t_n / r^(n-2), Horner in 1/r from the top rank
+#pragma unroll
+    for (int n = ORDER; n >= 2; --n) {
+        const float *T = nd + node_off(n);
+        float vx = 0.f, vy = 0.f, vz = 0.f;   // T_n . u^(n-1)
+#pragma unroll
+        for (int fa = n - 1; fa >= 0; --fa)
+#pragma unroll
+            for (int fb = n - 1 - fa; fb >= 0; --fb) {
+                const int fc = n - 1 - fa - fb;
+                const float w = (factf(n - 1) / (factf(fa) * factf(fb) * factf(fc))) * (px[fa] * py[fb] * pz[fc]);
+                vx = fmaf(w, T[mono_idx(fa + 1, fb, fc)], vx);
+                vy = fmaf(w, T[mono_idx(fa, fb + 1, fc)], vy);
+                vz = fmaf(w, T[mono_idx(fa, fb, fc + 1)], vz);
+            }
+        const float sn = vx * ux + vy * uy + vz * uz;   // T_n . u^n
+        const float k1 = (float)n, k2 = (float)(2 * n + 1);
+        tx = tx * inv + (k1 * vx - k2 * sn * ux);
+        ty = ty * inv + (k1 * vy - k2 * sn * uy);
+        tz = tz * inv + (k1 * vz - k2 * sn * uz);
+    }
+    const float inv2 = inv * inv, M = nd[3];
+    ax += inv2 * (tx * inv2 - M * ux);
+    ay += inv2 * (ty * inv2 - M * uy);
+    az += inv2 * (tz * inv2 - M * uz);
 }
 
 // One warp walks the tree for a group of 32 consecutive spheres in leaf order.  Each round takes up to 32 nodes off the warp's stack, one per lane,
@@ -365,11 +504,14 @@ __device__ __forceinline__ void node_force(const float4 &A, const float4 &B, con
 // subtrees at level kSplitL (one warp each, grid dimension y), so that many
 // more warps hide the latency of the rounds; each writes its partial sum,
 // k_tree_combine adds them in order.
+template <int ORDER>
 __global__ void __launch_bounds__(32) k_tree_force(Arrays a, Sizes z)
 {
     // one warp per block: walks of very different lengths do not hold one
     // another's block resident
     __shared__ int st[kTreeStack];
+    // accepted cells of a round, staged for every lane (ranks above 2 only)
+    __shared__ float4 stage[ORDER > 2 ? 32 * kNodeF4 : 1];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
@@ -405,7 +547,7 @@ __global__ void __launch_bounds__(32) k_tree_force(Arrays a, Sizes z)
     }
     const float eps2 = (float)S.eps2;
     const int D = S.tD;
-    const float4 *nodes = a.tnode + 3 * S.tnode0;
+    const float4 *nodes = a.tnode + kNodeF4 * S.tnode0;
     const int2 *leaves = a.tleaf + S.tleaf0;
     const float4 *tp = a.tpos + s0;
     const int32_t *tg = a.tagg + s0;
@@ -425,16 +567,16 @@ __global__ void __launch_bounds__(32) k_tree_force(Arrays a, Sizes z)
         int2 lf = make_int2(0, 0);
         if (e >= 0) {
             const int n = e >> 3, L = e & 7;
-            A = nodes[3 * n];
+            A = nodes[kNodeF4 * n];
             if (A.w != 0.f) {
-                C = nodes[3 * n + 2];
+                B = nodes[kNodeF4 * n + 1];   // opening radius^2, T2
                 const float gx = fmaxf(fmaxf(bx0 - A.x, A.x - bx1), 0.f);
                 const float gy = fmaxf(fmaxf(by0 - A.y, A.y - by1), 0.f);
                 const float gz = fmaxf(fmaxf(bz0 - A.z, A.z - bz1), 0.f);
-                acc = gx * gx + gy * gy + gz * gz > C.z;
+                acc = gx * gx + gy * gy + gz * gz > B.x;
                 leaf = !acc && L == D;
                 open = !acc && L < D;
-                if (acc) B = nodes[3 * n + 1];
+                if (acc) C = nodes[kNodeF4 * n + 2];
                 if (leaf) lf = leaves[n - lvl_off(D)];
             }
         }
@@ -446,7 +588,7 @@ __global__ void __launch_bounds__(32) k_tree_force(Arrays a, Sizes z)
             if (open) {
                 acc = true;
                 open = false;
-                B = nodes[3 * (e >> 3) + 1];
+                C = nodes[kNodeF4 * (e >> 3) + 2];
             }
             full = true;
         } else if (open) {
@@ -457,18 +599,45 @@ __global__ void __launch_bounds__(32) k_tree_force(Arrays a, Sizes z)
         }
         if (sp + need <= kTreeStack) sp += need;
         __syncwarp();
-        // accepted cells: every lane adds each of them
+        // accepted cells: every lane adds each of them (rank 2: the cell's 3
+        // float4 passed by shuffles; higher ranks: its 9 float4 staged in
+        // shared memory by the lane that accepted it)
         unsigned am = __ballot_sync(FULL, acc);
+        if (ORDER > 2) {
+            if (acc) {
+                const float4 *nd = nodes + kNodeF4 * (e >> 3);
+                stage[kNodeF4 * lane] = A;
+                stage[kNodeF4 * lane + 1] = B;
+                stage[kNodeF4 * lane + 2] = C;
+#pragma unroll
+                for (int q = 3; q < kNodeF4; ++q) stage[kNodeF4 * lane + q] = nd[q];
+            }
+            __syncwarp();
+        }
         while (am) {
             const int b = __ffs(am) - 1;
             am &= am - 1;
-            const float4 Ab = make_float4(__shfl_sync(FULL, A.x, b), __shfl_sync(FULL, A.y, b),
-                                          __shfl_sync(FULL, A.z, b), __shfl_sync(FULL, A.w, b));
-            const float4 Bb = make_float4(__shfl_sync(FULL, B.x, b), __shfl_sync(FULL, B.y, b),
-                                          __shfl_sync(FULL, B.z, b), __shfl_sync(FULL, B.w, b));
-            const float4 Cb = make_float4(__shfl_sync(FULL, C.x, b), __shfl_sync(FULL, C.y, b), 0.f, 0.f);
-            if (mine) node_force(Ab, Bb, Cb, xi, ax, ay, az);
+            if (ORDER > 2) {
+                float nd[4 * kNodeF4];
+#pragma unroll
+                for (int q = 0; q < kNodeF4; ++q) {
+                    const float4 v = stage[kNodeF4 * b + q];
+                    nd[4 * q] = v.x; nd[4 * q + 1] = v.y; nd[4 * q + 2] = v.z; nd[4 * q + 3] = v.w;
+                }
+                if (mine) node_force<ORDER>(nd, xi, ax, ay, az);
+            } else {
+                float nd[12];
+                nd[0] = __shfl_sync(FULL, A.x, b); nd[1] = __shfl_sync(FULL, A.y, b);
+                nd[2] = __shfl_sync(FULL, A.z, b); nd[3] = __shfl_sync(FULL, A.w, b);
+                nd[4] = 0.f;
+                nd[5] = __shfl_sync(FULL, B.y, b); nd[6] = __shfl_sync(FULL, B.z, b);
+                nd[7] = __shfl_sync(FULL, B.w, b); nd[8] = __shfl_sync(FULL, C.x, b);
+                nd[9] = __shfl_sync(FULL, C.y, b); nd[10] = __shfl_sync(FULL, C.z, b);
+                nd[11] = 0.f;
+                if (mine) node_force<2>(nd, xi, ax, ay, az);
+            }
         }
+        if (ORDER > 2) __syncwarp();
         // opened leaves: lanes load a leaf's spheres side by side, then
         // every lane adds each of them (passed by shuffles)
         unsigned lm = __ballot_sync(FULL, leaf);
@@ -521,7 +690,7 @@ __global__ void k_tree_combine(Arrays a, Sizes z)
     a.fg[S.s0 + i] = make_dbl4(gm * sx.value(), gm * sy.value(), gm * sz.value(), 0.0);
 }
 
-void launch_tree_gravity(const Arrays &a, const Sizes &z, int max_depth, cudaStream_t st)
+void launch_tree_gravity(const Arrays &a, const Sizes &z, int max_depth, int order, cudaStream_t st)
 {
     if (z.N == 0 || z.TN == 0) return;
     const unsigned nb = (unsigned)((z.N + 255) / 256);
@@ -535,7 +704,8 @@ void launch_tree_gravity(const Arrays &a, const Sizes &z, int max_depth, cudaStr
     k_tree_leaves<<<(unsigned)((z.TL + 127) / 128), 128, 0, st>>>(a, z);
     for (int L = max_depth - 1; L >= 0; --L)
         k_tree_up<<<(unsigned)((z.TN + 255) / 256), 256, 0, st>>>(a, z, L);
-    k_tree_force<<<dim3((unsigned)z.TG, kSplit), 32, 0, st>>>(a, z);
+    if (order == 2) k_tree_force<2><<<dim3((unsigned)z.TG, kSplit), 32, 0, st>>>(a, z);
+    else k_tree_force<4><<<dim3((unsigned)z.TG, kSplit), 32, 0, st>>>(a, z);
     k_tree_combine<<<nb, 256, 0, st>>>(a, z);
 }
 

@@ -68,6 +68,7 @@ struct dem_world {
     bool grav_sym = true;             // mixed path: symmetric tile-pair form
     int grav_tile = 0;                // symmetric form's tile: 0 = automatic, 128 or 512
     double grav_theta = 0.0;          // > 0 (mixed path): tree gravity with this opening angle
+    int grav_order = 4;               // tree gravity: highest multipole rank (4 or 2)
     int tree_maxD = 0;                // deepest tree of the current layout
     int sm_count = 0;
     double cell_factor = 1.0;
@@ -220,7 +221,8 @@ void build_fields(dem_world *w)
     add((void **)&a.tagg, C_TSPH, 4, false);
     add((void **)&a.tpart, C_TSPH, 64 * 16, false);
     add((void **)&a.tbox, C_PILE, 32, false);
-    add((void **)&a.tnode, C_TNODE, 48, false);
+    add((void **)&a.tnode, C_TNODE, 144, false);
+    add((void **)&a.traw, C_TNODE, 128, false);
     add((void **)&a.tnode_pile, C_TNODE, 4, false);
     add((void **)&a.tleaf, C_TLEAF, 8, false);
     add((void **)&a.tleaf_pile, C_TLEAF, 4, false);
@@ -563,7 +565,7 @@ void enqueue_phase(dem_world *w, int ph)
     case DEM_K_GATHER: launch_gather(a, z, d, st); break;
     case DEM_K_CONTACT: launch_contact(a, z, d, w->K, st); break;
     case DEM_K_GRAVITY:
-        if (z.TN > 0) launch_tree_gravity(a, z, w->tree_maxD, st);
+        if (z.TN > 0) launch_tree_gravity(a, z, w->tree_maxD, w->grav_order, st);
         else launch_gravity(a, z, d, w->grav_block, w->grav_ib, w->grav_pack, use_sym(w), st);
         break;
     case DEM_K_AGG_END: launch_agg_end(a, z, d, st); break;
@@ -1455,6 +1457,10 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
         w->grav_theta = value;
         dem_status s = relayout(w, w->piles, nullptr);   // tree arrays change size
         if (s != DEM_OK) { w->grav_theta = old; return s; }
+    } else if (k == "grav_order") {
+        const int o = (int)value;
+        if (o != 2 && o != 4) return fail(w, DEM_ERR_ARG, "grav_order must be 2 or 4");
+        w->grav_order = o;
     } else if (k == "grav_item") {
         if (!(value >= 1024.0)) return fail(w, DEM_ERR_ARG, "grav_item must be >= 1024");
         w->grav_item = value;
