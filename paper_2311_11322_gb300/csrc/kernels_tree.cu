@@ -440,7 +440,14 @@ __global__ void k_tree_up(Arrays a, Sizes z, int L)
     put_node(a, g, c, M, R, opening2(c, cell_centre(lo, edge, L, m), edge / (float)(1 << L), S.theta));
 }
 
-constexpr int kTreeStack = 2048;   // per warp
+// traversal stack per warp: each round pops up to 32 cells and pushes at most
+// 8 children of each, and cells of one level are all popped before their
+// parents' remaining siblings, so at most 8 x 32 cells of each level below
+// the walk's start wait on the stack: 256 x 4 = 1,024 for the deepest tree
+#ifndef DEM_TREE_STACK
+#define DEM_TREE_STACK 1024
+#endif
+constexpr int kTreeStack = DEM_TREE_STACK;
 // the walk of each group of spheres is split over the subtrees at this level
 #ifndef DEM_TREE_SPLIT_LEVEL
 #define DEM_TREE_SPLIT_LEVEL 2
@@ -504,8 +511,13 @@ __device__ __forceinline__ void node_force(const float *nd, const float4 &x, flo
 // subtrees at level kSplitL (one warp each, grid dimension y), so that many
 // more warps hide the latency of the rounds; each writes its partial sum,
 // k_tree_combine adds them in order.
+#ifdef DEM_TREE_MINB
+#define DEM_TREE_BOUNDS __launch_bounds__(32, DEM_TREE_MINB)
+#else
+#define DEM_TREE_BOUNDS __launch_bounds__(32)
+#endif
 template <int ORDER>
-__global__ void __launch_bounds__(32) k_tree_force(Arrays a, Sizes z)
+__global__ void DEM_TREE_BOUNDS k_tree_force(Arrays a, Sizes z)
 {
     // one warp per block: walks of very different lengths do not hold one
     // another's block resident
