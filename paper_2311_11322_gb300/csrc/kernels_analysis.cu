@@ -18,6 +18,7 @@
 
 #include "dem_internal.h"
 #include "devmath.cuh"
+#include "launch.cuh"
 
 namespace dem {
 
@@ -82,6 +83,7 @@ __device__ __forceinline__ void agg_moments(const Arrays &a, int64_t g, const Pi
 
 __global__ void __launch_bounds__(kBulkBlock) k_bulk_partials(Arrays a, Sizes z, int mode, int only)
 {
+    pdl_enter();
     const int64_t ch = blockIdx.x;
     if (ch >= z.CH) return;
     const int p = a.chunk_pile[ch];
@@ -214,6 +216,7 @@ __device__ void bulk_record(const double *s, const PileStatic &S, const PileDyn 
 
 __global__ void __launch_bounds__(kBulkBlock) k_bulk_finalize(Arrays a, Sizes z, int mode, int only)
 {
+    pdl_enter();
     const int p = blockIdx.x;
     if (p >= z.P || !bulk_due(a, p, mode, only)) return;
     const PileStatic &S = a.ps[p];
@@ -248,8 +251,8 @@ __global__ void __launch_bounds__(kBulkBlock) k_bulk_finalize(Arrays a, Sizes z,
 void launch_bulk(const Arrays &a, const Sizes &z, int mode, int only, cudaStream_t st)
 {
     if (z.CH == 0 || z.P == 0) return;
-    k_bulk_partials<<<(unsigned)z.CH, kBulkBlock, 0, st>>>(a, z, mode, only);
-    k_bulk_finalize<<<(unsigned)z.P, kBulkBlock, 0, st>>>(a, z, mode, only);
+    launch_pdl(k_bulk_partials, (unsigned)z.CH, kBulkBlock, 0, st, a, z, mode, only);
+    launch_pdl(k_bulk_finalize, (unsigned)z.P, kBulkBlock, 0, st, a, z, mode, only);
 }
 
 }  // namespace dem

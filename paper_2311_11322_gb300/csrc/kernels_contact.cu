@@ -53,6 +53,7 @@
 //   sphere b: -F,            tau = (l_b n) x F - M.
 #include "dem_internal.h"
 #include "devmath.cuh"
+#include "launch.cuh"
 
 namespace dem {
 
@@ -412,6 +413,7 @@ __device__ __forceinline__ float filter_tol(const PileStatic &S, float4 p)
 template <bool FP64>
 __global__ void __launch_bounds__(kContactBlock) k_contact_filter(Arrays a, Sizes z)
 {
+    pdl_enter();
     typedef typename CT<FP64>::P4 P4;
     // per thread: the hits found so far, (partner index << 32 | sorted
     // position), kept in increasing order by insertion
@@ -522,6 +524,7 @@ __device__ __noinline__ int64_t overflow_next(const Arrays &a, const PileStatic 
 template <bool FP64>
 __global__ void DEM_CONTACT_BOUNDS k_contact(Arrays a, Sizes z)
 {
+    pdl_enter();
     typedef typename CT<FP64>::P4 P4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int K = z.K;
@@ -669,11 +672,11 @@ void launch_contact(const Arrays &a, const Sizes &z, bool fp64, int K, cudaStrea
     unsigned nb = (unsigned)((z.N + kContactBlock - 1) / kContactBlock);
     size_t smem = contact_smem(fp64, K);
     if (fp64) {
-        k_contact_filter<true><<<nb, kContactBlock, 0, st>>>(a, z);
-        k_contact<true><<<nb, kContactBlock, smem, st>>>(a, z);
+        launch_pdl(k_contact_filter<true>, nb, kContactBlock, 0, st, a, z);
+        launch_pdl(k_contact<true>, nb, kContactBlock, smem, st, a, z);
     } else {
-        k_contact_filter<false><<<nb, kContactBlock, 0, st>>>(a, z);
-        k_contact<false><<<nb, kContactBlock, smem, st>>>(a, z);
+        launch_pdl(k_contact_filter<false>, nb, kContactBlock, 0, st, a, z);
+        launch_pdl(k_contact<false>, nb, kContactBlock, smem, st, a, z);
     }
 }
 

@@ -33,6 +33,7 @@
 // partials in FP64 in tile order (deterministic).
 #include "dem_internal.h"
 #include "devmath.cuh"
+#include "launch.cuh"
 
 namespace dem {
 
@@ -321,9 +322,22 @@ __device__ __forceinline__ void gravity32p_item(const Arrays &a, const int4 it, 
         }
 }
 
+// Next work item of a persistent grid.  Every block takes items until it
+// draws one past the end, so a launch makes exactly GI + gridDim.x draws; the
+// last draw puts the counter back to zero for the next launch (the counter
+// is zeroed once when the layout is uploaded), so no memset node is needed
+// between the kernels of a step.
+__device__ __forceinline__ int grab_item(int32_t *counter, int64_t GI)
+{
+    const int v = atomicAdd(counter, 1);
+    if ((int64_t)v == GI + (int64_t)gridDim.x - 1) atomicExch(counter, 0);
+    return v;
+}
+
 template <int BS, int NP>
 __global__ void __launch_bounds__(BS) k_gravity32p(Arrays a, Sizes z)
 {
+    pdl_enter();
     __shared__ float4 sp[2 * BS];
     __shared__ int sag[BS];
     __shared__ int excl[2];
@@ -331,7 +345,7 @@ __global__ void __launch_bounds__(BS) k_gravity32p(Arrays a, Sizes z)
     __shared__ int next;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) next = atomicAdd(a.gcounter, 1);
+        if (threadIdx.x == 0) next = grab_item(a.gcounter, z.GI);
         __syncthreads();
         const int item = next;
         if (item >= z.GI) return;
@@ -339,20 +353,21 @@ __global__ void __launch_bounds__(BS) k_gravity32p(Arrays a, Sizes z)
     }
 }
 
-// Persistent grid: each block takes the next item from a counter that a
-// memset node zeroes before the launch, until the list is exhausted.  Items
-// are listed largest first; which block runs an item does not change its
-// result, so the sums stay deterministic.
+// Persistent grid: each block takes the next item from a counter (see
+// grab_item) until the list is exhausted.  Items are listed largest first;
+// which block runs an item does not change its result, so the sums stay
+// deterministic.
 template <int BS, int IB>
 __global__ void __launch_bounds__(BS) k_gravity32(Arrays a, Sizes z)
 {
+    pdl_enter();
     __shared__ float4 sp[BS];
     __shared__ int sag[BS];
     __shared__ int excl[2];
     __shared__ int next;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) next = atomicAdd(a.gcounter, 1);
+        if (threadIdx.x == 0) next = grab_item(a.gcounter, z.GI);
         __syncthreads();
         const int item = next;
         if (item >= z.GI) return;
@@ -363,6 +378,7 @@ __global__ void __launch_bounds__(BS) k_gravity32(Arrays a, Sizes z)
 template <int BS, int IB>
 __global__ void __launch_bounds__(BS) k_gravity64(Arrays a, Sizes z)
 {
+    pdl_enter();
     __shared__ dbl4 sp[BS];
     __shared__ int sag[BS];
     __shared__ int excl[2];
@@ -684,6 +700,7 @@ __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, 
 template <int WPB>
 __global__ void DEM_GSYM_BOUNDS k_gravity32s(Arrays a, Sizes z)
 {
+    pdl_enter();
     constexpr int kTile = 32 * WPB * kSymIB;
     __shared__ float4 sp[kTile];
     __shared__ int sag[kTile];
@@ -691,7 +708,7 @@ __global__ void DEM_GSYM_BOUNDS k_gravity32s(Arrays a, Sizes z)
     __shared__ int next;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) next = atomicAdd(a.gcounter, 1);
+        if (threadIdx.x == 0) next = grab_item(a.gcounter, z.GI);
         __syncthreads();
         const int item = next;
         if (item >= z.GI) return;
@@ -819,6 +836,7 @@ constexpr size_t kSym64Smem = sizeof(dbl4) * kSymTile * 5 + sizeof(int) * kSymTi
 
 __global__ void __launch_bounds__(kSymBS) k_gravity64s(Arrays a, Sizes z)
 {
+    pdl_enter();
     extern __shared__ __align__(32) unsigned char sm64[];
     dbl4 *sp = (dbl4 *)sm64;
     dbl4 *sj = sp + kSymTile;
@@ -826,7 +844,7 @@ __global__ void __launch_bounds__(kSymBS) k_gravity64s(Arrays a, Sizes z)
     __shared__ int next;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) next = atomicAdd(a.gcounter, 1);
+        if (threadIdx.x == 0) next = grab_item(a.gcounter, z.GI);
         __syncthreads();
         const int item = next;
         if (item >= z.GI) return;
@@ -836,6 +854,7 @@ __global__ void __launch_bounds__(kSymBS) k_gravity64s(Arrays a, Sizes z)
 
 __global__ void k_grav_combine_sym64(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= z.N) return;
     int p = a.sph_pile[i];
@@ -863,6 +882,7 @@ __global__ void k_grav_combine_sym64(Arrays a, Sizes z)
 // items (a, t), a < t, in that fixed order, as float-float sums (FFSum).
 __global__ void k_grav_combine_sym(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= z.N) return;
     int p = a.sph_pile[i];
@@ -890,6 +910,7 @@ __global__ void k_grav_combine_sym(Arrays a, Sizes z)
 template <bool FP64>
 __global__ void k_grav_combine(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= z.N) return;
     int p = a.sph_pile[i];
@@ -917,17 +938,16 @@ template <int BS, int IB>
 static void launch_g(const Arrays &a, const Sizes &z, bool fp64, bool pack, cudaStream_t st)
 {
     if (fp64) {
-        k_gravity64<BS, IB><<<(unsigned)z.GI, BS, 0, st>>>(a, z);
+        launch_pdl(k_gravity64<BS, IB>, (unsigned)z.GI, BS, 0, st, a, z);
     } else {
         int64_t nb = z.GB > 0 && z.GB < z.GI ? z.GB : z.GI;
-        cudaMemsetAsync(a.gcounter, 0, sizeof(int32_t), st);
         if constexpr (IB % 2 == 0) {
             if (pack) {
-                k_gravity32p<BS, IB / 2><<<(unsigned)nb, BS, 0, st>>>(a, z);
+                launch_pdl(k_gravity32p<BS, IB / 2>, (unsigned)nb, BS, 0, st, a, z);
                 return;
             }
         }
-        k_gravity32<BS, IB><<<(unsigned)nb, BS, 0, st>>>(a, z);
+        launch_pdl(k_gravity32<BS, IB>, (unsigned)nb, BS, 0, st, a, z);
     }
 }
 
@@ -973,14 +993,13 @@ void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int i
     if (z.GI == 0) return;
     if (sym) {
         int64_t nb = z.GB > 0 && z.GB < z.GI ? z.GB : z.GI;
-        cudaMemsetAsync(a.gcounter, 0, sizeof(int32_t), st);
         if (fp64) {
-            k_gravity64s<<<(unsigned)nb, kSymBS, kSym64Smem, st>>>(a, z);
-            if (z.GP > 0) k_grav_combine_sym64<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+            launch_pdl(k_gravity64s, (unsigned)nb, kSymBS, kSym64Smem, st, a, z);
+            if (z.GP > 0) launch_pdl(k_grav_combine_sym64, (unsigned)((z.N + 255) / 256), 256, 0, st, a, z);
         } else {
-            if (z.gtile == 128) k_gravity32s<1><<<(unsigned)nb, 32, 0, st>>>(a, z);
-            else k_gravity32s<4><<<(unsigned)nb, kSymBS, 0, st>>>(a, z);
-            if (z.GP > 0) k_grav_combine_sym<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+            if (z.gtile == 128) launch_pdl(k_gravity32s<1>, (unsigned)nb, 32, 0, st, a, z);
+            else launch_pdl(k_gravity32s<4>, (unsigned)nb, kSymBS, 0, st, a, z);
+            if (z.GP > 0) launch_pdl(k_grav_combine_sym, (unsigned)((z.N + 255) / 256), 256, 0, st, a, z);
         }
         return;
     }
@@ -994,8 +1013,8 @@ void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int i
     else if (block == 256 && ib == 2) launch_g<256, 2>(a, z, fp64, pack, st);
     else launch_g<256, 4>(a, z, fp64, pack, st);
     if (z.GP > 0) {
-        if (fp64) k_grav_combine<true><<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
-        else k_grav_combine<false><<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+        if (fp64) launch_pdl(k_grav_combine<true>, (unsigned)((z.N + 255) / 256), 256, 0, st, a, z);
+        else launch_pdl(k_grav_combine<false>, (unsigned)((z.N + 255) / 256), 256, 0, st, a, z);
     }
 }
 

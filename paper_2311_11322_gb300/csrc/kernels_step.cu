@@ -11,6 +11,7 @@
 // point), YORP increment (Sec. 4.1), point-mass planet (Sec. 4.2).
 #include "dem_internal.h"
 #include "devmath.cuh"
+#include "launch.cuh"
 
 namespace dem {
 
@@ -33,6 +34,7 @@ __device__ int find_slot(const PileStatic *ps, int P, int64_t idx, int which)
 
 __global__ void k_fill_ids(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int P = (int)z.P;
     if (t < z.N) a.sph_pile[t] = find_slot(a.ps, P, t, 0);
@@ -45,7 +47,7 @@ void launch_fill_ids(const Arrays &a, const Sizes &z, cudaStream_t st)
     int64_t n = z.N > z.A ? z.N : z.A;
     if (z.CH > n) n = z.CH;
     if (n == 0 || z.P == 0) return;
-    k_fill_ids<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, z);
+    launch_pdl(k_fill_ids, (unsigned)((n + 255) / 256), 256, 0, st, a, z);
 }
 
 // ---------------------------------------------------------------- rotation
@@ -193,6 +195,7 @@ __device__ void free_rotate_adaptive(double *q, double3 &wb, const double *I, co
 template <bool FP64, bool ADAPT>
 __global__ void k_agg_begin(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= z.A) return;
     int p = a.agg_pile[g];
@@ -290,11 +293,11 @@ void launch_agg_begin(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t s
     // the adaptive rotor needs many more registers: its variant runs only when
     // some pile asks for it
     if (z.adapt) {
-        if (fp64) k_agg_begin<true, true><<<nb, 128, 0, st>>>(a, z);
-        else k_agg_begin<false, true><<<nb, 128, 0, st>>>(a, z);
+        if (fp64) launch_pdl(k_agg_begin<true, true>, nb, 128, 0, st, a, z);
+        else launch_pdl(k_agg_begin<false, true>, nb, 128, 0, st, a, z);
     } else {
-        if (fp64) k_agg_begin<true, false><<<nb, 128, 0, st>>>(a, z);
-        else k_agg_begin<false, false><<<nb, 128, 0, st>>>(a, z);
+        if (fp64) launch_pdl(k_agg_begin<true, false>, nb, 128, 0, st, a, z);
+        else launch_pdl(k_agg_begin<false, false>, nb, 128, 0, st, a, z);
     }
 }
 
@@ -305,6 +308,7 @@ void launch_agg_begin(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t s
 template <int MODE>
 __global__ void k_pile_partials(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t ch = blockIdx.x;
     if (ch >= z.CH) return;
     int p = a.chunk_pile[ch];
@@ -349,6 +353,7 @@ __global__ void k_pile_partials(Arrays a, Sizes z)
 template <int MODE>
 __global__ void k_pile_finalize(Arrays a, Sizes z)
 {
+    pdl_enter();
     const int p = blockIdx.x;
     if (p >= z.P || !pile_active(a, p)) return;
     const PileStatic &S = a.ps[p];
@@ -401,15 +406,15 @@ __global__ void k_pile_finalize(Arrays a, Sizes z)
 void launch_pile_begin(const Arrays &a, const Sizes &z, cudaStream_t st)
 {
     if (z.CH == 0) return;
-    k_pile_partials<0><<<(unsigned)z.CH, 128, 0, st>>>(a, z);
-    k_pile_finalize<0><<<(unsigned)z.P, 128, 0, st>>>(a, z);
+    launch_pdl(k_pile_partials<0>, (unsigned)z.CH, 128, 0, st, a, z);
+    launch_pdl(k_pile_finalize<0>, (unsigned)z.P, 128, 0, st, a, z);
 }
 
 void launch_pile_end(const Arrays &a, const Sizes &z, cudaStream_t st)
 {
     if (z.CH == 0) return;
-    k_pile_partials<1><<<(unsigned)z.CH, 128, 0, st>>>(a, z);
-    k_pile_finalize<1><<<(unsigned)z.P, 128, 0, st>>>(a, z);
+    launch_pdl(k_pile_partials<1>, (unsigned)z.CH, 128, 0, st, a, z);
+    launch_pdl(k_pile_finalize<1>, (unsigned)z.P, 128, 0, st, a, z);
 }
 
 // ---------------------------------------------------------------- expansion
@@ -462,6 +467,7 @@ __device__ __forceinline__ int cell_coord_d(double x, double inv_cell, int n)
 template <bool FP64>
 __global__ void k_keys(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= z.N) return;
     int p = a.sph_pile[i];
@@ -495,6 +501,7 @@ __device__ int tile_pile(const Arrays &a, const Sizes &z, int64_t t);
 // Zero the cell counts of the piles that rebuild this step.
 __global__ void k_clear_cells(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= z.C) return;
     int p = tile_pile(a, z, c / kScanTile);
@@ -504,16 +511,17 @@ __global__ void k_clear_cells(Arrays a, Sizes z)
 void launch_keys(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
 {
     if (z.N == 0) return;
-    k_clear_cells<<<(unsigned)((z.C + 255) / 256), 256, 0, st>>>(a, z);
+    launch_pdl(k_clear_cells, (unsigned)((z.C + 255) / 256), 256, 0, st, a, z);
     unsigned nb = (unsigned)((z.N + 255) / 256);
-    if (fp64) k_keys<true><<<nb, 256, 0, st>>>(a, z);
-    else k_keys<false><<<nb, 256, 0, st>>>(a, z);
+    if (fp64) launch_pdl(k_keys<true>, nb, 256, 0, st, a, z);
+    else launch_pdl(k_keys<false>, nb, 256, 0, st, a, z);
 }
 
 // Host request (after a state write or a new layout): the next step rebuilds
 // the cell list and hit lists of pile `slot` (all piles for slot < 0).
 __global__ void k_force_rebuild(Arrays a, Sizes z, int slot)
 {
+    pdl_enter();
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= z.P || (slot >= 0 && p != slot)) return;
     a.pd[p].rebuild = 1;
@@ -522,7 +530,7 @@ __global__ void k_force_rebuild(Arrays a, Sizes z, int slot)
 void launch_force_rebuild(const Arrays &a, const Sizes &z, int slot, cudaStream_t st)
 {
     if (z.P == 0) return;
-    k_force_rebuild<<<(unsigned)((z.P + 127) / 128), 128, 0, st>>>(a, z, slot);
+    launch_pdl(k_force_rebuild, (unsigned)((z.P + 127) / 128), 128, 0, st, a, z, slot);
 }
 
 // ---------------------------------------------------------------- scan of cell counts
@@ -539,6 +547,7 @@ __device__ int tile_pile(const Arrays &a, const Sizes &z, int64_t t)
 
 __global__ void k_scan_tiles(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t t = blockIdx.x;
     int p = tile_pile(a, z, t);
     if (!pile_active(a, p) || !a.pd[p].rebuild) return;
@@ -559,6 +568,7 @@ __global__ void k_scan_tiles(Arrays a, Sizes z)
 // One block per pile: exclusive scan of its tile sums (in place).
 __global__ void k_scan_piles(Arrays a, Sizes z)
 {
+    pdl_enter();
     int p = blockIdx.x;
     if (!pile_active(a, p) || !a.pd[p].rebuild) return;
     const PileStatic &S = a.ps[p];
@@ -588,6 +598,7 @@ __global__ void k_scan_piles(Arrays a, Sizes z)
 // One block (256 threads x 8 cells) per tile: exclusive scan plus tile offset.
 __global__ void k_scan_cells(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t t = blockIdx.x;
     int p = tile_pile(a, z, t);
     if (!pile_active(a, p) || !a.pd[p].rebuild) return;
@@ -618,14 +629,15 @@ __global__ void k_scan_cells(Arrays a, Sizes z)
 void launch_scan(const Arrays &a, const Sizes &z, cudaStream_t st)
 {
     if (z.T == 0) return;
-    k_scan_tiles<<<(unsigned)z.T, 256, 0, st>>>(a, z);
-    k_scan_piles<<<(unsigned)z.P, 1024, 0, st>>>(a, z);
-    k_scan_cells<<<(unsigned)z.T, 256, 0, st>>>(a, z);
+    launch_pdl(k_scan_tiles, (unsigned)z.T, 256, 0, st, a, z);
+    launch_pdl(k_scan_piles, (unsigned)z.P, 1024, 0, st, a, z);
+    launch_pdl(k_scan_cells, (unsigned)z.T, 256, 0, st, a, z);
 }
 
 // ---------------------------------------------------------------- scatter and cell order
 __global__ void k_scatter(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= z.N) return;
     int p = a.sph_pile[i];
@@ -638,7 +650,7 @@ __global__ void k_scatter(Arrays a, Sizes z)
 void launch_scatter(const Arrays &a, const Sizes &z, cudaStream_t st)
 {
     if (z.N == 0) return;
-    k_scatter<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+    launch_pdl(k_scatter, (unsigned)((z.N + 255) / 256), 256, 0, st, a, z);
 }
 
 // The thread at the first position of each cell sorts that cell's entries by
@@ -646,6 +658,7 @@ void launch_scatter(const Arrays &a, const Sizes &z, cudaStream_t st)
 // the order of neighbours, and so every contact sum, deterministic.
 __global__ void k_cell_order(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= z.N) return;
     int p = a.sph_pile[k];
@@ -671,7 +684,7 @@ __global__ void k_cell_order(Arrays a, Sizes z)
 void launch_cell_order(const Arrays &a, const Sizes &z, cudaStream_t st)
 {
     if (z.N == 0) return;
-    k_cell_order<<<(unsigned)((z.N + 255) / 256), 256, 0, st>>>(a, z);
+    launch_pdl(k_cell_order, (unsigned)((z.N + 255) / 256), 256, 0, st, a, z);
 }
 
 // ---------------------------------------------------------------- gather
@@ -680,6 +693,7 @@ void launch_cell_order(const Arrays &a, const Sizes &z, cudaStream_t st)
 template <bool FP64>
 __global__ void k_gather(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= z.N) return;
     int p = a.sph_pile[k];
@@ -722,8 +736,8 @@ void launch_gather(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
 {
     if (z.N == 0) return;
     unsigned nb = (unsigned)((z.N + 255) / 256);
-    if (fp64) k_gather<true><<<nb, 256, 0, st>>>(a, z);
-    else k_gather<false><<<nb, 256, 0, st>>>(a, z);
+    if (fp64) launch_pdl(k_gather<true>, nb, 256, 0, st, a, z);
+    else launch_pdl(k_gather<false>, nb, 256, 0, st, a, z);
 }
 
 // ---------------------------------------------------------------- step end
@@ -735,6 +749,7 @@ void launch_gather(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
 template <bool FP64>
 __global__ void k_agg_end(Arrays a, Sizes z)
 {
+    pdl_enter();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= z.A) return;
     int p = a.agg_pile[g];
@@ -858,8 +873,8 @@ void launch_agg_end(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
 {
     if (z.A == 0) return;
     unsigned nb = (unsigned)((z.A + 127) / 128);
-    if (fp64) k_agg_end<true><<<nb, 128, 0, st>>>(a, z);
-    else k_agg_end<false><<<nb, 128, 0, st>>>(a, z);
+    if (fp64) launch_pdl(k_agg_end<true>, nb, 128, 0, st, a, z);
+    else launch_pdl(k_agg_end<false>, nb, 128, 0, st, a, z);
 }
 
 }  // namespace dem

@@ -23,6 +23,7 @@
 // per-sphere gravity array as the direct sum.
 #include "dem_internal.h"
 #include "devmath.cuh"
+#include "launch.cuh"
 
 namespace dem {
 
@@ -55,6 +56,7 @@ __device__ __forceinline__ uint32_t spread3(uint32_t v)
 // One block per pile: reset the box and the leaf counts.
 __global__ void k_tree_init(Arrays a, Sizes z)
 {
+    pdl_enter();
     const int p = blockIdx.x;
     if (p >= z.P || !tree_pile(a, p)) return;
     const PileStatic &S = a.ps[p];
@@ -71,6 +73,7 @@ __global__ void k_tree_init(Arrays a, Sizes z)
 // per warp and pile (min/max do not depend on the order).
 __global__ void k_tree_box(Arrays a, Sizes z)
 {
+    pdl_enter();
     const unsigned FULL = 0xffffffffu;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int p = i < z.N ? a.sph_pile[i] : -1;
@@ -111,6 +114,7 @@ __device__ __forceinline__ void tree_cube(const Arrays &a, int p, float3 &lo, fl
 
 __global__ void k_tree_keys(Arrays a, Sizes z)
 {
+    pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= z.N) return;
     const int p = a.sph_pile[i];
@@ -133,6 +137,7 @@ __global__ void k_tree_keys(Arrays a, Sizes z)
 // One block of 1024 threads per pile: exclusive scan of the leaf counts.
 __global__ void k_tree_scan(Arrays a, Sizes z)
 {
+    pdl_enter();
     const int p = blockIdx.x;
     if (p >= z.P || !tree_pile(a, p)) return;
     const PileStatic &S = a.ps[p];
@@ -160,6 +165,7 @@ __global__ void k_tree_scan(Arrays a, Sizes z)
 
 __global__ void k_tree_scatter(Arrays a, Sizes z)
 {
+    pdl_enter();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= z.N) return;
     const int p = a.sph_pile[i];
@@ -172,6 +178,7 @@ __global__ void k_tree_scatter(Arrays a, Sizes z)
 // sort; leaves hold a handful of spheres): deterministic sums.
 __global__ void k_tree_leaf_order(Arrays a, Sizes z)
 {
+    pdl_enter();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= z.N) return;
     const int p = a.sph_pile[k];
@@ -196,6 +203,7 @@ __global__ void k_tree_leaf_order(Arrays a, Sizes z)
 // that a leaf's spheres are contiguous for the moments and the walk.
 __global__ void k_tree_gather(Arrays a, Sizes z)
 {
+    pdl_enter();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= z.N) return;
     const int p = a.sph_pile[k];
@@ -317,6 +325,7 @@ __device__ __forceinline__ float opening2(float3 com, float3 ctr, float size, fl
 // Leaf moments: one thread per leaf of every tree pile.
 __global__ void k_tree_leaves(Arrays a, Sizes z)
 {
+    pdl_enter();
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= z.TL) return;
     const int p = a.tleaf_pile[g];
@@ -371,6 +380,7 @@ __global__ void k_tree_leaves(Arrays a, Sizes z)
 // thread per node of every tree pile deep enough.
 __global__ void k_tree_up(Arrays a, Sizes z, int L)
 {
+    pdl_enter();
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= z.TN) return;
     const int p = a.tnode_pile[g];
@@ -519,6 +529,7 @@ __device__ __forceinline__ void node_force(const float *nd, const float4 &x, flo
 template <int ORDER>
 __global__ void DEM_TREE_BOUNDS k_tree_force(Arrays a, Sizes z)
 {
+    pdl_enter();
     // one warp per block: walks of very different lengths do not hold one
     // another's block resident
     __shared__ int st[kTreeStack];
@@ -687,6 +698,7 @@ __global__ void DEM_TREE_BOUNDS k_tree_force(Arrays a, Sizes z)
 // Sum the subtree partials of each sphere (float-float, fixed order).
 __global__ void k_tree_combine(Arrays a, Sizes z)
 {
+    pdl_enter();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= z.N) return;
     const int p = a.sph_pile[k];
@@ -706,19 +718,19 @@ void launch_tree_gravity(const Arrays &a, const Sizes &z, int max_depth, int ord
 {
     if (z.N == 0 || z.TN == 0) return;
     const unsigned nb = (unsigned)((z.N + 255) / 256);
-    k_tree_init<<<(unsigned)z.P, 256, 0, st>>>(a, z);
-    k_tree_box<<<nb, 256, 0, st>>>(a, z);
-    k_tree_keys<<<nb, 256, 0, st>>>(a, z);
-    k_tree_scan<<<(unsigned)z.P, 1024, 0, st>>>(a, z);
-    k_tree_scatter<<<nb, 256, 0, st>>>(a, z);
-    k_tree_leaf_order<<<nb, 256, 0, st>>>(a, z);
-    k_tree_gather<<<nb, 256, 0, st>>>(a, z);
-    k_tree_leaves<<<(unsigned)((z.TL + 127) / 128), 128, 0, st>>>(a, z);
+    launch_pdl(k_tree_init, (unsigned)z.P, 256, 0, st, a, z);
+    launch_pdl(k_tree_box, nb, 256, 0, st, a, z);
+    launch_pdl(k_tree_keys, nb, 256, 0, st, a, z);
+    launch_pdl(k_tree_scan, (unsigned)z.P, 1024, 0, st, a, z);
+    launch_pdl(k_tree_scatter, nb, 256, 0, st, a, z);
+    launch_pdl(k_tree_leaf_order, nb, 256, 0, st, a, z);
+    launch_pdl(k_tree_gather, nb, 256, 0, st, a, z);
+    launch_pdl(k_tree_leaves, (unsigned)((z.TL + 127) / 128), 128, 0, st, a, z);
     for (int L = max_depth - 1; L >= 0; --L)
-        k_tree_up<<<(unsigned)((z.TN + 255) / 256), 256, 0, st>>>(a, z, L);
-    if (order == 2) k_tree_force<2><<<dim3((unsigned)z.TG, kSplit), 32, 0, st>>>(a, z);
-    else k_tree_force<4><<<dim3((unsigned)z.TG, kSplit), 32, 0, st>>>(a, z);
-    k_tree_combine<<<nb, 256, 0, st>>>(a, z);
+        launch_pdl(k_tree_up, (unsigned)((z.TN + 255) / 256), 256, 0, st, a, z, L);
+    if (order == 2) launch_pdl(k_tree_force<2>, dim3((unsigned)z.TG, kSplit), 32, 0, st, a, z);
+    else launch_pdl(k_tree_force<4>, dim3((unsigned)z.TG, kSplit), 32, 0, st, a, z);
+    launch_pdl(k_tree_combine, nb, 256, 0, st, a, z);
 }
 
 }  // namespace dem

@@ -270,11 +270,11 @@ struct GravPlan {
 bool use_sym(const dem_world *w) { return w->grav_sym; }
 
 // Tile of the symmetric form.  512-sphere tiles unless the mixed path's
-// 512-tile pairs of all piles would fill less than a sixteenth of one wave of
-// the persistent grid (single piles up to ~4,600 spheres; measured: 1,000
-// spheres 105 -> 86 us per step, 5,000 even, 8,000 slower) and no pile
-// exceeds 8,192 spheres: then 128-sphere tiles, 16 times the work items for
-// the same pairs (their partial rows, 2 T x N, stay <= 17 MB).
+// 512-tile pairs of all piles would not fill one wave of the persistent grid
+// and no pile exceeds 8,192 spheres: then 128-sphere tiles, 16 times the work
+// items for the same pairs (their partial rows, 2 T x N, stay <= 17 MB).
+// Measured per step, 512 -> 128: 1,000 spheres 89 -> 75 us, 5,000 97 -> 91,
+// 8,000 118 -> 108.
 int sym_tile(dem_world *w)
 {
     if (w->precision != DEM_MIXED) return kGravSymTile;
@@ -297,7 +297,7 @@ int sym_tile(dem_world *w)
     }
     const int bps = gravity_blocks_per_sm(false, 128, 4, false, true, kGravSymTile);
     cudaGetLastError();
-    return 16 * items < (int64_t)std::max(1, bps) * w->sm_count ? kGravSymTileSmall : kGravSymTile;
+    return items < (int64_t)std::max(1, bps) * w->sm_count ? kGravSymTileSmall : kGravSymTile;
 }
 
 GravPlan plan_gravity(dem_world *w)
@@ -529,6 +529,8 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
                            cudaMemcpyHostToDevice, w->stream));
         CU(cudaStreamSynchronize(w->stream));   // host vectors go out of scope
     }
+    // the persistent gravity grid's work counter (it resets itself after each launch)
+    CU(cudaMemsetAsync(w->A.gcounter, 0, sizeof(int32_t), w->stream));
     launch_fill_ids(w->A, w->Z, w->stream);
     // a new layout leaves the transient sort and hit lists undefined
     launch_force_rebuild(w->A, w->Z, -1, w->stream);
