@@ -139,6 +139,7 @@ struct Arrays {
     // pile reductions
     double *chunk_part;            // [chunks][kPartialDoubles]
     int32_t *chunk_pile;           // [chunks] pile slot of each chunk
+    int32_t *pile_arrive;          // [piles] chunk blocks of a reduction finished so far (0 between launches)
     double *bulk_part;             // [chunks][32] bulk-shape sums (kBulkParts used)
     PileWatch *watch;              // [piles]
     // gravity work list and j-chunk partial sums

@@ -10,10 +10,11 @@
 // (a b c)^(1/3) of the uniform ellipsoid with the pile's mass and principal
 // moments of inertia, which also gives the bulk density.
 //
-// Two kernels, like the pile reductions of the step: blocks of kAggChunk
-// aggregates sum 25 moments about the pile frame (fixed tree order), then one
-// block per pile adds the chunks in order and its first thread finishes the
-// record in FP64 (parallel-axis shift, 3x3 Jacobi eigenvalues, Cramer solve).
+// One kernel, like the pile reductions of the step: blocks of kAggChunk
+// aggregates sum 25 moments about the pile frame (fixed tree order), then the
+// pile's last block to finish adds the chunks in order and its first thread
+// finishes the record in FP64 (parallel-axis shift, 3x3 Jacobi eigenvalues,
+// Cramer solve).
 #include <math_constants.h>
 
 #include "dem_internal.h"
@@ -81,6 +82,8 @@ __device__ __forceinline__ void agg_moments(const Arrays &a, int64_t g, const Pi
     for (int c = 0; c < 3; ++c) m[22 + c] = T[3 * c] * wb[0] + T[3 * c + 1] * wb[1] + T[3 * c + 2] * wb[2];
 }
 
+__device__ void bulk_finalize(const Arrays &a, int p, int mode, double (&sh)[kBulkParts][kBulkBlock]);
+
 __global__ void __launch_bounds__(kBulkBlock) k_bulk_partials(Arrays a, Sizes z, int mode, int only)
 {
     pdl_enter();
@@ -107,7 +110,18 @@ __global__ void __launch_bounds__(kBulkBlock) k_bulk_partials(Arrays a, Sizes z,
             for (int k = 0; k < kBulkParts; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x < kBulkParts) a.bulk_part[ch * 32 + threadIdx.x] = sh[threadIdx.x][0];
+    // the pile's last chunk block to finish adds up the pile (see bulk_finalize)
+    __shared__ int last;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kBulkParts; ++k) a.bulk_part[ch * 32 + k] = sh[k][0];
+        __threadfence();   // the sums are visible before this block is counted
+        last = atomicAdd(a.pile_arrive + p, 1) == (int)S.nch - 1;
+        if (last) a.pile_arrive[p] = 0;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    bulk_finalize(a, p, mode, sh);
 }
 
 // Eigenvalues of the symmetric 3x3 matrix (xx yy zz xy xz yz), ascending, by
@@ -214,17 +228,17 @@ __device__ void bulk_record(const double *s, const PileStatic &S, const PileDyn 
     out[DEM_BULK_PLANET_DIST] = dist;
 }
 
-__global__ void __launch_bounds__(kBulkBlock) k_bulk_finalize(Arrays a, Sizes z, int mode, int only)
+// Run by the last chunk block of pile p: thread t adds chunks t, t+128, ... in
+// order, a fixed tree combines the threads (deterministic whichever block is
+// last), thread 0 forms the record and updates the watch.
+__device__ void bulk_finalize(const Arrays &a, int p, int mode, double (&sh)[kBulkParts][kBulkBlock])
 {
-    pdl_enter();
-    const int p = blockIdx.x;
-    if (p >= z.P || !bulk_due(a, p, mode, only)) return;
     const PileStatic &S = a.ps[p];
-    __shared__ double sh[kBulkParts][kBulkBlock];
     double s[kBulkParts];
     for (int k = 0; k < kBulkParts; ++k) s[k] = 0.0;
     for (int64_t ch = S.ch0 + threadIdx.x; ch < S.ch0 + S.nch; ch += kBulkBlock)
-        for (int k = 0; k < kBulkParts; ++k) s[k] += a.bulk_part[ch * 32 + k];
+        for (int k = 0; k < kBulkParts; ++k) s[k] += __ldcg(a.bulk_part + ch * 32 + k);
+    __syncthreads();   // sh is free again
     for (int k = 0; k < kBulkParts; ++k) sh[k][threadIdx.x] = s[k];
     __syncthreads();
     for (int o = kBulkBlock / 2; o > 0; o >>= 1) {
@@ -252,7 +266,6 @@ void launch_bulk(const Arrays &a, const Sizes &z, int mode, int only, cudaStream
 {
     if (z.CH == 0 || z.P == 0) return;
     launch_pdl(k_bulk_partials, (unsigned)z.CH, kBulkBlock, 0, st, a, z, mode, only);
-    launch_pdl(k_bulk_finalize, (unsigned)z.P, kBulkBlock, 0, st, a, z, mode, only);
 }
 
 }  // namespace dem

@@ -304,63 +304,19 @@ void launch_agg_begin(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t s
 // ---------------------------------------------------------------- pile reductions
 // Block b sums kAggChunk aggregates of one pile.  Mode 0 (after the drift):
 // sum M, sum M r, sum M v.  Mode 1 (after the closing kick): sum of the planet
-// force on the pile.  Fixed tree order: deterministic.
+// force on the pile.  The last of a pile's chunk blocks to finish (counted in
+// pile_arrive, which it puts back to zero) then adds the pile's chunk sums and
+// updates the pile: thread t adds chunks t, t+128, ... in order and a fixed
+// tree combines the threads, so the result does not depend on which block
+// came last.  Fixed tree orders throughout: deterministic.
 template <int MODE>
-__global__ void k_pile_partials(Arrays a, Sizes z)
+__device__ void pile_finalize_block(const Arrays &a, int p, double (&sh)[7][128])
 {
-    pdl_enter();
-    int64_t ch = blockIdx.x;
-    if (ch >= z.CH) return;
-    int p = a.chunk_pile[ch];
-    __shared__ double sh[7][128];
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (pile_active(a, p)) {
-        const PileStatic &S = a.ps[p];
-        int64_t beg = S.a0 + (ch - S.ch0) * kAggChunk;
-        int64_t end = beg + kAggChunk;
-        if (end > S.a0 + S.na) end = S.a0 + S.na;
-        for (int64_t g = beg + threadIdx.x; g < end; g += blockDim.x) {
-            if (MODE == 0) {
-                if (a.pd[p].rebuild) {   // new neighbour-list reference
-                    const PileDyn &D = a.pd[p];
-                    double *ar = a.aref + 8 * g;
-                    for (int c = 0; c < 3; ++c) ar[c] = a.r[3 * g + c] - D.O[c] - S.h * D.V[c];
-                    for (int c = 0; c < 4; ++c) ar[3 + c] = a.q[4 * g + c];
-                }
-                double M = a.M[g];
-                acc[0] += M;
-                for (int c = 0; c < 3; ++c) {
-                    acc[1 + c] += M * a.r[3 * g + c];
-                    acc[4 + c] += M * a.v[3 * g + c];
-                }
-            } else {
-                for (int c = 0; c < 3; ++c) acc[c] += a.out[18 * g + 12 + c];
-            }
-        }
-    }
-    for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = acc[k];
-    __syncthreads();
-    for (int s = 64; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s)
-            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x < 7) a.chunk_part[ch * kPartialDoubles + threadIdx.x] = sh[threadIdx.x][0];
-}
-
-// One block per pile: thread t adds chunks t, t+128, ... in order, then a fixed
-// tree combines the threads (deterministic for a given pile size).
-template <int MODE>
-__global__ void k_pile_finalize(Arrays a, Sizes z)
-{
-    pdl_enter();
-    const int p = blockIdx.x;
-    if (p >= z.P || !pile_active(a, p)) return;
     const PileStatic &S = a.ps[p];
-    __shared__ double sh[7][128];
     double s[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int64_t ch = S.ch0 + threadIdx.x; ch < S.ch0 + S.nch; ch += blockDim.x)
-        for (int k = 0; k < 7; ++k) s[k] += a.chunk_part[ch * kPartialDoubles + k];
+        for (int k = 0; k < 7; ++k) s[k] += __ldcg(a.chunk_part + ch * kPartialDoubles + k);
+    __syncthreads();   // sh is free again
     for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = s[k];
     __syncthreads();
     for (int o = 64; o > 0; o >>= 1) {
@@ -403,18 +359,70 @@ __global__ void k_pile_finalize(Arrays a, Sizes z)
     }
 }
 
+template <int MODE>
+__global__ void __launch_bounds__(128) k_pile_reduce(Arrays a, Sizes z)
+{
+    pdl_enter();
+    int64_t ch = blockIdx.x;
+    if (ch >= z.CH) return;
+    int p = a.chunk_pile[ch];
+    __shared__ double sh[7][128];
+    __shared__ int last;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    const bool act = pile_active(a, p);
+    if (act) {
+        const PileStatic &S = a.ps[p];
+        int64_t beg = S.a0 + (ch - S.ch0) * kAggChunk;
+        int64_t end = beg + kAggChunk;
+        if (end > S.a0 + S.na) end = S.a0 + S.na;
+        for (int64_t g = beg + threadIdx.x; g < end; g += blockDim.x) {
+            if (MODE == 0) {
+                if (a.pd[p].rebuild) {   // new neighbour-list reference
+                    const PileDyn &D = a.pd[p];
+                    double *ar = a.aref + 8 * g;
+                    for (int c = 0; c < 3; ++c) ar[c] = a.r[3 * g + c] - D.O[c] - S.h * D.V[c];
+                    for (int c = 0; c < 4; ++c) ar[3 + c] = a.q[4 * g + c];
+                }
+                double M = a.M[g];
+                acc[0] += M;
+                for (int c = 0; c < 3; ++c) {
+                    acc[1 + c] += M * a.r[3 * g + c];
+                    acc[4 + c] += M * a.v[3 * g + c];
+                }
+            } else {
+                for (int c = 0; c < 3; ++c) acc[c] += a.out[18 * g + 12 + c];
+            }
+        }
+    }
+    for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = 64; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 7; ++k) a.chunk_part[ch * kPartialDoubles + k] = sh[k][0];
+        __threadfence();   // the sums are visible before this block is counted
+        last = atomicAdd(a.pile_arrive + p, 1) == (int)a.ps[p].nch - 1;
+        if (last) a.pile_arrive[p] = 0;
+    }
+    __syncthreads();
+    if (!last || !act) return;
+    __threadfence();
+    pile_finalize_block<MODE>(a, p, sh);
+}
+
 void launch_pile_begin(const Arrays &a, const Sizes &z, cudaStream_t st)
 {
     if (z.CH == 0) return;
-    launch_pdl(k_pile_partials<0>, (unsigned)z.CH, 128, 0, st, a, z);
-    launch_pdl(k_pile_finalize<0>, (unsigned)z.P, 128, 0, st, a, z);
+    launch_pdl(k_pile_reduce<0>, (unsigned)z.CH, 128, 0, st, a, z);
 }
 
 void launch_pile_end(const Arrays &a, const Sizes &z, cudaStream_t st)
 {
     if (z.CH == 0) return;
-    launch_pdl(k_pile_partials<1>, (unsigned)z.CH, 128, 0, st, a, z);
-    launch_pdl(k_pile_finalize<1>, (unsigned)z.P, 128, 0, st, a, z);
+    launch_pdl(k_pile_reduce<1>, (unsigned)z.CH, 128, 0, st, a, z);
 }
 
 // ---------------------------------------------------------------- expansion

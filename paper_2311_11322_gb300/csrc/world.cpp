@@ -205,6 +205,7 @@ void build_fields(dem_world *w)
     add((void **)&a.chunk_part, C_CHUNK, 8 * kPartialDoubles, false);
     add((void **)&a.chunk_pile, C_CHUNK, 4, false);
     add((void **)&a.bulk_part, C_CHUNK, 8 * 32, false);
+    add((void **)&a.pile_arrive, C_PILE, 4, false);
     add((void **)&a.watch, C_PILE, sizeof(PileWatch), true);
     add((void **)&a.ps, C_PILE, sizeof(PileStatic), false);
     add((void **)&a.pd, C_PILE, sizeof(PileDyn), true);
@@ -531,6 +532,8 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     }
     // the persistent gravity grid's work counter (it resets itself after each launch)
     CU(cudaMemsetAsync(w->A.gcounter, 0, sizeof(int32_t), w->stream));
+    // arrival counters of the pile reductions (each reduction leaves them at zero)
+    if (w->Z.P > 0) CU(cudaMemsetAsync(w->A.pile_arrive, 0, sizeof(int32_t) * (size_t)w->Z.P, w->stream));
     launch_fill_ids(w->A, w->Z, w->stream);
     // a new layout leaves the transient sort and hit lists undefined
     launch_force_rebuild(w->A, w->Z, -1, w->stream);
@@ -1640,7 +1643,7 @@ size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contact
     size_t bytes = sph * (size_t)n_spheres + sphk * (size_t)n_spheres * (size_t)max_contacts +
                    agg * (size_t)n_agg + 8 * (size_t)cells + 4 * (size_t)(cells / kScanTile + 1) +
                    (size_t)(n_agg / kAggChunk + 1) * (8 * kPartialDoubles + 4 + 8 * 32) +
-                   sizeof(PileStatic) + sizeof(PileDyn) + sizeof(PileWatch) + 16 + 16 * (size_t)(n_spheres / 64 + 1);
+                   sizeof(PileStatic) + sizeof(PileDyn) + sizeof(PileWatch) + 20 + 16 * (size_t)(n_spheres / 64 + 1);
     // direct-sum gravity: partial sums of the 512-sphere tile pairs (2 T rows of
     // n spheres) and the work items (T (T + 1) / 2)
     // (up to 8,192 spheres the mixed path may use 128-sphere tiles: count those)

@@ -96,7 +96,7 @@ def test_watch_latches_where_a_host_scan_finds_the_growth(dem):
         before = w.bulk(pid)
         k0 = w.graph_kernel_count()
         w.watch(pid, growth, every)
-        assert w.graph_kernel_count() == k0 + 2
+        assert w.graph_kernel_count() == k0 + 1
         res = w.watch_result(pid)
         assert res["armed"] and res["fired_step"] is None
         for k in before:
