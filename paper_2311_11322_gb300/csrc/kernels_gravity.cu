@@ -455,6 +455,12 @@ __global__ void __launch_bounds__(BS) k_gravity64(Arrays a, Sizes z)
 
 // ---------------------------------------------------------------- symmetric form
 constexpr int kSymBS = 128, kSymIB = 4, kSymTile = kSymBS * kSymIB;   // 512 spheres per tile
+// shape of the mixed path's 512-sphere tiles: warps per block x i-spheres per lane
+#ifndef DEM_SYM_WPB
+#define DEM_SYM_WPB 4
+#endif
+constexpr int kBigWPB = DEM_SYM_WPB, kBigIB = 512 / (32 * DEM_SYM_WPB);
+static_assert(32 * kBigWPB * kBigIB == kSymTile, "512-sphere tiles");
 // launch bounds of the symmetric kernel (optionally with a minimum number of
 // resident blocks per SM, which caps its registers)
 #ifdef DEM_GSYM_MINB
@@ -470,16 +476,16 @@ __device__ __forceinline__ int64_t sym_slot(const Arrays &a, int p, int64_t ns, 
     return a.gpart_base[p] + row * ns + i;
 }
 
-// One step of the ring: the lane's 4 i-spheres against the j-sphere it holds.
-template <bool MASK>
-__device__ __forceinline__ void sym_pairs(const float4 &pj, int aj, const float4 (&xi)[kSymIB],
-                                          const float (&nm)[kSymIB], const int (&ai)[kSymIB],
-                                          float (&ax)[kSymIB], float (&ay)[kSymIB],
-                                          float (&az)[kSymIB], float &fx, float &fy, float &fz,
+// One step of the ring: the lane's IB i-spheres against the j-sphere it holds.
+template <bool MASK, int IB>
+__device__ __forceinline__ void sym_pairs(const float4 &pj, int aj, const float4 (&xi)[IB],
+                                          const float (&nm)[IB], const int (&ai)[IB],
+                                          float (&ax)[IB], float (&ay)[IB],
+                                          float (&az)[IB], float &fx, float &fy, float &fz,
                                           float eps2)
 {
 #pragma unroll
-    for (int k = 0; k < kSymIB; ++k) {
+    for (int k = 0; k < IB; ++k) {
         const float dx = pj.x - xi[k].x, dy = pj.y - xi[k].y, dz = pj.z - xi[k].z;
         const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
         const float inv = rsqrtf(r2);
@@ -497,17 +503,17 @@ __device__ __forceinline__ void sym_pairs(const float4 &pj, int aj, const float4
 
 // 32 ring steps over one chunk of 32 j-spheres (one per lane at the start,
 // back in its lane at the end with the sum over the warp's 128 i-spheres).
-template <bool MASK>
-__device__ __forceinline__ float4 sym_ring(float4 pj, int aj, const float4 (&xi)[kSymIB],
-                                           const float (&nm)[kSymIB], const int (&ai)[kSymIB],
-                                           float (&ax)[kSymIB], float (&ay)[kSymIB],
-                                           float (&az)[kSymIB], float eps2)
+template <bool MASK, int IB>
+__device__ __forceinline__ float4 sym_ring(float4 pj, int aj, const float4 (&xi)[IB],
+                                           const float (&nm)[IB], const int (&ai)[IB],
+                                           float (&ax)[IB], float (&ay)[IB],
+                                           float (&az)[IB], float eps2)
 {
     const int src = (threadIdx.x + 1) & 31;
     float fx = 0.f, fy = 0.f, fz = 0.f;
 #pragma unroll 4
     for (int s = 0; s < 32; ++s) {
-        sym_pairs<MASK>(pj, aj, xi, nm, ai, ax, ay, az, fx, fy, fz, eps2);
+        sym_pairs<MASK, IB>(pj, aj, xi, nm, ai, ax, ay, az, fx, fy, fz, eps2);
         pj.x = __shfl_sync(0xffffffffu, pj.x, src);
         pj.y = __shfl_sync(0xffffffffu, pj.y, src);
         pj.z = __shfl_sync(0xffffffffu, pj.z, src);
@@ -531,10 +537,11 @@ constexpr int kRingUnroll = DEM_RING_UNROLL;
 // both halves, so one f32x2 instruction evaluates the same step of two pairs.
 // A chunk is 64 j-spheres (j and j + 32 in lane l).  The i-sums are kept per
 // half and added at the end of the item; the j-sums travel with their j.
+template <int IB>
 __device__ __forceinline__ void sym_ring2(const float4 &pa, const float4 &pb,
-                                          const f2_t (&xx)[kSymIB], const f2_t (&xy)[kSymIB],
-                                          const f2_t (&xz)[kSymIB], const f2_t (&nm2)[kSymIB],
-                                          f2_t (&qx)[kSymIB], f2_t (&qy)[kSymIB], f2_t (&qz)[kSymIB],
+                                          const f2_t (&xx)[IB], const f2_t (&xy)[IB],
+                                          const f2_t (&xz)[IB], const f2_t (&nm2)[IB],
+                                          f2_t (&qx)[IB], f2_t (&qy)[IB], f2_t (&qz)[IB],
                                           f2_t e2, float4 &fa, float4 &fb)
 {
     const int src = (threadIdx.x + 1) & 31;
@@ -544,7 +551,7 @@ __device__ __forceinline__ void sym_ring2(const float4 &pa, const float4 &pb,
 #pragma unroll kRingUnroll
     for (int s = 0; s < 32; ++s) {
 #pragma unroll
-        for (int k = 0; k < kSymIB; ++k) {
+        for (int k = 0; k < IB; ++k) {
             const f2_t dx = f2_sub(jx, xx[k]), dy = f2_sub(jy, xy[k]), dz = f2_sub(jz, xz[k]);
             const f2_t r2 = f2_fma(dz, dz, f2_fma(dy, dy, f2_fma(dx, dx, e2)));
             float ra, rb;
@@ -578,13 +585,13 @@ __device__ __forceinline__ void sym_ring2(const float4 &pa, const float4 &pb,
 // Work item (pile, tile a, tile b): the symmetric pass for a < b, the
 // one-sided pass over the tile itself for a == b.  sp/sag: tile b staged in
 // shared memory; sj: per-warp j-sums.  WPB warps per block, each with
-// 32 x kSymIB i-spheres: tiles of 128 WPB spheres (512 for the large-pile
+// 32 x IB i-spheres: tiles of 32 WPB IB spheres (512 for the large-pile
 // form, 128 for small piles whose 512-sphere tile pairs would not fill the GPU).
-template <int WPB>
+template <int WPB, int IB>
 __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, float4 *sp, int *sag,
                                                 float4 *sj)
 {
-    constexpr int kSymBS = 32 * WPB, kSymTile = kSymBS * kSymIB;
+    constexpr int kSymBS = 32 * WPB, kSymTile = kSymBS * IB;
     const int p = it.x;
     if (a.enabled[p] == 0 || a.pd[p].failed) return;
     const PileStatic &S = a.ps[p];
@@ -602,13 +609,13 @@ __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, 
         sp[m] = j < ns ? a.gpos32[s0 + j] : make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.f);
         sag[m] = j < ns ? a.sph_agg[s0 + j] : -1;
     }
-    float4 xi[kSymIB];
-    float nm[kSymIB];
-    int ai[kSymIB];
-    float ax[kSymIB], ay[kSymIB], az[kSymIB];
-    const int i0 = ta * kSymTile + w * (32 * kSymIB) + l;
+    float4 xi[IB];
+    float nm[IB];
+    int ai[IB];
+    float ax[IB], ay[IB], az[IB];
+    const int i0 = ta * kSymTile + w * (32 * IB) + l;
 #pragma unroll
-    for (int k = 0; k < kSymIB; ++k) {
+    for (int k = 0; k < IB; ++k) {
         const int i = i0 + 32 * k;
         const bool ok = i < ns;
         xi[k] = ok ? a.gpos32[s0 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -624,7 +631,7 @@ __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, 
             const float4 pj = sp[jj];
             const int aj = sag[jj];
 #pragma unroll
-            for (int k = 0; k < kSymIB; ++k) {
+            for (int k = 0; k < IB; ++k) {
                 const float dx = pj.x - xi[k].x, dy = pj.y - xi[k].y, dz = pj.z - xi[k].z;
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
                 const float inv = rsqrtf(r2);
@@ -639,13 +646,13 @@ __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, 
         for (int c = 0; c * 32 < nj; ++c) {
             const float4 pj = sp[c * 32 + l];
             const int aj = sag[c * 32 + l];
-            sj[w * kSymTile + c * 32 + l] = sym_ring<true>(pj, aj, xi, nm, ai, ax, ay, az, eps2);
+            sj[w * kSymTile + c * 32 + l] = sym_ring<true, IB>(pj, aj, xi, nm, ai, ax, ay, az, eps2);
         }
     } else {
-        f2_t xx[kSymIB], xy[kSymIB], xz[kSymIB], nm2[kSymIB], qx[kSymIB], qy[kSymIB], qz[kSymIB];
+        f2_t xx[IB], xy[IB], xz[IB], nm2[IB], qx[IB], qy[IB], qz[IB];
         const f2_t zero2 = f2_pack(0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < kSymIB; ++k) {
+        for (int k = 0; k < IB; ++k) {
             xx[k] = f2_pack(xi[k].x, xi[k].x);
             xy[k] = f2_pack(xi[k].y, xi[k].y);
             xz[k] = f2_pack(xi[k].z, xi[k].z);
@@ -655,12 +662,12 @@ __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, 
         const f2_t e2 = f2_pack(eps2, eps2);
         for (int c = 0; c * 64 < nj; ++c) {
             float4 fa, fb;
-            sym_ring2(sp[c * 64 + l], sp[c * 64 + 32 + l], xx, xy, xz, nm2, qx, qy, qz, e2, fa, fb);
+            sym_ring2<IB>(sp[c * 64 + l], sp[c * 64 + 32 + l], xx, xy, xz, nm2, qx, qy, qz, e2, fa, fb);
             sj[w * kSymTile + c * 64 + l] = fa;
             sj[w * kSymTile + c * 64 + 32 + l] = fb;
         }
 #pragma unroll
-        for (int k = 0; k < kSymIB; ++k) {
+        for (int k = 0; k < IB; ++k) {
             float lo, hi;
             f2_unpack(qx[k], lo, hi);
             ax[k] = lo + hi;
@@ -685,7 +692,7 @@ __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, 
         }
     }
 #pragma unroll
-    for (int k = 0; k < kSymIB; ++k) {
+    for (int k = 0; k < IB; ++k) {
         const int i = i0 + 32 * k;
         if (i >= ns) continue;
         if (T == 1) {
@@ -697,11 +704,11 @@ __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, 
     }
 }
 
-template <int WPB>
+template <int WPB, int IB>
 __global__ void DEM_GSYM_BOUNDS k_gravity32s(Arrays a, Sizes z)
 {
     pdl_enter();
-    constexpr int kTile = 32 * WPB * kSymIB;
+    constexpr int kTile = 32 * WPB * IB;
     __shared__ float4 sp[kTile];
     __shared__ int sag[kTile];
     __shared__ float4 sj[WPB * kTile];
@@ -712,7 +719,7 @@ __global__ void DEM_GSYM_BOUNDS k_gravity32s(Arrays a, Sizes z)
         __syncthreads();
         const int item = next;
         if (item >= z.GI) return;
-        gravity32s_item<WPB>(a, a.gitems[item], sp, sag, sj);
+        gravity32s_item<WPB, IB>(a, a.gitems[item], sp, sag, sj);
     }
 }
 
@@ -977,8 +984,8 @@ int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym, int
             cudaFuncSetAttribute(k_gravity64s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSym64Smem);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity64s, kSymBS, kSym64Smem);
         } else {
-            if (tile == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s<1>, 32, 0);
-            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s<4>, kSymBS, 0);
+            if (tile == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s<1, 4>, 32, 0);
+            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s<kBigWPB, kBigIB>, 32 * kBigWPB, 0);
         }
         return n;
     }
@@ -997,8 +1004,8 @@ void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int i
             launch_pdl(k_gravity64s, (unsigned)nb, kSymBS, kSym64Smem, st, a, z);
             if (z.GP > 0) launch_pdl(k_grav_combine_sym64, (unsigned)((z.N + 255) / 256), 256, 0, st, a, z);
         } else {
-            if (z.gtile == 128) launch_pdl(k_gravity32s<1>, (unsigned)nb, 32, 0, st, a, z);
-            else launch_pdl(k_gravity32s<4>, (unsigned)nb, kSymBS, 0, st, a, z);
+            if (z.gtile == 128) launch_pdl(k_gravity32s<1, 4>, (unsigned)nb, 32, 0, st, a, z);
+            else launch_pdl(k_gravity32s<kBigWPB, kBigIB>, (unsigned)nb, 32 * kBigWPB, 0, st, a, z);
             if (z.GP > 0) launch_pdl(k_grav_combine_sym, (unsigned)((z.N + 255) / 256), 256, 0, st, a, z);
         }
         return;
