@@ -199,6 +199,9 @@ void launch_fill_ids(const Arrays &a, const Sizes &z, cudaStream_t st);
 // order: highest multipole rank of accepted cells (2 or 4)
 void launch_tree_gravity(const Arrays &a, const Sizes &z, int max_depth, int order, cudaStream_t st);
 void launch_force_rebuild(const Arrays &a, const Sizes &z, int slot, cudaStream_t st);
+// programmatic dependent launch for the launches that follow on this host
+// thread: on for worlds of at most kPdlMaxSpheres spheres (launch.cuh)
+void set_launch_pdl(int64_t n_spheres);
 // bulk record of piles into watch.now (mode 0: every pile, or only slot
 // `only` when >= 0; mode 1: the watch evaluation inside the step graph, armed
 // piles whose step is due)

@@ -535,6 +535,8 @@ __global__ void k_force_rebuild(Arrays a, Sizes z, int slot)
     a.pd[p].rebuild = 1;
 }
 
+void set_launch_pdl(int64_t n_spheres) { tl_pdl = n_spheres <= kPdlMaxSpheres; }
+
 void launch_force_rebuild(const Arrays &a, const Sizes &z, int slot, cudaStream_t st)
 {
     if (z.P == 0) return;

@@ -556,6 +556,7 @@ void enqueue_watch(dem_world *w)
 
 void enqueue_phase(dem_world *w, int ph)
 {
+    set_launch_pdl(w->Z.N);
     const Arrays &a = w->A;
     const Sizes &z = w->Z;
     bool d = w->precision == DEM_FP64;
