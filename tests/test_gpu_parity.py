@@ -500,6 +500,23 @@ def test_tree_gravity_error_bound(dem):
     assert med[4, 0.5] / med[4, 0.3] > med[2, 0.5] / med[2, 0.3]
 
 
+def test_tree_gravity_against_oracle(dem, oracle):
+    """The hexadecapole tree against the oracle's direct sum (same positions:
+    a cloud at rest, whose first step evaluates gravity where it was built):
+    per-sphere relative errors within the tree's bounds for theta 0.5."""
+    ic, p = W.config2(2, n_spheres=6000, ball=2000.0 * 0.06 ** (1 / 3))
+    agg = oracle.build_aggregates(ic.counts, ic.pos, ic.radius, ic.density)
+    ref = oracle.gravity(ic.pos, agg["m"], agg["agg_of"], p.G, p.eps, exclude_same_agg=True)
+    fg, flags, _ = _fg(dem, ic, p, 0.5, order=4)
+    assert not flags & dem.DEM_FLAG_TREE
+    e = np.linalg.norm(fg - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    _, p50, p99 = TREE_BOUNDS[4][1]
+    assert np.median(e) < p50 and np.quantile(e, 0.99) < p99, (np.median(e), np.quantile(e, 0.99))
+    direct, _, _ = _fg(dem, ic, p)
+    ed = np.linalg.norm(direct - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    assert ed.max() < 1e-5          # the direct sum itself: FP32 pair terms only
+
+
 def test_tree_gravity_deterministic_and_batched(dem):
     """Tree gravity is bitwise reproducible and per pile: a pile alone and in a
     batch with others gives the same state."""
