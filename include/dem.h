@@ -243,7 +243,7 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
  * tile-pair form, each pair evaluated once and applied to both spheres, the
  * default in both precisions; 0 = one-sided form shaped by the keys above),
  * "grav_tile" (spheres per tile of the symmetric form in the mixed path:
- * 512, or 128 for worlds whose piles all have at most 8,192 spheres -- more,
+ * 512, or 128 or 256 for worlds whose piles all have at most 8,192 spheres -- more,
  * smaller work items when the 512-sphere tile pairs would not fill the GPU;
  * 0 = choose automatically (128 when the 512-sphere tile pairs of all piles
  * fill less than one wave of the persistent grid), the default; piles above

@@ -190,6 +190,11 @@ cudaError_t contact_setup(bool fp64, int K);
 // sym: symmetric tile-pair form (items are (pile, tile a, tile b), gnchunk =
 // tiles per pile); tiles of 512 spheres, or of 128 (mixed path, small piles)
 constexpr int kGravSymTile = 512, kGravSymTileSmall = 128;
+// largest pile (spheres) of a world that may use tiles smaller than 512
+#ifndef DEM_SMALL_TILE_MAX
+#define DEM_SMALL_TILE_MAX 8192
+#endif
+constexpr int64_t kSmallTileMaxN = DEM_SMALL_TILE_MAX;
 void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int ib, bool pack,
                     bool sym, cudaStream_t st);
 int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym, int tile);

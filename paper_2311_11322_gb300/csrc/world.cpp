@@ -286,7 +286,7 @@ int sym_tile(dem_world *w)
         items += T * (T + 1) / 2;
         nmax = std::max(nmax, q.ns);
     }
-    if (nmax == 0 || nmax > 8192) return kGravSymTile;
+    if (nmax == 0 || nmax > kSmallTileMaxN) return kGravSymTile;
     if (w->grav_tile) return w->grav_tile;
     if (w->sm_count == 0) {
         int dev = 0;
@@ -1455,7 +1455,8 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
         w->grav_sym = value != 0.0;
     } else if (k == "grav_tile") {
         const int t = (int)value;
-        if (t != 0 && t != 128 && t != 512) return fail(w, DEM_ERR_ARG, "grav_tile must be 0, 128 or 512");
+        if (t != 0 && t != 128 && t != 256 && t != 512)
+            return fail(w, DEM_ERR_ARG, "grav_tile must be 0, 128, 256 or 512");
         w->grav_tile = t;
     } else if (k == "grav_theta") {
         if (!(value >= 0.0) || !(value < 1.0)) return fail(w, DEM_ERR_ARG, "grav_theta must be in [0, 1)");
@@ -1648,7 +1649,7 @@ size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contact
     // direct-sum gravity: partial sums of the 512-sphere tile pairs (2 T rows of
     // n spheres) and the work items (T (T + 1) / 2)
     // (up to 8,192 spheres the mixed path may use 128-sphere tiles: count those)
-    const int64_t tile = (!d && n_spheres <= 8192) ? kGravSymTileSmall : kGravSymTile;
+    const int64_t tile = (!d && n_spheres <= kSmallTileMaxN) ? kGravSymTileSmall : kGravSymTile;
     const int64_t T = (n_spheres + tile - 1) / tile;
     if (T > 1) bytes += (size_t)(2 * T) * (size_t)n_spheres * (d ? 32 : 16);
     bytes += 16 * (size_t)(T * (T + 1) / 2);
