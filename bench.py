@@ -73,11 +73,12 @@ def parse():
     ap.add_argument("--no-e2-collapse", action="store_true")
     ap.add_argument("--no-tree", action="store_true")
     ap.add_argument("--no-analysis", action="store_true")
-    ap.add_argument("--part", default="all", choices=["all", "contact", "e2", "tree", "analysis"],
+    ap.add_argument("--part", default="all", choices=["all", "contact", "e2", "tree", "analysis", "analysis-sweep"],
                     help="contact: only the contact-pass roofline on the 1M-sphere lattice; "
                          "e2: only the paper's 2e4-sphere profiling collapse; "
                          "tree: only tree vs direct gravity; "
-                         "analysis: only the spin-up and encounter runs with device-side watches")
+                         "analysis: only the spin-up and encounter runs with device-side watches; "
+                         "analysis-sweep: those runs for six grain shapes at 2,000 spheres (not part of all)")
     ap.add_argument("--contact-n", type=int, default=1_048_576)
     return ap.parse_args()
 
@@ -406,6 +407,66 @@ def run_analysis(dem, W, n_agg=250, settle=150_000, omega_target=1.5, ramp_pcrit
     return out
 
 
+SWEEP_SHAPES = ("single", "dumbbell", "tetra", "diamond", "rod4", "cube8")
+
+
+def run_analysis_sweep(dem, W, n_spheres=2000, settle=150_000, omega_target=1.5, ramp_pcrit=2.0,
+                       max_steps=900_000, chunk=20_000):
+    """The spin-up and encounter analyses (Sec. 4.1, 4.2) over grain shapes at a
+    fixed sphere count: one progenitor per shape (a lattice pile of ~n_spheres
+    spheres), all settled together in one world, then the 2 x shapes runs
+    stepped together in a second world, each pile with its own device watch."""
+    from paper_2311_11322_gb300 import analysis
+    shp = {}
+    with dem.World() as w:
+        ids = {}
+        for k, sh in enumerate(SWEEP_SHAPES):
+            rng = np.random.default_rng(100 + k)
+            n_agg = max(1, n_spheres // W.SHAPE_SIZE[sh])
+            ic = W.lattice_pile(rng, n_agg, shapes=(sh,))
+            p = W.settled_params(ic, 1.0, max_contacts=24)
+            ids[sh] = (w.add_pile(ic, p), p)
+        t0 = time.perf_counter()
+        done = 0
+        while done < settle:
+            w.step(min(chunk, settle - done))
+            done += min(chunk, settle - done)
+        w.sync()
+        t_settle = time.perf_counter() - t0
+        for sh, (pid, p) in ids.items():
+            shp[sh] = {"ic": w.ic_of(pid), "p": p, "bulk": w.bulk(pid)}
+    with dem.World() as w:
+        runs = {}
+        for sh, d in shp.items():
+            b = d["bulk"]
+            ps = analysis.spinup_params(d["p"], d["ic"], omega_target * 2 * math.pi / b["p_crit"],
+                                        int(ramp_pcrit * b["p_crit"] / d["p"].dt))
+            pe, _ = analysis.encounter_params(d["p"], d["ic"])
+            a, e = w.add_pile(d["ic"], ps), w.add_pile(d["ic"], pe)
+            w.watch(a, 0.05, 10)
+            w.watch(e, 0.005, 10)
+            runs[sh] = (a, e)
+        live = [x for ab in runs.values() for x in ab]
+        taken = 0
+        t0 = time.perf_counter()
+        while live and taken < max_steps:
+            w.step(chunk, piles=live)
+            taken += chunk
+            live = [x for x in live if w.watch_result(x)["fired_step"] is None]
+        w.sync()
+        t_runs = time.perf_counter() - t0
+        out = {"n_spheres_target": n_spheres, "settle_steps": settle, "settle_s": t_settle, "runs_s": t_runs,
+               "spin_ramp": f"{omega_target} x nominal critical spin over {ramp_pcrit} critical periods",
+               "shapes": {}}
+        for sh, (a, e) in runs.items():
+            ra, re_ = w.watch_result(a), w.watch_result(e)
+            out["shapes"][sh] = {"n_spheres": int(shp[sh]["ic"].n_sph), "n_grains": int(shp[sh]["ic"].n_agg),
+                                 "settled_density": shp[sh]["bulk"]["density"],
+                                 "critical_spin_ratio": analysis.critical_spin_ratio(ra),
+                                 "disruption_ratio": analysis.disruption_ratio(re_)}
+    return out
+
+
 def run_batched(dem, W, steps=5, n_piles=256):
     """256 independent piles of tetrahedra (sizes lognormal in [500, 20000]):
     all stepped by one graph launch per step after autotuning, against looping
@@ -704,6 +765,16 @@ def run_analysis_only(args):
     print(json.dumps({"part": "analysis", "analysis": run_analysis(dem, W)}), flush=True)
 
 
+def run_analysis_sweep_only(args):
+    import torch
+    from paper_2311_11322_gb300 import dem
+    from paper_2311_11322_gb300 import workloads as W
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    print(json.dumps({"part": "analysis-sweep", "analysis_sweep": run_analysis_sweep(dem, W)}), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
@@ -716,5 +787,7 @@ if __name__ == "__main__":
         run_tree_only(a)
     elif a.part == "analysis":
         run_analysis_only(a)
+    elif a.part == "analysis-sweep":
+        run_analysis_sweep_only(a)
     else:
         run_ours(a)
