@@ -885,6 +885,10 @@ __global__ void k_grav_combine_sym64(Arrays a, Sizes z)
     a.fg[i] = make_dbl4(gm * sx, gm * sy, gm * sz, 0.0);
 }
 
+#ifndef DEM_COMBINE_UNROLL
+#define DEM_COMBINE_UNROLL 8
+#endif
+constexpr int kCombineUnroll = DEM_COMBINE_UNROLL;
 // Sphere x of tile t: its i-sums of items (t, b), b >= t, then its j-sums of
 // items (a, t), a < t, in that fixed order, as float-float sums (FFSum).
 __global__ void k_grav_combine_sym(Arrays a, Sizes z)
@@ -901,12 +905,15 @@ __global__ void k_grav_combine_sym(Arrays a, Sizes z)
     const int t = (int)(il / z.gtile);
     const float4 *gp = (const float4 *)a.gpart;
     FFSum sx, sy, sz;
+    // unrolled so that several rows' loads are in flight (the sums stay in order)
+#pragma unroll kCombineUnroll
     for (int b = t; b < T; ++b) {
-        const float4 v = gp[sym_slot(a, p, S.ns, b, il)];
+        const float4 v = __ldcs(gp + sym_slot(a, p, S.ns, b, il));
         sx.add(v.x); sy.add(v.y); sz.add(v.z);
     }
+#pragma unroll kCombineUnroll
     for (int r = 0; r < t; ++r) {
-        const float4 v = gp[sym_slot(a, p, S.ns, T + r, il)];
+        const float4 v = __ldcs(gp + sym_slot(a, p, S.ns, T + r, il));
         sx.add(v.x); sy.add(v.y); sz.add(v.z);
     }
     const double gm = S.G * a.m64[i];
