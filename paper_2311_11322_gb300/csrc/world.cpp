@@ -56,6 +56,7 @@ struct dem_world {
     Sizes Z{};
     int64_t cap[C_NCLS] = {0};
     std::vector<Field> fields;
+    void *slab = nullptr;             // every field's device memory, one allocation
     size_t held = 0;
     // graph
     cudaGraphExec_t exec = nullptr;
@@ -398,9 +399,9 @@ dem_status relayout(dem_world *w, const std::vector<PileHost> &newp, const GravP
             grow = true;
         }
     }
-    // bytes after the change
+    // bytes after the change (each field 256-byte aligned in one slab)
     size_t total = 0;
-    for (auto &f : w->fields) total += f.el * (size_t)ncap[f.cls];
+    for (auto &f : w->fields) total += (f.el * (size_t)ncap[f.cls] + 255) / 256 * 256;
     if (w->budget && total > w->budget)
         return fail(w, DEM_ERR_OOM, "HBM budget exceeded: need %zu bytes, budget %zu", total, w->budget);
     // old and new offsets of the surviving piles
@@ -421,14 +422,14 @@ dem_status relayout(dem_world *w, const std::vector<PileHost> &newp, const GravP
         // only the transient classes may need new capacity (none grew)
         return DEM_OK;
     }
+    // one slab for every field (offsets 256-byte aligned): one allocator call per layout
     std::vector<void *> fresh(w->fields.size(), nullptr);
-    for (size_t f = 0; f < w->fields.size(); ++f) {
-        fresh[f] = dev_alloc(w, w->fields[f].el * (size_t)ncap[w->fields[f].cls]);
-        if (!fresh[f]) {
-            for (size_t g = 0; g < f; ++g) dev_free(w, fresh[g]);
-            return fail(w, DEM_ERR_OOM, "device allocation of %zu bytes failed",
-                        w->fields[f].el * (size_t)ncap[w->fields[f].cls]);
-        }
+    const size_t slab_bytes = total;
+    char *slab = (char *)dev_alloc(w, slab_bytes);
+    if (!slab) return fail(w, DEM_ERR_OOM, "device allocation of %zu bytes failed", slab_bytes);
+    for (size_t f = 0, o = 0; f < w->fields.size(); ++f) {
+        fresh[f] = slab + o;
+        o += (w->fields[f].el * (size_t)ncap[w->fields[f].cls] + 255) / 256 * 256;
     }
     for (size_t f = 0; f < w->fields.size(); ++f) {
         const Field &fd = w->fields[f];
@@ -445,12 +446,11 @@ dem_status relayout(dem_world *w, const std::vector<PileHost> &newp, const GravP
         }
     }
     CU(cudaStreamSynchronize(w->stream));
-    for (size_t f = 0; f < w->fields.size(); ++f) {
-        dev_free(w, *w->fields[f].ptr);
-        *w->fields[f].ptr = fresh[f];
-    }
+    dev_free(w, w->slab);
+    w->slab = slab;
+    for (size_t f = 0; f < w->fields.size(); ++f) *w->fields[f].ptr = fresh[f];
     for (int c = 0; c < C_NCLS; ++c) w->cap[c] = ncap[c];
-    w->held = total;
+    w->held = slab_bytes;
     return DEM_OK;
 }
 
@@ -1653,6 +1653,7 @@ size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contact
     const int64_t T = (n_spheres + tile - 1) / tile;
     if (T > 1) bytes += (size_t)(2 * T) * (size_t)n_spheres * (d ? 32 : 16);
     bytes += 16 * (size_t)(T * (T + 1) / 2);
+    bytes += 256 * 80;   // each of the world's arrays starts on a 256-byte boundary of one slab
     return bytes;
 }
 
@@ -1669,7 +1670,7 @@ void dem_destroy(dem_world *w)
     if (!w) return;
     cudaStreamSynchronize(w->stream);
     if (w->exec) cudaGraphExecDestroy(w->exec);
-    for (auto &f : w->fields) dev_free(w, *f.ptr);
+    dev_free(w, w->slab);
     if (w->h_dyn) cudaFreeHost(w->h_dyn);
     if (w->ev_flags) cudaEventDestroy(w->ev_flags);
     for (int k = 0; k < 2; ++k) {
