@@ -154,6 +154,24 @@ def test_watch_survives_relayout_and_batching(dem):
         assert w.watch_result(ib)["armed"]
 
 
+def test_bulk_of_a_single_sphere(dem):
+    """Degenerate pile, one free sphere: its own equal-moment ellipsoid (axes =
+    radius, bulk density = its density, P_crit = sqrt(3 pi / (G rho))), at rest
+    (infinite period), no planet."""
+    ic = W.PileIC(counts=np.array([1], np.int32), pos=np.array([[3.0, -1.0, 2.0]]),
+                  radius=np.array([2.5]), density=np.array([1800.0]))
+    p = W.Params(dt=0.01, kn=1e3, kt=2e3 / 7, eps=0.1, precision=W.PRECISION_MIXED)
+    with dem.World() as w:
+        pid = w.add_pile(ic, p)
+        b = w.bulk(pid)
+    assert np.allclose(b["axes"], 2.5, rtol=1e-12)
+    assert b["radius"] == pytest.approx(2.5, rel=1e-12)
+    assert b["density"] == pytest.approx(1800.0, rel=1e-12)
+    assert b["p_crit"] == pytest.approx(math.sqrt(3 * math.pi / (p.G * 1800.0)), rel=1e-12)
+    assert math.isinf(b["period"]) and b["planet_dist"] == 0.0
+    assert np.allclose(b["com"], [3.0, -1.0, 2.0], atol=1e-12)
+
+
 def test_watch_rejects_bad_arguments(dem):
     ic, p = W.random_cluster(4, n_agg=10, box=4.0, precision=W.PRECISION_MIXED)
     with dem.World() as w:
