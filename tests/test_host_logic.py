@@ -215,3 +215,68 @@ def test_e2_collapse_populations():
         assert abs(d.min() - 2.0) < 1e-12          # touching, never overlapping
         assert abs(o.mean(axis=0)).max() < 1e-12   # offsets about the centre
         assert len(o) == W.SHAPE_SIZE[sh]
+
+
+# ---------------------------------------------------------------- analysis runs (host side)
+class _FakeWatchWorld:
+    """Stands in for a World: the watch latches after a set number of steps."""
+
+    def __init__(self, latch_after, at_arm, at_fire):
+        self.latch_after, self.at_arm, self.at_fire = latch_after, at_arm, at_fire
+        self.steps, self.armed, self.stepped = 0, None, []
+
+    def watch(self, pile, growth, every):
+        self.armed = (pile, growth, every)
+
+    def step(self, n, piles=None):
+        self.steps += n
+        self.stepped.append((n, tuple(piles)))
+
+    def watch_result(self, pile):
+        fired = self.latch_after if self.steps >= self.latch_after else None
+        return {"fired_step": fired, "growth": self.armed[1], "every": self.armed[2], "armed": True,
+                "at_arm": self.at_arm, "at_fire": self.at_fire if fired is not None else None}
+
+
+def test_run_until_growth_polls_the_watch_and_stops():
+    from paper_2311_11322_gb300 import analysis
+    w = _FakeWatchWorld(12_500, {"p_crit": 100.0, "density": 1000.0}, {"period": 123.0, "planet_dist": 5e6})
+    res = analysis.run_until_growth(w, 7, 0.05, every=10, max_steps=100_000, chunk=5_000)
+    assert w.armed == (7, 0.05, 10)
+    assert res["fired_step"] == 12_500 and res["steps_run"] == 15_000
+    assert all(p == (7,) for _, p in w.stepped)
+    assert analysis.critical_spin_ratio(res) == pytest.approx(1.23)
+    # Roche normalisation: d / (1.26 R (rho_M / rho_m)^(1/3))
+    d_roche = 1.26 * W.EARTH_RADIUS * (5514.0 / 1000.0) ** (1 / 3)
+    assert analysis.disruption_ratio(res) == pytest.approx(5e6 / d_roche)
+    never = _FakeWatchWorld(10 ** 9, {"p_crit": 1.0, "density": 1.0}, {})
+    res = analysis.run_until_growth(never, 0, 0.005, max_steps=20_000, chunk=3_000)
+    assert res["fired_step"] is None and res["steps_run"] == 20_000
+    assert analysis.critical_spin_ratio(res) is None and analysis.disruption_ratio(res) is None
+
+
+def test_spinup_and_encounter_parameters():
+    """The spin ramp reaches the target over the stated steps about the axis;
+    the encounter starts the planet on the incoming branch at the requested
+    multiple of the Roche distance with the requested periapsis."""
+    import math
+    from paper_2311_11322_gb300 import analysis
+    rng = np.random.default_rng(2)
+    ic = W.lattice_pile(rng, 60, shapes=("tetra",))
+    p = W.settled_params(ic, 1.0)
+    ps = analysis.spinup_params(p, ic, 2e-3, 4000, axis=(0.0, 3.0, 4.0))
+    assert np.allclose(np.array(ps.spin_inc) * 4000, [0.0, 1.2e-3, 1.6e-3])
+    pe, orb = analysis.encounter_params(p, ic, periapsis_rp=1.2, v_inf_kms=3.0, start_roche=3.0)
+    assert pe.ext_mass == W.EARTH_MASS
+    assert orb["q"] == pytest.approx(1.2 * W.EARTH_RADIUS) and orb["vinf"] == pytest.approx(3e3)
+    m = W.sphere_mass(ic.radius, ic.density)
+    com = (m[:, None] * ic.pos).sum(0) / m.sum()
+    rel = np.array(pe.ext_pos) - com
+    d_roche = 1.26 * W.EARTH_RADIUS * (5514.0 / (2500.0 * 0.6)) ** (1 / 3)
+    assert np.linalg.norm(rel) == pytest.approx(3.0 * d_roche, rel=1e-9)
+    assert np.dot(rel, pe.ext_vel) < 0          # approaching
+    # hyperbolic energy: v^2/2 - mu/r = v_inf^2/2
+    mu = W.G_SI * W.EARTH_MASS
+    e = 0.5 * np.dot(pe.ext_vel, pe.ext_vel) - mu / np.linalg.norm(rel)
+    assert e == pytest.approx(0.5 * 3e3 ** 2, rel=1e-9)
+    assert math.isfinite(analysis.roche_distance(1.0, 2.0, 3.0))
