@@ -533,8 +533,12 @@ __global__ void DEM_TREE_BOUNDS k_tree_force(Arrays a, Sizes z)
     // one warp per block: walks of very different lengths do not hold one
     // another's block resident
     __shared__ int st[kTreeStack];
-    // accepted cells of a round, staged for every lane (ranks above 2 only)
-    __shared__ float4 stage[ORDER > 2 ? 32 * kNodeF4 : 1];
+    // accepted cells of a round (ranks above 2), then the spheres of its
+    // opened leaves, staged for every lane
+    constexpr int kStage = ORDER > 2 ? 32 * kNodeF4 : 128;
+    __shared__ float4 stage[kStage];
+    __shared__ int sagg[kStage];
+    __shared__ int lbase[32], lfirst[32];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
@@ -661,24 +665,41 @@ __global__ void DEM_TREE_BOUNDS k_tree_force(Arrays a, Sizes z)
             }
         }
         if (ORDER > 2) __syncwarp();
-        // opened leaves: lanes load a leaf's spheres side by side, then
-        // every lane adds each of them (passed by shuffles)
-        unsigned lm = __ballot_sync(FULL, leaf);
-        while (lm) {
-            const int b = __ffs(lm) - 1;
-            lm &= lm - 1;
-            const int l0 = __shfl_sync(FULL, lf.x, b), ln = __shfl_sync(FULL, lf.y, b);
-            for (int c0 = 0; c0 < ln; c0 += 32) {
-                const int t = l0 + c0 + lane;
-                const bool ok = c0 + lane < ln;
-                const float4 xq = ok ? tp[t] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const int aq = ok ? tg[t] : -3;
-                const int m = min(32, ln - c0);
-                for (int u = 0; u < m; ++u) {
-                    const float4 xj = make_float4(__shfl_sync(FULL, xq.x, u), __shfl_sync(FULL, xq.y, u),
-                                                  __shfl_sync(FULL, xq.z, u), __shfl_sync(FULL, xq.w, u));
-                    const int aj = __shfl_sync(FULL, aq, u);
-                    if (mine && l0 + c0 + u != ti && aj != ai) {
+        // opened leaves: the spheres of all of them (leaves in lane order,
+        // spheres in leaf order) are staged in shared memory kStage at a
+        // time, one round of loads for the whole round's leaves, then every
+        // lane adds each of them.  A sphere's own aggregate is skipped, and
+        // with it the sphere itself.
+        const int lcnt = leaf ? lf.y : 0;
+        int incl = lcnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        if (total > 0) {
+            lbase[lane] = incl - lcnt;   // first staged position of this lane's leaf
+            lfirst[lane] = lf.x;        // first sphere of the leaf (leaf order)
+            __syncwarp();
+            for (int c0 = 0; c0 < total; c0 += kStage) {
+                const int nb = min(kStage, total - c0);
+                for (int t = lane; t < nb; t += 32) {
+                    // the leaf holding staged position c0 + t: the last lane whose
+                    // first staged position is not after it
+                    const int g = c0 + t;
+                    int lo2 = 0, hi2 = 31;
+                    while (lo2 < hi2) {
+                        const int mid = (lo2 + hi2 + 1) >> 1;
+                        if (lbase[mid] <= g) lo2 = mid; else hi2 = mid - 1;
+                    }
+                    const int idx = lfirst[lo2] + (g - lbase[lo2]);
+                    stage[t] = tp[idx];
+                    sagg[t] = tg[idx];
+                }
+                __syncwarp();
+                for (int u = 0; u < nb; ++u) {
+                    const float4 xj = stage[u];
+                    if (mine && sagg[u] != ai) {
                         const float ex = xj.x - xi.x, ey = xj.y - xi.y, ez = xj.z - xi.z;
                         const float q2 = fmaf(ez, ez, fmaf(ey, ey, fmaf(ex, ex, eps2)));
                         const float iv = rsqrtf(q2);
@@ -688,6 +709,7 @@ __global__ void DEM_TREE_BOUNDS k_tree_force(Arrays a, Sizes z)
                         az = fmaf(ez, sj, az);
                     }
                 }
+                __syncwarp();
             }
         }
     }
