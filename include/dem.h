@@ -243,11 +243,12 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
  * tile-pair form, each pair evaluated once and applied to both spheres, the
  * default in both precisions; 0 = one-sided form shaped by the keys above),
  * "grav_tile" (spheres per tile of the symmetric form in the mixed path:
- * 512, or 128 or 256 for worlds whose piles all have at most 8,192 spheres -- more,
- * smaller work items when the 512-sphere tile pairs would not fill the GPU;
- * 0 = choose automatically (128 when the 512-sphere tile pairs of all piles
- * fill less than one wave of the persistent grid), the default; piles above
- * 8,192 spheres always use 512),
+ * 512, or 128 or 256 for worlds whose piles all have at most 8,192 spheres,
+ * or 64 when they have at most 2,048 -- more, smaller work items when the
+ * 512-sphere tile pairs would not fill the GPU; 0 = choose automatically
+ * (when the 512-sphere tile pairs of all piles fill less than one wave of
+ * the persistent grid: 64 up to 2,048 spheres, else 128), the default;
+ * larger piles always use 512),
  * "grav_theta" (mixed path: > 0 replaces the direct sum by tree gravity with
  * this opening angle, in [0, 1): cells of an octree rebuilt every step with
  * multipoles up to the hexadecapole (Sec. 2.1), leaves of ~4 spheres summed

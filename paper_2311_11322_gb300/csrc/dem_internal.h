@@ -189,7 +189,8 @@ void launch_contact(const Arrays &a, const Sizes &z, bool fp64, int K, cudaStrea
 cudaError_t contact_setup(bool fp64, int K);
 // sym: symmetric tile-pair form (items are (pile, tile a, tile b), gnchunk =
 // tiles per pile); tiles of 512 spheres, or of 128 (mixed path, small piles)
-constexpr int kGravSymTile = 512, kGravSymTileSmall = 128;
+constexpr int kGravSymTile = 512, kGravSymTileSmall = 128, kGravSymTileTiny = 64;
+constexpr int64_t kTinyTileMaxN = 2048;   // largest pile that may use 64-sphere tiles
 // largest pile (spheres) of a world that may use tiles smaller than 512
 #ifndef DEM_SMALL_TILE_MAX
 #define DEM_SMALL_TILE_MAX 8192

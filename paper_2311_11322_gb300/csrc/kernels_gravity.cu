@@ -991,7 +991,8 @@ int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym, int
             cudaFuncSetAttribute(k_gravity64s, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSym64Smem);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity64s, kSymBS, kSym64Smem);
         } else {
-            if (tile == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s<1, 4>, 32, 0);
+            if (tile == 64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s<1, 2>, 32, 0);
+            else if (tile == 128) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s<1, 4>, 32, 0);
             else if (tile == 256) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s<2, 4>, 64, 0);
             else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gravity32s<kBigWPB, kBigIB>, 32 * kBigWPB, 0);
         }
@@ -1012,7 +1013,8 @@ void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int i
             launch_pdl(k_gravity64s, (unsigned)nb, kSymBS, kSym64Smem, st, a, z);
             if (z.GP > 0) launch_pdl(k_grav_combine_sym64, (unsigned)((z.N + 255) / 256), 256, 0, st, a, z);
         } else {
-            if (z.gtile == 128) launch_pdl(k_gravity32s<1, 4>, (unsigned)nb, 32, 0, st, a, z);
+            if (z.gtile == 64) launch_pdl(k_gravity32s<1, 2>, (unsigned)nb, 32, 0, st, a, z);
+            else if (z.gtile == 128) launch_pdl(k_gravity32s<1, 4>, (unsigned)nb, 32, 0, st, a, z);
             else if (z.gtile == 256) launch_pdl(k_gravity32s<2, 4>, (unsigned)nb, 64, 0, st, a, z);
             else launch_pdl(k_gravity32s<kBigWPB, kBigIB>, (unsigned)nb, 32 * kBigWPB, 0, st, a, z);
             if (z.GP > 0) launch_pdl(k_grav_combine_sym, (unsigned)((z.N + 255) / 256), 256, 0, st, a, z);

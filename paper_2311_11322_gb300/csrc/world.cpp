@@ -276,7 +276,9 @@ bool use_sym(const dem_world *w) { return w->grav_sym; }
 // and no pile exceeds 8,192 spheres: then 128-sphere tiles, 16 times the work
 // items for the same pairs (their partial rows, 2 T x N, stay <= 17 MB).
 // Measured per step, 512 -> 128: 1,000 spheres 89 -> 75 us, 5,000 97 -> 91,
-// 8,000 118 -> 108.
+// 8,000 118 -> 108.  Piles of at most 2,048 spheres use 64-sphere tiles
+// (512 -> 128 -> 64: 500 spheres 93 -> 79 -> 68 us, 2,000 101 -> 83 -> 81;
+// at 4,000 the two small tiles are even).
 int sym_tile(dem_world *w)
 {
     if (w->precision != DEM_MIXED) return kGravSymTile;
@@ -288,6 +290,7 @@ int sym_tile(dem_world *w)
         nmax = std::max(nmax, q.ns);
     }
     if (nmax == 0 || nmax > kSmallTileMaxN) return kGravSymTile;
+    if (w->grav_tile == kGravSymTileTiny && nmax > kTinyTileMaxN) return kGravSymTileSmall;
     if (w->grav_tile) return w->grav_tile;
     if (w->sm_count == 0) {
         int dev = 0;
@@ -299,7 +302,8 @@ int sym_tile(dem_world *w)
     }
     const int bps = gravity_blocks_per_sm(false, 128, 4, false, true, kGravSymTile);
     cudaGetLastError();
-    return items < (int64_t)std::max(1, bps) * w->sm_count ? kGravSymTileSmall : kGravSymTile;
+    if (items >= (int64_t)std::max(1, bps) * w->sm_count) return kGravSymTile;
+    return nmax <= kTinyTileMaxN ? kGravSymTileTiny : kGravSymTileSmall;
 }
 
 GravPlan plan_gravity(dem_world *w)
@@ -1455,8 +1459,8 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
         w->grav_sym = value != 0.0;
     } else if (k == "grav_tile") {
         const int t = (int)value;
-        if (t != 0 && t != 128 && t != 256 && t != 512)
-            return fail(w, DEM_ERR_ARG, "grav_tile must be 0, 128, 256 or 512");
+        if (t != 0 && t != 64 && t != 128 && t != 256 && t != 512)
+            return fail(w, DEM_ERR_ARG, "grav_tile must be 0, 64, 128, 256 or 512");
         w->grav_tile = t;
     } else if (k == "grav_theta") {
         if (!(value >= 0.0) || !(value < 1.0)) return fail(w, DEM_ERR_ARG, "grav_theta must be in [0, 1)");
@@ -1648,8 +1652,11 @@ size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contact
                    sizeof(PileStatic) + sizeof(PileDyn) + sizeof(PileWatch) + 20 + 16 * (size_t)(n_spheres / 64 + 1);
     // direct-sum gravity: partial sums of the 512-sphere tile pairs (2 T rows of
     // n spheres) and the work items (T (T + 1) / 2)
-    // (up to 8,192 spheres the mixed path may use 128-sphere tiles: count those)
-    const int64_t tile = (!d && n_spheres <= kSmallTileMaxN) ? kGravSymTileSmall : kGravSymTile;
+    // (up to 8,192 spheres the mixed path may use 128-sphere tiles, up to
+    // 2,048 spheres 64-sphere tiles: count those)
+    const int64_t tile = d ? kGravSymTile
+                           : n_spheres <= kTinyTileMaxN ? kGravSymTileTiny
+                           : n_spheres <= kSmallTileMaxN ? kGravSymTileSmall : kGravSymTile;
     const int64_t T = (n_spheres + tile - 1) / tile;
     if (T > 1) bytes += (size_t)(2 * T) * (size_t)n_spheres * (d ? 32 : 16);
     bytes += 16 * (size_t)(T * (T + 1) / 2);

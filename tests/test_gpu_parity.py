@@ -230,9 +230,9 @@ def test_step_subset_freezes_others(dem):
         assert w.info(ids[0])["steps"] == 7 and w.info(ids[1])["steps"] == 3
 
 
-@pytest.mark.parametrize("n", [6000, 20_000])
+@pytest.mark.parametrize("n", [1500, 6000, 20_000])
 def test_gravity_split_and_shapes_agree(dem, n):
-    """The symmetric form with 512- and (up to 8,192 spheres) 128- and 256-sphere tiles,
+    """The symmetric form with 512- and (up to 8,192 spheres) 128- and 256-sphere tiles (and 64 up to 2,048),
     and the one-sided form with split j-ranges and other block shapes, only
     reorder sums: the gravity on every sphere agrees to FP32 rounding."""
     ic, p = W.config2(1, n_spheres=n, ball=800.0 * (n / 20_000) ** (1 / 3))
@@ -240,7 +240,7 @@ def test_gravity_split_and_shapes_agree(dem, n):
               dict(grav_sym=0, grav_block=64, grav_ib=1, grav_jchunk=n // 4),
               dict(grav_sym=0, grav_block=256, grav_ib=2, grav_jchunk=n // 3)]
     if n <= 8192:
-        shapes += [dict(grav_tile=128), dict(grav_tile=256)]
+        shapes += [dict(grav_tile=128), dict(grav_tile=256), dict(grav_tile=64)]   # 64: 128 above 2,048
     outs = []
     for kw in shapes:
         with new_world(dem) as w:
