@@ -11,11 +11,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dem_internal.h"
 
 using namespace dem;
 
 namespace {
+
+// NVTX range over a host call (visible in Nsight Systems; a no-op without a tool)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 enum Cls { C_SPH, C_SPHK, C_SPHL, C_AGG, C_CELL, C_TILE, C_CHUNK, C_PILE, C_GITEM, C_GPART, C_TNODE,
            C_TLEAF, C_TSPH, C_NCLS };
@@ -587,6 +597,7 @@ void enqueue_phase(dem_world *w, int ph)
 dem_status prepare(dem_world *w)
 {
     if (w->graph_valid) return DEM_OK;
+    Range range("dem: layout and step graph");
     GravPlan gp = plan_gravity(w);
     dem_status s = relayout(w, w->piles, &gp);
     if (s != DEM_OK) return s;
@@ -821,6 +832,7 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
                               const double *dens, const double *agg_vel, const double *agg_omega,
                               int32_t *out_pile_id)
 {
+    Range range("dem_add_aggregates");
     if (!w) return DEM_ERR_ARG;
     if (!p || !spa || !pos || !rad || !dens || !out_pile_id || n_agg <= 0)
         return fail(w, DEM_ERR_ARG, "NULL argument or n_agg <= 0");
@@ -1034,6 +1046,7 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
 
 dem_status dem_step(dem_world *w, const int32_t *pile_ids, int32_t n_piles, int64_t n_steps)
 {
+    Range range("dem_step");
     if (!w) return DEM_ERR_ARG;
     if (n_steps < 0 || (pile_ids && n_piles < 0)) return fail(w, DEM_ERR_ARG, "negative count");
     dem_status prev = collect_flags(w);
@@ -1057,6 +1070,7 @@ dem_status dem_sync(dem_world *w)
 
 dem_status dem_step_profiled(dem_world *w, int64_t n_steps, int32_t which, float *ms_out)
 {
+    Range range("dem_step_profiled");
     if (!w) return DEM_ERR_ARG;
     if (n_steps < 0 || which < 0 || which >= DEM_K_COUNT || (n_steps > 0 && !ms_out))
         return fail(w, DEM_ERR_ARG, "bad arguments");
@@ -1070,6 +1084,10 @@ dem_status dem_step_profiled(dem_world *w, int64_t n_steps, int32_t which, float
     for (auto &e : ev) CU(cudaEventCreate(&e));
     for (int64_t t = 0; t < n_steps; ++t) {
         for (int ph = 0; ph < DEM_K_COUNT; ++ph) {
+            static const char *names[DEM_K_COUNT] = {"agg_begin", "pile_begin", "keys", "scan", "scatter",
+                                                     "cell_order", "gather", "contact", "gravity", "agg_end",
+                                                     "pile_end"};
+            Range phase(names[ph]);
             if (ph == which) CU(cudaEventRecord(ev[2 * t], w->stream));
             enqueue_phase(w, ph);
             if (ph == which) CU(cudaEventRecord(ev[2 * t + 1], w->stream));
@@ -1134,6 +1152,7 @@ dem_status dem_graph_kernel_count(dem_world *w, int32_t *n_out)
 
 dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *out, int64_t n_out)
 {
+    Range range("dem_read_state");
     if (!w) return DEM_ERR_ARG;
     int slot = find_pile(w, pile_id);
     if (slot < 0) return fail(w, DEM_ERR_ARG, "unknown pile id %d", pile_id);
@@ -1316,6 +1335,7 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
 dem_status dem_write_state(dem_world *w, int32_t pile_id, int32_t field, const double *in,
                            int64_t n_in)
 {
+    Range range("dem_write_state");
     if (!w) return DEM_ERR_ARG;
     int slot = find_pile(w, pile_id);
     if (slot < 0) return fail(w, DEM_ERR_ARG, "unknown pile id %d", pile_id);
@@ -1424,6 +1444,7 @@ dem_status dem_pile_flags(dem_world *w, int32_t pile_id, int32_t *flags_out)
 
 dem_status dem_remove_pile(dem_world *w, int32_t pile_id)
 {
+    Range range("dem_remove_pile");
     if (!w) return DEM_ERR_ARG;
     int slot = find_pile(w, pile_id);
     if (slot < 0) return fail(w, DEM_ERR_ARG, "unknown pile id %d", pile_id);
@@ -1496,6 +1517,7 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
 
 dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
 {
+    Range range("dem_autotune");
     if (!w || trial_steps < 1) return DEM_ERR_ARG;
     if (w->piles.empty()) return DEM_OK;
     struct Cand { int blk, ib; double item; bool pack, sym; int tile; };
@@ -1570,6 +1592,7 @@ dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
 
 dem_status dem_pile_bulk(dem_world *w, int32_t pile_id, double *out, int64_t n_out)
 {
+    Range range("dem_pile_bulk");
     if (!w) return DEM_ERR_ARG;
     if (!out || n_out < DEM_BULK_LEN) return fail(w, DEM_ERR_ARG, "output needs %d doubles", DEM_BULK_LEN);
     int slot = find_pile(w, pile_id);
