@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -867,57 +868,96 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
         if (!(rad[i] > 0) || !(dens[i] > 0)) return fail(w, DEM_ERR_ARG, "radius and density must be > 0");
 
     // ---- host set-up in FP64 (Sec. 2.2.1) ----
+    // Aggregates are set up in 16 fixed ranges (on up to 16 host threads for
+    // large piles); the pile sums are added range by range in order, so the
+    // result does not depend on the number of threads.
     const int A = (int)n_agg;
     std::vector<int32_t> first(A), sph_agg(N);
-    std::vector<double> m(N), b(3 * N), M(A), com(3 * A), I(9 * A), Iinv(9 * A);
-    std::vector<double> q(4 * A, 0.0), r(3 * A), v(3 * A, 0.0), wb(3 * A, 0.0), zero3(3 * A, 0.0);
+    std::vector<double> m(N), b(3 * N), M(A), I(9 * A), Iinv(9 * A);
+    std::vector<double> q(4 * A, 0.0), r(3 * A), v(3 * A, 0.0), wb(3 * A, 0.0);
+    {
+        int64_t k = 0;
+        for (int a = 0; a < A; ++a) { first[a] = (int32_t)k; k += spa[a]; }
+    }
+    struct Part {
+        double smax = 0, Mtot = 0, Rp[3] = {0, 0, 0}, Vp[3] = {0, 0, 0};
+        int bad = -1;   // first aggregate of the range with a singular inertia tensor
+    };
+    constexpr int kRanges = 16;
+    Part part[kRanges];
+    auto setup_range = [&](int rg) {
+        Part &P = part[rg];
+        const int a_lo = (int)((int64_t)A * rg / kRanges), a_hi = (int)((int64_t)A * (rg + 1) / kRanges);
+        for (int a = a_lo; a < a_hi; ++a) {
+            int64_t k = first[a];
+            // mass-weighted mean about the first member: a one-sphere aggregate
+            // gets its COM exactly at the sphere (zero offset, zero lever)
+            double Ma = 0, c[3] = {0, 0, 0}, x0[3] = {pos[3 * k], pos[3 * k + 1], pos[3 * k + 2]};
+            for (int t = 0; t < spa[a]; ++t, ++k) {
+                m[k] = dens[k] * (4.0 / 3.0) * M_PI * rad[k] * rad[k] * rad[k];
+                sph_agg[k] = a;
+                Ma += m[k];
+                for (int d = 0; d < 3; ++d) c[d] += m[k] * (pos[3 * k + d] - x0[d]);
+                P.smax = std::max(P.smax, rad[k]);
+            }
+            for (int d = 0; d < 3; ++d) c[d] = x0[d] + c[d] / Ma;
+            M[a] = Ma;
+            double T[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            for (int64_t i = first[a]; i < first[a] + spa[a]; ++i) {
+                double bi[3];
+                for (int d = 0; d < 3; ++d) bi[d] = b[3 * i + d] = pos[3 * i + d] - c[d];
+                double bb = bi[0] * bi[0] + bi[1] * bi[1] + bi[2] * bi[2];
+                double sph = 0.4 * m[i] * rad[i] * rad[i];
+                for (int x = 0; x < 3; ++x)
+                    for (int y = 0; y < 3; ++y)
+                        T[3 * x + y] += (x == y ? sph + m[i] * bb : 0.0) - m[i] * bi[x] * bi[y];
+            }
+            // inverse by cofactors
+            double c00 = T[4] * T[8] - T[5] * T[7], c01 = T[5] * T[6] - T[3] * T[8],
+                   c02 = T[3] * T[7] - T[4] * T[6];
+            double det = T[0] * c00 + T[1] * c01 + T[2] * c02;
+            if (!(std::fabs(det) > 0) || !std::isfinite(det)) {
+                if (P.bad < 0) P.bad = a;
+                continue;
+            }
+            double inv[9] = {c00, T[2] * T[7] - T[1] * T[8], T[1] * T[5] - T[2] * T[4],
+                             c01, T[0] * T[8] - T[2] * T[6], T[2] * T[3] - T[0] * T[5],
+                             c02, T[1] * T[6] - T[0] * T[7], T[0] * T[4] - T[1] * T[3]};
+            for (int e = 0; e < 9; ++e) {
+                I[9 * a + e] = T[e];
+                Iinv[9 * a + e] = inv[e] / det;
+            }
+            for (int d = 0; d < 3; ++d) {
+                r[3 * a + d] = c[d];
+                if (agg_vel) v[3 * a + d] = agg_vel[3 * a + d];
+                if (agg_omega) wb[3 * a + d] = agg_omega[3 * a + d];
+            }
+            q[4 * a] = 1.0;
+            P.Mtot += Ma;
+            for (int d = 0; d < 3; ++d) { P.Rp[d] += Ma * c[d]; P.Vp[d] += Ma * v[3 * a + d]; }
+        }
+    };
+    {
+        // ranges a thread could not be started for run here (no exception leaves the ABI)
+        std::vector<std::thread> pool;
+        int rg = 1;
+        if (A >= 8192) {
+            try {
+                for (; rg < kRanges; ++rg) pool.emplace_back(setup_range, rg);
+            } catch (...) {
+            }
+        }
+        setup_range(0);
+        for (int r2 = (A >= 8192 ? rg : 1); r2 < kRanges; ++r2) setup_range(r2);
+        for (auto &t : pool) t.join();
+    }
     double smax = 0, Mtot = 0, Rp[3] = {0, 0, 0}, Vp[3] = {0, 0, 0};
-    int64_t k = 0;
-    for (int a = 0; a < A; ++a) {
-        first[a] = (int32_t)k;
-        // mass-weighted mean about the first member: a one-sphere aggregate
-        // gets its COM exactly at the sphere (zero offset, zero lever)
-        double Ma = 0, c[3] = {0, 0, 0}, x0[3] = {pos[3 * k], pos[3 * k + 1], pos[3 * k + 2]};
-        for (int t = 0; t < spa[a]; ++t, ++k) {
-            m[k] = dens[k] * (4.0 / 3.0) * M_PI * rad[k] * rad[k] * rad[k];
-            sph_agg[k] = a;
-            Ma += m[k];
-            for (int d = 0; d < 3; ++d) c[d] += m[k] * (pos[3 * k + d] - x0[d]);
-            smax = std::max(smax, rad[k]);
-        }
-        for (int d = 0; d < 3; ++d) c[d] = x0[d] + c[d] / Ma;
-        M[a] = Ma;
-        double T[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int64_t i = first[a]; i < first[a] + spa[a]; ++i) {
-            double bi[3];
-            for (int d = 0; d < 3; ++d) bi[d] = b[3 * i + d] = pos[3 * i + d] - c[d];
-            double bb = bi[0] * bi[0] + bi[1] * bi[1] + bi[2] * bi[2];
-            double sph = 0.4 * m[i] * rad[i] * rad[i];
-            for (int x = 0; x < 3; ++x)
-                for (int y = 0; y < 3; ++y)
-                    T[3 * x + y] += (x == y ? sph + m[i] * bb : 0.0) - m[i] * bi[x] * bi[y];
-        }
-        // inverse by cofactors
-        double c00 = T[4] * T[8] - T[5] * T[7], c01 = T[5] * T[6] - T[3] * T[8],
-               c02 = T[3] * T[7] - T[4] * T[6];
-        double det = T[0] * c00 + T[1] * c01 + T[2] * c02;
-        if (!(std::fabs(det) > 0) || !std::isfinite(det))
-            return fail(w, DEM_ERR_ARG, "aggregate %d has a singular inertia tensor", a);
-        double inv[9] = {c00, T[2] * T[7] - T[1] * T[8], T[1] * T[5] - T[2] * T[4],
-                         c01, T[0] * T[8] - T[2] * T[6], T[2] * T[3] - T[0] * T[5],
-                         c02, T[1] * T[6] - T[0] * T[7], T[0] * T[4] - T[1] * T[3]};
-        for (int e = 0; e < 9; ++e) {
-            I[9 * a + e] = T[e];
-            Iinv[9 * a + e] = inv[e] / det;
-        }
-        for (int d = 0; d < 3; ++d) {
-            r[3 * a + d] = c[d];
-            if (agg_vel) v[3 * a + d] = agg_vel[3 * a + d];
-            if (agg_omega) wb[3 * a + d] = agg_omega[3 * a + d];
-        }
-        q[4 * a] = 1.0;
-        Mtot += Ma;
-        for (int d = 0; d < 3; ++d) { Rp[d] += Ma * c[d]; Vp[d] += Ma * v[3 * a + d]; }
+    for (int rg = 0; rg < kRanges; ++rg) {
+        if (part[rg].bad >= 0)
+            return fail(w, DEM_ERR_ARG, "aggregate %d has a singular inertia tensor", part[rg].bad);
+        smax = std::max(smax, part[rg].smax);
+        Mtot += part[rg].Mtot;
+        for (int d = 0; d < 3; ++d) { Rp[d] += part[rg].Rp[d]; Vp[d] += part[rg].Vp[d]; }
     }
     for (int d = 0; d < 3; ++d) { Rp[d] /= Mtot; Vp[d] /= Mtot; }
 
@@ -975,9 +1015,8 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     UP(D.b64 + 3 * s0, b.data(), 24 * N);
     UP(D.s64 + s0, rad, 8 * N);
     UP(D.m64 + s0, m.data(), 8 * N);
-    std::vector<int32_t> zeros_i(N, 0);
-    UP(D.hist_n[0] + s0, zeros_i.data(), 4 * N);
-    UP(D.hist_n[1] + s0, zeros_i.data(), 4 * N);
+    CU(cudaMemsetAsync(D.hist_n[0] + s0, 0, 4 * N, st));
+    CU(cudaMemsetAsync(D.hist_n[1] + s0, 0, 4 * N, st));
     std::vector<int32_t> iota(N);
     for (int64_t i = 0; i < N; ++i) iota[i] = (int32_t)i;
     UP(D.pos_of_home[0] + s0, iota.data(), 4 * N);
@@ -1015,8 +1054,8 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     UP(D.v + 3 * a0, v.data(), 24 * A);
     UP(D.q + 4 * a0, q.data(), 32 * A);
     UP(D.wb + 3 * a0, wb.data(), 24 * A);
-    UP(D.acc + 3 * a0, zero3.data(), 24 * A);
-    UP(D.torque + 3 * a0, zero3.data(), 24 * A);
+    CU(cudaMemsetAsync(D.acc + 3 * a0, 0, 24 * A, st));
+    CU(cudaMemsetAsync(D.torque + 3 * a0, 0, 24 * A, st));
     CU(cudaMemsetAsync(D.out + 18 * a0, 0, 144 * A, st));
     std::vector<double> aref(8 * (size_t)A, 0.0);
     for (int a = 0; a < A; ++a) {
