@@ -264,6 +264,189 @@ def test_twisting_couple_law(oracle_lib):
     assert out["Tc"][1][0] == pytest.approx(+0.3 * FN * 0.5, rel=1e-12)
 
 
+# ---------------------------------------------------------------- tangential history
+# Sec. 2.1: the tangential displacement of a contact is tracked for as long as the
+# two particles stay in contact.  These pins feed the history returned by one
+# contact evaluation into the next one, as the step does.
+def _hist(n, entries, hcap=None):
+    """History arrays with the given (owner, partner, S) entries, in list order."""
+    import oracle
+    hcap = hcap or oracle.HCAP
+    hn = np.zeros(n, np.int32)
+    hp = np.zeros(n * hcap, np.int32)
+    hS = np.zeros(n * hcap * 3)
+    for i, j, S in entries:
+        k = i * hcap + hn[i]
+        hp[k] = j
+        hS[3 * k:3 * k + 3] = S
+        hn[i] += 1
+    return hn, hp, hS
+
+
+def _hist_entries(hist, i, hcap=None):
+    import oracle
+    hcap = hcap or oracle.HCAP
+    hn, hp, hS = hist
+    return [(int(hp[i * hcap + t]), hS[3 * (i * hcap + t):3 * (i * hcap + t) + 3].copy())
+            for t in range(hn[i])]
+
+
+def test_history_grows_by_ut_h_until_the_cap(oracle_lib):
+    """Fixed overlap x = 0.01 along +x (F_N = kn x = 100), constant tangential velocity
+    u = 0.3 along +y, k_t = 1e3, c_t = 5, h = 0.01, mu_s = 0.5 (cap 50).  After the
+    k-th evaluation S = k u h exactly and F_T = k_t k u h + c_t u = 3 k + 1.5 on
+    sphere 0, below the cap for k <= 16; the 17th evaluation is the first capped one
+    (3 * 17 + 1.5 = 52.5 > 50): F_T = 50 and S = (50 - c_t u)/k_t = 0.0485, and it
+    stays there while the slip goes on."""
+    pos = np.array([[0, 0, 0], [1.99, 0, 0]], float)
+    vel = np.array([[0, 0, 0], [0, 0.3, 0]], float)
+    ao = np.array([0, 1], np.int32)
+    p = free_params(kn=1e4, kt=1e3, ct=5.0, mu_s=0.5, dt=0.01)
+    hist = None
+    for k in range(1, 21):
+        out = oracle_lib.contacts(pos, vel, np.zeros((2, 3)), np.ones(2), ao, p, hist=hist)
+        hist = out["hist"]
+        F0 = out["Fc"][0]
+        assert F0[0] == pytest.approx(-100.0, rel=1e-12)
+        assert F0[2] == 0.0
+        (partner, S), = _hist_entries(hist, 0)
+        assert partner == 1
+        if k <= 16:
+            assert S[1] == pytest.approx(k * 0.003, rel=1e-12)
+            assert F0[1] == pytest.approx(3.0 * k + 1.5, rel=1e-12)
+        else:
+            assert S[1] == pytest.approx(0.0485, rel=1e-12)
+            assert F0[1] == pytest.approx(50.0, rel=1e-12)
+        assert S[0] == 0.0 and S[2] == 0.0
+        # the partner feels the opposite force (Newton's third law)
+        assert np.array_equal(out["Fc"][1], -F0)
+
+
+@pytest.mark.parametrize("axis", ["z", "y"])
+def test_history_follows_a_rotating_normal(oracle_lib, axis):
+    """At rest, a stored S = (0, s0, 0) on a contact whose normal turns: S is projected
+    on the new tangent plane and rescaled to |S_prev|.  Turning the pair about z by
+    10 degrees per evaluation carries S rigidly with it, S = s0 (-sin t, cos t, 0) after
+    a total turn t (the projection s0 cos(10 deg) (-sin t, cos t, 0) rescaled to s0); turning
+    it about y (S along the axis) leaves S unchanged.  F_T = k_t S (no slip velocity,
+    below the cap)."""
+    s0, kt = 0.01, 1e3
+    p = free_params(kn=1e4, kt=kt, ct=0.0, mu_s=0.5)
+    ao = np.array([0, 1], np.int32)
+    hist = _hist(2, [(0, 1, (0.0, s0, 0.0))])
+    step = math.radians(10.0)
+    for m in range(1, 9):
+        t = m * step
+        if axis == "z":
+            nrm = np.array([math.cos(t), math.sin(t), 0.0])
+            S_expect = s0 * np.array([-math.sin(t), math.cos(t), 0.0])
+        else:
+            nrm = np.array([math.cos(t), 0.0, -math.sin(t)])
+            S_expect = np.array([0.0, s0, 0.0])
+        pos = np.array([[0, 0, 0], 1.99 * nrm])
+        out = oracle_lib.contacts(pos, np.zeros((2, 3)), np.zeros((2, 3)), np.ones(2), ao, p,
+                                  hist=hist)
+        hist = out["hist"]
+        (partner, S), = _hist_entries(hist, 0)
+        assert partner == 1
+        assert np.allclose(S, S_expect, rtol=0, atol=1e-15)
+        assert np.linalg.norm(S) == pytest.approx(s0, rel=1e-14)
+        assert abs(np.dot(S, nrm)) < 1e-16
+        F0 = out["Fc"][0]
+        FT = F0 - np.dot(F0, nrm) * nrm
+        assert np.allclose(FT, kt * S_expect, rtol=0, atol=1e-11)
+        assert np.dot(F0, nrm) == pytest.approx(-100.0, rel=1e-12)
+
+
+def test_history_found_by_partner_not_by_slot(oracle_lib):
+    """Sphere 0 touches sphere 1 (normal +x, overlap 0.01) and sphere 2 (normal +y,
+    overlap 0.02).  Its stored list holds partner 2 first, partner 1 second and a stale
+    partner 3 that no longer touches it.  Each contact must take its own S: sphere 1
+    feels +kn 0.01 x - k_t S_1 and sphere 2 feels +kn 0.02 y - k_t S_2 (at rest, S
+    already tangent, below the cap).  The new list is in ascending partner order and
+    drops partner 3."""
+    kn, kt = 1e4, 1e3
+    p = free_params(kn=kn, kt=kt, ct=0.0, mu_s=0.9)
+    pos = np.array([[0, 0, 0], [1.99, 0, 0], [0, 1.98, 0], [0, 0, -5.0]], float)
+    ao = np.array([0, 1, 2, 3], np.int32)
+    S1 = np.array([0.0, 0.01, 0.005])
+    S2 = np.array([0.02, 0.0, -0.004])
+    hist = _hist(4, [(0, 2, S2), (0, 1, S1), (0, 3, (0.0, 0.0, 0.03))])
+    out = oracle_lib.contacts(pos, np.zeros((4, 3)), np.zeros((4, 3)), np.ones(4), ao, p,
+                              hist=hist)
+    assert out["pairs"].tolist() == [[0, 1], [0, 2]]
+    F1 = np.array([kn * 0.01, 0, 0]) - kt * S1
+    F2 = np.array([0, kn * 0.02, 0]) - kt * S2
+    assert np.allclose(out["Fc"][1], F1, rtol=1e-12, atol=1e-12)
+    assert np.allclose(out["Fc"][2], F2, rtol=1e-12, atol=1e-12)
+    assert np.allclose(out["Fc"][0], -(F1 + F2), rtol=1e-12, atol=1e-12)
+    assert np.array_equal(out["Fc"][3], np.zeros(3))
+    ent = _hist_entries(out["hist"], 0)
+    assert [e[0] for e in ent] == [1, 2]
+    assert np.allclose(ent[0][1], S1, rtol=1e-14, atol=0)
+    assert np.allclose(ent[1][1], S2, rtol=1e-14, atol=0)
+
+
+# ---------------------------------------------------------------- Eq. pred-vel spin
+def test_predicted_velocity_uses_the_full_step_spin(oracle_lib):
+    """Golden (hand-worked step): a dumbbell spinning about a principal axis with a
+    stored torque.  The spheres' predicted velocities and spins of the step carry
+    w_{n+1} = drifted spin + h/2 I^-1 N_n (0.55), not w_n (0.5) or the drifted 0.525;
+    positions follow the RK4 rotation of the quaternion."""
+    g = read_golden("spinning_dumbbell_step.txt")
+    ic = W.PileIC(counts=np.array([2], np.int32),
+                  pos=np.array([[1.0, 0, 0], [-1.0, 0, 0]]), radius=np.ones(2),
+                  density=np.full(2, g["density"]), vel=np.zeros((1, 3)),
+                  omega=np.array([[0.0, 0.0, g["spin_n"]]]))
+    pile = oracle_lib.Pile(ic, free_params(dt=g["h"]))
+    assert np.allclose(pile.m, 1.0, rtol=1e-14)
+    assert pile.I[0][2, 2] == pytest.approx(2.8, rel=1e-14)
+    pile.acc[0] = (g["accel_x"], 0.0, 0.0)
+    pile.torque[0] = (0.0, 0.0, g["torque_z"])
+    pile.step()
+    t = 1e-12
+    assert pile.sph_w[0] == pytest.approx([0, 0, g["spin_pred"]], rel=t, abs=t)
+    assert pile.sph_w[1] == pytest.approx([0, 0, g["spin_pred"]], rel=t, abs=t)
+    assert pile.sph_pos[0] == pytest.approx([g["pos0_x"], g["pos0_y"], 0], rel=t, abs=t)
+    assert pile.sph_vel[0] == pytest.approx([g["vel0_x"], g["vel0_y"], 0], rel=t, abs=t)
+    assert pile.sph_vel[1] == pytest.approx([g["vel1_x"], g["vel1_y"], 0], rel=t, abs=t)
+    assert pile.r[0] == pytest.approx([g["com_x"], 0, 0], rel=t, abs=t)
+    assert pile.v[0] == pytest.approx([g["v_half_x"], 0, 0], rel=t, abs=t)
+    assert pile.wb[0] == pytest.approx([0, 0, g["spin_half"]], rel=t, abs=t)
+    assert pile.q[0] == pytest.approx(
+        [math.sqrt(0.5 * (1 + g["cos_t"])), 0, 0, math.sqrt(0.5 * (1 - g["cos_t"]))], rel=t, abs=t)
+    assert np.array_equal(pile.torque[0], np.zeros(3))
+
+
+def test_spin_and_damping_enter_an_oblique_contact(oracle_lib):
+    """One step of two free spheres in contact, sphere 0 spinning about z with a stored
+    torque, normal and tangential dashpots on: the tangential force is
+    c_t u_t + k_t u_t h with the contact-point velocity u_t = -w_{n+1} l_0 y of the
+    full-step spin (hand values: l_0 = 0.995 for equal radii at |d| = 1.99)."""
+    rho = 3.0 / (4.0 * math.pi)                      # unit sphere mass
+    ic = W.PileIC(counts=np.array([1, 1], np.int32),
+                  pos=np.array([[0.0, 0, 0], [1.99, 0, 0]]), radius=np.ones(2),
+                  density=np.full(2, rho), vel=np.zeros((2, 3)),
+                  omega=np.array([[0.0, 0.0, 0.4], [0.0, 0.0, 0.0]]))
+    h, kn, kt, cn, ct = 0.01, 1e4, 1e3, 3.0, 2.0
+    pile = oracle_lib.Pile(ic, free_params(dt=h, kn=kn, kt=kt, cn=cn, ct=ct, mu_s=10.0))
+    # sphere inertia 2/5 m s^2 = 0.4, stored torque 0.2 about z: w_{n+1} = 0.4 + h * 0.5
+    pile.torque[0] = (0.0, 0.0, 0.2)
+    pile.step()
+    w1 = 0.4 + h * 0.2 / 0.4
+    assert pile.sph_w[0][2] == pytest.approx(w1, rel=1e-13)
+    # the spheres do not move during the drift (no stored accelerations); a free
+    # sphere's orientation turns but its centre stays
+    assert np.allclose(pile.sph_pos, ic.pos, rtol=0, atol=1e-15)
+    l0 = 0.995
+    ut_y = -w1 * l0                                  # u = v_1 - (w x l0 x) = -w l0 y
+    FT = ct * ut_y + kt * ut_y * h
+    F0 = pile.Fc[0]
+    assert F0[0] == pytest.approx(-kn * 0.01, rel=1e-12)
+    assert F0[1] == pytest.approx(FT, rel=1e-12)
+    assert pile.Tc[0][2] == pytest.approx(l0 * FT, rel=1e-12)
+
+
 # ---------------------------------------------------------------- pin 4
 def restitution_run(oracle_lib, e_target, steps_per_contact):
     ic = W.tiny_pair(gap=1e-3, v=0.02)
