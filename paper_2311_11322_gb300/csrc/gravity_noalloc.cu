@@ -9,7 +9,9 @@
 // obtains its buffers at add time), but it can hand this entry point device
 // buffers it already owns for the inputs and the output.
 //
-// The computation is the same as the world's gravity kernel with the j range
+// The formula is the world's gravity formula (FP32 pair terms, FP64 sums;
+// results agree with the world's within the mixed-precision tolerance, not
+// bitwise, since the world sums symmetric tile pairs), with the j range
 // split into kNAChunks parts: each part writes an FP64 partial sum per sphere,
 // and a second kernel adds the parts in a fixed order.  Those partial sums are
 // the only scratch memory, and here they live in the file-scope array
@@ -73,7 +75,9 @@ k_na_partial(const float4 *__restrict__ pm, const int32_t *__restrict__ agg, int
             const float r2 = fmaf(ddz, ddz, fmaf(ddy, ddy, fmaf(ddx, ddx, eps2)));
             const float inv = rsqrtf(r2);
             float s = (pj.w * inv) * (inv * inv);
-            s = (sa[jj] == ai) ? 0.f : s;   // same aggregate (and i itself): skipped
+            // same aggregate (and i itself): skipped; with eps = 0 two coincident
+            // spheres of different aggregates exert no force on each other
+            s = (sa[jj] == ai || !(r2 > 0.f)) ? 0.f : s;
             ax = fmaf(ddx, s, ax);
             ay = fmaf(ddy, s, ay);
             az = fmaf(ddz, s, az);
@@ -133,9 +137,10 @@ extern "C" dem_status dem_gravity_noalloc(const void *pos_mass, const double *ma
         set_msg(msg, msg_len, "dem_gravity_noalloc: G and eps_soft must be finite and >= 0");
         return DEM_ERR_ARG;
     }
-    if ((((uintptr_t)pos_mass) & 15) || (((uintptr_t)force_out) & 31)) {
-        set_msg(msg, msg_len, "dem_gravity_noalloc: pos_mass must be 16-byte and force_out "
-                              "32-byte aligned");
+    if ((((uintptr_t)pos_mass) & 15) || (((uintptr_t)force_out) & 31) || (((uintptr_t)mass) & 7) ||
+        (((uintptr_t)agg_id) & 3)) {
+        set_msg(msg, msg_len, "dem_gravity_noalloc: pos_mass must be 16-byte, force_out 32-byte, "
+                              "mass 8-byte and agg_id 4-byte aligned");
         return DEM_ERR_ARG;
     }
     int dev = 0;

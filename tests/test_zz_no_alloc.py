@@ -69,3 +69,57 @@ def test_gravity_noalloc_matches_world_gravity_twice():
     rc = L.dem_gravity_noalloc(t_pm.data_ptr(), t_m.data_ptr(), t_a.data_ptr(), 131073,
                                p.G, p.eps, out.data_ptr(), stream, msg, len(msg))
     assert rc == dem.DEM_ERR_ARG and b"131072" in msg.value
+    # so are buffers below their stated alignment (mass 8 B, agg_id 4 B)
+    rc = L.dem_gravity_noalloc(t_pm.data_ptr(), t_m.data_ptr() + 4, t_a.data_ptr(), 10,
+                               p.G, p.eps, out.data_ptr(), stream, msg, len(msg))
+    assert rc == dem.DEM_ERR_ARG and b"aligned" in msg.value
+    rc = L.dem_gravity_noalloc(t_pm.data_ptr(), t_m.data_ptr(), t_a.data_ptr() + 2, 10,
+                               p.G, p.eps, out.data_ptr(), stream, msg, len(msg))
+    assert rc == dem.DEM_ERR_ARG and b"aligned" in msg.value
+
+
+@pytest.mark.parametrize("n", [1, 3, 131072])
+def test_gravity_noalloc_edge_sizes_against_oracle(n):
+    """The edges of the fixed scratch: n below the number of j-range parts (the
+    empty parts must contribute zeros) and the largest accepted n (the scratch
+    filled to its end), each against the oracle's softened direct sum (same
+    mixed-precision bound), twice in a row.  n = 1 has no partner: zero force."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_2311_11322_gb300 import dem
+    from paper_2311_11322_gb300 import workloads as W
+
+    rng = np.random.default_rng(n)
+    pos = rng.uniform(-500.0, 500.0, (n, 3))
+    rad = rng.uniform(1.0, 3.0, n)
+    m = W.sphere_mass(rad, 2500.0)
+    agg = (np.arange(n) // 2).astype(np.int32)          # pairs of spheres share an aggregate
+    G, eps = W.G_SI, 0.5
+    rows = np.arange(n) if n < 5000 else np.sort(rng.choice(n, 2000, replace=False))
+    ref, fmag = oracle.gravity(pos, m, agg, G, eps, exclude_same_agg=True, rows=rows, want_mag=True)
+    pm = np.concatenate([pos.astype(np.float32), m.astype(np.float32)[:, None]], 1)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t_pm = torch.from_numpy(np.ascontiguousarray(pm)).to(dev)
+    t_m = torch.from_numpy(np.ascontiguousarray(m)).to(dev)
+    t_a = torch.from_numpy(agg).to(dev)
+    out = torch.empty((n, 4), dtype=torch.float64, device=dev)
+    L = dem.load()
+    msg = C.create_string_buffer(256)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    for _ in range(2):
+        out.fill_(float("nan"))
+        rc = L.dem_gravity_noalloc(t_pm.data_ptr(), t_m.data_ptr(), t_a.data_ptr(), n, G, eps,
+                                   out.data_ptr(), stream, msg, len(msg))
+        assert rc == dem.DEM_OK, msg.value
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        if n <= 2:
+            assert np.array_equal(got[:, :3], np.zeros((n, 3)))
+        else:
+            err = np.linalg.norm(got[rows, :3] - ref, axis=1) / np.maximum(fmag, 1e-300)
+            assert err.max() <= TOL, err.max()
