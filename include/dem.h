@@ -268,13 +268,28 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
  */
 dem_status dem_set_tuning(dem_world *w, const char *key, double value);
 
+/* Current value of a tuning knob (the keys of dem_set_tuning).
+ * Errors: DEM_ERR_ARG (NULL argument, unknown key). */
+dem_status dem_get_tuning(dem_world *w, const char *key, double *value_out);
+
 /*
- * Autotuner: time the candidate gravity shapes (the symmetric form in the
- * mixed path; block 64/128/256, 1/2/4 i-spheres per thread, scalar or packed,
- * three work-item sizes of the one-sided form) and then
- * cell factors 1, 1.25, 1.5, 2 on the current piles, running `trial_steps`
- * real steps per candidate (so the state advances), and keep the fastest.
- * best_ms_out (may be NULL) receives its step time.
+ * Autotuner: time the candidate gravity shapes (the symmetric form, with
+ * 512-sphere tiles and, in the mixed path, 64-, 128- and 256-sphere tiles;
+ * the one-sided form with block 64/128/256, 1/2/4 i-spheres per thread,
+ * scalar or packed, three work-item sizes) and then cell factors 1, 1.25,
+ * 1.5, 2 on the current piles, one warm and `trial_steps` timed step graph
+ * launches per candidate, and keep the fastest.  The trials step the live
+ * piles, so the tuner first copies every field that carries state from step
+ * to step (positions, velocities, orientations, spins, stored accelerations
+ * and torques, contact history, step counters, flags, planet) into a
+ * temporary device buffer (one allocation through the world's allocator, the
+ * size of that state) and copies it back at the end, on success and on every
+ * error path: the piles leave the tuner in the state they entered it, and the
+ * next step recomputes the cell and candidate lists.  On an error the
+ * original tuning is restored.  best_ms_out (may be NULL) receives the
+ * fastest step time.  Synchronises the stream.
+ * Errors: DEM_ERR_ARG (trial_steps < 1), DEM_ERR_OOM (no room for the
+ * snapshot), DEM_ERR_CUDA.
  */
 dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out);
 
@@ -341,11 +356,15 @@ dem_status dem_watch_result(dem_world *w, int32_t pile_id, double *out, int64_t 
  * plugins whose host owns every allocation -- and so cannot create a world.
  * It computes, for i < n,
  *   F_i = G m_i sum_{j : agg_id[j] != agg_id[i]} m_j (r_j - r_i) / (|r_j - r_i|^2 + eps^2)^{3/2}
- * with FP32 pair terms and FP64 sums, exactly like the world's gravity pass.
+ * with FP32 pair terms and FP64 sums: the world's gravity formula, agreeing
+ * with the world's gravity pass within the mixed-precision tolerance (not
+ * bitwise: the summation order differs).  With eps_soft = 0, two coincident
+ * spheres of different aggregates contribute nothing to each other.
  *   pos_mass  device, float4 [n] (16-byte aligned): x, y, z in m about any
  *             common origin, mass in kg (used in the pair terms);
- *   mass      device, double [n]: masses in kg (the final G m_i factor);
- *   agg_id    device, int32 [n]: aggregate of each sphere (pairs with equal
+ *   mass      device, double [n] (8-byte aligned): masses in kg (the final
+ *             G m_i factor);
+ *   agg_id    device, int32 [n] (4-byte aligned): aggregate of each sphere (pairs with equal
  *             ids are skipped, and so is i = j);
  *   force_out device, double [n][4] (32-byte aligned): Fx, Fy, Fz, 0 in N.
  * The caller owns all four buffers.  Work is queued on cuda_stream (NULL =
@@ -359,12 +378,43 @@ dem_status dem_watch_result(dem_world *w, int32_t pile_id, double *out, int64_t 
  * race on it and must be serialised by the caller.  No value from an earlier
  * call is read, so nothing needs clearing.  msg (may be NULL) receives a
  * one-line error text of at most msg_len bytes.
- * Errors: DEM_ERR_ARG (NULL pointer, n out of range, bad G/eps, misaligned
- * buffer), DEM_ERR_CUDA (no device, symbol lookup or launch failure).
+ * Errors: DEM_ERR_ARG (NULL pointer, n out of range, G or eps_soft negative
+ * or not finite, a buffer below its stated alignment: pos_mass 16, force_out
+ * 32, mass 8, agg_id 4 bytes), DEM_ERR_CUDA (no device, symbol lookup or
+ * launch failure).
  */
 dem_status dem_gravity_noalloc(const void *pos_mass, const double *mass, const int32_t *agg_id,
                                int32_t n, double G, double eps_soft, double *force_out,
                                void *cuda_stream, char *msg, size_t msg_len);
+
+/*
+ * Throughput probe: the peak rates that bound the step's kernels on this GPU,
+ * measured the way the step uses the hardware (the paper has no counterpart;
+ * these are the denominators of the roofline fractions the benchmark reports).
+ *   kind DEM_PROBE_FMA32:   FP32 FMA rate of the CUDA cores (the gravity pair
+ *                           terms), flop/s, 2 flop per FMA;
+ *        DEM_PROBE_FMA32X2: the same with packed f32x2 FMAs, 4 flop each;
+ *        DEM_PROBE_FMA64:   FP64 FMA rate (the all-FP64 path), flop/s;
+ *        DEM_PROBE_COPY:    HBM copy, bytes read + written per second.
+ *   size: FMA kinds: rounds per thread (each round 32 FMAs per thread, on a
+ *         grid of 4 x 256 threads per SM); copy: bytes per buffer (multiple
+ *         of 16).
+ *   reps: launches, each timed alone with CUDA events on cuda_stream (NULL =
+ *         legacy stream); the fastest is reported.
+ *   src, dst: device buffers owned by the caller.  Copy: `size` bytes each,
+ *         16-byte aligned, not overlapping.  FMA kinds: src unused, dst an
+ *         8-byte aligned device word the kernel could write (it never does
+ *         in practice).
+ *   rate_out: the rate; ms_out (may be NULL): the fastest launch's time;
+ *   sm_count_out (may be NULL): the device's SM count.
+ * Synchronises cuda_stream.  msg (may be NULL) receives a one-line error text.
+ * Errors: DEM_ERR_ARG (unknown kind, size or reps < 1, NULL or misaligned
+ * buffer), DEM_ERR_CUDA.
+ */
+enum { DEM_PROBE_FMA32 = 0, DEM_PROBE_FMA32X2 = 1, DEM_PROBE_FMA64 = 2, DEM_PROBE_COPY = 3 };
+dem_status dem_probe_peak(int32_t kind, int64_t size, int32_t reps, const void *src, void *dst,
+                          void *cuda_stream, double *rate_out, double *ms_out, int32_t *sm_count_out,
+                          char *msg, size_t msg_len);
 
 /* Device bytes one pile of this size needs with direct-sum gravity (state, sorted
  * copies, cells, history, gravity partial sums).  Tree gravity (grav_theta > 0)

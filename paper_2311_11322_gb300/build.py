@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdem.so")
 
 SOURCES = ["kernels_step.cu", "kernels_contact.cu", "kernels_gravity.cu", "kernels_tree.cu",
-           "kernels_analysis.cu", "gravity_noalloc.cu", "world.cpp"]
+           "kernels_analysis.cu", "gravity_noalloc.cu", "kernels_probe.cu", "world.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

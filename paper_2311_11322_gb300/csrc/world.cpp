@@ -1554,79 +1554,152 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
     return DEM_OK;
 }
 
+dem_status dem_get_tuning(dem_world *w, const char *key, double *value_out)
+{
+    if (!w || !key || !value_out) return DEM_ERR_ARG;
+    const std::string k = key;
+    if (k == "grav_block") *value_out = w->grav_block;
+    else if (k == "grav_ib") *value_out = w->grav_ib;
+    else if (k == "grav_jchunk") *value_out = (double)w->grav_jchunk;
+    else if (k == "grav_pack") *value_out = w->grav_pack ? 1.0 : 0.0;
+    else if (k == "grav_sym") *value_out = w->grav_sym ? 1.0 : 0.0;
+    else if (k == "grav_tile") *value_out = w->grav_tile;
+    else if (k == "grav_theta") *value_out = w->grav_theta;
+    else if (k == "grav_order") *value_out = w->grav_order;
+    else if (k == "grav_item") *value_out = w->grav_item;
+    else if (k == "cell_factor") *value_out = w->cell_factor;
+    else if (k == "skin") *value_out = w->skin_frac;
+    else return fail(w, DEM_ERR_ARG, "unknown tuning key '%s'", key);
+    return DEM_OK;
+}
+
 dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
 {
     Range range("dem_autotune");
     if (!w || trial_steps < 1) return DEM_ERR_ARG;
     if (w->piles.empty()) return DEM_OK;
-    struct Cand { int blk, ib; double item; bool pack, sym; int tile; };
-    std::vector<Cand> cands;
-    cands.push_back({128, 4, 1048576.0, false, true, 512});
-    if (w->precision == DEM_MIXED) cands.push_back({128, 4, 1048576.0, false, true, 128});
+    dem_status s = collect_flags(w);
+    if (s != DEM_OK) return s;
+    struct Knobs { int blk, ib; double item; bool pack, sym; int tile; double cell; };
+    const Knobs orig = {w->grav_block, w->grav_ib, w->grav_item, w->grav_pack, w->grav_sym, w->grav_tile,
+                        w->cell_factor};
+    const int64_t orig_jchunk = w->grav_jchunk;
+    std::vector<Knobs> cands;
+    cands.push_back({128, 4, 1048576.0, false, true, 512, 0});
+    if (w->precision == DEM_MIXED)
+        for (int tile : {64, 128, 256}) cands.push_back({128, 4, 1048576.0, false, true, tile, 0});
     for (int blk : {64, 128, 256})
         for (int ib : {1, 2, 4})
             for (double item : {262144.0, 1048576.0, 4194304.0}) {
-                cands.push_back({blk, ib, item, false, false, 0});
-                if (ib % 2 == 0) cands.push_back({blk, ib, item, true, false, 0});
+                cands.push_back({blk, ib, item, false, false, 0, 0});
+                if (ib % 2 == 0) cands.push_back({blk, ib, item, true, false, 0, 0});
             }
-    cudaEvent_t e0, e1;
-    CU(cudaEventCreate(&e0));
-    CU(cudaEventCreate(&e1));
-    double best = 1e300;
-    Cand bc = {w->grav_block, w->grav_ib, w->grav_item, w->grav_pack, w->grav_sym, w->grav_tile};
-    w->grav_jchunk = 0;
-    for (auto &c : cands) {
-        w->grav_block = c.blk; w->grav_ib = c.ib; w->grav_item = c.item; w->grav_pack = c.pack;
-        w->grav_sym = c.sym;
-        w->grav_tile = c.tile;
+    // The trials step the live piles.  Snapshot every field that carries state
+    // from step to step (the fields a layout change preserves) and put it back
+    // afterwards, so the piles leave the tuner exactly as they entered it.
+    std::vector<std::pair<size_t, size_t>> snap_of;   // field index -> (offset, bytes)
+    size_t snap_bytes = 0;
+    for (size_t f = 0; f < w->fields.size(); ++f) {
+        const Field &fd = w->fields[f];
+        if (!fd.keep || *fd.ptr == nullptr) continue;
+        int64_t n = 0;
+        for (auto &q : w->piles) n += pile_count(w, q, fd.cls);
+        const size_t bytes = (size_t)n * fd.el;
+        snap_of.push_back({f, bytes});
+        snap_bytes += (bytes + 255) / 256 * 256;
+    }
+    char *snap = snap_bytes ? (char *)dev_alloc(w, snap_bytes) : nullptr;
+    if (snap_bytes && !snap) return fail(w, DEM_ERR_OOM, "autotune: snapshot of %zu bytes failed", snap_bytes);
+    {
+        size_t o = 0;
+        for (auto &fb : snap_of) {
+            cudaError_t e = cudaMemcpyAsync(snap + o, *w->fields[fb.first].ptr, fb.second,
+                                            cudaMemcpyDeviceToDevice, w->stream);
+            if (e != cudaSuccess) {
+                dev_free(w, snap);
+                return fail(w, DEM_ERR_CUDA, "autotune snapshot: %s", cudaGetErrorString(e));
+            }
+            o += (fb.second + 255) / 256 * 256;
+        }
+    }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    auto set_knobs = [&](const Knobs &k) -> dem_status {
+        w->grav_block = k.blk; w->grav_ib = k.ib; w->grav_item = k.item; w->grav_pack = k.pack;
+        w->grav_sym = k.sym; w->grav_tile = k.tile;
         w->graph_valid = false;
-        dem_status s = prepare(w);
-        if (s != DEM_OK) return s;
-        s = set_enabled(w, nullptr, 0);
-        if (s != DEM_OK) return s;
-        CU(cudaGraphLaunch(w->exec, w->stream));   // warm
-        CU(cudaEventRecord(e0, w->stream));
-        for (int t = 0; t < trial_steps; ++t) CU(cudaGraphLaunch(w->exec, w->stream));
-        CU(cudaEventRecord(e1, w->stream));
-        CU(cudaEventSynchronize(e1));
-        float ms;
-        CU(cudaEventElapsedTime(&ms, e0, e1));
-        double per = ms / trial_steps;
-        if (per < best) { best = per; bc = c; }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    w->grav_block = bc.blk; w->grav_ib = bc.ib; w->grav_item = bc.item; w->grav_pack = bc.pack;
-    w->grav_sym = bc.sym;
-    w->grav_tile = bc.tile;
-    w->graph_valid = false;
-    // then the cell edge (contact search), with the chosen gravity shape
-    double bf = w->cell_factor;
-    for (double f : {1.0, 1.25, 1.5, 2.0}) {
-        dem_status s = dem_set_tuning(w, "cell_factor", f);
-        if (s != DEM_OK) return s;
-        s = prepare(w);
-        if (s != DEM_OK) return s;
-        s = set_enabled(w, nullptr, 0);
-        if (s != DEM_OK) return s;
-        cudaEvent_t f0, f1;
-        CU(cudaEventCreate(&f0));
-        CU(cudaEventCreate(&f1));
+        if (k.cell > 0 && k.cell != w->cell_factor) return dem_set_tuning(w, "cell_factor", k.cell);
+        return DEM_OK;
+    };
+    // time trial_steps graph launches after one warm launch
+    auto trial = [&](double &per) -> dem_status {
+        dem_status t = prepare(w);
+        if (t == DEM_OK) t = set_enabled(w, nullptr, 0);
+        if (t != DEM_OK) return t;
         CU(cudaGraphLaunch(w->exec, w->stream));
-        CU(cudaEventRecord(f0, w->stream));
-        for (int t = 0; t < trial_steps; ++t) CU(cudaGraphLaunch(w->exec, w->stream));
-        CU(cudaEventRecord(f1, w->stream));
-        CU(cudaEventSynchronize(f1));
-        float ms;
-        CU(cudaEventElapsedTime(&ms, f0, f1));
-        cudaEventDestroy(f0);
-        cudaEventDestroy(f1);
-        if (ms / trial_steps < best) { best = ms / trial_steps; bf = f; }
+        CU(cudaEventRecord(ev[0], w->stream));
+        for (int i = 0; i < trial_steps; ++i) CU(cudaGraphLaunch(w->exec, w->stream));
+        CU(cudaEventRecord(ev[1], w->stream));
+        CU(cudaEventSynchronize(ev[1]));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        per = ms / trial_steps;
+        return DEM_OK;
+    };
+    // restore the state (and, on failure, the original knobs) on every way out
+    auto finish = [&](dem_status st, const Knobs &k) -> dem_status {
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+        std::string err = st == DEM_OK ? std::string() : w->err;
+        w->grav_jchunk = st == DEM_OK ? 0 : orig_jchunk;
+        dem_status r = set_knobs(st == DEM_OK ? k : orig);
+        if (r == DEM_OK) r = prepare(w);
+        if (r == DEM_OK && snap) {
+            size_t o = 0;
+            for (auto &fb : snap_of) {
+                if (cudaMemcpyAsync(*w->fields[fb.first].ptr, snap + o, fb.second, cudaMemcpyDeviceToDevice,
+                                    w->stream) != cudaSuccess) {
+                    r = fail(w, DEM_ERR_CUDA, "autotune: restoring the pile state failed");
+                    break;
+                }
+                o += (fb.second + 255) / 256 * 256;
+            }
+            // the transient sort and candidate lists belong to the trials' state
+            if (r == DEM_OK) launch_force_rebuild(w->A, w->Z, -1, w->stream);
+            if (r == DEM_OK && cudaStreamSynchronize(w->stream) != cudaSuccess)
+                r = fail(w, DEM_ERR_CUDA, "autotune: restoring the pile state failed");
+        }
+        if (snap) dev_free(w, snap);
+        if (st != DEM_OK) {
+            w->err = err;
+            return st;
+        }
+        return r;
+    };
+    if (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess)
+        return finish(fail(w, DEM_ERR_CUDA, "autotune: cudaEventCreate failed"), orig);
+    w->grav_jchunk = 0;
+    double best = 1e300;
+    Knobs bk = orig;
+    for (auto c : cands) {
+        c.cell = orig.cell;
+        s = set_knobs(c);
+        double per = 0.0;
+        if (s == DEM_OK) s = trial(per);
+        if (s != DEM_OK) return finish(s, orig);
+        if (per < best) { best = per; bk = c; }
     }
-    dem_status s2 = dem_set_tuning(w, "cell_factor", bf);
-    if (s2 != DEM_OK) return s2;
+    // then the cell edge (contact search), with the chosen gravity shape
+    for (double f : {1.0, 1.25, 1.5, 2.0}) {
+        Knobs c = bk;
+        c.cell = f;
+        s = set_knobs(c);
+        double per = 0.0;
+        if (s == DEM_OK) s = trial(per);
+        if (s != DEM_OK) return finish(s, orig);
+        if (per < best) { best = per; bk = c; }
+    }
     if (best_ms_out) *best_ms_out = best;
-    return DEM_OK;
+    return finish(DEM_OK, bk);
 }
 
 dem_status dem_pile_bulk(dem_world *w, int32_t pile_id, double *out, int64_t n_out)

@@ -84,6 +84,7 @@ def load():
         "dem_pile_flags": (i32, [vp, i32, C.POINTER(i32)]),
         "dem_remove_pile": (i32, [vp, i32]),
         "dem_set_tuning": (i32, [vp, C.c_char_p, dbl]),
+        "dem_get_tuning": (i32, [vp, C.c_char_p, C.POINTER(dbl)]),
         "dem_autotune": (i32, [vp, i32, C.POINTER(dbl)]),
         "dem_footprint_bytes": (sz, [i64, i64, i32, i32]),
         "dem_world_bytes": (sz, [vp]),
@@ -93,6 +94,8 @@ def load():
         "dem_step_timed": (i32, [vp, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
         "dem_graph_kernel_count": (i32, [vp, C.POINTER(i32)]),
         "dem_gravity_noalloc": (i32, [vp, vp, vp, i32, dbl, dbl, vp, vp, C.c_char_p, sz]),
+        "dem_probe_peak": (i32, [i32, i64, i32, vp, vp, vp, C.POINTER(dbl), C.POINTER(dbl),
+                                 C.POINTER(i32), C.c_char_p, sz]),
         "dem_write_state": (i32, [vp, i32, i32, vp, i64]),
         "dem_pile_bulk": (i32, [vp, i32, vp, i64]),
         "dem_watch": (i32, [vp, i32, dbl, i64]),
@@ -145,6 +148,21 @@ def dem_create(stream: int = 0, budget: int = 0):
 
 def dem_footprint_bytes(n_spheres, n_agg, max_contacts, precision):
     return int(load().dem_footprint_bytes(n_spheres, n_agg, max_contacts, precision))
+
+
+PROBES = {"FMA32": 0, "FMA32X2": 1, "FMA64": 2, "COPY": 3}
+
+
+def dem_probe_peak(kind: str, size: int, reps: int, src_ptr: int, dst_ptr: int, stream: int = 0):
+    """Peak-rate probe (include/dem.h): returns (rate per s, fastest ms, SM count)."""
+    rate, ms, sms = C.c_double(), C.c_double(), C.c_int32()
+    msg = C.create_string_buffer(256)
+    s = load().dem_probe_peak(PROBES[kind], int(size), int(reps), C.c_void_p(src_ptr),
+                              C.c_void_p(dst_ptr), C.c_void_p(stream), C.byref(rate), C.byref(ms),
+                              C.byref(sms), msg, len(msg))
+    if s != DEM_OK:
+        raise DemError(s, msg.value.decode())
+    return rate.value, ms.value, sms.value
 
 
 def dem_last_error(w) -> str:
@@ -338,6 +356,11 @@ class World:
     # ---- tuning
     def set_tuning(self, key, value):
         self._check(self._L.dem_set_tuning(self.w, key.encode(), float(value)))
+
+    def get_tuning(self, key) -> float:
+        v = C.c_double()
+        self._check(self._L.dem_get_tuning(self.w, key.encode(), C.byref(v)))
+        return v.value
 
     def autotune(self, trial_steps=3):
         best = C.c_double()
