@@ -53,9 +53,13 @@ N_SPHERES = 100_000
 # 2 mul for r^-3, 2 mul for the two mass factors, 6 FMA for the two sums).
 FLOP_PER_INTERACTION = 20.0
 FLOP_PER_PAIR_SYM = 27.0
-# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-SM_MAX_MHZ = 2070.0
+# Contact pass, algorithmic bytes per sphere-step (the hot-path scope's count):
+# read position+radius, predicted velocity+aggregate, spin (16 B each) and the
+# cell range (4 B), write F and tau (16 B each); per canonical pair (one per
+# contact, z / 2 per sphere) read and write one 16-byte history record
+# (partner 4 B, S 12 B).
+CONTACT_BYTES_PER_SPHERE = 16 + 16 + 16 + 4 + 32
+CONTACT_BYTES_PER_PAIR = 16 + 16
 
 
 def parse():
@@ -72,22 +76,21 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-e2-collapse", action="store_true")
     ap.add_argument("--no-tree", action="store_true")
-    ap.add_argument("--no-analysis", action="store_true")
-    ap.add_argument("--part", default="all", choices=["all", "contact", "e2", "tree", "analysis", "analysis-sweep"],
+    ap.add_argument("--part", default="all", choices=["all", "contact", "e2", "tree", "analysis", "probe"],
                     help="contact: only the contact-pass roofline on the 1M-sphere lattice; "
                          "e2: only the paper's 2e4-sphere profiling collapse; "
                          "tree: only tree vs direct gravity; "
-                         "analysis: only the spin-up and encounter runs with device-side watches; "
-                         "analysis-sweep: those runs for six grain shapes at 2,000 spheres (not part of all)")
+                         "analysis: only the spin-up and encounter runs with device-side watches "
+                         "(not part of all); probe: only the peak-rate probes")
     ap.add_argument("--contact-n", type=int, default=1_048_576)
     return ap.parse_args()
 
 
-def workload_config(ic):
+def workload_config(ic, precision="mixed"):
     return {"workload": "collapse-100k: 100,000 spheres in %d rigid aggregates (dumbbell, rod3, "
                         "tetra, square; radii lognormal median 5 m sigma 0.2) uniform in a 2 km "
                         "ball at rest, contacts + softened direct-sum self-gravity" % ic.n_agg,
-            "n_spheres": int(ic.n_sph), "n_aggregates": int(ic.n_agg), "precision": "mixed",
+            "n_spheres": int(ic.n_sph), "n_aggregates": int(ic.n_agg), "precision": precision,
             "l2": "flushed between timed steps (512 MiB write on the library stream)",
             "seed": 0}
 
@@ -242,7 +245,8 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3):
     # counts (5 x 4), F and tau out (2 x float4 = 32), the candidate list (4 per
     # entry, at least one per contact) and every contact's history slot read
     # and written (float4 each)
-    algo = N * (64 + 20 + 32) + z * (4 + 32)
+    layout = N * (64 + 20 + 32) + z * (4 + 32)
+    algo = N * CONTACT_BYTES_PER_SPHERE + (z / 2) * CONTACT_BYTES_PER_PAIR
     ms = statistics.median(ks)
     achieved = algo / (ms / 1e3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
@@ -252,8 +256,13 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3):
             "kernel_ms": ms, "rebuilds_in_timed_steps": info["rebuilds"] - r0,
             "rebuild_step_contact_ms": statistics.median(rb),
             "n_spheres": N, "contacts_per_sphere": z / N,
-            "algorithmic_bytes_per_launch": algo, "workload": "dense FCC tetrahedra lattice, "
-            "1,048,576 spheres, overlaps 0.5% R, gravity off"}
+            "algorithmic_bytes_per_launch": algo,
+            "algorithmic_bytes": "84 B per sphere (position, velocity, spin 16 B each, cell range 4 B "
+                                 "read; F, tau 32 B written) + 32 B per contact pair (16-byte history "
+                                 "record read and written)",
+            "layout_bytes_per_launch": layout, "frac_on_layout_bytes": layout / (ms / 1e3) / 1e9 / peak_gbs,
+            "layout_bytes": "this library's own layout: 116 B per sphere + 36 B per contact side",
+            "workload": "dense FCC tetrahedra lattice, %d spheres, overlaps 0.5%% R, gravity off" % N}
 
 
 PHASES = {"aggregate": ("AGG_BEGIN", "PILE_BEGIN", "AGG_END", "PILE_END"),
@@ -407,66 +416,6 @@ def run_analysis(dem, W, n_agg=250, settle=150_000, omega_target=1.5, ramp_pcrit
     return out
 
 
-SWEEP_SHAPES = ("single", "dumbbell", "tetra", "diamond", "rod4", "cube8")
-
-
-def run_analysis_sweep(dem, W, n_spheres=2000, settle=150_000, omega_target=1.5, ramp_pcrit=2.0,
-                       max_steps=900_000, chunk=20_000):
-    """The spin-up and encounter analyses (Sec. 4.1, 4.2) over grain shapes at a
-    fixed sphere count: one progenitor per shape (a lattice pile of ~n_spheres
-    spheres), all settled together in one world, then the 2 x shapes runs
-    stepped together in a second world, each pile with its own device watch."""
-    from paper_2311_11322_gb300 import analysis
-    shp = {}
-    with dem.World() as w:
-        ids = {}
-        for k, sh in enumerate(SWEEP_SHAPES):
-            rng = np.random.default_rng(100 + k)
-            n_agg = max(1, n_spheres // W.SHAPE_SIZE[sh])
-            ic = W.lattice_pile(rng, n_agg, shapes=(sh,))
-            p = W.settled_params(ic, 1.0, max_contacts=24)
-            ids[sh] = (w.add_pile(ic, p), p)
-        t0 = time.perf_counter()
-        done = 0
-        while done < settle:
-            w.step(min(chunk, settle - done))
-            done += min(chunk, settle - done)
-        w.sync()
-        t_settle = time.perf_counter() - t0
-        for sh, (pid, p) in ids.items():
-            shp[sh] = {"ic": w.ic_of(pid), "p": p, "bulk": w.bulk(pid)}
-    with dem.World() as w:
-        runs = {}
-        for sh, d in shp.items():
-            b = d["bulk"]
-            ps = analysis.spinup_params(d["p"], d["ic"], omega_target * 2 * math.pi / b["p_crit"],
-                                        int(ramp_pcrit * b["p_crit"] / d["p"].dt))
-            pe, _ = analysis.encounter_params(d["p"], d["ic"])
-            a, e = w.add_pile(d["ic"], ps), w.add_pile(d["ic"], pe)
-            w.watch(a, 0.05, 10)
-            w.watch(e, 0.005, 10)
-            runs[sh] = (a, e)
-        live = [x for ab in runs.values() for x in ab]
-        taken = 0
-        t0 = time.perf_counter()
-        while live and taken < max_steps:
-            w.step(chunk, piles=live)
-            taken += chunk
-            live = [x for x in live if w.watch_result(x)["fired_step"] is None]
-        w.sync()
-        t_runs = time.perf_counter() - t0
-        out = {"n_spheres_target": n_spheres, "settle_steps": settle, "settle_s": t_settle, "runs_s": t_runs,
-               "spin_ramp": f"{omega_target} x nominal critical spin over {ramp_pcrit} critical periods",
-               "shapes": {}}
-        for sh, (a, e) in runs.items():
-            ra, re_ = w.watch_result(a), w.watch_result(e)
-            out["shapes"][sh] = {"n_spheres": int(shp[sh]["ic"].n_sph), "n_grains": int(shp[sh]["ic"].n_agg),
-                                 "settled_density": shp[sh]["bulk"]["density"],
-                                 "critical_spin_ratio": analysis.critical_spin_ratio(ra),
-                                 "disruption_ratio": analysis.disruption_ratio(re_)}
-    return out
-
-
 def run_batched(dem, W, steps=5, n_piles=256):
     """256 independent piles of tetrahedra (sizes lognormal in [500, 20000]):
     all stepped by one graph launch per step after autotuning, against looping
@@ -565,6 +514,39 @@ def cpu_baseline(W, ic, p, rows_frac=1.0):
                       "all spheres), %.1f s" % (len(rows), n, n // len(rows), t)}
 
 
+def run_probes(dem, clocks_index=0):
+    """Peak rates of this GPU measured in this run (dem_probe_peak): FP32 FMA
+    (scalar and packed f32x2), FP64 FMA and HBM copy, with nvidia-smi clocks
+    sampled while the probes run."""
+    import torch
+    sink = torch.zeros(64, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    ck = Clocks(clocks_index)
+    ck.start()
+    out = {}
+    for kind, size, reps in (("FMA32", 300_000, 10), ("FMA32X2", 150_000, 10), ("FMA64", 5_000, 5)):
+        rate, ms, sms = dem.dem_probe_peak(kind, size, reps, 0, sink.data_ptr(), st)
+        out[kind] = {"tflops": rate / 1e12, "ms": ms}
+    nbytes = 4 << 30
+    src = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    dst = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    src.fill_(1)
+    rate, ms, sms = dem.dem_probe_peak("COPY", nbytes, 10, src.data_ptr(), dst.data_ptr(), st)
+    out["COPY"] = {"gbs": rate / 1e9, "ms": ms, "bytes_per_buffer": nbytes}
+    del src, dst
+    torch.cuda.synchronize()
+    out["clocks"] = ck.stop()
+    out["sm_count"] = int(sms)
+    out["sm_count_torch"] = int(torch.cuda.get_device_properties(0).multi_processor_count)
+    out["fp32_peak_tflops"] = max(out["FMA32"]["tflops"], out["FMA32X2"]["tflops"])
+    out["fp32_peak_form"] = ("packed f32x2 FMA" if out["FMA32X2"]["tflops"] > out["FMA32"]["tflops"]
+                             else "scalar FMA")
+    out["what"] = ("dem_probe_peak: 4 blocks x 256 threads per SM, 8 independent FMA chains per thread "
+                   "(2 flop per FMA, 4 per packed f32x2 FMA), fastest of the launches; copy: float4 "
+                   "streaming copy of 4 GiB, read + write bytes")
+    return out
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -622,9 +604,12 @@ def run_ours(args):
     value = ws * ic.n_sph * args.steps / t_max
     g_ms = statistics.mean(grav_ms)
     n_int = interactions(ic)
-    flops = FLOP_PER_PAIR_SYM * n_int / 2.0
+    flops = FLOP_PER_INTERACTION * n_int
     achieved = flops / (g_ms / 1e3) / 1e12
+    executed = FLOP_PER_PAIR_SYM * n_int / 2.0
     w.close()
+    probes = run_probes(dem, local)
+    fp32_peak = probes["fp32_peak_tflops"]
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
@@ -632,17 +617,27 @@ def run_ours(args):
            "dtype": "f32/f64", "data": "synthetic (seeded generator, no dataset)",
            "config": workload_config(ic), "wall_s_timed_region": wall,
            "gpu_launches": n_kern * args.steps,
-           "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                        "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                        "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                         "traffic": traffic_for("kernels_gravity.cu", "k_gravity32s"),
                         "kernel": "k_gravity32s (softened direct-sum gravity, symmetric "
                                   "tile pairs, packed f32x2) + k_grav_combine_sym",
                         "kernel_ms": g_ms, "share_of_step": g_ms / statistics.mean(step_ms),
                         "flops_per_launch": flops,
-                        "flop_count": "27 per unordered pair of spheres in different aggregates",
+                        "flop_count": "20 per ordered pair of spheres in different aggregates "
+                                      "(the direct-sum convention: 3 sub, 3 FMA, rsqrt as 2, 3 mul, "
+                                      "3 FMA)",
                         "interactions_per_s": n_int / (g_ms / 1e3),
-                        "one_sided_equivalent_tflops": FLOP_PER_INTERACTION * n_int / (g_ms / 1e3) / 1e12,
-                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"},
+                        "executed_flops_per_launch": executed,
+                        "executed_tflops": executed / (g_ms / 1e3) / 1e12,
+                        "executed_frac": executed / (g_ms / 1e3) / 1e12 / fp32_peak,
+                        "executed_flop_count": "27 per unordered pair: each pair is evaluated once "
+                                               "and applied to both spheres",
+                        "peak_source": "measured in this run: %s probe (dem_probe_peak) on %d SMs, "
+                                       "median SM clock %s MHz during the probes"
+                                       % (probes["fp32_peak_form"], probes["sm_count"],
+                                          probes["clocks"].get("sm_mhz"))},
+           "peaks_measured": probes,
            "clocks": ck}
     if rank == 0 and not args.no_fp64:
         out["fp64_path"] = run_fp64(dem, W, steps=3)
@@ -673,8 +668,6 @@ def run_ours(args):
         out["e2_collapse"] = run_e2_collapse(dem, W)
     if rank == 0 and not args.no_tree:
         out["tree_gravity"] = run_tree_gravity(dem, W)
-    if rank == 0 and not args.no_analysis:
-        out["analysis"] = run_analysis(dem, W)
     if not args.no_e2e:
         e = run_e2e(dem, W, ic, p, steps=args.steps)
         e_t = max_over_ranks(ic.n_sph * args.steps / e["value"], ws, device="cuda")
@@ -715,8 +708,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic (seeded generator, no dataset)", "config": workload_config(ic),
-           "cpu_baseline": cb,
+           "data": "synthetic (seeded generator, no dataset)",
+           "config": workload_config(ic, precision="fp64 (the oracle)"), "cpu_baseline": cb,
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -755,6 +748,16 @@ def run_tree_only(args):
           flush=True)
 
 
+def run_probe_only(args):
+    import torch
+    from paper_2311_11322_gb300 import dem
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    dem.load()
+    print(json.dumps({"part": "probe", "peaks_measured": run_probes(dem)}), flush=True)
+
+
 def run_analysis_only(args):
     import torch
     from paper_2311_11322_gb300 import dem
@@ -763,16 +766,6 @@ def run_analysis_only(args):
     __graft_entry__.build()
     torch.cuda.set_device(0)
     print(json.dumps({"part": "analysis", "analysis": run_analysis(dem, W)}), flush=True)
-
-
-def run_analysis_sweep_only(args):
-    import torch
-    from paper_2311_11322_gb300 import dem
-    from paper_2311_11322_gb300 import workloads as W
-    import __graft_entry__
-    __graft_entry__.build()
-    torch.cuda.set_device(0)
-    print(json.dumps({"part": "analysis-sweep", "analysis_sweep": run_analysis_sweep(dem, W)}), flush=True)
 
 
 if __name__ == "__main__":
@@ -787,7 +780,7 @@ if __name__ == "__main__":
         run_tree_only(a)
     elif a.part == "analysis":
         run_analysis_only(a)
-    elif a.part == "analysis-sweep":
-        run_analysis_sweep_only(a)
+    elif a.part == "probe":
+        run_probe_only(a)
     else:
         run_ours(a)
