@@ -76,6 +76,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-e2-collapse", action="store_true")
     ap.add_argument("--no-tree", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--part", default="all", choices=["all", "contact", "e2", "tree", "analysis", "probe"],
                     help="contact: only the contact-pass roofline on the 1M-sphere lattice; "
                          "e2: only the paper's 2e4-sphere profiling collapse; "
@@ -465,6 +466,32 @@ def run_serving(dem, W, n_req=24, steps=2000, n_hi=20000, theta=0.0, rate=4.0):
     return st
 
 
+def run_accuracy(dem, W):
+    """100 steps of collapse-100k, mixed and all-FP64, side by side with the FP64
+    oracle's stored 100-step trajectory (tests/golden, written by a script that
+    calls only the oracle): per-step condition-relative and |X|-relative force
+    and torque errors of 256 sampled aggregates, COM and quaternion deviations."""
+    from tests.parity_util import ic_fingerprint, summarize_trajectory, trajectory_errors
+    path = os.path.join(ROOT, "tests", "golden", "collapse100k_100steps.npz")
+    if not os.path.exists(path):
+        return {"unavailable": "stored oracle trajectory missing"}
+    gold = np.load(path)
+    out = {"reference": "FP64 oracle, 100 full steps of the same workload, 256 sampled aggregates",
+           "bound": {"mixed": 1e-5, "fp64": 1e-9},
+           "measure": "condition-relative: |X_gpu - X_oracle| / sum of the magnitudes of the summed "
+                      "terms; abs_rel: / |X_oracle|"}
+    for name, prec in (("mixed", W.PRECISION_MIXED), ("fp64", W.PRECISION_FP64)):
+        ic, p = W.config2(0, precision=prec)
+        if ic_fingerprint(ic) != str(gold["fingerprint"]):
+            out[name] = {"unavailable": "input generator differs from the stored run"}
+            continue
+        with dem.World() as w:
+            pid = w.add_pile(ic, p)
+            rows = trajectory_errors(w, pid, gold)
+        out[name] = summarize_trajectory(rows)
+    return out
+
+
 def run_e2e(dem, W, ic, p, steps):
     """Through the public API with pinned host buffers: add the pile (host->device
     copy of the initial conditions), then per step dem_step + read the COMs back."""
@@ -639,6 +666,8 @@ def run_ours(args):
                                           probes["clocks"].get("sm_mhz"))},
            "peaks_measured": probes,
            "clocks": ck}
+    if rank == 0 and not args.no_accuracy:
+        out["accuracy_collapse100k"] = run_accuracy(dem, W)
     if rank == 0 and not args.no_fp64:
         out["fp64_path"] = run_fp64(dem, W, steps=3)
         out["fp64_path"]["mixed_over_fp64"] = value / ws / out["fp64_path"]["value"]

@@ -134,3 +134,62 @@ def resynced_steps(world, pid, pile, steps, tol, K, r_ref=1.0):
         worst["contacts"] = max(worst["contacts"], ns)
         assert worst["F"] <= tol and worst["N"] <= tol, f"step {k + 1}: {worst}"
     return worst
+
+
+def ic_fingerprint(ic) -> str:
+    """SHA-256 of the initial conditions (counts, positions, radii, densities)."""
+    import hashlib
+    h = hashlib.sha256()
+    for a in (ic.counts.astype(np.int32), ic.pos.astype(np.float64), ic.radius.astype(np.float64),
+              ic.density.astype(np.float64)):
+        h.update(np.ascontiguousarray(a).tobytes())
+    return h.hexdigest()
+
+
+def trajectory_errors(world, pid, gold, steps=None):
+    """Step a GPU pile side by side with a stored oracle trajectory (the npz
+    written by tests/golden/make_collapse100k_trajectory.py) and return per-step
+    errors of the sampled aggregates: condition-relative (error / sum of the
+    magnitudes of the summed terms) and |X|-relative (error / |X_oracle|)
+    maxima and 99th percentiles of F_A and N_A, and every `pose_every` steps
+    the largest COM deviation (m) and quaternion deviation."""
+    idx = gold["sample"]
+    n = int(steps or gold["F"].shape[0])
+    every = int(gold["pose_every"])
+    rows = []
+    for k in range(n):
+        world.step(1)
+        F = world.read(pid, "FORCE")[idx]
+        N = world.read(pid, "TORQUE")[idx]
+        dF = np.linalg.norm(F - gold["F"][k], axis=1)
+        dN = np.linalg.norm(N - gold["N"][k], axis=1)
+        cF = dF / np.maximum(gold["scaleF"][k], 1e-300)
+        cN = dN / np.maximum(gold["scaleN"][k], 1e-300)
+        xF = dF / np.maximum(np.linalg.norm(gold["F"][k], axis=1), 1e-300)
+        xN = dN / np.maximum(np.linalg.norm(gold["N"][k], axis=1), 1e-300)
+        r = {"step": k + 1, "F_cond_max": float(cF.max()), "F_cond_p99": float(np.quantile(cF, 0.99)),
+             "N_cond_max": float(cN.max()), "N_cond_p99": float(np.quantile(cN, 0.99)),
+             "F_abs_rel_max": float(xF.max()), "F_abs_rel_p99": float(np.quantile(xF, 0.99)),
+             "N_abs_rel_max": float(xN.max()), "N_abs_rel_p99": float(np.quantile(xN, 0.99)),
+             "oracle_contacts": int(gold["n_pairs"][k])}
+        if (k + 1) % every == 0:
+            j = (k + 1) // every - 1
+            com = world.read(pid, "COM")[idx]
+            q = world.read(pid, "QUAT")[idx]
+            r["com_dev_m"] = float(np.abs(com - gold["com"][j]).max())
+            r["quat_dev"] = float(np.minimum(np.abs(q - gold["quat"][j]).max(1),
+                                             np.abs(q + gold["quat"][j]).max(1)).max())
+        rows.append(r)
+    return rows
+
+
+def summarize_trajectory(rows):
+    keys = [k for k in rows[0] if k not in ("step", "oracle_contacts")]
+    out = {}
+    for k in keys + ["com_dev_m", "quat_dev"]:
+        vals = [r[k] for r in rows if k in r]
+        if vals:
+            out[k] = max(vals)
+    out["steps"] = len(rows)
+    out["oracle_contacts_max"] = max(r["oracle_contacts"] for r in rows)
+    return out
