@@ -100,6 +100,8 @@ def test_gravity_noalloc_edge_sizes_against_oracle(n):
     agg = (np.arange(n) // 2).astype(np.int32)          # pairs of spheres share an aggregate
     G, eps = W.G_SI, 0.5
     rows = np.arange(n) if n < 5000 else np.sort(rng.choice(n, 2000, replace=False))
+    # the entry point takes FP32 positions: the oracle sees the same rounded inputs
+    pos = pos.astype(np.float32).astype(np.float64)
     ref, fmag = oracle.gravity(pos, m, agg, G, eps, exclude_same_agg=True, rows=rows, want_mag=True)
     pm = np.concatenate([pos.astype(np.float32), m.astype(np.float32)[:, None]], 1)
     dev = torch.device("cuda", torch.cuda.current_device())
