@@ -471,7 +471,7 @@ def run_accuracy(dem, W):
     oracle's stored 100-step trajectory (tests/golden, written by a script that
     calls only the oracle): per-step condition-relative and |X|-relative force
     and torque errors of 256 sampled aggregates, COM and quaternion deviations."""
-    from tests.parity_util import ic_fingerprint, summarize_trajectory, trajectory_errors
+    from tests.parity_util import same_inputs, summarize_trajectory, trajectory_errors
     path = os.path.join(ROOT, "tests", "golden", "collapse100k_100steps.npz")
     if not os.path.exists(path):
         return {"unavailable": "stored oracle trajectory missing"}
@@ -482,7 +482,7 @@ def run_accuracy(dem, W):
                       "terms; abs_rel: / |X_oracle|"}
     for name, prec in (("mixed", W.PRECISION_MIXED), ("fp64", W.PRECISION_FP64)):
         ic, p = W.config2(0, precision=prec)
-        if ic_fingerprint(ic) != str(gold["fingerprint"]):
+        if not same_inputs(ic, gold):
             out[name] = {"unavailable": "input generator differs from the stored run"}
             continue
         with dem.World() as w:

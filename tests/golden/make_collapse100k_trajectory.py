@@ -42,6 +42,16 @@ def fingerprint(ic) -> str:
     return h.hexdigest()
 
 
+def describe(ic) -> dict:
+    """Descriptors of the initial conditions that survive a change of machine
+    (the generator's floating-point results may differ there in the last bit):
+    the shape counts exactly, sums of positions, squared positions, radii and
+    densities to be compared within 1e-12 relative."""
+    return {"counts_sha256": np.array(hashlib.sha256(ic.counts.astype(np.int32).tobytes()).hexdigest()),
+            "pos_sum": ic.pos.sum(0), "pos_sq_sum": (ic.pos ** 2).sum(0),
+            "radius_sum": np.array(ic.radius.sum()), "density_sum": np.array(ic.density.sum())}
+
+
 def sample_aggregates(n_agg: int) -> np.ndarray:
     return np.sort(np.random.default_rng(20231120).choice(n_agg, N_SAMPLE, replace=False))
 
@@ -75,9 +85,25 @@ def main():
         print(f"step {k + 1}: {time.time() - t0:.0f} s", flush=True)
     np.savez_compressed(OUT, fingerprint=np.array(fingerprint(ic)), sample=idx, dt=np.array(p.dt),
                         F=F, N=N, scaleF=sF, scaleN=sN, n_pairs=npairs, com=com, quat=quat,
-                        pose_every=np.array(POSE_EVERY), oracle_threads=np.array(oracle.threads()))
+                        pose_every=np.array(POSE_EVERY), oracle_threads=np.array(oracle.threads()),
+                        **describe(ic))
     print("wrote", OUT, flush=True)
 
 
+def add_descriptors():
+    """Add the input descriptors to a stored trajectory written before they
+    existed (the oracle's values are kept as they are)."""
+    from paper_2311_11322_gb300 import workloads as W
+    ic, _ = W.config2(0)
+    old = dict(np.load(OUT))
+    assert str(old["fingerprint"]) == fingerprint(ic), "stored run is of other inputs"
+    old.update(describe(ic))
+    np.savez_compressed(OUT, **old)
+    print("descriptors added to", OUT, flush=True)
+
+
 if __name__ == "__main__":
-    main()
+    if "--add-descriptors" in sys.argv:
+        add_descriptors()
+    else:
+        main()

@@ -61,16 +61,15 @@ def test_skin_and_cell_size_do_not_change_results(dem, prec):
     assert 1 <= reb[0.3] < reb[0.01]
 
 
-def test_overflowing_hit_lists_do_not_change_results(dem):
-    """A violently overlapping cluster whose candidate lists overflow (more than
-    24 candidates for some spheres): those spheres search their cells again
-    every step, taking partners in the same order, so results still do not
-    depend on the skin."""
+def test_long_candidate_lists_do_not_change_results(dem):
+    """A violently overlapping cluster with more than 24 candidates for some
+    spheres (long lists, many pairs per tile): results still do not depend on
+    the skin."""
     ic, p = W.random_cluster(5, n_agg=120, box=5.0, precision=W.PRECISION_MIXED)
     agg = np.repeat(np.arange(len(ic.counts)), ic.counts)
     d = np.linalg.norm(ic.pos[:, None] - ic.pos[None], axis=2)
     near = (d < ic.radius[:, None] + ic.radius[None]) & (agg[:, None] != agg[None])
-    assert near.sum(1).max() > 24         # some lists overflow at the first step
+    assert near.sum(1).max() > 24         # long lists at the first step
     ref, info0 = _run(dem, ic, p, 40, skin=0.0)
     got, info = _run(dem, ic, p, 40, skin=0.5)
     assert info0["rebuilds"] == 40
@@ -116,3 +115,27 @@ def test_batched_piles_rebuild_independently(dem):
             assert np.array_equal(w.read(pid, "TORQUE"), tq)
             assert w.info(pid)["rebuilds"] == nreb
         assert w.info(ids[0])["rebuilds"] > w.info(ids[1])["rebuilds"]
+
+
+@pytest.mark.parametrize("prec", [W.PRECISION_FP64, W.PRECISION_MIXED])
+def test_inbox_ranges_do_not_change_results(dem, prec):
+    """Each contact tile evaluates the pairs inside it once and shares both
+    halves through its inbox; tiles whose lists do not fit are split into
+    sphere ranges, and pairs between ranges are evaluated by both.  Forcing
+    small ranges (most pairs then cross) must give bit-identical states,
+    forces and histories: every pair's shares come from the same canonical
+    evaluation and every sphere sums them in partner order."""
+    ic, p = W.dense_lattice(n_spheres=4000, seed=3, precision=prec, speed=0.01)
+    res = []
+    for cap in (2560, 96, 40):
+        with dem.World() as w:
+            w.set_tuning("contact_inbox", cap)
+            assert w.get_tuning("contact_inbox") == cap
+            pid = w.add_pile(ic, p)
+            w.step(30)
+            w.sync()
+            res.append({f: w.read(pid, f) for f in FIELDS})
+    assert res[0]["CONTACTS"][:, 0].sum() > 10_000
+    for got in res[1:]:
+        for f in FIELDS:
+            assert np.array_equal(got[f], res[0][f]), f

@@ -539,10 +539,10 @@ def test_tree_gravity_deterministic_and_batched(dem):
 
 @pytest.mark.parametrize("prec", PRECS)
 def test_pair_forces_bitwise_opposite(dem, prec):
-    """Each sphere evaluates a pair taking itself as sphere a; the two evaluations
-    must give bitwise opposite forces (Newton's third law exactly) and the same
-    tangential displacement in the contact history (reported from the lower
-    index's side), with unequal radii, an oblique approach, spin and friction."""
+    """One evaluation of each pair gives both spheres' shares: bitwise opposite
+    forces (Newton's third law exactly) and one tangential displacement in the
+    contact history (reported from the lower index's side for both rows), with
+    unequal radii, an oblique approach, spin and friction."""
     ic = W.tiny_pair(s1=1.0, s2=0.7, gap=-0.02, v=0.05, b=0.2)
     ic.omega = np.array([[0.01, -0.02, 0.03], [-0.03, 0.01, 0.02]])
     p = W.calibrate(ic, v_max=0.05, r_med=0.85, precision=prec, mu_r=0.1, mu_t=0.05).replace(G=0.0)

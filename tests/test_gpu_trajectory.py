@@ -6,7 +6,7 @@ aggregates, with the sums of the magnitudes of the summed terms, and every 10
 steps their COM and orientation) is stored in tests/golden/ by
 make_collapse100k_trajectory.py, which calls only the oracle; running the
 oracle here would take ~7 minutes of host time.  Both sides start from the
-same seeded initial conditions (checked by a fingerprint) and run side by side
+same seeded initial conditions (checked by their descriptors) and run side by side
 without re-synchronisation.  Bound: condition-relative error 1e-5 (mixed) and
 1e-9 (FP64) at every step; the |X|-relative errors are computed alongside.
 """
@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 from paper_2311_11322_gb300 import workloads as W
-from tests.parity_util import TOL, ic_fingerprint, summarize_trajectory, trajectory_errors
+from tests.parity_util import TOL, same_inputs, summarize_trajectory, trajectory_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -38,8 +38,8 @@ def dem():
 def test_collapse100k_100_steps_against_oracle_trajectory(dem, prec):
     gold = np.load(GOLD)
     ic, p = W.config2(0, precision=prec)
-    assert ic_fingerprint(ic) == str(gold["fingerprint"]), "input generator differs from the stored run"
-    assert p.dt == float(gold["dt"])
+    assert same_inputs(ic, gold), "input generator differs from the stored run"
+    assert p.dt == pytest.approx(float(gold["dt"]), rel=1e-12)
     with dem.World() as w:
         pid = w.add_pile(ic, p)
         rows = trajectory_errors(w, pid, gold)
