@@ -255,6 +255,11 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
  * directly; 0 = direct sum, the default), "grav_order" (highest multipole
  * rank of the tree's accepted cells: 4, the default, or 2 -- monopole and
  * quadrupole only, cheaper per cell and less accurate),
+ * "contact_inbox" (list entries a contact tile evaluates together through
+ * its shared-memory inbox, 1..2560, default 2560 (the FP64 path uses at most
+ * 1280); tiles with more entries are split into sphere ranges that fit, and
+ * pairs across ranges are evaluated from both sides: results are bitwise the
+ * same for every value, only the speed changes),
  * "cell_factor" (cell edge / (2 x
  * largest radius), >= 1), "skin" (neighbour-list skin as a fraction of the
  * pile's largest radius, in [0, 4], default 0.1; 0 = search contacts afresh

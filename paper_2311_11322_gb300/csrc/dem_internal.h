@@ -21,7 +21,31 @@ constexpr int kMaxK = 64;          // largest max_contacts
 constexpr int kScanTile = 2048;    // cells per scan block (256 threads x 8)
 constexpr int kAggChunk = 512;     // aggregates per pile-reduction block
 constexpr int kPartialDoubles = 16;
-constexpr int kHitCap = 24;        // contact candidates listed per sphere (more: searched again)
+// Contact pass: tiles of consecutive sorted spheres, one block each; the
+// candidate lists of a pile hold kEntPerSphere entries per sphere on average
+// at the default skin (more for larger skins, in proportion to the candidate
+// volume; a pile whose lists need more is flagged DEM_FLAG_SLOTS and frozen);
+// a tile with at most kInboxCap list entries evaluates each of its inner pairs
+// once and passes the partner's share through shared memory.
+constexpr int kCTile = 256;
+constexpr int kEntPerSphere = 32;
+constexpr int kInboxCap = 2560;
+
+// Cell index of wrapped cell coordinates (cx, cy, cz) on an nx x ny x nz grid:
+// bricks of 4 x 4 x 4 cells in row-major brick order, row-major inside a brick
+// (x fastest).  Consecutive sorted spheres then fill compact blocks of space,
+// and the three x-neighbours of a cell are consecutive unless a brick
+// boundary falls between them.  The grid has ceil(n/4)*4 cells per axis.
+__host__ __device__ __forceinline__ int64_t cell_id(int cx, int cy, int cz, int nx, int ny)
+{
+    const int64_t nbx = (nx + 3) >> 2, nby = (ny + 3) >> 2;
+    const int64_t brick = ((int64_t)(cz >> 2) * nby + (cy >> 2)) * nbx + (cx >> 2);
+    return (brick << 6) | (((cz & 3) << 4) | ((cy & 3) << 2) | (cx & 3));
+}
+__host__ __device__ __forceinline__ int64_t cell_count(int nx, int ny, int nz)
+{
+    return (int64_t)((nx + 3) >> 2) * ((ny + 3) >> 2) * ((nz + 3) >> 2) * 64;
+}
 
 // Static description of one pile (host-owned; re-uploaded on membership change).
 struct PileStatic {
@@ -37,6 +61,13 @@ struct PileStatic {
     double ext_mass, M_total;
     double spin_inc[3];
     double rot_tol;        // 0: RK4 rotation; > 0: adaptive RK5(4) tolerance
+    // contact lists: entry range [e0, e0 + ne) and tile range [ct0, ct0 + nct);
+    // mixed path: fixed-point position quantum q = 2^qexp (m) and the skin in
+    // quanta (the exact integer candidate test)
+    int64_t e0, ne, ct0, nct;
+    int32_t qexp;
+    int32_t pad_q;
+    int64_t skin_q;
     // tree gravity (0 levels = direct sum): depth, opening angle, node and leaf ranges
     int32_t tD;
     float theta;
@@ -52,8 +83,8 @@ struct PileDyn {
     int32_t flags;            // DEM_FLAG_* bits
     int32_t parity;           // history buffer holding the previous contacts
     int32_t failed;           // frozen after a fatal flag
-    int32_t rebuild;          // this step rebuilds the cell list and hit lists
-    int32_t hit_overflow;     // a hit list overflowed: rebuild again next step
+    int32_t rebuild;          // this step rebuilds the cell list and candidate lists
+    int32_t cpar;             // candidate-list buffer of the current lists
     int32_t rebuilds;         // number of rebuilds so far
 };
 
@@ -102,11 +133,24 @@ struct Arrays {
     int32_t *rank;       // rank among spheres counted into the same cell
     int32_t *sorted;     // sorted position (pile-local) -> home index (pile-local)
     // sorted copies for the contact pass
-    float4 *sph_, *spl_, *sv_, *sw_;   // mixed: pos hi (+s hi), pos lo (+s lo), vel (+agg), spin (+gid)
-    dbl4 *dp_, *dv_, *dw_;          // fp64: pos (+s), vel (+agg), spin (+gid)
+    int4 *xq;                       // mixed: low 32 bits of round((r_i - O) / q) per axis, round(radius / q)
+    float4 *xr;                     // mixed: what those roundings left (in quanta, |.| <= 1/2)
+    float4 *sph_, *sv_, *sw_;       // mixed: pos hi (+s hi; rebuild steps only), vel (+agg), spin (+home id)
+    dbl4 *dp_, *dv_, *dw_;          // fp64: pos (+s), vel (+agg), spin (+home id)
     int32_t *sagg;                  // aggregate (pile-local) of each sorted position
-    int32_t *hits;                  // contact candidates, slot-major per pile like the history
-    int32_t *hitn;                  // number of candidates of each sorted position
+    // candidate lists (compressed rows per sorted sphere, entries in the
+    // order of the partners' home indices), double-buffered by PileDyn::cpar
+    // so that a rebuild can carry the history over from the previous lists:
+    // ccnt/coff per sorted position (coff pile-local into the pile's entries),
+    // cand per entry (partner sorted position | owner bit << 31, entry of this
+    // sphere in the partner's list), cand_id per entry (partner home index)
+    int32_t *ccnt[2], *coff[2];
+    int2 *cand[2];
+    int32_t *cand_id[2];
+    // contact tiles: (pile slot, first sorted position, spheres, 0); entries
+    // of each tile and their pile-local base (rebuild steps)
+    int4 *ctile;
+    int32_t *ctile_cnt, *ctile_base;
     // gravity inputs / outputs
     float4 *gpos32;      // mixed: pos hi (+mass)
     dbl4 *gpos64;     // fp64: pos (+mass)
@@ -116,12 +160,12 @@ struct Arrays {
     dbl4 *ftc64;
     // sorted position (pile-local) of each home sphere, double-buffered by parity
     int32_t *pos_of_home[2];
-    // contact history in sorted order, double-buffered by pile parity.  Slots
-    // are slot-major inside each pile: slot t of the sphere at pile-local
-    // sorted position k is element s0*K + t*ns + k; counts hist_n[s0 + k].
-    float4 *hist32[2];
-    dbl4 *hist64[2];
-    int32_t *hist_n[2];
+    // contact history per candidate-list entry of the pair's owner (its lower
+    // home index): S from the owner's side and 1 in .w while the pair is in
+    // contact, double-buffered by pile parity; *_rm: the previous history
+    // carried over to new lists at a rebuild
+    float4 *hist32[2], *hist32_rm;
+    dbl4 *hist64[2], *hist64_rm;
     // aggregates
     int32_t *agg_first, *agg_count, *agg_pile;
     double *M, *I, *Iinv;          // [A], [A][9], [A][9]
@@ -170,11 +214,13 @@ struct Arrays {
 
 struct Sizes {
     int64_t N, A, C, T, CH, P, GI, GP;
+    int64_t CT, E;   // contact tiles and candidate-list entries of all piles
     int64_t GB;   // blocks of the persistent gravity grid (0 = one block per item)
     int64_t TN, TL, TG;   // tree nodes, leaves and 32-sphere groups of all piles (TN = 0: direct sum)
     int32_t K;    // history slots per sphere (world-wide)
     int32_t adapt;   // some pile integrates rotation with the adaptive RK5(4)
     int32_t gtile;   // spheres per tile of the symmetric gravity form (512, or 128 in the mixed path)
+    int32_t icap;    // contact inbox entries used per tile range (<= the kernel's capacity)
 };
 
 // ---- kernel launchers (kernels_*.cu) -------------------------------------

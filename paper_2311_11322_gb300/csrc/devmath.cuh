@@ -94,6 +94,25 @@ struct FFSum {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// Low 32 bits of round((hi + lo) x 2^e), the float-float value scaled by a
+// power of two (exact) and rounded to an integer: hi is rounded first (exact
+// in 64-bit integers below 2^63), the remainder (hi - round(hi)) + lo is
+// rounded second.  Two's-complement wrap-around keeps differences of nearby
+// values exact.
+// The remainder (hi + lo) x 2^e - round(...) goes to rem (|rem| <= 1/2).
+__device__ __forceinline__ int ff_to_fixed(ff v, int e, float &rem)
+{
+    const float sc = __int_as_float((e + 127) << 23);   // 2^e
+    const float h = __fmul_rn(v.hi, sc), l = __fmul_rn(v.lo, sc);
+    const float hr = rintf(h);
+    const long long i1 = __float2ll_rn(hr);
+    const float t = __fadd_rn(__fsub_rn(h, hr), l);
+    const float tr = rintf(t);
+    rem = __fsub_rn(t, tr);
+    const int i2 = __float2int_rn(tr);
+    return (int)(unsigned)((unsigned long long)i1 + (unsigned long long)(long long)i2);
+}
+
 // Split a double into hi + lo floats.
 __host__ __device__ __forceinline__ void split_d(double x, float &hi, float &lo)
 {

@@ -353,9 +353,11 @@ __device__ void pile_finalize_block(const Arrays &a, int p, double (&sh)[7][128]
         D.steps += 1;
         D.parity ^= 1;
         if (D.flags & (DEM_FLAG_SLOTS | DEM_FLAG_NONFINITE)) D.failed = 1;
-        if (D.rebuild) D.rebuilds += 1;
-        D.rebuild = (S.skin <= 0.0 || D.hit_overflow) ? 1 : 0;
-        D.hit_overflow = 0;
+        if (D.rebuild) {
+            D.rebuilds += 1;
+            D.cpar ^= 1;   // the lists built this step become the current ones
+        }
+        D.rebuild = S.skin <= 0.0 ? 1 : 0;
     }
 }
 
@@ -499,7 +501,7 @@ __global__ void k_keys(Arrays a, Sizes z)
         a.gpos32[i] = make_float4(px.hi, py.hi, pz.hi, (float)a.m64[i]);
     }
     if (!a.pd[p].rebuild) return;   // cell list kept from the last rebuild
-    int key = (cz * S.ny + cy) * S.nx + cx;
+    const int key = (int)cell_id(cx, cy, cz, S.nx, S.ny);
     a.key[i] = key;
     a.rank[i] = atomicAdd(a.ccount + S.c0 + key, 1);
 }
@@ -735,8 +737,16 @@ __global__ void k_gather(Arrays a, Sizes z)
                        rec.Rh[6] * bh.x + rec.Rh[7] * bh.y + rec.Rh[8] * bh.z);
         float3 w = f3(rec.w[0], rec.w[1], rec.w[2]);
         float3 v = f3(rec.vb[0], rec.vb[1], rec.vb[2]) + cross(w, rb);
-        a.sph_[k] = make_float4(px.hi, py.hi, pz.hi, bh.w);
-        a.spl_[k] = make_float4(px.lo, py.lo, pz.lo, bl.w);
+        // fixed point in quanta q = 2^qexp: low 32 bits of round((r_i - O) / q)
+        // per axis (differences of nearby spheres are exact int32) and
+        // round(radius / q), with what the rounding left in FP32
+        const int e = -S.qexp;
+        float4 rm;
+        const int X = ff_to_fixed(px, e, rm.x), Y = ff_to_fixed(py, e, rm.y), Z = ff_to_fixed(pz, e, rm.z);
+        const int Sr = ff_to_fixed(ff{bh.w, bl.w}, e, rm.w);
+        a.xq[k] = make_int4(X, Y, Z, Sr);
+        a.xr[k] = rm;
+        if (a.pd[p].rebuild) a.sph_[k] = make_float4(px.hi, py.hi, pz.hi, bh.w);
         a.sv_[k] = make_float4(v.x, v.y, v.z, __int_as_float(al));
         a.sw_[k] = make_float4(w.x, w.y, w.z, __int_as_float(hl));
     }

@@ -28,7 +28,7 @@ struct Range {
     Range &operator=(const Range &) = delete;
 };
 
-enum Cls { C_SPH, C_SPHK, C_SPHL, C_AGG, C_CELL, C_TILE, C_CHUNK, C_PILE, C_GITEM, C_GPART, C_TNODE,
+enum Cls { C_SPH, C_ENT, C_CTILE, C_AGG, C_CELL, C_TILE, C_CHUNK, C_PILE, C_GITEM, C_GPART, C_TNODE,
            C_TLEAF, C_TSPH, C_NCLS };
 
 struct Field {
@@ -41,6 +41,7 @@ struct Field {
 struct PileHost {
     int32_t id;
     int64_t ns, na, nc, nch, nt;
+    int64_t ne;            // candidate-list entries (never shrinks)
     int nx, ny, nz;
     double cell, smax;
     double ext[3];         // extent of the wrapped grid at creation (cell x dims)
@@ -85,6 +86,7 @@ struct dem_world {
     int sm_count = 0;
     double cell_factor = 1.0;
     double skin_frac = 0.1;           // neighbour-list skin / largest radius
+    int contact_inbox = kInboxCap;    // contact inbox entries per tile range (testing: smaller splits more)
     // flags readback
     PileDyn *h_dyn = nullptr;   // pinned
     int64_t h_dyn_cap = 0;
@@ -152,6 +154,17 @@ double skin_of(const dem_world *w, const PileHost &q)
     return std::max(0.0, std::min(want, room));
 }
 
+// Candidate-list entries of a pile: kEntPerSphere per sphere at the default
+// skin (0.1 of the largest radius), scaled by the candidate volume
+// ((2 + skin) / 2.1)^3 for larger skins; a pile's capacity never shrinks, so
+// offsets of lists built earlier stay inside it.
+void size_lists(const dem_world *w, PileHost &q)
+{
+    const double f = std::max(1.0, std::pow((2.0 + w->skin_frac) / 2.1, 3.0));
+    const int64_t per = (int64_t)std::ceil(kEntPerSphere * f);
+    q.ne = std::max<int64_t>(q.ne, q.ns * per);
+}
+
 void build_fields(dem_world *w)
 {
     Arrays &a = w->A;
@@ -167,11 +180,18 @@ void build_fields(dem_world *w)
     add((void **)&a.rank, C_SPH, 4, false);
     add((void **)&a.sorted, C_SPH, 4, false);
     add((void **)&a.sagg, C_SPH, 4, false);
-    add((void **)&a.hits, C_SPHL, 4, false);
-    add((void **)&a.hitn, C_SPH, 4, false);
     add((void **)&a.fg, C_SPH, 32, true);
-    add((void **)&a.hist_n[0], C_SPH, 4, true);
-    add((void **)&a.hist_n[1], C_SPH, 4, true);
+    // candidate lists (both buffers: a rebuild after a layout change reads the
+    // previous ones) and contact tiles
+    for (int b = 0; b < 2; ++b) {
+        add((void **)&a.ccnt[b], C_SPH, 4, true);
+        add((void **)&a.coff[b], C_SPH, 4, true);
+        add((void **)&a.cand[b], C_ENT, 8, true);
+        add((void **)&a.cand_id[b], C_ENT, 4, true);
+    }
+    add((void **)&a.ctile, C_CTILE, 16, false);
+    add((void **)&a.ctile_cnt, C_CTILE, 4, false);
+    add((void **)&a.ctile_base, C_CTILE, 4, false);
     add((void **)&a.pos_of_home[0], C_SPH, 4, true);
     add((void **)&a.pos_of_home[1], C_SPH, 4, true);
     if (d) {
@@ -180,20 +200,23 @@ void build_fields(dem_world *w)
         add((void **)&a.dw_, C_SPH, 32, false);
         add((void **)&a.gpos64, C_SPH, 32, false);
         add((void **)&a.ftc64, C_SPH, 64, true);
-        add((void **)&a.hist64[0], C_SPHK, 32, true);
-        add((void **)&a.hist64[1], C_SPHK, 32, true);
+        add((void **)&a.hist64[0], C_ENT, 32, true);
+        add((void **)&a.hist64[1], C_ENT, 32, true);
+        add((void **)&a.hist64_rm, C_ENT, 32, false);
         add((void **)&a.rec64, C_AGG, sizeof(AggRec64), false);
     } else {
         add((void **)&a.bh, C_SPH, 16, true);
         add((void **)&a.bl, C_SPH, 16, true);
+        add((void **)&a.xq, C_SPH, 16, false);
+        add((void **)&a.xr, C_SPH, 16, false);
         add((void **)&a.sph_, C_SPH, 16, false);
-        add((void **)&a.spl_, C_SPH, 16, false);
         add((void **)&a.sv_, C_SPH, 16, false);
         add((void **)&a.sw_, C_SPH, 16, false);
         add((void **)&a.gpos32, C_SPH, 16, false);
         add((void **)&a.ftc32, C_SPH, 32, true);
-        add((void **)&a.hist32[0], C_SPHK, 16, true);
-        add((void **)&a.hist32[1], C_SPHK, 16, true);
+        add((void **)&a.hist32[0], C_ENT, 16, true);
+        add((void **)&a.hist32[1], C_ENT, 16, true);
+        add((void **)&a.hist32_rm, C_ENT, 16, false);
         add((void **)&a.rec32, C_AGG, sizeof(AggRecMixed), false);
         add((void **)&a.I32, C_AGG, 72, true);
     }
@@ -256,8 +279,8 @@ int64_t pile_count(const dem_world *w, const PileHost &q, Cls c)
 {
     switch (c) {
     case C_SPH: return q.ns;
-    case C_SPHK: return q.ns * w->K;
-    case C_SPHL: return q.ns * kHitCap;
+    case C_ENT: return q.ne;
+    case C_CTILE: return (q.ns + kCTile - 1) / kCTile;
     case C_AGG: return q.na;
     case C_CELL: return q.nc;
     case C_TILE: return q.nt;
@@ -432,7 +455,7 @@ dem_status relayout(dem_world *w, const std::vector<PileHost> &newp, const GravP
             if (w->piles[o].id == newp[k].id) from[k] = (int)o;
     bool moved = grow || newp.size() < w->piles.size();
     for (size_t k = 0; k < newp.size() && !moved; ++k)
-        if (from[k] >= 0 && from[k] != (int)k) moved = true;
+        if (from[k] >= 0 && (from[k] != (int)k || newp[k].ne != w->piles[from[k]].ne)) moved = true;
     if (!moved) {
         // only the transient classes may need new capacity (none grew)
         return DEM_OK;
@@ -453,9 +476,11 @@ dem_status relayout(dem_world *w, const std::vector<PileHost> &newp, const GravP
         for (size_t k = 0; k < newp.size(); ++k) {
             int64_t n = pile_count(w, newp[k], fd.cls);
             if (from[k] >= 0 && n > 0) {
+                // a class may grow for a surviving pile (its list entries): copy what it had
+                const int64_t nold = pile_count(w, w->piles[from[k]], fd.cls);
                 size_t src = (size_t)old_off[fd.cls][from[k]] * fd.el;
                 CU(cudaMemcpyAsync((char *)fresh[f] + (size_t)o * fd.el, (char *)*fd.ptr + src,
-                                   (size_t)n * fd.el, cudaMemcpyDeviceToDevice, w->stream));
+                                   (size_t)std::min(n, nold) * fd.el, cudaMemcpyDeviceToDevice, w->stream));
             }
             o += n;
         }
@@ -473,7 +498,8 @@ dem_status relayout(dem_world *w, const std::vector<PileHost> &newp, const GravP
 dem_status upload_tables(dem_world *w, const GravPlan &gp)
 {
     std::vector<PileStatic> ps;
-    int64_t s0 = 0, a0 = 0, c0 = 0, ch0 = 0, tn0 = 0, tl0 = 0, tg0 = 0;
+    std::vector<int4> ctiles;
+    int64_t s0 = 0, a0 = 0, c0 = 0, ch0 = 0, tn0 = 0, tl0 = 0, tg0 = 0, e0 = 0;
     std::vector<int32_t> tnode_pile, tleaf_pile;
     w->tree_maxD = 0;
     for (auto &q : w->piles) {
@@ -495,6 +521,19 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
         S.nx = q.nx; S.ny = q.ny; S.nz = q.nz; S.K = w->K;
         S.cell = q.cell; S.inv_cell = 1.0 / q.cell;
         S.skin = skin_of(w, q);
+        // contact lists and tiles; fixed-point quantum q = 2^qexp with
+        // 2^31 q >= 10.5 x the largest radius (depends on nothing else, so
+        // results do not depend on the cell size or the skin)
+        S.e0 = e0;
+        S.ne = pile_count(w, q, C_ENT);
+        S.ct0 = (int64_t)ctiles.size();
+        S.nct = pile_count(w, q, C_CTILE);
+        for (int64_t t = 0; t < S.nct; ++t)
+            ctiles.push_back(make_int4((int)ps.size(), (int)(t * kCTile),
+                                       (int)std::min<int64_t>(kCTile, q.ns - t * kCTile), 0));
+        e0 += S.ne;
+        S.qexp = (int32_t)std::ceil(std::log2(10.5 * q.smax)) - 31;
+        S.skin_q = (int64_t)std::llround(S.skin / std::ldexp(1.0, S.qexp));
         const dem_params &P = q.P;
         S.G = P.G; S.h = P.dt; S.kn = P.kn; S.kt = P.kt; S.cn = P.cn; S.ct = P.ct;
         S.mu_s = P.mu_s; S.mu_r = P.mu_r; S.mu_t = P.mu_t; S.w0 = P.w0;
@@ -506,6 +545,8 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
         s0 += q.ns; a0 += q.na; c0 += q.nc; ch0 += q.nch;
     }
     w->Z.N = s0; w->Z.A = a0; w->Z.C = c0; w->Z.T = c0 / kScanTile; w->Z.CH = ch0;
+    w->Z.CT = (int64_t)ctiles.size();
+    w->Z.E = e0;
     w->Z.P = (int64_t)w->piles.size();
     w->Z.GI = (int64_t)gp.items.size();
     w->Z.GP = gp.gp;
@@ -522,6 +563,7 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
         CU(cudaDeviceGetAttribute(&w->sm_count, cudaDevAttrMultiProcessorCount, dev));
     }
     w->Z.gtile = gp.tile;
+    w->Z.icap = w->contact_inbox;
     int bps = gravity_blocks_per_sm(w->precision == DEM_FP64, w->grav_block, w->grav_ib, w->grav_pack,
                                     use_sym(w), gp.tile);
     CU(cudaGetLastError());
@@ -538,6 +580,10 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     if (!gp.items.empty())
         CU(cudaMemcpyAsync(w->A.gitems, gp.items.data(), 16 * gp.items.size(),
                            cudaMemcpyHostToDevice, w->stream));
+    if (!ctiles.empty()) {
+        CU(cudaMemcpyAsync(w->A.ctile, ctiles.data(), 16 * ctiles.size(), cudaMemcpyHostToDevice, w->stream));
+        CU(cudaStreamSynchronize(w->stream));   // the host vector goes out of scope
+    }
     if (tn0 > 0) {
         CU(cudaMemcpyAsync(w->A.tnode_pile, tnode_pile.data(), 4 * tnode_pile.size(),
                            cudaMemcpyHostToDevice, w->stream));
@@ -755,13 +801,13 @@ void set_grid(const dem_world *w, PileHost &q, const double *ext, int pad)
     }
     q.cell = cell;
     q.nx = dims[0]; q.ny = dims[1]; q.nz = dims[2];
-    int64_t cells = (int64_t)q.nx * q.ny * q.nz;
+    const int64_t cells = cell_count(q.nx, q.ny, q.nz);
     q.nc = (cells + kScanTile - 1) / kScanTile * kScanTile;
     q.nt = q.nc / kScanTile;
 }
 
-// New grids for every pile (cells, hit lists and the sort are transient:
-// nothing to preserve; every pile rebuilds at its next step).
+// New grids for every pile (cells, candidate lists and the sort are rebuilt at
+// every pile's next step; the history is carried over by partner index).
 dem_status regrid(dem_world *w);
 
 void choose_grid(const dem_world *w, PileHost &q, const double *pos_rel, int64_t N)
@@ -781,7 +827,10 @@ void choose_grid(const dem_world *w, PileHost &q, const double *pos_rel, int64_t
 dem_status regrid(dem_world *w)
 {
     std::vector<PileHost> newp = w->piles;
-    for (auto &q : newp) set_grid(w, q, q.ext, 0);
+    for (auto &q : newp) {
+        set_grid(w, q, q.ext, 0);
+        size_lists(w, q);
+    }
     dem_status s = relayout(w, newp, nullptr);
     if (s != DEM_OK) return s;
     w->piles = newp;
@@ -977,6 +1026,7 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
             return fail(w, DEM_ERR_ARG, "cell_size must be >= 2 x the largest radius");
         choose_grid(w, ph, rel.data(), N);
     }
+    size_lists(w, ph);
 
     // ---- first pile fixes the world's precision and slot count ----
     bool first_pile = w->precision < 0;
@@ -1015,8 +1065,11 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     UP(D.b64 + 3 * s0, b.data(), 24 * N);
     UP(D.s64 + s0, rad, 8 * N);
     UP(D.m64 + s0, m.data(), 8 * N);
-    CU(cudaMemsetAsync(D.hist_n[0] + s0, 0, 4 * N, st));
-    CU(cudaMemsetAsync(D.hist_n[1] + s0, 0, 4 * N, st));
+    // no previous candidate lists: nothing to carry over at the first rebuild
+    CU(cudaMemsetAsync(D.ccnt[0] + s0, 0, 4 * N, st));
+    CU(cudaMemsetAsync(D.ccnt[1] + s0, 0, 4 * N, st));
+    CU(cudaMemsetAsync(D.coff[0] + s0, 0, 4 * N, st));
+    CU(cudaMemsetAsync(D.coff[1] + s0, 0, 4 * N, st));
     std::vector<int32_t> iota(N);
     for (int64_t i = 0; i < N; ++i) iota[i] = (int32_t)i;
     UP(D.pos_of_home[0] + s0, iota.data(), 4 * N);
@@ -1312,41 +1365,53 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
         break;
     }
     case DEM_FIELD_CONTACTS: {
+        // the current candidate lists (entries in partner order) and the
+        // history at each pair's owner entry (S from the lower-index sphere)
         const int K = w->K;
         CHK(need(N * (1 + 4 * (int64_t)K)));
-        int par = dyn.parity;
-        std::vector<int32_t> cnt(N), pos(N);
-        CHK(get(cnt.data(), D.hist_n[par] + s0, 4 * N));
+        const int par = dyn.parity, cp = dyn.cpar;
+        int64_t e0 = 0;
+        for (int t = 0; t < slot; ++t) e0 += pile_count(w, w->piles[t], C_ENT);
+        std::vector<int32_t> cnt(N), off(N), pos(N);
+        CHK(get(cnt.data(), D.ccnt[cp] + s0, 4 * N));
+        CHK(get(off.data(), D.coff[cp] + s0, 4 * N));
         CHK(get(pos.data(), D.pos_of_home[par] + s0, 4 * N));
-        std::fill(out, out + N * (1 + 4 * (int64_t)K), 0.0);
-        std::vector<double> slot(4 * N * K);
-        if (w->precision == DEM_FP64) {
-            std::vector<dbl4> h(N * K);
-            CHK(get(h.data(), D.hist64[par] + s0 * K, 32 * N * K));
-            for (int64_t e = 0; e < N * K; ++e) {
-                slot[4 * e] = h[e].w; slot[4 * e + 1] = h[e].x; slot[4 * e + 2] = h[e].y; slot[4 * e + 3] = h[e].z;
-            }
-        } else {
-            std::vector<float4> h(N * K);
-            CHK(get(h.data(), D.hist32[par] + s0 * K, 16 * N * K));
-            for (int64_t e = 0; e < N * K; ++e) {
-                int32_t pid;
-                std::memcpy(&pid, &h[e].w, 4);
-                slot[4 * e] = pid; slot[4 * e + 1] = h[e].x; slot[4 * e + 2] = h[e].y; slot[4 * e + 3] = h[e].z;
+        int64_t E = 0;
+        for (int64_t k = 0; k < N; ++k) E = std::max<int64_t>(E, (int64_t)off[k] + cnt[k]);
+        E = std::min<int64_t>(E, pile_count(w, q, C_ENT));
+        std::vector<int32_t> ids(E);
+        std::vector<int2> cd(E);
+        std::vector<double> hs(4 * E);
+        if (E > 0) {
+            CHK(get(ids.data(), D.cand_id[cp] + e0, 4 * E));
+            CHK(get(cd.data(), D.cand[cp] + e0, 8 * E));
+            if (w->precision == DEM_FP64) {
+                std::vector<dbl4> h(E);
+                CHK(get(h.data(), D.hist64[par] + e0, 32 * E));
+                for (int64_t f = 0; f < E; ++f) { hs[4 * f] = h[f].x; hs[4 * f + 1] = h[f].y; hs[4 * f + 2] = h[f].z; hs[4 * f + 3] = h[f].w; }
+            } else {
+                std::vector<float4> h(E);
+                CHK(get(h.data(), D.hist32[par] + e0, 16 * E));
+                for (int64_t f = 0; f < E; ++f) { hs[4 * f] = h[f].x; hs[4 * f + 1] = h[f].y; hs[4 * f + 2] = h[f].z; hs[4 * f + 3] = h[f].w; }
             }
         }
-        // each sphere keeps S from its own side (S_b = -S_a); the field reports
-        // the pair's S from the side of its lower-index sphere
+        std::fill(out, out + N * (1 + 4 * (int64_t)K), 0.0);
         for (int64_t i = 0; i < N; ++i) {
             double *o = out + i * (1 + 4 * K);
-            int64_t k = pos[i];
-            int n = cnt[k];
-            o[0] = n;
-            for (int t = 0; t < n; ++t) {
-                const double *e = &slot[4 * ((int64_t)t * N + k)];
-                const double sg = (double)i > e[0] ? -1.0 : 1.0;
-                o[1 + 4 * t] = e[0]; o[2 + 4 * t] = sg * e[1]; o[3 + 4 * t] = sg * e[2]; o[4 + 4 * t] = sg * e[3];
+            const int64_t k = pos[i];
+            int n = 0;
+            for (int e = 0; e < cnt[k]; ++e) {
+                const int64_t f = (int64_t)off[k] + e;
+                if (f >= E) break;
+                const int64_t h = cd[f].x < 0 ? f : (int64_t)cd[f].y;
+                if (h < 0 || h >= E || hs[4 * h + 3] == 0.0) continue;
+                if (n < K) {
+                    o[1 + 4 * n] = ids[f];
+                    o[2 + 4 * n] = hs[4 * h]; o[3 + 4 * n] = hs[4 * h + 1]; o[4 + 4 * n] = hs[4 * h + 2];
+                }
+                ++n;
             }
+            o[0] = std::min(n, K);
         }
         break;
     }
@@ -1419,42 +1484,90 @@ dem_status dem_write_state(dem_world *w, int32_t pile_id, int32_t field, const d
         break;
     }
     case DEM_FIELD_CONTACTS: {
+        // written as the pile's current candidate lists (one entry per
+        // contact, both spheres of a pair listing each other, partner order)
+        // with the history at the owner entries; the next step rebuilds the
+        // lists and carries S over by partner index
         const int K = w->K;
         const int64_t row = 1 + 4 * (int64_t)K;
         if (n_in < N * row) return fail(w, DEM_ERR_ARG, "input too small: need %lld doubles", (long long)(N * row));
-        const int par = dyn.parity;
-        std::vector<int32_t> pos(N), cnt(N, 0);
+        const int par = dyn.parity, cp = dyn.cpar;
+        int64_t e0 = 0;
+        for (int t = 0; t < slot; ++t) e0 += pile_count(w, w->piles[t], C_ENT);
+        const int64_t cap = pile_count(w, q, C_ENT);
+        std::vector<int32_t> pos(N), home(N);
         CU(cudaMemcpy(pos.data(), D.pos_of_home[par] + s0, 4 * N, cudaMemcpyDeviceToHost));
-        const bool d64 = w->precision == DEM_FP64;
-        std::vector<float4> h32(d64 ? 0 : N * K);
-        std::vector<dbl4> h64(d64 ? N * K : 0);
+        for (int64_t i = 0; i < N; ++i) {
+            if (pos[i] < 0 || pos[i] >= N) return fail(w, DEM_ERR_STATE, "sorted order unavailable");
+            home[pos[i]] = (int32_t)i;
+        }
+        // rows sorted by partner
+        std::vector<std::vector<std::pair<int32_t, int>>> rows(N);   // (partner, input slot)
         for (int64_t i = 0; i < N; ++i) {
             const double *e = in + i * row;
-            int n = (int)e[0];
+            const int n = (int)e[0];
             if (!(e[0] >= 0) || n > K || (double)n != e[0])
                 return fail(w, DEM_ERR_ARG, "sphere %lld: bad contact count", (long long)i);
-            int64_t k = pos[i];
-            cnt[k] = n;
             for (int t = 0; t < n; ++t) {
                 const double *sl = e + 1 + 4 * t;
-                if (!(sl[0] >= 0 && sl[0] < (double)N) || !finite_all(sl + 1, 3))
+                if (!(sl[0] >= 0 && sl[0] < (double)N) || (double)(int64_t)sl[0] != sl[0] || sl[0] == (double)i ||
+                    !finite_all(sl + 1, 3))
                     return fail(w, DEM_ERR_ARG, "sphere %lld: bad contact entry", (long long)i);
-                int64_t idx = (int64_t)t * N + k;
-                // stored from this sphere's own side (S_b = -S_a)
-                const double sg = (double)i > sl[0] ? -1.0 : 1.0;
-                if (d64) {
-                    h64[idx] = make_dbl4(sg * sl[1], sg * sl[2], sg * sl[3], sl[0]);
-                } else {
-                    int32_t pid = (int32_t)sl[0];
-                    float pf;
-                    std::memcpy(&pf, &pid, 4);
-                    h32[idx] = make_float4((float)(sg * sl[1]), (float)(sg * sl[2]), (float)(sg * sl[3]), pf);
+                rows[i].push_back({(int32_t)sl[0], t});
+            }
+            std::sort(rows[i].begin(), rows[i].end());
+            for (size_t t = 1; t < rows[i].size(); ++t)
+                if (rows[i][t].first == rows[i][t - 1].first)
+                    return fail(w, DEM_ERR_ARG, "sphere %lld: partner listed twice", (long long)i);
+        }
+        // offsets in sorted-position order
+        std::vector<int32_t> cnt(N), off(N);
+        int64_t E = 0;
+        for (int64_t k = 0; k < N; ++k) {
+            cnt[k] = (int32_t)rows[home[k]].size();
+            off[k] = (int32_t)E;
+            E += cnt[k];
+        }
+        if (E > cap) return fail(w, DEM_ERR_ARG, "too many contacts for the pile's candidate lists");
+        std::vector<int32_t> ids(E);
+        std::vector<int2> cd(E);
+        std::vector<double> hs(4 * E, 0.0);
+        for (int64_t k = 0; k < N; ++k) {
+            const int32_t i = home[k];
+            for (int e = 0; e < cnt[k]; ++e) {
+                const int64_t f = off[k] + e;
+                const int32_t J = rows[i][e].first;
+                // this pair in J's row
+                const auto &rj = rows[J];
+                auto it = std::lower_bound(rj.begin(), rj.end(), std::make_pair(i, -1));
+                if (it == rj.end() || it->first != i)
+                    return fail(w, DEM_ERR_ARG, "contact %d-%d listed by one sphere only", i, J);
+                const int64_t mir = off[pos[J]] + (it - rj.begin());
+                ids[f] = J;
+                const bool owned = i < J;
+                cd[f] = make_int2(pos[J] | (owned ? (int)0x80000000u : 0), (int)mir);
+                if (owned) {
+                    const double *sl = in + (int64_t)i * row + 1 + 4 * rows[i][e].second;
+                    hs[4 * f] = sl[1]; hs[4 * f + 1] = sl[2]; hs[4 * f + 2] = sl[3]; hs[4 * f + 3] = 1.0;
                 }
             }
         }
-        CHK(put(D.hist_n[par] + s0, cnt.data(), 4 * N));
-        if (d64) CHK(put(D.hist64[par] + s0 * K, h64.data(), 32 * N * K));
-        else CHK(put(D.hist32[par] + s0 * K, h32.data(), 16 * N * K));
+        CHK(put(D.ccnt[cp] + s0, cnt.data(), 4 * N));
+        CHK(put(D.coff[cp] + s0, off.data(), 4 * N));
+        if (E > 0) {
+            CHK(put(D.cand_id[cp] + e0, ids.data(), 4 * E));
+            CHK(put(D.cand[cp] + e0, cd.data(), 8 * E));
+            if (w->precision == DEM_FP64) {
+                std::vector<dbl4> h(E);
+                for (int64_t f = 0; f < E; ++f) h[f] = make_dbl4(hs[4 * f], hs[4 * f + 1], hs[4 * f + 2], hs[4 * f + 3]);
+                CHK(put(D.hist64[par] + e0, h.data(), 32 * E));
+            } else {
+                std::vector<float4> h(E);
+                for (int64_t f = 0; f < E; ++f)
+                    h[f] = make_float4((float)hs[4 * f], (float)hs[4 * f + 1], (float)hs[4 * f + 2], (float)hs[4 * f + 3]);
+                CHK(put(D.hist32[par] + e0, h.data(), 16 * E));
+            }
+        }
         break;
     }
     default:
@@ -1535,6 +1648,10 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
     } else if (k == "grav_item") {
         if (!(value >= 1024.0)) return fail(w, DEM_ERR_ARG, "grav_item must be >= 1024");
         w->grav_item = value;
+    } else if (k == "contact_inbox") {
+        if (!(value >= 1.0) || value > kInboxCap)
+            return fail(w, DEM_ERR_ARG, "contact_inbox must be in [1, %d]", kInboxCap);
+        w->contact_inbox = (int)value;
     } else if (k == "cell_factor" || k == "skin") {
         if (k == "cell_factor" && (!(value >= 1.0) || value > 16.0))
             return fail(w, DEM_ERR_ARG, "cell_factor must be in [1, 16]");
@@ -1569,6 +1686,7 @@ dem_status dem_get_tuning(dem_world *w, const char *key, double *value_out)
     else if (k == "grav_item") *value_out = w->grav_item;
     else if (k == "cell_factor") *value_out = w->cell_factor;
     else if (k == "skin") *value_out = w->skin_frac;
+    else if (k == "contact_inbox") *value_out = w->contact_inbox;
     else return fail(w, DEM_ERR_ARG, "unknown tuning key '%s'", key);
     return DEM_OK;
 }
@@ -1774,14 +1892,18 @@ size_t dem_footprint_bytes(int64_t n_spheres, int64_t n_agg, int32_t max_contact
 {
     if (n_spheres < 0 || n_agg < 0 || max_contacts < 1) return 0;
     bool d = precision == DEM_FP64;
-    size_t sph = 4 + 4 + 24 + 8 + 8 + 4 + 4 + 4 + 4 + 4 + 32 + 4 + 4 + 4 * kHitCap;
-    sph += 8;   // pos_of_home, both parities
-    sph += d ? (32 * 3 + 32 + 64) : (16 * 2 + 16 * 4 + 16 + 32);
-    size_t sphk = d ? 2 * 32 : 2 * 16;
+    size_t sph = 4 + 4 + 24 + 8 + 8 + 4 + 4 + 4 + 4 + 32;
+    sph += 8;        // pos_of_home, both parities
+    sph += 2 * 8;    // candidate counts and offsets, both buffers
+    sph += d ? (32 * 3 + 32 + 64) : (16 * 2 + 16 * 5 + 16 + 32);
+    // candidate-list entries: partner and mirror, partner index (both
+    // buffers), history (both parities) and the carried-over history
+    size_t ent = 2 * (8 + 4) + 3 * (d ? 32 : 16);
     size_t agg = 4 * 3 + 8 + 72 * 2 + 24 * 2 + 32 + 24 * 3 + 144 + 64 +
                  (d ? sizeof(AggRec64) : sizeof(AggRecMixed) + 72);
     int64_t cells = std::max<int64_t>(4 * n_spheres, 27) + kScanTile;
-    size_t bytes = sph * (size_t)n_spheres + sphk * (size_t)n_spheres * (size_t)max_contacts +
+    size_t bytes = sph * (size_t)n_spheres + ent * (size_t)n_spheres * (size_t)kEntPerSphere +
+                   24 * (size_t)((n_spheres + kCTile - 1) / kCTile) +
                    agg * (size_t)n_agg + 8 * (size_t)cells + 4 * (size_t)(cells / kScanTile + 1) +
                    (size_t)(n_agg / kAggChunk + 1) * (8 * kPartialDoubles + 4 + 8 * 32) +
                    sizeof(PileStatic) + sizeof(PileDyn) + sizeof(PileWatch) + 20 + 16 * (size_t)(n_spheres / 64 + 1);
