@@ -84,6 +84,8 @@ def parse():
                          "analysis: only the spin-up and encounter runs with device-side watches "
                          "(not part of all); probe: only the peak-rate probes")
     ap.add_argument("--contact-n", type=int, default=1_048_576)
+    ap.add_argument("--contact-mode", type=int, default=None, choices=[0, 1],
+                    help="contact part: 0 = one thread per sphere, 1 = tiles with a shared-memory inbox")
     return ap.parse_args()
 
 
@@ -207,7 +209,7 @@ def run_fp64(dem, W, steps):
             "steps": steps, "dtype": "f64"}
 
 
-def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3):
+def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3, mode=None):
     """Contact pass on a dense FCC-tetrahedra lattice (0.5% R overlaps, 9 contacts
     per sphere), gravity off, working set far above L2.  Steady state: the pair
     pass over the candidate lists kept since the last rebuild (the lattice moves
@@ -217,6 +219,8 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3):
     ic, p = W.dense_lattice(n_spheres=n, seed=0, precision=W.PRECISION_MIXED)
     p = p.replace(G=0.0)
     with dem.World() as w:
+        if mode is not None:
+            w.set_tuning("contact_mode", mode)
         pid = w.add_pile(ic, p)
         w.set_timed_kernel("CONTACT")
         flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -751,7 +755,7 @@ def run_contact_only(args):
     __graft_entry__.build()
     torch.cuda.set_device(0)
     r = run_contact_roofline(dem, W, float(peaks().get("hbm_gbs", 6800.0)), steps=args.steps,
-                             n=args.contact_n, warmup=args.warmup)
+                             n=args.contact_n, warmup=args.warmup, mode=args.contact_mode)
     print(json.dumps({"part": "contact", "roofline_contact": r}), flush=True)
 
 

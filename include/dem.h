@@ -255,11 +255,15 @@ dem_status dem_remove_pile(dem_world *w, int32_t pile_id);
  * directly; 0 = direct sum, the default), "grav_order" (highest multipole
  * rank of the tree's accepted cells: 4, the default, or 2 -- monopole and
  * quadrupole only, cheaper per cell and less accurate),
- * "contact_inbox" (list entries a contact tile evaluates together through
- * its shared-memory inbox, 1..2560, default 2560 (the FP64 path uses at most
- * 1280); tiles with more entries are split into sphere ranges that fit, and
- * pairs across ranges are evaluated from both sides: results are bitwise the
- * same for every value, only the speed changes),
+ * "contact_mode" (0, the default: one thread per sphere evaluates every pair
+ * of its candidate list; 1: tiles of 128 consecutive sorted spheres evaluate
+ * each pair inside the tile once and pass both halves through a
+ * shared-memory inbox; the two give bitwise the same results),
+ * "contact_inbox" (mode 1: list entries a tile evaluates together through
+ * its inbox, 1..1280, default 1280 (the FP64 path uses at most 640); tiles
+ * with more entries are split into sphere ranges that fit, and pairs across
+ * ranges are evaluated from both sides: results are bitwise the same for
+ * every value, only the speed changes),
  * "cell_factor" (cell edge / (2 x
  * largest radius), >= 1), "skin" (neighbour-list skin as a fraction of the
  * pile's largest radius, in [0, 4], default 0.1; 0 = search contacts afresh

@@ -27,9 +27,9 @@ constexpr int kPartialDoubles = 16;
 // volume; a pile whose lists need more is flagged DEM_FLAG_SLOTS and frozen);
 // a tile with at most kInboxCap list entries evaluates each of its inner pairs
 // once and passes the partner's share through shared memory.
-constexpr int kCTile = 256;
+constexpr int kCTile = 128;
 constexpr int kEntPerSphere = 32;
-constexpr int kInboxCap = 2560;
+constexpr int kInboxCap = 1280;
 
 // Cell index of wrapped cell coordinates (cx, cy, cz) on an nx x ny x nz grid:
 // bricks of 4 x 4 x 4 cells in row-major brick order, row-major inside a brick
@@ -133,9 +133,13 @@ struct Arrays {
     int32_t *rank;       // rank among spheres counted into the same cell
     int32_t *sorted;     // sorted position (pile-local) -> home index (pile-local)
     // sorted copies for the contact pass
-    int4 *xq;                       // mixed: low 32 bits of round((r_i - O) / q) per axis, round(radius / q)
-    float4 *xr;                     // mixed: what those roundings left (in quanta, |.| <= 1/2)
-    float4 *sph_, *sv_, *sw_;       // mixed: pos hi (+s hi; rebuild steps only), vel (+agg), spin (+home id)
+    // mixed: per sphere two 16-byte halves of one 32-byte sector each:
+    // xqr[2k] = low 32 bits of round((r_i - O) / q) per axis and round(radius / q),
+    // xqr[2k+1] = what those roundings left (FP32 bits, in quanta, |.| <= 1/2);
+    // svw[2k] = velocity (+agg), svw[2k+1] = spin (+home id)
+    int4 *xqr;
+    float4 *svw;
+    float4 *sph_;                   // mixed: pos hi (+s hi; rebuild steps only)
     dbl4 *dp_, *dv_, *dw_;          // fp64: pos (+s), vel (+agg), spin (+home id)
     int32_t *sagg;                  // aggregate (pile-local) of each sorted position
     // candidate lists (compressed rows per sorted sphere, entries in the
@@ -221,6 +225,7 @@ struct Sizes {
     int32_t adapt;   // some pile integrates rotation with the adaptive RK5(4)
     int32_t gtile;   // spheres per tile of the symmetric gravity form (512, or 128 in the mixed path)
     int32_t icap;    // contact inbox entries used per tile range (<= the kernel's capacity)
+    int32_t cmode;   // contact pass: 0 = one thread per sphere, 1 = tiles with a shared-memory inbox
 };
 
 // ---- kernel launchers (kernels_*.cu) -------------------------------------

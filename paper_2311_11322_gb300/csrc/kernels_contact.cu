@@ -15,19 +15,27 @@
 // (checked at the drift).  The candidate test is exact and symmetric, so
 // both spheres of a pair always list each other.
 //
-// One evaluation per pair.  The law is evaluated with the owner as sphere a
-// (canonical orientation), so both spheres' shares come from one evaluation:
+// Shares of a pair.  Both spheres' shares come from one evaluation with the
+// owner as sphere a:
 //   a:  F,  tau_a = (l_a n) x F + M;   b:  -F,  tau_b = (l_b n) x F - M.
-// k_contact works on tiles of kCTile consecutive sorted spheres, which fill
-// compact blocks of space (cells are numbered brick by brick).  A pair inside
-// a tile is evaluated once, by the thread that drew it from the tile's work
-// queue, and both shares go to the spheres' slots in a shared-memory inbox; a
-// pair that crosses tiles is evaluated by both tiles, each keeping its own
-// sphere's share.  Every sphere then sums its inbox slots in list order, i.e.
-// in the order of its partners' home indices, so forces, torques and history
-// are bitwise the same whatever the tiles, the cell size, the skin or the
-// steps at which the lists were rebuilt.  Nothing is written with atomics
-// except error flags and the work-queue counter.
+// The law is written with every operation's rounding pinned, and each of its
+// steps maps exactly onto its negative or onto itself when the two spheres
+// swap, so an evaluation with b as sphere a gives b's share bit for bit.
+// Two forms of the pass, with bitwise the same results:
+//   k_contact_sphere (the default): one thread per sorted sphere evaluates
+//     every entry of its list with itself as sphere a (each pair twice, once
+//     per sphere) and sums its shares in list order; the owner's thread
+//     writes the history;
+//   k_contact (contact_mode 1): tiles of kCTile consecutive sorted spheres,
+//     which fill compact blocks of space (cells are numbered brick by brick);
+//     a pair inside a tile is evaluated once, by the thread that drew it from
+//     the tile's work queue, and both shares go to the spheres' slots in a
+//     shared-memory inbox; a pair that crosses tiles is evaluated by both
+//     tiles, each keeping its own sphere's share.
+// Every sphere sums its shares in list order, i.e. in the order of its
+// partners' home indices, so forces, torques and history are bitwise the same
+// whatever the form, the tiles, the cell size, the skin or the steps at which
+// the lists were rebuilt.  Nothing is written with atomics except error flags.
 //
 // History (Sec. 2.1: the tangential displacement is tracked while the two
 // spheres stay in contact) lives at the owner's list entry, from the owner's
@@ -81,47 +89,83 @@ __device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float qsqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 __device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
 
+// Correctly rounded operations for the force law: every product, sum and
+// fused multiply-add is written out, so the compiler neither contracts nor
+// reassociates anything and the law gives the same bits in every kernel
+// that inlines it (the pair kernels rely on that for bitwise results).
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <typename T, typename V> __device__ __forceinline__ V vmk(T x, T y, T z);
+template <> __device__ __forceinline__ float3 vmk<float, float3>(float x, float y, float z) { return f3(x, y, z); }
+template <> __device__ __forceinline__ double3 vmk<double, double3>(double x, double y, double z) { return d3(x, y, z); }
+template <typename T, typename V> __device__ __forceinline__ V vscale(T s, V a)
+{ return vmk<T, V>(rmul(s, a.x), rmul(s, a.y), rmul(s, a.z)); }
+template <typename T, typename V> __device__ __forceinline__ V vadd(V a, V b)
+{ return vmk<T, V>(radd(a.x, b.x), radd(a.y, b.y), radd(a.z, b.z)); }
+template <typename T, typename V> __device__ __forceinline__ V vsub(V a, V b)
+{ return vmk<T, V>(rsub(a.x, b.x), rsub(a.y, b.y), rsub(a.z, b.z)); }
+template <typename T, typename V> __device__ __forceinline__ V vaxpy(T s, V a, V b)   // s a + b
+{ return vmk<T, V>(rfma(s, a.x, b.x), rfma(s, a.y, b.y), rfma(s, a.z, b.z)); }
+template <typename T, typename V> __device__ __forceinline__ T vdot(V a, V b)
+{ return rfma(a.z, b.z, rfma(a.y, b.y, rmul(a.x, b.x))); }
+template <typename T, typename V> __device__ __forceinline__ V vcross(V a, V b)
+{
+    return vmk<T, V>(rfma(a.y, b.z, -rmul(a.z, b.y)), rfma(a.z, b.x, -rmul(a.x, b.z)),
+                     rfma(a.x, b.y, -rmul(a.y, b.x)));
+}
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double rdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float rnorm(float x) { return x > 0.f ? rmul(x, rsqrtf(x)) : 0.f; }
+__device__ __forceinline__ double rnorm(double x) { return __dsqrt_rn(x); }
+
 // Tangential spring, Coulomb cap and rolling/twisting couples, shared by
 // both precisions (T = float or double).
 template <typename T, typename V, typename P>
 __device__ __forceinline__ void force_law(V n, T x, T la, T lb, V va, V wa, V vb, V wb, T sa,
                                           T sb, V Sprev, const P &prm, PairOut<T, V> &o)
 {
-    V ca = la * n, cb = (-lb) * n;
-    V u = (vb + cross(wb, cb)) - (va + cross(wa, ca));
-    T uns = dot(u, n);
-    V un = uns * n;
-    V ut = u - un;
+    // relative velocity of b's contact point with respect to a's
+    const V ca = vscale<T, V>(la, n), cb = vscale<T, V>(-lb, n);
+    const V u = vsub<T, V>(vadd<T, V>(vb, vcross<T, V>(wb, cb)), vadd<T, V>(va, vcross<T, V>(wa, ca)));
+    const T uns = vdot<T, V>(u, n);
+    const V ut = vaxpy<T, V>(-uns, n, u);                 // u - (u.n) n
     // F_N is along n: its signed magnitude is -kn x + cn (u.n)
-    const T fn = prm.cn * uns - prm.kn * x;
-    V FN = fn * n;
-    T FNm = fabs(fn);
-    T sn = dot(Sprev, n);
-    V Sp = Sprev - sn * n;
-    T Spm = qsqrt(dot(Sp, Sp)), Sprevm = qsqrt(dot(Sprev, Sprev));
-    Sp = Spm > T(0) ? qdiv(Sprevm, Spm) * Sp : T(0) * Sp;
-    V S = Sp + prm.h * ut;
-    V FT = prm.kt * S + prm.ct * ut;
-    T FTm = qsqrt(dot(FT, FT)), cap = prm.mu_s * FNm;
+    const T fn = rfma(prm.cn, uns, -rmul(prm.kn, x));
+    const T FNm = fabs(fn);
+    // tangential spring: S_prev on the new tangent plane, rescaled to |S_prev|
+    V Sp = vaxpy<T, V>(-vdot<T, V>(Sprev, n), n, Sprev);
+    const T Spm = rnorm(vdot<T, V>(Sp, Sp)), Sprevm = rnorm(vdot<T, V>(Sprev, Sprev));
+    Sp = Spm > T(0) ? vscale<T, V>(rdiv(Sprevm, Spm), Sp) : vmk<T, V>(T(0), T(0), T(0));
+    V S = vaxpy<T, V>(prm.h, ut, Sp);
+    V FT = vaxpy<T, V>(prm.ct, ut, vscale<T, V>(prm.kt, S));
+    const T FTm = rnorm(vdot<T, V>(FT, FT)), cap = rmul(prm.mu_s, FNm);
     if (FTm > cap) {
-        FT = qdiv(cap, FTm) * FT;
-        S = prm.kt > T(0) ? qdiv(T(1), prm.kt) * (FT - prm.ct * ut) : T(0) * S;
+        FT = vscale<T, V>(rdiv(cap, FTm), FT);
+        S = prm.kt > T(0) ? vscale<T, V>(rdiv(T(1), prm.kt), vaxpy<T, V>(-prm.ct, ut, FT))
+                          : vmk<T, V>(T(0), T(0), T(0));
     }
-    V w = wa - wb;
-    T wn = dot(w, n);
-    V wt = wn * n;
-    V wr = w - wt;
-    T Rred = qdiv(sa * sb, sa + sb);
-    V M = T(0) * n;
+    // rolling and twisting couples
+    const V w = vsub<T, V>(wa, wb);
+    const T wn = vdot<T, V>(w, n);
+    const V wt = vscale<T, V>(wn, n);
+    const V wr = vsub<T, V>(w, wt);
+    const T Rred = rdiv(rmul(sa, sb), radd(sa, sb));
+    V M = vmk<T, V>(T(0), T(0), T(0));
     if (prm.mu_r > T(0)) {
-        T wrm = qsqrt(dot(wr, wr));
-        if (wrm > T(0)) M = M + qdiv(-prm.mu_r * FNm * Rred, fmax(wrm, prm.w0)) * wr;
+        const T wrm = rnorm(vdot<T, V>(wr, wr));
+        if (wrm > T(0)) M = vscale<T, V>(rdiv(-rmul(rmul(prm.mu_r, FNm), Rred), fmax(wrm, prm.w0)), wr);
     }
     if (prm.mu_t > T(0)) {
-        T wtm = qsqrt(dot(wt, wt));
-        if (wtm > T(0)) M = M + qdiv(-prm.mu_t * FNm * Rred, fmax(wtm, prm.w0)) * wt;
+        const T wtm = rnorm(vdot<T, V>(wt, wt));
+        if (wtm > T(0)) M = vaxpy<T, V>(rdiv(-rmul(rmul(prm.mu_t, FNm), Rred), fmax(wtm, prm.w0)), wt, M);
     }
-    o.F = FN + FT;
+    o.F = vaxpy<T, V>(fn, n, FT);                         // F_N + F_T
     o.M = M;
     o.S = S;
     o.n = n;
@@ -183,12 +227,12 @@ __device__ __forceinline__ bool pair_mixed(int4 A, float4 RA, int4 B, float4 RB,
 __device__ __forceinline__ bool pair_64(dbl4 ap, dbl4 av, dbl4 aw, dbl4 bp, dbl4 bv, dbl4 bw,
                                         double3 Sprev, const ParamsD &prm, PairOut<double, double3> &o)
 {
-    double3 d = d3(bp.x - ap.x, bp.y - ap.y, bp.z - ap.z);
-    double dist = sqrt(dot(d, d));
-    double x = ap.w + bp.w - dist;
+    const double3 d = d3(__dsub_rn(bp.x, ap.x), __dsub_rn(bp.y, ap.y), __dsub_rn(bp.z, ap.z));
+    const double dist = __dsqrt_rn(vdot<double, double3>(d, d));
+    const double x = __dsub_rn(__dadd_rn(ap.w, bp.w), dist);
     if (!(x > 0.0) || !(dist > 0.0)) return false;
-    const double inv = 1.0 / dist;
-    double3 n = inv * d;
+    const double inv = __ddiv_rn(1.0, dist);
+    const double3 n = vscale<double, double3>(inv, d);
     const double hd = __dmul_rn(0.5, dist);
     const double g = __dmul_rn(__dmul_rn(__dsub_rn(ap.w, bp.w), __dadd_rn(ap.w, bp.w)), __dmul_rn(0.5, inv));
     double la = __dadd_rn(hd, g);
@@ -216,19 +260,15 @@ __device__ __forceinline__ double3 lever_x_force(double l, double3 n, double3 F)
 __device__ __forceinline__ float addr(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double addr(double a, double b) { return __dadd_rn(a, b); }
 
+// One sphere's share of an evaluation: sphere a (side_a) gets F and
+// (l_a n) x F + M, sphere b gets -F and (l_b n) x F - M.
 template <typename T, typename V>
-__device__ __forceinline__ void share_a(const PairOut<T, V> &o, V &F, V &Tq)
+__device__ __forceinline__ void share(const PairOut<T, V> &o, bool side_a, V &F, V &Tq)
 {
-    F = o.F;
-    const V c = lever_x_force(o.la, o.n, o.F);
-    Tq.x = addr(c.x, o.M.x); Tq.y = addr(c.y, o.M.y); Tq.z = addr(c.z, o.M.z);
-}
-template <typename T, typename V>
-__device__ __forceinline__ void share_b(const PairOut<T, V> &o, V &F, V &Tq)
-{
-    F.x = -o.F.x; F.y = -o.F.y; F.z = -o.F.z;
-    const V c = lever_x_force(o.lb, o.n, o.F);
-    Tq.x = addr(c.x, -o.M.x); Tq.y = addr(c.y, -o.M.y); Tq.z = addr(c.z, -o.M.z);
+    const T sg = side_a ? T(1) : T(-1);
+    const V c = lever_x_force(side_a ? o.la : o.lb, o.n, o.F);
+    F = vmk<T, V>(sg * o.F.x, sg * o.F.y, sg * o.F.z);
+    Tq = vmk<T, V>(addr(c.x, sg * o.M.x), addr(c.y, sg * o.M.y), addr(c.z, sg * o.M.z));
 }
 
 template <bool FP64> struct CT;
@@ -238,6 +278,7 @@ template <> struct CT<false> {
     typedef ParamsF Prm;
     typedef float4 H;                      // history record
     typedef int4 P;                        // position record
+    typedef float4 VR;                     // velocity / spin record
     static constexpr int kCap = kInboxCap; // inbox entries per block
 };
 template <> struct CT<true> {
@@ -246,6 +287,7 @@ template <> struct CT<true> {
     typedef ParamsD Prm;
     typedef dbl4 H;
     typedef dbl4 P;
+    typedef dbl4 VR;
     static constexpr int kCap = kInboxCap / 2;
 };
 
@@ -273,6 +315,10 @@ __device__ __forceinline__ int cellc_d(double x, double inv_cell, int n)
 }
 
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+__device__ __forceinline__ float4 as_f4(int4 v)
+{
+    return make_float4(__int_as_float(v.x), __int_as_float(v.y), __int_as_float(v.z), __int_as_float(v.w));
+}
 
 // Candidate test of sphere k (own data) against sorted position kk.  Exact and
 // symmetric: swapping the spheres gives the same answer.
@@ -292,13 +338,19 @@ __device__ __forceinline__ bool cand_test(const Arrays &a, const PileStatic &S, 
         const double t = m.p.w + q.w + S.skin;
         return __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx))) < __dmul_rn(t, t);
     } else {
-        // coarse FP32 test first: rejects spheres of another wrap of the grid,
-        // whose 32-bit fixed-point difference would alias
+        // FP32 test first (it rejects the spheres of other wraps of the grid,
+        // whose 32-bit fixed-point difference would alias): the FP32 centres
+        // are the rounded float-float positions, so a margin of a few units in
+        // the last place of both keeps every candidate; the margin depends on
+        // both spheres alike, so the test stays symmetric
         const float4 q = a.sph_[kk];
         const float dx = __fsub_rn(q.x, m.ph.x), dy = __fsub_rn(q.y, m.ph.y), dz = __fsub_rn(q.z, m.ph.z);
-        const float tc = __fmul_rn(2.0f, __fadd_rn(__fadd_rn(q.w, m.ph.w), (float)S.skin)) + 1e-30f;
+        const float big = __fadd_rn(fmaxf(fabsf(q.x), fmaxf(fabsf(q.y), fabsf(q.z))),
+                                    fmaxf(fabsf(m.ph.x), fmaxf(fabsf(m.ph.y), fabsf(m.ph.z))));
+        const float sr = __fadd_rn(q.w, m.ph.w);
+        const float tc = __fadd_rn(__fadd_rn(sr, (float)S.skin), __fmaf_rn(1e-6f, big, __fmul_rn(1e-5f, sr)));
         if (!(__fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) < __fmul_rn(tc, tc))) return false;
-        const int4 B = a.xq[kk];
+        const int4 B = a.xqr[2 * kk];
         const int ex = (int)((unsigned)B.x - (unsigned)m.xq.x);
         const int ey = (int)((unsigned)B.y - (unsigned)m.xq.y);
         const int ez = (int)((unsigned)B.z - (unsigned)m.xq.z);
@@ -329,16 +381,30 @@ __device__ __forceinline__ void for_candidates(const Arrays &a, const PileStatic
     }
     const int32_t *cstart = a.cstart + S.c0, *ccount = a.ccount + S.c0;
     const int64_t s0 = S.s0;
-    const bool one = cx >= 1 && cx + 1 < S.nx && ((cx - 1) >> 2) == ((cx + 1) >> 2);
+    // without wrap-around the three x-neighbours are consecutive cell ids
+    // except across a brick boundary: one or two index ranges
+    const bool nowrap = cx >= 1 && cx + 1 < S.nx;
+    const int split = (cx & 3) == 0 ? 1 : (cx & 3) == 3 ? 2 : 3;   // first cell of the second range
     for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy) {
             const int yy = wrapc(cy + dy, S.ny), zz = wrapc(cz + dz, S.nz);
             int beg[3], end[3], nr;
-            if (one) {
-                const int64_t c0 = cell_id(cx - 1, yy, zz, S.nx, S.ny);
-                beg[0] = cstart[c0];
-                end[0] = cstart[c0 + 2] + ccount[c0 + 2];
-                nr = 1;
+            if (nowrap) {
+                const int64_t cl = cell_id(cx - 1, yy, zz, S.nx, S.ny);
+                const int64_t cs = cell_id(cx - 1 + split, yy, zz, S.nx, S.ny);
+                const int64_t ce = cell_id(cx + 1, yy, zz, S.nx, S.ny);
+                if (split == 3) {
+                    beg[0] = cstart[cl];
+                    end[0] = cstart[ce] + ccount[ce];
+                    nr = 1;
+                } else {
+                    const int64_t cm = split == 1 ? cl : cell_id(cx, yy, zz, S.nx, S.ny);
+                    beg[0] = cstart[cl];
+                    end[0] = cstart[cm] + ccount[cm];
+                    beg[1] = cstart[cs];
+                    end[1] = cstart[ce] + ccount[ce];
+                    nr = 2;
+                }
             } else {
                 nr = 0;
                 for (int ddx = -1; ddx <= 1; ++ddx) {
@@ -362,7 +428,7 @@ __device__ __forceinline__ void load_me(const Arrays &a, int64_t k, CandMe &m)
 {
     if constexpr (FP64) m.p = a.dp_[k];
     else {
-        m.xq = a.xq[k];
+        m.xq = a.xqr[2 * k];
         m.ph = a.sph_[k];
     }
     m.agg = a.sagg[k];
@@ -380,8 +446,9 @@ __global__ void __launch_bounds__(kCTile) k_cand_count(Arrays a, Sizes z)
 {
     pdl_enter();
     __shared__ int red[kCTile / 32];
-    const int4 tl = a.ctile[blockIdx.x];
-    if (!tile_rebuilds(a, tl)) return;
+    for (int64_t tile = blockIdx.x; tile < z.CT; tile += gridDim.x) {
+    const int4 tl = a.ctile[tile];
+    if (!tile_rebuilds(a, tl)) continue;
     const int p = tl.x;
     const PileStatic &S = a.ps[p];
     const int lp = a.pd[p].cpar ^ 1;
@@ -393,14 +460,17 @@ __global__ void __launch_bounds__(kCTile) k_cand_count(Arrays a, Sizes z)
         for_candidates<FP64>(a, S, k, m, [&](int) { ++n; });
         a.ccnt[lp][k] = n;
     }
-    int v = n;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    // entries of the tile: every slice of 32 spheres (a warp) is as wide as
+    // its longest list
+    const int wmax = __reduce_max_sync(0xffffffffu, n);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = 32 * wmax;
     __syncthreads();
     if (threadIdx.x == 0) {
         int s = 0;
         for (int w = 0; w < kCTile / 32; ++w) s += red[w];
-        a.ctile_cnt[blockIdx.x] = s;
+        a.ctile_cnt[tile] = s;
+    }
+    __syncthreads();   // red[] is reused by the next tile
     }
 }
 
@@ -440,31 +510,29 @@ __global__ void __launch_bounds__(1024) k_cand_scan(Arrays a, Sizes z)
 }
 
 // Offsets, then the candidates themselves, sorted by partner home index.
+// Sliced layout: the 32 spheres of a slice (a warp) store entry e of their
+// lists side by side, so sphere k's entry e is at coff[k] + 32 e (coalesced
+// when a warp walks its lists together).
+constexpr int kFillCap = 20;   // candidates sorted in shared memory per sphere (more: in place)
+
 template <bool FP64>
-__global__ void __launch_bounds__(kCTile) k_cand_fill(Arrays a, Sizes z)
+__device__ __forceinline__ void cand_fill_tile(const Arrays &a, int4 tl, int base, int *sw,
+                                               int2 (*s_list)[kCTile])
 {
-    pdl_enter();
-    __shared__ int pre[kCTile];
-    const int4 tl = a.ctile[blockIdx.x];
-    if (!tile_rebuilds(a, tl)) return;
-    const int base = a.ctile_base[blockIdx.x];
-    if (base < 0) return;
     const int p = tl.x;
     const PileStatic &S = a.ps[p];
     const int lp = a.pd[p].cpar ^ 1;
     const bool mine = (int)threadIdx.x < tl.z;
     const int64_t k = S.s0 + tl.y + threadIdx.x;
     const int n = mine ? a.ccnt[lp][k] : 0;
-    pre[threadIdx.x] = n;
+    const int wmax = __reduce_max_sync(0xffffffffu, n);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sw[wid] = 32 * wmax;
     __syncthreads();
-    for (int o = 1; o < kCTile; o <<= 1) {
-        const int add = threadIdx.x >= (unsigned)o ? pre[threadIdx.x - o] : 0;
-        __syncthreads();
-        pre[threadIdx.x] += add;
-        __syncthreads();
-    }
+    int sb = base;
+    for (int w = 0; w < wid; ++w) sb += sw[w];
     if (!mine) return;
-    const int off = base + pre[threadIdx.x] - n;
+    const int off = sb + lane;
     a.coff[lp][k] = off;
     int32_t *ids = a.cand_id[lp] + S.e0 + off;
     int2 *cd = a.cand[lp] + S.e0 + off;
@@ -472,32 +540,64 @@ __global__ void __launch_bounds__(kCTile) k_cand_fill(Arrays a, Sizes z)
     CandMe m;
     load_me<FP64>(a, k, m);
     int j = 0;
+    if (n <= kFillCap) {
+        // insertion by partner home index in shared memory, then one write
+        int2 *l = &s_list[0][threadIdx.x];
+        for_candidates<FP64>(a, S, k, m, [&](int t) {
+            if (j >= n) return;   // (the count pass visited the same candidates)
+            const int id = srt[t];
+            int y = j++;
+            while (y > 0 && l[(y - 1) * kCTile].x > id) {
+                l[y * kCTile] = l[(y - 1) * kCTile];
+                --y;
+            }
+            l[y * kCTile] = make_int2(id, t);
+        });
+        for (int y = 0; y < j; ++y) {
+            const int2 v = l[y * kCTile];
+            ids[32 * y] = v.x;
+            cd[32 * y] = make_int2(v.y, 0);
+        }
+        return;
+    }
     for_candidates<FP64>(a, S, k, m, [&](int t) {
-        if (j >= n) return;   // (the count pass visited the same candidates)
-        // insertion by partner home index (lists are short)
+        if (j >= n) return;
+        // long list: insertion by partner home index in place
         const int id = srt[t];
         int y = j++;
-        while (y > 0 && ids[y - 1] > id) {
-            ids[y] = ids[y - 1];
-            cd[y] = cd[y - 1];
+        while (y > 0 && ids[32 * (y - 1)] > id) {
+            ids[32 * y] = ids[32 * (y - 1)];
+            cd[32 * y] = cd[32 * (y - 1)];
             --y;
         }
-        ids[y] = id;
-        cd[y] = make_int2(t, 0);
+        ids[32 * y] = id;
+        cd[32 * y] = make_int2(t, 0);
     });
 }
+
+template <bool FP64>
+__global__ void __launch_bounds__(kCTile) k_cand_fill(Arrays a, Sizes z)
+{
+    pdl_enter();
+    __shared__ int sw[kCTile / 32];
+    __shared__ int2 s_list[kFillCap][kCTile];   // (partner home index, sorted position)
+    for (int64_t tile = blockIdx.x; tile < z.CT; tile += gridDim.x) {
+        __syncthreads();   // sw[] of the previous tile
+        const int4 tl = a.ctile[tile];
+        if (!tile_rebuilds(a, tl)) continue;
+        const int base = a.ctile_base[tile];
+        if (base < 0) continue;
+        cand_fill_tile<FP64>(a, tl, base, sw, s_list);
+    }
+}
+
 
 // Owner bit and mirror entry of every list entry; history carried from the
 // previous lists (by the home indices of both spheres) into hist_rm.
 template <bool FP64>
-__global__ void __launch_bounds__(kCTile) k_cand_link(Arrays a, Sizes z)
+__device__ __forceinline__ void cand_link_sphere(const Arrays &a, int4 tl)
 {
-    pdl_enter();
     typedef typename CT<FP64>::H H;
-    const int4 tl = a.ctile[blockIdx.x];
-    if (!tile_rebuilds(a, tl)) return;
-    if (a.ctile_base[blockIdx.x] < 0) return;
-    if ((int)threadIdx.x >= tl.z) return;
     const int p = tl.x;
     const PileStatic &S = a.ps[p];
     const PileDyn &D = a.pd[p];
@@ -516,7 +616,7 @@ __global__ void __launch_bounds__(kCTile) k_cand_link(Arrays a, Sizes z)
     else { hprev = a.hist32[par] + e0; hrm = a.hist32_rm + e0; }
     int cursor = 0;
     for (int e = 0; e < n; ++e) {
-        const int f = off + e;
+        const int f = off + 32 * e;
         const int2 c = a.cand[lp][e0 + f];
         const int kk = c.x;
         const int id = a.cand_id[lp][e0 + f];
@@ -526,8 +626,8 @@ __global__ void __launch_bounds__(kCTile) k_cand_link(Arrays a, Sizes z)
         int lo = 0, hi = pn2 - 1, mir = -1;
         while (lo <= hi) {
             const int mid = (lo + hi) >> 1;
-            const int v = ids2[mid];
-            if (v == me) { mir = po2 + mid; break; }
+            const int v = ids2[32 * mid];
+            if (v == me) { mir = po2 + 32 * mid; break; }
             if (v < me) lo = mid + 1; else hi = mid - 1;
         }
         if (mir < 0) atomicOr(&a.pd[p].flags, DEM_FLAG_SLOTS);   // lists not symmetric: cannot happen
@@ -539,47 +639,90 @@ __global__ void __launch_bounds__(kCTile) k_cand_link(Arrays a, Sizes z)
         H h;
         if constexpr (FP64) h = make_dbl4(0.0, 0.0, 0.0, 0.0);
         else h = make_float4(0.f, 0.f, 0.f, 0.f);
-        while (cursor < pn && pids[cursor] < id) ++cursor;
-        if (cursor < pn && pids[cursor] == id) {
-            const H g = hprev[poff + cursor];
+        while (cursor < pn && pids[32 * cursor] < id) ++cursor;
+        if (cursor < pn && pids[32 * cursor] == id) {
+            const H g = hprev[poff + 32 * cursor];
             if (g.w != 0) h = g;
         }
         hrm[f] = h;
     }
 }
 
+template <bool FP64>
+__global__ void __launch_bounds__(kCTile) k_cand_link(Arrays a, Sizes z)
+{
+    pdl_enter();
+    for (int64_t tile = blockIdx.x; tile < z.CT; tile += gridDim.x) {
+        const int4 tl = a.ctile[tile];
+        if (!tile_rebuilds(a, tl) || a.ctile_base[tile] < 0 || (int)threadIdx.x >= tl.z) continue;
+        cand_link_sphere<FP64>(a, tl);
+    }
+}
+
 // ---------------------------------------------------------------- step
-// Shared memory of k_contact (dynamic): list offsets of the tile's spheres,
-// staged sphere data, the inbox (each entry's share: F, tau) with contact
-// flags, and the work queue.
+// Shared memory of k_contact (dynamic): list offsets and lengths of the
+// tile's spheres and its slice bases, staged sphere data, the inbox (each
+// entry's share: F and tau as six arrays, and a contact flag) and the work
+// queue.
 template <bool FP64>
 struct Smem {
     typedef typename CT<FP64>::T T;
     static constexpr int kCap = CT<FP64>::kCap;
-    static constexpr size_t off_bytes = sizeof(int) * (kCTile + 8);   // keeps what follows 32-byte aligned
+    static constexpr size_t off_bytes = sizeof(int) * (2 * kCTile + 32);   // keeps what follows 32-byte aligned
     static constexpr size_t stage_bytes = (FP64 ? 3 * sizeof(dbl4) : 4 * sizeof(float4)) * kCTile;
     static constexpr size_t inbox_bytes = 6 * sizeof(T) * kCap;
     static constexpr size_t flag_bytes = kCap;
     static constexpr size_t queue_bytes = sizeof(int) * kCap;
-    static constexpr size_t total = off_bytes + stage_bytes + inbox_bytes + flag_bytes + queue_bytes + 16;
+    static constexpr size_t scan_bytes = sizeof(int) * (kCTile / 32 + 8);
+    static constexpr size_t total = off_bytes + stage_bytes + inbox_bytes + flag_bytes + queue_bytes + scan_bytes;
 };
 
+// Exclusive prefix sum over the block (kCTile threads); *total gets the sum.
+__device__ __forceinline__ int block_exclusive_scan(int v, int *ws, int *total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < kCTile / 32 ? ws[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < kCTile / 32) ws[lane] = t;
+        if (lane == kCTile / 32 - 1) ws[kCTile / 32] = t;
+    }
+    __syncthreads();
+    const int r = (wid ? ws[wid - 1] : 0) + x - v;
+    *total = ws[kCTile / 32];
+    __syncthreads();
+    return r;
+}
+
 template <bool FP64>
-__global__ void __launch_bounds__(kCTile, FP64 ? 1 : 2) k_contact(Arrays a, Sizes z)
+__global__ void __launch_bounds__(kCTile, FP64 ? 2 : 4) k_contact(Arrays a, Sizes z)
 {
     pdl_enter();
     typedef typename CT<FP64>::T T;
     typedef typename CT<FP64>::V V;
     typedef typename CT<FP64>::H H;
     typedef Smem<FP64> SM;
-    const int kCap = min(SM::kCap, max(1, z.icap));
+    const int kCap = min(SM::kCap, max(32, z.icap));
     extern __shared__ __align__(32) unsigned char smem[];
-    int *s_off = (int *)smem;
+    int *s_off = (int *)smem;                 // [kCTile] list offsets (pile-local entries)
+    int *s_cnt = s_off + kCTile;              // [kCTile] list lengths
+    int *s_sb = s_cnt + kCTile;               // [kSl + 1] slice bases, then the tile's end
     unsigned char *stage = smem + SM::off_bytes;
-    T *inbox = (T *)(stage + SM::stage_bytes);
+    T *inbox = (T *)(stage + SM::stage_bytes);   // [6][SM::kCap]
     unsigned char *flag = (unsigned char *)(inbox + 6 * SM::kCap);
     int *queue = (int *)(flag + SM::kCap);
-    __shared__ int qn, pile_flags;
+    int *ws = (int *)((unsigned char *)queue + SM::queue_bytes);
+    __shared__ int pile_flags;
 
     const int4 tl = a.ctile[blockIdx.x];
     const int p = tl.x;
@@ -607,59 +750,73 @@ __global__ void __launch_bounds__(kCTile, FP64 ? 1 : 2) k_contact(Arrays a, Size
     }
     const float q = pow2f(S.qexp);
     const int2 *cand = a.cand[lp] + e0;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nsl = (nt + 31) >> 5;
     if (tid == 0) pile_flags = 0;
-    if (tid < nt) {
-        const int64_t k = s0 + first + tid;
-        const int off = a.coff[lp][k];
-        s_off[tid] = off;
-        if (tid == nt - 1) s_off[nt] = off + a.ccnt[lp][k];
-        if constexpr (FP64) {
-            dbl4 *st = (dbl4 *)stage;
-            st[tid] = a.dp_[k];
-            st[kCTile + tid] = a.dv_[k];
-            st[2 * kCTile + tid] = a.dw_[k];
-        } else {
-            int4 *sx = (int4 *)stage;
-            float4 *sv = (float4 *)(sx + kCTile);
-            sx[tid] = a.xq[k];
-            sv[tid] = a.sv_[k];
-            sv[kCTile + tid] = a.sw_[k];
-            sv[2 * kCTile + tid] = a.xr[k];
+    {
+        int off = 0, n = 0;
+        if (tid < nt) {
+            const int64_t k = s0 + first + tid;
+            off = a.coff[lp][k];
+            n = a.ccnt[lp][k];
+            if constexpr (FP64) {
+                dbl4 *st = (dbl4 *)stage;
+                st[tid] = a.dp_[k];
+                st[kCTile + tid] = a.dv_[k];
+                st[2 * kCTile + tid] = a.dw_[k];
+            } else {
+                int4 *sx = (int4 *)stage;
+                float4 *sv = (float4 *)(sx + kCTile);
+                const int4 xr = a.xqr[2 * k + 1];
+                sx[tid] = a.xqr[2 * k];
+                sv[tid] = a.svw[2 * k];
+                sv[kCTile + tid] = a.svw[2 * k + 1];
+                sv[2 * kCTile + tid] = make_float4(__int_as_float(xr.x), __int_as_float(xr.y),
+                                                   __int_as_float(xr.z), __int_as_float(xr.w));
+            }
         }
+        s_off[tid] = off;
+        s_cnt[tid] = n;
+        const int wmax = __reduce_max_sync(0xffffffffu, n);
+        if (lane == 0 && wid < nsl) s_sb[wid] = off;               // lane 0 sits at its slice's base
+        if (lane == 0 && wid == nsl - 1) s_sb[nsl] = off + 32 * wmax;
     }
     __syncthreads();
     int myflags = 0;
-    // sphere ranges [r0, r1) of the tile whose list entries fit the inbox
-    for (int r0 = 0; r0 < nt;) {
-        int r1 = nt;
-        while (s_off[r1] - s_off[r0] > kCap && r1 - r0 > 1) r1 = r0 + (r1 - r0 + 1) / 2;
-        const int E0 = s_off[r0];
-        if (s_off[r1] - E0 > SM::kCap) {   // one sphere with more candidates than the inbox holds
+    // slice ranges [r0, r1) of the tile whose list entries fit the inbox
+    for (int r0 = 0; r0 < nsl;) {
+        int r1 = nsl;
+        while (s_sb[r1] - s_sb[r0] > kCap && r1 - r0 > 1) r1 = r0 + (r1 - r0 + 1) / 2;
+        const int E0 = s_sb[r0], nE = s_sb[r1] - E0;
+        if (nE > SM::kCap) {   // one slice with more entries than the inbox holds
             if (tid == 0) atomicOr(&pile_flags, DEM_FLAG_SLOTS);
             r0 = r1;
             continue;
         }
-        if (tid == 0) qn = 0;
-        __syncthreads();
-        // work queue: entries this range evaluates -- pairs it owns, and pairs
-        // that leave the range (from this sphere's side)
-        const unsigned lo = (unsigned)(first + r0), span = (unsigned)(r1 - r0);
-        if (tid >= r0 && tid < r1) {
-            const int off = s_off[tid], n = s_off[tid + 1] - off;
-            for (int e = 0; e < n; ++e) {
-                const int2 c = cand[off + e];
-                const unsigned kk = (unsigned)c.x & 0x7fffffffu;
-                const bool owned = c.x < 0, inner = kk - lo < span;
-                if (owned || !inner) queue[atomicAdd(&qn, 1)] = (tid << 12) | e;
-            }
+        const int i0 = 32 * r0, i1 = min(32 * r1, nt);
+        // work queue in (sphere, entry) order: pairs this range owns, and
+        // pairs that leave the range (from this sphere's side)
+        const unsigned lo = (unsigned)(first + i0), span = (unsigned)(i1 - i0);
+        const bool inr = tid >= i0 && tid < i1;
+        const int off = s_off[tid], n = inr ? s_cnt[tid] : 0;
+        int cnt = 0;
+        for (int e = 0; e < n; ++e) {
+            const int2 c = cand[off + 32 * e];
+            const unsigned kk = (unsigned)c.x & 0x7fffffffu;
+            cnt += (c.x < 0 || kk - lo >= span) ? 1 : 0;
+        }
+        int nq;
+        int pos = block_exclusive_scan(cnt, ws, &nq);
+        for (int e = 0; e < n; ++e) {
+            const int2 c = cand[off + 32 * e];
+            const unsigned kk = (unsigned)c.x & 0x7fffffffu;
+            if (c.x < 0 || kk - lo >= span) queue[pos++] = (tid << 12) | e;
         }
         __syncthreads();
-        const int nq = qn;
         for (int r = tid; r < nq; r += kCTile) {
             const int rec = queue[r];
             const int i = rec >> 12, e = rec & 0xfff;
-            const int f = s_off[i] + e;
+            const int f = s_off[i] + 32 * e;
             const int2 c = cand[f];
             const int kk = c.x & 0x7fffffff;
             const bool owned = c.x < 0;
@@ -670,7 +827,6 @@ __global__ void __launch_bounds__(kCTile, FP64 ? 1 : 2) k_contact(Arrays a, Size
             const int hidx = owned ? f : c.y;
             if ((unsigned)kk >= (unsigned)S.ns || (unsigned)hidx >= (unsigned)S.ne) continue;   // (never taken)
             const H hp = hread[hidx];
-            V Sprev;
             PairOut<T, V> o;
             bool hit;
             if constexpr (FP64) {
@@ -680,17 +836,18 @@ __global__ void __launch_bounds__(kCTile, FP64 ? 1 : 2) k_contact(Arrays a, Size
                            aw = a_loc ? st[2 * kCTile + ia] : a.dw_[ga];
                 const dbl4 bp = b_loc ? st[ib] : a.dp_[gb], bv = b_loc ? st[kCTile + ib] : a.dv_[gb],
                            bw = b_loc ? st[2 * kCTile + ib] : a.dw_[gb];
-                Sprev = hp.w != 0 ? d3(hp.x, hp.y, hp.z) : d3(0, 0, 0);
+                const double3 Sprev = hp.w != 0 ? d3(hp.x, hp.y, hp.z) : d3(0, 0, 0);
                 hit = pair_64(ap, av, aw, bp, bv, bw, Sprev, prm, o);
             } else {
                 const int4 *sx = (const int4 *)stage;
                 const float4 *sv = (const float4 *)(sx + kCTile);
                 const int64_t ga = s0 + (owned ? first + i : kk), gb = s0 + (owned ? kk : first + i);
-                const int4 A = a_loc ? sx[ia] : a.xq[ga], B = b_loc ? sx[ib] : a.xq[gb];
-                const float4 RA = a_loc ? sv[2 * kCTile + ia] : a.xr[ga], RB = b_loc ? sv[2 * kCTile + ib] : a.xr[gb];
-                const float4 av = a_loc ? sv[ia] : a.sv_[ga], aw = a_loc ? sv[kCTile + ia] : a.sw_[ga];
-                const float4 bv = b_loc ? sv[ib] : a.sv_[gb], bw = b_loc ? sv[kCTile + ib] : a.sw_[gb];
-                Sprev = hp.w != 0.f ? f3(hp.x, hp.y, hp.z) : f3(0.f, 0.f, 0.f);
+                const int4 A = a_loc ? sx[ia] : a.xqr[2 * ga], B = b_loc ? sx[ib] : a.xqr[2 * gb];
+                const float4 RA = a_loc ? sv[2 * kCTile + ia] : as_f4(a.xqr[2 * ga + 1]);
+                const float4 RB = b_loc ? sv[2 * kCTile + ib] : as_f4(a.xqr[2 * gb + 1]);
+                const float4 av = a_loc ? sv[ia] : a.svw[2 * ga], aw = a_loc ? sv[kCTile + ia] : a.svw[2 * ga + 1];
+                const float4 bv = b_loc ? sv[ib] : a.svw[2 * gb], bw = b_loc ? sv[kCTile + ib] : a.svw[2 * gb + 1];
+                const float3 Sprev = hp.w != 0.f ? f3(hp.x, hp.y, hp.z) : f3(0.f, 0.f, 0.f);
                 hit = pair_mixed(A, RA, B, RB, q, av, aw, bv, bw, Sprev, prm, o);
             }
             if (owned) {
@@ -701,42 +858,43 @@ __global__ void __launch_bounds__(kCTile, FP64 ? 1 : 2) k_contact(Arrays a, Size
             }
             if (hit && o.x > T(0.1) * o.rmin) myflags |= DEM_FLAG_OVERLAP;
             V F, Tq;
-            const unsigned nE = (unsigned)(s_off[r1] - E0);
             if (a_loc) {
                 const int slot = (owned ? f : c.y) - E0;
-                if ((unsigned)slot >= nE) continue;   // (lists are symmetric: never taken)
+                if ((unsigned)slot >= (unsigned)nE) continue;   // (lists are symmetric: never taken)
                 if (hit) {
-                    share_a<T, V>(o, F, Tq);
-                    T *ib_ = inbox + 6 * slot;
-                    ib_[0] = F.x; ib_[1] = F.y; ib_[2] = F.z; ib_[3] = Tq.x; ib_[4] = Tq.y; ib_[5] = Tq.z;
+                    share<T, V>(o, true, F, Tq);
+                    inbox[slot] = F.x; inbox[SM::kCap + slot] = F.y; inbox[2 * SM::kCap + slot] = F.z;
+                    inbox[3 * SM::kCap + slot] = Tq.x; inbox[4 * SM::kCap + slot] = Tq.y;
+                    inbox[5 * SM::kCap + slot] = Tq.z;
                 }
                 flag[slot] = hit ? 1 : 0;
             }
             if (b_loc) {
                 const int slot = (owned ? c.y : f) - E0;
-                if ((unsigned)slot >= nE) continue;
+                if ((unsigned)slot >= (unsigned)nE) continue;
                 if (hit) {
-                    share_b<T, V>(o, F, Tq);
-                    T *ib_ = inbox + 6 * slot;
-                    ib_[0] = F.x; ib_[1] = F.y; ib_[2] = F.z; ib_[3] = Tq.x; ib_[4] = Tq.y; ib_[5] = Tq.z;
+                    share<T, V>(o, false, F, Tq);
+                    inbox[slot] = F.x; inbox[SM::kCap + slot] = F.y; inbox[2 * SM::kCap + slot] = F.z;
+                    inbox[3 * SM::kCap + slot] = Tq.x; inbox[4 * SM::kCap + slot] = Tq.y;
+                    inbox[5 * SM::kCap + slot] = Tq.z;
                 }
                 flag[slot] = hit ? 1 : 0;
             }
         }
         __syncthreads();
         // every sphere of the range sums its slots in list order
-        if (tid >= r0 && tid < r1) {
-            const int off = s_off[tid], n = s_off[tid + 1] - off;
+        if (inr) {
             V F, Tq;
             if constexpr (FP64) { F = d3(0, 0, 0); Tq = d3(0, 0, 0); }
             else { F = f3(0.f, 0.f, 0.f); Tq = f3(0.f, 0.f, 0.f); }
             int nc = 0;
             for (int e = 0; e < n; ++e) {
-                const int slot = off + e - E0;
+                const int slot = off - E0 + 32 * e;
                 if (!flag[slot]) continue;
-                const T *ib_ = inbox + 6 * slot;
-                F.x = addr(F.x, ib_[0]); F.y = addr(F.y, ib_[1]); F.z = addr(F.z, ib_[2]);
-                Tq.x = addr(Tq.x, ib_[3]); Tq.y = addr(Tq.y, ib_[4]); Tq.z = addr(Tq.z, ib_[5]);
+                F.x = addr(F.x, inbox[slot]); F.y = addr(F.y, inbox[SM::kCap + slot]);
+                F.z = addr(F.z, inbox[2 * SM::kCap + slot]);
+                Tq.x = addr(Tq.x, inbox[3 * SM::kCap + slot]); Tq.y = addr(Tq.y, inbox[4 * SM::kCap + slot]);
+                Tq.z = addr(Tq.z, inbox[5 * SM::kCap + slot]);
                 ++nc;
             }
             const int64_t k = s0 + first + tid;
@@ -744,7 +902,7 @@ __global__ void __launch_bounds__(kCTile, FP64 ? 1 : 2) k_contact(Arrays a, Size
                 a.ftc64[2 * k] = make_dbl4(F.x, F.y, F.z, 0.0);
                 a.ftc64[2 * k + 1] = make_dbl4(Tq.x, Tq.y, Tq.z, 0.0);
             } else {
-                a.ftc32[2 * k] = make_float4(F.x, F.y, F.z, __int_as_float(nc));
+                a.ftc32[2 * k] = make_float4(F.x, F.y, F.z, 0.f);
                 a.ftc32[2 * k + 1] = make_float4(Tq.x, Tq.y, Tq.z, 0.f);
             }
             if (nc > K) myflags |= DEM_FLAG_SLOTS;
@@ -755,6 +913,183 @@ __global__ void __launch_bounds__(kCTile, FP64 ? 1 : 2) k_contact(Arrays a, Size
     if (myflags) atomicOr(&pile_flags, myflags);
     __syncthreads();
     if (tid == 0 && pile_flags) atomicOr(&a.pd[p].flags, pile_flags);
+}
+
+// One thread per sorted sphere: every entry of the sphere's list is evaluated
+// in the canonical orientation (owner as sphere a, the same evaluation the
+// tiles make) and the sphere keeps its own share, summed in list order; the
+// owner's thread writes the pair's history.  Each pair is evaluated twice
+// (once per sphere), with bitwise the same result both times, so the forces
+// equal the tile form's bit for bit.
+template <bool FP64>
+__global__ void __launch_bounds__(128) k_contact_sphere(Arrays a, Sizes z)
+{
+    pdl_enter();
+    typedef typename CT<FP64>::T T;
+    typedef typename CT<FP64>::V V;
+    typedef typename CT<FP64>::H H;
+    const int64_t kb0 = (int64_t)blockIdx.x * 128;
+    const int64_t k = kb0 + threadIdx.x;
+    // mixed path: the block's own 128 sorted spheres staged in shared memory
+    // (consecutive sorted spheres fill a compact block of space, so most
+    // partners are among them)
+    __shared__ int4 s_x[FP64 ? 1 : 2 * 128];
+    __shared__ float4 s_v[FP64 ? 1 : 2 * 128];
+    if constexpr (!FP64) {
+        if (k < z.N) {
+            s_x[2 * threadIdx.x] = a.xqr[2 * k];
+            s_x[2 * threadIdx.x + 1] = a.xqr[2 * k + 1];
+            s_v[2 * threadIdx.x] = a.svw[2 * k];
+            s_v[2 * threadIdx.x + 1] = a.svw[2 * k + 1];
+        }
+        __syncthreads();
+    }
+    if (k >= z.N) return;
+    const int p = a.sph_pile[k];
+    if (!pile_live(a, p)) return;
+    const PileStatic &S = a.ps[p];
+    const PileDyn &D = a.pd[p];
+    if (D.flags & DEM_FLAG_SLOTS) return;
+    const bool rb = D.rebuild != 0;
+    const int lp = rb ? D.cpar ^ 1 : D.cpar, par = D.parity;
+    const int64_t s0 = S.s0, e0 = S.e0;
+    typename CT<FP64>::Prm prm;
+    const H *hread;
+    H *hwrite;
+    if constexpr (FP64) {
+        prm = {S.kn, S.kt, S.cn, S.ct, S.mu_s, S.mu_r, S.mu_t, S.w0, S.h};
+        hread = (rb ? a.hist64_rm : a.hist64[par]) + e0;
+        hwrite = a.hist64[par ^ 1] + e0;
+    } else {
+        prm = {(float)S.kn, (float)S.kt, (float)S.cn, (float)S.ct, (float)S.mu_s, (float)S.mu_r,
+               (float)S.mu_t, (float)S.w0, (float)S.h};
+        hread = (rb ? a.hist32_rm : a.hist32[par]) + e0;
+        hwrite = a.hist32[par ^ 1] + e0;
+    }
+    const float q = pow2f(S.qexp);
+    const int2 *cand = a.cand[lp] + e0;
+    const int off = a.coff[lp][k], n = a.ccnt[lp][k];
+    // own data
+    typename CT<FP64>::P mp;
+    float4 mr;
+    typename CT<FP64>::VR mv, mw;
+    if constexpr (FP64) { mp = a.dp_[k]; mv = a.dv_[k]; mw = a.dw_[k]; }
+    else {
+        mp = s_x[2 * threadIdx.x]; mr = as_f4(s_x[2 * threadIdx.x + 1]);
+        mv = s_v[2 * threadIdx.x]; mw = s_v[2 * threadIdx.x + 1];
+    }
+    V F, Tq;
+    if constexpr (FP64) { F = d3(0, 0, 0); Tq = d3(0, 0, 0); }
+    else { F = f3(0.f, 0.f, 0.f); Tq = f3(0.f, 0.f, 0.f); }
+    int nc = 0, flags = 0;
+    // One entry: this sphere as sphere a.  Every step of the law maps exactly
+    // onto its negative or onto itself when the spheres swap (differences and
+    // products of negated operands round to the negated or the same value),
+    // so this evaluation's share a is bit for bit the share of this side of
+    // the owner's evaluation; the owner's S is seen from this side with the
+    // opposite sign.  The owner's thread writes the history.
+    auto entry = [&](int f, bool owned, bool ok, const H &hp, const typename CT<FP64>::P &pp,
+                     const float4 &pr, const typename CT<FP64>::VR &pv, const typename CT<FP64>::VR &pw) {
+        PairOut<T, V> o;
+        bool hit = false;
+        const T sgn = owned ? T(1) : T(-1);
+        if (ok) {
+            if constexpr (FP64) {
+                const double3 Sprev = hp.w != 0 ? d3(sgn * hp.x, sgn * hp.y, sgn * hp.z) : d3(0, 0, 0);
+                hit = pair_64(mp, mv, mw, pp, pv, pw, Sprev, prm, o);
+            } else {
+                const float3 Sprev = hp.w != 0.f ? f3(sgn * hp.x, sgn * hp.y, sgn * hp.z) : f3(0.f, 0.f, 0.f);
+                hit = pair_mixed(mp, mr, pp, pr, q, mv, mw, pv, pw, Sprev, prm, o);
+            }
+        }
+        if (owned && ok) {
+            H h;
+            if constexpr (FP64) h = hit ? make_dbl4(o.S.x, o.S.y, o.S.z, 1.0) : make_dbl4(0, 0, 0, 0);
+            else h = hit ? make_float4(o.S.x, o.S.y, o.S.z, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+            hwrite[f] = h;
+        }
+        if (!hit) return;
+        if (o.x > T(0.1) * o.rmin) flags |= DEM_FLAG_OVERLAP;
+        V sF, sT;
+        share<T, V>(o, true, sF, sT);
+        F.x = addr(F.x, sF.x); F.y = addr(F.y, sF.y); F.z = addr(F.z, sF.z);
+        Tq.x = addr(Tq.x, sT.x); Tq.y = addr(Tq.y, sT.y); Tq.z = addr(Tq.z, sT.z);
+        ++nc;
+    };
+    // an entry's partner and history indices (clamped: the checks never fail)
+    auto where = [&](int2 c, int f, int64_t &g, int &hidx, bool &ok) {
+        const int kk = c.x & 0x7fffffff;
+        hidx = c.x < 0 ? f : c.y;
+        ok = (unsigned)kk < (unsigned)S.ns && (unsigned)hidx < (unsigned)S.ne;
+        g = s0 + (ok ? kk : 0);
+        if (!ok) hidx = 0;
+    };
+    if constexpr (FP64) {
+        for (int e = 0; e < n; ++e) {
+            const int f = off + 32 * e;
+            const int2 c = cand[f];
+            int64_t g;
+            int hidx;
+            bool ok;
+            where(c, f, g, hidx, ok);
+            entry(f, c.x < 0, ok, hread[hidx], a.dp_[g], make_float4(0.f, 0.f, 0.f, 0.f), a.dv_[g], a.dw_[g]);
+        }
+    } else {
+        // software pipeline: the list entry two ahead and the partner data and
+        // history one ahead are in flight while an entry is evaluated
+        int2 c1 = make_int2(0, 0);
+        if (n > 1) c1 = cand[off + 32];
+        int2 cc = make_int2(0, 0);
+        int4 px = make_int4(0, 0, 0, 0), pr = px;
+        float4 pv = make_float4(0.f, 0.f, 0.f, 0.f), pw = pv;
+        H hp = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool ok = false;
+        if (n > 0) {
+            cc = cand[off];
+            int64_t g;
+            int hidx;
+            where(cc, off, g, hidx, ok);
+            const int64_t lk = g - kb0;
+            if ((uint64_t)lk < 128) {
+                px = s_x[2 * lk]; pr = s_x[2 * lk + 1]; pv = s_v[2 * lk]; pw = s_v[2 * lk + 1];
+            } else {
+                px = a.xqr[2 * g]; pr = a.xqr[2 * g + 1]; pv = a.svw[2 * g]; pw = a.svw[2 * g + 1];
+            }
+            hp = hread[hidx];
+        }
+        for (int e = 0; e < n; ++e) {
+            const int f = off + 32 * e;
+            int4 nx = px, nr = pr;
+            float4 nv = pv, nw = pw;
+            H nh = hp;
+            bool nok = false;
+            if (e + 1 < n) {
+                int64_t g;
+                int hidx;
+                where(c1, f + 32, g, hidx, nok);
+                const int64_t lk = g - kb0;
+                if ((uint64_t)lk < 128) {
+                    nx = s_x[2 * lk]; nr = s_x[2 * lk + 1]; nv = s_v[2 * lk]; nw = s_v[2 * lk + 1];
+                } else {
+                    nx = a.xqr[2 * g]; nr = a.xqr[2 * g + 1]; nv = a.svw[2 * g]; nw = a.svw[2 * g + 1];
+                }
+                nh = hread[hidx];
+            }
+            const int2 c2 = e + 2 < n ? cand[f + 64] : make_int2(0, 0);
+            entry(f, cc.x < 0, ok, hp, px, as_f4(pr), pv, pw);
+            cc = c1; c1 = c2;
+            px = nx; pr = nr; pv = nv; pw = nw; hp = nh; ok = nok;
+        }
+    }
+    if constexpr (FP64) {
+        a.ftc64[2 * k] = make_dbl4(F.x, F.y, F.z, 0.0);
+        a.ftc64[2 * k + 1] = make_dbl4(Tq.x, Tq.y, Tq.z, 0.0);
+    } else {
+        a.ftc32[2 * k] = make_float4(F.x, F.y, F.z, 0.f);
+        a.ftc32[2 * k + 1] = make_float4(Tq.x, Tq.y, Tq.z, 0.f);
+    }
+    if (nc > S.K) flags |= DEM_FLAG_SLOTS;
+    if (flags) atomicOr(&a.pd[p].flags, flags);
 }
 
 cudaError_t contact_setup(bool fp64, int)
@@ -770,18 +1105,23 @@ void launch_contact(const Arrays &a, const Sizes &z, bool fp64, int, cudaStream_
 {
     if (z.N == 0 || z.CT == 0) return;
     const unsigned nt = (unsigned)z.CT;
+    // the rebuild kernels walk the tiles with a grid of a few blocks per SM:
+    // in steps without a rebuild they only read each tile's pile flags
+    const unsigned ng = (unsigned)(z.CT < 1024 ? z.CT : 1024);
     if (fp64) {
-        launch_pdl(k_cand_count<true>, nt, kCTile, 0, st, a, z);
+        launch_pdl(k_cand_count<true>, ng, kCTile, 0, st, a, z);
         launch_pdl(k_cand_scan, (unsigned)z.P, 1024, 0, st, a, z);
-        launch_pdl(k_cand_fill<true>, nt, kCTile, 0, st, a, z);
-        launch_pdl(k_cand_link<true>, nt, kCTile, 0, st, a, z);
-        launch_pdl(k_contact<true>, nt, kCTile, Smem<true>::total, st, a, z);
+        launch_pdl(k_cand_fill<true>, ng, kCTile, 0, st, a, z);
+        launch_pdl(k_cand_link<true>, ng, kCTile, 0, st, a, z);
+        if (z.cmode == 1) launch_pdl(k_contact<true>, nt, kCTile, Smem<true>::total, st, a, z);
+        else launch_pdl(k_contact_sphere<true>, (unsigned)((z.N + 127) / 128), 128, 0, st, a, z);
     } else {
-        launch_pdl(k_cand_count<false>, nt, kCTile, 0, st, a, z);
+        launch_pdl(k_cand_count<false>, ng, kCTile, 0, st, a, z);
         launch_pdl(k_cand_scan, (unsigned)z.P, 1024, 0, st, a, z);
-        launch_pdl(k_cand_fill<false>, nt, kCTile, 0, st, a, z);
-        launch_pdl(k_cand_link<false>, nt, kCTile, 0, st, a, z);
-        launch_pdl(k_contact<false>, nt, kCTile, Smem<false>::total, st, a, z);
+        launch_pdl(k_cand_fill<false>, ng, kCTile, 0, st, a, z);
+        launch_pdl(k_cand_link<false>, ng, kCTile, 0, st, a, z);
+        if (z.cmode == 1) launch_pdl(k_contact<false>, nt, kCTile, Smem<false>::total, st, a, z);
+        else launch_pdl(k_contact_sphere<false>, (unsigned)((z.N + 127) / 128), 128, 0, st, a, z);
     }
 }
 

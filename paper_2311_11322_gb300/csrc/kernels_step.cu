@@ -744,11 +744,12 @@ __global__ void k_gather(Arrays a, Sizes z)
         float4 rm;
         const int X = ff_to_fixed(px, e, rm.x), Y = ff_to_fixed(py, e, rm.y), Z = ff_to_fixed(pz, e, rm.z);
         const int Sr = ff_to_fixed(ff{bh.w, bl.w}, e, rm.w);
-        a.xq[k] = make_int4(X, Y, Z, Sr);
-        a.xr[k] = rm;
+        a.xqr[2 * k] = make_int4(X, Y, Z, Sr);
+        a.xqr[2 * k + 1] = make_int4(__float_as_int(rm.x), __float_as_int(rm.y), __float_as_int(rm.z),
+                                     __float_as_int(rm.w));
         if (a.pd[p].rebuild) a.sph_[k] = make_float4(px.hi, py.hi, pz.hi, bh.w);
-        a.sv_[k] = make_float4(v.x, v.y, v.z, __int_as_float(al));
-        a.sw_[k] = make_float4(w.x, w.y, w.z, __int_as_float(hl));
+        a.svw[2 * k] = make_float4(v.x, v.y, v.z, __int_as_float(al));
+        a.svw[2 * k + 1] = make_float4(w.x, w.y, w.z, __int_as_float(hl));
     }
 }
 

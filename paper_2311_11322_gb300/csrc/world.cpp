@@ -87,6 +87,7 @@ struct dem_world {
     double cell_factor = 1.0;
     double skin_frac = 0.1;           // neighbour-list skin / largest radius
     int contact_inbox = kInboxCap;    // contact inbox entries per tile range (testing: smaller splits more)
+    int contact_mode = 0;             // 0: one thread per sphere, 1: tiles with a shared-memory inbox
     // flags readback
     PileDyn *h_dyn = nullptr;   // pinned
     int64_t h_dyn_cap = 0;
@@ -207,11 +208,9 @@ void build_fields(dem_world *w)
     } else {
         add((void **)&a.bh, C_SPH, 16, true);
         add((void **)&a.bl, C_SPH, 16, true);
-        add((void **)&a.xq, C_SPH, 16, false);
-        add((void **)&a.xr, C_SPH, 16, false);
+        add((void **)&a.xqr, C_SPH, 32, false);
         add((void **)&a.sph_, C_SPH, 16, false);
-        add((void **)&a.sv_, C_SPH, 16, false);
-        add((void **)&a.sw_, C_SPH, 16, false);
+        add((void **)&a.svw, C_SPH, 32, false);
         add((void **)&a.gpos32, C_SPH, 16, false);
         add((void **)&a.ftc32, C_SPH, 32, true);
         add((void **)&a.hist32[0], C_ENT, 16, true);
@@ -564,6 +563,7 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     }
     w->Z.gtile = gp.tile;
     w->Z.icap = w->contact_inbox;
+    w->Z.cmode = w->contact_mode;
     int bps = gravity_blocks_per_sm(w->precision == DEM_FP64, w->grav_block, w->grav_ib, w->grav_pack,
                                     use_sym(w), gp.tile);
     CU(cudaGetLastError());
@@ -1376,8 +1376,10 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
         CHK(get(cnt.data(), D.ccnt[cp] + s0, 4 * N));
         CHK(get(off.data(), D.coff[cp] + s0, 4 * N));
         CHK(get(pos.data(), D.pos_of_home[par] + s0, 4 * N));
+        // sliced layout: entry e of sorted sphere k at off[k] + 32 e
         int64_t E = 0;
-        for (int64_t k = 0; k < N; ++k) E = std::max<int64_t>(E, (int64_t)off[k] + cnt[k]);
+        for (int64_t k = 0; k < N; ++k)
+            if (cnt[k] > 0) E = std::max<int64_t>(E, (int64_t)off[k] + 32 * ((int64_t)cnt[k] - 1) + 1);
         E = std::min<int64_t>(E, pile_count(w, q, C_ENT));
         std::vector<int32_t> ids(E);
         std::vector<int2> cd(E);
@@ -1401,8 +1403,8 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
             const int64_t k = pos[i];
             int n = 0;
             for (int e = 0; e < cnt[k]; ++e) {
-                const int64_t f = (int64_t)off[k] + e;
-                if (f >= E) break;
+                const int64_t f = (int64_t)off[k] + 32 * (int64_t)e;
+                if (f < 0 || f >= E) break;
                 const int64_t h = cd[f].x < 0 ? f : (int64_t)cd[f].y;
                 if (h < 0 || h >= E || hs[4 * h + 3] == 0.0) continue;
                 if (n < K) {
@@ -1520,13 +1522,19 @@ dem_status dem_write_state(dem_world *w, int32_t pile_id, int32_t field, const d
                 if (rows[i][t].first == rows[i][t - 1].first)
                     return fail(w, DEM_ERR_ARG, "sphere %lld: partner listed twice", (long long)i);
         }
-        // offsets in sorted-position order
+        // sliced layout as the library builds it: slices of 32 sorted
+        // positions, each as wide as its longest list, entry e of sphere k at
+        // off[k] + 32 e
         std::vector<int32_t> cnt(N), off(N);
         int64_t E = 0;
-        for (int64_t k = 0; k < N; ++k) {
-            cnt[k] = (int32_t)rows[home[k]].size();
-            off[k] = (int32_t)E;
-            E += cnt[k];
+        for (int64_t k0 = 0; k0 < N; k0 += 32) {
+            int64_t wmax = 0;
+            for (int64_t k = k0; k < std::min<int64_t>(N, k0 + 32); ++k) {
+                cnt[k] = (int32_t)rows[home[k]].size();
+                wmax = std::max<int64_t>(wmax, cnt[k]);
+                off[k] = (int32_t)(E + (k - k0));
+            }
+            E += 32 * wmax;
         }
         if (E > cap) return fail(w, DEM_ERR_ARG, "too many contacts for the pile's candidate lists");
         std::vector<int32_t> ids(E);
@@ -1535,14 +1543,14 @@ dem_status dem_write_state(dem_world *w, int32_t pile_id, int32_t field, const d
         for (int64_t k = 0; k < N; ++k) {
             const int32_t i = home[k];
             for (int e = 0; e < cnt[k]; ++e) {
-                const int64_t f = off[k] + e;
+                const int64_t f = off[k] + 32 * (int64_t)e;
                 const int32_t J = rows[i][e].first;
                 // this pair in J's row
                 const auto &rj = rows[J];
                 auto it = std::lower_bound(rj.begin(), rj.end(), std::make_pair(i, -1));
                 if (it == rj.end() || it->first != i)
                     return fail(w, DEM_ERR_ARG, "contact %d-%d listed by one sphere only", i, J);
-                const int64_t mir = off[pos[J]] + (it - rj.begin());
+                const int64_t mir = off[pos[J]] + 32 * (int64_t)(it - rj.begin());
                 ids[f] = J;
                 const bool owned = i < J;
                 cd[f] = make_int2(pos[J] | (owned ? (int)0x80000000u : 0), (int)mir);
@@ -1648,6 +1656,9 @@ dem_status dem_set_tuning(dem_world *w, const char *key, double value)
     } else if (k == "grav_item") {
         if (!(value >= 1024.0)) return fail(w, DEM_ERR_ARG, "grav_item must be >= 1024");
         w->grav_item = value;
+    } else if (k == "contact_mode") {
+        if (value != 0.0 && value != 1.0) return fail(w, DEM_ERR_ARG, "contact_mode must be 0 or 1");
+        w->contact_mode = (int)value;
     } else if (k == "contact_inbox") {
         if (!(value >= 1.0) || value > kInboxCap)
             return fail(w, DEM_ERR_ARG, "contact_inbox must be in [1, %d]", kInboxCap);
@@ -1687,6 +1698,7 @@ dem_status dem_get_tuning(dem_world *w, const char *key, double *value_out)
     else if (k == "cell_factor") *value_out = w->cell_factor;
     else if (k == "skin") *value_out = w->skin_frac;
     else if (k == "contact_inbox") *value_out = w->contact_inbox;
+    else if (k == "contact_mode") *value_out = w->contact_mode;
     else return fail(w, DEM_ERR_ARG, "unknown tuning key '%s'", key);
     return DEM_OK;
 }

@@ -124,13 +124,15 @@ def test_inbox_ranges_do_not_change_results(dem, prec):
     sphere ranges, and pairs between ranges are evaluated by both.  Forcing
     small ranges (most pairs then cross) must give bit-identical states,
     forces and histories: every pair's shares come from the same canonical
-    evaluation and every sphere sums them in partner order."""
+    evaluation and every sphere sums them in partner order.  The one-thread-
+    per-sphere form (each pair evaluated by both spheres) must agree too."""
     ic, p = W.dense_lattice(n_spheres=4000, seed=3, precision=prec, speed=0.01)
     res = []
-    for cap in (2560, 96, 40):
+    for mode, cap in ((1, 1280), (1, 96), (1, 40), (0, 1280)):
         with dem.World() as w:
+            w.set_tuning("contact_mode", mode)
             w.set_tuning("contact_inbox", cap)
-            assert w.get_tuning("contact_inbox") == cap
+            assert w.get_tuning("contact_inbox") == cap and w.get_tuning("contact_mode") == mode
             pid = w.add_pile(ic, p)
             w.step(30)
             w.sync()
