@@ -77,6 +77,8 @@ struct PileStatic {
 // Dynamic per-pile state (device-owned; written by kernels).
 struct PileDyn {
     double O[3], V[3];        // frame of positions / velocities used this step
+    float hVf[3];             // h V in FP32 (the neighbour-list test)
+    int32_t pad_dyn;
     double Rc[3], Vc[3];      // pile COM after the drift, mean velocity after the first kick
     double P_pos[3], P_vel[3], P_acc[3];   // planet
     int64_t steps;
@@ -177,11 +179,14 @@ struct Arrays {
     double *r, *v, *q, *wb, *acc, *torque;   // [A][3], q [A][4]
     AggRecMixed *rec32;
     AggRec64 *rec64;
-    double *out;                   // [A][18]: FA_c NA_c FA_g NA_g FA_e NA_e
+    double *out;                   // [A][18]: FA_c NA_c FA_g NA_g FA_e NA_e (FP64 path); in the
+                                   // mixed path the same 144 bytes hold 18 float-float pairs
+    int32_t out_ff;                // 1: out holds float-float pairs
+    double *invM;                  // [A] 1 / M
     // neighbour-list reference per aggregate: position relative to the
     // extrapolated pile frame and orientation at the last rebuild, and the
     // largest member offset |b| (fixed): [A][8] = c_ref[3], q_ref[4], bmax
-    double *aref;
+    float *aref;
     // cells
     int32_t *ccount, *cstart, *tile_sum;
     // pile reductions

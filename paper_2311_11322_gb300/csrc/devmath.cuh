@@ -79,6 +79,45 @@ __device__ __forceinline__ ff ff_dot3(const float *Rh, const float *Rl, float bx
     return r;
 }
 
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    float p, e;
+    two_prod(a.hi, b.hi, p, e);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    ff r;
+    fast_two_sum(p, e, r.hi, r.lo);
+    return r;
+}
+
+__device__ __forceinline__ ff ff_of(double x)
+{
+    ff r;
+    r.hi = __double2float_rn(x);
+    r.lo = __double2float_rn(x - (double)r.hi);
+    return r;
+}
+
+__device__ __forceinline__ double ff_value(ff v) { return (double)v.hi + (double)v.lo; }
+
+// Rotation matrix (body -> space) of the unit quaternion q = (w, x, y, z) in
+// float-float, to ~2^-44: the FP64 quaternion is split once and every product
+// and sum is an error-free FP32 transformation (FP64 instructions are ~60
+// times slower than FP32 ones on this part).
+__device__ __forceinline__ void quat_to_R_ff(const double *q, float *Rh, float *Rl, float *qhi)
+{
+    const ff w = ff_of(q[0]), x = ff_of(q[1]), y = ff_of(q[2]), z = ff_of(q[3]);
+    qhi[0] = w.hi; qhi[1] = x.hi; qhi[2] = y.hi; qhi[3] = z.hi;
+    const ff xx = ff_mul(x, x), yy = ff_mul(y, y), zz = ff_mul(z, z);
+    const ff xy = ff_mul(x, y), xz = ff_mul(x, z), yz = ff_mul(y, z);
+    const ff wx = ff_mul(w, x), wy = ff_mul(w, y), wz = ff_mul(w, z);
+    const ff one = {1.0f, 0.0f};
+    auto twice = [](ff a) { return ff{2.0f * a.hi, 2.0f * a.lo}; };
+    const ff R[9] = {ff_sub(one, twice(ff_add(yy, zz))), twice(ff_sub(xy, wz)), twice(ff_add(xz, wy)),
+                     twice(ff_add(xy, wz)), ff_sub(one, twice(ff_add(xx, zz))), twice(ff_sub(yz, wx)),
+                     twice(ff_sub(xz, wy)), twice(ff_add(yz, wx)), ff_sub(one, twice(ff_add(xx, yy)))};
+    for (int k = 0; k < 9; ++k) { Rh[k] = R[k].hi; Rl[k] = R[k].lo; }
+}
+
 // Running float-float sum (TwoSum of each term, rounding errors collected in
 // the low word): FP32 terms added with ~FP64 accuracy on the FP32 units (the
 // FP64 units of this part are ~60 times slower).

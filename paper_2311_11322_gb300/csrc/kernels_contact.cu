@@ -440,12 +440,22 @@ __device__ __forceinline__ bool tile_rebuilds(const Arrays &a, int4 tl)
     return pile_live(a, tl.x) && a.pd[tl.x].rebuild;
 }
 
+// Whether any pile rebuilds this step (the block's threads read the piles'
+// flags together): in most steps no pile does, and the rebuild kernels end here.
+__device__ __forceinline__ bool any_rebuild(const Arrays &a, const Sizes &z)
+{
+    int mine = 0;
+    for (int p = threadIdx.x; p < z.P; p += blockDim.x) mine |= pile_live(a, p) && a.pd[p].rebuild;
+    return __syncthreads_or(mine) != 0;
+}
+
 // Candidates per sphere (new list buffer) and per tile.
 template <bool FP64>
 __global__ void __launch_bounds__(kCTile) k_cand_count(Arrays a, Sizes z)
 {
     pdl_enter();
     __shared__ int red[kCTile / 32];
+    if (!any_rebuild(a, z)) return;
     for (int64_t tile = blockIdx.x; tile < z.CT; tile += gridDim.x) {
     const int4 tl = a.ctile[tile];
     if (!tile_rebuilds(a, tl)) continue;
@@ -581,6 +591,7 @@ __global__ void __launch_bounds__(kCTile) k_cand_fill(Arrays a, Sizes z)
     pdl_enter();
     __shared__ int sw[kCTile / 32];
     __shared__ int2 s_list[kFillCap][kCTile];   // (partner home index, sorted position)
+    if (!any_rebuild(a, z)) return;
     for (int64_t tile = blockIdx.x; tile < z.CT; tile += gridDim.x) {
         __syncthreads();   // sw[] of the previous tile
         const int4 tl = a.ctile[tile];
@@ -652,6 +663,7 @@ template <bool FP64>
 __global__ void __launch_bounds__(kCTile) k_cand_link(Arrays a, Sizes z)
 {
     pdl_enter();
+    if (!any_rebuild(a, z)) return;
     for (int64_t tile = blockIdx.x; tile < z.CT; tile += gridDim.x) {
         const int4 tl = a.ctile[tile];
         if (!tile_rebuilds(a, tl) || a.ctile_base[tile] < 0 || (int)threadIdx.x >= tl.z) continue;
@@ -1107,7 +1119,7 @@ void launch_contact(const Arrays &a, const Sizes &z, bool fp64, int, cudaStream_
     const unsigned nt = (unsigned)z.CT;
     // the rebuild kernels walk the tiles with a grid of a few blocks per SM:
     // in steps without a rebuild they only read each tile's pile flags
-    const unsigned ng = (unsigned)(z.CT < 1024 ? z.CT : 1024);
+    const unsigned ng = (unsigned)(z.CT < 512 ? z.CT : 512);
     if (fp64) {
         launch_pdl(k_cand_count<true>, ng, kCTile, 0, st, a, z);
         launch_pdl(k_cand_scan, (unsigned)z.P, 1024, 0, st, a, z);

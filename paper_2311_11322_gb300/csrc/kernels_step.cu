@@ -103,10 +103,10 @@ __device__ __forceinline__ void rot_rhs_f(const float *y, const float *I, const 
     dy[4] = dw.x; dy[5] = dw.y; dy[6] = dw.z;
 }
 
-__device__ void free_rotate_mixed(double *q, double3 &wb, const float *I, const float *Iinv, float h)
+__device__ void free_rotate_mixed(double *q, double3 &wb, const float *qf, const float *I, const float *Iinv,
+                                  float h)
 {
-    float y[7] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3],
-                  (float)wb.x, (float)wb.y, (float)wb.z};
+    float y[7] = {qf[0], qf[1], qf[2], qf[3], (float)wb.x, (float)wb.y, (float)wb.z};
     float k1[7], k2[7], k3[7], k4[7], t[7];
     rot_rhs_f(y, I, Iinv, k1);
     for (int c = 0; c < 7; ++c) t[c] = y[c] + 0.5f * h * k1[c];
@@ -118,7 +118,10 @@ __device__ void free_rotate_mixed(double *q, double3 &wb, const float *I, const 
     float d[7];
     for (int c = 0; c < 7; ++c) d[c] = (h / 6.0f) * (k1[c] + 2.0f * k2[c] + 2.0f * k3[c] + k4[c]);
     double q0 = q[0] + d[0], q1 = q[1] + d[1], q2 = q[2] + d[2], q3 = q[3] + d[3];
-    double inv = rsqrt(q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+    // |q|^2 = 1 + e with e ~ |d|^2 (the increment is tangent to the unit
+    // sphere): 1/|q| = 1 - e/2 + 3e^2/8 - ..., the dropped terms O(e^3)
+    const double e = (q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3) - 1.0;
+    const double inv = 1.0 + e * (-0.5 + 0.375 * e);
     q[0] = q0 * inv; q[1] = q1 * inv; q[2] = q2 * inv; q[3] = q3 * inv;
     wb = d3(wb.x + d[4], wb.y + d[5], wb.z + d[6]);
 }
@@ -206,6 +209,7 @@ __global__ void k_agg_begin(Arrays a, Sizes z)
     double3 r = ld3(a.r + 3 * g), v = ld3(a.v + 3 * g), wb = ld3(a.wb + 3 * g);
     double3 acc = ld3(a.acc + 3 * g), N = ld3(a.torque + 3 * g);
     double R[9];
+    float Rf[9], Rlo[9], qf[4];
     double3 ws;
     float3 wsf;
     if constexpr (FP64) {
@@ -223,8 +227,7 @@ __global__ void k_agg_begin(Arrays a, Sizes z)
         // spin kicks and the rotor's stage derivatives are increments: FP32
         const float *I32 = a.I32 + 18 * g, *Iinv32 = I32 + 9;
         const float hf = (float)h;
-        float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
-        float Rf[9];
+        for (int c = 0; c < 4; ++c) qf[c] = (float)q[c];
         quat_to_Rf(qf, Rf);
         const float3 Nf = f3((float)N.x, (float)N.y, (float)N.z);
         const float3 dw = (0.5f * hf) * mat_mulf(Iinv32, mat_tmulf(Rf, Nf));
@@ -232,10 +235,9 @@ __global__ void k_agg_begin(Arrays a, Sizes z)
         wb = d3(wb.x + dw.x, wb.y + dw.y, wb.z + dw.z);
         r = r + h * v;
         if (ADAPT && a.ps[p].rot_tol > 0.0) free_rotate_adaptive(q, wb, I, Iinv, h, a.ps[p].rot_tol);
-        else free_rotate_mixed(q, wb, I32, Iinv32, hf);
-        quat_to_R(q, R);
-        for (int c = 0; c < 4; ++c) qf[c] = (float)q[c];
-        quat_to_Rf(qf, Rf);
+        else free_rotate_mixed(q, wb, qf, I32, Iinv32, hf);
+        // rotation matrix in float-float straight from the FP64 quaternion
+        quat_to_R_ff(q, Rf, Rlo, qf);
         const float3 wpred = f3((float)wb.x, (float)wb.y, (float)wb.z) +
                              (0.5f * hf) * mat_mulf(Iinv32, mat_tmulf(Rf, Nf));
         wsf = mat_mulf(Rf, wpred);
@@ -248,23 +250,36 @@ __global__ void k_agg_begin(Arrays a, Sizes z)
     const PileDyn &D = a.pd[p];
     double3 c = r - ld3(D.O);
     double3 vb = v + (0.5 * h) * acc - ld3(D.V);
+    ff cx, cy, cz;
+    if constexpr (!FP64) { cx = ff_of(c.x); cy = ff_of(c.y); cz = ff_of(c.z); }
+    else { cx = ff{(float)c.x, 0.f}; cy = ff{(float)c.y, 0.f}; cz = ff{(float)c.z, 0.f}; }
     // Neighbour-list validity.  Every sphere of the aggregate moved, relative
     // to the pile frame extrapolated by one step (O + h V), by at most
     // |c' - c'_ref| + |(R - R_ref) b| <= |c' - c'_ref| + 2 |b|max min|q -+ q_ref|
-    // since the last rebuild.  The hit lists hold every pair closer than the
-    // radii sum plus the skin at the rebuild, so they stay complete while no
-    // sphere has moved more than half the skin.
+    // since the last rebuild.  The candidate lists hold every pair closer than
+    // the radii sum plus the skin at the rebuild, so they stay complete while
+    // no sphere has moved more than half the skin.  The bound is taken in
+    // FP32 (positions relative to the pile frame, reference stored in FP32)
+    // with a margin of a few units in the last place of the positions and
+    // 1e-4 relative, far above its rounding.
     const double skin = a.ps[p].skin;
     if (skin > 0.0) {
-        const double *ar = a.aref + 8 * g;
-        double3 dc = c - h * ld3(D.V) - d3(ar[0], ar[1], ar[2]);
-        double dm = 0.0, dp = 0.0;
+        const float *ar = a.aref + 8 * g;
+        const float *hv = D.hVf;
+        const float3 dcf = f3(cx.hi - hv[0] - ar[0], cy.hi - hv[1] - ar[1], cz.hi - hv[2] - ar[2]);
+        float qn[4];
+        if constexpr (FP64) { for (int k = 0; k < 4; ++k) qn[k] = (float)q[k]; }
+        else { for (int k = 0; k < 4; ++k) qn[k] = qf[k]; }
+        float dm = 0.f, dp = 0.f;
         for (int k = 0; k < 4; ++k) {
-            dm += (q[k] - ar[3 + k]) * (q[k] - ar[3 + k]);
-            dp += (q[k] + ar[3 + k]) * (q[k] + ar[3 + k]);
+            const float m = qn[k] - ar[3 + k], s_ = qn[k] + ar[3 + k];
+            dm = fmaf(m, m, dm);
+            dp = fmaf(s_, s_, dp);
         }
-        double disp = sqrt(dot(dc, dc)) + 2.0 * ar[7] * sqrt(fmin(dm, dp));
-        if (!(disp <= 0.5 * skin * (1.0 - 1e-6))) atomicOr(&a.pd[p].rebuild, 1);
+        const float big = fmaxf(fabsf(cx.hi), fmaxf(fabsf(cy.hi), fabsf(cz.hi))) +
+                          fmaxf(fabsf(ar[0]), fmaxf(fabsf(ar[1]), fabsf(ar[2])));
+        const float disp = sqrtf(dot(dcf, dcf)) + 2.0f * ar[7] * sqrtf(fminf(dm, dp)) + 1e-6f * (big + ar[7]);
+        if (!(disp * 1.0001f <= 0.5f * (float)skin)) atomicOr(&a.pd[p].rebuild, 1);
     }
     if (FP64) {
         AggRec64 rec;
@@ -275,10 +290,10 @@ __global__ void k_agg_begin(Arrays a, Sizes z)
         a.rec64[g] = rec;
     } else {
         AggRecMixed rec;
-        for (int k = 0; k < 9; ++k) split_d(R[k], rec.Rh[k], rec.Rl[k]);
-        split_d(c.x, rec.ch[0], rec.cl[0]);
-        split_d(c.y, rec.ch[1], rec.cl[1]);
-        split_d(c.z, rec.ch[2], rec.cl[2]);
+        for (int k = 0; k < 9; ++k) { rec.Rh[k] = Rf[k]; rec.Rl[k] = Rlo[k]; }
+        rec.ch[0] = cx.hi; rec.cl[0] = cx.lo;
+        rec.ch[1] = cy.hi; rec.cl[1] = cy.lo;
+        rec.ch[2] = cz.hi; rec.cl[2] = cz.lo;
         rec.vb[0] = (float)vb.x; rec.vb[1] = (float)vb.y; rec.vb[2] = (float)vb.z;
         rec.w[0] = wsf.x; rec.w[1] = wsf.y; rec.w[2] = wsf.z;
         rec.pad[0] = rec.pad[1] = 0.f;
@@ -349,6 +364,7 @@ __device__ void pile_finalize_block(const Arrays &a, int p, double (&sh)[7][128]
         for (int c = 0; c < 3; ++c) {
             D.O[c] = D.Rc[c];
             D.V[c] = D.Vc[c];
+            D.hVf[c] = (float)(h * D.Vc[c]);
         }
         D.steps += 1;
         D.parity ^= 1;
@@ -381,9 +397,9 @@ __global__ void __launch_bounds__(128) k_pile_reduce(Arrays a, Sizes z)
             if (MODE == 0) {
                 if (a.pd[p].rebuild) {   // new neighbour-list reference
                     const PileDyn &D = a.pd[p];
-                    double *ar = a.aref + 8 * g;
-                    for (int c = 0; c < 3; ++c) ar[c] = a.r[3 * g + c] - D.O[c] - S.h * D.V[c];
-                    for (int c = 0; c < 4; ++c) ar[3 + c] = a.q[4 * g + c];
+                    float *ar = a.aref + 8 * g;
+                    for (int c = 0; c < 3; ++c) ar[c] = (float)(a.r[3 * g + c] - D.O[c] - S.h * D.V[c]);
+                    for (int c = 0; c < 4; ++c) ar[3 + c] = (float)a.q[4 * g + c];
                 }
                 double M = a.M[g];
                 acc[0] += M;
@@ -391,6 +407,9 @@ __global__ void __launch_bounds__(128) k_pile_reduce(Arrays a, Sizes z)
                     acc[1 + c] += M * a.r[3 * g + c];
                     acc[4 + c] += M * a.v[3 * g + c];
                 }
+            } else if (a.out_ff) {   // mixed path: the parts are float-float pairs
+                const float2 *o32 = (const float2 *)(a.out + 18 * g);
+                for (int c = 0; c < 3; ++c) acc[c] += (double)o32[12 + c].x + (double)o32[12 + c].y;
             } else {
                 for (int c = 0; c < 3; ++c) acc[c] += a.out[18 * g + 12 + c];
             }
@@ -816,21 +835,37 @@ __global__ void k_agg_end(Arrays a, Sizes z)
         const AggRecMixed &rec = a.rec32[g];
         float Rh[9];
         for (int k = 0; k < 9; ++k) Rh[k] = rec.Rh[k];
-        for (int t = 0; t < n; ++t) {
-            int64_t i = i0 + t;
-            const float4 bh = a.bh[i];
+        // members in order; the loads of two members are issued together
+        auto term = [&](float4 bh, float4 f, float4 tq, dbl4 gg) {
             const float3 lever = mat_mulf(Rh, f3(bh.x, bh.y, bh.z));
-            const int64_t ks = S.s0 + poh[i];
-            const float4 f = a.ftc32[2 * ks], tq = a.ftc32[2 * ks + 1];
             const float3 fc = f3(f.x, f.y, f.z);
             const float3 nc = cross(lever, fc) + f3(tq.x, tq.y, tq.z);
-            const dbl4 gg = a.fg[i];
             const float3 fg = f3((float)gg.x, (float)gg.y, (float)gg.z);
             const float3 ng = cross(lever, fg);
             s[0].add(fc.x); s[1].add(fc.y); s[2].add(fc.z);
             s[3].add(nc.x); s[4].add(nc.y); s[5].add(nc.z);
             s[6].add(fg.x); s[7].add(fg.y); s[8].add(fg.z);
             s[9].add(ng.x); s[10].add(ng.y); s[11].add(ng.z);
+        };
+        int t2 = 0;
+        if (!planet) {
+            for (; t2 + 1 < n; t2 += 2) {
+                const int64_t i = i0 + t2;
+                const int64_t ka = S.s0 + poh[i], kb = S.s0 + poh[i + 1];
+                const float4 bha = a.bh[i], bhb = a.bh[i + 1];
+                const float4 fa = a.ftc32[2 * ka], ta = a.ftc32[2 * ka + 1];
+                const float4 fb = a.ftc32[2 * kb], tb = a.ftc32[2 * kb + 1];
+                const dbl4 ga = a.fg[i], gb = a.fg[i + 1];
+                term(bha, fa, ta, ga);
+                term(bhb, fb, tb, gb);
+            }
+        }
+        for (int t = t2; t < n; ++t) {
+            int64_t i = i0 + t;
+            const float4 bh = a.bh[i];
+            const float3 lever = mat_mulf(Rh, f3(bh.x, bh.y, bh.z));
+            const int64_t ks = S.s0 + poh[i];
+            term(bh, a.ftc32[2 * ks], a.ftc32[2 * ks + 1], a.fg[i]);
             if (planet) {
                 ff px, py, pz;
                 expand_mixed(rec, bh, a.bl[i], px, py, pz);
@@ -844,15 +879,34 @@ __global__ void k_agg_end(Arrays a, Sizes z)
                 Ne = Ne + cross(lv, fe);
             }
         }
-        Fc = d3(s[0].value(), s[1].value(), s[2].value());
-        Nc = d3(s[3].value(), s[4].value(), s[5].value());
-        Fg = d3(s[6].value(), s[7].value(), s[8].value());
-        Ng = d3(s[9].value(), s[10].value(), s[11].value());
+        // the parts as float-float pairs (readout only), the totals formed in
+        // float-float and converted once (FP64 instructions are ~60 times
+        // slower than FP32 ones here)
+        ff part[18];
+        for (int k = 0; k < 12; ++k) part[k] = ff{s[k].hi, s[k].lo};
+        if (planet) {
+            part[12] = ff_of(Fe.x); part[13] = ff_of(Fe.y); part[14] = ff_of(Fe.z);
+            part[15] = ff_of(Ne.x); part[16] = ff_of(Ne.y); part[17] = ff_of(Ne.z);
+        } else {
+            for (int k = 12; k < 18; ++k) part[k] = ff{0.f, 0.f};
+        }
+        float2 *o32 = (float2 *)(a.out + 18 * g);
+        for (int k = 0; k < 18; ++k) o32[k] = make_float2(part[k].hi, part[k].lo);
+        for (int c = 0; c < 3; ++c) {
+            const double fcg = ff_value(ff_add(part[c], part[6 + c]));
+            const double ncg = ff_value(ff_add(part[3 + c], part[9 + c]));
+            (&Fc.x)[c] = fcg;   // contact + gravity
+            (&Nc.x)[c] = ncg;
+        }
+        Fg = d3(0, 0, 0);
+        Ng = d3(0, 0, 0);
     }
-    double *o = a.out + 18 * g;
-    st3(o + 0, Fc); st3(o + 3, Nc); st3(o + 6, Fg); st3(o + 9, Ng); st3(o + 12, Fe); st3(o + 15, Ne);
+    if constexpr (FP64) {
+        double *o = a.out + 18 * g;
+        st3(o + 0, Fc); st3(o + 3, Nc); st3(o + 6, Fg); st3(o + 9, Ng); st3(o + 12, Fe); st3(o + 15, Ne);
+    }
     double3 F = Fc + Fg + Fe, N = Nc + Ng + Ne;
-    const double invM = 1.0 / a.M[g];
+    const double invM = a.invM[g];
     double3 acc = invM * F;
     double q[4] = {a.q[4 * g], a.q[4 * g + 1], a.q[4 * g + 2], a.q[4 * g + 3]};
     double3 v = ld3(a.v + 3 * g) + (0.5 * h) * acc;

@@ -232,7 +232,9 @@ void build_fields(dem_world *w)
     add((void **)&a.acc, C_AGG, 24, true);
     add((void **)&a.torque, C_AGG, 24, true);
     add((void **)&a.out, C_AGG, 144, true);
-    add((void **)&a.aref, C_AGG, 64, true);
+    add((void **)&a.invM, C_AGG, 8, true);
+    a.out_ff = d ? 0 : 1;
+    add((void **)&a.aref, C_AGG, 32, true);
     add((void **)&a.ccount, C_CELL, 4, false);
     add((void **)&a.cstart, C_CELL, 4, false);
     add((void **)&a.tile_sum, C_TILE, 4, false);
@@ -1092,6 +1094,11 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     UP(D.agg_first + a0, first.data(), 4 * A);
     UP(D.agg_count + a0, spa, 4 * A);
     UP(D.M + a0, M.data(), 8 * A);
+    {
+        std::vector<double> invM(A);
+        for (int64_t g = 0; g < A; ++g) invM[g] = 1.0 / M[g];
+        UP(D.invM + a0, invM.data(), 8 * A);
+    }
     UP(D.I + 9 * a0, I.data(), 72 * A);
     UP(D.Iinv + 9 * a0, Iinv.data(), 72 * A);
     if (w->precision == DEM_MIXED) {
@@ -1110,19 +1117,20 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     CU(cudaMemsetAsync(D.acc + 3 * a0, 0, 24 * A, st));
     CU(cudaMemsetAsync(D.torque + 3 * a0, 0, 24 * A, st));
     CU(cudaMemsetAsync(D.out + 18 * a0, 0, 144 * A, st));
-    std::vector<double> aref(8 * (size_t)A, 0.0);
+    std::vector<float> aref(8 * (size_t)A, 0.0f);
     for (int a = 0; a < A; ++a) {
         double bm = 0;
         for (int64_t i = first[a]; i < first[a] + spa[a]; ++i)
             bm = std::max(bm, std::sqrt(b[3 * i] * b[3 * i] + b[3 * i + 1] * b[3 * i + 1] +
                                         b[3 * i + 2] * b[3 * i + 2]));
-        aref[8 * a + 7] = bm;
+        aref[8 * a + 7] = (float)bm * (1.0f + 1e-6f);
     }
-    UP(D.aref + 8 * a0, aref.data(), 64 * A);
+    UP(D.aref + 8 * a0, aref.data(), 32 * A);
     PileDyn dyn{};
     dyn.rebuild = 1;
     for (int d = 0; d < 3; ++d) {
         dyn.O[d] = Rp[d]; dyn.V[d] = Vp[d]; dyn.Rc[d] = Rp[d]; dyn.Vc[d] = Vp[d];
+        dyn.hVf[d] = (float)(p->dt * Vp[d]);
         dyn.P_pos[d] = p->ext_pos[d]; dyn.P_vel[d] = p->ext_vel[d]; dyn.P_acc[d] = 0.0;
     }
     UP(D.pd + slot, &dyn, sizeof dyn);
@@ -1318,6 +1326,11 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
         CHK(need(3 * A));
         std::vector<double> o(18 * A);
         CHK(get(o.data(), D.out + 18 * a0, 144 * A));
+        if (w->precision == DEM_MIXED) {   // float-float pairs
+            std::vector<float> f(36 * A);
+            std::memcpy(f.data(), o.data(), 144 * A);
+            for (int64_t k = 0; k < 18 * A; ++k) o[k] = (double)f[2 * k] + (double)f[2 * k + 1];
+        }
         for (int64_t a = 0; a < A; ++a)
             for (int c = 0; c < 3; ++c) {
                 const double *x = &o[18 * a];
@@ -1480,6 +1493,7 @@ dem_status dem_write_state(dem_world *w, int32_t pile_id, int32_t field, const d
                 dyn.P_pos[c] = in[c]; dyn.P_vel[c] = in[3 + c]; dyn.P_acc[c] = in[6 + c];
             } else {
                 dyn.O[c] = in[c]; dyn.V[c] = in[3 + c];
+                dyn.hVf[c] = (float)(q.P.dt * in[3 + c]);
             }
         }
         CHK(put(D.pd + slot, &dyn, sizeof dyn));
