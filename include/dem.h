@@ -49,7 +49,9 @@ typedef enum {
     DEM_ERR_CUDA = 3,      /* a CUDA runtime call failed (message has the CUDA error string) */
     DEM_ERR_OVERLAP = 4,   /* reserved: overlaps above 10% of a radius are reported as flags */
     DEM_ERR_SLOTS = 5,     /* a sphere had more contacts than max_contacts history slots */
-    DEM_ERR_NONFINITE = 6, /* a pile's state became NaN or infinite; that pile is frozen */
+    DEM_ERR_NONFINITE = 6, /* a pile's state became NaN or infinite, or its gravity sum left
+                              the range of its accumulators (DEM_FLAG_GRAV_RANGE); that pile
+                              is frozen */
     DEM_ERR_TIMEOUT = 7,   /* reserved for bounded device waits */
     DEM_ERR_STATE = 8      /* call not valid in the current state (e.g. pile removed) */
 } dem_status;
@@ -115,7 +117,15 @@ enum dem_field {
 /* DEM_FLAG_TREE: tree gravity ran out of traversal stack for some group of
  * spheres and took a cell as far that it would have opened (less accurate,
  * not fatal). */
-enum { DEM_FLAG_SLOTS = 1, DEM_FLAG_NONFINITE = 2, DEM_FLAG_OVERLAP = 4, DEM_FLAG_TREE = 8 };
+/* DEM_FLAG_GRAV_RANGE (mixed precision, direct sum): a tile's gravity sum on
+ * some sphere exceeded the range of the pile's fixed-point gravity
+ * accumulators.  The range is set when the pile is added, from its total mass
+ * and min(0.385 / eps_soft^2, 4 / s_min^2) (s_min = smallest radius): it holds
+ * for any configuration when eps_soft >= 0.31 s_min, else for any in which
+ * spheres of different aggregates stay more than s_min / 2 apart.  Fatal: the
+ * pile is frozen. */
+enum { DEM_FLAG_SLOTS = 1, DEM_FLAG_NONFINITE = 2, DEM_FLAG_OVERLAP = 4, DEM_FLAG_TREE = 8,
+       DEM_FLAG_GRAV_RANGE = 16 };
 
 /* Kernels that dem_step_profiled can time. */
 enum dem_kernel {

@@ -72,6 +72,12 @@ struct PileStatic {
     int32_t tD;
     float theta;
     int64_t tnode0, tleaf0, tg0;   // first node, leaf and 32-sphere group of the pile
+    // mixed symmetric gravity: tile sums enter 64-bit integer accumulators
+    // scaled by gscale = 2^k (the largest power of two with gscale x (bound on
+    // a sphere's sum of |terms|) <= 2^61, |k| <= 120); ginv = 1 / gscale
+    double ginv;
+    float gscale_f;
+    int32_t pad_g;
 };
 
 // Dynamic per-pile state (device-owned; written by kernels).
@@ -202,6 +208,8 @@ struct Arrays {
     int64_t *gpart_base;           // per pile: first slot in gpart (or -1 = direct)
     int32_t *gnchunk;              // per pile: number of j-chunks
     int32_t *gcounter;             // [0]: next work item of the persistent gravity grid
+    unsigned long long *gacc;      // mixed symmetric form: per sphere 4 x int64 (x, y, z, 0)
+                                   // fixed-point sums of the tile items (zero between steps)
     // tree gravity: per sphere leaf key, rank in its leaf, leaf-ordered home
     // index; per pile cube (ordered-int min/max, 8 ints); nodes (3 float4 each:
     // COM + mass, quadrupole, opening radius^2) level by level, Morton order

@@ -28,9 +28,13 @@
 // each j carrying its own running sum, so a j-sphere visits all 128 i-spheres
 // of the warp in 32 steps; per pair this costs 16 FP32 instructions and one
 // reciprocal square root where the one-sided form needs 24 and two.  Items
-// (a, a) take the one-sided form.  Every item writes its i-sums (one per b)
-// and j-sums (one per a) as FP32 partials; k_grav_combine_sym adds a sphere's
-// partials in FP64 in tile order (deterministic).
+// (a, a) take the one-sided form.  Mixed path: every item adds its FP32
+// i-sums and j-sums, scaled by a power of two and rounded once, to 64-bit
+// integer accumulators per sphere (atomic integer adds, which give the same
+// result in any order, so nothing depends on the schedule);
+// k_grav_acc_to_force turns them into forces.  FP64 path: every item writes
+// its i-sums (one per b) and j-sums (one per a) as FP64 partials, and
+// k_grav_combine_sym64 adds a sphere's partials in tile order.
 #include "dem_internal.h"
 #include "devmath.cuh"
 #include "launch.cuh"
@@ -469,6 +473,28 @@ static_assert(32 * kBigWPB * kBigIB == kSymTile, "512-sphere tiles");
 #define DEM_GSYM_BOUNDS __launch_bounds__(32 * WPB)
 #endif
 
+// Mixed symmetric form: add one tile item's FP32 sum on home sphere s to its
+// 64-bit integer accumulators.  The sum is scaled by the pile's power of two
+// (exact) and rounded to the nearest integer once; integer additions are
+// exact, so the accumulated value does not depend on the order in which the
+// items finish, and the result is the same in any schedule or batch.  A sum
+// outside the accumulators' range (or NaN) adds nothing and returns the
+// pile flag to raise.
+__device__ __forceinline__ void grav_accumulate(const Arrays &a, int64_t s, float x, float y, float z,
+                                                float scale, int *bad)
+{
+    // x * 2^k is exact in FP32 (a power-of-two scale; results below the
+    // normal range flush to zero, far below half a quantum)
+    const float vx = x * scale, vy = y * scale, vz = z * scale;
+    const float lim = 2305843009213693952.0f;   // 2^61
+    const bool ok = fabsf(vx) < lim && fabsf(vy) < lim && fabsf(vz) < lim;
+    unsigned long long *g = a.gacc + 4 * s;
+    atomicAdd(g, (unsigned long long)(ok ? __float2ll_rn(vx) : 0ll));
+    atomicAdd(g + 1, (unsigned long long)(ok ? __float2ll_rn(vy) : 0ll));
+    atomicAdd(g + 2, (unsigned long long)(ok ? __float2ll_rn(vz) : 0ll));
+    if (!ok) atomicOr(bad, (vx != vx || vy != vy || vz != vz) ? DEM_FLAG_NONFINITE : DEM_FLAG_GRAV_RANGE);
+}
+
 // Partial slots of pile p: i-sums of tile pair (a, b) at [b][i], j-sums at
 // [T + a][j], rows of ns spheres from gpart_base[p].
 __device__ __forceinline__ int64_t sym_slot(const Arrays &a, int p, int64_t ns, int64_t row, int64_t i)
@@ -589,7 +615,7 @@ __device__ __forceinline__ void sym_ring2(const float4 &pa, const float4 &pb,
 // form, 128 for small piles whose 512-sphere tile pairs would not fill the GPU).
 template <int WPB, int IB>
 __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, float4 *sp, int *sag,
-                                                float4 *sj)
+                                                float4 *sj, int *bad)
 {
     constexpr int kSymBS = 32 * WPB, kSymTile = kSymBS * IB;
     const int p = it.x;
@@ -688,7 +714,7 @@ __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, 
                 u.y += t.y;
                 u.z += t.z;
             }
-            ((float4 *)a.gpart)[sym_slot(a, p, ns, T + ta, jb0 + m)] = make_float4(u.x, u.y, u.z, 0.f);
+            grav_accumulate(a, s0 + jb0 + m, u.x, u.y, u.z, S.gscale_f, bad);
         }
     }
 #pragma unroll
@@ -699,7 +725,7 @@ __device__ __forceinline__ void gravity32s_item(const Arrays &a, const int4 it, 
             const double gm = S.G * a.m64[s0 + i];
             a.fg[s0 + i] = make_dbl4(gm * ax[k], gm * ay[k], gm * az[k], 0.0);
         } else {
-            ((float4 *)a.gpart)[sym_slot(a, p, ns, tb, i)] = make_float4(ax[k], ay[k], az[k], 0.f);
+            grav_accumulate(a, s0 + i, ax[k], ay[k], az[k], S.gscale_f, bad);
         }
     }
 }
@@ -712,14 +738,22 @@ __global__ void DEM_GSYM_BOUNDS k_gravity32s(Arrays a, Sizes z)
     __shared__ float4 sp[kTile];
     __shared__ int sag[kTile];
     __shared__ float4 sj[WPB * kTile];
-    __shared__ int next;
+    __shared__ int next, bad, bad_pile;   // flags raised by the block's last item, and its pile
+    if (threadIdx.x == 0) bad = 0;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) next = grab_item(a.gcounter, z.GI);
+        if (threadIdx.x == 0) {
+            if (bad) {
+                atomicOr(&a.pd[bad_pile].flags, bad);
+                bad = 0;
+            }
+            next = grab_item(a.gcounter, z.GI);
+            if (next < z.GI) bad_pile = a.gitems[next].x;
+        }
         __syncthreads();
         const int item = next;
         if (item >= z.GI) return;
-        gravity32s_item<WPB, IB>(a, a.gitems[item], sp, sag, sj);
+        gravity32s_item<WPB, IB>(a, a.gitems[item], sp, sag, sj, &bad);
     }
 }
 
@@ -885,39 +919,24 @@ __global__ void k_grav_combine_sym64(Arrays a, Sizes z)
     a.fg[i] = make_dbl4(gm * sx, gm * sy, gm * sz, 0.0);
 }
 
-#ifndef DEM_COMBINE_UNROLL
-#define DEM_COMBINE_UNROLL 8
-#endif
-constexpr int kCombineUnroll = DEM_COMBINE_UNROLL;
-// Sphere x of tile t: its i-sums of items (t, b), b >= t, then its j-sums of
-// items (a, t), a < t, in that fixed order, as float-float sums (FFSum).
-__global__ void k_grav_combine_sym(Arrays a, Sizes z)
+// Mixed symmetric form: turn the integer sums of piles with more than one
+// tile into F_i = G m_i sum (in FP64) and clear the accumulators for the next
+// step.
+__global__ void k_grav_acc_to_force(Arrays a, Sizes z)
 {
     pdl_enter();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= z.N) return;
     int p = a.sph_pile[i];
     if (a.enabled[p] == 0 || a.pd[p].failed) return;
-    const int T = a.gnchunk[p];
-    if (T <= 1) return;
+    if (a.gnchunk[p] <= 1) return;
     const PileStatic &S = a.ps[p];
-    const int64_t il = i - S.s0;
-    const int t = (int)(il / z.gtile);
-    const float4 *gp = (const float4 *)a.gpart;
-    FFSum sx, sy, sz;
-    // unrolled so that several rows' loads are in flight (the sums stay in order)
-#pragma unroll kCombineUnroll
-    for (int b = t; b < T; ++b) {
-        const float4 v = __ldcs(gp + sym_slot(a, p, S.ns, b, il));
-        sx.add(v.x); sy.add(v.y); sz.add(v.z);
-    }
-#pragma unroll kCombineUnroll
-    for (int r = 0; r < t; ++r) {
-        const float4 v = __ldcs(gp + sym_slot(a, p, S.ns, T + r, il));
-        sx.add(v.x); sy.add(v.y); sz.add(v.z);
-    }
-    const double gm = S.G * a.m64[i];
-    a.fg[i] = make_dbl4(gm * sx.value(), gm * sy.value(), gm * sz.value(), 0.0);
+    longlong2 *g = (longlong2 *)(a.gacc + 4 * i);
+    const longlong2 xy = g[0], zw = g[1];
+    g[0] = make_longlong2(0, 0);
+    g[1] = make_longlong2(0, 0);
+    const double gm = S.G * a.m64[i] * S.ginv;
+    a.fg[i] = make_dbl4(gm * (double)xy.x, gm * (double)xy.y, gm * (double)zw.x, 0.0);
 }
 
 // Sum the j-range partials of piles that were split, in range order.
@@ -1017,7 +1036,7 @@ void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int i
             else if (z.gtile == 128) launch_pdl(k_gravity32s<1, 4>, (unsigned)nb, 32, 0, st, a, z);
             else if (z.gtile == 256) launch_pdl(k_gravity32s<2, 4>, (unsigned)nb, 64, 0, st, a, z);
             else launch_pdl(k_gravity32s<kBigWPB, kBigIB>, (unsigned)nb, 32 * kBigWPB, 0, st, a, z);
-            if (z.GP > 0) launch_pdl(k_grav_combine_sym, (unsigned)((z.N + 255) / 256), 256, 0, st, a, z);
+            launch_pdl(k_grav_acc_to_force, (unsigned)((z.N + 255) / 256), 256, 0, st, a, z);
         }
         return;
     }

@@ -368,7 +368,7 @@ __device__ void pile_finalize_block(const Arrays &a, int p, double (&sh)[7][128]
         }
         D.steps += 1;
         D.parity ^= 1;
-        if (D.flags & (DEM_FLAG_SLOTS | DEM_FLAG_NONFINITE)) D.failed = 1;
+        if (D.flags & (DEM_FLAG_SLOTS | DEM_FLAG_NONFINITE | DEM_FLAG_GRAV_RANGE)) D.failed = 1;
         if (D.rebuild) {
             D.rebuilds += 1;
             D.cpar ^= 1;   // the lists built this step become the current ones

@@ -43,7 +43,7 @@ struct PileHost {
     int64_t ns, na, nc, nch, nt;
     int64_t ne;            // candidate-list entries (never shrinks)
     int nx, ny, nz;
-    double cell, smax;
+    double cell, smax, smin;
     double ext[3];         // extent of the wrapped grid at creation (cell x dims)
     dem_params P;
     double M_total;
@@ -218,6 +218,7 @@ void build_fields(dem_world *w)
         add((void **)&a.hist32_rm, C_ENT, 16, false);
         add((void **)&a.rec32, C_AGG, sizeof(AggRecMixed), false);
         add((void **)&a.I32, C_AGG, 72, true);
+        add((void **)&a.gacc, C_SPH, 32, false);
     }
     add((void **)&a.agg_first, C_AGG, 4, true);
     add((void **)&a.agg_count, C_AGG, 4, true);
@@ -363,10 +364,10 @@ GravPlan plan_gravity(dem_world *w)
                 continue;
             }
             g.nch.push_back((int32_t)T);
-            if (T > 1) {
+            if (T > 1 && w->precision == DEM_FP64) {
                 g.base.push_back(g.gp);
                 g.gp += 2 * T * q.ns;
-            } else {
+            } else {   // one tile, or the mixed path's integer accumulators
                 g.base.push_back(-1);
             }
             for (int64_t ta = 0; ta < T; ++ta)
@@ -540,6 +541,20 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
         S.mu_s = P.mu_s; S.mu_r = P.mu_r; S.mu_t = P.mu_t; S.w0 = P.w0;
         S.eps2 = P.eps_soft * P.eps_soft;
         S.ext_mass = P.ext_mass; S.M_total = q.M_total;
+        {
+            // a pair term of the gravity sum is at most m_j x 0.385 / eps^2
+            // (the maximum of d / (d^2 + eps^2)^1.5), and at most m_j x 4 / s_min^2
+            // while spheres of different aggregates stay > s_min / 2 apart, so a
+            // sphere's sum of |terms| is below B = M x min(...); margin for the
+            // FP32 masses and rounding
+            double b = 4.0 / (q.smin * q.smin);
+            if (S.eps2 > 0) b = std::min(b, 0.3849 / S.eps2);
+            const double B = q.M_total * b * 1.01;
+            int k = (B > 0 && std::isfinite(B)) ? (int)std::floor(61.0 - std::log2(B)) : 0;
+            k = std::max(-120, std::min(120, k));   // a normal FP32 power of two
+            S.gscale_f = std::ldexp(1.0f, k);
+            S.ginv = std::ldexp(1.0, -k);
+        }
         for (int c = 0; c < 3; ++c) S.spin_inc[c] = P.spin_inc[c];
         S.rot_tol = P.rot_tol;
         ps.push_back(S);
@@ -595,6 +610,8 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     }
     // the persistent gravity grid's work counter (it resets itself after each launch)
     CU(cudaMemsetAsync(w->A.gcounter, 0, sizeof(int32_t), w->stream));
+    // the mixed path's gravity accumulators (each step's conversion leaves them at zero)
+    if (w->A.gacc && w->Z.N > 0) CU(cudaMemsetAsync(w->A.gacc, 0, 32 * (size_t)w->Z.N, w->stream));
     // arrival counters of the pile reductions (each reduction leaves them at zero)
     if (w->Z.P > 0) CU(cudaMemsetAsync(w->A.pile_arrive, 0, sizeof(int32_t) * (size_t)w->Z.P, w->stream));
     launch_fill_ids(w->A, w->Z, w->stream);
@@ -715,6 +732,9 @@ dem_status collect_flags(dem_world *w)
             if (D.flags & DEM_FLAG_NONFINITE) {
                 st = DEM_ERR_NONFINITE;
                 fail(w, st, "pile %d: state became non-finite; pile frozen", q.id);
+            } else if (D.flags & DEM_FLAG_GRAV_RANGE) {
+                st = DEM_ERR_NONFINITE;
+                fail(w, st, "pile %d: gravity sum beyond the range of its accumulators; pile frozen", q.id);
             } else if (st == DEM_OK) {
                 st = DEM_ERR_SLOTS;
                 fail(w, st, "pile %d: more contacts than %d history slots; pile frozen", q.id, w->K);
@@ -931,7 +951,7 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
         for (int a = 0; a < A; ++a) { first[a] = (int32_t)k; k += spa[a]; }
     }
     struct Part {
-        double smax = 0, Mtot = 0, Rp[3] = {0, 0, 0}, Vp[3] = {0, 0, 0};
+        double smax = 0, smin = HUGE_VAL, Mtot = 0, Rp[3] = {0, 0, 0}, Vp[3] = {0, 0, 0};
         int bad = -1;   // first aggregate of the range with a singular inertia tensor
     };
     constexpr int kRanges = 16;
@@ -950,6 +970,7 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
                 Ma += m[k];
                 for (int d = 0; d < 3; ++d) c[d] += m[k] * (pos[3 * k + d] - x0[d]);
                 P.smax = std::max(P.smax, rad[k]);
+                P.smin = std::min(P.smin, rad[k]);
             }
             for (int d = 0; d < 3; ++d) c[d] = x0[d] + c[d] / Ma;
             M[a] = Ma;
@@ -1002,11 +1023,12 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
         for (int r2 = (A >= 8192 ? rg : 1); r2 < kRanges; ++r2) setup_range(r2);
         for (auto &t : pool) t.join();
     }
-    double smax = 0, Mtot = 0, Rp[3] = {0, 0, 0}, Vp[3] = {0, 0, 0};
+    double smax = 0, smin = HUGE_VAL, Mtot = 0, Rp[3] = {0, 0, 0}, Vp[3] = {0, 0, 0};
     for (int rg = 0; rg < kRanges; ++rg) {
         if (part[rg].bad >= 0)
             return fail(w, DEM_ERR_ARG, "aggregate %d has a singular inertia tensor", part[rg].bad);
         smax = std::max(smax, part[rg].smax);
+        smin = std::min(smin, part[rg].smin);
         Mtot += part[rg].Mtot;
         for (int d = 0; d < 3; ++d) { Rp[d] += part[rg].Rp[d]; Vp[d] += part[rg].Vp[d]; }
     }
@@ -1018,6 +1040,7 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     ph.na = A;
     ph.nch = (A + kAggChunk - 1) / kAggChunk;
     ph.smax = smax;
+    ph.smin = smin;
     ph.P = *p;
     ph.M_total = Mtot;
     {
