@@ -22,8 +22,10 @@ value is all spheres x steps / the slowest rank's time.
 One JSON line on rank 0.  Extra keys: fp64_path (the all-FP64 GPU path on
 the same workload), roofline_contact (the contact pass on a 1M-sphere dense
 lattice), batched (256 piles in one graph launch vs one pile at a time),
-serving (p50/p99 time-to-finish of a served Poisson trace), e2e (through the
-public API with host buffers).
+serving_config5 (p50/p99 time-to-finish and throughput of configuration 5's
+served Poisson trace, direct sum; serving_config5_tree beside it),
+accuracy_* (GPU vs stored FP64-oracle trajectories), e2e (through the public
+API with host buffers).
 """
 from __future__ import annotations
 
@@ -77,12 +79,14 @@ def parse():
     ap.add_argument("--no-e2-collapse", action="store_true")
     ap.add_argument("--no-tree", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
-    ap.add_argument("--part", default="all", choices=["all", "contact", "e2", "tree", "analysis", "probe"],
+    ap.add_argument("--part", default="all",
+                    choices=["all", "contact", "e2", "tree", "analysis", "probe", "serving"],
                     help="contact: only the contact-pass roofline on the 1M-sphere lattice; "
                          "e2: only the paper's 2e4-sphere profiling collapse; "
                          "tree: only tree vs direct gravity; "
                          "analysis: only the spin-up and encounter runs with device-side watches "
-                         "(not part of all); probe: only the peak-rate probes")
+                         "(not part of all); probe: only the peak-rate probes; serving: only "
+                         "the served traces of configuration 5")
     ap.add_argument("--contact-n", type=int, default=1_048_576)
     ap.add_argument("--contact-mode", type=int, default=None, choices=[0, 1],
                     help="contact part: 0 = one thread per sphere, 1 = tiles with a shared-memory inbox")
@@ -449,24 +453,33 @@ def run_batched(dem, W, steps=5, n_piles=256):
                         "each on a jittered lattice in a ball, mixed precision"}
 
 
-def run_serving(dem, W, n_req=24, steps=2000, n_hi=20000, theta=0.0, rate=4.0):
-    """Poisson trace (`rate` arrivals/s) of tidal-flyby piles, sizes log-uniform
-    in [1,000, n_hi] spheres, `steps` steps each, served by continuous batching
-    (with tree gravity at opening angle theta when theta > 0)."""
+def run_serving(dem, W, n_req=64, steps=20_000, n_hi=100_000, theta=0.0, rate=4.0):
+    """Served tidal encounters: a Poisson trace (`rate` arrivals/s) of `n_req`
+    flyby piles, sizes log-uniform in [1,000, n_hi] spheres, `steps` steps each,
+    served by continuous batching in one world (admission by footprint, state
+    resident on the device), direct-sum gravity unless theta > 0 (tree)."""
     from paper_2311_11322_gb300 import serve
     trace = W.config5_trace(0, n_arrivals=n_req, rate=rate, n_hi=n_hi, steps=steps)
+    t0 = time.perf_counter()
     reqs = serve.trace_requests(trace, W.config5_pile)
+    t_gen = time.perf_counter() - t0
     with dem.World() as w:
         if theta:
             w.set_tuning("grav_theta", theta)
         srv = serve.Server(w, dem.dem_footprint_bytes, budget_bytes=64 << 30, max_piles=64,
                            chunk=250)
         st = srv.run(reqs)
-    st["mean_request_sphere_steps"] = float(np.mean([r.n_spheres * r.steps for r in reqs]))
-    st.update({"trace": "%d Poisson arrivals at %.2f/s, sizes log-uniform [1000, %d] spheres, %d "
-                        "steps each (reduced from 20,000 to keep the run short), tidal flyby "
-                        "of an Earth-mass planet" % (n_req, rate, n_hi, steps),
-               "gravity": "tree (hexadecapole), theta %.2f" % theta if theta else "direct sum"})
+    n = np.array([r.n_spheres for r in reqs], float)
+    st["mean_request_sphere_steps"] = float(np.mean(n * steps))
+    st["host_generation_s"] = t_gen
+    st.update({"trace": "%d Poisson arrivals at %.2f/s, sizes log-uniform [1000, %d] spheres "
+                        "(drawn: min %d, median %d, max %d), %d steps each, settled lattice piles "
+                        "of tetrahedra on a hyperbolic flyby of an Earth-mass planet (periapsis "
+                        "1.5-4 planet radii, v_inf 1-10 km/s)"
+                        % (n_req, rate, n_hi, n.min(), np.median(n), n.max(), steps),
+               "gravity": "tree (hexadecapole), theta %.2f" % theta if theta else "direct sum",
+               "batching": "every resident pile in one step graph; rounds of <= 250 steps; "
+                           "up to 64 piles, 64 GiB footprint budget"})
     return st
 
 
@@ -652,7 +665,7 @@ def run_ours(args):
                         "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                         "traffic": traffic_for("kernels_gravity.cu", "k_gravity32s"),
                         "kernel": "k_gravity32s (softened direct-sum gravity, symmetric "
-                                  "tile pairs, packed f32x2) + k_grav_combine_sym",
+                                  "tile pairs, packed f32x2) + k_grav_acc_to_force",
                         "kernel_ms": g_ms, "share_of_step": g_ms / statistics.mean(step_ms),
                         "flops_per_launch": flops,
                         "flop_count": "20 per ordered pair of spheres in different aggregates "
@@ -685,18 +698,12 @@ def run_ours(args):
                                                                     "frac", "rebuild_step_contact_ms")})
     if rank == 0 and not args.no_batched:
         out["batched"] = run_batched(dem, W)
-    if rank == 0 and not args.no_serving:
-        out["serving"] = run_serving(dem, W)
-        # the configuration's full size range (1,000-100,000 spheres) with tree gravity
-        out["serving_tree"] = run_serving(dem, W, n_hi=100_000, theta=0.7)
-        # the same traces with arrivals at 0.8x the capacity the saturated runs measured
-        # (requests/s = sphere-steps/s / mean sphere-steps per request)
-        for key, kw in (("serving", {}), ("serving_tree", {"n_hi": 100_000, "theta": 0.7})):
-            sat = out[key]
-            cap = sat["sphere_steps_per_s"] / sat["mean_request_sphere_steps"]
-            r08 = run_serving(dem, W, rate=0.8 * cap, **kw)
-            r08["capacity_requests_per_s"] = cap
-            out[key + "_at_0.8_capacity"] = r08
+    if rank == 0 and ws == 1 and not args.no_serving:
+        # configuration 5 as stated: 64 arrivals at 4/s, 1,000-100,000 spheres, 20,000
+        # steps each, direct sum (about 7 minutes of GPU time)
+        out["serving_config5"] = run_serving(dem, W)
+        # the same trace with tree gravity, 2,000 steps per request
+        out["serving_config5_tree"] = run_serving(dem, W, steps=2000, theta=0.7)
     if rank == 0 and not args.no_e2_collapse:
         out["e2_collapse"] = run_e2_collapse(dem, W)
     if rank == 0 and not args.no_tree:
@@ -791,6 +798,19 @@ def run_probe_only(args):
     print(json.dumps({"part": "probe", "peaks_measured": run_probes(dem)}), flush=True)
 
 
+def run_serving_only(args):
+    import torch
+    from paper_2311_11322_gb300 import dem
+    from paper_2311_11322_gb300 import workloads as W
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    dem.load()
+    out = {"part": "serving", "serving_config5": run_serving(dem, W)}
+    out["serving_config5_tree"] = run_serving(dem, W, steps=2000, theta=0.7)
+    print(json.dumps(out), flush=True)
+
+
 def run_analysis_only(args):
     import torch
     from paper_2311_11322_gb300 import dem
@@ -815,5 +835,7 @@ if __name__ == "__main__":
         run_analysis_only(a)
     elif a.part == "probe":
         run_probe_only(a)
+    elif a.part == "serving":
+        run_serving_only(a)
     else:
         run_ours(a)

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "DEM_OK", 1: "DEM_ERR_ARG", 2: "DEM_ERR_OOM", 3: "DEM_ERR_CUD
                 4: "DEM_ERR_OVERLAP", 5: "DEM_ERR_SLOTS", 6: "DEM_ERR_NONFINITE",
                 7: "DEM_ERR_TIMEOUT", 8: "DEM_ERR_STATE"}
 DEM_FP64, DEM_MIXED = 0, 1
-DEM_FLAG_SLOTS, DEM_FLAG_NONFINITE, DEM_FLAG_OVERLAP, DEM_FLAG_TREE = 1, 2, 4, 8
+DEM_FLAG_SLOTS, DEM_FLAG_NONFINITE, DEM_FLAG_OVERLAP, DEM_FLAG_TREE, DEM_FLAG_GRAV_RANGE = 1, 2, 4, 8, 16
 
 FIELDS = {  # name: (id, rows ('A' aggregates / 'N' spheres / int), cols)
     "COM": (0, "A", 3), "VEL": (1, "A", 3), "QUAT": (2, "A", 4), "OMEGA": (3, "A", 3),

@@ -417,6 +417,79 @@ def config3(seed=0, precision=PRECISION_MIXED, n_spheres=200_000):
     return ic, p
 
 
+def config3_settled(seed=0, precision=PRECISION_MIXED, n_spheres=200_000, overlap=1e-5):
+    """Spin-up pile, pre-settled: equal spheres (s = 1 m) on a face-centred cubic
+    packing clipped to a 3:2:1.5 ellipsoid, neighbours overlapping by
+    `overlap` x s (about what the pile's own weight presses into the contacts
+    at its centre), so nearly every sphere starts with contacts.  The sites
+    are cut into aggregates of 2-8 face-adjacent spheres (size uniform, grown
+    from a random seed site by random attachment to the cluster; a site left
+    with no free neighbour joins an adjacent aggregate of fewer than 8, else
+    stays a single sphere).  At rest; spin increment 1e-6 rad/s per 1,000
+    steps about the shortest axis (z).  A geometric stand-in for a pile
+    settled by the dynamics (settling with this library would make the
+    oracle's input a product of the CUDA path)."""
+    rng = np.random.default_rng(seed)
+    s = 1.0
+    h = s * (1.0 - overlap / 2.0) * math.sqrt(2.0)      # half the cubic cell: site (i, j, k) * h
+    ax = np.array([3.0, 2.0, 1.5])
+    c = (n_spheres * 2.0 * h ** 3 / (4.0 / 3.0 * math.pi * 9.0)) ** (1.0 / 3.0) * 1.05
+    while True:
+        n = [int(math.ceil(x * c / h)) + 1 for x in ax]
+        g = [np.arange(-m, m + 1) for m in n]
+        I, J, K = np.meshgrid(*g, indexing="ij")
+        ijk = np.stack([I.ravel(), J.ravel(), K.ravel()], 1)
+        ijk = ijk[(ijk.sum(1) % 2) == 0]
+        e2 = np.sum((ijk * h / (ax * c)) ** 2, 1)
+        if int((e2 <= 1.0).sum()) >= n_spheres:
+            break
+        c *= 1.05
+    order = np.lexsort((ijk[:, 2], ijk[:, 1], ijk[:, 0], e2))[:n_spheres]
+    ijk = ijk[order]
+    site = {tuple(v): t for t, v in enumerate(ijk.tolist())}
+    nb = np.array([(a, b, 0) for a in (-1, 1) for b in (-1, 1)] + [(a, 0, b) for a in (-1, 1) for b in (-1, 1)]
+                  + [(0, a, b) for a in (-1, 1) for b in (-1, 1)])
+    N = n_spheres
+    adj = np.full((N, 12), -1, np.int64)
+    for t, v in enumerate(ijk):
+        for q, d in enumerate(nb):
+            adj[t, q] = site.get((v[0] + d[0], v[1] + d[1], v[2] + d[2]), -1)
+    owner = np.full(N, -1, np.int64)
+    members = []
+    for t in rng.permutation(N):
+        if owner[t] >= 0:
+            continue
+        want = int(rng.integers(2, 9))
+        cl = [int(t)]
+        owner[t] = len(members)
+        while len(cl) < want:
+            front = [u for m in cl for u in adj[m] if u >= 0 and owner[u] < 0]
+            if not front:
+                break
+            u = int(front[rng.integers(0, len(front))])
+            owner[u] = len(members)
+            cl.append(u)
+        if len(cl) == 1:
+            near = [owner[u] for u in adj[t] if u >= 0 and owner[u] >= 0 and owner[u] != len(members)
+                    and len(members[owner[u]]) < 8]
+            if near:
+                g_ = int(min(near, key=lambda x: (len(members[x]), x)))
+                owner[t] = g_
+                members[g_].append(int(t))
+                continue
+        members.append(cl)
+    counts = np.array([len(m) for m in members], np.int32)
+    flat = np.concatenate([np.array(sorted(m), np.int64) for m in members])
+    pos = (ijk[flat] * h).astype(np.float64)
+    A = len(members)
+    ic = PileIC(counts=counts, pos=pos, radius=np.full(N, s), density=np.full(N, 2500.0),
+                vel=np.zeros((A, 3)), omega=np.zeros((A, 3)))
+    p = settled_params(ic, s, precision=precision, eps=0.1 * s)
+    p = p.replace(spin_inc=(0.0, 0.0, 1e-9))
+    ic.meta = dict(name="config3_settled", seed=seed, overlap=overlap)
+    return ic, p
+
+
 def _touching_cluster(rng, k):
     """Offsets (unit radius) of k spheres grown by tangent attachment to a random
     member without overlapping any other member; centred on the mean."""

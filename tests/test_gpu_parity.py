@@ -271,6 +271,29 @@ def test_slot_overflow_reported_and_frozen(dem):
         assert w.info(pid)["steps"] == steps
 
 
+def test_gravity_range_reported_and_frozen(dem):
+    """Mixed direct sum with eps_soft = 0: two aggregates of a 600-sphere pile
+    (two 512-sphere tiles, so the integer accumulators are used) put with
+    spheres 0.001 s apart, closer than the accumulators' range assumes
+    (s_min / 2), raise DEM_FLAG_GRAV_RANGE; the pile is frozen."""
+    ic, p = W.config1(0, precision=W.PRECISION_MIXED, n_agg=150)
+    p = p.replace(eps=0.0)
+    k1 = int(ic.counts[0])
+    shift = ic.pos[0] + np.array([1e-3 * ic.radius[0], 0.0, 0.0]) - ic.pos[k1]
+    ic.pos[k1:k1 + int(ic.counts[1])] += shift
+    with new_world(dem) as w:
+        pid = w.add_pile(ic, p)
+        w.step(1)
+        with pytest.raises(dem.DemError) as ei:
+            w.sync()
+        assert ei.value.status == dem.DEM_ERR_NONFINITE
+        assert w.flags(pid) & dem.DEM_FLAG_GRAV_RANGE
+        steps = w.info(pid)["steps"]
+        w.step(2, check=False)
+        w.sync(check=False)
+        assert w.info(pid)["steps"] == steps
+
+
 def test_invalid_inputs_rejected(dem):
     ic, p = W.config1(0, n_agg=10, ball=12.0)
     with new_world(dem) as w:
