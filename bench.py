@@ -483,29 +483,42 @@ def run_serving(dem, W, n_req=64, steps=20_000, n_hi=100_000, theta=0.0, rate=4.
     return st
 
 
-def run_accuracy(dem, W):
-    """100 steps of collapse-100k, mixed and all-FP64, side by side with the FP64
-    oracle's stored 100-step trajectory (tests/golden, written by a script that
-    calls only the oracle): per-step condition-relative and |X|-relative force
-    and torque errors of 256 sampled aggregates, COM and quaternion deviations."""
-    from tests.parity_util import same_inputs, summarize_trajectory, trajectory_errors
-    path = os.path.join(ROOT, "tests", "golden", "collapse100k_100steps.npz")
+def run_accuracy(dem, W, name="collapse100k"):
+    """GPU (mixed and all-FP64) side by side with a stored FP64-oracle trajectory
+    (tests/golden, written by scripts that call only the oracle): 100 steps of
+    collapse-100k, or 30 steps of the pre-settled 200,000-sphere spin-up pile
+    (~940,000 contact pairs under the spin ramp).  Per-step condition-relative
+    and |X|-relative force and torque errors of 256 sampled aggregates, COM and
+    quaternion deviations, and for the pile the contact-pair counts."""
+    from tests.parity_util import (contact_pair_count, same_inputs, summarize_trajectory,
+                                   trajectory_errors)
+    if name == "collapse100k":
+        path = os.path.join(ROOT, "tests", "golden", "collapse100k_100steps.npz")
+        make, steps = W.config2, 100
+        what = "collapse-100k (100,000 spheres, no contacts yet)"
+    else:
+        path = os.path.join(ROOT, "tests", "golden", "config3_settled_30steps.npz")
+        make, steps = W.config3_settled, 30
+        what = ("pre-settled spin-up pile (200,000 equal spheres of a 3:2:1.5 FCC packing in "
+                "2-8-sphere aggregates, neighbours overlapping 1e-5 s, spin ramp 1e-9 rad/s per step)")
     if not os.path.exists(path):
         return {"unavailable": "stored oracle trajectory missing"}
     gold = np.load(path)
-    out = {"reference": "FP64 oracle, 100 full steps of the same workload, 256 sampled aggregates",
+    out = {"reference": "FP64 oracle, %d full steps of %s, 256 sampled aggregates" % (steps, what),
            "bound": {"mixed": 1e-5, "fp64": 1e-9},
            "measure": "condition-relative: |X_gpu - X_oracle| / sum of the magnitudes of the summed "
                       "terms; abs_rel: / |X_oracle|"}
-    for name, prec in (("mixed", W.PRECISION_MIXED), ("fp64", W.PRECISION_FP64)):
-        ic, p = W.config2(0, precision=prec)
+    for prec_name, prec in (("mixed", W.PRECISION_MIXED), ("fp64", W.PRECISION_FP64)):
+        ic, p = make(0, precision=prec)
         if not same_inputs(ic, gold):
-            out[name] = {"unavailable": "input generator differs from the stored run"}
+            out[prec_name] = {"unavailable": "input generator differs from the stored run"}
             continue
         with dem.World() as w:
             pid = w.add_pile(ic, p)
             rows = trajectory_errors(w, pid, gold)
-        out[name] = summarize_trajectory(rows)
+            pairs = contact_pair_count(w, pid)
+        out[prec_name] = summarize_trajectory(rows)
+        out[prec_name]["contact_pairs_last_step"] = {"gpu": pairs, "oracle": int(gold["n_pairs"][-1])}
     return out
 
 
@@ -683,8 +696,9 @@ def run_ours(args):
                                           probes["clocks"].get("sm_mhz"))},
            "peaks_measured": probes,
            "clocks": ck}
-    if rank == 0 and not args.no_accuracy:
+    if rank == 0 and ws == 1 and not args.no_accuracy:
         out["accuracy_collapse100k"] = run_accuracy(dem, W)
+        out["accuracy_config3_settled"] = run_accuracy(dem, W, "config3_settled")
     if rank == 0 and not args.no_fp64:
         out["fp64_path"] = run_fp64(dem, W, steps=3)
         out["fp64_path"]["mixed_over_fp64"] = value / ws / out["fp64_path"]["value"]

@@ -295,9 +295,11 @@ dem_status dem_get_tuning(dem_world *w, const char *key, double *value_out);
  * Autotuner: time the candidate gravity shapes (the symmetric form, with
  * 512-sphere tiles and, in the mixed path, 64-, 128- and 256-sphere tiles;
  * the one-sided form with block 64/128/256, 1/2/4 i-spheres per thread,
- * scalar or packed, three work-item sizes) and then cell factors 1, 1.25,
- * 1.5, 2 on the current piles, one warm and `trial_steps` timed step graph
- * launches per candidate, and keep the fastest.  The trials step the live
+ * scalar or packed, three work-item sizes), then cell factors 1, 1.25,
+ * 1.5, 2, then both forms of the contact pass (contact_mode 0 and 1) on the
+ * current piles, one warm and `trial_steps` timed step graph launches per
+ * candidate, and keep the fastest (no candidate changes the contact results;
+ * the gravity shapes reorder FP32 sums only).  The trials step the live
  * piles, so the tuner first copies every field that carries state from step
  * to step (positions, velocities, orientations, spins, stored accelerations
  * and torques, contact history, step counters, flags, planet) into a

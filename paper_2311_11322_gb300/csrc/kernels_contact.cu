@@ -201,7 +201,12 @@ __device__ __forceinline__ bool pair_mixed(int4 A, float4 RA, int4 B, float4 RB,
     const float ee = __fmaf_rn(ez, ez, __fmaf_rn(ey, ey, __fmul_rn(ex, ex)));
     const float corr = __fsub_rn(__fsub_rn(__fmaf_rn(__fmul_rn(2.0f, Ssf), rho, __fmul_rn(rho, rho)),
                                            __fmul_rn(2.0f, cr)), ee);
-    const float num = __fadd_rn(__ll2float_rn(num_i), corr);
+    // the int64 bracket to FP32 from its 32-bit halves (two 32-bit conversions
+    // and one FMA, off the FP64 unit that a 64-bit conversion would use;
+    // within 2 ulp of the correctly rounded value and symmetric in a, b)
+    const float numi = __fmaf_rn(__int2float_rn((int)(num_i >> 32)), 4294967296.0f,
+                                 __uint2float_rn((unsigned)(num_i & 0xffffffffll)));
+    const float num = __fadd_rn(numi, corr);
     if (!(num > 0.0f)) return false;
     const float3 d = f3(__fadd_rn(fx, ex), __fadd_rn(fy, ey), __fadd_rn(fz, ez));
     const float Df = __fmaf_rn(d.z, d.z, __fmaf_rn(d.y, d.y, __fmul_rn(d.x, d.x)));
@@ -672,6 +677,151 @@ __global__ void __launch_bounds__(kCTile) k_cand_link(Arrays a, Sizes z)
 }
 
 // ---------------------------------------------------------------- step
+// One sorted sphere k: every entry of its list is evaluated in the canonical
+// orientation (owner as sphere a, the same evaluation the tiles make) and the
+// sphere keeps its own share, summed in list order; the owner's side writes
+// the pair's history.  Each pair is evaluated twice (once per sphere), with
+// bitwise the same result both times, so the forces equal the tile form's bit
+// for bit.  s_x / s_v: the sorted spheres [kb0, kb0 + 128) staged in shared
+// memory (mixed path), or null.
+template <bool FP64>
+__device__ __forceinline__ void sphere_contacts(const Arrays &a, const PileStatic &S, int lp,
+                                                const typename CT<FP64>::H *hread,
+                                                typename CT<FP64>::H *hwrite,
+                                                const typename CT<FP64>::Prm &prm, float q, int64_t k,
+                                                int64_t kb0, const int4 *s_x, const float4 *s_v, int &flags)
+{
+    typedef typename CT<FP64>::T T;
+    typedef typename CT<FP64>::V V;
+    typedef typename CT<FP64>::H H;
+    const int64_t s0 = S.s0, e0 = S.e0;
+    const int2 *cand = a.cand[lp] + e0;
+    const int off = a.coff[lp][k], n = a.ccnt[lp][k];
+    // own data
+    typename CT<FP64>::P mp;
+    float4 mr;
+    typename CT<FP64>::VR mv, mw;
+    if constexpr (FP64) { mp = a.dp_[k]; mv = a.dv_[k]; mw = a.dw_[k]; }
+    else if (s_x) {
+        const int64_t lk = k - kb0;
+        mp = s_x[2 * lk]; mr = as_f4(s_x[2 * lk + 1]);
+        mv = s_v[2 * lk]; mw = s_v[2 * lk + 1];
+    } else {
+        mp = a.xqr[2 * k]; mr = as_f4(a.xqr[2 * k + 1]);
+        mv = a.svw[2 * k]; mw = a.svw[2 * k + 1];
+    }
+    V F, Tq;
+    if constexpr (FP64) { F = d3(0, 0, 0); Tq = d3(0, 0, 0); }
+    else { F = f3(0.f, 0.f, 0.f); Tq = f3(0.f, 0.f, 0.f); }
+    int nc = 0;
+    // One entry: this sphere as sphere a.  Every step of the law maps exactly
+    // onto its negative or onto itself when the spheres swap (differences and
+    // products of negated operands round to the negated or the same value),
+    // so this evaluation's share a is bit for bit the share of this side of
+    // the owner's evaluation; the owner's S is seen from this side with the
+    // opposite sign.  The owner's side writes the history.
+    auto entry = [&](int f, bool owned, bool ok, const H &hp, const typename CT<FP64>::P &pp,
+                     const float4 &pr, const typename CT<FP64>::VR &pv, const typename CT<FP64>::VR &pw) {
+        PairOut<T, V> o;
+        bool hit = false;
+        const T sgn = owned ? T(1) : T(-1);
+        if (ok) {
+            if constexpr (FP64) {
+                const double3 Sprev = hp.w != 0 ? d3(sgn * hp.x, sgn * hp.y, sgn * hp.z) : d3(0, 0, 0);
+                hit = pair_64(mp, mv, mw, pp, pv, pw, Sprev, prm, o);
+            } else {
+                const float3 Sprev = hp.w != 0.f ? f3(sgn * hp.x, sgn * hp.y, sgn * hp.z) : f3(0.f, 0.f, 0.f);
+                hit = pair_mixed(mp, mr, pp, pr, q, mv, mw, pv, pw, Sprev, prm, o);
+            }
+        }
+        if (owned && ok) {
+            H h;
+            if constexpr (FP64) h = hit ? make_dbl4(o.S.x, o.S.y, o.S.z, 1.0) : make_dbl4(0, 0, 0, 0);
+            else h = hit ? make_float4(o.S.x, o.S.y, o.S.z, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+            hwrite[f] = h;
+        }
+        if (!hit) return;
+        if (o.x > T(0.1) * o.rmin) flags |= DEM_FLAG_OVERLAP;
+        V sF, sT;
+        share<T, V>(o, true, sF, sT);
+        F.x = addr(F.x, sF.x); F.y = addr(F.y, sF.y); F.z = addr(F.z, sF.z);
+        Tq.x = addr(Tq.x, sT.x); Tq.y = addr(Tq.y, sT.y); Tq.z = addr(Tq.z, sT.z);
+        ++nc;
+    };
+    // an entry's partner and history indices (clamped: the checks never fail)
+    auto where = [&](int2 c, int f, int64_t &g, int &hidx, bool &ok) {
+        const int kk = c.x & 0x7fffffff;
+        hidx = c.x < 0 ? f : c.y;
+        ok = (unsigned)kk < (unsigned)S.ns && (unsigned)hidx < (unsigned)S.ne;
+        g = s0 + (ok ? kk : 0);
+        if (!ok) hidx = 0;
+    };
+    if constexpr (FP64) {
+        for (int e = 0; e < n; ++e) {
+            const int f = off + 32 * e;
+            const int2 c = cand[f];
+            int64_t g;
+            int hidx;
+            bool ok;
+            where(c, f, g, hidx, ok);
+            entry(f, c.x < 0, ok, hread[hidx], a.dp_[g], make_float4(0.f, 0.f, 0.f, 0.f), a.dv_[g], a.dw_[g]);
+        }
+    } else {
+        // partner data from the staged block when it is there, else from global memory
+        auto fetch = [&](int64_t g, int4 &x, int4 &r, float4 &v, float4 &w) {
+            const int64_t lk = g - kb0;
+            if (s_x && (uint64_t)lk < 128) {
+                x = s_x[2 * lk]; r = s_x[2 * lk + 1]; v = s_v[2 * lk]; w = s_v[2 * lk + 1];
+            } else {
+                x = a.xqr[2 * g]; r = a.xqr[2 * g + 1]; v = a.svw[2 * g]; w = a.svw[2 * g + 1];
+            }
+        };
+        // software pipeline: the list entry two ahead and the partner data and
+        // history one ahead are in flight while an entry is evaluated
+        int2 c1 = make_int2(0, 0);
+        if (n > 1) c1 = cand[off + 32];
+        int2 cc = make_int2(0, 0);
+        int4 px = make_int4(0, 0, 0, 0), pr = px;
+        float4 pv = make_float4(0.f, 0.f, 0.f, 0.f), pw = pv;
+        H hp = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool ok = false;
+        if (n > 0) {
+            cc = cand[off];
+            int64_t g;
+            int hidx;
+            where(cc, off, g, hidx, ok);
+            fetch(g, px, pr, pv, pw);
+            hp = hread[hidx];
+        }
+        for (int e = 0; e < n; ++e) {
+            const int f = off + 32 * e;
+            int4 nx = px, nr = pr;
+            float4 nv = pv, nw = pw;
+            H nh = hp;
+            bool nok = false;
+            if (e + 1 < n) {
+                int64_t g;
+                int hidx;
+                where(c1, f + 32, g, hidx, nok);
+                fetch(g, nx, nr, nv, nw);
+                nh = hread[hidx];
+            }
+            const int2 c2 = e + 2 < n ? cand[f + 64] : make_int2(0, 0);
+            entry(f, cc.x < 0, ok, hp, px, as_f4(pr), pv, pw);
+            cc = c1; c1 = c2;
+            px = nx; pr = nr; pv = nv; pw = nw; hp = nh; ok = nok;
+        }
+    }
+    if constexpr (FP64) {
+        a.ftc64[2 * k] = make_dbl4(F.x, F.y, F.z, 0.0);
+        a.ftc64[2 * k + 1] = make_dbl4(Tq.x, Tq.y, Tq.z, 0.0);
+    } else {
+        a.ftc32[2 * k] = make_float4(F.x, F.y, F.z, 0.f);
+        a.ftc32[2 * k + 1] = make_float4(Tq.x, Tq.y, Tq.z, 0.f);
+    }
+    if (nc > S.K) flags |= DEM_FLAG_SLOTS;
+}
+
 // Shared memory of k_contact (dynamic): list offsets and lengths of the
 // tile's spheres and its slice bases, staged sphere data, the inbox (each
 // entry's share: F and tau as six arrays, and a contact flag) and the work
@@ -800,8 +950,12 @@ __global__ void __launch_bounds__(kCTile, FP64 ? 2 : 4) k_contact(Arrays a, Size
         int r1 = nsl;
         while (s_sb[r1] - s_sb[r0] > kCap && r1 - r0 > 1) r1 = r0 + (r1 - r0 + 1) / 2;
         const int E0 = s_sb[r0], nE = s_sb[r1] - E0;
-        if (nE > SM::kCap) {   // one slice with more entries than the inbox holds
-            if (tid == 0) atomicOr(&pile_flags, DEM_FLAG_SLOTS);
+        if (nE > SM::kCap) {
+            // one slice with more list entries than the inbox holds: its
+            // spheres evaluate their own lists (bitwise the same results)
+            if (tid >= 32 * r0 && tid < min(32 * r1, nt))
+                sphere_contacts<FP64>(a, S, lp, hread, hwrite, prm, q, s0 + first + tid, 0, nullptr, nullptr,
+                                      myflags);
             r0 = r1;
             continue;
         }
@@ -927,24 +1081,16 @@ __global__ void __launch_bounds__(kCTile, FP64 ? 2 : 4) k_contact(Arrays a, Size
     if (tid == 0 && pile_flags) atomicOr(&a.pd[p].flags, pile_flags);
 }
 
-// One thread per sorted sphere: every entry of the sphere's list is evaluated
-// in the canonical orientation (owner as sphere a, the same evaluation the
-// tiles make) and the sphere keeps its own share, summed in list order; the
-// owner's thread writes the pair's history.  Each pair is evaluated twice
-// (once per sphere), with bitwise the same result both times, so the forces
-// equal the tile form's bit for bit.
+// One thread per sorted sphere (sphere_contacts); the block's own 128 sorted
+// spheres are staged in shared memory in the mixed path (consecutive sorted
+// spheres fill a compact block of space, so most partners are among them).
 template <bool FP64>
 __global__ void __launch_bounds__(128) k_contact_sphere(Arrays a, Sizes z)
 {
     pdl_enter();
-    typedef typename CT<FP64>::T T;
-    typedef typename CT<FP64>::V V;
     typedef typename CT<FP64>::H H;
     const int64_t kb0 = (int64_t)blockIdx.x * 128;
     const int64_t k = kb0 + threadIdx.x;
-    // mixed path: the block's own 128 sorted spheres staged in shared memory
-    // (consecutive sorted spheres fill a compact block of space, so most
-    // partners are among them)
     __shared__ int4 s_x[FP64 ? 1 : 2 * 128];
     __shared__ float4 s_v[FP64 ? 1 : 2 * 128];
     if constexpr (!FP64) {
@@ -964,143 +1110,22 @@ __global__ void __launch_bounds__(128) k_contact_sphere(Arrays a, Sizes z)
     if (D.flags & DEM_FLAG_SLOTS) return;
     const bool rb = D.rebuild != 0;
     const int lp = rb ? D.cpar ^ 1 : D.cpar, par = D.parity;
-    const int64_t s0 = S.s0, e0 = S.e0;
     typename CT<FP64>::Prm prm;
     const H *hread;
     H *hwrite;
     if constexpr (FP64) {
         prm = {S.kn, S.kt, S.cn, S.ct, S.mu_s, S.mu_r, S.mu_t, S.w0, S.h};
-        hread = (rb ? a.hist64_rm : a.hist64[par]) + e0;
-        hwrite = a.hist64[par ^ 1] + e0;
+        hread = (rb ? a.hist64_rm : a.hist64[par]) + S.e0;
+        hwrite = a.hist64[par ^ 1] + S.e0;
     } else {
         prm = {(float)S.kn, (float)S.kt, (float)S.cn, (float)S.ct, (float)S.mu_s, (float)S.mu_r,
                (float)S.mu_t, (float)S.w0, (float)S.h};
-        hread = (rb ? a.hist32_rm : a.hist32[par]) + e0;
-        hwrite = a.hist32[par ^ 1] + e0;
+        hread = (rb ? a.hist32_rm : a.hist32[par]) + S.e0;
+        hwrite = a.hist32[par ^ 1] + S.e0;
     }
-    const float q = pow2f(S.qexp);
-    const int2 *cand = a.cand[lp] + e0;
-    const int off = a.coff[lp][k], n = a.ccnt[lp][k];
-    // own data
-    typename CT<FP64>::P mp;
-    float4 mr;
-    typename CT<FP64>::VR mv, mw;
-    if constexpr (FP64) { mp = a.dp_[k]; mv = a.dv_[k]; mw = a.dw_[k]; }
-    else {
-        mp = s_x[2 * threadIdx.x]; mr = as_f4(s_x[2 * threadIdx.x + 1]);
-        mv = s_v[2 * threadIdx.x]; mw = s_v[2 * threadIdx.x + 1];
-    }
-    V F, Tq;
-    if constexpr (FP64) { F = d3(0, 0, 0); Tq = d3(0, 0, 0); }
-    else { F = f3(0.f, 0.f, 0.f); Tq = f3(0.f, 0.f, 0.f); }
-    int nc = 0, flags = 0;
-    // One entry: this sphere as sphere a.  Every step of the law maps exactly
-    // onto its negative or onto itself when the spheres swap (differences and
-    // products of negated operands round to the negated or the same value),
-    // so this evaluation's share a is bit for bit the share of this side of
-    // the owner's evaluation; the owner's S is seen from this side with the
-    // opposite sign.  The owner's thread writes the history.
-    auto entry = [&](int f, bool owned, bool ok, const H &hp, const typename CT<FP64>::P &pp,
-                     const float4 &pr, const typename CT<FP64>::VR &pv, const typename CT<FP64>::VR &pw) {
-        PairOut<T, V> o;
-        bool hit = false;
-        const T sgn = owned ? T(1) : T(-1);
-        if (ok) {
-            if constexpr (FP64) {
-                const double3 Sprev = hp.w != 0 ? d3(sgn * hp.x, sgn * hp.y, sgn * hp.z) : d3(0, 0, 0);
-                hit = pair_64(mp, mv, mw, pp, pv, pw, Sprev, prm, o);
-            } else {
-                const float3 Sprev = hp.w != 0.f ? f3(sgn * hp.x, sgn * hp.y, sgn * hp.z) : f3(0.f, 0.f, 0.f);
-                hit = pair_mixed(mp, mr, pp, pr, q, mv, mw, pv, pw, Sprev, prm, o);
-            }
-        }
-        if (owned && ok) {
-            H h;
-            if constexpr (FP64) h = hit ? make_dbl4(o.S.x, o.S.y, o.S.z, 1.0) : make_dbl4(0, 0, 0, 0);
-            else h = hit ? make_float4(o.S.x, o.S.y, o.S.z, 1.f) : make_float4(0.f, 0.f, 0.f, 0.f);
-            hwrite[f] = h;
-        }
-        if (!hit) return;
-        if (o.x > T(0.1) * o.rmin) flags |= DEM_FLAG_OVERLAP;
-        V sF, sT;
-        share<T, V>(o, true, sF, sT);
-        F.x = addr(F.x, sF.x); F.y = addr(F.y, sF.y); F.z = addr(F.z, sF.z);
-        Tq.x = addr(Tq.x, sT.x); Tq.y = addr(Tq.y, sT.y); Tq.z = addr(Tq.z, sT.z);
-        ++nc;
-    };
-    // an entry's partner and history indices (clamped: the checks never fail)
-    auto where = [&](int2 c, int f, int64_t &g, int &hidx, bool &ok) {
-        const int kk = c.x & 0x7fffffff;
-        hidx = c.x < 0 ? f : c.y;
-        ok = (unsigned)kk < (unsigned)S.ns && (unsigned)hidx < (unsigned)S.ne;
-        g = s0 + (ok ? kk : 0);
-        if (!ok) hidx = 0;
-    };
-    if constexpr (FP64) {
-        for (int e = 0; e < n; ++e) {
-            const int f = off + 32 * e;
-            const int2 c = cand[f];
-            int64_t g;
-            int hidx;
-            bool ok;
-            where(c, f, g, hidx, ok);
-            entry(f, c.x < 0, ok, hread[hidx], a.dp_[g], make_float4(0.f, 0.f, 0.f, 0.f), a.dv_[g], a.dw_[g]);
-        }
-    } else {
-        // software pipeline: the list entry two ahead and the partner data and
-        // history one ahead are in flight while an entry is evaluated
-        int2 c1 = make_int2(0, 0);
-        if (n > 1) c1 = cand[off + 32];
-        int2 cc = make_int2(0, 0);
-        int4 px = make_int4(0, 0, 0, 0), pr = px;
-        float4 pv = make_float4(0.f, 0.f, 0.f, 0.f), pw = pv;
-        H hp = make_float4(0.f, 0.f, 0.f, 0.f);
-        bool ok = false;
-        if (n > 0) {
-            cc = cand[off];
-            int64_t g;
-            int hidx;
-            where(cc, off, g, hidx, ok);
-            const int64_t lk = g - kb0;
-            if ((uint64_t)lk < 128) {
-                px = s_x[2 * lk]; pr = s_x[2 * lk + 1]; pv = s_v[2 * lk]; pw = s_v[2 * lk + 1];
-            } else {
-                px = a.xqr[2 * g]; pr = a.xqr[2 * g + 1]; pv = a.svw[2 * g]; pw = a.svw[2 * g + 1];
-            }
-            hp = hread[hidx];
-        }
-        for (int e = 0; e < n; ++e) {
-            const int f = off + 32 * e;
-            int4 nx = px, nr = pr;
-            float4 nv = pv, nw = pw;
-            H nh = hp;
-            bool nok = false;
-            if (e + 1 < n) {
-                int64_t g;
-                int hidx;
-                where(c1, f + 32, g, hidx, nok);
-                const int64_t lk = g - kb0;
-                if ((uint64_t)lk < 128) {
-                    nx = s_x[2 * lk]; nr = s_x[2 * lk + 1]; nv = s_v[2 * lk]; nw = s_v[2 * lk + 1];
-                } else {
-                    nx = a.xqr[2 * g]; nr = a.xqr[2 * g + 1]; nv = a.svw[2 * g]; nw = a.svw[2 * g + 1];
-                }
-                nh = hread[hidx];
-            }
-            const int2 c2 = e + 2 < n ? cand[f + 64] : make_int2(0, 0);
-            entry(f, cc.x < 0, ok, hp, px, as_f4(pr), pv, pw);
-            cc = c1; c1 = c2;
-            px = nx; pr = nr; pv = nv; pw = nw; hp = nh; ok = nok;
-        }
-    }
-    if constexpr (FP64) {
-        a.ftc64[2 * k] = make_dbl4(F.x, F.y, F.z, 0.0);
-        a.ftc64[2 * k + 1] = make_dbl4(Tq.x, Tq.y, Tq.z, 0.0);
-    } else {
-        a.ftc32[2 * k] = make_float4(F.x, F.y, F.z, 0.f);
-        a.ftc32[2 * k + 1] = make_float4(Tq.x, Tq.y, Tq.z, 0.f);
-    }
-    if (nc > S.K) flags |= DEM_FLAG_SLOTS;
+    int flags = 0;
+    sphere_contacts<FP64>(a, S, lp, hread, hwrite, prm, pow2f(S.qexp), k, kb0, FP64 ? nullptr : s_x,
+                          FP64 ? nullptr : s_v, flags);
     if (flags) atomicOr(&a.pd[p].flags, flags);
 }
 

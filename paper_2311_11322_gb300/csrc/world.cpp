@@ -1747,19 +1747,19 @@ dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
     if (w->piles.empty()) return DEM_OK;
     dem_status s = collect_flags(w);
     if (s != DEM_OK) return s;
-    struct Knobs { int blk, ib; double item; bool pack, sym; int tile; double cell; };
+    struct Knobs { int blk, ib; double item; bool pack, sym; int tile; double cell; int cmode; };
     const Knobs orig = {w->grav_block, w->grav_ib, w->grav_item, w->grav_pack, w->grav_sym, w->grav_tile,
-                        w->cell_factor};
+                        w->cell_factor, w->contact_mode};
     const int64_t orig_jchunk = w->grav_jchunk;
     std::vector<Knobs> cands;
-    cands.push_back({128, 4, 1048576.0, false, true, 512, 0});
+    cands.push_back({128, 4, 1048576.0, false, true, 512, 0, orig.cmode});
     if (w->precision == DEM_MIXED)
-        for (int tile : {64, 128, 256}) cands.push_back({128, 4, 1048576.0, false, true, tile, 0});
+        for (int tile : {64, 128, 256}) cands.push_back({128, 4, 1048576.0, false, true, tile, 0, orig.cmode});
     for (int blk : {64, 128, 256})
         for (int ib : {1, 2, 4})
             for (double item : {262144.0, 1048576.0, 4194304.0}) {
-                cands.push_back({blk, ib, item, false, false, 0, 0});
-                if (ib % 2 == 0) cands.push_back({blk, ib, item, true, false, 0, 0});
+                cands.push_back({blk, ib, item, false, false, 0, 0, orig.cmode});
+                if (ib % 2 == 0) cands.push_back({blk, ib, item, true, false, 0, 0, orig.cmode});
             }
     // The trials step the live piles.  Snapshot every field that carries state
     // from step to step (the fields a layout change preserves) and put it back
@@ -1792,7 +1792,7 @@ dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
     cudaEvent_t ev[2] = {nullptr, nullptr};
     auto set_knobs = [&](const Knobs &k) -> dem_status {
         w->grav_block = k.blk; w->grav_ib = k.ib; w->grav_item = k.item; w->grav_pack = k.pack;
-        w->grav_sym = k.sym; w->grav_tile = k.tile;
+        w->grav_sym = k.sym; w->grav_tile = k.tile; w->contact_mode = k.cmode;
         w->graph_valid = false;
         if (k.cell > 0 && k.cell != w->cell_factor) return dem_set_tuning(w, "cell_factor", k.cell);
         return DEM_OK;
@@ -1859,6 +1859,18 @@ dem_status dem_autotune(dem_world *w, int32_t trial_steps, double *best_ms_out)
     for (double f : {1.0, 1.25, 1.5, 2.0}) {
         Knobs c = bk;
         c.cell = f;
+        s = set_knobs(c);
+        double per = 0.0;
+        if (s == DEM_OK) s = trial(per);
+        if (s != DEM_OK) return finish(s, orig);
+        if (per < best) { best = per; bk = c; }
+    }
+    // then the contact pass's form (one thread per sphere, or 128-sphere tile
+    // blocks with a shared-memory inbox; both give bitwise the same results)
+    for (int m : {0, 1}) {
+        if (m == bk.cmode) continue;
+        Knobs c = bk;
+        c.cmode = m;
         s = set_knobs(c);
         double per = 0.0;
         if (s == DEM_OK) s = trial(per);

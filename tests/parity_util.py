@@ -195,3 +195,8 @@ def summarize_trajectory(rows):
     out["steps"] = len(rows)
     out["oracle_contacts_max"] = max(r["oracle_contacts"] for r in rows)
     return out
+
+
+def contact_pair_count(world, pid) -> int:
+    """Contact pairs of a pile after the last step (each pair is listed by both spheres)."""
+    return int(world.read(pid, "CONTACTS")[:, 0].sum()) // 2

@@ -1,6 +1,7 @@
 """The autotuner (dem_autotune) through the C ABI.
 
-It times candidate gravity shapes and cell sizes by stepping the live piles;
+It times candidate gravity shapes, cell sizes and the two forms of the
+contact pass by stepping the live piles;
 the piles must leave it in exactly the state they entered it, the knobs it
 keeps must be among its candidates, and the steps after it must still agree
 with the FP64 oracle within the tolerance of the precision.
@@ -59,6 +60,7 @@ def test_autotune_leaves_state_and_keeps_parity(dem, oracle, prec):
         tile = w.get_tuning("grav_tile")
         sym = w.get_tuning("grav_sym")
         assert w.get_tuning("cell_factor") in (1.0, 1.25, 1.5, 2.0)
+        assert w.get_tuning("contact_mode") in (0, 1)
         if sym:
             assert tile in ((0, 512, 64, 128, 256) if prec == W.PRECISION_MIXED else (0, 512))
         else:

@@ -141,3 +141,36 @@ def test_inbox_ranges_do_not_change_results(dem, prec):
     for got in res[1:]:
         for f in FIELDS:
             assert np.array_equal(got[f], res[0][f]), f
+
+
+def test_lists_longer_than_the_inbox(dem):
+    """FP64 tiles hold 640 list entries in their inbox, so a 32-sphere slice of
+    a list longer than 20 entries does not fit; the tile form then evaluates
+    that slice sphere by sphere and must still agree bitwise with the
+    one-thread-per-sphere form, without flagging the pile.  (The mixed path's
+    inbox holds 1,280 entries: lists of more than 40.)"""
+    from scipy.spatial import cKDTree
+    ic, p = W.random_cluster(5, n_agg=40, box=4.0, precision=W.PRECISION_FP64)
+    p = p.replace(G=W.G_SI * 1e4, max_contacts=32)
+    res, skin = [], None
+    for mode in (0, 1):
+        with dem.World() as w:
+            w.set_tuning("contact_mode", mode)
+            w.set_tuning("skin", 0.3)
+            pid = w.add_pile(ic, p)
+            skin = w.info(pid)["skin"]
+            w.step(3)
+            w.sync()
+            assert w.flags(pid) & dem.DEM_FLAG_SLOTS == 0
+            res.append({f: w.read(pid, f) for f in FIELDS})
+    # candidate lists at the first step: spheres of other aggregates within the
+    # radii sum plus the skin (the positions have barely moved by then)
+    agg = np.repeat(np.arange(len(ic.counts)), ic.counts)
+    n = np.zeros(len(ic.pos), int)
+    for i, j in cKDTree(ic.pos).query_pairs(2.0 * ic.radius.max() + skin):
+        if agg[i] != agg[j] and np.linalg.norm(ic.pos[i] - ic.pos[j]) < ic.radius[i] + ic.radius[j] + skin:
+            n[i] += 1
+            n[j] += 1
+    assert n.max() >= 22, n.max()
+    for f in FIELDS:
+        assert np.array_equal(res[1][f], res[0][f]), f
