@@ -225,6 +225,7 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3, mode=
     with dem.World() as w:
         if mode is not None:
             w.set_tuning("contact_mode", mode)
+        mode_used = int(w.get_tuning("contact_mode"))
         pid = w.add_pile(ic, p)
         w.set_timed_kernel("CONTACT")
         flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
@@ -249,19 +250,20 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3, mode=
             rb.append(w.step_timed()[1])
     z = float(cnt.sum())
     N = ic.n_sph
-    # compulsory bytes per step: own sorted state 4 x float4 (64), candidate
-    # count, sorted index, previous sorted position, previous and new history
-    # counts (5 x 4), F and tau out (2 x float4 = 32), the candidate list (4 per
-    # entry, at least one per contact) and every contact's history slot read
-    # and written (float4 each)
-    layout = N * (64 + 20 + 32) + z * (4 + 32)
+    # this library's own compulsory bytes per step: own sorted records (fixed-
+    # point position with its rounding remainders 32 B, velocity and spin 32 B),
+    # list offset and length (8 B), F and tau out (32 B); per list entry the
+    # entry (partner, mirror: 8 B); per pair its history record read and written
+    # (16 B each)
+    layout = N * (64 + 8 + 32) + z * 8 + (z / 2) * 32
     algo = N * CONTACT_BYTES_PER_SPHERE + (z / 2) * CONTACT_BYTES_PER_PAIR
     ms = statistics.median(ks)
     achieved = algo / (ms / 1e3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
             "frac": achieved / peak_gbs, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-            "traffic": traffic_for("kernels_contact.cu", "k_contact_mixed"),
-            "kernel": "k_contact (pair pass over the kept candidate lists)",
+            "traffic": traffic_for("kernels_contact.cu", "k_contact_sphere" if mode_used == 0 else "k_contact"),
+            "kernel": ("k_contact_sphere (one thread per sphere over its kept candidate list)" if mode_used == 0
+                       else "k_contact (128-sphere tiles, each inner pair once, shared-memory inbox)"),
             "kernel_ms": ms, "rebuilds_in_timed_steps": info["rebuilds"] - r0,
             "rebuild_step_contact_ms": statistics.median(rb),
             "n_spheres": N, "contacts_per_sphere": z / N,
@@ -270,7 +272,8 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3, mode=
                                  "read; F, tau 32 B written) + 32 B per contact pair (16-byte history "
                                  "record read and written)",
             "layout_bytes_per_launch": layout, "frac_on_layout_bytes": layout / (ms / 1e3) / 1e9 / peak_gbs,
-            "layout_bytes": "this library's own layout: 116 B per sphere + 36 B per contact side",
+            "layout_bytes": "this library's own layout: 104 B per sphere + 8 B per list entry + 32 B per "
+                            "contact pair",
             "workload": "dense FCC tetrahedra lattice, %d spheres, overlaps 0.5%% R, gravity off" % N}
 
 

@@ -78,6 +78,10 @@ struct PileStatic {
     double ginv;
     float gscale_f;
     int32_t pad_g;
+    // the contact law's constants in FP32 for the mixed path (kn, kt, cn, ct,
+    // mu_s, mu_r, mu_t, w0, h), rounded once on the host
+    float lawf[9];
+    int32_t pad_law;
 };
 
 // Dynamic per-pile state (device-owned; written by kernels).

@@ -905,8 +905,8 @@ __global__ void __launch_bounds__(kCTile, FP64 ? 2 : 4) k_contact(Arrays a, Size
         hread = (rb ? a.hist64_rm : a.hist64[par]) + e0;
         hwrite = a.hist64[par ^ 1] + e0;
     } else {
-        prm = {(float)S.kn, (float)S.kt, (float)S.cn, (float)S.ct, (float)S.mu_s, (float)S.mu_r,
-               (float)S.mu_t, (float)S.w0, (float)S.h};
+        prm = {S.lawf[0], S.lawf[1], S.lawf[2], S.lawf[3], S.lawf[4], S.lawf[5], S.lawf[6], S.lawf[7],
+               S.lawf[8]};
         hread = (rb ? a.hist32_rm : a.hist32[par]) + e0;
         hwrite = a.hist32[par ^ 1] + e0;
     }
@@ -1118,8 +1118,8 @@ __global__ void __launch_bounds__(128) k_contact_sphere(Arrays a, Sizes z)
         hread = (rb ? a.hist64_rm : a.hist64[par]) + S.e0;
         hwrite = a.hist64[par ^ 1] + S.e0;
     } else {
-        prm = {(float)S.kn, (float)S.kt, (float)S.cn, (float)S.ct, (float)S.mu_s, (float)S.mu_r,
-               (float)S.mu_t, (float)S.w0, (float)S.h};
+        prm = {S.lawf[0], S.lawf[1], S.lawf[2], S.lawf[3], S.lawf[4], S.lawf[5], S.lawf[6], S.lawf[7],
+               S.lawf[8]};
         hread = (rb ? a.hist32_rm : a.hist32[par]) + S.e0;
         hwrite = a.hist32[par ^ 1] + S.e0;
     }

@@ -538,6 +538,10 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
         S.skin_q = (int64_t)std::llround(S.skin / std::ldexp(1.0, S.qexp));
         const dem_params &P = q.P;
         S.G = P.G; S.h = P.dt; S.kn = P.kn; S.kt = P.kt; S.cn = P.cn; S.ct = P.ct;
+        {
+            const double law[9] = {P.kn, P.kt, P.cn, P.ct, P.mu_s, P.mu_r, P.mu_t, P.w0, P.dt};
+            for (int c = 0; c < 9; ++c) S.lawf[c] = (float)law[c];
+        }
         S.mu_s = P.mu_s; S.mu_r = P.mu_r; S.mu_t = P.mu_t; S.w0 = P.w0;
         S.eps2 = P.eps_soft * P.eps_soft;
         S.ext_mass = P.ext_mass; S.M_total = q.M_total;
