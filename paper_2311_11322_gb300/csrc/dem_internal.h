@@ -81,7 +81,11 @@ struct PileStatic {
     // the contact law's constants in FP32 for the mixed path (kn, kt, cn, ct,
     // mu_s, mu_r, mu_t, w0, h), rounded once on the host
     float lawf[9];
-    int32_t pad_law;
+    // mixed path: h as a float-float pair, the spin increment in FP32 and
+    // whether it is nonzero
+    float hff[2];
+    float spin_f[3];
+    int32_t yorp;
 };
 
 // Dynamic per-pile state (device-owned; written by kernels).
@@ -89,6 +93,9 @@ struct PileDyn {
     double O[3], V[3];        // frame of positions / velocities used this step
     float hVf[3];             // h V in FP32 (the neighbour-list test)
     int32_t pad_dyn;
+    // mixed path: O, V and Rc as float-float pairs (hi, lo)
+    float2 Of[3], Vf[3], Rcf[3];
+    float2 pad_dyn2;
     double Rc[3], Vc[3];      // pile COM after the drift, mean velocity after the first kick
     double P_pos[3], P_vel[3], P_acc[3];   // planet
     int64_t steps;
@@ -191,7 +198,10 @@ struct Arrays {
     AggRec64 *rec64;
     double *out;                   // [A][18]: FA_c NA_c FA_g NA_g FA_e NA_e (FP64 path); in the
                                    // mixed path the same 144 bytes hold 18 float-float pairs
-    int32_t out_ff;                // 1: out holds float-float pairs
+    // 1 in the mixed path: out holds float-float pairs, and so does each FP64
+    // slot of the aggregate state (r, v, q, w_body, a, N) and of 1/M: a pair
+    // (hi, lo) with hi = fl(hi + lo) in the 8 bytes of one double
+    int32_t out_ff;
     double *invM;                  // [A] 1 / M
     // neighbour-list reference per aggregate: position relative to the
     // extrapolated pile frame and orientation at the last rebuild, and the

@@ -99,6 +99,45 @@ __device__ __forceinline__ ff ff_of(double x)
 
 __device__ __forceinline__ double ff_value(ff v) { return (double)v.hi + (double)v.lo; }
 
+// a + b for a float b
+__device__ __forceinline__ ff ff_addf(ff a, float b)
+{
+    float s, e;
+    two_sum(a.hi, b, s, e);
+    e = __fadd_rn(e, a.lo);
+    ff r;
+    fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+
+// The pair with lo cut (towards zero) to the bits an FP64 number holds below
+// hi: multiples of 2^(e - 52), e the exponent of hi (lo = 0 when hi is below
+// 2^-74).  Then hi + lo is exactly a double and splitting that double gives
+// the same pair back, so a state read out as doubles and written back is
+// bitwise the state it was.
+__device__ __forceinline__ ff ff_canon(ff v)
+{
+    const int e = ((__float_as_int(v.hi) >> 23) & 255) - 127;
+    if (e < -74) return ff{v.hi, 0.f};
+    const float up = __int_as_float((52 - e + 127) << 23);   // 2^(52 - e)
+    const float dn = __int_as_float((e - 52 + 127) << 23);   // 2^(e - 52)
+    return ff{v.hi, __fmul_rn(truncf(__fmul_rn(v.lo, up)), dn)};
+}
+
+// A float-float pair stored in the 8 bytes of one FP64 slot (the mixed
+// path's aggregate state), stored in the canonical form above.
+__device__ __forceinline__ ff ldff(const double *p)
+{
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    return ff{v.x, v.y};
+}
+__device__ __forceinline__ void stff(double *p, ff v)
+{
+    const ff c = ff_canon(v);
+    *reinterpret_cast<float2 *>(p) = make_float2(c.hi, c.lo);
+}
+__device__ __forceinline__ ff ff_of2(float2 v) { return ff{v.x, v.y}; }
+
 // Rotation matrix (body -> space) of the unit quaternion q = (w, x, y, z) in
 // float-float, to ~2^-44: the FP64 quaternion is split once and every product
 // and sum is an error-free FP32 transformation (FP64 instructions are ~60
@@ -107,6 +146,21 @@ __device__ __forceinline__ void quat_to_R_ff(const double *q, float *Rh, float *
 {
     const ff w = ff_of(q[0]), x = ff_of(q[1]), y = ff_of(q[2]), z = ff_of(q[3]);
     qhi[0] = w.hi; qhi[1] = x.hi; qhi[2] = y.hi; qhi[3] = z.hi;
+    const ff xx = ff_mul(x, x), yy = ff_mul(y, y), zz = ff_mul(z, z);
+    const ff xy = ff_mul(x, y), xz = ff_mul(x, z), yz = ff_mul(y, z);
+    const ff wx = ff_mul(w, x), wy = ff_mul(w, y), wz = ff_mul(w, z);
+    const ff one = {1.0f, 0.0f};
+    auto twice = [](ff a) { return ff{2.0f * a.hi, 2.0f * a.lo}; };
+    const ff R[9] = {ff_sub(one, twice(ff_add(yy, zz))), twice(ff_sub(xy, wz)), twice(ff_add(xz, wy)),
+                     twice(ff_add(xy, wz)), ff_sub(one, twice(ff_add(xx, zz))), twice(ff_sub(yz, wx)),
+                     twice(ff_sub(xz, wy)), twice(ff_add(yz, wx)), ff_sub(one, twice(ff_add(xx, yy)))};
+    for (int k = 0; k < 9; ++k) { Rh[k] = R[k].hi; Rl[k] = R[k].lo; }
+}
+
+// The same from a float-float quaternion (no FP64 instruction at all).
+__device__ __forceinline__ void quat_ff_to_R_ff(const ff *q, float *Rh, float *Rl)
+{
+    const ff w = q[0], x = q[1], y = q[2], z = q[3];
     const ff xx = ff_mul(x, x), yy = ff_mul(y, y), zz = ff_mul(z, z);
     const ff xy = ff_mul(x, y), xz = ff_mul(x, z), yz = ff_mul(y, z);
     const ff wx = ff_mul(w, x), wy = ff_mul(w, y), wz = ff_mul(w, z);

@@ -45,10 +45,13 @@ __device__ __forceinline__ bool bulk_due(const Arrays &a, int p, int mode, int o
 __device__ __forceinline__ void agg_moments(const Arrays &a, int64_t g, const PileDyn &D, double *m)
 {
     const double M = a.M[g];
-    const double x[3] = {a.r[3 * g] - D.O[0], a.r[3 * g + 1] - D.O[1], a.r[3 * g + 2] - D.O[2]};
-    const double u[3] = {a.v[3 * g] - D.V[0], a.v[3 * g + 1] - D.V[1], a.v[3 * g + 2] - D.V[2]};
+    // the state as doubles (the mixed path stores float-float pairs)
+    auto st = [&](const double *s, int k) { return a.out_ff ? ff_value(ldff(s + k)) : s[k]; };
+    const double x[3] = {st(a.r, 3 * g) - D.O[0], st(a.r, 3 * g + 1) - D.O[1], st(a.r, 3 * g + 2) - D.O[2]};
+    const double u[3] = {st(a.v, 3 * g) - D.V[0], st(a.v, 3 * g + 1) - D.V[1], st(a.v, 3 * g + 2) - D.V[2]};
+    const double qd[4] = {st(a.q, 4 * g), st(a.q, 4 * g + 1), st(a.q, 4 * g + 2), st(a.q, 4 * g + 3)};
     double R[9];
-    quat_to_R(a.q + 4 * g, R);
+    quat_to_R(qd, R);
     const double *Ib = a.I + 9 * g;
     double T[9];   // R I_body
     for (int i = 0; i < 3; ++i)
@@ -58,7 +61,7 @@ __device__ __forceinline__ void agg_moments(const Arrays &a, int64_t g, const Pi
     auto rirt = [&](int i, int j) {
         return T[3 * i] * R[3 * j] + T[3 * i + 1] * R[3 * j + 1] + T[3 * i + 2] * R[3 * j + 2];
     };
-    const double *wb = a.wb + 3 * g;
+    const double wb[3] = {st(a.wb, 3 * g), st(a.wb, 3 * g + 1), st(a.wb, 3 * g + 2)};
     m[0] = M;
     for (int c = 0; c < 3; ++c) {
         m[1 + c] = M * x[c];

@@ -86,11 +86,7 @@ __device__ void free_rotate(double *q, double3 &wb, const double *I, const doubl
     wb = d3(y[4], y[5], y[6]);
 }
 
-// Mixed path: the same RK4 step with the stage derivatives evaluated in FP32
-// (from FP32 copies of q, w and the inertia tensor) and the step's increment
-// added to the FP64 state, which is then renormalised in FP64.  The increment
-// is O(h |w|), so its FP32 rounding is ~1e-7 of the change per step, far below
-// the FP32 error of the forces that drive it.
+// Stage derivatives of the torque-free rotor in FP32 (mixed path).
 __device__ __forceinline__ void rot_rhs_f(const float *y, const float *I, const float *Iinv, float *dy)
 {
     const float *q = y, *w = y + 4;
@@ -101,29 +97,6 @@ __device__ __forceinline__ void rot_rhs_f(const float *y, const float *I, const 
     const float3 wv = f3(w[0], w[1], w[2]);
     const float3 dw = mat_mulf(Iinv, -cross(wv, mat_mulf(I, wv)));
     dy[4] = dw.x; dy[5] = dw.y; dy[6] = dw.z;
-}
-
-__device__ void free_rotate_mixed(double *q, double3 &wb, const float *qf, const float *I, const float *Iinv,
-                                  float h)
-{
-    float y[7] = {qf[0], qf[1], qf[2], qf[3], (float)wb.x, (float)wb.y, (float)wb.z};
-    float k1[7], k2[7], k3[7], k4[7], t[7];
-    rot_rhs_f(y, I, Iinv, k1);
-    for (int c = 0; c < 7; ++c) t[c] = y[c] + 0.5f * h * k1[c];
-    rot_rhs_f(t, I, Iinv, k2);
-    for (int c = 0; c < 7; ++c) t[c] = y[c] + 0.5f * h * k2[c];
-    rot_rhs_f(t, I, Iinv, k3);
-    for (int c = 0; c < 7; ++c) t[c] = y[c] + h * k3[c];
-    rot_rhs_f(t, I, Iinv, k4);
-    float d[7];
-    for (int c = 0; c < 7; ++c) d[c] = (h / 6.0f) * (k1[c] + 2.0f * k2[c] + 2.0f * k3[c] + k4[c]);
-    double q0 = q[0] + d[0], q1 = q[1] + d[1], q2 = q[2] + d[2], q3 = q[3] + d[3];
-    // |q|^2 = 1 + e with e ~ |d|^2 (the increment is tangent to the unit
-    // sphere): 1/|q| = 1 - e/2 + 3e^2/8 - ..., the dropped terms O(e^3)
-    const double e = (q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3) - 1.0;
-    const double inv = 1.0 + e * (-0.5 + 0.375 * e);
-    q[0] = q0 * inv; q[1] = q1 * inv; q[2] = q2 * inv; q[3] = q3 * inv;
-    wb = d3(wb.x + d[4], wb.y + d[5], wb.z + d[6]);
 }
 
 // The paper's rotation integrator (Sec. 2.2.1): time-adaptive fifth-order
@@ -190,11 +163,176 @@ __device__ void free_rotate_adaptive(double *q, double3 &wb, const double *I, co
 }
 
 // ---------------------------------------------------------------- step begin
-// Per aggregate: half kick of COM and spin with the stored a_A,n / N_A,n,
-// drift, torque-free rotation, then the record the sphere kernels read:
-// rotation, COM relative to the pile frame, predicted COM velocity
-// v_A,n+1/2 + h/2 a_A,n (Eq. pred-vel) and predicted spin w_A,n+1 (the
-// drifted spin plus the second half kick of the old torque).
+// Neighbour-list validity.  Every sphere of the aggregate moved, relative to
+// the pile frame extrapolated by one step (O + h V), by at most
+// |c' - c'_ref| + |(R - R_ref) b| <= |c' - c'_ref| + 2 |b|max min|q -+ q_ref|
+// since the last rebuild.  The candidate lists hold every pair closer than the
+// radii sum plus the skin at the rebuild, so they stay complete while no
+// sphere has moved more than half the skin.  The bound is taken in FP32
+// (positions relative to the pile frame, reference stored in FP32) with a
+// margin of a few units in the last place of the positions and 1e-4
+// relative, far above its rounding.  c: COM relative to the frame (hi parts),
+// qn: the new orientation in FP32.
+__device__ __forceinline__ void rebuild_test(const Arrays &a, int p, int64_t g, const float (&c)[3],
+                                             const float (&qn)[4])
+{
+    const double skin = a.ps[p].skin;
+    if (!(skin > 0.0)) return;
+    const float *ar = a.aref + 8 * g;
+    const float *hv = a.pd[p].hVf;
+    const float3 dcf = f3(c[0] - hv[0] - ar[0], c[1] - hv[1] - ar[1], c[2] - hv[2] - ar[2]);
+    float dm = 0.f, dp = 0.f;
+    for (int k = 0; k < 4; ++k) {
+        const float m = qn[k] - ar[3 + k], s_ = qn[k] + ar[3 + k];
+        dm = fmaf(m, m, dm);
+        dp = fmaf(s_, s_, dp);
+    }
+    const float big = fmaxf(fabsf(c[0]), fmaxf(fabsf(c[1]), fabsf(c[2]))) +
+                      fmaxf(fabsf(ar[0]), fmaxf(fabsf(ar[1]), fabsf(ar[2])));
+    const float disp = sqrtf(dot(dcf, dcf)) + 2.0f * ar[7] * sqrtf(fminf(dm, dp)) + 1e-6f * (big + ar[7]);
+    if (!(disp * 1.0001f <= 0.5f * (float)skin)) atomicOr(&a.pd[p].rebuild, 1);
+}
+
+// FP64 path.  Per aggregate: half kick of COM and spin with the stored
+// a_A,n / N_A,n, drift, torque-free rotation, then the record the sphere
+// kernels read: rotation, COM relative to the pile frame, predicted COM
+// velocity v_A,n+1/2 + h/2 a_A,n (Eq. pred-vel) and predicted spin w_A,n+1
+// (the drifted spin plus the second half kick of the old torque).
+template <bool ADAPT>
+__device__ __forceinline__ void agg_begin_64(const Arrays &a, int64_t g, int p)
+{
+    const double h = a.ps[p].h;
+    const double *I = a.I + 9 * g, *Iinv = a.Iinv + 9 * g;
+    double q[4] = {a.q[4 * g], a.q[4 * g + 1], a.q[4 * g + 2], a.q[4 * g + 3]};
+    double3 r = ld3(a.r + 3 * g), v = ld3(a.v + 3 * g), wb = ld3(a.wb + 3 * g);
+    const double3 acc = ld3(a.acc + 3 * g), N = ld3(a.torque + 3 * g);
+    double R[9];
+    quat_to_R(q, R);
+    v = v + (0.5 * h) * acc;
+    wb = wb + (0.5 * h) * mat_mul(Iinv, mat_tmul(R, N));
+    r = r + h * v;
+    if (ADAPT && a.ps[p].rot_tol > 0.0) free_rotate_adaptive(q, wb, I, Iinv, h, a.ps[p].rot_tol);
+    else free_rotate(q, wb, I, Iinv, h);
+    quat_to_R(q, R);
+    const double3 wpred_b = wb + (0.5 * h) * mat_mul(Iinv, mat_tmul(R, N));
+    const double3 ws = mat_mul(R, wpred_b);
+    st3(a.r + 3 * g, r);
+    st3(a.v + 3 * g, v);
+    st3(a.wb + 3 * g, wb);
+    a.q[4 * g] = q[0]; a.q[4 * g + 1] = q[1]; a.q[4 * g + 2] = q[2]; a.q[4 * g + 3] = q[3];
+    const PileDyn &D = a.pd[p];
+    const double3 c = r - ld3(D.O);
+    const double3 vb = v + (0.5 * h) * acc - ld3(D.V);
+    const float cf[3] = {(float)c.x, (float)c.y, (float)c.z};
+    const float qn[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
+    rebuild_test(a, p, g, cf, qn);
+    AggRec64 rec;
+    for (int k = 0; k < 9; ++k) rec.R[k] = R[k];
+    st3(rec.c, c);
+    st3(rec.vb, vb);
+    st3(rec.w, ws);
+    a.rec64[g] = rec;
+}
+
+// Mixed path: the torque-free RK4 step with the stage derivatives evaluated
+// in FP32 (from FP32 copies of q, w and the inertia tensor) and the step's
+// increment added to the float-float state; q is then renormalised in
+// float-float by the series 1/|q| = 1 - e/2 + 3e^2/8 - ..., e = |q|^2 - 1
+// ~ |increment|^2 (the increment is tangent to the unit sphere; the dropped
+// terms are O(e^3)).  The increment is O(h |w|), so its FP32 rounding is
+// ~1e-7 of the change per step, far below the FP32 error of the forces that
+// drive it.
+__device__ __forceinline__ void free_rotate_ff(ff (&q)[4], ff (&wb)[3], const float *qf, const float *I,
+                                               const float *Iinv, float h)
+{
+    float y[7] = {qf[0], qf[1], qf[2], qf[3], wb[0].hi, wb[1].hi, wb[2].hi};
+    float k1[7], k2[7], k3[7], k4[7], t[7];
+    rot_rhs_f(y, I, Iinv, k1);
+    for (int c = 0; c < 7; ++c) t[c] = y[c] + 0.5f * h * k1[c];
+    rot_rhs_f(t, I, Iinv, k2);
+    for (int c = 0; c < 7; ++c) t[c] = y[c] + 0.5f * h * k2[c];
+    rot_rhs_f(t, I, Iinv, k3);
+    for (int c = 0; c < 7; ++c) t[c] = y[c] + h * k3[c];
+    rot_rhs_f(t, I, Iinv, k4);
+    float d[7];
+    for (int c = 0; c < 7; ++c) d[c] = (h / 6.0f) * (k1[c] + 2.0f * k2[c] + 2.0f * k3[c] + k4[c]);
+    for (int c = 0; c < 4; ++c) q[c] = ff_addf(q[c], d[c]);
+    ff n2 = ff_mul(q[0], q[0]);
+    for (int c = 1; c < 4; ++c) n2 = ff_add(n2, ff_mul(q[c], q[c]));
+    const ff em = ff_addf(n2, -1.0f);
+    const float e = __fadd_rn(em.hi, em.lo);
+    const ff inv = {1.0f, e * (-0.5f + 0.375f * e)};
+    for (int c = 0; c < 4; ++c) q[c] = ff_mul(q[c], inv);
+    for (int c = 0; c < 3; ++c) wb[c] = ff_addf(wb[c], d[4 + c]);
+}
+
+// Mixed path: the same step with the aggregate state in float-float pairs
+// and every operation on the FP32 units (no FP64 instruction on this path
+// unless the pile asks for the adaptive rotor, which runs in FP64).
+template <bool ADAPT>
+__device__ __forceinline__ void agg_begin_mixed(const Arrays &a, int64_t g, int p)
+{
+    const PileStatic &S = a.ps[p];
+    const PileDyn &D = a.pd[p];
+    const float hf = S.lawf[8];
+    const ff hh = {0.5f * S.hff[0], 0.5f * S.hff[1]}, hfull = {S.hff[0], S.hff[1]};
+    ff q[4], r[3], v[3], wb[3], acc[3];
+    float3 Nf;
+    for (int c = 0; c < 4; ++c) q[c] = ldff(a.q + 4 * g + c);
+    for (int c = 0; c < 3; ++c) {
+        r[c] = ldff(a.r + 3 * g + c);
+        v[c] = ldff(a.v + 3 * g + c);
+        wb[c] = ldff(a.wb + 3 * g + c);
+        acc[c] = ldff(a.acc + 3 * g + c);
+    }
+    Nf = f3(ldff(a.torque + 3 * g).hi, ldff(a.torque + 3 * g + 1).hi, ldff(a.torque + 3 * g + 2).hi);
+    // spin kicks and the rotor's stage derivatives are increments: FP32
+    const float *I32 = a.I32 + 18 * g, *Iinv32 = I32 + 9;
+    float qf[4] = {q[0].hi, q[1].hi, q[2].hi, q[3].hi};
+    float Rf[9], Rlo[9];
+    quat_to_Rf(qf, Rf);
+    const float3 dw = (0.5f * hf) * mat_mulf(Iinv32, mat_tmulf(Rf, Nf));
+    for (int c = 0; c < 3; ++c) v[c] = ff_add(v[c], ff_mul(hh, acc[c]));
+    wb[0] = ff_addf(wb[0], dw.x); wb[1] = ff_addf(wb[1], dw.y); wb[2] = ff_addf(wb[2], dw.z);
+    for (int c = 0; c < 3; ++c) r[c] = ff_add(r[c], ff_mul(hfull, v[c]));
+    if (ADAPT && S.rot_tol > 0.0) {
+        double qd[4] = {ff_value(q[0]), ff_value(q[1]), ff_value(q[2]), ff_value(q[3])};
+        double3 wd = d3(ff_value(wb[0]), ff_value(wb[1]), ff_value(wb[2]));
+        free_rotate_adaptive(qd, wd, a.I + 9 * g, a.Iinv + 9 * g, S.h, S.rot_tol);
+        for (int c = 0; c < 4; ++c) q[c] = ff_of(qd[c]);
+        wb[0] = ff_of(wd.x); wb[1] = ff_of(wd.y); wb[2] = ff_of(wd.z);
+    } else {
+        free_rotate_ff(q, wb, qf, I32, Iinv32, hf);
+    }
+    // rotation matrix in float-float from the float-float quaternion
+    quat_ff_to_R_ff(q, Rf, Rlo);
+    for (int c = 0; c < 4; ++c) qf[c] = q[c].hi;
+    const float3 wpred = f3(wb[0].hi, wb[1].hi, wb[2].hi) + (0.5f * hf) * mat_mulf(Iinv32, mat_tmulf(Rf, Nf));
+    const float3 wsf = mat_mulf(Rf, wpred);
+    for (int c = 0; c < 4; ++c) stff(a.q + 4 * g + c, q[c]);
+    for (int c = 0; c < 3; ++c) {
+        stff(a.r + 3 * g + c, r[c]);
+        stff(a.v + 3 * g + c, v[c]);
+        stff(a.wb + 3 * g + c, wb[c]);
+    }
+    if (!(isfinite(r[0].hi) && isfinite(r[1].hi) && isfinite(r[2].hi)))
+        atomicOr(&a.pd[p].flags, DEM_FLAG_NONFINITE);
+    ff cc[3];
+    float vb[3];
+    for (int c = 0; c < 3; ++c) {
+        cc[c] = ff_sub(r[c], ff_of2(D.Of[c]));
+        vb[c] = ff_sub(ff_add(v[c], ff_mul(hh, acc[c])), ff_of2(D.Vf[c])).hi;
+    }
+    const float cf[3] = {cc[0].hi, cc[1].hi, cc[2].hi};
+    rebuild_test(a, p, g, cf, qf);
+    AggRecMixed rec;
+    for (int k = 0; k < 9; ++k) { rec.Rh[k] = Rf[k]; rec.Rl[k] = Rlo[k]; }
+    for (int c = 0; c < 3; ++c) { rec.ch[c] = cc[c].hi; rec.cl[c] = cc[c].lo; rec.vb[c] = vb[c]; }
+    rec.w[0] = wsf.x; rec.w[1] = wsf.y; rec.w[2] = wsf.z;
+    rec.pad[0] = rec.pad[1] = 0.f;
+    a.rec32[g] = rec;
+}
+
 template <bool FP64, bool ADAPT>
 __global__ void k_agg_begin(Arrays a, Sizes z)
 {
@@ -203,102 +341,8 @@ __global__ void k_agg_begin(Arrays a, Sizes z)
     if (g >= z.A) return;
     int p = a.agg_pile[g];
     if (!pile_active(a, p)) return;
-    const double h = a.ps[p].h;
-    const double *I = a.I + 9 * g, *Iinv = a.Iinv + 9 * g;
-    double q[4] = {a.q[4 * g], a.q[4 * g + 1], a.q[4 * g + 2], a.q[4 * g + 3]};
-    double3 r = ld3(a.r + 3 * g), v = ld3(a.v + 3 * g), wb = ld3(a.wb + 3 * g);
-    double3 acc = ld3(a.acc + 3 * g), N = ld3(a.torque + 3 * g);
-    double R[9];
-    float Rf[9], Rlo[9], qf[4];
-    double3 ws;
-    float3 wsf;
-    if constexpr (FP64) {
-        quat_to_R(q, R);
-        v = v + (0.5 * h) * acc;
-        wb = wb + (0.5 * h) * mat_mul(Iinv, mat_tmul(R, N));
-        r = r + h * v;
-        if (ADAPT && a.ps[p].rot_tol > 0.0) free_rotate_adaptive(q, wb, I, Iinv, h, a.ps[p].rot_tol);
-        else free_rotate(q, wb, I, Iinv, h);
-        quat_to_R(q, R);
-        double3 wpred_b = wb + (0.5 * h) * mat_mul(Iinv, mat_tmul(R, N));
-        ws = mat_mul(R, wpred_b);
-        wsf = f3(0.f, 0.f, 0.f);
-    } else {
-        // spin kicks and the rotor's stage derivatives are increments: FP32
-        const float *I32 = a.I32 + 18 * g, *Iinv32 = I32 + 9;
-        const float hf = (float)h;
-        for (int c = 0; c < 4; ++c) qf[c] = (float)q[c];
-        quat_to_Rf(qf, Rf);
-        const float3 Nf = f3((float)N.x, (float)N.y, (float)N.z);
-        const float3 dw = (0.5f * hf) * mat_mulf(Iinv32, mat_tmulf(Rf, Nf));
-        v = v + (0.5 * h) * acc;
-        wb = d3(wb.x + dw.x, wb.y + dw.y, wb.z + dw.z);
-        r = r + h * v;
-        if (ADAPT && a.ps[p].rot_tol > 0.0) free_rotate_adaptive(q, wb, I, Iinv, h, a.ps[p].rot_tol);
-        else free_rotate_mixed(q, wb, qf, I32, Iinv32, hf);
-        // rotation matrix in float-float straight from the FP64 quaternion
-        quat_to_R_ff(q, Rf, Rlo, qf);
-        const float3 wpred = f3((float)wb.x, (float)wb.y, (float)wb.z) +
-                             (0.5f * hf) * mat_mulf(Iinv32, mat_tmulf(Rf, Nf));
-        wsf = mat_mulf(Rf, wpred);
-        ws = d3(0, 0, 0);
-    }
-    st3(a.r + 3 * g, r);
-    st3(a.v + 3 * g, v);
-    st3(a.wb + 3 * g, wb);
-    a.q[4 * g] = q[0]; a.q[4 * g + 1] = q[1]; a.q[4 * g + 2] = q[2]; a.q[4 * g + 3] = q[3];
-    const PileDyn &D = a.pd[p];
-    double3 c = r - ld3(D.O);
-    double3 vb = v + (0.5 * h) * acc - ld3(D.V);
-    ff cx, cy, cz;
-    if constexpr (!FP64) { cx = ff_of(c.x); cy = ff_of(c.y); cz = ff_of(c.z); }
-    else { cx = ff{(float)c.x, 0.f}; cy = ff{(float)c.y, 0.f}; cz = ff{(float)c.z, 0.f}; }
-    // Neighbour-list validity.  Every sphere of the aggregate moved, relative
-    // to the pile frame extrapolated by one step (O + h V), by at most
-    // |c' - c'_ref| + |(R - R_ref) b| <= |c' - c'_ref| + 2 |b|max min|q -+ q_ref|
-    // since the last rebuild.  The candidate lists hold every pair closer than
-    // the radii sum plus the skin at the rebuild, so they stay complete while
-    // no sphere has moved more than half the skin.  The bound is taken in
-    // FP32 (positions relative to the pile frame, reference stored in FP32)
-    // with a margin of a few units in the last place of the positions and
-    // 1e-4 relative, far above its rounding.
-    const double skin = a.ps[p].skin;
-    if (skin > 0.0) {
-        const float *ar = a.aref + 8 * g;
-        const float *hv = D.hVf;
-        const float3 dcf = f3(cx.hi - hv[0] - ar[0], cy.hi - hv[1] - ar[1], cz.hi - hv[2] - ar[2]);
-        float qn[4];
-        if constexpr (FP64) { for (int k = 0; k < 4; ++k) qn[k] = (float)q[k]; }
-        else { for (int k = 0; k < 4; ++k) qn[k] = qf[k]; }
-        float dm = 0.f, dp = 0.f;
-        for (int k = 0; k < 4; ++k) {
-            const float m = qn[k] - ar[3 + k], s_ = qn[k] + ar[3 + k];
-            dm = fmaf(m, m, dm);
-            dp = fmaf(s_, s_, dp);
-        }
-        const float big = fmaxf(fabsf(cx.hi), fmaxf(fabsf(cy.hi), fabsf(cz.hi))) +
-                          fmaxf(fabsf(ar[0]), fmaxf(fabsf(ar[1]), fabsf(ar[2])));
-        const float disp = sqrtf(dot(dcf, dcf)) + 2.0f * ar[7] * sqrtf(fminf(dm, dp)) + 1e-6f * (big + ar[7]);
-        if (!(disp * 1.0001f <= 0.5f * (float)skin)) atomicOr(&a.pd[p].rebuild, 1);
-    }
-    if (FP64) {
-        AggRec64 rec;
-        for (int k = 0; k < 9; ++k) rec.R[k] = R[k];
-        st3(rec.c, c);
-        st3(rec.vb, vb);
-        st3(rec.w, ws);
-        a.rec64[g] = rec;
-    } else {
-        AggRecMixed rec;
-        for (int k = 0; k < 9; ++k) { rec.Rh[k] = Rf[k]; rec.Rl[k] = Rlo[k]; }
-        rec.ch[0] = cx.hi; rec.cl[0] = cx.lo;
-        rec.ch[1] = cy.hi; rec.cl[1] = cy.lo;
-        rec.ch[2] = cz.hi; rec.cl[2] = cz.lo;
-        rec.vb[0] = (float)vb.x; rec.vb[1] = (float)vb.y; rec.vb[2] = (float)vb.z;
-        rec.w[0] = wsf.x; rec.w[1] = wsf.y; rec.w[2] = wsf.z;
-        rec.pad[0] = rec.pad[1] = 0.f;
-        a.rec32[g] = rec;
-    }
+    if constexpr (FP64) agg_begin_64<ADAPT>(a, g, p);
+    else agg_begin_mixed<ADAPT>(a, g, p);
 }
 
 void launch_agg_begin(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
@@ -347,6 +391,8 @@ __device__ void pile_finalize_block(const Arrays &a, int p, double (&sh)[7][128]
         for (int c = 0; c < 3; ++c) {
             D.Rc[c] = s[1 + c] / s[0];
             D.Vc[c] = s[4 + c] / s[0];
+            const ff rc = ff_of(D.Rc[c]);
+            D.Rcf[c] = make_float2(rc.hi, rc.lo);
         }
         if (S.ext_mass > 0) {   // planet: kick with the stored acceleration, drift
             for (int c = 0; c < 3; ++c) {
@@ -365,6 +411,9 @@ __device__ void pile_finalize_block(const Arrays &a, int p, double (&sh)[7][128]
             D.O[c] = D.Rc[c];
             D.V[c] = D.Vc[c];
             D.hVf[c] = (float)(h * D.Vc[c]);
+            D.Of[c] = D.Rcf[c];
+            const ff vc = ff_of(D.Vc[c]);
+            D.Vf[c] = make_float2(vc.hi, vc.lo);
         }
         D.steps += 1;
         D.parity ^= 1;
@@ -387,6 +436,8 @@ __global__ void __launch_bounds__(128) k_pile_reduce(Arrays a, Sizes z)
     __shared__ double sh[7][128];
     __shared__ int last;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    ff accf[7];
+    for (int k = 0; k < 7; ++k) accf[k] = ff{0.f, 0.f};
     const bool act = pile_active(a, p);
     if (act) {
         const PileStatic &S = a.ps[p];
@@ -394,7 +445,25 @@ __global__ void __launch_bounds__(128) k_pile_reduce(Arrays a, Sizes z)
         int64_t end = beg + kAggChunk;
         if (end > S.a0 + S.na) end = S.a0 + S.na;
         for (int64_t g = beg + threadIdx.x; g < end; g += blockDim.x) {
-            if (MODE == 0) {
+            if (MODE == 0 && a.out_ff) {
+                // mixed path: float-float state, M as FP32 (the sums fix the
+                // frame origin and velocity, whose exact values do not enter
+                // any result: positions and velocities are taken relative to
+                // them exactly)
+                const PileDyn &D = a.pd[p];
+                if (D.rebuild) {   // new neighbour-list reference, as the test forms it
+                    float *ar = a.aref + 8 * g;
+                    for (int c = 0; c < 3; ++c)
+                        ar[c] = ff_sub(ldff(a.r + 3 * g + c), ff_of2(D.Of[c])).hi - D.hVf[c];
+                    for (int c = 0; c < 4; ++c) ar[3 + c] = ldff(a.q + 4 * g + c).hi;
+                }
+                const float Mf = (float)a.M[g];
+                accf[0] = ff_addf(accf[0], Mf);
+                for (int c = 0; c < 3; ++c) {
+                    accf[1 + c] = ff_add(accf[1 + c], ff_mul(ff{Mf, 0.f}, ldff(a.r + 3 * g + c)));
+                    accf[4 + c] = ff_add(accf[4 + c], ff_mul(ff{Mf, 0.f}, ldff(a.v + 3 * g + c)));
+                }
+            } else if (MODE == 0) {
                 if (a.pd[p].rebuild) {   // new neighbour-list reference
                     const PileDyn &D = a.pd[p];
                     float *ar = a.aref + 8 * g;
@@ -409,21 +478,41 @@ __global__ void __launch_bounds__(128) k_pile_reduce(Arrays a, Sizes z)
                 }
             } else if (a.out_ff) {   // mixed path: the parts are float-float pairs
                 const float2 *o32 = (const float2 *)(a.out + 18 * g);
-                for (int c = 0; c < 3; ++c) acc[c] += (double)o32[12 + c].x + (double)o32[12 + c].y;
+                for (int c = 0; c < 3; ++c) accf[c] = ff_add(accf[c], ff_of2(o32[12 + c]));
             } else {
                 for (int c = 0; c < 3; ++c) acc[c] += a.out[18 * g + 12 + c];
             }
         }
     }
-    for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = acc[k];
-    __syncthreads();
-    for (int s = 64; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s)
-            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+    if (a.out_ff) {
+        // mixed path: the block's tree in float-float on the FP32 units (the
+        // FP64 units of this part are ~75 times slower), one conversion
+        float2 (*shf)[128] = reinterpret_cast<float2 (*)[128]>(sh);
+        for (int k = 0; k < 7; ++k) shf[k][threadIdx.x] = make_float2(accf[k].hi, accf[k].lo);
         __syncthreads();
+        for (int s = 64; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s)
+                for (int k = 0; k < 7; ++k) {
+                    const ff t = ff_add(ff_of2(shf[k][threadIdx.x]), ff_of2(shf[k][threadIdx.x + s]));
+                    shf[k][threadIdx.x] = make_float2(t.hi, t.lo);
+                }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 7; ++k) acc[k] = ff_value(ff_of2(shf[k][0]));
+    } else {
+        for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = acc[k];
+        __syncthreads();
+        for (int s = 64; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s)
+                for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 7; ++k) acc[k] = sh[k][0];
     }
     if (threadIdx.x == 0) {
-        for (int k = 0; k < 7; ++k) a.chunk_part[ch * kPartialDoubles + k] = sh[k][0];
+        for (int k = 0; k < 7; ++k) a.chunk_part[ch * kPartialDoubles + k] = acc[k];
         __threadfence();   // the sums are visible before this block is counted
         last = atomicAdd(a.pile_arrive + p, 1) == (int)a.ps[p].nch - 1;
         if (last) a.pile_arrive[p] = 0;
@@ -892,56 +981,65 @@ __global__ void k_agg_end(Arrays a, Sizes z)
         }
         float2 *o32 = (float2 *)(a.out + 18 * g);
         for (int k = 0; k < 18; ++k) o32[k] = make_float2(part[k].hi, part[k].lo);
+        // totals, a_A = F_A / M and the closing kick in float-float (the
+        // state is float-float pairs: no FP64 instruction here)
+        const ff hh = {0.5f * S.hff[0], 0.5f * S.hff[1]};
+        const ff iM = ldff(a.invM + g);
+        ff Ft[3], Nt[3], accf[3], v[3], wb[3];
         for (int c = 0; c < 3; ++c) {
-            const double fcg = ff_value(ff_add(part[c], part[6 + c]));
-            const double ncg = ff_value(ff_add(part[3 + c], part[9 + c]));
-            (&Fc.x)[c] = fcg;   // contact + gravity
-            (&Nc.x)[c] = ncg;
+            Ft[c] = ff_add(ff_add(part[c], part[6 + c]), part[12 + c]);
+            Nt[c] = ff_add(ff_add(part[3 + c], part[9 + c]), part[15 + c]);
+            accf[c] = ff_mul(Ft[c], iM);
+            v[c] = ff_add(ldff(a.v + 3 * g + c), ff_mul(hh, accf[c]));
+            wb[c] = ldff(a.wb + 3 * g + c);
         }
-        Fg = d3(0, 0, 0);
-        Ng = d3(0, 0, 0);
+        // closing spin kick: an increment, FP32, with the step's rotation
+        // matrix (the record's FP32 part)
+        const float3 Nf = f3(Nt[0].hi, Nt[1].hi, Nt[2].hi);
+        const float3 dw = (0.5f * S.lawf[8]) * mat_mulf(a.I32 + 18 * g + 9, mat_tmulf(Rh, Nf));
+        wb[0] = ff_addf(wb[0], dw.x); wb[1] = ff_addf(wb[1], dw.y); wb[2] = ff_addf(wb[2], dw.z);
+        if (S.yorp) {   // rigid-rotation increment of the whole pile: increments in FP32
+            const float3 dwy = f3(S.spin_f[0], S.spin_f[1], S.spin_f[2]);
+            const float3 lev = f3(ff_sub(ldff(a.r + 3 * g), ff_of2(D.Rcf[0])).hi,
+                                  ff_sub(ldff(a.r + 3 * g + 1), ff_of2(D.Rcf[1])).hi,
+                                  ff_sub(ldff(a.r + 3 * g + 2), ff_of2(D.Rcf[2])).hi);
+            const float3 dv = cross(dwy, lev), dwb = mat_tmulf(Rh, dwy);
+            v[0] = ff_addf(v[0], dv.x); v[1] = ff_addf(v[1], dv.y); v[2] = ff_addf(v[2], dv.z);
+            wb[0] = ff_addf(wb[0], dwb.x); wb[1] = ff_addf(wb[1], dwb.y); wb[2] = ff_addf(wb[2], dwb.z);
+        }
+        bool fin = true;
+        for (int c = 0; c < 3; ++c) {
+            stff(a.acc + 3 * g + c, accf[c]);
+            stff(a.torque + 3 * g + c, Nt[c]);
+            stff(a.v + 3 * g + c, v[c]);
+            stff(a.wb + 3 * g + c, wb[c]);
+            fin = fin && isfinite(v[c].hi) && isfinite(wb[c].hi) && isfinite(Nt[c].hi);
+        }
+        if (!fin) atomicOr(&a.pd[p].flags, DEM_FLAG_NONFINITE);
     }
     if constexpr (FP64) {
         double *o = a.out + 18 * g;
         st3(o + 0, Fc); st3(o + 3, Nc); st3(o + 6, Fg); st3(o + 9, Ng); st3(o + 12, Fe); st3(o + 15, Ne);
-    }
-    double3 F = Fc + Fg + Fe, N = Nc + Ng + Ne;
-    const double invM = a.invM[g];
-    double3 acc = invM * F;
-    double q[4] = {a.q[4 * g], a.q[4 * g + 1], a.q[4 * g + 2], a.q[4 * g + 3]};
-    double3 v = ld3(a.v + 3 * g) + (0.5 * h) * acc;
-    double3 wb = ld3(a.wb + 3 * g);
-    const double3 dwy = ld3(S.spin_inc);
-    const bool yorp = dwy.x != 0.0 || dwy.y != 0.0 || dwy.z != 0.0;
-    if constexpr (FP64) {
+        const double3 F = Fc + Fg + Fe, N = Nc + Ng + Ne;
+        const double3 acc = a.invM[g] * F;
+        const double q[4] = {a.q[4 * g], a.q[4 * g + 1], a.q[4 * g + 2], a.q[4 * g + 3]};
+        double3 v = ld3(a.v + 3 * g) + (0.5 * h) * acc;
+        double3 wb = ld3(a.wb + 3 * g);
+        const double3 dwy = ld3(S.spin_inc);
         double R[9];
         quat_to_R(q, R);
         wb = wb + (0.5 * h) * mat_mul(a.Iinv + 9 * g, mat_tmul(R, N));
-        if (yorp) {
+        if (dwy.x != 0.0 || dwy.y != 0.0 || dwy.z != 0.0) {
             v = v + cross(dwy, ld3(a.r + 3 * g) - ld3(D.Rc));
             wb = wb + mat_tmul(R, dwy);
         }
-    } else {
-        // closing spin kick: an increment, FP32
-        const float qf[4] = {(float)q[0], (float)q[1], (float)q[2], (float)q[3]};
-        float Rf[9];
-        quat_to_Rf(qf, Rf);
-        const float3 Nf = f3((float)N.x, (float)N.y, (float)N.z);
-        const float3 dw = (0.5f * (float)h) * mat_mulf(a.I32 + 18 * g + 9, mat_tmulf(Rf, Nf));
-        wb = d3(wb.x + dw.x, wb.y + dw.y, wb.z + dw.z);
-        if (yorp) {   // rigid-rotation increment of the whole pile, FP64 as the state
-            double R[9];
-            quat_to_R(q, R);
-            v = v + cross(dwy, ld3(a.r + 3 * g) - ld3(D.Rc));
-            wb = wb + mat_tmul(R, dwy);
-        }
+        st3(a.acc + 3 * g, acc);
+        st3(a.torque + 3 * g, N);
+        st3(a.v + 3 * g, v);
+        st3(a.wb + 3 * g, wb);
+        if (!finite3(v) || !finite3(wb) || !finite3(N) || !finite3(ld3(a.r + 3 * g)))
+            atomicOr(&a.pd[p].flags, DEM_FLAG_NONFINITE);
     }
-    st3(a.acc + 3 * g, acc);
-    st3(a.torque + 3 * g, N);
-    st3(a.v + 3 * g, v);
-    st3(a.wb + 3 * g, wb);
-    if (!finite3(v) || !finite3(wb) || !finite3(N) || !finite3(ld3(a.r + 3 * g)))
-        atomicOr(&a.pd[p].flags, DEM_FLAG_NONFINITE);
 }
 
 void launch_agg_end(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)

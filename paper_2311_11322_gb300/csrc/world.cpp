@@ -496,6 +496,8 @@ dem_status relayout(dem_world *w, const std::vector<PileHost> &newp, const GravP
     return DEM_OK;
 }
 
+void split(double x, float &hi, float &lo);
+
 // Rebuild the device pile table, ids and the gravity plan; capture the graph.
 dem_status upload_tables(dem_world *w, const GravPlan &gp)
 {
@@ -541,6 +543,9 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
         {
             const double law[9] = {P.kn, P.kt, P.cn, P.ct, P.mu_s, P.mu_r, P.mu_t, P.w0, P.dt};
             for (int c = 0; c < 9; ++c) S.lawf[c] = (float)law[c];
+            split(P.dt, S.hff[0], S.hff[1]);
+            for (int c = 0; c < 3; ++c) S.spin_f[c] = (float)P.spin_inc[c];
+            S.yorp = (P.spin_inc[0] != 0.0 || P.spin_inc[1] != 0.0 || P.spin_inc[2] != 0.0) ? 1 : 0;
         }
         S.mu_s = P.mu_s; S.mu_r = P.mu_r; S.mu_t = P.mu_t; S.w0 = P.w0;
         S.eps2 = P.eps_soft * P.eps_soft;
@@ -792,6 +797,37 @@ void split(double x, float &hi, float &lo)
 {
     hi = (float)x;
     lo = (float)(x - (double)hi);
+}
+
+// Mixed path: each FP64 slot of the aggregate state (r, v, q, w_body, a, N)
+// and of 1/M holds the float-float pair (hi, lo) of its value.  hi is the
+// value rounded to FP32 and lo the rounded remainder, so hi = fl(hi + lo):
+// a value read out and written back gives the same pair.
+double pack_ff(double x)
+{
+    float2 f;
+    split(x, f.x, f.y);
+    double d;
+    std::memcpy(&d, &f, sizeof d);
+    return d;
+}
+double unpack_ff(double d)
+{
+    float2 f;
+    std::memcpy(&f, &d, sizeof f);
+    return (double)f.x + (double)f.y;
+}
+void unpack_all(const dem_world *w, double *x, int64_t n)
+{
+    if (w->precision == DEM_MIXED)
+        for (int64_t k = 0; k < n; ++k) x[k] = unpack_ff(x[k]);
+}
+std::vector<double> packed(const dem_world *w, const double *x, int64_t n)
+{
+    std::vector<double> out(x, x + n);
+    if (w->precision == DEM_MIXED)
+        for (auto &d : out) d = pack_ff(d);
+    return out;
 }
 
 void rotmat(const double *q, double *R)
@@ -1124,7 +1160,7 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     {
         std::vector<double> invM(A);
         for (int64_t g = 0; g < A; ++g) invM[g] = 1.0 / M[g];
-        UP(D.invM + a0, invM.data(), 8 * A);
+        UP(D.invM + a0, packed(w, invM.data(), A).data(), 8 * A);
     }
     UP(D.I + 9 * a0, I.data(), 72 * A);
     UP(D.Iinv + 9 * a0, Iinv.data(), 72 * A);
@@ -1137,10 +1173,10 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
             }
         UP(D.I32 + 18 * a0, I32.data(), 72 * A);
     }
-    UP(D.r + 3 * a0, r.data(), 24 * A);
-    UP(D.v + 3 * a0, v.data(), 24 * A);
-    UP(D.q + 4 * a0, q.data(), 32 * A);
-    UP(D.wb + 3 * a0, wb.data(), 24 * A);
+    UP(D.r + 3 * a0, packed(w, r.data(), 3 * A).data(), 24 * A);
+    UP(D.v + 3 * a0, packed(w, v.data(), 3 * A).data(), 24 * A);
+    UP(D.q + 4 * a0, packed(w, q.data(), 4 * A).data(), 32 * A);
+    UP(D.wb + 3 * a0, packed(w, wb.data(), 3 * A).data(), 24 * A);
     CU(cudaMemsetAsync(D.acc + 3 * a0, 0, 24 * A, st));
     CU(cudaMemsetAsync(D.torque + 3 * a0, 0, 24 * A, st));
     CU(cudaMemsetAsync(D.out + 18 * a0, 0, 144 * A, st));
@@ -1158,6 +1194,9 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     for (int d = 0; d < 3; ++d) {
         dyn.O[d] = Rp[d]; dyn.V[d] = Vp[d]; dyn.Rc[d] = Rp[d]; dyn.Vc[d] = Vp[d];
         dyn.hVf[d] = (float)(p->dt * Vp[d]);
+        split(Rp[d], dyn.Of[d].x, dyn.Of[d].y);
+        split(Vp[d], dyn.Vf[d].x, dyn.Vf[d].y);
+        dyn.Rcf[d] = dyn.Of[d];
         dyn.P_pos[d] = p->ext_pos[d]; dyn.P_vel[d] = p->ext_vel[d]; dyn.P_acc[d] = 0.0;
     }
     UP(D.pd + slot, &dyn, sizeof dyn);
@@ -1303,12 +1342,14 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
     PileDyn dyn;
     CHK(get(&dyn, D.pd + slot, sizeof dyn));
     switch (field) {
-    case DEM_FIELD_COM: CHK(need(3 * A)); CHK(get(out, D.r + 3 * a0, 24 * A)); break;
-    case DEM_FIELD_VEL: CHK(need(3 * A)); CHK(get(out, D.v + 3 * a0, 24 * A)); break;
-    case DEM_FIELD_QUAT: CHK(need(4 * A)); CHK(get(out, D.q + 4 * a0, 32 * A)); break;
-    case DEM_FIELD_OMEGA_BODY: CHK(need(3 * A)); CHK(get(out, D.wb + 3 * a0, 24 * A)); break;
-    case DEM_FIELD_ACC: CHK(need(3 * A)); CHK(get(out, D.acc + 3 * a0, 24 * A)); break;
-    case DEM_FIELD_TORQUE_STORED: CHK(need(3 * A)); CHK(get(out, D.torque + 3 * a0, 24 * A)); break;
+    case DEM_FIELD_COM: CHK(need(3 * A)); CHK(get(out, D.r + 3 * a0, 24 * A)); unpack_all(w, out, 3 * A); break;
+    case DEM_FIELD_VEL: CHK(need(3 * A)); CHK(get(out, D.v + 3 * a0, 24 * A)); unpack_all(w, out, 3 * A); break;
+    case DEM_FIELD_QUAT: CHK(need(4 * A)); CHK(get(out, D.q + 4 * a0, 32 * A)); unpack_all(w, out, 4 * A); break;
+    case DEM_FIELD_OMEGA_BODY:
+        CHK(need(3 * A)); CHK(get(out, D.wb + 3 * a0, 24 * A)); unpack_all(w, out, 3 * A); break;
+    case DEM_FIELD_ACC: CHK(need(3 * A)); CHK(get(out, D.acc + 3 * a0, 24 * A)); unpack_all(w, out, 3 * A); break;
+    case DEM_FIELD_TORQUE_STORED:
+        CHK(need(3 * A)); CHK(get(out, D.torque + 3 * a0, 24 * A)); unpack_all(w, out, 3 * A); break;
     case DEM_FIELD_FRAME:
         CHK(need(6));
         for (int c = 0; c < 3; ++c) { out[c] = dyn.O[c]; out[3 + c] = dyn.V[c]; }
@@ -1320,6 +1361,8 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
         std::vector<double> qq(4 * A), ww(3 * A);
         CHK(get(qq.data(), D.q + 4 * a0, 32 * A));
         CHK(get(ww.data(), D.wb + 3 * a0, 24 * A));
+        unpack_all(w, qq.data(), 4 * A);
+        unpack_all(w, ww.data(), 3 * A);
         for (int64_t a = 0; a < A; ++a) {
             double R[9];
             rotmat(&qq[4 * a], R);
@@ -1334,6 +1377,8 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
         std::vector<int32_t> ag(N);
         CHK(get(qq.data(), D.q + 4 * a0, 32 * A));
         CHK(get(rr.data(), D.r + 3 * a0, 24 * A));
+        unpack_all(w, qq.data(), 4 * A);
+        unpack_all(w, rr.data(), 3 * A);
         CHK(get(bb.data(), D.b64 + 3 * s0, 24 * N));
         CHK(get(ag.data(), D.sph_agg + s0, 4 * N));
         for (int64_t i = 0; i < N; ++i) {
@@ -1506,12 +1551,14 @@ dem_status dem_write_state(dem_world *w, int32_t pile_id, int32_t field, const d
     PileDyn dyn;
     CU(cudaMemcpy(&dyn, D.pd + slot, sizeof dyn, cudaMemcpyDeviceToHost));
     switch (field) {
-    case DEM_FIELD_COM: CHK(need(3 * A)); CHK(put(D.r + 3 * a0, in, 24 * A)); break;
-    case DEM_FIELD_VEL: CHK(need(3 * A)); CHK(put(D.v + 3 * a0, in, 24 * A)); break;
-    case DEM_FIELD_QUAT: CHK(need(4 * A)); CHK(put(D.q + 4 * a0, in, 32 * A)); break;
-    case DEM_FIELD_OMEGA_BODY: CHK(need(3 * A)); CHK(put(D.wb + 3 * a0, in, 24 * A)); break;
-    case DEM_FIELD_ACC: CHK(need(3 * A)); CHK(put(D.acc + 3 * a0, in, 24 * A)); break;
-    case DEM_FIELD_TORQUE_STORED: CHK(need(3 * A)); CHK(put(D.torque + 3 * a0, in, 24 * A)); break;
+    case DEM_FIELD_COM: CHK(need(3 * A)); CHK(put(D.r + 3 * a0, packed(w, in, 3 * A).data(), 24 * A)); break;
+    case DEM_FIELD_VEL: CHK(need(3 * A)); CHK(put(D.v + 3 * a0, packed(w, in, 3 * A).data(), 24 * A)); break;
+    case DEM_FIELD_QUAT: CHK(need(4 * A)); CHK(put(D.q + 4 * a0, packed(w, in, 4 * A).data(), 32 * A)); break;
+    case DEM_FIELD_OMEGA_BODY:
+        CHK(need(3 * A)); CHK(put(D.wb + 3 * a0, packed(w, in, 3 * A).data(), 24 * A)); break;
+    case DEM_FIELD_ACC: CHK(need(3 * A)); CHK(put(D.acc + 3 * a0, packed(w, in, 3 * A).data(), 24 * A)); break;
+    case DEM_FIELD_TORQUE_STORED:
+        CHK(need(3 * A)); CHK(put(D.torque + 3 * a0, packed(w, in, 3 * A).data(), 24 * A)); break;
     case DEM_FIELD_PLANET:
     case DEM_FIELD_FRAME: {
         CHK(need(field == DEM_FIELD_PLANET ? 9 : 6));
@@ -1521,6 +1568,8 @@ dem_status dem_write_state(dem_world *w, int32_t pile_id, int32_t field, const d
             } else {
                 dyn.O[c] = in[c]; dyn.V[c] = in[3 + c];
                 dyn.hVf[c] = (float)(q.P.dt * in[3 + c]);
+                split(in[c], dyn.Of[c].x, dyn.Of[c].y);
+                split(in[3 + c], dyn.Vf[c].x, dyn.Vf[c].y);
             }
         }
         CHK(put(D.pd + slot, &dyn, sizeof dyn));
