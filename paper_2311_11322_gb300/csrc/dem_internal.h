@@ -105,6 +105,8 @@ struct PileDyn {
     int32_t rebuild;          // this step rebuilds the cell list and candidate lists
     int32_t cpar;             // candidate-list buffer of the current lists
     int32_t rebuilds;         // number of rebuilds so far
+    int32_t rebuilt_prev;     // the previous step rebuilt (its sorted order is new)
+    int32_t pad_dyn3;
 };
 
 // Bulk shape and spin of a pile (record laid out as enum dem_bulk) and its

@@ -422,6 +422,7 @@ __device__ void pile_finalize_block(const Arrays &a, int p, double (&sh)[7][128]
             D.rebuilds += 1;
             D.cpar ^= 1;   // the lists built this step become the current ones
         }
+        D.rebuilt_prev = D.rebuild;
         D.rebuild = S.skin <= 0.0 ? 1 : 0;
     }
 }
@@ -821,10 +822,15 @@ __global__ void k_gather(Arrays a, Sizes z)
     const PileStatic &S = a.ps[p];
     int hl = a.sorted[k];
     int64_t i = S.s0 + hl;
-    int al = a.sph_agg[i];
+    // the sorted order changes only at rebuilds: the sorted aggregate ids and
+    // the home -> sorted map (double-buffered by parity) are written in a
+    // rebuild step and the step after it, and read otherwise
+    const PileDyn &D = a.pd[p];
+    const bool fresh = D.rebuild != 0, refresh = fresh || D.rebuilt_prev != 0;
+    const int al = fresh ? a.sph_agg[i] : a.sagg[k];
     int64_t g = S.a0 + al;
-    a.pos_of_home[a.pd[p].parity ^ 1][i] = (int32_t)(k - S.s0);
-    a.sagg[k] = al;
+    if (refresh) a.pos_of_home[D.parity ^ 1][i] = (int32_t)(k - S.s0);
+    if (fresh) a.sagg[k] = al;
     if (FP64) {
         const AggRec64 &rec = a.rec64[g];
         const double *b = a.b64 + 3 * i;
@@ -855,7 +861,7 @@ __global__ void k_gather(Arrays a, Sizes z)
         a.xqr[2 * k] = make_int4(X, Y, Z, Sr);
         a.xqr[2 * k + 1] = make_int4(__float_as_int(rm.x), __float_as_int(rm.y), __float_as_int(rm.z),
                                      __float_as_int(rm.w));
-        if (a.pd[p].rebuild) a.sph_[k] = make_float4(px.hi, py.hi, pz.hi, bh.w);
+        if (fresh) a.sph_[k] = make_float4(px.hi, py.hi, pz.hi, bh.w);
         a.svw[2 * k] = make_float4(v.x, v.y, v.z, __int_as_float(al));
         a.svw[2 * k + 1] = make_float4(w.x, w.y, w.z, __int_as_float(hl));
     }
@@ -936,6 +942,9 @@ __global__ void k_agg_end(Arrays a, Sizes z)
             s[6].add(fg.x); s[7].add(fg.y); s[8].add(fg.z);
             s[9].add(ng.x); s[10].add(ng.y); s[11].add(ng.z);
         };
+        // a pile without self-gravity has zero sphere gravity: not read
+        const bool grav = S.G != 0.0;
+        const dbl4 g0 = make_dbl4(0.0, 0.0, 0.0, 0.0);
         int t2 = 0;
         if (!planet) {
             for (; t2 + 1 < n; t2 += 2) {
@@ -944,7 +953,7 @@ __global__ void k_agg_end(Arrays a, Sizes z)
                 const float4 bha = a.bh[i], bhb = a.bh[i + 1];
                 const float4 fa = a.ftc32[2 * ka], ta = a.ftc32[2 * ka + 1];
                 const float4 fb = a.ftc32[2 * kb], tb = a.ftc32[2 * kb + 1];
-                const dbl4 ga = a.fg[i], gb = a.fg[i + 1];
+                const dbl4 ga = grav ? a.fg[i] : g0, gb = grav ? a.fg[i + 1] : g0;
                 term(bha, fa, ta, ga);
                 term(bhb, fb, tb, gb);
             }
@@ -954,7 +963,7 @@ __global__ void k_agg_end(Arrays a, Sizes z)
             const float4 bh = a.bh[i];
             const float3 lever = mat_mulf(Rh, f3(bh.x, bh.y, bh.z));
             const int64_t ks = S.s0 + poh[i];
-            term(bh, a.ftc32[2 * ks], a.ftc32[2 * ks + 1], a.fg[i]);
+            term(bh, a.ftc32[2 * ks], a.ftc32[2 * ks + 1], grav ? a.fg[i] : g0);
             if (planet) {
                 ff px, py, pz;
                 expand_mixed(rec, bh, a.bl[i], px, py, pz);
@@ -979,8 +988,11 @@ __global__ void k_agg_end(Arrays a, Sizes z)
         } else {
             for (int k = 12; k < 18; ++k) part[k] = ff{0.f, 0.f};
         }
+        // the gravity and planet parts of a pile without them stay zero (as
+        // set when the pile was added): not rewritten
         float2 *o32 = (float2 *)(a.out + 18 * g);
-        for (int k = 0; k < 18; ++k) o32[k] = make_float2(part[k].hi, part[k].lo);
+        for (int k = 0; k < 18; ++k)
+            if (k < 6 || (k < 12 && grav) || (k >= 12 && planet)) o32[k] = make_float2(part[k].hi, part[k].lo);
         // totals, a_A = F_A / M and the closing kick in float-float (the
         // state is float-float pairs: no FP64 instruction here)
         const ff hh = {0.5f * S.hff[0], 0.5f * S.hff[1]};

@@ -1191,6 +1191,7 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     UP(D.aref + 8 * a0, aref.data(), 32 * A);
     PileDyn dyn{};
     dyn.rebuild = 1;
+    dyn.rebuilt_prev = 1;
     for (int d = 0; d < 3; ++d) {
         dyn.O[d] = Rp[d]; dyn.V[d] = Vp[d]; dyn.Rc[d] = Rp[d]; dyn.Vc[d] = Vp[d];
         dyn.hVf[d] = (float)(p->dt * Vp[d]);
