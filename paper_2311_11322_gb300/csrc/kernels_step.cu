@@ -365,26 +365,54 @@ void launch_agg_begin(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t s
 // sum M, sum M r, sum M v.  Mode 1 (after the closing kick): sum of the planet
 // force on the pile.  The last of a pile's chunk blocks to finish (counted in
 // pile_arrive, which it puts back to zero) then adds the pile's chunk sums and
-// updates the pile: thread t adds chunks t, t+128, ... in order and a fixed
-// tree combines the threads, so the result does not depend on which block
-// came last.  Fixed tree orders throughout: deterministic.
+// updates the pile: thread t adds chunks t, t+128, ... in order and
+// block_sum7 combines the threads in a fixed order, so the result does not
+// depend on which block came last.  Fixed orders throughout: deterministic.
+// Without a planet the closing pass has nothing to sum: the pile's first
+// chunk block alone updates it.
+// Sum of v over the block's 128 threads in a fixed order (each warp by
+// shuffles, then the four warp sums in warp order); the result is in
+// thread 0.  ws: 4 x 7 scratch doubles.
+__device__ __forceinline__ void block_sum7(double (&v)[7], double *ws)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 7; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < 7; ++k) ws[7 * wid + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 7; ++k) v[k] = (ws[k] + ws[7 + k]) + (ws[14 + k] + ws[21 + k]);
+}
+
+// The same in float-float (mixed path: FP32 units only).
+__device__ __forceinline__ void block_sum7(ff (&v)[7], ff *ws)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 7; ++k) {
+            const ff t = {__shfl_down_sync(0xffffffffu, v[k].hi, o), __shfl_down_sync(0xffffffffu, v[k].lo, o)};
+            v[k] = ff_add(v[k], t);
+        }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < 7; ++k) ws[7 * wid + k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 7; ++k) v[k] = ff_add(ff_add(ws[k], ws[7 + k]), ff_add(ws[14 + k], ws[21 + k]));
+}
+
 template <int MODE>
 __device__ void pile_finalize_block(const Arrays &a, int p, double (&sh)[7][128])
 {
     const PileStatic &S = a.ps[p];
     double s[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int64_t ch = S.ch0 + threadIdx.x; ch < S.ch0 + S.nch; ch += blockDim.x)
-        for (int k = 0; k < 7; ++k) s[k] += __ldcg(a.chunk_part + ch * kPartialDoubles + k);
-    __syncthreads();   // sh is free again
-    for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = s[k];
-    __syncthreads();
-    for (int o = 64; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o)
-            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + o];
-        __syncthreads();
+    if (MODE == 0 || S.ext_mass > 0) {   // the closing pass sums only the planet's reaction
+        for (int64_t ch = S.ch0 + threadIdx.x; ch < S.ch0 + S.nch; ch += blockDim.x)
+            for (int k = 0; k < 7; ++k) s[k] += __ldcg(a.chunk_part + ch * kPartialDoubles + k);
+        __syncthreads();   // sh is free again
+        block_sum7(s, &sh[0][0]);
     }
     if (threadIdx.x != 0) return;
-    for (int k = 0; k < 7; ++k) s[k] = sh[k][0];
     PileDyn &D = a.pd[p];
     const double h = S.h;
     if (MODE == 0) {
@@ -436,6 +464,12 @@ __global__ void __launch_bounds__(128) k_pile_reduce(Arrays a, Sizes z)
     int p = a.chunk_pile[ch];
     __shared__ double sh[7][128];
     __shared__ int last;
+    if (MODE == 1 && !(a.ps[p].ext_mass > 0)) {
+        // no planet: nothing to sum, the pile's first chunk block finishes it
+        if (ch != a.ps[p].ch0 || !pile_active(a, p)) return;
+        pile_finalize_block<MODE>(a, p, sh);
+        return;
+    }
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     ff accf[7];
     for (int k = 0; k < 7; ++k) accf[k] = ff{0.f, 0.f};
@@ -486,31 +520,13 @@ __global__ void __launch_bounds__(128) k_pile_reduce(Arrays a, Sizes z)
         }
     }
     if (a.out_ff) {
-        // mixed path: the block's tree in float-float on the FP32 units (the
+        // mixed path: the block's sum in float-float on the FP32 units (the
         // FP64 units of this part are ~75 times slower), one conversion
-        float2 (*shf)[128] = reinterpret_cast<float2 (*)[128]>(sh);
-        for (int k = 0; k < 7; ++k) shf[k][threadIdx.x] = make_float2(accf[k].hi, accf[k].lo);
-        __syncthreads();
-        for (int s = 64; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s)
-                for (int k = 0; k < 7; ++k) {
-                    const ff t = ff_add(ff_of2(shf[k][threadIdx.x]), ff_of2(shf[k][threadIdx.x + s]));
-                    shf[k][threadIdx.x] = make_float2(t.hi, t.lo);
-                }
-            __syncthreads();
-        }
+        block_sum7(accf, reinterpret_cast<ff *>(&sh[0][0]));
         if (threadIdx.x == 0)
-            for (int k = 0; k < 7; ++k) acc[k] = ff_value(ff_of2(shf[k][0]));
+            for (int k = 0; k < 7; ++k) acc[k] = ff_value(accf[k]);
     } else {
-        for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = acc[k];
-        __syncthreads();
-        for (int s = 64; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s)
-                for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0)
-            for (int k = 0; k < 7; ++k) acc[k] = sh[k][0];
+        block_sum7(acc, &sh[0][0]);
     }
     if (threadIdx.x == 0) {
         for (int k = 0; k < 7; ++k) a.chunk_part[ch * kPartialDoubles + k] = acc[k];
