@@ -255,6 +255,8 @@ struct Sizes {
     int32_t gtile;   // spheres per tile of the symmetric gravity form (512, or 128 in the mixed path)
     int32_t icap;    // contact inbox entries used per tile range (<= the kernel's capacity)
     int32_t cmode;   // contact pass: 0 = one thread per sphere, 1 = tiles with a shared-memory inbox
+    int32_t gacc_on; // mixed symmetric gravity: piles of more than one tile leave their sums in gacc,
+                     // which k_agg_end turns into forces
 };
 
 // ---- kernel launchers (kernels_*.cu) -------------------------------------

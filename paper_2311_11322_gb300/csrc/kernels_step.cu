@@ -958,9 +958,24 @@ __global__ void k_agg_end(Arrays a, Sizes z)
             s[6].add(fg.x); s[7].add(fg.y); s[8].add(fg.z);
             s[9].add(ng.x); s[10].add(ng.y); s[11].add(ng.z);
         };
-        // a pile without self-gravity has zero sphere gravity: not read
+        // a pile without self-gravity has zero sphere gravity: not read.
+        // Mixed symmetric gravity leaves the sums of a pile of more than one
+        // tile in 64-bit integer accumulators: F_i = G m_i x sum x 2^-k here,
+        // stored for the read-out, and the accumulators cleared for the next step
         const bool grav = S.G != 0.0;
+        const bool gint = grav && z.gacc_on && a.gnchunk[p] > 1;
         const dbl4 g0 = make_dbl4(0.0, 0.0, 0.0, 0.0);
+        auto gravity_of = [&](int64_t i) -> dbl4 {
+            if (!gint) return grav ? a.fg[i] : g0;
+            longlong2 *gp = reinterpret_cast<longlong2 *>(a.gacc + 4 * i);
+            const longlong2 xy = gp[0], zw = gp[1];
+            gp[0] = make_longlong2(0, 0);
+            gp[1] = make_longlong2(0, 0);
+            const double gm = S.G * a.m64[i] * S.ginv;
+            const dbl4 f = make_dbl4(gm * (double)xy.x, gm * (double)xy.y, gm * (double)zw.x, 0.0);
+            a.fg[i] = f;
+            return f;
+        };
         int t2 = 0;
         if (!planet) {
             for (; t2 + 1 < n; t2 += 2) {
@@ -969,7 +984,7 @@ __global__ void k_agg_end(Arrays a, Sizes z)
                 const float4 bha = a.bh[i], bhb = a.bh[i + 1];
                 const float4 fa = a.ftc32[2 * ka], ta = a.ftc32[2 * ka + 1];
                 const float4 fb = a.ftc32[2 * kb], tb = a.ftc32[2 * kb + 1];
-                const dbl4 ga = grav ? a.fg[i] : g0, gb = grav ? a.fg[i + 1] : g0;
+                const dbl4 ga = gravity_of(i), gb = gravity_of(i + 1);
                 term(bha, fa, ta, ga);
                 term(bhb, fb, tb, gb);
             }
@@ -979,7 +994,7 @@ __global__ void k_agg_end(Arrays a, Sizes z)
             const float4 bh = a.bh[i];
             const float3 lever = mat_mulf(Rh, f3(bh.x, bh.y, bh.z));
             const int64_t ks = S.s0 + poh[i];
-            term(bh, a.ftc32[2 * ks], a.ftc32[2 * ks + 1], grav ? a.fg[i] : g0);
+            term(bh, a.ftc32[2 * ks], a.ftc32[2 * ks + 1], gravity_of(i));
             if (planet) {
                 ff px, py, pz;
                 expand_mixed(rec, bh, a.bl[i], px, py, pz);

@@ -589,6 +589,7 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     }
     w->Z.gtile = gp.tile;
     w->Z.icap = w->contact_inbox;
+    w->Z.gacc_on = (w->precision == DEM_MIXED && use_sym(w) && !(w->grav_theta > 0)) ? 1 : 0;
     w->Z.cmode = w->contact_mode;
     int bps = gravity_blocks_per_sm(w->precision == DEM_FP64, w->grav_block, w->grav_ib, w->grav_pack,
                                     use_sym(w), gp.tile);
