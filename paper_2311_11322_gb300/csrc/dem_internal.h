@@ -180,7 +180,7 @@ struct Arrays {
     float4 *gpos32;      // mixed: pos hi (+mass)
     dbl4 *gpos64;     // fp64: pos (+mass)
     dbl4 *fg;         // gravity on each sphere (from other aggregates)
-    // contact outputs in sorted order, interleaved: [2k] = force, [2k+1] = torque
+    // contact outputs at each sphere's home index, interleaved: [2i] = force, [2i+1] = torque
     float4 *ftc32;
     dbl4 *ftc64;
     // sorted position (pile-local) of each home sphere, double-buffered by parity
@@ -194,12 +194,15 @@ struct Arrays {
     // aggregates
     int32_t *agg_first, *agg_count, *agg_pile;
     double *M, *I, *Iinv;          // [A], [A][9], [A][9]
-    float *I32;                    // mixed: [A][18] FP32 copies of I and I^-1
+    float *I32, *Iinv32;           // mixed: [A][9] FP32 copies of I and of I^-1
     double *r, *v, *q, *wb, *acc, *torque;   // [A][3], q [A][4]
     AggRecMixed *rec32;
     AggRec64 *rec64;
-    double *out;                   // [A][18]: FA_c NA_c FA_g NA_g FA_e NA_e (FP64 path); in the
-                                   // mixed path the same 144 bytes hold 18 float-float pairs
+    // per-aggregate force and torque by part: out[0] contact, out[1] sphere
+    // gravity, out[2] planet, each [A][6] = F then N (FP64 path; in the mixed
+    // path the same 48 bytes hold 6 float-float pairs).  One array per part,
+    // so that a step that writes only the contact part writes whole sectors.
+    double *out[3];
     // 1 in the mixed path: out holds float-float pairs, and so does each FP64
     // slot of the aggregate state (r, v, q, w_body, a, N) and of 1/M: a pair
     // (hi, lo) with hi = fl(hi + lo) in the 8 bytes of one double
@@ -257,6 +260,7 @@ struct Sizes {
     int32_t cmode;   // contact pass: 0 = one thread per sphere, 1 = tiles with a shared-memory inbox
     int32_t gacc_on; // mixed symmetric gravity: piles of more than one tile leave their sums in gacc,
                      // which k_agg_end turns into forces
+    int32_t grav;    // some pile has self-gravity (G > 0)
 };
 
 // ---- kernel launchers (kernels_*.cu) -------------------------------------

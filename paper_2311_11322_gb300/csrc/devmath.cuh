@@ -278,6 +278,24 @@ __device__ __forceinline__ float3 mat_tmulf(const float *A, float3 x)
               A[2] * x.x + A[5] * x.y + A[8] * x.z);
 }
 
+// Two float4 as one 32-byte store (256-bit global stores exist from sm_100 on);
+// p must be 32-byte aligned.  One request per thread where two 16-byte
+// stores would be two, for stores that scatter across a warp.
+__device__ __forceinline__ void st_f4x2(float4 *p, float4 a, float4 b)
+{
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :: "l"(p), "f"(a.x), "f"(a.y), "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
+
+// Two float4 from one 32-byte load; p must be 32-byte aligned.
+__device__ __forceinline__ void ld_f4x2(const float4 *p, float4 &a, float4 &b)
+{
+    asm("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+
 __device__ __forceinline__ bool finite3(double3 v)
 {
     return isfinite(v.x) && isfinite(v.y) && isfinite(v.z);

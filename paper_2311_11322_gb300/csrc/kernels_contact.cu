@@ -812,12 +812,15 @@ __device__ __forceinline__ void sphere_contacts(const Arrays &a, const PileStati
             px = nx; pr = nr; pv = nv; pw = nw; hp = nh; ok = nok;
         }
     }
+    // stored at the sphere's home index (its aggregate's members are then
+    // contiguous for k_agg_end); the gathered spin record carries that index
     if constexpr (FP64) {
-        a.ftc64[2 * k] = make_dbl4(F.x, F.y, F.z, 0.0);
-        a.ftc64[2 * k + 1] = make_dbl4(Tq.x, Tq.y, Tq.z, 0.0);
+        const int64_t kh = s0 + (int64_t)mw.w;
+        a.ftc64[2 * kh] = make_dbl4(F.x, F.y, F.z, 0.0);
+        a.ftc64[2 * kh + 1] = make_dbl4(Tq.x, Tq.y, Tq.z, 0.0);
     } else {
-        a.ftc32[2 * k] = make_float4(F.x, F.y, F.z, 0.f);
-        a.ftc32[2 * k + 1] = make_float4(Tq.x, Tq.y, Tq.z, 0.f);
+        const int64_t kh = s0 + __float_as_int(mw.w);
+        st_f4x2(a.ftc32 + 2 * kh, make_float4(F.x, F.y, F.z, 0.f), make_float4(Tq.x, Tq.y, Tq.z, 0.f));
     }
     if (nc > S.K) flags |= DEM_FLAG_SLOTS;
 }
@@ -1063,13 +1066,15 @@ __global__ void __launch_bounds__(kCTile, FP64 ? 2 : 4) k_contact(Arrays a, Size
                 Tq.z = addr(Tq.z, inbox[5 * SM::kCap + slot]);
                 ++nc;
             }
-            const int64_t k = s0 + first + tid;
+            // at the sphere's home index (from the staged spin record)
             if constexpr (FP64) {
-                a.ftc64[2 * k] = make_dbl4(F.x, F.y, F.z, 0.0);
-                a.ftc64[2 * k + 1] = make_dbl4(Tq.x, Tq.y, Tq.z, 0.0);
+                const int64_t kh = s0 + (int64_t)((const dbl4 *)stage)[2 * kCTile + tid].w;
+                a.ftc64[2 * kh] = make_dbl4(F.x, F.y, F.z, 0.0);
+                a.ftc64[2 * kh + 1] = make_dbl4(Tq.x, Tq.y, Tq.z, 0.0);
             } else {
-                a.ftc32[2 * k] = make_float4(F.x, F.y, F.z, 0.f);
-                a.ftc32[2 * k + 1] = make_float4(Tq.x, Tq.y, Tq.z, 0.f);
+                const float4 *sv = (const float4 *)((const int4 *)stage + kCTile);
+                const int64_t kh = s0 + __float_as_int(sv[kCTile + tid].w);
+                st_f4x2(a.ftc32 + 2 * kh, make_float4(F.x, F.y, F.z, 0.f), make_float4(Tq.x, Tq.y, Tq.z, 0.f));
             }
             if (nc > K) myflags |= DEM_FLAG_SLOTS;
         }

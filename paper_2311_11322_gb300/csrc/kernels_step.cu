@@ -287,7 +287,7 @@ __device__ __forceinline__ void agg_begin_mixed(const Arrays &a, int64_t g, int 
     }
     Nf = f3(ldff(a.torque + 3 * g).hi, ldff(a.torque + 3 * g + 1).hi, ldff(a.torque + 3 * g + 2).hi);
     // spin kicks and the rotor's stage derivatives are increments: FP32
-    const float *I32 = a.I32 + 18 * g, *Iinv32 = I32 + 9;
+    const float *I32 = a.I32 + 9 * g, *Iinv32 = a.Iinv32 + 9 * g;
     float qf[4] = {q[0].hi, q[1].hi, q[2].hi, q[3].hi};
     float Rf[9], Rlo[9];
     quat_to_Rf(qf, Rf);
@@ -479,26 +479,45 @@ __global__ void __launch_bounds__(128) k_pile_reduce(Arrays a, Sizes z)
         int64_t beg = S.a0 + (ch - S.ch0) * kAggChunk;
         int64_t end = beg + kAggChunk;
         if (end > S.a0 + S.na) end = S.a0 + S.na;
-        for (int64_t g = beg + threadIdx.x; g < end; g += blockDim.x) {
-            if (MODE == 0 && a.out_ff) {
-                // mixed path: float-float state, M as FP32 (the sums fix the
-                // frame origin and velocity, whose exact values do not enter
-                // any result: positions and velocities are taken relative to
-                // them exactly)
-                const PileDyn &D = a.pd[p];
+        if (MODE == 0 && a.out_ff) {
+            // mixed path: float-float state, M as FP32 (the sums fix the
+            // frame origin and velocity, whose exact values do not enter any
+            // result: positions and velocities are taken relative to them
+            // exactly).  The thread's kAggChunk / 128 aggregates are loaded
+            // together, then added in index order.
+            constexpr int kPer = kAggChunk / 128;
+            static_assert(kAggChunk % 128 == 0, "k_pile_reduce runs 128 threads per chunk");
+            const PileDyn &D = a.pd[p];
+            float Mf[kPer];
+            ff rr[kPer][3], vv[kPer][3];
+#pragma unroll
+            for (int t = 0; t < kPer; ++t) {
+                const int64_t g = beg + threadIdx.x + 128 * t;
+                const bool in = g < end;
+                Mf[t] = in ? (float)a.M[g] : 0.f;
+                for (int c = 0; c < 3; ++c) {
+                    rr[t][c] = in ? ldff(a.r + 3 * g + c) : ff{0.f, 0.f};
+                    vv[t][c] = in ? ldff(a.v + 3 * g + c) : ff{0.f, 0.f};
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < kPer; ++t) {
+                const int64_t g = beg + threadIdx.x + 128 * t;
+                if (g >= end) break;
                 if (D.rebuild) {   // new neighbour-list reference, as the test forms it
                     float *ar = a.aref + 8 * g;
-                    for (int c = 0; c < 3; ++c)
-                        ar[c] = ff_sub(ldff(a.r + 3 * g + c), ff_of2(D.Of[c])).hi - D.hVf[c];
+                    for (int c = 0; c < 3; ++c) ar[c] = ff_sub(rr[t][c], ff_of2(D.Of[c])).hi - D.hVf[c];
                     for (int c = 0; c < 4; ++c) ar[3 + c] = ldff(a.q + 4 * g + c).hi;
                 }
-                const float Mf = (float)a.M[g];
-                accf[0] = ff_addf(accf[0], Mf);
+                accf[0] = ff_addf(accf[0], Mf[t]);
                 for (int c = 0; c < 3; ++c) {
-                    accf[1 + c] = ff_add(accf[1 + c], ff_mul(ff{Mf, 0.f}, ldff(a.r + 3 * g + c)));
-                    accf[4 + c] = ff_add(accf[4 + c], ff_mul(ff{Mf, 0.f}, ldff(a.v + 3 * g + c)));
+                    accf[1 + c] = ff_add(accf[1 + c], ff_mul(ff{Mf[t], 0.f}, rr[t][c]));
+                    accf[4 + c] = ff_add(accf[4 + c], ff_mul(ff{Mf[t], 0.f}, vv[t][c]));
                 }
-            } else if (MODE == 0) {
+            }
+        } else
+        for (int64_t g = beg + threadIdx.x; g < end; g += blockDim.x) {
+            if (MODE == 0) {
                 if (a.pd[p].rebuild) {   // new neighbour-list reference
                     const PileDyn &D = a.pd[p];
                     float *ar = a.aref + 8 * g;
@@ -512,10 +531,10 @@ __global__ void __launch_bounds__(128) k_pile_reduce(Arrays a, Sizes z)
                     acc[4 + c] += M * a.v[3 * g + c];
                 }
             } else if (a.out_ff) {   // mixed path: the parts are float-float pairs
-                const float2 *o32 = (const float2 *)(a.out + 18 * g);
-                for (int c = 0; c < 3; ++c) accf[c] = ff_add(accf[c], ff_of2(o32[12 + c]));
+                const float2 *o32 = (const float2 *)(a.out[2] + 6 * g);
+                for (int c = 0; c < 3; ++c) accf[c] = ff_add(accf[c], ff_of2(o32[c]));
             } else {
-                for (int c = 0; c < 3; ++c) acc[c] += a.out[18 * g + 12 + c];
+                for (int c = 0; c < 3; ++c) acc[c] += a.out[2][6 * g + c];
             }
         }
     }
@@ -598,7 +617,9 @@ __device__ __forceinline__ int cell_coord_d(double x, double inv_cell, int n)
 
 // Per sphere (home order): expand, cell key, atomic count into the cell (the
 // returned rank is made deterministic later by ordering each cell), gravity
-// input (position relative to the pile frame, mass).
+// input (position relative to the pile frame, mass).  A pile without
+// self-gravity needs no gravity input: in its steps without a rebuild there
+// is nothing to do.
 template <bool FP64>
 __global__ void k_keys(Arrays a, Sizes z)
 {
@@ -608,6 +629,8 @@ __global__ void k_keys(Arrays a, Sizes z)
     int p = a.sph_pile[i];
     if (!pile_active(a, p)) return;
     const PileStatic &S = a.ps[p];
+    const bool grav = S.G != 0.0;
+    if (!grav && !a.pd[p].rebuild) return;
     int64_t g = S.a0 + a.sph_agg[i];
     int cx, cy, cz;
     if (FP64) {
@@ -615,7 +638,7 @@ __global__ void k_keys(Arrays a, Sizes z)
         cx = cell_coord_d(pos.x, S.inv_cell, S.nx);
         cy = cell_coord_d(pos.y, S.inv_cell, S.ny);
         cz = cell_coord_d(pos.z, S.inv_cell, S.nz);
-        a.gpos64[i] = make_dbl4(pos.x, pos.y, pos.z, a.m64[i]);
+        if (grav) a.gpos64[i] = make_dbl4(pos.x, pos.y, pos.z, a.m64[i]);
     } else {
         ff px, py, pz;
         expand_mixed(a.rec32[g], a.bh[i], a.bl[i], px, py, pz);
@@ -623,7 +646,7 @@ __global__ void k_keys(Arrays a, Sizes z)
         cx = cell_coord_f(px.hi, ic, S.nx);
         cy = cell_coord_f(py.hi, ic, S.ny);
         cz = cell_coord_f(pz.hi, ic, S.nz);
-        a.gpos32[i] = make_float4(px.hi, py.hi, pz.hi, (float)a.m64[i]);
+        if (grav) a.gpos32[i] = make_float4(px.hi, py.hi, pz.hi, (float)a.m64[i]);
     }
     if (!a.pd[p].rebuild) return;   // cell list kept from the last rebuild
     const int key = (int)cell_id(cx, cy, cz, S.nx, S.ny);
@@ -897,8 +920,10 @@ void launch_gather(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
 // gravity and planet; a_A = F_A / M; closing half kick of COM and spin; YORP
 // increment dw: v_A += dw x (r_A - R_pile), w_A += dw (rigid rotation of the
 // whole pile).  Members are contiguous (spheres stored in aggregate order).
-template <bool FP64>
-__global__ void k_agg_end(Arrays a, Sizes z)
+// GRAV = false: no pile of the world has self-gravity (the gravity sums are
+// left out, and with them their registers).
+template <bool FP64, bool GRAV>
+__global__ void __launch_bounds__(128) k_agg_end(Arrays a, Sizes z)
 {
     pdl_enter();
     int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -915,7 +940,6 @@ __global__ void k_agg_end(Arrays a, Sizes z)
     const bool planet = S.ext_mass > 0;
     double3 Pp = planet ? ld3(D.P_pos) : d3(0, 0, 0);
     double3 O = ld3(D.O);
-    const int32_t *poh = a.pos_of_home[D.parity ^ 1];
     if constexpr (FP64) {
         Fc = Nc = Fg = Ng = d3(0, 0, 0);
         const AggRec64 &rec = a.rec64[g];
@@ -923,10 +947,9 @@ __global__ void k_agg_end(Arrays a, Sizes z)
             int64_t i = i0 + t;
             const double *b = a.b64 + 3 * i;
             const double3 lever = mat_mul(rec.R, d3(b[0], b[1], b[2]));
-            const int64_t ks = S.s0 + poh[i];
-            const dbl4 f = a.ftc64[2 * ks], tq = a.ftc64[2 * ks + 1];
+            const dbl4 f = a.ftc64[2 * i], tq = a.ftc64[2 * i + 1];
             const double3 fc = d3(f.x, f.y, f.z), tc = d3(tq.x, tq.y, tq.z);
-            const dbl4 gg = a.fg[i];
+            const dbl4 gg = GRAV ? a.fg[i] : make_dbl4(0.0, 0.0, 0.0, 0.0);
             const double3 fg = d3(gg.x, gg.y, gg.z);
             Fc = Fc + fc;
             Nc = Nc + cross(lever, fc) + tc;
@@ -946,23 +969,25 @@ __global__ void k_agg_end(Arrays a, Sizes z)
         const AggRecMixed &rec = a.rec32[g];
         float Rh[9];
         for (int k = 0; k < 9; ++k) Rh[k] = rec.Rh[k];
-        // members in order; the loads of two members are issued together
+        // members in order (without self-gravity the gravity sums stay zero)
         auto term = [&](float4 bh, float4 f, float4 tq, dbl4 gg) {
             const float3 lever = mat_mulf(Rh, f3(bh.x, bh.y, bh.z));
             const float3 fc = f3(f.x, f.y, f.z);
             const float3 nc = cross(lever, fc) + f3(tq.x, tq.y, tq.z);
-            const float3 fg = f3((float)gg.x, (float)gg.y, (float)gg.z);
-            const float3 ng = cross(lever, fg);
             s[0].add(fc.x); s[1].add(fc.y); s[2].add(fc.z);
             s[3].add(nc.x); s[4].add(nc.y); s[5].add(nc.z);
-            s[6].add(fg.x); s[7].add(fg.y); s[8].add(fg.z);
-            s[9].add(ng.x); s[10].add(ng.y); s[11].add(ng.z);
+            if (GRAV) {
+                const float3 fg = f3((float)gg.x, (float)gg.y, (float)gg.z);
+                const float3 ng = cross(lever, fg);
+                s[6].add(fg.x); s[7].add(fg.y); s[8].add(fg.z);
+                s[9].add(ng.x); s[10].add(ng.y); s[11].add(ng.z);
+            }
         };
         // a pile without self-gravity has zero sphere gravity: not read.
         // Mixed symmetric gravity leaves the sums of a pile of more than one
         // tile in 64-bit integer accumulators: F_i = G m_i x sum x 2^-k here,
         // stored for the read-out, and the accumulators cleared for the next step
-        const bool grav = S.G != 0.0;
+        const bool grav = GRAV && S.G != 0.0;
         const bool gint = grav && z.gacc_on && a.gnchunk[p] > 1;
         const dbl4 g0 = make_dbl4(0.0, 0.0, 0.0, 0.0);
         auto gravity_of = [&](int64_t i) -> dbl4 {
@@ -977,13 +1002,13 @@ __global__ void k_agg_end(Arrays a, Sizes z)
             return f;
         };
         int t2 = 0;
-        if (!planet) {
+        if (!planet) {   // the loads of two members issued together
             for (; t2 + 1 < n; t2 += 2) {
                 const int64_t i = i0 + t2;
-                const int64_t ka = S.s0 + poh[i], kb = S.s0 + poh[i + 1];
                 const float4 bha = a.bh[i], bhb = a.bh[i + 1];
-                const float4 fa = a.ftc32[2 * ka], ta = a.ftc32[2 * ka + 1];
-                const float4 fb = a.ftc32[2 * kb], tb = a.ftc32[2 * kb + 1];
+                float4 fa, ta, fb, tb;
+                ld_f4x2(a.ftc32 + 2 * i, fa, ta);
+                ld_f4x2(a.ftc32 + 2 * i + 2, fb, tb);
                 const dbl4 ga = gravity_of(i), gb = gravity_of(i + 1);
                 term(bha, fa, ta, ga);
                 term(bhb, fb, tb, gb);
@@ -992,10 +1017,11 @@ __global__ void k_agg_end(Arrays a, Sizes z)
         for (int t = t2; t < n; ++t) {
             int64_t i = i0 + t;
             const float4 bh = a.bh[i];
-            const float3 lever = mat_mulf(Rh, f3(bh.x, bh.y, bh.z));
-            const int64_t ks = S.s0 + poh[i];
-            term(bh, a.ftc32[2 * ks], a.ftc32[2 * ks + 1], gravity_of(i));
+            float4 fc, tc;
+            ld_f4x2(a.ftc32 + 2 * i, fc, tc);
+            term(bh, fc, tc, gravity_of(i));
             if (planet) {
+                const float3 lever = mat_mulf(Rh, f3(bh.x, bh.y, bh.z));
                 ff px, py, pz;
                 expand_mixed(rec, bh, a.bl[i], px, py, pz);
                 const double3 pos = O + d3((double)px.hi + (double)px.lo, (double)py.hi + (double)py.lo,
@@ -1021,9 +1047,9 @@ __global__ void k_agg_end(Arrays a, Sizes z)
         }
         // the gravity and planet parts of a pile without them stay zero (as
         // set when the pile was added): not rewritten
-        float2 *o32 = (float2 *)(a.out + 18 * g);
         for (int k = 0; k < 18; ++k)
-            if (k < 6 || (k < 12 && grav) || (k >= 12 && planet)) o32[k] = make_float2(part[k].hi, part[k].lo);
+            if (k < 6 || (k < 12 && grav) || (k >= 12 && planet))
+                reinterpret_cast<float2 *>(a.out[k / 6] + 6 * g)[k % 6] = make_float2(part[k].hi, part[k].lo);
         // totals, a_A = F_A / M and the closing kick in float-float (the
         // state is float-float pairs: no FP64 instruction here)
         const ff hh = {0.5f * S.hff[0], 0.5f * S.hff[1]};
@@ -1039,7 +1065,7 @@ __global__ void k_agg_end(Arrays a, Sizes z)
         // closing spin kick: an increment, FP32, with the step's rotation
         // matrix (the record's FP32 part)
         const float3 Nf = f3(Nt[0].hi, Nt[1].hi, Nt[2].hi);
-        const float3 dw = (0.5f * S.lawf[8]) * mat_mulf(a.I32 + 18 * g + 9, mat_tmulf(Rh, Nf));
+        const float3 dw = (0.5f * S.lawf[8]) * mat_mulf(a.Iinv32 + 9 * g, mat_tmulf(Rh, Nf));
         wb[0] = ff_addf(wb[0], dw.x); wb[1] = ff_addf(wb[1], dw.y); wb[2] = ff_addf(wb[2], dw.z);
         if (S.yorp) {   // rigid-rotation increment of the whole pile: increments in FP32
             const float3 dwy = f3(S.spin_f[0], S.spin_f[1], S.spin_f[2]);
@@ -1061,8 +1087,9 @@ __global__ void k_agg_end(Arrays a, Sizes z)
         if (!fin) atomicOr(&a.pd[p].flags, DEM_FLAG_NONFINITE);
     }
     if constexpr (FP64) {
-        double *o = a.out + 18 * g;
-        st3(o + 0, Fc); st3(o + 3, Nc); st3(o + 6, Fg); st3(o + 9, Ng); st3(o + 12, Fe); st3(o + 15, Ne);
+        st3(a.out[0] + 6 * g, Fc); st3(a.out[0] + 6 * g + 3, Nc);
+        st3(a.out[1] + 6 * g, Fg); st3(a.out[1] + 6 * g + 3, Ng);
+        st3(a.out[2] + 6 * g, Fe); st3(a.out[2] + 6 * g + 3, Ne);
         const double3 F = Fc + Fg + Fe, N = Nc + Ng + Ne;
         const double3 acc = a.invM[g] * F;
         const double q[4] = {a.q[4 * g], a.q[4 * g + 1], a.q[4 * g + 2], a.q[4 * g + 3]};
@@ -1089,8 +1116,13 @@ void launch_agg_end(const Arrays &a, const Sizes &z, bool fp64, cudaStream_t st)
 {
     if (z.A == 0) return;
     unsigned nb = (unsigned)((z.A + 127) / 128);
-    if (fp64) launch_pdl(k_agg_end<true>, nb, 128, 0, st, a, z);
-    else launch_pdl(k_agg_end<false>, nb, 128, 0, st, a, z);
+    if (fp64) {
+        if (z.grav) launch_pdl(k_agg_end<true, true>, nb, 128, 0, st, a, z);
+        else launch_pdl(k_agg_end<true, false>, nb, 128, 0, st, a, z);
+    } else {
+        if (z.grav) launch_pdl(k_agg_end<false, true>, nb, 128, 0, st, a, z);
+        else launch_pdl(k_agg_end<false, false>, nb, 128, 0, st, a, z);
+    }
 }
 
 }  // namespace dem

@@ -217,7 +217,8 @@ void build_fields(dem_world *w)
         add((void **)&a.hist32[1], C_ENT, 16, true);
         add((void **)&a.hist32_rm, C_ENT, 16, false);
         add((void **)&a.rec32, C_AGG, sizeof(AggRecMixed), false);
-        add((void **)&a.I32, C_AGG, 72, true);
+        add((void **)&a.I32, C_AGG, 36, true);
+        add((void **)&a.Iinv32, C_AGG, 36, true);
         add((void **)&a.gacc, C_SPH, 32, false);
     }
     add((void **)&a.agg_first, C_AGG, 4, true);
@@ -232,7 +233,7 @@ void build_fields(dem_world *w)
     add((void **)&a.wb, C_AGG, 24, true);
     add((void **)&a.acc, C_AGG, 24, true);
     add((void **)&a.torque, C_AGG, 24, true);
-    add((void **)&a.out, C_AGG, 144, true);
+    for (int k = 0; k < 3; ++k) add((void **)&a.out[k], C_AGG, 48, true);
     add((void **)&a.invM, C_AGG, 8, true);
     a.out_ff = d ? 0 : 1;
     add((void **)&a.aref, C_AGG, 32, true);
@@ -580,8 +581,11 @@ dem_status upload_tables(dem_world *w, const GravPlan &gp)
     w->Z.TL = tl0;
     w->Z.TG = tg0;
     w->Z.adapt = 0;
-    for (auto &q : w->piles)
+    w->Z.grav = 0;
+    for (auto &q : w->piles) {
         if (q.P.rot_tol > 0) w->Z.adapt = 1;
+        if (q.P.G != 0.0) w->Z.grav = 1;
+    }
     if (w->sm_count == 0) {
         int dev = 0;
         CU(cudaGetDevice(&dev));
@@ -1166,13 +1170,13 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     UP(D.I + 9 * a0, I.data(), 72 * A);
     UP(D.Iinv + 9 * a0, Iinv.data(), 72 * A);
     if (w->precision == DEM_MIXED) {
-        std::vector<float> I32(18 * (size_t)A);
-        for (int a = 0; a < A; ++a)
-            for (int e = 0; e < 9; ++e) {
-                I32[18 * a + e] = (float)I[9 * a + e];
-                I32[18 * a + 9 + e] = (float)Iinv[9 * a + e];
-            }
-        UP(D.I32 + 18 * a0, I32.data(), 72 * A);
+        std::vector<float> I32(9 * (size_t)A), Iinv32(9 * (size_t)A);
+        for (int64_t e = 0; e < 9 * (int64_t)A; ++e) {
+            I32[e] = (float)I[e];
+            Iinv32[e] = (float)Iinv[e];
+        }
+        UP(D.I32 + 9 * a0, I32.data(), 36 * A);
+        UP(D.Iinv32 + 9 * a0, Iinv32.data(), 36 * A);
     }
     UP(D.r + 3 * a0, packed(w, r.data(), 3 * A).data(), 24 * A);
     UP(D.v + 3 * a0, packed(w, v.data(), 3 * A).data(), 24 * A);
@@ -1180,7 +1184,7 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     UP(D.wb + 3 * a0, packed(w, wb.data(), 3 * A).data(), 24 * A);
     CU(cudaMemsetAsync(D.acc + 3 * a0, 0, 24 * A, st));
     CU(cudaMemsetAsync(D.torque + 3 * a0, 0, 24 * A, st));
-    CU(cudaMemsetAsync(D.out + 18 * a0, 0, 144 * A, st));
+    for (int k = 0; k < 3; ++k) CU(cudaMemsetAsync(D.out[k] + 6 * a0, 0, 48 * A, st));
     std::vector<float> aref(8 * (size_t)A, 0.0f);
     for (int a = 0; a < A; ++a) {
         double bm = 0;
@@ -1398,8 +1402,9 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
     case DEM_FIELD_FORCE_GRAV: case DEM_FIELD_TORQUE_GRAV:
     case DEM_FIELD_FORCE_EXT: case DEM_FIELD_TORQUE_EXT: {
         CHK(need(3 * A));
+        // the three parts (contact, gravity, planet), each [A][6]: F then N
         std::vector<double> o(18 * A);
-        CHK(get(o.data(), D.out + 18 * a0, 144 * A));
+        for (int k = 0; k < 3; ++k) CHK(get(o.data() + 6 * A * k, D.out[k] + 6 * a0, 48 * A));
         if (w->precision == DEM_MIXED) {   // float-float pairs
             std::vector<float> f(36 * A);
             std::memcpy(f.data(), o.data(), 144 * A);
@@ -1407,17 +1412,17 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
         }
         for (int64_t a = 0; a < A; ++a)
             for (int c = 0; c < 3; ++c) {
-                const double *x = &o[18 * a];
+                const double *xc = &o[6 * a], *xg = &o[6 * (A + a)], *xe = &o[6 * (2 * A + a)];
                 double val = 0;
                 switch (field) {
-                case DEM_FIELD_FORCE: val = x[c] + x[6 + c] + x[12 + c]; break;
-                case DEM_FIELD_TORQUE: val = x[3 + c] + x[9 + c] + x[15 + c]; break;
-                case DEM_FIELD_FORCE_CONTACT: val = x[c]; break;
-                case DEM_FIELD_TORQUE_CONTACT: val = x[3 + c]; break;
-                case DEM_FIELD_FORCE_GRAV: val = x[6 + c]; break;
-                case DEM_FIELD_TORQUE_GRAV: val = x[9 + c]; break;
-                case DEM_FIELD_FORCE_EXT: val = x[12 + c]; break;
-                default: val = x[15 + c]; break;
+                case DEM_FIELD_FORCE: val = xc[c] + xg[c] + xe[c]; break;
+                case DEM_FIELD_TORQUE: val = xc[3 + c] + xg[3 + c] + xe[3 + c]; break;
+                case DEM_FIELD_FORCE_CONTACT: val = xc[c]; break;
+                case DEM_FIELD_TORQUE_CONTACT: val = xc[3 + c]; break;
+                case DEM_FIELD_FORCE_GRAV: val = xg[c]; break;
+                case DEM_FIELD_TORQUE_GRAV: val = xg[3 + c]; break;
+                case DEM_FIELD_FORCE_EXT: val = xe[c]; break;
+                default: val = xe[3 + c]; break;
                 }
                 out[3 * a + c] = val;
             }
@@ -1431,21 +1436,20 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
             for (int64_t i = 0; i < N; ++i) { out[3 * i] = f[i].x; out[3 * i + 1] = f[i].y; out[3 * i + 2] = f[i].z; }
             break;
         }
-        std::vector<int32_t> pos(N);
-        CHK(get(pos.data(), D.pos_of_home[dyn.parity] + s0, 4 * N));
+        // (stored at home indices)
         const int sel = field == DEM_FIELD_SPHERE_FC ? 0 : 1;
         if (w->precision == DEM_FP64) {
             std::vector<dbl4> f(2 * N);
             CHK(get(f.data(), D.ftc64 + 2 * s0, 64 * N));
             for (int64_t i = 0; i < N; ++i) {
-                const dbl4 &e = f[2 * (int64_t)pos[i] + sel];
+                const dbl4 &e = f[2 * i + sel];
                 out[3 * i] = e.x; out[3 * i + 1] = e.y; out[3 * i + 2] = e.z;
             }
         } else {
             std::vector<float4> f(2 * N);
             CHK(get(f.data(), D.ftc32 + 2 * s0, 32 * N));
             for (int64_t i = 0; i < N; ++i) {
-                const float4 &e = f[2 * (int64_t)pos[i] + sel];
+                const float4 &e = f[2 * i + sel];
                 out[3 * i] = e.x; out[3 * i + 1] = e.y; out[3 * i + 2] = e.z;
             }
         }
