@@ -239,6 +239,20 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3, mode=
                 flush.zero_()
             ks.append(w.step_timed()[1])
         info = w.info(pid)
+        # the other kernels of the same steps, each between event nodes in the graph
+        others = {}
+        step_ms = []
+        for kname in ("AGG_BEGIN", "PILE_BEGIN", "KEYS", "GATHER", "AGG_END", "PILE_END"):
+            w.set_timed_kernel(kname)
+            km = []
+            for _ in range(steps):
+                with torch.cuda.stream(st):
+                    flush.zero_()
+                sm_, k_ = w.step_timed()
+                km.append(k_)
+                step_ms.append(sm_)
+            others[kname] = statistics.median(km) * 1e3
+        w.set_timed_kernel("CONTACT")
         cnt = w.read(pid, "CONTACTS")[:, 0]
         # rebuild steps: a state write (the same velocities) forces one
         vel = w.read(pid, "VEL")
@@ -274,6 +288,9 @@ def run_contact_roofline(dem, W, peak_gbs, steps=5, n=1_048_576, warmup=3, mode=
             "layout_bytes_per_launch": layout, "frac_on_layout_bytes": layout / (ms / 1e3) / 1e9 / peak_gbs,
             "layout_bytes": "this library's own layout: 104 B per sphere + 8 B per list entry + 32 B per "
                             "contact pair",
+            "other_kernels_us": others, "step_ms": statistics.median(step_ms),
+            "other_kernels": "CUDA events around each kernel inside the step graph, median over the steps "
+                             "(the rebuild-only kernels return at once in these steps)",
             "workload": "dense FCC tetrahedra lattice, %d spheres, overlaps 0.5%% R, gravity off" % N}
 
 
