@@ -698,7 +698,7 @@ def run_ours(args):
                         "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                         "traffic": traffic_for("kernels_gravity.cu", "k_gravity32s"),
                         "kernel": "k_gravity32s (softened direct-sum gravity, symmetric "
-                                  "tile pairs, packed f32x2; its integer sums become forces in k_agg_end)",
+                                  "tile pairs, packed f32x2) + k_grav_acc_to_force (its integer sums to forces)",
                         "kernel_ms": g_ms, "share_of_step": g_ms / statistics.mean(step_ms),
                         "flops_per_launch": flops,
                         "flop_count": "20 per ordered pair of spheres in different aggregates "

@@ -259,7 +259,7 @@ struct Sizes {
     int32_t icap;    // contact inbox entries used per tile range (<= the kernel's capacity)
     int32_t cmode;   // contact pass: 0 = one thread per sphere, 1 = tiles with a shared-memory inbox
     int32_t gacc_on; // mixed symmetric gravity: piles of more than one tile leave their sums in gacc,
-                     // which k_agg_end turns into forces
+                     // which k_grav_acc_to_force turns into forces
     int32_t grav;    // some pile has self-gravity (G > 0)
 };
 

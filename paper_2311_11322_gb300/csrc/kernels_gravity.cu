@@ -31,8 +31,8 @@
 // (a, a) take the one-sided form.  Mixed path: every item adds its FP32
 // i-sums and j-sums, scaled by a power of two and rounded once, to 64-bit
 // integer accumulators per sphere (atomic integer adds, which give the same
-// result in any order, so nothing depends on the schedule); k_agg_end turns
-// them into forces as it sums each aggregate.  FP64 path: every item writes
+// result in any order, so nothing depends on the schedule);
+// k_grav_acc_to_force turns them into forces.  FP64 path: every item writes
 // its i-sums (one per b) and j-sums (one per a) as FP64 partials, and
 // k_grav_combine_sym64 adds a sphere's partials in tile order.
 #include "dem_internal.h"
@@ -1002,6 +1002,28 @@ int gravity_blocks_per_sm(bool fp64, int block, int ib, bool pack, bool sym, int
     return ib == 1 ? occ<256, 1>(fp64, pack) : ib == 2 ? occ<256, 2>(fp64, pack) : occ<256, 4>(fp64, pack);
 }
 
+// Mixed symmetric form: turn the integer sums of piles with more than one
+// tile into F_i = G m_i sum 2^-k and clear the accumulators for the next step
+// (one thread per sphere: the accumulators are read once, coalesced, with
+// every sphere in flight; done inside the per-aggregate pass instead, one
+// thread walking an aggregate's members, it was 4x slower on 256 small piles).
+__global__ void k_grav_acc_to_force(Arrays a, Sizes z)
+{
+    pdl_enter();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= z.N) return;
+    int p = a.sph_pile[i];
+    if (a.enabled[p] == 0 || a.pd[p].failed) return;
+    if (a.gnchunk[p] <= 1) return;
+    const PileStatic &S = a.ps[p];
+    longlong2 *g = (longlong2 *)(a.gacc + 4 * i);
+    const longlong2 xy = g[0], zw = g[1];
+    g[0] = make_longlong2(0, 0);
+    g[1] = make_longlong2(0, 0);
+    const double gm = S.G * a.m64[i] * S.ginv;
+    a.fg[i] = make_dbl4(gm * (double)xy.x, gm * (double)xy.y, gm * (double)zw.x, 0.0);
+}
+
 void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int ib, bool pack,
                     bool sym, cudaStream_t st)
 {
@@ -1016,7 +1038,7 @@ void launch_gravity(const Arrays &a, const Sizes &z, bool fp64, int block, int i
             else if (z.gtile == 128) launch_pdl(k_gravity32s<1, 4>, (unsigned)nb, 32, 0, st, a, z);
             else if (z.gtile == 256) launch_pdl(k_gravity32s<2, 4>, (unsigned)nb, 64, 0, st, a, z);
             else launch_pdl(k_gravity32s<kBigWPB, kBigIB>, (unsigned)nb, 32 * kBigWPB, 0, st, a, z);
-            // the integer sums become forces in k_agg_end (z.gacc_on)
+            if (z.gacc_on) launch_pdl(k_grav_acc_to_force, (unsigned)((z.N + 255) / 256), 256, 0, st, a, z);
         }
         return;
     }

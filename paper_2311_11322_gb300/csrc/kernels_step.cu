@@ -983,24 +983,10 @@ __global__ void __launch_bounds__(128) k_agg_end(Arrays a, Sizes z)
                 s[9].add(ng.x); s[10].add(ng.y); s[11].add(ng.z);
             }
         };
-        // a pile without self-gravity has zero sphere gravity: not read.
-        // Mixed symmetric gravity leaves the sums of a pile of more than one
-        // tile in 64-bit integer accumulators: F_i = G m_i x sum x 2^-k here,
-        // stored for the read-out, and the accumulators cleared for the next step
+        // a pile without self-gravity has zero sphere gravity: not read
         const bool grav = GRAV && S.G != 0.0;
-        const bool gint = grav && z.gacc_on && a.gnchunk[p] > 1;
         const dbl4 g0 = make_dbl4(0.0, 0.0, 0.0, 0.0);
-        auto gravity_of = [&](int64_t i) -> dbl4 {
-            if (!gint) return grav ? a.fg[i] : g0;
-            longlong2 *gp = reinterpret_cast<longlong2 *>(a.gacc + 4 * i);
-            const longlong2 xy = gp[0], zw = gp[1];
-            gp[0] = make_longlong2(0, 0);
-            gp[1] = make_longlong2(0, 0);
-            const double gm = S.G * a.m64[i] * S.ginv;
-            const dbl4 f = make_dbl4(gm * (double)xy.x, gm * (double)xy.y, gm * (double)zw.x, 0.0);
-            a.fg[i] = f;
-            return f;
-        };
+        auto gravity_of = [&](int64_t i) -> dbl4 { return grav ? a.fg[i] : g0; };
         int t2 = 0;
         if (!planet) {   // the loads of two members issued together
             for (; t2 + 1 < n; t2 += 2) {
