@@ -7,9 +7,11 @@
 #include <cstdarg>
 #include <cstddef>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -91,6 +93,10 @@ struct dem_world {
     // flags readback
     PileDyn *h_dyn = nullptr;   // pinned
     int64_t h_dyn_cap = 0;
+    // host staging of dem_add_aggregates, kept between calls (pinned if possible)
+    char *h_stage = nullptr;
+    size_t h_stage_cap = 0;
+    bool h_stage_pinned = false;
     cudaEvent_t ev_flags = nullptr;
     bool pending = false;
     int64_t pending_n = 0;
@@ -988,9 +994,53 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     // large piles); the pile sums are added range by range in order, so the
     // result does not depend on the number of threads.
     const int A = (int)n_agg;
-    std::vector<int32_t> first(A), sph_agg(N);
-    std::vector<double> m(N), b(3 * N), M(A), I(9 * A), Iinv(9 * A);
-    std::vector<double> q(4 * A, 0.0), r(3 * A), v(3 * A, 0.0), wb(3 * A, 0.0);
+    // Host arrays of the set-up, carved from one staging buffer that the
+    // world keeps between calls (pinned when possible): no allocation, page
+    // faults or zero fill per call, and the uploads below run asynchronously
+    // from it.  Every array is fully written before it is read or uploaded.
+    int32_t *first, *sph_agg, *iota;
+    double *m, *b, *M, *I, *Iinv, *q, *r, *v, *wb, *rel, *pk_invM, *pk_r, *pk_v, *pk_q, *pk_wb;
+    float4 *bh, *bl;
+    float *I32, *Iinv32, *aref;
+    auto carve = [&](char *base) -> size_t {
+        size_t off = 0;
+        auto take = [&](auto *&ptr, int64_t n) {
+            off = (off + 255) & ~(size_t)255;
+            ptr = reinterpret_cast<std::remove_reference_t<decltype(ptr)>>(base + off);
+            off += (size_t)n * sizeof(*ptr);
+        };
+        take(first, A); take(sph_agg, N); take(iota, N);
+        take(m, N); take(b, 3 * N); take(M, A); take(I, 9 * A); take(Iinv, 9 * A);
+        take(q, 4 * A); take(r, 3 * A); take(v, 3 * A); take(wb, 3 * A); take(rel, 3 * N);
+        take(pk_invM, A); take(pk_r, 3 * A); take(pk_v, 3 * A); take(pk_q, 4 * A); take(pk_wb, 3 * A);
+        take(bh, N); take(bl, N); take(I32, 9 * A); take(Iinv32, 9 * A); take(aref, 8 * A);
+        return off;
+    };
+    {
+        const size_t need = carve(nullptr);
+        if (need > w->h_stage_cap) {
+            if (w->h_stage) {
+                if (w->h_stage_pinned) cudaFreeHost(w->h_stage);
+                else std::free(w->h_stage);
+            }
+            w->h_stage = nullptr;
+            w->h_stage_cap = 0;
+            const size_t cap = need + need / 4;
+            void *hp = nullptr;
+            // pinned up to 1 GiB; pageable above that or if pinning fails
+            if (cap <= ((size_t)1 << 30) && cudaMallocHost(&hp, cap) == cudaSuccess) {
+                w->h_stage_pinned = true;
+            } else {
+                cudaGetLastError();
+                hp = std::malloc(cap);
+                w->h_stage_pinned = false;
+            }
+            if (!hp) return fail(w, DEM_ERR_OOM, "host staging of %zu bytes failed", cap);
+            w->h_stage = (char *)hp;
+            w->h_stage_cap = cap;
+        }
+        carve(w->h_stage);
+    }
     {
         int64_t k = 0;
         for (int a = 0; a < A; ++a) { first[a] = (int32_t)k; k += spa[a]; }
@@ -1046,10 +1096,11 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
             }
             for (int d = 0; d < 3; ++d) {
                 r[3 * a + d] = c[d];
-                if (agg_vel) v[3 * a + d] = agg_vel[3 * a + d];
-                if (agg_omega) wb[3 * a + d] = agg_omega[3 * a + d];
+                v[3 * a + d] = agg_vel ? agg_vel[3 * a + d] : 0.0;
+                wb[3 * a + d] = agg_omega ? agg_omega[3 * a + d] : 0.0;
             }
             q[4 * a] = 1.0;
+            q[4 * a + 1] = q[4 * a + 2] = q[4 * a + 3] = 0.0;
             P.Mtot += Ma;
             for (int d = 0; d < 3; ++d) { P.Rp[d] += Ma * c[d]; P.Vp[d] += Ma * v[3 * a + d]; }
         }
@@ -1089,12 +1140,11 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     ph.P = *p;
     ph.M_total = Mtot;
     {
-        std::vector<double> rel(3 * N);
         for (int64_t i = 0; i < N; ++i)
             for (int d = 0; d < 3; ++d) rel[3 * i + d] = pos[3 * i + d] - Rp[d];
         if (p->cell_size > 0 && p->cell_size < 2.0 * smax)
             return fail(w, DEM_ERR_ARG, "cell_size must be >= 2 x the largest radius");
-        choose_grid(w, ph, rel.data(), N);
+        choose_grid(w, ph, rel, N);
     }
     size_lists(w, ph);
 
@@ -1131,69 +1181,73 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
         dem_status s_ = up((dst), (src), (bytes));  \
         if (s_ != DEM_OK) return s_;                \
     } while (0)
-    UP(D.sph_agg + s0, sph_agg.data(), 4 * N);
-    UP(D.b64 + 3 * s0, b.data(), 24 * N);
+    UP(D.sph_agg + s0, sph_agg, 4 * N);
+    UP(D.b64 + 3 * s0, b, 24 * N);
     UP(D.s64 + s0, rad, 8 * N);
-    UP(D.m64 + s0, m.data(), 8 * N);
+    UP(D.m64 + s0, m, 8 * N);
     // no previous candidate lists: nothing to carry over at the first rebuild
     CU(cudaMemsetAsync(D.ccnt[0] + s0, 0, 4 * N, st));
     CU(cudaMemsetAsync(D.ccnt[1] + s0, 0, 4 * N, st));
     CU(cudaMemsetAsync(D.coff[0] + s0, 0, 4 * N, st));
     CU(cudaMemsetAsync(D.coff[1] + s0, 0, 4 * N, st));
-    std::vector<int32_t> iota(N);
     for (int64_t i = 0; i < N; ++i) iota[i] = (int32_t)i;
-    UP(D.pos_of_home[0] + s0, iota.data(), 4 * N);
-    UP(D.pos_of_home[1] + s0, iota.data(), 4 * N);
+    UP(D.pos_of_home[0] + s0, iota, 4 * N);
+    UP(D.pos_of_home[1] + s0, iota, 4 * N);
     CU(cudaMemsetAsync(D.fg + s0, 0, 32 * N, st));
     if (w->precision == DEM_MIXED) {
-        std::vector<float4> bh(N), bl(N);
         for (int64_t i = 0; i < N; ++i) {
             split(b[3 * i], bh[i].x, bl[i].x);
             split(b[3 * i + 1], bh[i].y, bl[i].y);
             split(b[3 * i + 2], bh[i].z, bl[i].z);
             split(rad[i], bh[i].w, bl[i].w);
         }
-        UP(D.bh + s0, bh.data(), 16 * N);
-        UP(D.bl + s0, bl.data(), 16 * N);
+        UP(D.bh + s0, bh, 16 * N);
+        UP(D.bl + s0, bl, 16 * N);
         CU(cudaMemsetAsync(D.ftc32 + 2 * s0, 0, 32 * N, st));
     } else {
         CU(cudaMemsetAsync(D.ftc64 + 2 * s0, 0, 64 * N, st));
     }
-    UP(D.agg_first + a0, first.data(), 4 * A);
+    UP(D.agg_first + a0, first, 4 * A);
     UP(D.agg_count + a0, spa, 4 * A);
-    UP(D.M + a0, M.data(), 8 * A);
-    {
-        std::vector<double> invM(A);
-        for (int64_t g = 0; g < A; ++g) invM[g] = 1.0 / M[g];
-        UP(D.invM + a0, packed(w, invM.data(), A).data(), 8 * A);
-    }
-    UP(D.I + 9 * a0, I.data(), 72 * A);
-    UP(D.Iinv + 9 * a0, Iinv.data(), 72 * A);
+    UP(D.M + a0, M, 8 * A);
+    // the state in the world's slot format (float-float pairs in the mixed path)
+    const bool ffs = w->precision == DEM_MIXED;
+    auto slot_fmt = [&](double *dst, const double *src, int64_t n) {
+        for (int64_t k = 0; k < n; ++k) dst[k] = ffs ? pack_ff(src[k]) : src[k];
+    };
+    for (int64_t g = 0; g < A; ++g) pk_invM[g] = 1.0 / M[g];
+    slot_fmt(pk_invM, pk_invM, A);
+    UP(D.invM + a0, pk_invM, 8 * A);
+    UP(D.I + 9 * a0, I, 72 * A);
+    UP(D.Iinv + 9 * a0, Iinv, 72 * A);
     if (w->precision == DEM_MIXED) {
-        std::vector<float> I32(9 * (size_t)A), Iinv32(9 * (size_t)A);
         for (int64_t e = 0; e < 9 * (int64_t)A; ++e) {
             I32[e] = (float)I[e];
             Iinv32[e] = (float)Iinv[e];
         }
-        UP(D.I32 + 9 * a0, I32.data(), 36 * A);
-        UP(D.Iinv32 + 9 * a0, Iinv32.data(), 36 * A);
+        UP(D.I32 + 9 * a0, I32, 36 * A);
+        UP(D.Iinv32 + 9 * a0, Iinv32, 36 * A);
     }
-    UP(D.r + 3 * a0, packed(w, r.data(), 3 * A).data(), 24 * A);
-    UP(D.v + 3 * a0, packed(w, v.data(), 3 * A).data(), 24 * A);
-    UP(D.q + 4 * a0, packed(w, q.data(), 4 * A).data(), 32 * A);
-    UP(D.wb + 3 * a0, packed(w, wb.data(), 3 * A).data(), 24 * A);
+    slot_fmt(pk_r, r, 3 * A);
+    slot_fmt(pk_v, v, 3 * A);
+    slot_fmt(pk_q, q, 4 * A);
+    slot_fmt(pk_wb, wb, 3 * A);
+    UP(D.r + 3 * a0, pk_r, 24 * A);
+    UP(D.v + 3 * a0, pk_v, 24 * A);
+    UP(D.q + 4 * a0, pk_q, 32 * A);
+    UP(D.wb + 3 * a0, pk_wb, 24 * A);
     CU(cudaMemsetAsync(D.acc + 3 * a0, 0, 24 * A, st));
     CU(cudaMemsetAsync(D.torque + 3 * a0, 0, 24 * A, st));
     for (int k = 0; k < 3; ++k) CU(cudaMemsetAsync(D.out[k] + 6 * a0, 0, 48 * A, st));
-    std::vector<float> aref(8 * (size_t)A, 0.0f);
     for (int a = 0; a < A; ++a) {
+        for (int c = 0; c < 7; ++c) aref[8 * a + c] = 0.0f;
         double bm = 0;
         for (int64_t i = first[a]; i < first[a] + spa[a]; ++i)
             bm = std::max(bm, std::sqrt(b[3 * i] * b[3 * i] + b[3 * i + 1] * b[3 * i + 1] +
                                         b[3 * i + 2] * b[3 * i + 2]));
         aref[8 * a + 7] = (float)bm * (1.0f + 1e-6f);
     }
-    UP(D.aref + 8 * a0, aref.data(), 32 * A);
+    UP(D.aref + 8 * a0, aref, 32 * A);
     PileDyn dyn{};
     dyn.rebuild = 1;
     dyn.rebuilt_prev = 1;
@@ -1211,7 +1265,7 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     wat.fired = -1;
     UP(D.watch + slot, &wat, sizeof wat);
 #undef UP
-    CU(cudaStreamSynchronize(st));   // host staging vectors go out of scope
+    CU(cudaStreamSynchronize(st));   // the staging buffer is free for the next call
     *out_pile_id = ph.id;
     return DEM_OK;
 }
@@ -1345,8 +1399,10 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
     };
     dem_status s;
 #define CHK(x) do { s = (x); if (s != DEM_OK) return s; } while (0)
-    PileDyn dyn;
-    CHK(get(&dyn, D.pd + slot, sizeof dyn));
+    PileDyn dyn{};   // the pile's device record: read only for the fields that use it
+    if (field == DEM_FIELD_FRAME || field == DEM_FIELD_CONTACTS || field == DEM_FIELD_PLANET ||
+        field == DEM_FIELD_INFO)
+        CHK(get(&dyn, D.pd + slot, sizeof dyn));
     switch (field) {
     case DEM_FIELD_COM: CHK(need(3 * A)); CHK(get(out, D.r + 3 * a0, 24 * A)); unpack_all(w, out, 3 * A); break;
     case DEM_FIELD_VEL: CHK(need(3 * A)); CHK(get(out, D.v + 3 * a0, 24 * A)); unpack_all(w, out, 3 * A); break;
@@ -2056,6 +2112,10 @@ void dem_destroy(dem_world *w)
     if (w->exec) cudaGraphExecDestroy(w->exec);
     dev_free(w, w->slab);
     if (w->h_dyn) cudaFreeHost(w->h_dyn);
+    if (w->h_stage) {
+        if (w->h_stage_pinned) cudaFreeHost(w->h_stage);
+        else std::free(w->h_stage);
+    }
     if (w->ev_flags) cudaEventDestroy(w->ev_flags);
     for (int k = 0; k < 2; ++k) {
         if (w->kev[k]) cudaEventDestroy(w->kev[k]);

@@ -272,19 +272,26 @@ class World:
         return ms
 
     # ---- readout
-    def read(self, pile, field):
+    def read(self, pile, field, out=None):
+        """One field of a pile as float64; `out` (optional): a C-contiguous
+        float64 array of the field's shape to fill instead of a new one (for
+        repeated reads, e.g. into pinned host memory)."""
         fid, rows, cols = FIELDS[field]
         if pile not in self.piles:   # let the library report the unknown id
             buf = np.zeros(16)
             self._check(self._L.dem_read_state(self.w, int(pile), fid, _ptr(buf), buf.size))
         A, N, K = self.piles[pile]
         if field == "CONTACTS":
-            out = np.zeros((N, 1 + 4 * K))
+            shape = (N, 1 + 4 * K)
         elif isinstance(rows, int):
-            out = np.zeros(rows)
+            shape = (rows,)
         else:
             n = A if rows == "A" else N
-            out = np.zeros((n, cols)) if cols > 1 else np.zeros(n)
+            shape = (n, cols) if cols > 1 else (n,)
+        if out is None:
+            out = np.zeros(shape)
+        elif out.shape != shape or out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError(f"out must be a C-contiguous float64 array of shape {shape}")
         self._check(self._L.dem_read_state(self.w, pile, fid, _ptr(out), out.size))
         return out
 
