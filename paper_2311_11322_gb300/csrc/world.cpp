@@ -883,14 +883,15 @@ void set_grid(const dem_world *w, PileHost &q, const double *ext, int pad)
 // every pile's next step; the history is carried over by partner index).
 dem_status regrid(dem_world *w);
 
-void choose_grid(const dem_world *w, PileHost &q, const double *pos_rel, int64_t N)
+// lo, hi: the box of the sphere centres relative to the pile's COM (the grid
+// spans it and the origin).
+void choose_grid(const dem_world *w, PileHost &q, const double (&lo_rel)[3], const double (&hi_rel)[3])
 {
-    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-    for (int64_t i = 0; i < N; ++i)
-        for (int c = 0; c < 3; ++c) {
-            lo[c] = std::min(lo[c], pos_rel[3 * i + c]);
-            hi[c] = std::max(hi[c], pos_rel[3 * i + c]);
-        }
+    double lo[3], hi[3];
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = std::min(0.0, lo_rel[c]);
+        hi[c] = std::max(0.0, hi_rel[c]);
+    }
     double ext[3];
     for (int c = 0; c < 3; ++c) ext[c] = hi[c] - lo[c] + 2.0 * q.smax;
     set_grid(w, q, ext, 2);
@@ -983,23 +984,20 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
         N += spa[a];
     }
     if (N > ((int64_t)1 << 30)) return fail(w, DEM_ERR_ARG, "too many spheres");
-    if (!finite_all(pos, 3 * N) || !finite_all(rad, N) || !finite_all(dens, N) ||
-        (agg_vel && !finite_all(agg_vel, 3 * n_agg)) || (agg_omega && !finite_all(agg_omega, 3 * n_agg)))
-        return fail(w, DEM_ERR_ARG, "non-finite input");
-    for (int64_t i = 0; i < N; ++i)
-        if (!(rad[i] > 0) || !(dens[i] > 0)) return fail(w, DEM_ERR_ARG, "radius and density must be > 0");
 
     // ---- host set-up in FP64 (Sec. 2.2.1) ----
     // Aggregates are set up in 16 fixed ranges (on up to 16 host threads for
-    // large piles); the pile sums are added range by range in order, so the
-    // result does not depend on the number of threads.
+    // large piles), each range also checking its inputs, putting its part of
+    // the state into the world's formats and boxing its sphere centres; the
+    // pile sums are added range by range in order, so the result does not
+    // depend on the number of threads.
     const int A = (int)n_agg;
     // Host arrays of the set-up, carved from one staging buffer that the
     // world keeps between calls (pinned when possible): no allocation, page
     // faults or zero fill per call, and the uploads below run asynchronously
     // from it.  Every array is fully written before it is read or uploaded.
     int32_t *first, *sph_agg, *iota;
-    double *m, *b, *M, *I, *Iinv, *q, *r, *v, *wb, *rel, *pk_invM, *pk_r, *pk_v, *pk_q, *pk_wb;
+    double *m, *b, *M, *I, *Iinv, *q, *r, *v, *wb, *pk_invM, *pk_r, *pk_v, *pk_q, *pk_wb;
     float4 *bh, *bl;
     float *I32, *Iinv32, *aref;
     auto carve = [&](char *base) -> size_t {
@@ -1011,7 +1009,7 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
         };
         take(first, A); take(sph_agg, N); take(iota, N);
         take(m, N); take(b, 3 * N); take(M, A); take(I, 9 * A); take(Iinv, 9 * A);
-        take(q, 4 * A); take(r, 3 * A); take(v, 3 * A); take(wb, 3 * A); take(rel, 3 * N);
+        take(q, 4 * A); take(r, 3 * A); take(v, 3 * A); take(wb, 3 * A);
         take(pk_invM, A); take(pk_r, 3 * A); take(pk_v, 3 * A); take(pk_q, 4 * A); take(pk_wb, 3 * A);
         take(bh, N); take(bl, N); take(I32, 9 * A); take(Iinv32, 9 * A); take(aref, 8 * A);
         return off;
@@ -1047,13 +1045,36 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     }
     struct Part {
         double smax = 0, smin = HUGE_VAL, Mtot = 0, Rp[3] = {0, 0, 0}, Vp[3] = {0, 0, 0};
+        double lo[3] = {HUGE_VAL, HUGE_VAL, HUGE_VAL}, hi[3] = {-HUGE_VAL, -HUGE_VAL, -HUGE_VAL};
+        bool nonfinite = false, nonpositive = false;
         int bad = -1;   // first aggregate of the range with a singular inertia tensor
     };
+    const bool mixed = p->precision == DEM_MIXED;
     constexpr int kRanges = 16;
     Part part[kRanges];
     auto setup_range = [&](int rg) {
         Part &P = part[rg];
         const int a_lo = (int)((int64_t)A * rg / kRanges), a_hi = (int)((int64_t)A * (rg + 1) / kRanges);
+        {
+            // inputs of the range: finite, radius and density > 0; box of the centres
+            const int64_t i_lo = first[a_lo], i_hi = a_hi < A ? (int64_t)first[a_hi] : N;
+            for (int64_t i = i_lo; i < i_hi; ++i) {
+                for (int c = 0; c < 3; ++c) {
+                    const double x = pos[3 * i + c];
+                    if (!std::isfinite(x)) P.nonfinite = true;
+                    P.lo[c] = std::min(P.lo[c], x);
+                    P.hi[c] = std::max(P.hi[c], x);
+                }
+                if (!std::isfinite(rad[i]) || !std::isfinite(dens[i])) P.nonfinite = true;
+                else if (!(rad[i] > 0) || !(dens[i] > 0)) P.nonpositive = true;
+            }
+            for (int a = a_lo; a < a_hi; ++a)
+                for (int c = 0; c < 3; ++c)
+                    if ((agg_vel && !std::isfinite(agg_vel[3 * a + c])) ||
+                        (agg_omega && !std::isfinite(agg_omega[3 * a + c])))
+                        P.nonfinite = true;
+            if (P.nonfinite || P.nonpositive) return;
+        }
         for (int a = a_lo; a < a_hi; ++a) {
             int64_t k = first[a];
             // mass-weighted mean about the first member: a one-sphere aggregate
@@ -1103,24 +1124,67 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
             q[4 * a + 1] = q[4 * a + 2] = q[4 * a + 3] = 0.0;
             P.Mtot += Ma;
             for (int d = 0; d < 3; ++d) { P.Rp[d] += Ma * c[d]; P.Vp[d] += Ma * v[3 * a + d]; }
+            // the device formats of this aggregate: state slots (float-float
+            // pairs in the mixed path), FP32 inertia copies, the list
+            // reference, and its members' float-float offsets
+            auto slot = [&](double x) { return mixed ? pack_ff(x) : x; };
+            pk_invM[a] = slot(1.0 / Ma);
+            for (int d = 0; d < 3; ++d) {
+                pk_r[3 * a + d] = slot(r[3 * a + d]);
+                pk_v[3 * a + d] = slot(v[3 * a + d]);
+                pk_wb[3 * a + d] = slot(wb[3 * a + d]);
+            }
+            for (int d = 0; d < 4; ++d) pk_q[4 * a + d] = slot(q[4 * a + d]);
+            for (int e = 0; e < 9; ++e) {
+                I32[9 * a + e] = (float)I[9 * a + e];
+                Iinv32[9 * a + e] = (float)Iinv[9 * a + e];
+            }
+            double bm = 0;
+            for (int64_t i = first[a]; i < first[a] + spa[a]; ++i) {
+                iota[i] = (int32_t)i;
+                bm = std::max(bm, std::sqrt(b[3 * i] * b[3 * i] + b[3 * i + 1] * b[3 * i + 1] +
+                                            b[3 * i + 2] * b[3 * i + 2]));
+                if (mixed) {
+                    split(b[3 * i], bh[i].x, bl[i].x);
+                    split(b[3 * i + 1], bh[i].y, bl[i].y);
+                    split(b[3 * i + 2], bh[i].z, bl[i].z);
+                    split(rad[i], bh[i].w, bl[i].w);
+                }
+            }
+            for (int e = 0; e < 7; ++e) aref[8 * a + e] = 0.0f;
+            aref[8 * a + 7] = (float)bm * (1.0f + 1e-6f);
         }
     };
     {
         // ranges a thread could not be started for run here (no exception leaves the ABI)
+        // threads: one per ~4,096 aggregates, at most one per range and per
+        // host core; thread t takes ranges t, t + nt, ...
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int nt = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)kRanges, (int64_t)hw, A / 4096}));
+        auto run = [&](int t) {
+            for (int rg = t; rg < kRanges; rg += nt) setup_range(rg);
+        };
         std::vector<std::thread> pool;
-        int rg = 1;
-        if (A >= 8192) {
-            try {
-                for (; rg < kRanges; ++rg) pool.emplace_back(setup_range, rg);
-            } catch (...) {
-            }
+        int started = 1;
+        try {
+            for (; started < nt; ++started) pool.emplace_back(run, started);
+        } catch (...) {
         }
-        setup_range(0);
-        for (int r2 = (A >= 8192 ? rg : 1); r2 < kRanges; ++r2) setup_range(r2);
+        run(0);
+        for (int t = started; t < nt; ++t) run(t);
         for (auto &t : pool) t.join();
     }
+    for (int rg = 0; rg < kRanges; ++rg)
+        if (part[rg].nonfinite) return fail(w, DEM_ERR_ARG, "non-finite input");
+    for (int rg = 0; rg < kRanges; ++rg)
+        if (part[rg].nonpositive) return fail(w, DEM_ERR_ARG, "radius and density must be > 0");
     double smax = 0, smin = HUGE_VAL, Mtot = 0, Rp[3] = {0, 0, 0}, Vp[3] = {0, 0, 0};
+    double lo[3] = {HUGE_VAL, HUGE_VAL, HUGE_VAL}, hi[3] = {-HUGE_VAL, -HUGE_VAL, -HUGE_VAL};
     for (int rg = 0; rg < kRanges; ++rg) {
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = std::min(lo[c], part[rg].lo[c]);
+            hi[c] = std::max(hi[c], part[rg].hi[c]);
+        }
         if (part[rg].bad >= 0)
             return fail(w, DEM_ERR_ARG, "aggregate %d has a singular inertia tensor", part[rg].bad);
         smax = std::max(smax, part[rg].smax);
@@ -1140,11 +1204,13 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     ph.P = *p;
     ph.M_total = Mtot;
     {
-        for (int64_t i = 0; i < N; ++i)
-            for (int d = 0; d < 3; ++d) rel[3 * i + d] = pos[3 * i + d] - Rp[d];
+        // the box relative to the COM (subtracting a constant keeps the order:
+        // the same as the box of the differences)
         if (p->cell_size > 0 && p->cell_size < 2.0 * smax)
             return fail(w, DEM_ERR_ARG, "cell_size must be >= 2 x the largest radius");
-        choose_grid(w, ph, rel, N);
+        double lo_rel[3], hi_rel[3];
+        for (int c = 0; c < 3; ++c) { lo_rel[c] = lo[c] - Rp[c]; hi_rel[c] = hi[c] - Rp[c]; }
+        choose_grid(w, ph, lo_rel, hi_rel);
     }
     size_lists(w, ph);
 
@@ -1190,17 +1256,10 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     CU(cudaMemsetAsync(D.ccnt[1] + s0, 0, 4 * N, st));
     CU(cudaMemsetAsync(D.coff[0] + s0, 0, 4 * N, st));
     CU(cudaMemsetAsync(D.coff[1] + s0, 0, 4 * N, st));
-    for (int64_t i = 0; i < N; ++i) iota[i] = (int32_t)i;
     UP(D.pos_of_home[0] + s0, iota, 4 * N);
     UP(D.pos_of_home[1] + s0, iota, 4 * N);
     CU(cudaMemsetAsync(D.fg + s0, 0, 32 * N, st));
     if (w->precision == DEM_MIXED) {
-        for (int64_t i = 0; i < N; ++i) {
-            split(b[3 * i], bh[i].x, bl[i].x);
-            split(b[3 * i + 1], bh[i].y, bl[i].y);
-            split(b[3 * i + 2], bh[i].z, bl[i].z);
-            split(rad[i], bh[i].w, bl[i].w);
-        }
         UP(D.bh + s0, bh, 16 * N);
         UP(D.bl + s0, bl, 16 * N);
         CU(cudaMemsetAsync(D.ftc32 + 2 * s0, 0, 32 * N, st));
@@ -1210,28 +1269,13 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     UP(D.agg_first + a0, first, 4 * A);
     UP(D.agg_count + a0, spa, 4 * A);
     UP(D.M + a0, M, 8 * A);
-    // the state in the world's slot format (float-float pairs in the mixed path)
-    const bool ffs = w->precision == DEM_MIXED;
-    auto slot_fmt = [&](double *dst, const double *src, int64_t n) {
-        for (int64_t k = 0; k < n; ++k) dst[k] = ffs ? pack_ff(src[k]) : src[k];
-    };
-    for (int64_t g = 0; g < A; ++g) pk_invM[g] = 1.0 / M[g];
-    slot_fmt(pk_invM, pk_invM, A);
     UP(D.invM + a0, pk_invM, 8 * A);
     UP(D.I + 9 * a0, I, 72 * A);
     UP(D.Iinv + 9 * a0, Iinv, 72 * A);
     if (w->precision == DEM_MIXED) {
-        for (int64_t e = 0; e < 9 * (int64_t)A; ++e) {
-            I32[e] = (float)I[e];
-            Iinv32[e] = (float)Iinv[e];
-        }
         UP(D.I32 + 9 * a0, I32, 36 * A);
         UP(D.Iinv32 + 9 * a0, Iinv32, 36 * A);
     }
-    slot_fmt(pk_r, r, 3 * A);
-    slot_fmt(pk_v, v, 3 * A);
-    slot_fmt(pk_q, q, 4 * A);
-    slot_fmt(pk_wb, wb, 3 * A);
     UP(D.r + 3 * a0, pk_r, 24 * A);
     UP(D.v + 3 * a0, pk_v, 24 * A);
     UP(D.q + 4 * a0, pk_q, 32 * A);
@@ -1239,14 +1283,6 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
     CU(cudaMemsetAsync(D.acc + 3 * a0, 0, 24 * A, st));
     CU(cudaMemsetAsync(D.torque + 3 * a0, 0, 24 * A, st));
     for (int k = 0; k < 3; ++k) CU(cudaMemsetAsync(D.out[k] + 6 * a0, 0, 48 * A, st));
-    for (int a = 0; a < A; ++a) {
-        for (int c = 0; c < 7; ++c) aref[8 * a + c] = 0.0f;
-        double bm = 0;
-        for (int64_t i = first[a]; i < first[a] + spa[a]; ++i)
-            bm = std::max(bm, std::sqrt(b[3 * i] * b[3 * i] + b[3 * i + 1] * b[3 * i + 1] +
-                                        b[3 * i + 2] * b[3 * i + 2]));
-        aref[8 * a + 7] = (float)bm * (1.0f + 1e-6f);
-    }
     UP(D.aref + 8 * a0, aref, 32 * A);
     PileDyn dyn{};
     dyn.rebuild = 1;

@@ -301,7 +301,18 @@ def test_invalid_inputs_rejected(dem):
         bad.pos[3, 1] = np.nan
         with pytest.raises(dem.DemError) as ei:
             w.add_pile(bad, p)
-        assert ei.value.status == dem.DEM_ERR_ARG
+        assert ei.value.status == dem.DEM_ERR_ARG and "non-finite" in str(ei.value)
+        # a non-positive radius in the last aggregate, and a NaN velocity
+        neg = W.PileIC(ic.counts, ic.pos, ic.radius.copy(), ic.density)
+        neg.radius[-1] = -1.0
+        with pytest.raises(dem.DemError) as ei:
+            w.add_pile(neg, p)
+        assert ei.value.status == dem.DEM_ERR_ARG and "radius" in str(ei.value)
+        vel = np.zeros((len(ic.counts), 3))
+        vel[-1, 2] = np.inf
+        with pytest.raises(dem.DemError) as ei:
+            w.add_pile(W.PileIC(ic.counts, ic.pos, ic.radius, ic.density, vel), p)
+        assert ei.value.status == dem.DEM_ERR_ARG and "non-finite" in str(ei.value)
         with pytest.raises(dem.DemError):
             w.add_pile(ic, p.replace(dt=0.0))
         with pytest.raises(dem.DemError):
