@@ -1004,7 +1004,7 @@ dem_status dem_add_aggregates(dem_world *w, const dem_params *p, int64_t n_agg,
         size_t off = 0;
         auto take = [&](auto *&ptr, int64_t n) {
             off = (off + 255) & ~(size_t)255;
-            ptr = reinterpret_cast<std::remove_reference_t<decltype(ptr)>>(base + off);
+            ptr = reinterpret_cast<std::remove_reference_t<decltype(ptr)>>(reinterpret_cast<uintptr_t>(base) + off);
             off += (size_t)n * sizeof(*ptr);
         };
         take(first, A); take(sph_agg, N); take(iota, N);
