@@ -814,13 +814,17 @@ __device__ __forceinline__ void sphere_contacts(const Arrays &a, const PileStati
     }
     // stored at the sphere's home index (its aggregate's members are then
     // contiguous for k_agg_end); the gathered spin record carries that index
+    // (checked against the pile's range: the check never fails)
     if constexpr (FP64) {
-        const int64_t kh = s0 + (int64_t)mw.w;
-        a.ftc64[2 * kh] = make_dbl4(F.x, F.y, F.z, 0.0);
-        a.ftc64[2 * kh + 1] = make_dbl4(Tq.x, Tq.y, Tq.z, 0.0);
+        const int hl = (int)mw.w;
+        if ((unsigned)hl < (unsigned)S.ns) {
+            a.ftc64[2 * (s0 + hl)] = make_dbl4(F.x, F.y, F.z, 0.0);
+            a.ftc64[2 * (s0 + hl) + 1] = make_dbl4(Tq.x, Tq.y, Tq.z, 0.0);
+        }
     } else {
-        const int64_t kh = s0 + __float_as_int(mw.w);
-        st_f4x2(a.ftc32 + 2 * kh, make_float4(F.x, F.y, F.z, 0.f), make_float4(Tq.x, Tq.y, Tq.z, 0.f));
+        const int hl = __float_as_int(mw.w);
+        if ((unsigned)hl < (unsigned)S.ns)
+            st_f4x2(a.ftc32 + 2 * (s0 + hl), make_float4(F.x, F.y, F.z, 0.f), make_float4(Tq.x, Tq.y, Tq.z, 0.f));
     }
     if (nc > S.K) flags |= DEM_FLAG_SLOTS;
 }
@@ -1066,15 +1070,20 @@ __global__ void __launch_bounds__(kCTile, FP64 ? 2 : 4) k_contact(Arrays a, Size
                 Tq.z = addr(Tq.z, inbox[5 * SM::kCap + slot]);
                 ++nc;
             }
-            // at the sphere's home index (from the staged spin record)
+            // at the sphere's home index (from the staged spin record; checked
+            // against the pile's range, which it never leaves)
             if constexpr (FP64) {
-                const int64_t kh = s0 + (int64_t)((const dbl4 *)stage)[2 * kCTile + tid].w;
-                a.ftc64[2 * kh] = make_dbl4(F.x, F.y, F.z, 0.0);
-                a.ftc64[2 * kh + 1] = make_dbl4(Tq.x, Tq.y, Tq.z, 0.0);
+                const int hl = (int)((const dbl4 *)stage)[2 * kCTile + tid].w;
+                if ((unsigned)hl < (unsigned)S.ns) {
+                    a.ftc64[2 * (s0 + hl)] = make_dbl4(F.x, F.y, F.z, 0.0);
+                    a.ftc64[2 * (s0 + hl) + 1] = make_dbl4(Tq.x, Tq.y, Tq.z, 0.0);
+                }
             } else {
                 const float4 *sv = (const float4 *)((const int4 *)stage + kCTile);
-                const int64_t kh = s0 + __float_as_int(sv[kCTile + tid].w);
-                st_f4x2(a.ftc32 + 2 * kh, make_float4(F.x, F.y, F.z, 0.f), make_float4(Tq.x, Tq.y, Tq.z, 0.f));
+                const int hl = __float_as_int(sv[kCTile + tid].w);
+                if ((unsigned)hl < (unsigned)S.ns)
+                    st_f4x2(a.ftc32 + 2 * (s0 + hl), make_float4(F.x, F.y, F.z, 0.f),
+                            make_float4(Tq.x, Tq.y, Tq.z, 0.f));
             }
             if (nc > K) myflags |= DEM_FLAG_SLOTS;
         }
