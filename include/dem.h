@@ -224,6 +224,30 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
                           int64_t n_out);
 
 /*
+ * Asynchronous read of one per-aggregate state field (DEM_FIELD_COM, VEL,
+ * QUAT, OMEGA_BODY, ACC, TORQUE_STORED or MASS; layouts as dem_read_state):
+ * enqueues the copy to host_out on the world's stream and returns without
+ * waiting, so that the host can issue the next dem_step and work on an
+ * earlier result while the device steps.  The copy sees the state after the
+ * steps issued before the call.  host_out (n_out doubles, owned by the
+ * caller; pinned memory lets the copy run asynchronously) must stay valid
+ * and untouched until dem_read_wait returns, and holds the world's internal
+ * slot format until then.  At most DEM_MAX_ASYNC_READS reads may be pending.
+ * Errors: DEM_ERR_ARG (unknown pile, a field other than those above, NULL or
+ * too small host_out, too many pending reads), DEM_ERR_CUDA.
+ */
+#define DEM_MAX_ASYNC_READS 8
+dem_status dem_read_state_async(dem_world *w, int32_t pile_id, int32_t field, double *host_out,
+                                int64_t n_out);
+
+/*
+ * Wait for every pending dem_read_state_async copy (and only for those: steps
+ * issued after them keep running) and convert the values to FP64 in place.
+ * Errors: DEM_ERR_CUDA.
+ */
+dem_status dem_read_wait(dem_world *w);
+
+/*
  * Overwrite one field of a pile from host memory (checkpoint restore, or
  * re-synchronising with another integrator).  Writable fields, same layouts
  * as dem_read_state: COM, VEL, QUAT (renormalised is the caller's duty),

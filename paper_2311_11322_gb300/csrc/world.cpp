@@ -98,6 +98,10 @@ struct dem_world {
     size_t h_stage_cap = 0;
     bool h_stage_pinned = false;
     cudaEvent_t ev_flags = nullptr;
+    // asynchronous reads: destination, doubles, whether they are float-float slots, event after the copy
+    struct AsyncRead { double *out; int64_t n; bool ff; };
+    std::vector<AsyncRead> reads;
+    cudaEvent_t rev[DEM_MAX_ASYNC_READS] = {};
     bool pending = false;
     int64_t pending_n = 0;
     bool own_stream = false;
@@ -1621,6 +1625,60 @@ dem_status dem_read_state(dem_world *w, int32_t pile_id, int32_t field, double *
     return DEM_OK;
 }
 
+dem_status dem_read_state_async(dem_world *w, int32_t pile_id, int32_t field, double *out, int64_t n_out)
+{
+    Range range("dem_read_state_async");
+    if (!w) return DEM_ERR_ARG;
+    int slot = find_pile(w, pile_id);
+    if (slot < 0) return fail(w, DEM_ERR_ARG, "unknown pile id %d", pile_id);
+    if (!out) return fail(w, DEM_ERR_ARG, "NULL output");
+    if ((int)w->reads.size() >= DEM_MAX_ASYNC_READS)
+        return fail(w, DEM_ERR_ARG, "%d asynchronous reads pending: call dem_read_wait", DEM_MAX_ASYNC_READS);
+    int64_t a0 = 0;
+    for (int t = 0; t < slot; ++t) a0 += w->piles[t].na;
+    const int64_t A = w->piles[slot].na;
+    const Arrays &D = w->A;
+    const double *src = nullptr;
+    int64_t n = 3 * A;
+    bool ff = w->precision == DEM_MIXED;
+    switch (field) {
+    case DEM_FIELD_COM: src = D.r + 3 * a0; break;
+    case DEM_FIELD_VEL: src = D.v + 3 * a0; break;
+    case DEM_FIELD_QUAT: src = D.q + 4 * a0; n = 4 * A; break;
+    case DEM_FIELD_OMEGA_BODY: src = D.wb + 3 * a0; break;
+    case DEM_FIELD_ACC: src = D.acc + 3 * a0; break;
+    case DEM_FIELD_TORQUE_STORED: src = D.torque + 3 * a0; break;
+    case DEM_FIELD_MASS: src = D.M + a0; n = A; ff = false; break;
+    default: return fail(w, DEM_ERR_ARG, "field %d cannot be read asynchronously", field);
+    }
+    if (n_out < n) return fail(w, DEM_ERR_ARG, "output too small: need %lld doubles", (long long)n);
+    const size_t k = w->reads.size();
+    if (!w->rev[k]) CU(cudaEventCreateWithFlags(&w->rev[k], cudaEventDisableTiming));
+    CU(cudaMemcpyAsync(out, src, 8 * (size_t)n, cudaMemcpyDeviceToHost, w->stream));
+    CU(cudaEventRecord(w->rev[k], w->stream));
+    w->reads.push_back({out, n, ff});
+    return DEM_OK;
+}
+
+dem_status dem_read_wait(dem_world *w)
+{
+    Range range("dem_read_wait");
+    if (!w) return DEM_ERR_ARG;
+    dem_status st = DEM_OK;
+    for (size_t k = 0; k < w->reads.size(); ++k) {
+        if (cudaEventSynchronize(w->rev[k]) != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(w, DEM_ERR_CUDA, "asynchronous read failed");
+            continue;
+        }
+        const auto &r = w->reads[k];
+        if (r.ff)
+            for (int64_t i = 0; i < r.n; ++i) r.out[i] = unpack_ff(r.out[i]);
+    }
+    w->reads.clear();
+    return st;
+}
+
 dem_status dem_write_state(dem_world *w, int32_t pile_id, int32_t field, const double *in,
                            int64_t n_in)
 {
@@ -2153,6 +2211,8 @@ void dem_destroy(dem_world *w)
         else std::free(w->h_stage);
     }
     if (w->ev_flags) cudaEventDestroy(w->ev_flags);
+    for (auto &e : w->rev)
+        if (e) cudaEventDestroy(e);
     for (int k = 0; k < 2; ++k) {
         if (w->kev[k]) cudaEventDestroy(w->kev[k]);
         if (w->sev[k]) cudaEventDestroy(w->sev[k]);

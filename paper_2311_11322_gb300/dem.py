@@ -81,6 +81,8 @@ def load():
         "dem_sync": (i32, [vp]),
         "dem_step_profiled": (i32, [vp, i64, i32, vp]),
         "dem_read_state": (i32, [vp, i32, i32, vp, i64]),
+        "dem_read_state_async": (i32, [vp, i32, i32, vp, i64]),
+        "dem_read_wait": (i32, [vp]),
         "dem_pile_flags": (i32, [vp, i32, C.POINTER(i32)]),
         "dem_remove_pile": (i32, [vp, i32]),
         "dem_set_tuning": (i32, [vp, C.c_char_p, dbl]),
@@ -206,6 +208,7 @@ class World:
             self._check(L.dem_set_allocator(self.w, self._cb[0], self._cb[1], None))
         self.piles = {}
         self._static = {}
+        self._pending = []   # destinations of read_async copies in flight
 
     def _check(self, s):
         if s != DEM_OK:
@@ -294,6 +297,31 @@ class World:
             raise ValueError(f"out must be a C-contiguous float64 array of shape {shape}")
         self._check(self._L.dem_read_state(self.w, pile, fid, _ptr(out), out.size))
         return out
+
+    # fields dem_read_state_async accepts
+    ASYNC_FIELDS = ("COM", "VEL", "QUAT", "OMEGA_BODY", "ACC", "TORQUE_STORED", "MASS")
+
+    def read_async(self, pile, field, out):
+        """Enqueue a read of a per-aggregate state field into `out` (a
+        C-contiguous float64 array of the field's shape, best in pinned memory)
+        and return at once; `out` holds the values after read_wait()."""
+        fid, rows, cols = FIELDS[field]
+        if pile not in self.piles:   # let the library report the unknown id
+            self._check(self._L.dem_read_state_async(self.w, int(pile), fid, None, 0))
+        A = self.piles[pile][0]
+        shape = (A, cols) if cols > 1 else (A,)
+        if out.shape != shape or out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError(f"out must be a C-contiguous float64 array of shape {shape}")
+        self._pending.append(out)   # kept alive until read_wait
+        self._check(self._L.dem_read_state_async(self.w, int(pile), fid, _ptr(out), out.size))
+
+    def read_wait(self):
+        """Wait for the pending read_async copies (not for later steps) and
+        convert them to FP64 in place."""
+        try:
+            self._check(self._L.dem_read_wait(self.w))
+        finally:
+            self._pending.clear()
 
     def write(self, pile, field, values):
         fid = FIELDS[field][0]
