@@ -353,6 +353,24 @@ int sym_tile(dem_world *w)
     return nmax <= kTinyTileMaxN ? kGravSymTileTiny : kGravSymTileSmall;
 }
 
+// Work items in decreasing cost, ties in generation order (a stable sort by
+// cost).  Most items share the largest cost (whole tiles or j-ranges): those
+// are taken first in order, and only the rest is sorted.
+struct GravItem { int4 v; int64_t cost; };
+void order_items(const std::vector<GravItem> &its, std::vector<int4> &out)
+{
+    int64_t top = 0;
+    for (const auto &x : its) top = std::max(top, x.cost);
+    out.reserve(out.size() + its.size());
+    std::vector<GravItem> rest;
+    for (const auto &x : its) {
+        if (x.cost == top) out.push_back(x.v);
+        else rest.push_back(x);
+    }
+    std::stable_sort(rest.begin(), rest.end(), [](const GravItem &x, const GravItem &y) { return x.cost > y.cost; });
+    for (const auto &x : rest) out.push_back(x.v);
+}
+
 GravPlan plan_gravity(dem_world *w)
 {
     GravPlan g;
@@ -364,8 +382,7 @@ GravPlan plan_gravity(dem_world *w)
         const int64_t tile = g.tile = sym_tile(w);
         // items: every pair of tiles (a, b), a <= b; partial rows
         // [b][i] and [T + a][j] (2 T rows of ns) for piles with more than one tile
-        struct It { int4 v; int64_t cost; };
-        std::vector<It> its;
+        std::vector<GravItem> its;
         for (size_t p = 0; p < w->piles.size(); ++p) {
             const PileHost &q = w->piles[p];
             const int64_t T = (q.ns + tile - 1) / tile;
@@ -387,13 +404,11 @@ GravPlan plan_gravity(dem_world *w)
                     its.push_back({make_int4((int)p, (int)ta, (int)tb, 0), nb});
                 }
         }
-        std::stable_sort(its.begin(), its.end(), [](const It &x, const It &y) { return x.cost > y.cost; });
-        for (auto &x : its) g.items.push_back(x.v);
+        order_items(its, g.items);
         return g;
     }
     int BI = w->grav_block * w->grav_ib;
-    struct It { int4 v; int64_t cost; };
-    std::vector<It> its;
+    std::vector<GravItem> its;
     for (size_t p = 0; p < w->piles.size(); ++p) {
         const PileHost &q = w->piles[p];
         int64_t ns = q.ns;
@@ -420,8 +435,7 @@ GravPlan plan_gravity(dem_world *w)
                 its.push_back({make_int4((int)p, (int)i0, (int)j0, (int)j1), j1 - j0});
             }
     }
-    std::stable_sort(its.begin(), its.end(), [](const It &x, const It &y) { return x.cost > y.cost; });
-    for (auto &x : its) g.items.push_back(x.v);
+    order_items(its, g.items);
     return g;
 }
 
