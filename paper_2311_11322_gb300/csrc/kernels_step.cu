@@ -861,9 +861,11 @@ __global__ void k_gather(Arrays a, Sizes z)
     const PileStatic &S = a.ps[p];
     int hl = a.sorted[k];
     int64_t i = S.s0 + hl;
-    // the sorted order changes only at rebuilds: the sorted aggregate ids and
-    // the home -> sorted map (double-buffered by parity) are written in a
-    // rebuild step and the step after it, and read otherwise
+    // the sorted order changes only at rebuilds: the sorted aggregate ids are
+    // written in a rebuild step (and read here otherwise); the home -> sorted
+    // map, which k_cand_link reads at the next rebuild to find each sphere's
+    // previous list, is double-buffered by parity and written in a rebuild
+    // step and the step after it
     const PileDyn &D = a.pd[p];
     const bool fresh = D.rebuild != 0, refresh = fresh || D.rebuilt_prev != 0;
     const int al = fresh ? a.sph_agg[i] : a.sagg[k];
